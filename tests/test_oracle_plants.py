@@ -1,0 +1,33 @@
+"""The oracle's pins must catch plausible mistakes: each planted variant of the oracle (a
+compile-time switch in the oracle source, built only here) has to fail at least one pin."""
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+# plant id -> (description, pin calls that must not all pass)
+PLANTS = {
+    1: ("zero margin counted as true", [lambda o: pins.test_fig1b_points(o, 0),
+                                        lambda o: pins.test_dense_form_agrees_on_boundaries(o, 0)]),
+    2: ("'<' evaluated as a negated '>'", [lambda o: pins.test_nan_and_inf_compare_false(o),
+                                           lambda o: pins.test_dense_form_agrees_on_boundaries(o, 1)]),
+    3: ("pair condition reads the wrong feature", [lambda o: pins.test_fig1b_points(o, 0),
+                                                   lambda o: pins.test_dense_form_agrees_on_boundaries(o, 2)]),
+    4: ("last firing rule wins", [lambda o: pins.test_fig1b_points(o, 0)]),
+    5: ("later rules not discounted", [lambda o: pins.test_soft_probabilities_sum_to_one(o)]),
+    6: ("threshold gradient sign", [lambda o: pins.test_one_rule_one_condition_is_logistic_regression(o, 0, False)]),
+    7: ("later outcomes dropped from the adjoint", [lambda o: pins.test_adjoint_matches_central_differences(o, 0)]),
+}
+
+
+@pytest.mark.parametrize("plant", sorted(PLANTS))
+def test_pins_catch_planted_mistake(plant):
+    desc, calls = PLANTS[plant]
+    o = oracle.planted(plant)
+    caught = 0
+    for call in calls:
+        try:
+            call(o)
+        except AssertionError:
+            caught += 1
+    assert caught == len(calls), f"plant {plant} ({desc}) escaped {len(calls) - caught} pin(s)"
