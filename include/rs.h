@@ -1,0 +1,211 @@
+/*
+ * rs.h -- C ABI of the GB300 (sm_103a) rule-set evaluation library (librs.so).
+ *
+ * The library evaluates whole populations of ordered rule sets against a tabular dataset, the
+ * evaluation step of accelerated evolutionary rule-based learning (Shahrzad & Miikkulainen,
+ * "GPU-Accelerated Rule Evaluation and Evolution", GECCO'25 Companion; Sec. 3 and Fig. 1).
+ *
+ *   condition  a*x[f] op t           (threshold)       Sec. 3 / Fig. 1a rows with one weight
+ *              a*x[f] op b*x[g]      (feature pair)    Sec. 3 / Fig. 1a row [0, 1.0, -0.38, ...]
+ *              op is '>' or '<'; each product is one correctly rounded float32 multiply and the
+ *              compare is strict and IEEE-ordered (NaN compares false, a zero margin is false,
+ *              Sec. 3: "clips negative values to zero ... rounds positives to one").
+ *   rule       conjunction of its conditions naming one class (Fig. 1b "&" and "->"); an empty
+ *              rule fires.
+ *   rule set   ordered list of rules (Sec. 1, list-based grammar): the first rule that fires gives
+ *              the class, otherwise the set's default class.
+ *   fitness    classification accuracy (Sec. 1), returned as exact int32 correct counts.
+ *   soft path  sigmoid relaxation for back-propagation fine-tuning of coefficients and thresholds
+ *              with the rule structure kept (Sec. 3, Fig. 1c).
+ *
+ * Conventions
+ *   - Every function returns rs_status (0 = RS_OK, < 0 = error). No exception crosses the ABI.
+ *     rs_last_error() returns a thread-local message for the last failing call of the thread.
+ *   - Pointers are plain host or device addresses as stated per argument. The caller owns every
+ *     buffer; synchronous calls borrow them until the call returns (default contexts) or until
+ *     the work enqueued on `stream` completes (RS_CTX_ASYNC contexts).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - A context is bound to one CUDA device; calls on one context are thread-safe.
+ *   - The library never reads memory outside the sizes given; malformed batches are rejected
+ *     with RS_ERR_INVALID before any count is produced.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rs_status;
+
+#define RS_OK               0
+#define RS_PENDING          1    /* rs_poll: the request has not finished yet */
+#define RS_ERR_INVALID     -1    /* bad argument, index, class or offset array */
+#define RS_ERR_TOO_LARGE   -2    /* a request larger than the whole memory budget or a limit */
+#define RS_ERR_OOM         -3    /* device allocation failed */
+#define RS_ERR_TIMEOUT     -4    /* a bounded device or host wait gave up */
+#define RS_ERR_DEVICE      -5    /* a CUDA error; sticky for the context */
+#define RS_ERR_UNSUPPORTED -6    /* device is not sm_103 / feature not available */
+#define RS_ERR_NOT_FOUND   -7    /* unknown dataset handle or ticket */
+#define RS_ERR_CANCELLED   -8    /* request cancelled before it ran */
+
+/* Limits enforced by the library. */
+#define RS_MAX_FEATURES  4096
+#define RS_MAX_CLASSES   4096
+
+typedef struct rs_ctx rs_ctx;
+
+#define RS_CTX_ASYNC        1u   /* eval calls return after enqueue; device-side errors are
+                                    reported by rs_check (sticky until read) */
+#define RS_CTX_NO_GRAPH     2u   /* launch kernels directly instead of replaying captured graphs */
+#define RS_CTX_NO_AUTOTUNE  4u   /* use the built-in tile heuristic, never time candidates */
+
+typedef struct {
+    int32_t device;              /* CUDA device ordinal */
+    uint32_t flags;              /* RS_CTX_* */
+    uint64_t mem_budget_bytes;   /* serving admission budget; 0 = 40 GiB */
+    const char *autotune_cache;  /* JSON file the autotuner reads at create and writes on update;
+                                    NULL = in-memory only */
+} rs_config;
+
+/* Create a context on cfg->device (cfg may be NULL: device 0, default flags). */
+rs_status rs_create(const rs_config *cfg, rs_ctx **out);
+/* Destroy a context: waits for its serving work, frees every dataset and cached graph. */
+rs_status rs_destroy(rs_ctx *ctx);
+/* Thread-local description of the last error of the calling thread ("" if none). */
+const char *rs_last_error(void);
+/* Library version string. */
+const char *rs_version(void);
+/* Synchronize `stream` and return (and clear) the first device-side error recorded by calls of
+ * an RS_CTX_ASYNC context; RS_OK if none. */
+rs_status rs_check(rs_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------------------------------ datasets */
+
+#define RS_MEM_HOST   0          /* arrays are host memory (pageable or pinned) */
+#define RS_MEM_DEVICE 1          /* arrays are device memory of the context's device */
+
+/*
+ * Register a dataset (Sec. 3: "GPU experiments loading candidates" -- the data stays resident
+ * while any number of populations is evaluated against it).
+ *   X      float32, row-major N x F (sample n, feature f at X[n*F + f]); host or device per `mem`
+ *   y      int32[N], labels in 0..K-1
+ *   N >= 1, 1 <= F <= RS_MAX_FEATURES, 1 <= K <= RS_MAX_CLASSES
+ * The library keeps its own copy (feature-major, samples grouped by label); the caller may free X
+ * and y when the call returns. Errors: RS_ERR_INVALID (sizes, a label out of range), RS_ERR_OOM.
+ * On success *ds_out receives a non-zero handle.
+ */
+rs_status rs_dataset_create(rs_ctx *ctx, const float *X, const int32_t *y, int64_t N, int32_t F,
+                            int32_t K, int32_t mem, void *stream, uint64_t *ds_out);
+rs_status rs_dataset_destroy(rs_ctx *ctx, uint64_t ds);
+/* Shape of a dataset; class_count (host, int64[K]) may be NULL. */
+rs_status rs_dataset_info(rs_ctx *ctx, uint64_t ds, int64_t *N, int32_t *F, int32_t *K,
+                          int64_t *class_count);
+
+/* --------------------------------------------------------------------------- rule sets */
+
+/*
+ * A population of P ordered rule sets in CSR form (Sec. 3 / Fig. 1a, one record per condition
+ * instead of a dense row). All arrays live in host or device memory according to `mem`.
+ *   set_rule_off  int32[P+1]  rules of set p: [set_rule_off[p], set_rule_off[p+1]); [0]=0, [P]=R
+ *   rule_cond_off int32[R+1]  conditions of rule r: [rule_cond_off[r], rule_cond_off[r+1]);
+ *                             [0]=0, [R]=C; non-decreasing
+ *   rule_class    int32[R]    class named by rule r, 0..K-1
+ *   set_default   int32[P]    class of set p when no rule fires, 0..K-1
+ *   cond_f        int32[C]    feature of the left-hand product, 0..F-1
+ *   cond_g        int32[C]    -1: threshold condition a*x[f] op t; else 0..F-1: a*x[f] op b*x[g]
+ *   cond_op       int8[C]     0: '>', 1: '<'
+ *   cond_a, cond_b, cond_t  float32[C]   (b unused for thresholds, t unused for pairs)
+ * P >= 0, R >= 0, C >= 0; P, R, C < 2^31 - 1.
+ */
+typedef struct {
+    int32_t P, R, C;
+    int32_t mem;
+    const int32_t *set_rule_off;
+    const int32_t *rule_cond_off;
+    const int32_t *rule_class;
+    const int32_t *set_default;
+    const int32_t *cond_f;
+    const int32_t *cond_g;
+    const int8_t *cond_op;
+    const float *cond_a;
+    const float *cond_b;
+    const float *cond_t;
+} rs_batch;
+
+/* ------------------------------------------------------------------------ hard evaluation */
+
+/*
+ * Exact first-fire evaluation of every set of `batch` on every sample of dataset `ds`
+ * (Sec. 3 inequalities + hard activation, Fig. 1b conjunction and rule order, Sec. 1 fitness).
+ *   correct    int32[P]     #{n : pred_p(n) = y_n}
+ *   per_class  int32[P*K]   #{n : pred_p(n) = y_n = k} at [p*K + k]; may be NULL
+ *   preds      int32[P*N]   pred_p(n) at [p*N + n] in the caller's sample order; may be NULL
+ * Outputs live in the memory space given by batch->mem (host buffers: the library copies).
+ * Results are bit-identical to the plain definition (no FMA, no flush-to-zero).
+ * Errors: RS_ERR_INVALID (malformed batch: nothing is counted, outputs undefined),
+ *         RS_ERR_NOT_FOUND (ds), RS_ERR_OOM, RS_ERR_DEVICE.
+ */
+rs_status rs_eval_hard(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,
+                       int32_t *per_class, int32_t *preds, void *stream);
+
+/* ------------------------------------------------------------------------- soft evaluation */
+
+/*
+ * Sigmoid-relaxed forward (Sec. 3, "a differentiable activation function (e.g., sigmoid)").
+ * Per condition u = s*(a*x[f] - rhs)/tau with s = +1 for '>' and -1 for '<', rhs = t or b*x[g];
+ * rule firing probability q_r = prod_c sigmoid(u_c); rule r decides with probability
+ * q_r * prod_{j<r} (1 - q_j); the default class takes prod_j (1 - q_j);
+ *   loss[p] = (1/N) sum_n -log p_p(y_n | x_n)      float32[P]
+ *   probs   float32[P*N*K] class probabilities at [(p*N + n)*K + k] (caller's sample order);
+ *           may be NULL
+ * Computed in float32 in the log domain. tau > 0.
+ */
+rs_status rs_eval_soft_fwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float tau,
+                           float *loss, float *probs, void *stream);
+
+/*
+ * Adjoint of rs_eval_soft_fwd (Sec. 3 back-propagation; Fig. 1c shows coefficients and thresholds
+ * moving). Given dloss float32[P] (dObjective/dloss[p]) it writes, for every condition c,
+ *   grad_a[c] = sum_p dloss[p] * dloss[p]/da_c,  grad_b[c] (pairs; 0 for thresholds),
+ *   grad_t[c] (thresholds; 0 for pairs)          float32[C] each
+ * and, if loss != NULL, the forward loss float32[P]. The forward is recomputed in the same pass.
+ * Reductions over samples use a fixed order: repeated calls give bit-identical results.
+ */
+rs_status rs_eval_soft_bwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float tau,
+                           const float *dloss, float *grad_a, float *grad_b, float *grad_t,
+                           float *loss, void *stream);
+
+/* ---------------------------------------------------------------------------- tile tuning */
+
+/* Number of compiled tile configurations of the hard evaluator. */
+int32_t rs_tile_config_count(void);
+/* Describe configuration `id`: samples per CTA tile, warps per CTA, samples per lane. */
+rs_status rs_tile_config_info(int32_t id, int32_t *samples_per_tile, int32_t *warps,
+                              int32_t *samples_per_lane);
+/* Force configuration `id` for every following hard evaluation of the context (-1 = automatic:
+ * autotuned table, else heuristic). */
+rs_status rs_set_tile_config(rs_ctx *ctx, int32_t id);
+/* Time every configuration on this dataset and batch (device pointers), record the fastest in the
+ * context's table (and its JSON cache file) and return its id in *best. */
+rs_status rs_autotune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, void *stream,
+                      int32_t *best);
+
+/* ---------------------------------------------------------------------------- test hooks */
+
+/*
+ * Self-check of the exact threshold rewrite used by the hard evaluator: for each (a[i], t[i],
+ * op[i]) (host arrays, n entries) and every one of the 2^32 float32 bit patterns x, compare
+ * fl(a*x) op t against the rewritten single compare. *mismatches (host) receives the total count.
+ */
+rs_status rs_selftest_threshold_rewrite(rs_ctx *ctx, const float *a, const float *t,
+                                        const int8_t *op, int32_t n, uint64_t *mismatches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H */

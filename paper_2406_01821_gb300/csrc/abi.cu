@@ -1,0 +1,230 @@
+// extern "C" entry points declared in include/rs.h. Every function converts exceptions and CUDA
+// errors into rs_status and never lets a C++ exception cross the boundary.
+#include <new>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+const char *last_error();
+rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, int32_t F,
+                         int32_t K, int32_t mem, cudaStream_t stream, uint64_t *out);
+rs_status dataset_destroy(Ctx *ctx, uint64_t h);
+rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
+                    int32_t *per_class, int32_t *preds, cudaStream_t stream, int tile_override);
+rs_status eval_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, float *loss,
+                    float *probs, const float *dloss, float *ga, float *gb, float *gt,
+                    cudaStream_t stream);
+rs_status autotune(Ctx *ctx, uint64_t ds_h, const rs_batch *b, cudaStream_t stream, int32_t *best);
+rs_status check_async(Ctx *ctx, cudaStream_t stream);
+rs_status selftest_rewrite(const float *a_h, const float *t_h, const int8_t *op_h, int n,
+                           uint64_t *mismatches, int sm_count);
+void load_tune_table(Ctx *ctx);
+void server_shutdown(Ctx *ctx);
+}  // namespace rs
+
+using namespace rs;
+
+#define RS_GUARD(...)                                                    \
+    try {                                                                \
+        __VA_ARGS__                                                      \
+    } catch (const std::bad_alloc &) {                                   \
+        set_error("host allocation failed");                             \
+        return RS_ERR_OOM;                                               \
+    } catch (...) {                                                      \
+        set_error("internal error");                                     \
+        return RS_ERR_DEVICE;                                            \
+    }
+
+static cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char *rs_last_error(void) { return rs::last_error(); }
+const char *rs_version(void) { return "rulesgpu 0.1 (sm_103a)"; }
+
+rs_status rs_create(const rs_config *cfg, rs_ctx **out)
+{
+    RS_GUARD({
+        if (!out) { set_error("out is NULL"); return RS_ERR_INVALID; }
+        *out = nullptr;
+        rs_config c{0, 0, 0, nullptr};
+        if (cfg) c = *cfg;
+        int ndev = 0;
+        cudaError_t e = cudaGetDeviceCount(&ndev);
+        if (e != cudaSuccess || ndev == 0) {
+            cudaGetLastError();
+            set_error("no CUDA device available");
+            return RS_ERR_UNSUPPORTED;
+        }
+        if (c.device < 0 || c.device >= ndev) { set_error("bad device %d", c.device); return RS_ERR_INVALID; }
+        RS_CUDA(cudaSetDevice(c.device));
+        cudaDeviceProp prop;
+        RS_CUDA(cudaGetDeviceProperties(&prop, c.device));
+        if (!(prop.major == 10 && prop.minor == 3)) {
+            set_error("device %d is sm_%d%d; this library is built for sm_103a", c.device, prop.major, prop.minor);
+            return RS_ERR_UNSUPPORTED;
+        }
+        auto *ctx = new rs_ctx();
+        ctx->device = c.device;
+        ctx->flags = c.flags;
+        ctx->sm_count = prop.multiProcessorCount;
+        ctx->smem_optin = prop.sharedMemPerBlockOptin;
+        ctx->budget = c.mem_budget_bytes ? c.mem_budget_bytes : (40ull << 30);
+        if (c.autotune_cache) ctx->autotune_path = c.autotune_cache;
+        if (cudaMalloc(&ctx->d_sticky, sizeof(uint32_t)) != cudaSuccess ||
+            cudaMemset(ctx->d_sticky, 0, sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            set_error("cannot allocate the context status word");
+            return RS_ERR_OOM;
+        }
+        // keep freed stream-ordered scratch in the pool instead of returning it to the OS
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, c.device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+        if (!(ctx->flags & RS_CTX_NO_AUTOTUNE)) load_tune_table(ctx);
+        *out = ctx;
+        return RS_OK;
+    })
+}
+
+rs_status rs_destroy(rs_ctx *ctx)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        cudaSetDevice(ctx->device);
+        server_shutdown(ctx);
+        cudaDeviceSynchronize();
+        std::vector<uint64_t> ids;
+        for (auto &kv : ctx->datasets) ids.push_back(kv.first);
+        for (auto id : ids) dataset_destroy(ctx, id);
+        ctx->graphs.clear();
+        cudaFree(ctx->d_sticky);
+        delete ctx;
+        return RS_OK;
+    })
+}
+
+rs_status rs_check(rs_ctx *ctx, void *stream)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return check_async(ctx, S(stream));
+    })
+}
+
+rs_status rs_dataset_create(rs_ctx *ctx, const float *X, const int32_t *y, int64_t N, int32_t F,
+                            int32_t K, int32_t mem, void *stream, uint64_t *ds_out)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return dataset_create(ctx, X, y, N, F, K, mem, S(stream), ds_out);
+    })
+}
+
+rs_status rs_dataset_destroy(rs_ctx *ctx, uint64_t ds)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return dataset_destroy(ctx, ds);
+    })
+}
+
+rs_status rs_dataset_info(rs_ctx *ctx, uint64_t ds, int64_t *N, int32_t *F, int32_t *K,
+                          int64_t *class_count)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        auto d = find_dataset(ctx, ds);
+        if (!d) { set_error("unknown dataset"); return RS_ERR_NOT_FOUND; }
+        if (N) *N = d->N;
+        if (F) *F = d->F;
+        if (K) *K = d->K;
+        if (class_count)
+            for (int k = 0; k < d->K; ++k) class_count[k] = d->class_count[k];
+        return RS_OK;
+    })
+}
+
+rs_status rs_eval_hard(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,
+                       int32_t *per_class, int32_t *preds, void *stream)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return eval_hard(ctx, ds, batch, correct, per_class, preds, S(stream), -1);
+    })
+}
+
+rs_status rs_eval_soft_fwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float tau,
+                           float *loss, float *probs, void *stream)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        if (!loss) { set_error("loss is NULL"); return RS_ERR_INVALID; }
+        return eval_soft(ctx, ds, batch, tau, loss, probs, nullptr, nullptr, nullptr, nullptr,
+                         S(stream));
+    })
+}
+
+rs_status rs_eval_soft_bwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float tau,
+                           const float *dloss, float *grad_a, float *grad_b, float *grad_t,
+                           float *loss, void *stream)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        if (!dloss) { set_error("dloss is NULL"); return RS_ERR_INVALID; }
+        return eval_soft(ctx, ds, batch, tau, loss, nullptr, dloss, grad_a, grad_b, grad_t,
+                         S(stream));
+    })
+}
+
+int32_t rs_tile_config_count(void) { return tile_config_count(); }
+
+rs_status rs_tile_config_info(int32_t id, int32_t *samples_per_tile, int32_t *warps,
+                              int32_t *samples_per_lane)
+{
+    if (id < 0 || id >= tile_config_count()) { set_error("bad tile config %d", id); return RS_ERR_INVALID; }
+    const TileConfig &t = tile_config(id);
+    if (samples_per_tile) *samples_per_tile = t.S();
+    if (warps) *warps = t.W;
+    if (samples_per_lane) *samples_per_lane = t.V;
+    return RS_OK;
+}
+
+rs_status rs_set_tile_config(rs_ctx *ctx, int32_t id)
+{
+    if (!ctx) return RS_ERR_INVALID;
+    if (id < -1 || id >= tile_config_count()) { set_error("bad tile config %d", id); return RS_ERR_INVALID; }
+    ctx->forced_tile = id;
+    return RS_OK;
+}
+
+rs_status rs_autotune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, void *stream, int32_t *best)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return autotune(ctx, ds, batch, S(stream), best);
+    })
+}
+
+rs_status rs_selftest_threshold_rewrite(rs_ctx *ctx, const float *a, const float *t,
+                                        const int8_t *op, int32_t n, uint64_t *mismatches)
+{
+    RS_GUARD({
+        if (!ctx || !a || !t || !op || !mismatches || n < 1) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return selftest_rewrite(a, t, op, n, mismatches, ctx->sm_count);
+    })
+}
+
+}  // extern "C"

@@ -1,0 +1,474 @@
+// Orchestration of one evaluation call: argument checks, host staging, scratch, packing, tile
+// configuration choice (autotuned table or heuristic), optional CUDA-graph replay, status check.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <fstream>
+#include <sstream>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+
+rs_status selftest_rewrite(const float *a_h, const float *t_h, const int8_t *op_h, int n,
+                           uint64_t *mismatches, int sm_count);
+
+// ------------------------------------------------------------------------ batch checks / staging
+
+static rs_status check_batch(const rs_batch *b)
+{
+    if (!b) { set_error("batch is NULL"); return RS_ERR_INVALID; }
+    if (b->P < 0 || b->R < 0 || b->C < 0 || b->P == INT32_MAX || b->R == INT32_MAX || b->C == INT32_MAX) {
+        set_error("negative batch sizes (P=%d R=%d C=%d)", b->P, b->R, b->C);
+        return RS_ERR_INVALID;
+    }
+    if (b->mem != RS_MEM_HOST && b->mem != RS_MEM_DEVICE) { set_error("bad batch mem kind"); return RS_ERR_INVALID; }
+    if (!b->set_rule_off || !b->rule_cond_off) { set_error("offset arrays are NULL"); return RS_ERR_INVALID; }
+    if (b->P > 0 && !b->set_default) { set_error("set_default is NULL"); return RS_ERR_INVALID; }
+    if (b->R > 0 && !b->rule_class) { set_error("rule_class is NULL"); return RS_ERR_INVALID; }
+    if (b->C > 0 && (!b->cond_f || !b->cond_g || !b->cond_op || !b->cond_a || !b->cond_b || !b->cond_t)) {
+        set_error("condition arrays are NULL");
+        return RS_ERR_INVALID;
+    }
+    return RS_OK;
+}
+
+// Device copy of a batch: either the caller's device pointers or a staged copy of host arrays.
+struct StagedBatch {
+    BatchDev d{};
+    void *buf = nullptr;
+};
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static rs_status stage_batch(const rs_batch *b, cudaStream_t stream, StagedBatch &out)
+{
+    out.d.P = b->P; out.d.R = b->R; out.d.C = b->C;
+    if (b->mem == RS_MEM_DEVICE) {
+        out.d.set_rule_off = b->set_rule_off; out.d.rule_cond_off = b->rule_cond_off;
+        out.d.rule_class = b->rule_class; out.d.set_default = b->set_default;
+        out.d.cond_f = b->cond_f; out.d.cond_g = b->cond_g; out.d.cond_op = b->cond_op;
+        out.d.cond_a = b->cond_a; out.d.cond_b = b->cond_b; out.d.cond_t = b->cond_t;
+        return RS_OK;
+    }
+    const size_t P = b->P, R = b->R, C = b->C;
+    size_t off[10], sz[10] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C};
+    const void *src[10] = {b->set_rule_off, b->rule_cond_off, b->rule_class, b->set_default,
+                           b->cond_f, b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t};
+    size_t total = 0;
+    for (int i = 0; i < 10; ++i) { off[i] = total; total = align_up(total + sz[i], 256); }
+    RS_CUDA(cudaMallocAsync(&out.buf, std::max<size_t>(total, 256), stream));
+    char *base = static_cast<char *>(out.buf);
+    for (int i = 0; i < 10; ++i)
+        if (sz[i]) RS_CUDA(cudaMemcpyAsync(base + off[i], src[i], sz[i], cudaMemcpyHostToDevice, stream));
+    out.d.set_rule_off = (const int32_t *)(base + off[0]);
+    out.d.rule_cond_off = (const int32_t *)(base + off[1]);
+    out.d.rule_class = (const int32_t *)(base + off[2]);
+    out.d.set_default = (const int32_t *)(base + off[3]);
+    out.d.cond_f = (const int32_t *)(base + off[4]);
+    out.d.cond_g = (const int32_t *)(base + off[5]);
+    out.d.cond_op = (const int8_t *)(base + off[6]);
+    out.d.cond_a = (const float *)(base + off[7]);
+    out.d.cond_b = (const float *)(base + off[8]);
+    out.d.cond_t = (const float *)(base + off[9]);
+    return RS_OK;
+}
+
+// ------------------------------------------------------------------------ tile configuration
+
+static std::string tune_key(const Dataset &ds, const rs_batch *b)
+{
+    const double meanC = b->R > 0 ? (double)b->C / b->R : 0.0;
+    const int cb = (int)std::lround(std::min(meanC, 16.0) * 2);   // half-condition buckets
+    const int nb = (int)std::floor(std::log2((double)ds.N));
+    std::ostringstream k;
+    k << "F" << ds.F << "|K" << ds.K << "|C" << cb << "|N" << nb;
+    return k.str();
+}
+
+static int heuristic_tile(const Dataset &ds)
+{
+    // 128-sample tiles with 8 warps when the feature tile fits three CTAs per SM; smaller tiles
+    // for wide data.
+    static const int prefs[] = {0, 3, 5};
+    for (int id : prefs)
+        if (tile_config_fits(tile_config(id), ds.F)) return id;
+    return 5;
+}
+
+static int pick_tile(Ctx *ctx, const Dataset &ds, const rs_batch *b)
+{
+    if (ctx->forced_tile >= 0 && tile_config_fits(tile_config(ctx->forced_tile), ds.F))
+        return ctx->forced_tile;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->tune_table.find(tune_key(ds, b));
+        if (it != ctx->tune_table.end() && tile_config_fits(tile_config(it->second), ds.F))
+            return it->second;
+    }
+    return heuristic_tile(ds);
+}
+
+void load_tune_table(Ctx *ctx)
+{
+    if (ctx->autotune_path.empty()) return;
+    std::ifstream in(ctx->autotune_path);
+    if (!in) return;
+    // minimal reader for {"key": id, ...}
+    std::string s((std::istreambuf_iterator<char>(in)), std::istreambuf_iterator<char>());
+    size_t i = 0;
+    while (true) {
+        size_t q0 = s.find('"', i);
+        if (q0 == std::string::npos) break;
+        size_t q1 = s.find('"', q0 + 1);
+        if (q1 == std::string::npos) break;
+        size_t colon = s.find(':', q1);
+        if (colon == std::string::npos) break;
+        int id = std::atoi(s.c_str() + colon + 1);
+        if (id >= 0 && id < tile_config_count()) ctx->tune_table[s.substr(q0 + 1, q1 - q0 - 1)] = id;
+        i = colon + 1;
+    }
+}
+
+static void save_tune_table(Ctx *ctx)
+{
+    if (ctx->autotune_path.empty()) return;
+    std::ofstream out(ctx->autotune_path + ".tmp");
+    out << "{";
+    bool first = true;
+    for (auto &kv : ctx->tune_table) {
+        out << (first ? "" : ",") << "\n  \"" << kv.first << "\": " << kv.second;
+        first = false;
+    }
+    out << "\n}\n";
+    out.close();
+    std::rename((ctx->autotune_path + ".tmp").c_str(), ctx->autotune_path.c_str());
+}
+
+// ------------------------------------------------------------------------ the call
+
+struct Scratch {
+    Rec *recs = nullptr;
+    SetInfo *sets = nullptr;
+    int32_t *order = nullptr;
+    uint32_t *status = nullptr;
+    int32_t *out_dev = nullptr;   // device outputs when the caller's are host memory
+};
+
+static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t N, bool per_class,
+                               bool preds, cudaStream_t stream, Scratch &s)
+{
+    size_t rec_b = align_up(sizeof(Rec) * std::max(b.C, 1), 256);
+    size_t set_b = align_up(sizeof(SetInfo) * std::max(b.P, 1), 256);
+    size_t ord_b = align_up(sizeof(int32_t) * std::max(b.P, 1), 256);
+    size_t st_b = 256;
+    size_t out_b = 0;
+    if (host_out) {
+        out_b = align_up(sizeof(int32_t) * b.P, 256);
+        if (per_class) out_b += align_up(sizeof(int32_t) * (size_t)b.P * K, 256);
+        if (preds) out_b += align_up(sizeof(int32_t) * (size_t)b.P * N, 256);
+    }
+    char *base = nullptr;
+    RS_CUDA(cudaMallocAsync(&base, rec_b + set_b + ord_b + st_b + out_b, stream));
+    s.recs = (Rec *)base;
+    s.sets = (SetInfo *)(base + rec_b);
+    s.order = (int32_t *)(base + rec_b + set_b);
+    s.status = (uint32_t *)(base + rec_b + set_b + ord_b);
+    s.out_dev = host_out ? (int32_t *)(base + rec_b + set_b + ord_b + st_b) : nullptr;
+    RS_CUDA(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream));
+    return RS_OK;
+}
+
+// Enqueue pack + evaluation (the part a graph captures).
+static rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
+                              const Scratch &s, int32_t *correct, int32_t *per_class,
+                              int32_t *preds, cudaStream_t stream)
+{
+    PackOut po{s.recs, s.sets, s.order, s.status};
+    launch_pack(bd, ds->F, ds->K, po, stream);
+    RS_CUDA(cudaGetLastError());
+    HardArgs a{};
+    a.recs = s.recs;
+    a.sets = s.sets;
+    a.order = s.order;
+    a.P = bd.P;
+    a.y = ds->y;
+    a.perm = ds->perm;
+    a.N = ds->N;
+    a.n_pad = ds->n_pad;
+    a.F = ds->F;
+    a.K = ds->K;
+    a.correct = correct;
+    a.per_class = per_class;
+    a.preds = preds;
+    a.groups = choose_groups(ctx, ds, tc, bd.P);
+    a.status = s.status;
+    return launch_hard(ctx, ds, tc, a, stream);
+}
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    ~GraphEntry() { if (exec) cudaGraphExecDestroy(exec); }
+};
+
+rs_status finish_status(Ctx *ctx, const uint32_t *d_status, cudaStream_t stream);
+
+__global__ void k_merge_status(const uint32_t *src, uint32_t *dst)
+{
+    if (*src) atomicOr(dst, *src);
+}
+
+rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
+                    int32_t *per_class, int32_t *preds, cudaStream_t stream, int tile_override)
+{
+    rs_status rc = check_batch(b);
+    if (rc) return rc;
+    if (!correct) { set_error("correct is NULL"); return RS_ERR_INVALID; }
+    auto ds = find_dataset(ctx, ds_h);
+    if (!ds) { set_error("unknown dataset %llu", (unsigned long long)ds_h); return RS_ERR_NOT_FOUND; }
+    if ((rc = device_guard(ctx))) return rc;
+    if (b->R > 0 && ds->K > 4096) return RS_ERR_UNSUPPORTED;
+
+    const bool host = b->mem == RS_MEM_HOST;
+    StagedBatch sb;
+    if ((rc = stage_batch(b, stream, sb))) return rc;
+    Scratch s;
+    if ((rc = alloc_scratch(sb.d, host, ds->K, ds->N, per_class != nullptr, preds != nullptr, stream, s))) {
+        if (sb.buf) cudaFreeAsync(sb.buf, stream);
+        return rc;
+    }
+    int32_t *d_correct = correct, *d_pc = per_class, *d_preds = preds;
+    if (host) {
+        d_correct = s.out_dev;
+        char *p = (char *)(s.out_dev) + align_up(sizeof(int32_t) * b->P, 256);
+        if (per_class) { d_pc = (int32_t *)p; p += align_up(sizeof(int32_t) * (size_t)b->P * ds->K, 256); }
+        if (preds) d_preds = (int32_t *)p;
+    }
+    const int tid = tile_override >= 0 ? tile_override : pick_tile(ctx, *ds, b);
+    const TileConfig &tc = tile_config(tid);
+
+    // Graph replay needs a capturable stream: not the legacy default stream, and not a stream the
+    // caller is capturing already (then the work simply joins the caller's graph).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (stream) RS_CUDA(cudaStreamIsCapturing(stream, &cap));
+    const bool use_graph = !(ctx->flags & RS_CTX_NO_GRAPH) && tile_override < 0 && stream != nullptr &&
+                           cap == cudaStreamCaptureStatusNone;
+    if (use_graph) {
+        // Capture pack + evaluate, then update the cached executable for this shape bucket
+        // (same topology -> in-place parameter update; otherwise re-instantiate).
+        std::ostringstream key;
+        key << "ds" << ds_h << "|t" << tid << "|s" << (uintptr_t)stream << "|pc" << (per_class != nullptr)
+            << "|pr" << (preds != nullptr) << "|P" << (b->P > 0) << "|R" << (b->R > 0);
+        cudaGraph_t g = nullptr;
+        RS_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        rs_status erc = enqueue_hard(ctx, ds.get(), tc, sb.d, s, d_correct, d_pc, d_preds, stream);
+        cudaError_t ce = cudaStreamEndCapture(stream, &g);
+        if (erc) { if (g) cudaGraphDestroy(g); return erc; }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        std::shared_ptr<GraphEntry> ge;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            auto &slot = ctx->graphs[key.str()];
+            if (!slot) slot = std::make_shared<GraphEntry>();
+            ge = slot;
+        }
+        bool ok = false;
+        if (ge->exec) {
+            cudaGraphExecUpdateResultInfo info;
+            ok = cudaGraphExecUpdate(ge->exec, g, &info) == cudaSuccess;
+            if (!ok) cudaGetLastError();
+        }
+        if (!ok) {
+            if (ge->exec) { cudaGraphExecDestroy(ge->exec); ge->exec = nullptr; }
+            cudaError_t ie = cudaGraphInstantiate(&ge->exec, g, 0);
+            if (ie != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ie, "cudaGraphInstantiate"); }
+        }
+        cudaGraphDestroy(g);
+        RS_CUDA(cudaGraphLaunch(ge->exec, stream));
+    } else {
+        if ((rc = enqueue_hard(ctx, ds.get(), tc, sb.d, s, d_correct, d_pc, d_preds, stream))) return rc;
+    }
+    if (host) {
+        RS_CUDA(cudaMemcpyAsync(correct, d_correct, sizeof(int32_t) * b->P, cudaMemcpyDeviceToHost, stream));
+        if (per_class)
+            RS_CUDA(cudaMemcpyAsync(per_class, d_pc, sizeof(int32_t) * (size_t)b->P * ds->K,
+                                    cudaMemcpyDeviceToHost, stream));
+        if (preds)
+            RS_CUDA(cudaMemcpyAsync(preds, d_preds, sizeof(int32_t) * (size_t)b->P * ds->N,
+                                    cudaMemcpyDeviceToHost, stream));
+    }
+    rc = finish_status(ctx, s.status, stream);
+    cudaFreeAsync(s.recs, stream);
+    if (sb.buf) cudaFreeAsync(sb.buf, stream);
+    return rc;
+}
+
+// Synchronous contexts: wait and report the device status word of this call. Asynchronous
+// contexts: fold it into the context's sticky word (read by rs_check) and return immediately.
+rs_status finish_status(Ctx *ctx, const uint32_t *d_status, cudaStream_t stream)
+{
+    if (ctx->flags & RS_CTX_ASYNC) {
+        k_merge_status<<<1, 1, 0, stream>>>(d_status, ctx->d_sticky);
+        RS_CUDA(cudaGetLastError());
+        return RS_OK;
+    }
+    uint32_t *hs = host_status_slot();
+    if (!hs) return RS_ERR_OOM;
+    RS_CUDA(cudaMemcpyAsync(hs, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    RS_CUDA(cudaStreamSynchronize(stream));
+    if (*hs) {
+        set_error("batch rejected: %s", status_text(*hs).c_str());
+        return (*hs & (ST_WAIT_TIMEOUT | ST_QUEUE_TIMEOUT)) ? RS_ERR_TIMEOUT : RS_ERR_INVALID;
+    }
+    return RS_OK;
+}
+
+rs_status check_async(Ctx *ctx, cudaStream_t stream)
+{
+    RS_CUDA(cudaStreamSynchronize(stream));
+    uint32_t h = 0;
+    RS_CUDA(cudaMemcpy(&h, ctx->d_sticky, sizeof(h), cudaMemcpyDeviceToHost));
+    RS_CUDA(cudaMemset(ctx->d_sticky, 0, sizeof(uint32_t)));
+    if (h) {
+        set_error("device reported: %s", status_text(h).c_str());
+        return (h & (ST_WAIT_TIMEOUT | ST_QUEUE_TIMEOUT)) ? RS_ERR_TIMEOUT : RS_ERR_INVALID;
+    }
+    return RS_OK;
+}
+
+// ------------------------------------------------------------------------ autotuner
+
+rs_status autotune(Ctx *ctx, uint64_t ds_h, const rs_batch *b, cudaStream_t stream, int32_t *best)
+{
+    rs_status rc = check_batch(b);
+    if (rc) return rc;
+    if (b->mem != RS_MEM_DEVICE) { set_error("rs_autotune takes a device batch"); return RS_ERR_INVALID; }
+    auto ds = find_dataset(ctx, ds_h);
+    if (!ds) return RS_ERR_NOT_FOUND;
+    if ((rc = device_guard(ctx))) return rc;
+    int32_t *correct = nullptr;
+    RS_CUDA(cudaMalloc(&correct, sizeof(int32_t) * std::max(1, b->P)));
+    cudaEvent_t e0, e1;
+    RS_CUDA(cudaEventCreate(&e0));
+    RS_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best_id = -1;
+    for (int id = 0; id < tile_config_count(); ++id) {
+        if (!tile_config_fits(tile_config(id), ds->F)) continue;
+        // one warm-up, then the best of two timed runs
+        if ((rc = eval_hard(ctx, ds_h, b, correct, nullptr, nullptr, stream, id))) break;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, stream);
+            if ((rc = eval_hard(ctx, ds_h, b, correct, nullptr, nullptr, stream, id))) break;
+            cudaEventRecord(e1, stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_min = std::min(ms_min, ms);
+        }
+        if (rc) break;
+        if (ms_min < best_ms) { best_ms = ms_min; best_id = id; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(correct);
+    if (rc) return rc;
+    if (best_id < 0) { set_error("no tile configuration fits F=%d", ds->F); return RS_ERR_UNSUPPORTED; }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->tune_table[tune_key(*ds, b)] = best_id;
+        save_tune_table(ctx);
+    }
+    if (best) *best = best_id;
+    return RS_OK;
+}
+
+// ------------------------------------------------------------------------ soft
+
+rs_status eval_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, float *loss,
+                    float *probs, const float *dloss, float *ga, float *gb, float *gt,
+                    cudaStream_t stream)
+{
+    rs_status rc = check_batch(b);
+    if (rc) return rc;
+    if (!(tau > 0.f) || !std::isfinite(tau)) { set_error("tau must be finite and > 0"); return RS_ERR_INVALID; }
+    auto ds = find_dataset(ctx, ds_h);
+    if (!ds) { set_error("unknown dataset %llu", (unsigned long long)ds_h); return RS_ERR_NOT_FOUND; }
+    if ((rc = device_guard(ctx))) return rc;
+    const bool host = b->mem == RS_MEM_HOST;
+    const bool bwd = dloss != nullptr;
+    if (bwd && b->C > 0 && (!ga || !gb || !gt)) { set_error("gradient outputs are NULL"); return RS_ERR_INVALID; }
+    StagedBatch sb;
+    if ((rc = stage_batch(b, stream, sb))) return rc;
+    // device-side outputs (+ staged dloss)
+    const size_t P = b->P, C = b->C;
+    float *d_loss = loss, *d_probs = probs, *d_ga = ga, *d_gb = gb, *d_gt = gt;
+    const float *d_dloss = dloss;
+    char *obuf = nullptr;
+    uint32_t *d_status = nullptr;
+    {
+        size_t need = 256;   // status word
+        if (host) {
+            need += align_up(4 * std::max<size_t>(P, 1), 256) * 2;
+            if (probs) need += align_up(4 * P * ds->N * ds->K, 256);
+            if (bwd) need += align_up(4 * std::max<size_t>(C, 1), 256) * 3;
+        }
+        RS_CUDA(cudaMallocAsync(&obuf, need, stream));
+        d_status = (uint32_t *)obuf;
+        char *p = obuf + 256;
+        if (host) {
+            d_loss = (float *)p; p += align_up(4 * std::max<size_t>(P, 1), 256);
+            float *dl = (float *)p; p += align_up(4 * std::max<size_t>(P, 1), 256);
+            if (probs) { d_probs = (float *)p; p += align_up(4 * P * ds->N * ds->K, 256); }
+            if (bwd) {
+                d_ga = (float *)p; p += align_up(4 * std::max<size_t>(C, 1), 256);
+                d_gb = (float *)p; p += align_up(4 * std::max<size_t>(C, 1), 256);
+                d_gt = (float *)p; p += align_up(4 * std::max<size_t>(C, 1), 256);
+                RS_CUDA(cudaMemcpyAsync(dl, dloss, 4 * P, cudaMemcpyHostToDevice, stream));
+                d_dloss = dl;
+            }
+        }
+        RS_CUDA(cudaMemsetAsync(d_status, 0, 4, stream));
+    }
+    float *tmp_loss = nullptr;
+    if (!d_loss) {   // the backward call may omit the loss output
+        RS_CUDA(cudaMallocAsync(&tmp_loss, 4 * std::max<size_t>(P, 1), stream));
+        d_loss = tmp_loss;
+    }
+    SoftArgs a{};
+    a.b = sb.d;
+    a.Xt = ds->Xt;
+    a.y = ds->y;
+    a.perm = ds->perm;
+    a.N = ds->N;
+    a.n_pad = ds->n_pad;
+    a.F = ds->F;
+    a.K = ds->K;
+    a.tau = tau;
+    a.loss = d_loss;
+    a.probs = d_probs;
+    a.dloss = d_dloss;
+    a.grad_a = d_ga;
+    a.grad_b = d_gb;
+    a.grad_t = d_gt;
+    a.status = d_status;
+    rc = launch_soft(ctx, a, stream);
+    if (rc == RS_OK && host) {
+        if (loss) RS_CUDA(cudaMemcpyAsync(loss, d_loss, 4 * P, cudaMemcpyDeviceToHost, stream));
+        if (probs) RS_CUDA(cudaMemcpyAsync(probs, d_probs, 4 * P * ds->N * ds->K, cudaMemcpyDeviceToHost, stream));
+        if (bwd && C) {
+            RS_CUDA(cudaMemcpyAsync(ga, d_ga, 4 * C, cudaMemcpyDeviceToHost, stream));
+            RS_CUDA(cudaMemcpyAsync(gb, d_gb, 4 * C, cudaMemcpyDeviceToHost, stream));
+            RS_CUDA(cudaMemcpyAsync(gt, d_gt, 4 * C, cudaMemcpyDeviceToHost, stream));
+        }
+    }
+    if (rc == RS_OK) rc = finish_status(ctx, d_status, stream);
+    cudaFreeAsync(obuf, stream);
+    if (tmp_loss) cudaFreeAsync(tmp_loss, stream);
+    if (sb.buf) cudaFreeAsync(sb.buf, stream);
+    if (host && rc == RS_OK) RS_CUDA(cudaStreamSynchronize(stream));
+    return rc;
+}
+
+}  // namespace rs

@@ -1,0 +1,305 @@
+// The hard evaluator: exact first-fire evaluation of a population of ordered rule sets.
+//
+// Grid: (sample tile, set group). A CTA stages the feature-major tile x[0..F)[S samples] of the
+// label-grouped dataset into shared memory with one 2-D TMA load per 256 features, then its
+// warps pull sets of the group from a shared counter (most expensive first). A warp evaluates a
+// whole set on the tile: lane l owns samples l*V .. l*V+V-1 and keeps, per sample, a "rule still
+// alive" flag (AND of the rule's conditions so far, seeded with "not yet claimed") and the
+// predicted class. Condition records stream through a per-warp shared-memory stage (32 records,
+// next chunk prefetched into registers) and are read as warp-uniform broadcasts. A rule whose
+// alive flags are all false across the warp skips its remaining conditions; a set whose samples
+// are all claimed stops early. At the end of a set the per-sample hits are bit-sliced with
+// __ballot_sync, popc-reduced and added to the set's int32 counters with one atomic per warp.
+//
+// Compiled without FMA contraction; every product is an explicit round-to-nearest multiply and
+// every compare is an IEEE ordered compare, so results equal the plain definition bit for bit.
+#include "rs_internal.cuh"
+#include "tma.cuh"
+
+namespace rs {
+
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr uint64_t TMA_WAIT_LIMIT_NS = 2000000000ull;   // 2 s
+
+template <int V>
+__device__ __forceinline__ void load_v(const float *p, float (&x)[V])
+{
+    if constexpr (V == 1) {
+        x[0] = p[0];
+    } else if constexpr (V == 2) {
+        float2 t = *reinterpret_cast<const float2 *>(p);
+        x[0] = t.x; x[1] = t.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k += 4) {
+            float4 t = *reinterpret_cast<const float4 *>(p + k);
+            x[k] = t.x; x[k + 1] = t.y; x[k + 2] = t.z; x[k + 3] = t.w;
+        }
+    }
+}
+
+__device__ __forceinline__ uint4 ldg_rec(const Rec *p)
+{
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+template <int V, int W>
+__global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtensorMap tmap, HardArgs a)
+{
+    constexpr int S = 32 * V;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int F = a.F;
+    const int Fb = F < 256 ? F : 256;
+    const int nbox = (F + Fb - 1) / Fb;
+    const int Frows = nbox * Fb;
+    float *xs = reinterpret_cast<float *>(smem);
+    Rec *stage = reinterpret_cast<Rec *>(smem + (size_t)Frows * S * sizeof(float));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(stage + W * 32);
+    int *next = reinterpret_cast<int *>(bar + 1);
+
+    const int tile = blockIdx.x, group = blockIdx.y, G = gridDim.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        *next = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(Frows * S * sizeof(float)));
+        for (int b = 0; b < nbox; ++b) tma_load_2d(xs + (size_t)b * Fb * S, &tmap, tile * S, b * Fb, bar);
+    }
+
+    // Per-lane samples (label-grouped order); padding samples carry label -1 and never count.
+    const int64_t n0 = (int64_t)tile * S + lane * V;
+    int y[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) y[v] = a.y[n0 + v];
+    int perm[V];
+    if (a.preds) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) perm[v] = (n0 + v < a.N) ? a.perm[n0 + v] : 0;
+    }
+    const int64_t t_first = (int64_t)tile * S;
+    const int64_t t_last = min((int64_t)tile * S + S, a.N) - 1;
+    const int kmin = a.y[t_first], kmax = a.y[t_last];   // labels are sorted within the dataset
+
+    if (!mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT_NS)) {
+        if (threadIdx.x == 0) atomicOr(a.status, ST_WAIT_TIMEOUT);
+        mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT_NS);   // let copies in flight land before exit
+        return;
+    }
+
+    const int count = (a.P - group + G - 1) / G;
+    Rec *st = stage + warp * 32;
+    const float *xl = xs + lane * V;
+
+    while (true) {
+        int m = 0;
+        if (lane == 0) m = atomicAdd(next, 1);
+        m = __shfl_sync(FULL, m, 0);
+        if (m >= count) break;
+        const int p = a.order[group + m * G];
+        const SetInfo si = a.sets[p];
+
+        int pred[V];
+        bool unc[V], al[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            pred[v] = si.deflt;
+            unc[v] = y[v] >= 0;
+            al[v] = unc[v];
+        }
+        int i = si.rec_begin;
+        const int re = si.rec_end;
+        int base = i;
+        uint4 pf = make_uint4(0, 0, 0, 0);
+        if (i < re) {
+            if (base + lane < re) reinterpret_cast<uint4 *>(st)[lane] = ldg_rec(a.recs + base + lane);
+            __syncwarp();
+            if (base + 32 + lane < re) pf = ldg_rec(a.recs + base + 32 + lane);
+        }
+        while (i < re) {
+            if (i >= base + 32) {
+                __syncwarp();
+                if (i < base + 64) {
+                    base += 32;
+                    reinterpret_cast<uint4 *>(st)[lane] = pf;
+                } else {
+                    base = i;
+                    if (base + lane < re) reinterpret_cast<uint4 *>(st)[lane] = ldg_rec(a.recs + base + lane);
+                }
+                __syncwarp();
+                pf = make_uint4(0, 0, 0, 0);
+                if (base + 32 + lane < re) pf = ldg_rec(a.recs + base + 32 + lane);
+            }
+            const uint4 raw = reinterpret_cast<const uint4 *>(st)[i - base];
+            const uint32_t meta = raw.x;
+            const int f = (int)(raw.y & 0xFFFFu), g = (int)(raw.y >> 16);
+            const float v0 = __uint_as_float(raw.z), v1 = __uint_as_float(raw.w);
+            const uint32_t kind = rec_kind(meta);
+            float x[V];
+            load_v<V>(xl + f * S, x);
+            if (kind == KIND_GT) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = al[v] && (x[v] > v0);
+            } else if (kind == KIND_LT) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = al[v] && (x[v] < v0);
+            } else if (kind == KIND_PAIR) {
+                float z[V];
+                load_v<V>(xl + g * S, z);
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = al[v] && (__fmul_rn(v0, x[v]) > __fmul_rn(v1, z[v]));
+            } else if (kind == KIND_MGT) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = al[v] && (__fmul_rn(v0, x[v]) > v1);
+            } else if (kind == KIND_MLT) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = al[v] && (__fmul_rn(v0, x[v]) < v1);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = false;
+            }
+            if (rec_last(meta)) {
+                const int cls = rec_cls(meta);
+                bool any_unc = false;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (al[v]) { pred[v] = cls; unc[v] = false; }
+                    any_unc |= unc[v];
+                }
+                if (!__any_sync(FULL, any_unc)) break;
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = unc[v];
+                ++i;
+            } else {
+                bool any_al = false;
+#pragma unroll
+                for (int v = 0; v < V; ++v) any_al |= al[v];
+                if (!__any_sync(FULL, any_al)) {
+                    i += rec_skip(meta) + 1;          // rule cannot fire: jump past it
+#pragma unroll
+                    for (int v = 0; v < V; ++v) al[v] = unc[v];
+                } else {
+                    ++i;
+                }
+            }
+        }
+        __syncwarp();
+
+        // Counts: hit = prediction equals the label (padding has label -1).
+        int hits = 0;
+        bool hit[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            hit[v] = pred[v] == y[v];
+            hits += __popc(__ballot_sync(FULL, hit[v]));
+        }
+        if (lane == 0 && hits) atomicAdd(&a.correct[p], hits);
+        if (a.per_class) {
+            if (kmin == kmax) {
+                if (lane == 0 && hits) atomicAdd(&a.per_class[(int64_t)p * a.K + kmin], hits);
+            } else {
+                for (int k = kmin; k <= kmax; ++k) {
+                    int ck = 0;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) ck += __popc(__ballot_sync(FULL, hit[v] && y[v] == k));
+                    if (lane == 0 && ck) atomicAdd(&a.per_class[(int64_t)p * a.K + k], ck);
+                }
+            }
+        }
+        if (a.preds) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (y[v] >= 0) a.preds[(int64_t)p * a.N + perm[v]] = pred[v];
+        }
+    }
+}
+
+template <int V, int W>
+size_t smem_bytes(int F)
+{
+    const int Fb = F < 256 ? F : 256;
+    const int Frows = ((F + Fb - 1) / Fb) * Fb;
+    return (size_t)Frows * 32 * V * sizeof(float) + (size_t)W * 32 * sizeof(Rec) + 16;
+}
+
+template <int V, int W>
+rs_status launch_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t stream)
+{
+    const size_t smem = smem_bytes<V, W>(a.F);
+    if (smem > ctx->smem_optin) return RS_ERR_TOO_LARGE;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(k_hard<V, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ctx->smem_optin);
+    });
+    if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute(k_hard)");
+    const CUtensorMap *tm = dataset_tmap(ds, 32 * V);
+    if (!tm) return RS_ERR_DEVICE;
+    const int tiles = (int)((a.N + 32 * V - 1) / (32 * V));
+    dim3 grid(tiles, a.groups);
+    k_hard<V, W><<<grid, W * 32, smem, stream>>>(*tm, a);
+    RS_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+// Compiled configurations: (samples per lane, warps per CTA).
+const TileConfig kConfigs[] = {
+    {0, 4, 8}, {1, 4, 4}, {2, 4, 16}, {3, 2, 8}, {4, 2, 16}, {5, 1, 16}, {6, 8, 8}, {7, 8, 4},
+};
+constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
+
+}  // namespace
+
+int tile_config_count() { return kNumConfigs; }
+const TileConfig &tile_config(int id) { return kConfigs[id]; }
+
+bool tile_config_fits(const TileConfig &tc, int F)
+{
+    const int Fb = F < 256 ? F : 256;
+    const int Frows = ((F + Fb - 1) / Fb) * Fb;
+    const size_t smem = (size_t)Frows * tc.S() * sizeof(float) + (size_t)tc.W * 32 * sizeof(Rec) + 16;
+    return smem <= 227 * 1024;
+}
+
+rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,
+                      cudaStream_t stream)
+{
+    if (a.P > 0) RS_CUDA(cudaMemsetAsync(a.correct, 0, sizeof(int32_t) * a.P, stream));
+    if (a.P > 0 && a.per_class)
+        RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
+    if (a.P == 0) return RS_OK;
+    switch (tc.id) {
+    case 0: return launch_t<4, 8>(ctx, ds, a, stream);
+    case 1: return launch_t<4, 4>(ctx, ds, a, stream);
+    case 2: return launch_t<4, 16>(ctx, ds, a, stream);
+    case 3: return launch_t<2, 8>(ctx, ds, a, stream);
+    case 4: return launch_t<2, 16>(ctx, ds, a, stream);
+    case 5: return launch_t<1, 16>(ctx, ds, a, stream);
+    case 6: return launch_t<8, 8>(ctx, ds, a, stream);
+    case 7: return launch_t<8, 4>(ctx, ds, a, stream);
+    default: return RS_ERR_INVALID;
+    }
+}
+
+int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P)
+{
+    const int64_t tiles = (ds->N + tc.S() - 1) / tc.S();
+    // aim for at least ~4 CTAs per SM in total so that warps of late tiles overlap early ones
+    const int64_t want = (int64_t)ctx->sm_count * 4;
+    int64_t g = (want + tiles - 1) / tiles;
+    if (g < 1) g = 1;
+    // keep >= 2 sets per warp in a group so the dynamic counter can balance within the CTA
+    const int64_t gmax = std::max<int64_t>(1, P / (2 * tc.W));
+    if (g > gmax) g = gmax;
+    if (g > 65535) g = 65535;
+    return (int)g;
+}
+
+}  // namespace rs

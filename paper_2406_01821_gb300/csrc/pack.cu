@@ -1,0 +1,236 @@
+// Batch validation and packing: CSR rule sets -> 16-byte condition records + per-set table, and
+// the cost order used to schedule sets (largest first).
+//
+// The exact threshold rewrite. For a finite non-zero coefficient a, the rounded product
+// fl(a*x) is a monotone function of x (non-decreasing for a > 0, non-increasing for a < 0):
+// the exact product is monotone and round-to-nearest is monotone, including in the subnormal
+// and overflow ranges. Hence the set {x : fl(a*x) op t} is an up-set or a down-set of the
+// ordered float32 line and equals {x > c} or {x < c} for one float32 c (NaN x is false in both
+// forms). c is found by binary search over the 2^32 ordered bit patterns, evaluating the
+// condition itself with a correctly rounded multiply, so the rewrite is exact by construction
+// (and checked exhaustively by rs_selftest_threshold_rewrite).
+#include "rs_internal.cuh"
+
+namespace rs {
+
+// Order-preserving map of non-NaN floats to uint32 (-0 and +0 are adjacent).
+__device__ inline uint32_t fkey(float x)
+{
+    uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ inline float keyf(uint32_t k)
+{
+    uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    return __uint_as_float(u);
+}
+
+__device__ inline bool thr_true(float a, float x, float t, int op)
+{
+    float p = __fmul_rn(a, x);
+    return op == 0 ? (p > t) : (p < t);
+}
+
+// Rewrite  fl(a*x) op t  into (kind, v0, v1).
+__device__ void rewrite_threshold(float a, float t, int op, uint32_t &kind, float &v0, float &v1)
+{
+    const float ninf = __uint_as_float(0xFF800000u), pinf = __uint_as_float(0x7F800000u);
+    if (isnan(a) || isnan(t)) { kind = KIND_NEVER; v0 = 0.f; v1 = 0.f; return; }
+    if (a == 0.f || isinf(a)) { kind = op == 0 ? KIND_MGT : KIND_MLT; v0 = a; v1 = t; return; }
+    const bool up = (a > 0.f) == (op == 0);     // condition set is {x > c}
+    uint32_t lo = fkey(ninf), hi = fkey(pinf);
+    if (up) {
+        // false at -inf always; true somewhere iff true at +inf
+        if (!thr_true(a, pinf, t, op)) { kind = KIND_NEVER; v0 = 0.f; v1 = 0.f; return; }
+        while (hi - lo > 1u) {        // invariant: false at lo, true at hi
+            uint32_t mid = lo + (hi - lo) / 2u;
+            if (thr_true(a, keyf(mid), t, op)) hi = mid; else lo = mid;
+        }
+        kind = KIND_GT; v0 = keyf(lo); v1 = 0.f;
+    } else {
+        // false at +inf always; true somewhere iff true at -inf
+        if (!thr_true(a, ninf, t, op)) { kind = KIND_NEVER; v0 = 0.f; v1 = 0.f; return; }
+        while (hi - lo > 1u) {        // invariant: true at lo, false at hi
+            uint32_t mid = lo + (hi - lo) / 2u;
+            if (thr_true(a, keyf(mid), t, op)) lo = mid; else hi = mid;
+        }
+        kind = KIND_LT; v0 = keyf(hi); v1 = 0.f;
+    }
+}
+
+__device__ inline bool rec_eval_scalar(uint32_t kind, float v0, float v1, float x)
+{
+    switch (kind) {
+    case KIND_GT: return x > v0;
+    case KIND_LT: return x < v0;
+    case KIND_MGT: return __fmul_rn(v0, x) > v1;
+    case KIND_MLT: return __fmul_rn(v0, x) < v1;
+    default: return false;
+    }
+}
+
+// One thread per set: offsets, default class, first empty rule (an empty rule fires for every
+// sample still unclaimed, so the set effectively ends there with that class as its default).
+__global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) {
+        if (b.set_rule_off[0] != 0 || b.set_rule_off[b.P] != b.R ||
+            b.rule_cond_off[0] != 0 || b.rule_cond_off[b.R] != b.C)
+            atomicOr(status, ST_BAD_OFFSETS);
+    }
+    if (p >= b.P) return;
+    SetInfo si{0, 0, 0, 0};
+    const int rb = b.set_rule_off[p], re = b.set_rule_off[p + 1];
+    int d = b.set_default[p];
+    if (d < 0 || d >= K) { atomicOr(status, ST_BAD_CLASS); d = 0; }
+    si.deflt = d;
+    if (rb < 0 || re < rb || re > b.R) {
+        atomicOr(status, ST_BAD_OFFSETS);
+        sets[p] = si;
+        return;
+    }
+    int c_begin = 0, c_end = 0;
+    bool ok = true;
+    for (int r = rb; r < re; ++r) {
+        const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
+        if (c0 < 0 || c1 < c0 || c1 > b.C || c1 - c0 > 0xFFFF) { ok = false; break; }
+        if (r == rb) { c_begin = c0; c_end = c0; }
+        const int cls = b.rule_class[r];
+        if (cls < 0 || cls >= K) { atomicOr(status, ST_BAD_CLASS); ok = false; break; }
+        if (c1 == c0) { si.deflt = cls; break; }   // empty rule: fires on everything left
+        c_end = c1;
+    }
+    if (!ok) {
+        atomicOr(status, ST_BAD_OFFSETS);
+        c_begin = c_end = 0;
+    }
+    si.rec_begin = c_begin;
+    si.rec_end = c_end;
+    si.cost = c_end - c_begin;
+    sets[p] = si;
+}
+
+// One thread per rule: build the records of its conditions.
+__global__ void k_pack_rules(BatchDev b, int F, int K, Rec *recs, uint32_t *status)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= b.R) return;
+    const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
+    if (c0 < 0 || c1 < c0 || c1 > b.C) { atomicOr(status, ST_BAD_OFFSETS); return; }
+    if (c1 - c0 > 0xFFFF) { atomicOr(status, ST_TOO_LARGE); return; }   // skip field is 16 bits
+    int cls = b.rule_class[r];
+    if (cls < 0 || cls >= K) { atomicOr(status, ST_BAD_CLASS); cls = 0; }
+    for (int c = c0; c < c1; ++c) {
+        const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
+        Rec rec;
+        uint32_t kind = KIND_NEVER;
+        float v0 = 0.f, v1 = 0.f;
+        int rf = 0, rg = 0;
+        if (f < 0 || f >= F || g < -1 || g >= F) {
+            atomicOr(status, ST_BAD_FEATURE);
+        } else if (op != 0 && op != 1) {
+            atomicOr(status, ST_BAD_OP);
+        } else if (g < 0) {
+            rewrite_threshold(b.cond_a[c], b.cond_t[c], op, kind, v0, v1);
+            rf = f;
+        } else if (op == 0) {      // a*x[f] > b*x[g]
+            kind = KIND_PAIR; rf = f; rg = g; v0 = b.cond_a[c]; v1 = b.cond_b[c];
+        } else {                   // a*x[f] < b*x[g]  <=>  b*x[g] > a*x[f]
+            kind = KIND_PAIR; rf = g; rg = f; v0 = b.cond_b[c]; v1 = b.cond_a[c];
+        }
+        const uint32_t last = (c == c1 - 1) ? 1u : 0u;
+        const uint32_t skip = (uint32_t)min(c1 - 1 - c, 0xFFFF);
+        rec.meta = kind | (last << 3) | ((uint32_t)cls << 4) | (skip << 16);
+        rec.f = (uint16_t)rf;
+        rec.g = (uint16_t)rg;
+        rec.v0 = v0;
+        rec.v1 = v1;
+        recs[c] = rec;
+    }
+}
+
+// Single-CTA counting sort of sets by cost, most expensive first (bucketed; the order only
+// schedules work, results do not depend on it).
+constexpr int ORDER_BUCKETS = 1024;
+__global__ void k_order(const SetInfo *sets, int P, int32_t *order)
+{
+    __shared__ int hist[ORDER_BUCKETS];
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    auto bucket = [](int cost) { return ORDER_BUCKETS - 1 - min(cost, ORDER_BUCKETS - 1); };
+    for (int p = threadIdx.x; p < P; p += blockDim.x) atomicAdd(&hist[bucket(sets[p].cost)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < ORDER_BUCKETS; ++i) { int h = hist[i]; hist[i] = run; run += h; }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        int pos = atomicAdd(&hist[bucket(sets[p].cost)], 1);
+        order[pos] = p;
+    }
+}
+
+void launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream)
+{
+    if (b.P > 0) k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.status);
+    if (b.R > 0) k_pack_rules<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status);
+    if (b.P > 0 && o.order) k_order<<<1, 1024, 0, stream>>>(o.sets, b.P, o.order);
+}
+
+// --------------------------------------------------------------- exhaustive rewrite self-check
+
+// Rewrite once per entry, then sweep x.
+__global__ void k_rewrite_table(const float *a, const float *t, const int8_t *op, int n,
+                                uint32_t *kind, float *v0, float *v1)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) rewrite_threshold(a[j], t[j], op[j], kind[j], v0[j], v1[j]);
+}
+
+__global__ void k_sweep(const float *a, const float *t, const int8_t *op, const uint32_t *kind,
+                        const float *v0, const float *v1, int j, unsigned long long *mismatches)
+{
+    uint64_t local = 0;
+    const float aj = a[j], tj = t[j];
+    const int oj = op[j];
+    const uint32_t kj = kind[j];
+    const float c0 = v0[j], c1 = v1[j];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (1ull << 32);
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const float x = __uint_as_float((uint32_t)i);
+        local += (thr_true(aj, x, tj, oj) != rec_eval_scalar(kj, c0, c1, x));
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xFFFFFFFFu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(mismatches, (unsigned long long)local);
+}
+
+rs_status selftest_rewrite(const float *a_h, const float *t_h, const int8_t *op_h, int n,
+                           uint64_t *mismatches, int sm_count)
+{
+    float *a = nullptr, *t = nullptr, *v0 = nullptr, *v1 = nullptr;
+    int8_t *op = nullptr;
+    uint32_t *kind = nullptr;
+    unsigned long long *mm = nullptr;
+    RS_CUDA(cudaMalloc(&a, sizeof(float) * n));
+    RS_CUDA(cudaMalloc(&t, sizeof(float) * n));
+    RS_CUDA(cudaMalloc(&v0, sizeof(float) * n));
+    RS_CUDA(cudaMalloc(&v1, sizeof(float) * n));
+    RS_CUDA(cudaMalloc(&op, n));
+    RS_CUDA(cudaMalloc(&kind, sizeof(uint32_t) * n));
+    RS_CUDA(cudaMalloc(&mm, sizeof(unsigned long long)));
+    RS_CUDA(cudaMemcpy(a, a_h, sizeof(float) * n, cudaMemcpyHostToDevice));
+    RS_CUDA(cudaMemcpy(t, t_h, sizeof(float) * n, cudaMemcpyHostToDevice));
+    RS_CUDA(cudaMemcpy(op, op_h, n, cudaMemcpyHostToDevice));
+    RS_CUDA(cudaMemset(mm, 0, sizeof(unsigned long long)));
+    k_rewrite_table<<<(n + 127) / 128, 128>>>(a, t, op, n, kind, v0, v1);
+    for (int j = 0; j < n; ++j) k_sweep<<<sm_count * 8, 256>>>(a, t, op, kind, v0, v1, j, mm);
+    unsigned long long h = 0;
+    RS_CUDA(cudaMemcpy(&h, mm, sizeof(h), cudaMemcpyDeviceToHost));
+    cudaFree(a); cudaFree(t); cudaFree(v0); cudaFree(v1); cudaFree(op); cudaFree(kind); cudaFree(mm);
+    *mismatches = h;
+    return RS_OK;
+}
+
+}  // namespace rs

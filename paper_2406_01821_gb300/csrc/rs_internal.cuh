@@ -1,0 +1,188 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rs.h"
+
+namespace rs {
+
+// ------------------------------------------------------------------------------ errors
+
+void set_error(const char *fmt, ...);
+rs_status cuda_fail(cudaError_t e, const char *what);
+
+#define RS_CUDA(call)                                                         \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ::rs::cuda_fail(e_, #call);             \
+    } while (0)
+
+// Device status word bits (set with atomicOr by kernels that find a problem).
+enum : uint32_t {
+    ST_BAD_OFFSETS = 1u << 0,
+    ST_BAD_CLASS = 1u << 1,
+    ST_BAD_FEATURE = 1u << 2,
+    ST_BAD_OP = 1u << 3,
+    ST_BAD_LABEL = 1u << 4,
+    ST_TOO_LARGE = 1u << 5,
+    ST_WAIT_TIMEOUT = 1u << 8,
+    ST_QUEUE_TIMEOUT = 1u << 9,
+};
+std::string status_text(uint32_t st);
+
+// ------------------------------------------------------------------------------ records
+
+// One condition packed for the evaluator (16 bytes, read as one 128-bit broadcast load).
+// Threshold conditions are rewritten into a single compare of the raw feature value against an
+// exact float32 cut (see pack.cu); '<' pair conditions are rewritten as '>' with the two sides
+// swapped. Both rewrites are exact for every input including NaN, infinities and subnormals.
+enum : uint32_t {
+    KIND_GT = 0,     // x[f] > v0
+    KIND_LT = 1,     // x[f] < v0
+    KIND_PAIR = 2,   // fl(v0 * x[f]) > fl(v1 * x[g])
+    KIND_MGT = 3,    // fl(v0 * x[f]) > v1  (coefficient 0 / inf: kept as the plain product)
+    KIND_MLT = 4,    // fl(v0 * x[f]) < v1
+    KIND_NEVER = 5,  // never true
+};
+
+struct __align__(16) Rec {
+    uint32_t meta;   // [0,3) kind | [3] last condition of its rule | [4,16) rule class | [16,32) skip
+    uint16_t f, g;
+    float v0, v1;
+};
+__host__ __device__ inline uint32_t rec_kind(uint32_t m) { return m & 7u; }
+__host__ __device__ inline bool rec_last(uint32_t m) { return (m >> 3) & 1u; }
+__host__ __device__ inline int rec_cls(uint32_t m) { return (int)((m >> 4) & 0xFFFu); }
+__host__ __device__ inline int rec_skip(uint32_t m) { return (int)(m >> 16); }
+
+// Per-set table written by the packer.
+struct __align__(16) SetInfo {
+    int32_t rec_begin, rec_end;  // records [rec_begin, rec_end) (truncated after an empty rule)
+    int32_t deflt;               // effective default (the class of a leading empty rule, if any)
+    int32_t cost;                // rec_end - rec_begin
+};
+
+// Device-side view of a batch (device pointers).
+struct BatchDev {
+    int32_t P, R, C;
+    const int32_t *set_rule_off, *rule_cond_off, *rule_class, *set_default;
+    const int32_t *cond_f, *cond_g;
+    const int8_t *cond_op;
+    const float *cond_a, *cond_b, *cond_t;
+};
+
+// ------------------------------------------------------------------------------ datasets
+
+struct Dataset {
+    int64_t N = 0, n_pad = 0;
+    int32_t F = 0, K = 0;
+    float *Xt = nullptr;          // [F][n_pad], samples grouped by label (stable), zero padded
+    int32_t *y = nullptr;         // [n_pad] labels in that order, -1 for padding
+    int32_t *perm = nullptr;      // [N] caller index of sorted position
+    std::vector<int64_t> class_count;
+    std::map<int, CUtensorMap> tmaps;   // keyed by samples per tile
+    std::mutex mu;
+};
+
+// ------------------------------------------------------------------------------ tile configs
+
+struct TileConfig {
+    int id;
+    int V;       // samples per lane
+    int W;       // warps per CTA
+    int S() const { return 32 * V; }
+};
+int tile_config_count();
+const TileConfig &tile_config(int id);
+// Largest F a configuration can stage (its x tile must fit in shared memory).
+bool tile_config_fits(const TileConfig &tc, int F);
+
+// ------------------------------------------------------------------------------ context
+
+struct GraphEntry;
+
+struct Ctx {
+    int device = 0;
+    uint32_t flags = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    uint64_t budget = 0;
+    std::string autotune_path;
+    std::mutex mu;
+    std::map<uint64_t, std::shared_ptr<Dataset>> datasets;
+    uint64_t next_ds = 1;
+    int forced_tile = -1;
+    std::map<std::string, int> tune_table;   // key -> tile config id
+    std::map<std::string, std::shared_ptr<GraphEntry>> graphs;
+    uint32_t *d_sticky = nullptr;            // async-mode sticky device status
+    struct Server *server = nullptr;
+};
+
+std::shared_ptr<Dataset> find_dataset(Ctx *ctx, uint64_t ds);
+rs_status device_guard(Ctx *ctx);
+
+// Pinned per-thread status slot used by synchronous calls to read back the device status word.
+uint32_t *host_status_slot();
+
+// ------------------------------------------------------------------------------ kernels / launchers
+
+struct PackOut {
+    Rec *recs;          // [C]
+    SetInfo *sets;      // [P]
+    int32_t *order;     // [P] set ids, most expensive first
+    uint32_t *status;   // device status word
+};
+
+// Validate + pack (+ order) a device batch. Enqueued on `stream`.
+void launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream);
+
+struct HardArgs {
+    const Rec *recs;
+    const SetInfo *sets;
+    const int32_t *order;
+    int32_t P;
+    const int32_t *y;        // sorted labels [n_pad], -1 padding
+    const int32_t *perm;     // [N]
+    int64_t N, n_pad;
+    int32_t F, K;
+    int32_t *correct;        // [P]  (zeroed by the launcher)
+    int32_t *per_class;      // [P*K] or null
+    int32_t *preds;          // [P*N] or null
+    int32_t groups;          // set groups (grid.y)
+    uint32_t *status;
+};
+// Zero outputs and run the evaluator with tile configuration `tc`.
+rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,
+                      cudaStream_t stream);
+int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P);
+const CUtensorMap *dataset_tmap(Dataset *ds, int S);
+
+struct SoftArgs {
+    const Rec *recs_unused;
+    BatchDev b;
+    const float *Xt;
+    const int32_t *y;
+    const int32_t *perm;
+    int64_t N, n_pad;
+    int32_t F, K;
+    float tau;
+    float *loss;        // [P]
+    float *probs;       // [P*N*K] or null
+    const float *dloss; // [P] or null (forward only)
+    float *grad_a, *grad_b, *grad_t;
+    uint32_t *status;
+};
+rs_status launch_soft(Ctx *ctx, const SoftArgs &a, cudaStream_t stream);
+
+}  // namespace rs
+
+struct rs_ctx : public rs::Ctx {};

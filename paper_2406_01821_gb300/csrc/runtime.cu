@@ -1,0 +1,335 @@
+// Runtime: errors, contexts, dataset registration (feature-major, label-grouped, on device).
+#include <cstdarg>
+#include <cstring>
+#include <cudaTypedefs.h>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+
+// ------------------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+const char *last_error() { return g_last_error.c_str(); }
+
+rs_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return RS_ERR_OOM;
+    }
+    return RS_ERR_DEVICE;
+}
+
+std::string status_text(uint32_t st)
+{
+    std::string s;
+    auto add = [&](uint32_t bit, const char *t) {
+        if (st & bit) { if (!s.empty()) s += ", "; s += t; }
+    };
+    add(ST_BAD_OFFSETS, "malformed offset arrays");
+    add(ST_BAD_CLASS, "class id out of range");
+    add(ST_BAD_FEATURE, "feature index out of range");
+    add(ST_BAD_OP, "comparison op not 0 ('>') or 1 ('<')");
+    add(ST_BAD_LABEL, "label out of range");
+    add(ST_TOO_LARGE, "a set exceeds the soft path's rule or condition limit");
+    add(ST_WAIT_TIMEOUT, "device wait limit reached");
+    add(ST_QUEUE_TIMEOUT, "work queue wait limit reached");
+    return s;
+}
+
+uint32_t *host_status_slot()
+{
+    // one pinned word per host thread, allocated on first use and kept for the thread's life
+    struct Slot {
+        uint32_t *p = nullptr;
+        ~Slot() { if (p) cudaFreeHost(p); }
+    };
+    static thread_local Slot slot;
+    if (!slot.p) {
+        if (cudaHostAlloc(&slot.p, 64, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            slot.p = nullptr;
+        }
+    }
+    return slot.p;
+}
+
+rs_status device_guard(Ctx *ctx)
+{
+    int cur = -1;
+    RS_CUDA(cudaGetDevice(&cur));
+    if (cur != ctx->device) RS_CUDA(cudaSetDevice(ctx->device));
+    return RS_OK;
+}
+
+std::shared_ptr<Dataset> find_dataset(Ctx *ctx, uint64_t ds)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->datasets.find(ds);
+    if (it == ctx->datasets.end()) return nullptr;
+    return it->second;
+}
+
+// ------------------------------------------------------------------------------ registration
+
+namespace {
+
+constexpr int REG_BLOCK = 1024;
+
+// Per block of REG_BLOCK samples: label histogram and each sample's rank among earlier samples
+// of the same label in the block (a stable order within the block).
+__global__ void k_label_rank(const int32_t *y, int64_t N, int K, int32_t *blk_count,
+                             int32_t *rank, uint32_t *status)
+{
+    extern __shared__ int32_t sh[];
+    int32_t *ys = sh;                 // [REG_BLOCK]
+    int32_t *hist = sh + REG_BLOCK;   // [K]
+    const int64_t n = (int64_t)blockIdx.x * REG_BLOCK + threadIdx.x;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) hist[k] = 0;
+    int lab = -1;
+    if (n < N) {
+        lab = y[n];
+        if (lab < 0 || lab >= K) { atomicOr(status, ST_BAD_LABEL); lab = -1; }
+    }
+    ys[threadIdx.x] = lab;
+    __syncthreads();
+    if (lab >= 0) atomicAdd(&hist[lab], 1);
+    int r = 0;
+    for (int i = 0; i < (int)threadIdx.x; ++i) r += (ys[i] == lab);
+    if (n < N) rank[n] = r;
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        blk_count[(int64_t)blockIdx.x * K + k] = hist[k];
+}
+
+// One thread per label: exclusive offsets of every block within the label-grouped order.
+__global__ void k_label_offsets(int32_t *blk_count, int64_t nblk, int K, int64_t *class_total)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int64_t run = 0;
+    for (int64_t b = 0; b < nblk; ++b) {
+        int32_t c = blk_count[b * K + k];
+        blk_count[b * K + k] = (int32_t)run;
+        run += c;
+    }
+    class_total[k] = run;
+}
+
+__global__ void k_class_start(const int64_t *class_total, int K, int64_t *class_start)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t run = 0;
+        for (int k = 0; k < K; ++k) { class_start[k] = run; run += class_total[k]; }
+    }
+}
+
+__global__ void k_label_scatter(const int32_t *y, int64_t N, int K, const int32_t *blk_off,
+                                const int64_t *class_start, const int32_t *rank, int32_t *perm,
+                                int32_t *y_sorted)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int lab = y[n];
+    if (lab < 0 || lab >= K) return;
+    const int64_t blk = n / REG_BLOCK;
+    const int64_t pos = class_start[lab] + blk_off[blk * K + lab] + rank[n];
+    perm[pos] = (int32_t)n;
+    y_sorted[pos] = lab;
+}
+
+// Xt[f][m] = X[perm[m]][f] for m < N, 0 for the padding; 32x32 tiles through shared memory.
+__global__ void k_transpose_gather(const float *X, int64_t N, int F, int64_t n_pad,
+                                   const int32_t *perm, float *Xt)
+{
+    __shared__ float tile[32][33];
+    const int64_t m0 = (int64_t)blockIdx.x * 32;
+    const int f0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t m = m0 + j;
+        const int f = f0 + tx;
+        float v = 0.f;
+        if (m < N && f < F) v = X[(int64_t)perm[m] * F + f];
+        tile[j][tx] = v;
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int f = f0 + j;
+        const int64_t m = m0 + tx;
+        if (f < F && m < n_pad) Xt[(int64_t)f * n_pad + m] = tile[tx][j];
+    }
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+const CUtensorMap *dataset_tmap(Dataset *ds, int S)
+{
+    std::lock_guard<std::mutex> lk(ds->mu);
+    auto it = ds->tmaps.find(S);
+    if (it != ds->tmaps.end()) return &it->second;
+    auto enc = get_encode();
+    if (!enc) { set_error("cuTensorMapEncodeTiled not available"); return nullptr; }
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)ds->n_pad, (cuuint64_t)ds->F};
+    cuuint64_t strides[1] = {(cuuint64_t)ds->n_pad * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)S, (cuuint32_t)(ds->F < 256 ? ds->F : 256)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ds->Xt, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for S=%d F=%d", (int)r, S, ds->F);
+        return nullptr;
+    }
+    auto res = ds->tmaps.emplace(S, m);
+    return &res.first->second;
+}
+
+rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, int32_t F,
+                         int32_t K, int32_t mem, cudaStream_t stream, uint64_t *out)
+{
+    if (!X || !y || !out) { set_error("null pointer"); return RS_ERR_INVALID; }
+    if (N < 1 || N > (int64_t)INT32_MAX - 1024 || F < 1 || F > RS_MAX_FEATURES || K < 1 ||
+        K > RS_MAX_CLASSES) {
+        set_error("dataset shape out of range (N=%lld F=%d K=%d)", (long long)N, F, K);
+        return RS_ERR_INVALID;
+    }
+    if (mem != RS_MEM_HOST && mem != RS_MEM_DEVICE) { set_error("bad mem kind"); return RS_ERR_INVALID; }
+    auto ds = std::make_shared<Dataset>();
+    ds->N = N;
+    ds->F = F;
+    ds->K = K;
+    ds->n_pad = (N + 255) / 256 * 256;
+    const int64_t nblk = (N + REG_BLOCK - 1) / REG_BLOCK;
+
+    float *Xd = nullptr;
+    int32_t *yd = nullptr, *blk = nullptr, *rank = nullptr;
+    int64_t *ctot = nullptr, *cstart = nullptr;
+    uint32_t *st = nullptr;
+    rs_status rc = RS_OK;
+    auto cleanup = [&] {
+        if (mem == RS_MEM_HOST) { cudaFree(Xd); cudaFree(yd); }
+        cudaFree(blk); cudaFree(rank); cudaFree(ctot); cudaFree(cstart); cudaFree(st);
+    };
+#define REG_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) {                            \
+            rc = cuda_fail(e_, #call);                      \
+            cleanup();                                      \
+            cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm); \
+            return rc;                                      \
+        }                                                   \
+    } while (0)
+
+    if (mem == RS_MEM_HOST) {
+        REG_CUDA(cudaMalloc(&Xd, sizeof(float) * N * F));
+        REG_CUDA(cudaMalloc(&yd, sizeof(int32_t) * N));
+        REG_CUDA(cudaMemcpyAsync(Xd, X, sizeof(float) * N * F, cudaMemcpyHostToDevice, stream));
+        REG_CUDA(cudaMemcpyAsync(yd, y, sizeof(int32_t) * N, cudaMemcpyHostToDevice, stream));
+    } else {
+        Xd = const_cast<float *>(X);
+        yd = const_cast<int32_t *>(y);
+    }
+    REG_CUDA(cudaMalloc(&ds->Xt, sizeof(float) * ds->n_pad * F));
+    REG_CUDA(cudaMalloc(&ds->y, sizeof(int32_t) * ds->n_pad));
+    REG_CUDA(cudaMalloc(&ds->perm, sizeof(int32_t) * N));
+    REG_CUDA(cudaMalloc(&blk, sizeof(int32_t) * nblk * K));
+    REG_CUDA(cudaMalloc(&rank, sizeof(int32_t) * N));
+    REG_CUDA(cudaMalloc(&ctot, sizeof(int64_t) * K));
+    REG_CUDA(cudaMalloc(&cstart, sizeof(int64_t) * K));
+    REG_CUDA(cudaMalloc(&st, sizeof(uint32_t)));
+    REG_CUDA(cudaMemsetAsync(st, 0, sizeof(uint32_t), stream));
+    k_fill_i32<<<(unsigned)((ds->n_pad + 255) / 256), 256, 0, stream>>>(ds->y, ds->n_pad, -1);
+    k_label_rank<<<(unsigned)nblk, REG_BLOCK, sizeof(int32_t) * (REG_BLOCK + K), stream>>>(
+        yd, N, K, blk, rank, st);
+    REG_CUDA(cudaGetLastError());
+    uint32_t hst = 0;
+    // labels must be valid before they are used as scatter positions
+    REG_CUDA(cudaMemcpyAsync(&hst, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    REG_CUDA(cudaStreamSynchronize(stream));
+    if (hst) {
+        cleanup();
+        set_error("dataset rejected: %s", status_text(hst).c_str());
+        cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm);
+        return RS_ERR_INVALID;
+    }
+    k_label_offsets<<<(K + 127) / 128, 128, 0, stream>>>(blk, nblk, K, ctot);
+    k_class_start<<<1, 32, 0, stream>>>(ctot, K, cstart);
+    k_label_scatter<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(yd, N, K, blk, cstart, rank,
+                                                                      ds->perm, ds->y);
+    dim3 tg((unsigned)(ds->n_pad / 32), (unsigned)((F + 31) / 32));
+    k_transpose_gather<<<tg, dim3(32, 8), 0, stream>>>(Xd, N, F, ds->n_pad, ds->perm, ds->Xt);
+    REG_CUDA(cudaGetLastError());
+    ds->class_count.resize(K);
+    REG_CUDA(cudaMemcpyAsync(ds->class_count.data(), ctot, sizeof(int64_t) * K,
+                             cudaMemcpyDeviceToHost, stream));
+    REG_CUDA(cudaStreamSynchronize(stream));
+    cleanup();
+#undef REG_CUDA
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const uint64_t h = ctx->next_ds++;
+    ctx->datasets[h] = ds;
+    *out = h;
+    return RS_OK;
+}
+
+rs_status dataset_destroy(Ctx *ctx, uint64_t h)
+{
+    std::shared_ptr<Dataset> ds;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->datasets.find(h);
+        if (it == ctx->datasets.end()) { set_error("unknown dataset %llu", (unsigned long long)h); return RS_ERR_NOT_FOUND; }
+        ds = it->second;
+        ctx->datasets.erase(it);
+        // drop cached graphs that reference this dataset
+        for (auto g = ctx->graphs.begin(); g != ctx->graphs.end();) {
+            if (g->first.rfind("ds" + std::to_string(h) + "|", 0) == 0) g = ctx->graphs.erase(g);
+            else ++g;
+        }
+    }
+    RS_CUDA(cudaDeviceSynchronize());
+    cudaFree(ds->Xt);
+    cudaFree(ds->y);
+    cudaFree(ds->perm);
+    return RS_OK;
+}
+
+}  // namespace rs

@@ -1,0 +1,387 @@
+// The soft path: sigmoid-relaxed first-fire evaluation (forward) and its hand-written adjoint.
+//
+// Per condition  u = s*(a*x[f] - rhs)/tau  (s = +1 for '>', -1 for '<'; rhs = t or b*x[g]).
+// Per rule       lq_r = sum_c log sigmoid(u_c)      (log of the firing probability q_r)
+//                l1q_r = log(1 - q_r) = log(-expm1(lq_r))
+//                lu_r = sum_{j<r} l1q_j             (log probability that no earlier rule fired)
+// Class k        log p_k = logsumexp over rules of class k of (lq_r + lu_r), plus lu_R for the
+//                default class.  Loss  L_p = (1/N) sum_n -log p_{y_n}.
+// Adjoint        lS_R = 0 if default = y else -inf;  lS_r = logsumexp([cls_r = y] lq_r, l1q_r + lS_{r+1})
+//                dl/dlq_r = exp(lq_r + lu_r + lS_{r+1} - lp) - [cls_r = y] exp(lq_r + lu_r - lp)
+//                dl/du_c  = dl/dlq_r * sigmoid(-u_c);  du/da = s x_f / tau, du/dt = -s / tau,
+//                du/db = -s x_g / tau.
+// Everything is evaluated in float32 in the log domain, which keeps 1 - q_r and the products of
+// many sigmoids representable where the linear form underflows.
+//
+// Work: one warp owns a (rule set, sample chunk) pair and walks the chunk 32 samples at a time
+// (lane = sample), so each partial sum has a fixed summation order. Chunks are a function of N
+// only; partial losses and gradients per chunk are reduced in a second kernel in a fixed order,
+// which makes results bit-reproducible run to run and independent of scheduling.
+#include "rs_internal.cuh"
+
+namespace rs {
+
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr int SOFT_W = 4;                 // warps per CTA
+constexpr int SOFT_MAX_RULES = 64;        // rules per set held in shared memory
+constexpr int SOFT_MAX_CONDS = 512;       // conditions per set accumulated in shared memory
+constexpr int SOFT_MAX_CHUNKS = 64;
+
+struct __align__(16) SoftRec {
+    uint32_t meta;    // bit 0: pair condition, bit 1: '<'
+    uint16_t f, g;
+    float a, bt;      // bt = threshold t, or the pair coefficient b
+};
+
+__global__ void k_pack_soft(BatchDev b, int F, int K, SoftRec *recs, uint32_t *status)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= b.C) return;
+    const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
+    SoftRec r{0, 0, 0, 0.f, 0.f};
+    if (f < 0 || f >= F || g < -1 || g >= F) atomicOr(status, ST_BAD_FEATURE);
+    else if (op != 0 && op != 1) atomicOr(status, ST_BAD_OP);
+    else {
+        r.meta = (g >= 0 ? 1u : 0u) | (op == 1 ? 2u : 0u);
+        r.f = (uint16_t)f;
+        r.g = (uint16_t)(g >= 0 ? g : 0);
+        r.a = b.cond_a[c];
+        r.bt = g >= 0 ? b.cond_b[c] : b.cond_t[c];
+    }
+    recs[c] = r;
+}
+
+// Validation of the set/rule structure (one thread per set).
+__global__ void k_check_sets_soft(BatchDev b, int K, uint32_t *status, int32_t *maxima)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) {
+        if (b.set_rule_off[0] != 0 || b.set_rule_off[b.P] != b.R ||
+            b.rule_cond_off[0] != 0 || b.rule_cond_off[b.R] != b.C)
+            atomicOr(status, ST_BAD_OFFSETS);
+    }
+    if (p >= b.P) return;
+    const int rb = b.set_rule_off[p], re = b.set_rule_off[p + 1];
+    const int d = b.set_default[p];
+    if (d < 0 || d >= K) atomicOr(status, ST_BAD_CLASS);
+    if (rb < 0 || re < rb || re > b.R) { atomicOr(status, ST_BAD_OFFSETS); return; }
+    if (re - rb > SOFT_MAX_RULES) { atomicOr(status, ST_TOO_LARGE); return; }
+    for (int r = rb; r < re; ++r) {
+        const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
+        if (c0 < 0 || c1 < c0 || c1 > b.C) { atomicOr(status, ST_BAD_OFFSETS); return; }
+        const int cls = b.rule_class[r];
+        if (cls < 0 || cls >= K) atomicOr(status, ST_BAD_CLASS);
+    }
+    const int nc = re > rb ? b.rule_cond_off[re] - b.rule_cond_off[rb] : 0;
+    if (nc > SOFT_MAX_CONDS) atomicOr(status, ST_TOO_LARGE);
+    atomicMax(&maxima[0], re - rb);
+    atomicMax(&maxima[1], nc);
+}
+
+__device__ __forceinline__ float log_sigmoid(float u)
+{
+    // log(1/(1+e^-u)) = -(max(-u,0) + log1p(e^-|u|))
+    const float e = expf(-fabsf(u));
+    return -(fmaxf(-u, 0.f) + log1pf(e));
+}
+
+__device__ __forceinline__ float sigmoid_neg(float u)     // 1/(1+e^u)
+{
+    const float e = expf(-fabsf(u));
+    return u >= 0.f ? e / (1.f + e) : 1.f / (1.f + e);
+}
+
+__device__ __forceinline__ float log_add(float a, float b)
+{
+    if (a == -INFINITY) return b;
+    if (b == -INFINITY) return a;
+    const float m = fmaxf(a, b);
+    return m + log1pf(expf(-fabsf(a - b)));
+}
+
+// Kahan-compensated accumulation.
+__device__ __forceinline__ void kadd(float &s, float &c, float v)
+{
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+struct SoftKArgs {
+    const SoftRec *recs;
+    const int32_t *set_rule_off, *rule_cond_off, *rule_class, *set_default;
+    int32_t P;
+    const float *Xt;
+    const int32_t *y;
+    const int32_t *perm;
+    int64_t N, n_pad;
+    int32_t K;
+    float inv_tau;
+    int32_t nchunks, chunk;          // chunk = samples per chunk (multiple of 32)
+    float *part_loss;                // [nchunks][P]
+    float *part_ga, *part_gbt;       // [nchunks][C]
+    float *probs;                    // [P*N*K] or null
+    int32_t backward;
+    int32_t *next;                   // work counter
+    int32_t maxR, maxC;              // shared-memory capacity per warp (rules, conditions)
+};
+
+template <bool BWD>
+__global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
+{
+    // per warp: lq[maxR][32], lu[maxR+1][32], acc[maxC][4] (ga sum/comp, gbt sum/comp)
+    extern __shared__ __align__(16) float sm[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t tasks = (int64_t)a.P * a.nchunks;
+    const size_t per_warp = (size_t)(2 * a.maxR + 1) * 32 + (size_t)a.maxC * 4;
+    float *base_w = sm + per_warp * w;
+    float(*lq)[32] = reinterpret_cast<float(*)[32]>(base_w);
+    float(*lu)[32] = reinterpret_cast<float(*)[32]>(base_w + (size_t)a.maxR * 32);
+    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * 32);
+
+    while (true) {
+        int64_t task = 0;
+        if (lane == 0) task = atomicAdd(a.next, 1);
+        task = __shfl_sync(FULL, task, 0);
+        if (task >= tasks) break;
+        const int p = (int)(task / a.nchunks);
+        const int ch = (int)(task % a.nchunks);
+        const int rb = a.set_rule_off[p], re = a.set_rule_off[p + 1];
+        const int R = re - rb;
+        const int cb = a.rule_cond_off[rb], ce = a.rule_cond_off[re];
+        const int deflt = a.set_default[p];
+        if (BWD) {
+            for (int i = lane; i < (ce - cb); i += 32) {
+                acc[i][0] = 0.f; acc[i][1] = 0.f; acc[i][2] = 0.f; acc[i][3] = 0.f;
+            }
+            __syncwarp();
+        }
+        float loss_s = 0.f, loss_c = 0.f;
+        const int64_t s0 = (int64_t)ch * a.chunk;
+        const int64_t s1 = min(s0 + a.chunk, a.N);
+        for (int64_t nb = s0; nb < s1; nb += 32) {
+            const int64_t n = nb + lane;
+            const bool valid = n < a.N;
+            const int yn = valid ? a.y[n] : -1;
+            const float *xcol = a.Xt + (valid ? n : 0);   // x[f] at xcol[f * n_pad]
+            // ---------------- forward
+            float lu_r = 0.f, lpy = -INFINITY;
+            for (int j = 0; j < R; ++j) {
+                const int r = rb + j;
+                const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
+                float s = 0.f;
+                for (int c = c0; c < c1; ++c) {
+                    const SoftRec rc = a.recs[c];
+                    const float lhs = rc.a * xcol[(int64_t)rc.f * a.n_pad];
+                    const float rhs = (rc.meta & 1u) ? rc.bt * xcol[(int64_t)rc.g * a.n_pad] : rc.bt;
+                    float u = (lhs - rhs) * a.inv_tau;
+                    if (rc.meta & 2u) u = -u;
+                    s += log_sigmoid(u);
+                }
+                lq[j][lane] = s;
+                lu[j][lane] = lu_r;
+                if (a.rule_class[r] == yn) lpy = log_add(lpy, s + lu_r);
+                lu_r += logf(-expm1f(s));
+            }
+            lu[R][lane] = lu_r;
+            if (deflt == yn) lpy = log_add(lpy, lu_r);
+            if (valid) kadd(loss_s, loss_c, -lpy);
+            if (a.probs && valid) {
+                const int64_t orig = a.perm[n];
+                for (int k = 0; k < a.K; ++k) {
+                    float lpk = (deflt == k) ? lu_r : -INFINITY;
+                    for (int j = 0; j < R; ++j)
+                        if (a.rule_class[rb + j] == k) lpk = log_add(lpk, lq[j][lane] + lu[j][lane]);
+                    a.probs[((int64_t)p * a.N + orig) * a.K + k] = expf(lpk);
+                }
+            }
+            if (!BWD) continue;
+            // ---------------- adjoint
+            float lS = (deflt == yn) ? 0.f : -INFINITY;
+            for (int j = R - 1; j >= 0; --j) {
+                const int r = rb + j;
+                const float lqj = lq[j][lane], luj = lu[j][lane];
+                const bool same = a.rule_class[r] == yn;
+                float gq = expf(lqj + luj + lS - lpy);
+                if (same) gq -= expf(lqj + luj - lpy);
+                if (!valid) gq = 0.f;
+                lS = log_add(same ? lqj : -INFINITY, logf(-expm1f(lqj)) + lS);
+                const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
+                for (int c = c0; c < c1; ++c) {
+                    const SoftRec rc = a.recs[c];
+                    const float xf = xcol[(int64_t)rc.f * a.n_pad];
+                    const bool pair = rc.meta & 1u;
+                    const float xg = pair ? xcol[(int64_t)rc.g * a.n_pad] : 0.f;
+                    const float lhs = rc.a * xf;
+                    const float rhs = pair ? rc.bt * xg : rc.bt;
+                    const float sg = (rc.meta & 2u) ? -1.f : 1.f;
+                    const float u = sg * (lhs - rhs) * a.inv_tau;
+                    const float du = gq * sigmoid_neg(u) * sg * a.inv_tau;
+                    float ga = du * xf;
+                    float gbt = pair ? -du * xg : -du;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        ga += __shfl_xor_sync(FULL, ga, o);
+                        gbt += __shfl_xor_sync(FULL, gbt, o);
+                    }
+                    const int ci = c - cb;
+                    if (lane == (ci & 31)) {
+                        kadd(acc[ci][0], acc[ci][1], ga);
+                        kadd(acc[ci][2], acc[ci][3], gbt);
+                    }
+                }
+            }
+        }
+        // chunk partials
+        float ls = loss_s;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(FULL, ls, o);
+        if (lane == 0) a.part_loss[(int64_t)ch * a.P + p] = ls;
+        if (BWD) {
+            __syncwarp();
+            const int64_t C = a.rule_cond_off[a.set_rule_off[a.P]];
+            for (int i = lane; i < (ce - cb); i += 32) {
+                a.part_ga[(int64_t)ch * C + cb + i] = acc[i][0];
+                a.part_gbt[(int64_t)ch * C + cb + i] = acc[i][2];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__device__ __forceinline__ float tree_sum_strided(const float *base, int64_t stride, int n)
+{
+    // pairwise sum of base[0], base[stride], ... (n <= SOFT_MAX_CHUNKS) in a fixed order
+    float v[SOFT_MAX_CHUNKS];
+#pragma unroll
+    for (int i = 0; i < SOFT_MAX_CHUNKS; ++i) v[i] = (i < n) ? base[(int64_t)i * stride] : 0.f;
+#pragma unroll
+    for (int w = 1; w < SOFT_MAX_CHUNKS; w <<= 1)
+#pragma unroll
+        for (int i = 0; i + w < SOFT_MAX_CHUNKS; i += 2 * w) v[i] += v[i + w];
+    return v[0];
+}
+
+__global__ void k_soft_reduce_loss(const float *part_loss, int nchunks, int P, float inv_n, float *loss)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    loss[p] = tree_sum_strided(part_loss + p, P, nchunks) * inv_n;
+}
+
+// One thread per set, looping over its conditions (grads scaled by dloss[p] / N).
+__global__ void k_soft_reduce_grad(const float *part_ga, const float *part_gbt, int nchunks,
+                                   const int32_t *set_rule_off, const int32_t *rule_cond_off,
+                                   const SoftRec *recs, int P, int64_t C, const float *dloss,
+                                   float inv_n, float *grad_a, float *grad_b, float *grad_t)
+{
+    const int p = blockIdx.x;
+    if (p >= P) return;
+    const int cb = rule_cond_off[set_rule_off[p]], ce = rule_cond_off[set_rule_off[p + 1]];
+    const float scale = dloss[p] * inv_n;
+    for (int c = cb + threadIdx.x; c < ce; c += blockDim.x) {
+        const float ga = tree_sum_strided(part_ga + c, C, nchunks) * scale;
+        const float gbt = tree_sum_strided(part_gbt + c, C, nchunks) * scale;
+        const bool pair = recs[c].meta & 1u;
+        grad_a[c] = ga;
+        grad_b[c] = pair ? gbt : 0.f;
+        grad_t[c] = pair ? 0.f : gbt;
+    }
+}
+
+}  // namespace
+
+rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
+{
+    const BatchDev &b = s.b;
+    const int P = b.P;
+    const int64_t C = b.C;
+    if (P == 0) return RS_OK;
+    int nchunks = (int)std::min<int64_t>(SOFT_MAX_CHUNKS, (s.N + 1023) / 1024);
+    if (nchunks < 1) nchunks = 1;
+    int64_t chunk = (s.N + nchunks - 1) / nchunks;
+    chunk = (chunk + 31) / 32 * 32;
+    nchunks = (int)((s.N + chunk - 1) / chunk);
+
+    SoftRec *recs = nullptr;
+    float *part_loss = nullptr, *part_ga = nullptr, *part_gbt = nullptr;
+    int32_t *next = nullptr;   // [0] work counter, [1..2] max rules / conditions per set
+    const bool bwd = s.dloss != nullptr;
+    RS_CUDA(cudaMallocAsync(&recs, sizeof(SoftRec) * std::max<int64_t>(C, 1), stream));
+    RS_CUDA(cudaMallocAsync(&part_loss, sizeof(float) * (size_t)nchunks * P, stream));
+    RS_CUDA(cudaMallocAsync(&next, sizeof(int32_t) * 4, stream));
+    if (bwd) {
+        RS_CUDA(cudaMallocAsync(&part_ga, sizeof(float) * (size_t)nchunks * std::max<int64_t>(C, 1), stream));
+        RS_CUDA(cudaMallocAsync(&part_gbt, sizeof(float) * (size_t)nchunks * std::max<int64_t>(C, 1), stream));
+    }
+    RS_CUDA(cudaMemsetAsync(next, 0, sizeof(int32_t) * 4, stream));
+    k_check_sets_soft<<<(P + 255) / 256, 256, 0, stream>>>(b, s.K, s.status, next + 1);
+    if (C > 0) k_pack_soft<<<(unsigned)((C + 255) / 256), 256, 0, stream>>>(b, s.F, s.K, recs, s.status);
+    // The main kernel reads only validated structure: skip it when validation failed.
+    SoftKArgs k{};
+    k.recs = recs;
+    k.set_rule_off = b.set_rule_off;
+    k.rule_cond_off = b.rule_cond_off;
+    k.rule_class = b.rule_class;
+    k.set_default = b.set_default;
+    k.P = P;
+    k.Xt = s.Xt;
+    k.y = s.y;
+    k.perm = s.perm;
+    k.N = s.N;
+    k.n_pad = s.n_pad;
+    k.K = s.K;
+    k.inv_tau = 1.0f / s.tau;
+    k.nchunks = nchunks;
+    k.chunk = (int32_t)chunk;
+    k.part_loss = part_loss;
+    k.part_ga = part_ga;
+    k.part_gbt = part_gbt;
+    k.probs = s.probs;
+    k.backward = bwd;
+    k.next = next;
+    rs_status rc = RS_OK;
+    uint32_t *hs = host_status_slot();
+    // validation must finish before the evaluator trusts the offsets: read the status word
+    RS_CUDA(cudaMemcpyAsync(hs, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    RS_CUDA(cudaMemcpyAsync(hs + 1, next + 1, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, stream));
+    RS_CUDA(cudaStreamSynchronize(stream));
+    k.maxR = std::max<int32_t>(1, (int32_t)hs[1]);
+    k.maxC = std::max<int32_t>(1, (int32_t)hs[2]);
+    const size_t smem = sizeof(float) * SOFT_W *
+                        ((size_t)(2 * k.maxR + 1) * 32 + (size_t)k.maxC * 4);
+    if (*hs) {
+        rc = (*hs & ST_TOO_LARGE) ? RS_ERR_TOO_LARGE : RS_ERR_INVALID;
+        set_error("soft evaluation rejected the batch: %s", status_text(*hs).c_str());
+    } else {
+        static std::once_flag once;
+        std::call_once(once, [&] {
+            cudaFuncSetAttribute(k_soft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
+            cudaFuncSetAttribute(k_soft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
+        });
+        int per_sm = 1;
+        if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true>, SOFT_W * 32, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false>, SOFT_W * 32, smem);
+        const int grid = ctx->sm_count * std::max(1, per_sm);
+        if (bwd) k_soft<true><<<grid, SOFT_W * 32, smem, stream>>>(k);
+        else k_soft<false><<<grid, SOFT_W * 32, smem, stream>>>(k);
+        k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
+                                                               1.0f / (float)s.N, s.loss);
+        if (bwd && C > 0)
+            k_soft_reduce_grad<<<P, 128, 0, stream>>>(part_ga, part_gbt, nchunks, b.set_rule_off,
+                                                     b.rule_cond_off, recs, P, C, s.dloss,
+                                                     1.0f / (float)s.N, s.grad_a, s.grad_b, s.grad_t);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "soft kernels");
+    }
+    cudaFreeAsync(recs, stream);
+    cudaFreeAsync(part_loss, stream);
+    cudaFreeAsync(next, stream);
+    if (bwd) { cudaFreeAsync(part_ga, stream); cudaFreeAsync(part_gbt, stream); }
+    return rc;
+}
+
+}  // namespace rs

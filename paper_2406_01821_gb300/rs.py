@@ -1,0 +1,355 @@
+"""ctypes binding of librs.so (include/rs.h): argument marshalling only.
+
+Every evaluation step runs in the library's CUDA kernels; this module turns tensors into the
+pointers and sizes the C ABI takes. PyTorch is used for device memory and streams. If the
+library has not been built (``paper_2406_01821_gb300.build``) the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "librs.so")
+
+OK, PENDING = 0, 1
+ERR = {-1: "RS_ERR_INVALID", -2: "RS_ERR_TOO_LARGE", -3: "RS_ERR_OOM", -4: "RS_ERR_TIMEOUT",
+       -5: "RS_ERR_DEVICE", -6: "RS_ERR_UNSUPPORTED", -7: "RS_ERR_NOT_FOUND", -8: "RS_ERR_CANCELLED"}
+MEM_HOST, MEM_DEVICE = 0, 1
+CTX_ASYNC, CTX_NO_GRAPH, CTX_NO_AUTOTUNE = 1, 2, 4
+
+
+class RsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rs_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("mem_budget_bytes", ctypes.c_uint64), ("autotune_cache", ctypes.c_char_p)]
+
+
+class rs_batch(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int32), ("R", ctypes.c_int32), ("C", ctypes.c_int32),
+                ("mem", ctypes.c_int32),
+                ("set_rule_off", ctypes.c_void_p), ("rule_cond_off", ctypes.c_void_p),
+                ("rule_class", ctypes.c_void_p), ("set_default", ctypes.c_void_p),
+                ("cond_f", ctypes.c_void_p), ("cond_g", ctypes.c_void_p),
+                ("cond_op", ctypes.c_void_p), ("cond_a", ctypes.c_void_p),
+                ("cond_b", ctypes.c_void_p), ("cond_t", ctypes.c_void_p)]
+
+
+_lib = None
+
+_SIGS = {
+    "rs_create": (ctypes.c_int32, [ctypes.POINTER(rs_config), ctypes.POINTER(ctypes.c_void_p)]),
+    "rs_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "rs_last_error": (ctypes.c_char_p, []),
+    "rs_version": (ctypes.c_char_p, []),
+    "rs_check": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "rs_dataset_create": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    "rs_dataset_destroy": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rs_dataset_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
+    "rs_eval_hard": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "rs_eval_soft_fwd": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
+                                          ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "rs_eval_soft_bwd": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
+                                          ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "rs_tile_config_count": (ctypes.c_int32, []),
+    "rs_tile_config_info": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "rs_set_tile_config": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "rs_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "rs_selftest_threshold_rewrite": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
+                                                       ctypes.c_void_p, ctypes.c_void_p,
+                                                       ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
+}
+
+
+def lib():
+    """Load librs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            raise RuntimeError(f"librs.so not built ({_SO}); run paper_2406_01821_gb300/build.py")
+        h = ctypes.CDLL(_SO)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(h, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def check(code):
+    if code < 0:
+        raise RsError(code, lib().rs_last_error().decode())
+    return code
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------------------- batches
+
+_FIELDS = ("set_rule_off", "rule_cond_off", "rule_class", "set_default", "cond_f", "cond_g",
+           "cond_op", "cond_a", "cond_b", "cond_t")
+_DTYPES = {"cond_op": np.int8, "cond_a": np.float32, "cond_b": np.float32, "cond_t": np.float32}
+
+
+class DeviceBatch:
+    """A rule-set batch held in device memory (torch tensors), ready for the C ABI."""
+
+    def __init__(self, tensors: dict):
+        self.t = tensors
+        self.P = int(tensors["set_default"].numel())
+        self.R = int(tensors["rule_class"].numel())
+        self.C = int(tensors["cond_f"].numel())
+
+    @classmethod
+    def from_host(cls, batch, device="cuda"):
+        import torch
+        t = {}
+        for f in _FIELDS:
+            a = np.ascontiguousarray(getattr(batch, f), _DTYPES.get(f, np.int32))
+            t[f] = torch.from_numpy(a).to(device)
+        return cls(t)
+
+    def with_params(self, a=None, b=None, t=None) -> "DeviceBatch":
+        d = dict(self.t)
+        if a is not None:
+            d["cond_a"] = a
+        if b is not None:
+            d["cond_b"] = b
+        if t is not None:
+            d["cond_t"] = t
+        return DeviceBatch(d)
+
+    def c(self) -> rs_batch:
+        return rs_batch(self.P, self.R, self.C, MEM_DEVICE, *[_ptr(self.t[f]) for f in _FIELDS])
+
+
+class HostBatch:
+    """A rule-set batch in host memory (numpy); the library copies it to the device per call."""
+
+    def __init__(self, batch):
+        self.a = {f: np.ascontiguousarray(getattr(batch, f), _DTYPES.get(f, np.int32)) for f in _FIELDS}
+        self.P = int(self.a["set_default"].shape[0])
+        self.R = int(self.a["rule_class"].shape[0])
+        self.C = int(self.a["cond_f"].shape[0])
+
+    def c(self) -> rs_batch:
+        return rs_batch(self.P, self.R, self.C, MEM_HOST, *[_ptr(self.a[f]) for f in _FIELDS])
+
+
+# ------------------------------------------------------------------------------- context
+
+class Context:
+    def __init__(self, device: int = 0, flags: int = 0, mem_budget_bytes: int = 0,
+                 autotune_cache: str | None = None):
+        cfg = rs_config(device, flags, mem_budget_bytes,
+                        autotune_cache.encode() if autotune_cache else None)
+        h = ctypes.c_void_p()
+        check(lib().rs_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            check(lib().rs_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # datasets
+    def dataset(self, X, y, K: int, stream=None) -> int:
+        """Register X (N x F float32) and y (int32[N]); numpy -> host path, torch cuda -> device."""
+        import torch
+        if isinstance(X, np.ndarray):
+            Xc = np.ascontiguousarray(X, np.float32)
+            yc = np.ascontiguousarray(y, np.int32)
+            mem = MEM_HOST
+        else:
+            Xc = X.contiguous().to(torch.float32)
+            yc = y.contiguous().to(torch.int32)
+            mem = MEM_DEVICE if Xc.is_cuda else MEM_HOST
+        N, F = Xc.shape
+        out = ctypes.c_uint64()
+        check(lib().rs_dataset_create(self.h, _ptr(Xc), _ptr(yc), N, F, K, mem,
+                                      _stream_ptr(stream), ctypes.byref(out)))
+        return out.value
+
+    def dataset_destroy(self, ds: int):
+        check(lib().rs_dataset_destroy(self.h, ds))
+
+    def dataset_info(self, ds: int):
+        N, F, K = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().rs_dataset_info(self.h, ds, ctypes.byref(N), ctypes.byref(F), ctypes.byref(K), None))
+        cc = np.zeros(K.value, np.int64)
+        check(lib().rs_dataset_info(self.h, ds, None, None, None, _ptr(cc)))
+        return N.value, F.value, K.value, cc
+
+    # hard
+    def eval_hard(self, ds: int, batch, K: int, N: int | None = None, per_class=True, preds=False,
+                  out=None, stream=None):
+        """Returns (correct, per_class or None, preds or None) as torch tensors (device batch)
+        or numpy arrays (host batch)."""
+        cb = batch.c()
+        P = cb.P
+        if cb.mem == MEM_DEVICE:
+            import torch
+            dev = batch.t["set_default"].device
+            if out is not None:
+                correct, pc, pr = out
+            else:
+                correct = torch.empty(P, dtype=torch.int32, device=dev)
+                pc = torch.empty((P, K), dtype=torch.int32, device=dev) if per_class else None
+                pr = torch.empty((P, N), dtype=torch.int32, device=dev) if preds else None
+        else:
+            correct = np.zeros(P, np.int32)
+            pc = np.zeros((P, K), np.int32) if per_class else None
+            pr = np.zeros((P, N), np.int32) if preds else None
+        check(lib().rs_eval_hard(self.h, ds, ctypes.byref(cb), _ptr(correct), _ptr(pc), _ptr(pr),
+                                 _stream_ptr(stream)))
+        return correct, pc, pr
+
+    # soft
+    def soft_fwd(self, ds: int, batch, tau: float, N: int | None = None, K: int | None = None,
+                 probs=False, stream=None):
+        import torch
+        cb = batch.c()
+        dev = batch.t["set_default"].device
+        loss = torch.empty(cb.P, dtype=torch.float32, device=dev)
+        pr = torch.empty((cb.P, N, K), dtype=torch.float32, device=dev) if probs else None
+        check(lib().rs_eval_soft_fwd(self.h, ds, ctypes.byref(cb), float(tau), _ptr(loss), _ptr(pr),
+                                     _stream_ptr(stream)))
+        return loss, pr
+
+    def soft_bwd(self, ds: int, batch, tau: float, dloss, want_loss=True, stream=None):
+        import torch
+        cb = batch.c()
+        dev = batch.t["set_default"].device
+        ga = torch.empty(cb.C, dtype=torch.float32, device=dev)
+        gb = torch.empty(cb.C, dtype=torch.float32, device=dev)
+        gt = torch.empty(cb.C, dtype=torch.float32, device=dev)
+        loss = torch.empty(cb.P, dtype=torch.float32, device=dev) if want_loss else None
+        dl = dloss.contiguous().to(torch.float32)
+        check(lib().rs_eval_soft_bwd(self.h, ds, ctypes.byref(cb), float(tau), _ptr(dl), _ptr(ga),
+                                     _ptr(gb), _ptr(gt), _ptr(loss), _stream_ptr(stream)))
+        return ga, gb, gt, loss
+
+    # tuning
+    def set_tile_config(self, cfg_id: int):
+        check(lib().rs_set_tile_config(self.h, cfg_id))
+
+    def autotune(self, ds: int, batch, stream=None) -> int:
+        best = ctypes.c_int32(-1)
+        cb = batch.c()
+        check(lib().rs_autotune(self.h, ds, ctypes.byref(cb), _stream_ptr(stream), ctypes.byref(best)))
+        return best.value
+
+    def check_async(self, stream=None):
+        check(lib().rs_check(self.h, _stream_ptr(stream)))
+
+    def selftest_threshold_rewrite(self, a, t, op) -> int:
+        a = np.ascontiguousarray(a, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        op = np.ascontiguousarray(op, np.int8)
+        mm = ctypes.c_uint64()
+        check(lib().rs_selftest_threshold_rewrite(self.h, _ptr(a), _ptr(t), _ptr(op), len(a),
+                                                  ctypes.byref(mm)))
+        return mm.value
+
+
+def tile_configs():
+    out = []
+    for i in range(lib().rs_tile_config_count()):
+        s, w, v = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().rs_tile_config_info(i, ctypes.byref(s), ctypes.byref(w), ctypes.byref(v)))
+        out.append({"id": i, "samples_per_tile": s.value, "warps": w.value, "samples_per_lane": v.value})
+    return out
+
+
+# ------------------------------------------------------------------------------- autograd
+
+def _make_soft_fn():
+    import torch
+
+    class RuleSoftFn(torch.autograd.Function):
+        """loss[P] = soft first-fire cross-entropy of every set; gradients w.r.t. the condition
+        coefficients a, b and thresholds t come from the library's adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, a, b, t, rsctx, ds, structure, tau):
+            batch = structure.with_params(a.detach().contiguous(), b.detach().contiguous(),
+                                          t.detach().contiguous())
+            loss, _ = rsctx.soft_fwd(ds, batch, tau)
+            ctx.save_for_backward(a, b, t)
+            ctx.rs = (rsctx, ds, structure, tau)
+            return loss
+
+        @staticmethod
+        def backward(ctx, dloss):
+            a, b, t = ctx.saved_tensors
+            rsctx, ds, structure, tau = ctx.rs
+            batch = structure.with_params(a.detach().contiguous(), b.detach().contiguous(),
+                                          t.detach().contiguous())
+            ga, gb, gt, _ = rsctx.soft_bwd(ds, batch, tau, dloss, want_loss=False)
+            return ga, gb, gt, None, None, None, None
+
+    return RuleSoftFn
+
+
+_soft_fn = None
+
+
+def rule_soft_loss(a, b, t, rsctx: Context, ds: int, structure: DeviceBatch, tau: float):
+    """Differentiable per-set loss (torch.autograd.Function over rs_eval_soft_fwd/bwd)."""
+    global _soft_fn
+    if _soft_fn is None:
+        _soft_fn = _make_soft_fn()
+    return _soft_fn.apply(a, b, t, rsctx, ds, structure, tau)

@@ -1,0 +1,255 @@
+"""GPU parity of the hard evaluator against the CPU oracle: bit-exact predictions and counts.
+
+All calls go through the C ABI (librs.so via the ctypes binding)."""
+import numpy as np
+import pytest
+
+from paper_2406_01821_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    assert torch.cuda.is_available()
+    c = rs.Context(0)
+    yield c
+    c.close()
+
+
+def run_gpu(ctx, X, y, K, batch, preds=True, tile=None, host=False):
+    import torch
+    from paper_2406_01821_gb300 import rs
+    ds = ctx.dataset(X, y, K)
+    try:
+        if tile is not None:
+            ctx.set_tile_config(tile)
+        b = rs.HostBatch(batch) if host else rs.DeviceBatch.from_host(batch)
+        correct, pc, pr = ctx.eval_hard(ds, b, K, len(X), per_class=True, preds=preds)
+        if not host:
+            torch.cuda.synchronize()
+            correct, pc = correct.cpu().numpy(), pc.cpu().numpy()
+            pr = pr.cpu().numpy() if pr is not None else None
+        return correct, pc, pr
+    finally:
+        ctx.set_tile_config(-1)
+        ctx.dataset_destroy(ds)
+
+
+def assert_same(got, want, preds=True):
+    assert np.array_equal(got[0], want[0]), "correct counts differ"
+    assert np.array_equal(got[1], want[1]), "per-class counts differ"
+    if preds:
+        assert np.array_equal(got[2], want[2]), "predictions differ"
+
+
+def test_plain_hard_config_bit_exact(ctx, orc):
+    w = synth.plain_hard(seed=0)
+    got = run_gpu(ctx, w.X, w.y, w.K, w.batch)
+    want = orc.eval_hard(w.X, w.y, w.K, w.batch, want_preds=True)
+    assert_same(got, want)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ragged_reduced_bit_exact(ctx, orc, seed):
+    """The ragged 10-class workload at reduced N (ragged tail: N not a multiple of any tile)."""
+    X, y = synth.gaussian_mixture(20011, 128, 10, seed)
+    b = synth.random_rulesets(synth.quantile_table(X), 10, 192, (1, 64), (1, 8), seed)
+    got = run_gpu(ctx, X, y, 10, b, preds=False)
+    want = orc.eval_hard(X, y, 10, b)
+    assert_same(got, want, preds=False)
+
+
+def test_every_tile_config_identical(ctx, orc):
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.gaussian_mixture(3001, 48, 4, 5)
+    b = synth.random_rulesets(synth.quantile_table(X), 4, 40, (1, 20), (1, 6), 5)
+    want = orc.eval_hard(X, y, 4, b, want_preds=True)
+    for cfg in rs.tile_configs():
+        got = run_gpu(ctx, X, y, 4, b, tile=cfg["id"])
+        assert_same(got, want)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_boundary_crowded_inputs(ctx, orc, seed):
+    rng = np.random.default_rng(seed)
+    F = int(rng.integers(1, 9))
+    X0 = rng.standard_normal((4096, F)).astype(np.float32)
+    b = synth.random_rulesets(synth.quantile_table(X0), 3, 24, (1, 8), (1, 4), seed,
+                              pair_prob=0.5 if F > 1 else 0.0)
+    X = synth.boundary_samples(b, F, 2500, seed, frac=0.9, ulps=2)
+    y = rng.integers(0, 3, len(X)).astype(np.int32)
+    got = run_gpu(ctx, X, y, 3, b)
+    want = orc.eval_hard(X, y, 3, b, want_preds=True)
+    assert_same(got, want)
+
+
+def special_values(rng, n):
+    pool = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-45, -1e-45, 1e-40, -1e-40, 1.17549435e-38,
+                     3.4028235e38, -3.4028235e38, 1.0, -1.0, 0.5, 2.0, 1e-30, 1e30], np.float32)
+    return pool[rng.integers(0, len(pool), n)]
+
+
+def test_special_values_in_data_and_coefficients(ctx, orc):
+    rng = np.random.default_rng(11)
+    N, F = 1500, 4
+    X = rng.standard_normal((N, F)).astype(np.float32)
+    mask = rng.random((N, F)) < 0.3
+    X[mask] = special_values(rng, int(mask.sum()))
+    b = synth.random_rulesets(synth.quantile_table(rng.standard_normal((256, F)).astype(np.float32)),
+                              2, 32, (1, 6), (1, 3), 11, pair_prob=0.4)
+    for arr in (b.cond_a, b.cond_b, b.cond_t):
+        m = rng.random(len(arr)) < 0.25
+        arr[m] = special_values(rng, int(m.sum()))
+    y = rng.integers(0, 2, N).astype(np.int32)
+    got = run_gpu(ctx, X, y, 2, b)
+    want = orc.eval_hard(X, y, 2, b, want_preds=True)
+    assert_same(got, want)
+
+
+def test_subnormal_products(ctx, orc):
+    """Products that land in the subnormal range must not be flushed to zero."""
+    rng = np.random.default_rng(3)
+    N = 2000
+    X = (rng.standard_normal((N, 2)) * 1e-20).astype(np.float32)
+    rules = []
+    for t in (0.0, 1e-42, -1e-42, 1e-40):
+        rules.append((1, [(0, -1, synth.GT, 1e-20, 0.0, t)]))
+        rules.append((1, [(1, 0, synth.LT, 3e-21, 2e-19, 0.0)]))
+    b = synth.from_lists([rules[i:i + 2] for i in range(0, len(rules), 2)], [0] * (len(rules) // 2))
+    y = rng.integers(0, 2, N).astype(np.int32)
+    got = run_gpu(ctx, X, y, 2, b)
+    want = orc.eval_hard(X, y, 2, b, want_preds=True)
+    assert_same(got, want)
+
+
+@pytest.mark.parametrize("N,F,K", [(1, 1, 2), (31, 3, 2), (33, 5, 3), (257, 256, 2), (700, 300, 4),
+                                   (129, 7, 40)])
+def test_shapes(ctx, orc, N, F, K):
+    rng = np.random.default_rng(N + F)
+    X = rng.standard_normal((N, F)).astype(np.float32)
+    y = rng.integers(0, K, N).astype(np.int32)
+    b = synth.random_rulesets(synth.quantile_table(X), K, 17, (1, 9), (1, 5), N, pair_prob=0.3 if F > 1 else 0)
+    got = run_gpu(ctx, X, y, K, b)
+    want = orc.eval_hard(X, y, K, b, want_preds=True)
+    assert_same(got, want)
+
+
+def test_empty_sets_rules_and_degenerate_cases(ctx, orc):
+    X, y = synth.two_class_gaussian(999, 4, 2)
+    sets = [
+        [],                                                    # empty set -> default
+        [(1, [])],                                             # empty rule fires everywhere
+        [(0, [(0, -1, synth.GT, 1.0, 0.0, 0.0)]), (1, []), (0, [(1, -1, synth.LT, 1.0, 0.0, 5.0)])],
+        [(1, [(0, -1, synth.GT, 1.0, 0.0, np.inf)])],          # never true
+        [(1, [(2, -1, synth.LT, 0.0, 0.0, 1.0)])],             # coefficient 0
+        [(0, [(3, 1, synth.GT, 1.0, 1.0, 0.0)])],              # x3 > x1
+        [(1, [(2, 2, synth.LT, 1.0, 1.0, 0.0)])],              # same feature both sides
+    ]
+    b = synth.from_lists(sets, [0, 1, 0, 1, 0, 1, 0])
+    got = run_gpu(ctx, X, y, 2, b)
+    want = orc.eval_hard(X, y, 2, b, want_preds=True)
+    assert_same(got, want)
+
+
+def test_zero_sets(ctx):
+    X, y = synth.two_class_gaussian(100, 3, 0)
+    b = synth.from_lists([], [])
+    got = run_gpu(ctx, X, y, 2, b)
+    assert got[0].shape == (0,)
+
+
+def test_host_batch_path_matches(ctx, orc):
+    w = synth.plain_hard(seed=3)
+    got = run_gpu(ctx, w.X, w.y, w.K, w.batch, host=True)
+    want = orc.eval_hard(w.X, w.y, w.K, w.batch, want_preds=True)
+    assert_same(got, want)
+
+
+def test_repeated_calls_and_graph_replay(ctx, orc):
+    """Consecutive calls of different shapes on one stream (graph update path) stay exact."""
+    import torch
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.gaussian_mixture(5000, 16, 3, 9)
+    ds = ctx.dataset(X, y, 3)
+    s = torch.cuda.Stream()
+    try:
+        for seed in range(4):
+            b = synth.random_rulesets(synth.quantile_table(X), 3, 20 + 7 * seed, (1, 12), (1, 5), seed)
+            with torch.cuda.stream(s):
+                c, pc, _ = ctx.eval_hard(ds, rs.DeviceBatch.from_host(b), 3, stream=s)
+            s.synchronize()
+            want = orc.eval_hard(X, y, 3, b)
+            assert np.array_equal(c.cpu().numpy(), want[0])
+            assert np.array_equal(pc.cpu().numpy(), want[1])
+    finally:
+        ctx.dataset_destroy(ds)
+
+
+@pytest.mark.parametrize("what", ["feature", "pair_feature", "class", "default", "op", "offsets"])
+def test_malformed_batch_rejected(ctx, what):
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.two_class_gaussian(300, 4, 0)
+    b = synth.random_rulesets(synth.quantile_table(X), 2, 6, 3, 2, 0, pair_prob=0.5)
+    if what == "feature":
+        b.cond_f[3] = 4
+    elif what == "pair_feature":
+        b.cond_g[2] = 9
+    elif what == "class":
+        b.rule_class[1] = 2
+    elif what == "default":
+        b.set_default[0] = -1
+    elif what == "op":
+        b.cond_op[0] = 7
+    else:
+        b.rule_cond_off[2] = b.rule_cond_off[3] + 1
+    ds = ctx.dataset(X, y, 2)
+    try:
+        with pytest.raises(rs.RsError) as ei:
+            ctx.eval_hard(ds, rs.DeviceBatch.from_host(b), 2)
+        assert ei.value.code == -1
+    finally:
+        ctx.dataset_destroy(ds)
+
+
+def test_threshold_rewrite_exhaustive(ctx):
+    """For every float32 x: fl(a*x) op t equals the rewritten single compare."""
+    a = [1.0, -1.0, 0.7, -0.3, 1e-30, -1e-30, 3e38, 1e-45, -1e-45, 2.5, 0.0, -0.0, np.inf, np.nan,
+         0.5, 1.0000001]
+    t = [0.38, -2.02, 1e-44, -1e-40, 1e-44, 5.0, -np.inf, 0.0, -0.0, np.inf, 1.0, -1.0, 0.3, 0.0,
+         3.4e38, -1e-38]
+    op = [0, 1] * 8
+    mm = ctx.selftest_threshold_rewrite(np.array(a, np.float32), np.array(t, np.float32),
+                                        np.array(op, np.int8))
+    assert mm == 0
+    # and the '<' of every pair too
+    mm = ctx.selftest_threshold_rewrite(np.array(a, np.float32), np.array(t, np.float32),
+                                        1 - np.array(op, np.int8))
+    assert mm == 0
+
+
+def test_ragged_full_size_sampled(ctx, orc):
+    """The full ragged workload (P=4096, N=2^20, F=128, 10 classes) in the benchmark's launch
+    configuration; sampled sets are recomputed one by one by the oracle, and every set satisfies
+    correct = sum_k per_class <= N."""
+    import torch
+    from paper_2406_01821_gb300 import rs
+    w = synth.ragged_hard(seed=0)
+    ds = ctx.dataset(w.X, w.y, w.K)
+    try:
+        db = rs.DeviceBatch.from_host(w.batch)
+        correct, pc, _ = ctx.eval_hard(ds, db, w.K)
+        torch.cuda.synchronize()
+        correct, pc = correct.cpu().numpy(), pc.cpu().numpy()
+    finally:
+        ctx.dataset_destroy(ds)
+    assert np.array_equal(pc.sum(axis=1), correct)
+    assert (correct <= w.N).all() and (correct >= 0).all()
+    sample = np.random.default_rng(0).choice(w.batch.P, 6, replace=False)
+    sub = w.batch.subset(sample)
+    want_c, want_pc, _ = orc.eval_hard(w.X, w.y, w.K, sub)
+    assert np.array_equal(correct[sample], want_c)
+    assert np.array_equal(pc[sample], want_pc)

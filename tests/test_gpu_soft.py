@@ -1,0 +1,162 @@
+"""GPU parity of the soft path (sigmoid-relaxed forward and hand-written adjoint) against the
+float64 oracle.
+
+Tolerance (float32 against float64): loss within 1e-5 relative; each gradient element within
+1e-5 x max(|g64|, m64), where m64 = |dloss| (1/N) sum_n |d ell_n / d theta| is the scale of the
+cancelling sum over samples that float32 round-off is measured against."""
+import numpy as np
+import pytest
+
+from paper_2406_01821_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    c = rs.Context(0)
+    yield c
+    c.close()
+
+
+def soft_gpu(ctx, X, y, K, b, tau, dloss, probs=False):
+    import torch
+    from paper_2406_01821_gb300 import rs
+    ds = ctx.dataset(X, y, K)
+    try:
+        db = rs.DeviceBatch.from_host(b)
+        dl = torch.tensor(np.asarray(dloss, np.float32), device="cuda")
+        ga, gb, gt, loss = ctx.soft_bwd(ds, db, tau, dl)
+        out = {"loss": loss, "grad_a": ga, "grad_b": gb, "grad_t": gt}
+        if probs:
+            lf, pr = ctx.soft_fwd(ds, db, tau, N=len(X), K=K, probs=True)
+            out["loss_fwd"], out["probs"] = lf, pr
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in out.items()}
+    finally:
+        ctx.dataset_destroy(ds)
+
+
+def check_against_oracle(got, ref):
+    assert np.allclose(got["loss"], ref["loss"], rtol=RTOL, atol=0), \
+        np.max(np.abs(got["loss"] / ref["loss"] - 1))
+    for n in ("a", "b", "t"):
+        g, r, m = got["grad_" + n], ref["grad_" + n], ref["mag_" + n]
+        err = np.abs(g - r)
+        bound = RTOL * np.maximum(np.abs(r), m) + 1e-30
+        assert (err <= bound).all(), (n, float(np.max(err / bound)))
+
+
+def reachable(b):
+    b.set_default[:] = np.where(b.rule_class[b.set_rule_off[:-1]] == 0, 1, 0)
+    return b
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_soft_small_vs_oracle(ctx, orc, seed):
+    X, y = synth.two_class_gaussian(3001, 8, seed)
+    b = reachable(synth.random_rulesets(synth.quantile_table(X), 2, 12, (1, 8), (1, 4), seed))
+    dl = np.random.default_rng(seed).uniform(-1, 2, b.P)
+    got = soft_gpu(ctx, X, y, 2, b, 0.1, dl)
+    ref = orc.soft(X, y, 2, b, 0.1, dloss=dl, want_mag=True)
+    check_against_oracle(got, ref)
+
+
+def test_soft_multiclass_probs(ctx, orc):
+    rng = np.random.default_rng(4)
+    X, _ = synth.gaussian_mixture(777, 6, 4, 4)
+    y = rng.integers(0, 4, len(X)).astype(np.int32)
+    b = synth.random_rulesets(synth.quantile_table(X), 4, 6, (3, 6), (1, 3), 4, default=3)
+    for p in range(b.P):      # classes 0..2 on the first rules, 3 by default: all reachable
+        r0 = b.set_rule_off[p]
+        b.rule_class[r0:r0 + 3] = np.arange(3)
+    got = soft_gpu(ctx, X, y, 4, b, 0.5, np.ones(b.P), probs=True)
+    ref = orc.soft(X, y, 4, b, 0.5, dloss=np.ones(b.P), want_probs=True, want_mag=True)
+    assert np.allclose(got["probs"].sum(axis=2), 1.0, atol=1e-5)
+    assert np.allclose(got["probs"], ref["probs"], rtol=1e-4, atol=1e-6)
+    assert np.array_equal(got["loss_fwd"], got["loss"])     # the forward and the fused pass agree
+    check_against_oracle(got, ref)
+
+
+def test_soft_ragged_and_pairs(ctx, orc):
+    X, y = synth.two_class_gaussian(2049, 16, 7)
+    b = reachable(synth.random_rulesets(synth.quantile_table(X), 2, 20, (1, 32), (1, 8), 7, pair_prob=0.5))
+    got = soft_gpu(ctx, X, y, 2, b, 0.25, np.ones(b.P))
+    ref = orc.soft(X, y, 2, b, 0.25, dloss=np.ones(b.P), want_mag=True)
+    check_against_oracle(got, ref)
+
+
+def test_soft_is_deterministic(ctx):
+    X, y = synth.two_class_gaussian(5000, 8, 1)
+    b = reachable(synth.random_rulesets(synth.quantile_table(X), 2, 16, (1, 8), (1, 4), 1))
+    g1 = soft_gpu(ctx, X, y, 2, b, 0.1, np.ones(b.P))
+    g2 = soft_gpu(ctx, X, y, 2, b, 0.1, np.ones(b.P))
+    for k in g1:
+        assert np.array_equal(g1[k], g2[k]), k
+
+
+def test_autograd_function(ctx, orc):
+    import torch
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.two_class_gaussian(1500, 6, 2)
+    b = reachable(synth.random_rulesets(synth.quantile_table(X), 2, 5, (1, 6), (1, 3), 2))
+    ds = ctx.dataset(X, y, 2)
+    try:
+        st = rs.DeviceBatch.from_host(b)
+        a = st.t["cond_a"].clone().requires_grad_(True)
+        bb = st.t["cond_b"].clone().requires_grad_(True)
+        t = st.t["cond_t"].clone().requires_grad_(True)
+        loss = rs.rule_soft_loss(a, bb, t, ctx, ds, st, 0.1)
+        w = torch.linspace(0.5, 1.5, b.P, device="cuda")
+        (loss * w).sum().backward()
+        ref = orc.soft(X, y, 2, b, 0.1, dloss=w.cpu().numpy().astype(np.float64), want_mag=True)
+        got = {"loss": loss.detach().cpu().numpy(), "grad_a": a.grad.cpu().numpy(),
+               "grad_b": bb.grad.cpu().numpy(), "grad_t": t.grad.cpu().numpy()}
+        check_against_oracle(got, ref)
+    finally:
+        ctx.dataset_destroy(ds)
+
+
+def test_soft_rejects_malformed(ctx):
+    from paper_2406_01821_gb300 import rs
+    import torch
+    X, y = synth.two_class_gaussian(100, 3, 0)
+    b = synth.random_rulesets(synth.quantile_table(X), 2, 3, 2, 2, 0)
+    b.cond_f[0] = 3
+    ds = ctx.dataset(X, y, 2)
+    try:
+        with pytest.raises(rs.RsError):
+            ctx.soft_bwd(ds, rs.DeviceBatch.from_host(b), 0.1, torch.ones(3, device="cuda"))
+    finally:
+        ctx.dataset_destroy(ds)
+
+
+def test_soft_full_size_sampled(ctx, orc):
+    """The fine-tuning workload at full size (P=1024 x R=32 x C=4, N=262144, F=64, tau=0.1):
+    loss and gradients of sampled sets against the float64 oracle."""
+    import torch
+    from paper_2406_01821_gb300 import rs
+    w = synth.soft_tune(seed=0)
+    b = reachable(w.batch)
+    ds = ctx.dataset(w.X, w.y, w.K)
+    try:
+        db = rs.DeviceBatch.from_host(b)
+        dl = torch.ones(b.P, device="cuda")
+        ga, gb, gt, loss = ctx.soft_bwd(ds, db, w.tau, dl)
+        torch.cuda.synchronize()
+        got_all = {"loss": loss.cpu().numpy(), "grad_a": ga.cpu().numpy(),
+                   "grad_b": gb.cpu().numpy(), "grad_t": gt.cpu().numpy()}
+    finally:
+        ctx.dataset_destroy(ds)
+    sample = np.array([0, 517, 1023])
+    sub = b.subset(sample)
+    ref = orc.soft(w.X, w.y, w.K, sub, w.tau, dloss=np.ones(len(sample)), want_mag=True)
+    conds = np.concatenate([np.arange(b.rule_cond_off[b.set_rule_off[p]],
+                                      b.rule_cond_off[b.set_rule_off[p + 1]]) for p in sample])
+    got = {"loss": got_all["loss"][sample]}
+    for n in ("a", "b", "t"):
+        got["grad_" + n] = got_all["grad_" + n][conds]
+    check_against_oracle(got, ref)
