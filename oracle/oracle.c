@@ -225,20 +225,25 @@ int orc_soft(const float *X, int64_t N, int32_t F, const int32_t *y, int32_t K,
                 if (probs)
                     for (int32_t k = 0; k < K; ++k) probs[((int64_t)p * N + n) * K + k] = exp(lp[k]);
                 if (!dloss) continue;
-                /* adjoint: lS = log P(outcome y | evaluation starts at rule j+1) */
+                /* adjoint. S_j = P(outcome y | evaluation starts at rule j), T_j = 1 - S_j, both
+                 * kept as logs of sums of positive terms. d ell / d lq_j = exp(lq_j + lu_j - lp_y)
+                 * * (S_{j+1} - [cls_j = y]), written as +exp(.. + lS) or -exp(.. + lT). */
                 const double scale = dloss[p] / (double)N;
                 const double lpy = lp[yn];
                 double lS = (b->set_default[p] == yn) ? 0.0 : -INFINITY;
+                double lT = (b->set_default[p] == yn) ? -INFINITY : 0.0;
                 for (int32_t j = R - 1; j >= 0; --j) {
                     const int32_t r = r0 + j;
                     const int same = (b->rule_class[r] == yn);
 #if ORC_PLANT == 7
-                    double gq = exp(lq[j] + lu[j] - lpy);     /* planted: later outcomes dropped */
+                    double gq = same ? -exp(lq[j] + lu[j] + lS - lpy)     /* planted: S for 1-S */
+                                     : exp(lq[j] + lu[j] + lS - lpy);
 #else
-                    double gq = exp(lq[j] + lu[j] + lS - lpy);
+                    double gq = same ? -exp(lq[j] + lu[j] + lT - lpy)
+                                     : exp(lq[j] + lu[j] + lS - lpy);
 #endif
-                    if (same) gq -= exp(lq[j] + lu[j] - lpy);
                     lS = log_add(same ? lq[j] : -INFINITY, l1q[j] + lS);
+                    lT = log_add(same ? -INFINITY : lq[j], l1q[j] + lT);
                     for (int32_t c = b->rule_cond_off[r]; c < b->rule_cond_off[r + 1]; ++c) {
                         const double u = margin(b, c, xrow, tau);
                         const double du = gq * exp(log_sigmoid(-u));      /* d ell / d u */

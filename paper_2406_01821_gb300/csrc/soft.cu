@@ -6,8 +6,14 @@
 //                lu_r = sum_{j<r} l1q_j             (log probability that no earlier rule fired)
 // Class k        log p_k = logsumexp over rules of class k of (lq_r + lu_r), plus lu_R for the
 //                default class.  Loss  L_p = (1/N) sum_n -log p_{y_n}.
-// Adjoint        lS_R = 0 if default = y else -inf;  lS_r = logsumexp([cls_r = y] lq_r, l1q_r + lS_{r+1})
-//                dl/dlq_r = exp(lq_r + lu_r + lS_{r+1} - lp) - [cls_r = y] exp(lq_r + lu_r - lp)
+// Adjoint        S_r = P(outcome y | evaluation starts at rule r), T_r = 1 - S_r, both kept as logs
+//                and both sums of positive terms:
+//                  lS_R = 0 if default = y else -inf;  lS_r = logsumexp([cls_r = y] lq_r, l1q_r + lS_{r+1})
+//                  lT_R = 0 if default != y else -inf; lT_r = logsumexp([cls_r != y] lq_r, l1q_r + lT_{r+1})
+//                dl/dlq_r = exp(lq_r + lu_r - lp) * (S_{r+1} - [cls_r = y])
+//                         =  exp(lq_r + lu_r + lS_{r+1} - lp)   if cls_r != y
+//                         = -exp(lq_r + lu_r + lT_{r+1} - lp)   if cls_r  = y
+//                (the second form avoids the cancellation of S_{r+1} - 1 when S_{r+1} is near 1)
 //                dl/du_c  = dl/dlq_r * sigmoid(-u_c);  du/da = s x_f / tau, du/dt = -s / tau,
 //                du/db = -s x_g / tau.
 // Everything is evaluated in float32 in the log domain, which keeps 1 - q_r and the products of
@@ -201,14 +207,16 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
             if (!BWD) continue;
             // ---------------- adjoint
             float lS = (deflt == yn) ? 0.f : -INFINITY;
+            float lT = (deflt == yn) ? -INFINITY : 0.f;
             for (int j = R - 1; j >= 0; --j) {
                 const int r = rb + j;
                 const float lqj = lq[j][lane], luj = lu[j][lane];
                 const bool same = a.rule_class[r] == yn;
-                float gq = expf(lqj + luj + lS - lpy);
-                if (same) gq -= expf(lqj + luj - lpy);
+                float gq = same ? -expf(lqj + luj + lT - lpy) : expf(lqj + luj + lS - lpy);
                 if (!valid) gq = 0.f;
-                lS = log_add(same ? lqj : -INFINITY, logf(-expm1f(lqj)) + lS);
+                const float l1q = logf(-expm1f(lqj));
+                lS = log_add(same ? lqj : -INFINITY, l1q + lS);
+                lT = log_add(same ? -INFINITY : lqj, l1q + lT);
                 const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
                 for (int c = c0; c < c1; ++c) {
                     const SoftRec rc = a.recs[c];

@@ -16,7 +16,7 @@ PLANTS = {
     4: ("last firing rule wins", [lambda o: pins.test_fig1b_points(o, 0)]),
     5: ("later rules not discounted", [lambda o: pins.test_soft_probabilities_sum_to_one(o)]),
     6: ("threshold gradient sign", [lambda o: pins.test_one_rule_one_condition_is_logistic_regression(o, 0, False)]),
-    7: ("later outcomes dropped from the adjoint", [lambda o: pins.test_adjoint_matches_central_differences(o, 0)]),
+    7: ("S used where 1 - S belongs in the adjoint", [lambda o: pins.test_adjoint_matches_central_differences(o, 0)]),
 }
 
 
