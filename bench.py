@@ -1,0 +1,407 @@
+"""Benchmark: population fitness evaluation of ordered rule sets on one GB300 (or N, one per rank).
+
+Headline workload: the ragged batched hard evaluation -- P=4096 rule sets with R~U{1..64} rules
+of C~U{1..8} conditions, N=2^20 samples x F=128 float32 features, 10 classes -- evaluated through
+the C ABI (rs_eval_hard) against a resident dataset. One step = one full population evaluation
+(packing + validation + the evaluator kernel + exact counts). value = nominal condition-evals/s
+(sum over sets and rules of the rule's condition count x N, per second), summed over ranks.
+
+Extra legs on the same line: the soft fine-tuning pass (P=1024 x R=32 x C=4, N=262144, F=64,
+tau=0.1, forward + adjoint). The CPU oracle is timed on a bounded sample of the same workload.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--no-extras]
+Multi-GPU: torchrun --nproc-per-node N bench.py --gpus N  (each rank evaluates its own
+population on its own GPU: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "condition-evals/s & rule-set·samples/s vs plain; p50/p99 served latency"
+UNIT = "condition-evals/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hard_eval_counters.json")
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def hard_algorithmic_ops(batch, N):
+    """Algorithmic lane operations of one evaluation: 1 compare per threshold condition-eval,
+    2 multiplies + 1 compare per pair condition-eval, and per rule 3 word operations (AND,
+    AND-NOT, popcount) per 32 samples."""
+    n_pair = int((batch.cond_g >= 0).sum())
+    n_thr = batch.C - n_pair
+    return N * (n_thr + 3 * n_pair) + 3 * batch.R * ((N + 31) // 32)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("hard_eval.cu", "pack.cu", "rs_internal.cuh", "tma.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_01821_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the evaluator from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    try:
+        with open(PROFILE_SUMMARY) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch_full")
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(w, n_sample: int, threads: int = 0):
+    import oracle
+    Xs, ys = w.X[:n_sample], w.y[:n_sample]
+    nt = oracle.num_threads(threads)
+    oracle.eval_hard(Xs[:256], ys[:256], w.K, w.batch, nthreads=nt)      # warm
+    t0 = time.perf_counter()
+    oracle.eval_hard(Xs, ys, w.K, w.batch, nthreads=nt)
+    dt = time.perf_counter() - t0
+    v = w.batch.nominal_conditions() * n_sample / dt
+    return {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"all {w.batch.P} sets on the first {n_sample} of {w.N} samples "
+                      f"({dt:.2f} s wall, OpenMP over sets)"}
+
+
+# ----------------------------------------------------------------------------- legs
+
+def hard_leg(args, rank, dev, ctx_mod, w):
+    import torch
+    from paper_2406_01821_gb300 import rs
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rs.Context(dev, flags=rs.CTX_PROFILE)
+    ds = ctx.dataset(w.X, w.y, w.K)
+    db = rs.DeviceBatch.from_host(w.batch, device=f"cuda:{dev}")
+    tile = ctx.autotune(ds, db, stream=stream)
+    P, K, N = w.batch.P, w.K, w.N
+    out = (torch.empty(P, dtype=torch.int32, device=dev),
+           torch.empty((P, K), dtype=torch.int32, device=dev), None)
+    for _ in range(args.warmup):
+        ctx.eval_hard(ds, db, K, out=out, stream=stream)
+    stream.synchronize()
+    ctx_mod.barrier()
+    ctx.profile(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.eval_hard(ds, db, K, out=out, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile(reset=True)
+    correct = out[0].cpu().numpy()
+
+    # end to end through the public call with pinned host buffers (copies inside the region)
+    hb = rs.HostBatch(w.batch)
+    pinned = {}
+    for f, a in hb.a.items():
+        t = torch.empty(a.shape, dtype=torch.from_numpy(a).dtype, pin_memory=True)
+        t.numpy()[...] = a
+        pinned[f] = t
+    hb.a = {f: t.numpy() for f, t in pinned.items()}
+    hc = torch.empty(P, dtype=torch.int32, pin_memory=True).numpy()
+    hpc = torch.empty((P, K), dtype=torch.int32, pin_memory=True).numpy()
+    ctx2 = rs.Context(dev)
+    ds2 = ctx2.dataset(w.X, w.y, w.K)
+    from paper_2406_01821_gb300.rs import check, lib, _ptr, _stream_ptr
+    import ctypes
+    cb = hb.c()
+
+    def e2e_call():
+        check(lib().rs_eval_hard(ctx2.h, ds2, ctypes.byref(cb), _ptr(hc), _ptr(hpc), None,
+                                 _stream_ptr(stream)))
+    for _ in range(max(1, args.warmup)):
+        e2e_call()
+    stream.synchronize()
+    t0 = time.perf_counter()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        e2e_call()
+    f1.record(stream)
+    f1.synchronize()
+    e2e_ms = max(f0.elapsed_time(f1), (time.perf_counter() - t0) * 1e3) / args.steps
+    e2e_ok = bool(np.array_equal(hc, correct))
+    ctx2.close()
+    ctx.close()
+    return {"ms": ms, "prof": prof, "tile": tile, "clocks": clk.summary(), "e2e_ms": e2e_ms,
+            "e2e_ok": e2e_ok, "h2d": hb_nbytes(hb), "d2h": hc.nbytes + hpc.nbytes}
+
+
+def hb_nbytes(hb):
+    return int(sum(a.nbytes for a in hb.a.values()))
+
+
+def soft_leg(args, dev):
+    import torch
+    from paper_2406_01821_gb300 import rs, synth
+    w = synth.soft_tune(seed=0)
+    ctx = rs.Context(dev, flags=rs.CTX_PROFILE)
+    stream = torch.cuda.Stream(device=dev)
+    ds = ctx.dataset(w.X, w.y, w.K)
+    db = rs.DeviceBatch.from_host(w.batch, device=f"cuda:{dev}")
+    dl = torch.ones(w.batch.P, device=dev)
+    steps = max(1, args.steps // 5)
+    for _ in range(1):
+        ctx.soft_bwd(ds, db, w.tau, dl, stream=stream)
+    stream.synchronize()
+    ctx.profile(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.soft_bwd(ds, db, w.tau, dl, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = ctx.profile(reset=True)
+    ctx.close()
+    cs = w.batch.nominal_conditions() * w.N
+    return {"workload": w.name, "ms_per_step": ms, "condition_samples_per_s": cs / (ms / 1e3),
+            "rule_set_samples_per_s": w.batch.P * w.N / (ms / 1e3),
+            "kernel_ms": prof["soft_ms"] / max(1, prof["soft_launches"]), "steps": steps,
+            "what": "forward + adjoint (loss and gradients w.r.t. a, b, t of every condition)"}
+
+
+# ----------------------------------------------------------------------------- distributed
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(self.local)
+            dist.init_process_group("nccl", device_id=torch.device(f"cuda:{self.local}"))
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{self.local}")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{self.local}")
+        self.pg.all_reduce(t)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- main
+
+def run_reference(args, d: Dist):
+    """The reference arm: the CPU oracle as it stands, on bounded samples of the workload."""
+    if d.rank != 0:
+        return
+    from paper_2406_01821_gb300 import synth
+    w = synth.ragged_hard(seed=0)
+    n_sample = args.cpu_sample
+    for _ in range(args.warmup):
+        cpu_baseline(w, min(n_sample, 4096))
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, n_sample))
+    dt = (time.perf_counter() - t_all) / args.steps
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": w.name, "sample_per_step": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=131072)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    d = Dist()
+    if args.impl == "reference":
+        run_reference(args, d)
+        d.close()
+        return
+
+    import torch
+    from paper_2406_01821_gb300 import build, rs, synth
+    if d.rank == 0 or d.world == 1:
+        build.build()
+    d.barrier()
+    dev = d.local
+    torch.cuda.set_device(dev)
+    w = synth.ragged_hard(seed=d.rank)         # each rank: its own population of 4096 sets
+    res = hard_leg(args, d.rank, dev, d, w)
+    ms_max = d.max(res["ms"])
+    e2e_max = d.max(res["e2e_ms"])
+    nominal = w.batch.nominal_conditions() * w.N
+    total_nominal = d.sum(float(nominal))
+    total_sets = d.sum(float(w.batch.P))
+    value = total_nominal / (ms_max / 1e3)
+
+    prof = res["prof"]
+    kern_ms = prof["hard_ms"] / max(1, prof["hard_launches"])
+    ops = hard_algorithmic_ops(w.batch, w.N)
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    traffic = profiled_traffic()
+    extras = {}
+    if not args.no_extras and d.rank == 0:
+        try:
+            extras["soft"] = soft_leg(args, dev)
+        except Exception as e:     # an extra leg never hides the headline number
+            extras["soft"] = {"error": repr(e)}
+
+    if d.rank == 0:
+        cb = cpu_baseline(w, args.cpu_sample)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "global_batch": int(total_sets), "samples": w.N,
+                       "features": w.F, "classes": w.K,
+                       "nominal_cond_evals_per_step": int(total_nominal),
+                       "tile_config": rs.tile_configs()[res["tile"]],
+                       "l2": "inputs larger than L2 (feature-major dataset 512 MiB per GPU)",
+                       "parallelism": f"population per GPU x{d.world}"},
+            "rule_set_samples_per_s": total_sets * w.N / (ms_max / 1e3),
+            "roofline": {"bound": "alu", "achieved": ops / (kern_ms / 1e3) / 1e12,
+                         "peak": peak_ops / 1e12, "unit": "Tops/s",
+                         "frac": (ops / (kern_ms / 1e3)) / peak_ops, "traffic": traffic,
+                         "kernel": "k_hard", "kernel_ms": kern_ms,
+                         "ops_per_launch": ops,
+                         "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                        f"({peak_src} max clock)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": total_nominal / (e2e_max / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"],
+                    "ms_per_step": e2e_max, "matches_device_run": res["e2e_ok"]},
+            "clocks": res["clocks"],
+            "gpu_launches": int(prof["launches"]),
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    d.close()
+
+
+if __name__ == "__main__":
+    main()

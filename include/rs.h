@@ -62,6 +62,8 @@ typedef struct rs_ctx rs_ctx;
                                     reported by rs_check (sticky until read) */
 #define RS_CTX_NO_GRAPH     2u   /* launch kernels directly instead of replaying captured graphs */
 #define RS_CTX_NO_AUTOTUNE  4u   /* use the built-in tile heuristic, never time candidates */
+#define RS_CTX_PROFILE      8u   /* bracket the evaluator kernels with CUDA events (read with
+                                    rs_profile_read); implies RS_CTX_NO_GRAPH */
 
 typedef struct {
     int32_t device;              /* CUDA device ordinal */
@@ -193,6 +195,19 @@ rs_status rs_set_tile_config(rs_ctx *ctx, int32_t id);
  * context's table (and its JSON cache file) and return its id in *best. */
 rs_status rs_autotune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, void *stream,
                       int32_t *best);
+
+/* ------------------------------------------------------------------------------- profile */
+
+typedef struct {
+    int64_t launches;        /* kernels the library launched since the last reset */
+    int64_t hard_launches;   /* evaluator (hard) kernel launches timed */
+    double hard_ms;          /* their summed CUDA-event durations (RS_CTX_PROFILE contexts) */
+    int64_t soft_launches;   /* soft forward/adjoint kernel launches timed */
+    double soft_ms;
+} rs_profile;
+
+/* Read the counters of `ctx` (waits for the timed launches to finish); reset them if `reset`. */
+rs_status rs_profile_read(rs_ctx *ctx, rs_profile *out, int32_t reset);
 
 /* ---------------------------------------------------------------------------- test hooks */
 

@@ -20,6 +20,7 @@ rs_status selftest_rewrite(const float *a_h, const float *t_h, const int8_t *op_
                            uint64_t *mismatches, int sm_count);
 void load_tune_table(Ctx *ctx);
 void server_shutdown(Ctx *ctx);
+rs_status profile_read(Ctx *ctx, rs_profile *out, int reset);
 }  // namespace rs
 
 using namespace rs;
@@ -184,6 +185,16 @@ rs_status rs_eval_soft_bwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, floa
         if (!dloss) { set_error("dloss is NULL"); return RS_ERR_INVALID; }
         return eval_soft(ctx, ds, batch, tau, loss, nullptr, dloss, grad_a, grad_b, grad_t,
                          S(stream));
+    })
+}
+
+rs_status rs_profile_read(rs_ctx *ctx, rs_profile *out, int32_t reset)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return profile_read(ctx, out, reset);
     })
 }
 

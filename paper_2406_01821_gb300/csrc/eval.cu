@@ -185,7 +185,7 @@ static rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const
                               int32_t *preds, cudaStream_t stream)
 {
     PackOut po{s.recs, s.sets, s.order, s.status};
-    launch_pack(bd, ds->F, ds->K, po, stream);
+    count_launch(ctx, launch_pack(bd, ds->F, ds->K, po, stream));
     RS_CUDA(cudaGetLastError());
     HardArgs a{};
     a.recs = s.recs;
@@ -251,7 +251,8 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
     // caller is capturing already (then the work simply joins the caller's graph).
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (stream) RS_CUDA(cudaStreamIsCapturing(stream, &cap));
-    const bool use_graph = !(ctx->flags & RS_CTX_NO_GRAPH) && tile_override < 0 && stream != nullptr &&
+    const bool use_graph = !(ctx->flags & (RS_CTX_NO_GRAPH | RS_CTX_PROFILE)) && tile_override < 0 &&
+                           stream != nullptr &&
                            cap == cudaStreamCaptureStatusNone;
     if (use_graph) {
         // Capture pack + evaluate, then update the cached executable for this shape bucket
@@ -310,6 +311,7 @@ rs_status finish_status(Ctx *ctx, const uint32_t *d_status, cudaStream_t stream)
     if (ctx->flags & RS_CTX_ASYNC) {
         k_merge_status<<<1, 1, 0, stream>>>(d_status, ctx->d_sticky);
         RS_CUDA(cudaGetLastError());
+        count_launch(ctx);
         return RS_OK;
     }
     uint32_t *hs = host_status_slot();

@@ -244,8 +244,12 @@ rs_status launch_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t stream
     if (!tm) return RS_ERR_DEVICE;
     const int tiles = (int)((a.N + 32 * V - 1) / (32 * V));
     dim3 grid(tiles, a.groups);
-    k_hard<V, W><<<grid, W * 32, smem, stream>>>(*tm, a);
+    {
+        TimedLaunch tl(ctx, TK_HARD, stream);
+        k_hard<V, W><<<grid, W * 32, smem, stream>>>(*tm, a);
+    }
     RS_CUDA(cudaGetLastError());
+    count_launch(ctx);
     return RS_OK;
 }
 

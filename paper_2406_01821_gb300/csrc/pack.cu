@@ -172,11 +172,13 @@ __global__ void k_order(const SetInfo *sets, int P, int32_t *order)
     }
 }
 
-void launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream)
+int launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream)
 {
-    if (b.P > 0) k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.status);
-    if (b.R > 0) k_pack_rules<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status);
-    if (b.P > 0 && o.order) k_order<<<1, 1024, 0, stream>>>(o.sets, b.P, o.order);
+    int n = 0;
+    if (b.P > 0) { k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.status); ++n; }
+    if (b.R > 0) { k_pack_rules<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status); ++n; }
+    if (b.P > 0 && o.order) { k_order<<<1, 1024, 0, stream>>>(o.sets, b.P, o.order); ++n; }
+    return n;
 }
 
 // --------------------------------------------------------------- exhaustive rewrite self-check

@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cstdint>
 #include <cstdio>
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -110,6 +111,18 @@ bool tile_config_fits(const TileConfig &tc, int F);
 
 struct GraphEntry;
 
+// Kernel launch counting and optional CUDA-event timing of the evaluator kernels.
+enum TimedKind { TK_HARD = 0, TK_SOFT = 1 };
+struct Profiler {
+    std::atomic<int64_t> launches{0};
+    std::mutex mu;
+    struct Pending { cudaEvent_t e0, e1; int kind; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    int64_t n[2] = {0, 0};
+    double ms[2] = {0, 0};
+};
+
 struct Ctx {
     int device = 0;
     uint32_t flags = 0;
@@ -124,10 +137,23 @@ struct Ctx {
     std::map<std::string, int> tune_table;   // key -> tile config id
     std::map<std::string, std::shared_ptr<GraphEntry>> graphs;
     uint32_t *d_sticky = nullptr;            // async-mode sticky device status
+    Profiler prof;
     struct Server *server = nullptr;
 };
 
 std::shared_ptr<Dataset> find_dataset(Ctx *ctx, uint64_t ds);
+
+// Count `n` kernel launches of the library.
+inline void count_launch(Ctx *ctx, int n = 1) { ctx->prof.launches += n; }
+// Begin / end a timed region around one kernel launch on `stream` (no-ops unless RS_CTX_PROFILE).
+struct TimedLaunch {
+    Ctx *ctx;
+    int kind;
+    cudaStream_t stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TimedLaunch(Ctx *c, int k, cudaStream_t s);
+    ~TimedLaunch();
+};
 rs_status device_guard(Ctx *ctx);
 
 // Pinned per-thread status slot used by synchronous calls to read back the device status word.
@@ -143,7 +169,8 @@ struct PackOut {
 };
 
 // Validate + pack (+ order) a device batch. Enqueued on `stream`.
-void launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream);
+// Returns the number of kernels launched.
+int launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream);
 
 struct HardArgs {
     const Rec *recs;

@@ -83,6 +83,61 @@ std::shared_ptr<Dataset> find_dataset(Ctx *ctx, uint64_t ds)
     return it->second;
 }
 
+// ------------------------------------------------------------------------------ profiling
+
+static cudaEvent_t take_event(Profiler &p)
+{
+    if (!p.pool.empty()) { cudaEvent_t e = p.pool.back(); p.pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+TimedLaunch::TimedLaunch(Ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), stream(s)
+{
+    if (!(ctx->flags & RS_CTX_PROFILE)) return;
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    e0 = take_event(ctx->prof);
+    e1 = take_event(ctx->prof);
+    if (e0) cudaEventRecord(e0, stream);
+}
+
+TimedLaunch::~TimedLaunch()
+{
+    if (!e0 || !e1) return;
+    cudaEventRecord(e1, stream);
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    ctx->prof.pending.push_back({e0, e1, kind});
+}
+
+rs_status profile_read(Ctx *ctx, rs_profile *out, int reset)
+{
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    for (auto &p : ctx->prof.pending) {
+        RS_CUDA(cudaEventSynchronize(p.e1));
+        float ms = 0.f;
+        RS_CUDA(cudaEventElapsedTime(&ms, p.e0, p.e1));
+        ctx->prof.n[p.kind] += 1;
+        ctx->prof.ms[p.kind] += ms;
+        ctx->prof.pool.push_back(p.e0);
+        ctx->prof.pool.push_back(p.e1);
+    }
+    ctx->prof.pending.clear();
+    if (out) {
+        out->launches = ctx->prof.launches.load();
+        out->hard_launches = ctx->prof.n[TK_HARD];
+        out->hard_ms = ctx->prof.ms[TK_HARD];
+        out->soft_launches = ctx->prof.n[TK_SOFT];
+        out->soft_ms = ctx->prof.ms[TK_SOFT];
+    }
+    if (reset) {
+        ctx->prof.launches = 0;
+        ctx->prof.n[0] = ctx->prof.n[1] = 0;
+        ctx->prof.ms[0] = ctx->prof.ms[1] = 0;
+    }
+    return RS_OK;
+}
+
 // ------------------------------------------------------------------------------ registration
 
 namespace {

@@ -328,6 +328,7 @@ rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
     RS_CUDA(cudaMemsetAsync(next, 0, sizeof(int32_t) * 4, stream));
     k_check_sets_soft<<<(P + 255) / 256, 256, 0, stream>>>(b, s.K, s.status, next + 1);
     if (C > 0) k_pack_soft<<<(unsigned)((C + 255) / 256), 256, 0, stream>>>(b, s.F, s.K, recs, s.status);
+    count_launch(ctx, 1 + (C > 0 ? 1 : 0));
     // The main kernel reads only validated structure: skip it when validation failed.
     SoftKArgs k{};
     k.recs = recs;
@@ -374,8 +375,12 @@ rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
         if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true>, SOFT_W * 32, smem);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false>, SOFT_W * 32, smem);
         const int grid = ctx->sm_count * std::max(1, per_sm);
-        if (bwd) k_soft<true><<<grid, SOFT_W * 32, smem, stream>>>(k);
-        else k_soft<false><<<grid, SOFT_W * 32, smem, stream>>>(k);
+        {
+            TimedLaunch tl(ctx, TK_SOFT, stream);
+            if (bwd) k_soft<true><<<grid, SOFT_W * 32, smem, stream>>>(k);
+            else k_soft<false><<<grid, SOFT_W * 32, smem, stream>>>(k);
+        }
+        count_launch(ctx, 2 + ((bwd && C > 0) ? 1 : 0));
         k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
                                                                1.0f / (float)s.N, s.loss);
         if (bwd && C > 0)

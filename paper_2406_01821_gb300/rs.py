@@ -18,7 +18,7 @@ OK, PENDING = 0, 1
 ERR = {-1: "RS_ERR_INVALID", -2: "RS_ERR_TOO_LARGE", -3: "RS_ERR_OOM", -4: "RS_ERR_TIMEOUT",
        -5: "RS_ERR_DEVICE", -6: "RS_ERR_UNSUPPORTED", -7: "RS_ERR_NOT_FOUND", -8: "RS_ERR_CANCELLED"}
 MEM_HOST, MEM_DEVICE = 0, 1
-CTX_ASYNC, CTX_NO_GRAPH, CTX_NO_AUTOTUNE = 1, 2, 4
+CTX_ASYNC, CTX_NO_GRAPH, CTX_NO_AUTOTUNE, CTX_PROFILE = 1, 2, 4, 8
 
 
 class RsError(RuntimeError):
@@ -40,6 +40,12 @@ class rs_batch(ctypes.Structure):
                 ("cond_f", ctypes.c_void_p), ("cond_g", ctypes.c_void_p),
                 ("cond_op", ctypes.c_void_p), ("cond_a", ctypes.c_void_p),
                 ("cond_b", ctypes.c_void_p), ("cond_t", ctypes.c_void_p)]
+
+
+class rs_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("hard_launches", ctypes.c_int64),
+                ("hard_ms", ctypes.c_double), ("soft_launches", ctypes.c_int64),
+                ("soft_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -68,6 +74,7 @@ _SIGS = {
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
+    "rs_profile_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rs_profile), ctypes.c_int32]),
     "rs_tile_config_count": (ctypes.c_int32, []),
     "rs_tile_config_info": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -291,6 +298,11 @@ class Context:
         cb = batch.c()
         check(lib().rs_autotune(self.h, ds, ctypes.byref(cb), _stream_ptr(stream), ctypes.byref(best)))
         return best.value
+
+    def profile(self, reset=False) -> dict:
+        p = rs_profile()
+        check(lib().rs_profile_read(self.h, ctypes.byref(p), int(reset)))
+        return {f: getattr(p, f) for f, _ in rs_profile._fields_}
 
     def check_async(self, stream=None):
         check(lib().rs_check(self.h, _stream_ptr(stream)))
