@@ -162,7 +162,9 @@ def hard_leg(args, rank, dev, ctx_mod, w):
     ctx = rs.Context(dev, flags=rs.CTX_PROFILE)
     ds = ctx.dataset(w.X, w.y, w.K)
     db = rs.DeviceBatch.from_host(w.batch, device=f"cuda:{dev}")
-    tile = ctx.autotune(ds, db, stream=stream)
+    tile = 0 if args.no_autotune else ctx.autotune(ds, db, stream=stream)
+    if args.no_autotune:
+        ctx.set_tile_config(tile)
     P, K, N = w.batch.P, w.K, w.N
     out = (torch.empty(P, dtype=torch.int32, device=dev),
            torch.empty((P, K), dtype=torch.int32, device=dev), None)
@@ -332,6 +334,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=131072)
+    ap.add_argument("--workload", default="ragged", choices=["ragged", "ragged-small"],
+                    help="ragged-small (N=2^19, P=512) is the case used for ncu captures")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     d = Dist()
@@ -347,7 +352,10 @@ def main():
     d.barrier()
     dev = d.local
     torch.cuda.set_device(dev)
-    w = synth.ragged_hard(seed=d.rank)         # each rank: its own population of 4096 sets
+    if args.workload == "ragged-small":
+        w = synth.ragged_hard(seed=d.rank, N=1 << 19, P=512)
+    else:
+        w = synth.ragged_hard(seed=d.rank)     # each rank: its own population of 4096 sets
     res = hard_leg(args, d.rank, dev, d, w)
     ms_max = d.max(res["ms"])
     e2e_max = d.max(res["e2e_ms"])
