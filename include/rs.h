@@ -181,6 +181,28 @@ rs_status rs_eval_soft_bwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, floa
                            const float *dloss, float *grad_a, float *grad_b, float *grad_t,
                            float *loss, void *stream);
 
+/*
+ * rs_eval_hard without any device allocation. The paper has no counterpart: this entry point
+ * exists for callers that must not call cudaMalloc or any allocating routine while they evaluate
+ * -- a host whose device memory is owned by another allocator or is fully reserved in advance, or
+ * a real-time loop that may not block in an allocator. It computes exactly what rs_eval_hard
+ * computes, with the per-call scratch taken from one fixed array of RS_STATIC_SCRATCH_BYTES that
+ * lives in the library's device image (every GPU that loads the library holds it until exit).
+ *   batch   device arrays only (batch->mem must be RS_MEM_DEVICE); outputs are device memory
+ *   limit   16*C + 20*P + 768 bytes (each part rounded up to 256 B) must fit in the array,
+ *           otherwise RS_ERR_TOO_LARGE with a message; nothing is launched then
+ *   set-up  the first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *           with that device current, and the first call for a dataset builds its tile
+ *           descriptor; make that first call before any stream capture
+ *   sharing every call uses the same array: calls whose GPU work overlaps (different streams,
+ *           host threads or contexts on one device) race on it and must be serialised by the
+ *           caller. Each call clears the status word it needs; the rest is rewritten before use.
+ * The dataset itself is registered beforehand with rs_dataset_create.
+ */
+#define RS_STATIC_SCRATCH_BYTES (8u << 20)
+rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,
+                              int32_t *per_class, int32_t *preds, void *stream);
+
 /* ---------------------------------------------------------------------------- tile tuning */
 
 /* Number of compiled tile configurations of the hard evaluator. */

@@ -21,6 +21,8 @@ rs_status selftest_rewrite(const float *a_h, const float *t_h, const int8_t *op_
 void load_tune_table(Ctx *ctx);
 void server_shutdown(Ctx *ctx);
 rs_status profile_read(Ctx *ctx, rs_profile *out, int reset);
+rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
+                           int32_t *per_class, int32_t *preds, cudaStream_t stream);
 }  // namespace rs
 
 using namespace rs;
@@ -162,6 +164,15 @@ rs_status rs_eval_hard(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t 
     RS_GUARD({
         if (!ctx) return RS_ERR_INVALID;
         return eval_hard(ctx, ds, batch, correct, per_class, preds, S(stream), -1);
+    })
+}
+
+rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,
+                              int32_t *per_class, int32_t *preds, void *stream)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return eval_hard_static(ctx, ds, batch, correct, per_class, preds, S(stream));
     })
 }
 

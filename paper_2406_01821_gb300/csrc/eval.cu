@@ -96,6 +96,8 @@ static int heuristic_tile(const Dataset &ds)
     return 5;
 }
 
+int heuristic_tile_for(const Dataset &ds) { return heuristic_tile(ds); }
+
 static int pick_tile(Ctx *ctx, const Dataset &ds, const rs_batch *b)
 {
     if (ctx->forced_tile >= 0 && tile_config_fits(tile_config(ctx->forced_tile), ds.F))
@@ -147,14 +149,6 @@ static void save_tune_table(Ctx *ctx)
 
 // ------------------------------------------------------------------------ the call
 
-struct Scratch {
-    Rec *recs = nullptr;
-    SetInfo *sets = nullptr;
-    int32_t *order = nullptr;
-    uint32_t *status = nullptr;
-    int32_t *out_dev = nullptr;   // device outputs when the caller's are host memory
-};
-
 static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t N, bool per_class,
                                bool preds, cudaStream_t stream, Scratch &s)
 {
@@ -180,7 +174,7 @@ static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t 
 }
 
 // Enqueue pack + evaluation (the part a graph captures).
-static rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
+rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
                               const Scratch &s, int32_t *correct, int32_t *per_class,
                               int32_t *preds, cudaStream_t stream)
 {

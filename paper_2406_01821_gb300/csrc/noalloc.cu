@@ -1,0 +1,127 @@
+// Hard evaluation for callers that cannot allocate device memory.
+//
+// rs_eval_hard_static runs the same packing and evaluator kernels as rs_eval_hard, but every
+// piece of per-call scratch (condition records, per-set table, schedule order, status word) lives
+// in one file-scope device array of fixed size instead of stream-ordered allocations. The array is
+// part of the loaded module: every GPU that loads this library holds it until the process exits.
+//
+// Host code must not use the array's name as a device address (in host code it names a host-side
+// stand-in). The device address is looked up once per device with cudaGetSymbolAddress, with that
+// device current, on the first call made on that device.
+#include <mutex>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[RS_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char *g_scratch_addr[kMaxDevices] = {};
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+rs_status static_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("device ordinal %d out of range for the static scratch table", device);
+        return RS_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_scratch_addr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_scratch_addr[device];
+    return RS_OK;
+}
+
+__global__ void k_fold_status(const uint32_t *src, uint32_t *dst)
+{
+    if (*src) atomicOr(dst, *src);
+}
+
+}  // namespace
+
+size_t static_scratch_need(int64_t P, int64_t C)
+{
+    return up256(sizeof(Rec) * (size_t)std::max<int64_t>(C, 1)) +
+           up256(sizeof(SetInfo) * (size_t)std::max<int64_t>(P, 1)) +
+           up256(sizeof(int32_t) * (size_t)std::max<int64_t>(P, 1)) + 256;
+}
+
+rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
+                           int32_t *per_class, int32_t *preds, cudaStream_t stream)
+{
+    if (!b) { set_error("batch is NULL"); return RS_ERR_INVALID; }
+    if (b->mem != RS_MEM_DEVICE) {
+        set_error("rs_eval_hard_static takes device arrays only (batch->mem = RS_MEM_DEVICE)");
+        return RS_ERR_INVALID;
+    }
+    if (b->P < 0 || b->R < 0 || b->C < 0) { set_error("negative batch sizes"); return RS_ERR_INVALID; }
+    if (!b->set_rule_off || !b->rule_cond_off || (b->P > 0 && (!b->set_default || !correct)) ||
+        (b->R > 0 && !b->rule_class) ||
+        (b->C > 0 && (!b->cond_f || !b->cond_g || !b->cond_op || !b->cond_a || !b->cond_b || !b->cond_t))) {
+        set_error("NULL batch or output array");
+        return RS_ERR_INVALID;
+    }
+    const size_t need = static_scratch_need(b->P, b->C);
+    if (need > RS_STATIC_SCRATCH_BYTES) {
+        set_error("batch needs %zu bytes of scratch (P=%d, C=%d); rs_eval_hard_static holds %zu "
+                  "(16 B per condition + 20 B per set + 768 B); use rs_eval_hard",
+                  need, b->P, b->C, (size_t)RS_STATIC_SCRATCH_BYTES);
+        return RS_ERR_TOO_LARGE;
+    }
+    auto ds = find_dataset(ctx, ds_h);
+    if (!ds) { set_error("unknown dataset %llu", (unsigned long long)ds_h); return RS_ERR_NOT_FOUND; }
+    rs_status rc = device_guard(ctx);
+    if (rc) return rc;
+    unsigned char *base = nullptr;
+    if ((rc = static_scratch(ctx->device, &base))) return rc;
+
+    Scratch s;
+    s.recs = reinterpret_cast<Rec *>(base);
+    s.sets = reinterpret_cast<SetInfo *>(base + up256(sizeof(Rec) * (size_t)std::max(b->C, 1)));
+    s.order = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(s.sets) +
+                                          up256(sizeof(SetInfo) * (size_t)std::max(b->P, 1)));
+    s.status = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(s.order) +
+                                            up256(sizeof(int32_t) * (size_t)std::max(b->P, 1)));
+    // The array keeps the previous call's contents: the status word must start at zero. Records,
+    // the set table and the order are fully rewritten by the packer before they are read.
+    RS_CUDA(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream));
+
+    BatchDev bd{};
+    bd.P = b->P; bd.R = b->R; bd.C = b->C;
+    bd.set_rule_off = b->set_rule_off; bd.rule_cond_off = b->rule_cond_off;
+    bd.rule_class = b->rule_class; bd.set_default = b->set_default;
+    bd.cond_f = b->cond_f; bd.cond_g = b->cond_g; bd.cond_op = b->cond_op;
+    bd.cond_a = b->cond_a; bd.cond_b = b->cond_b; bd.cond_t = b->cond_t;
+
+    const int tid = ctx->forced_tile >= 0 && tile_config_fits(tile_config(ctx->forced_tile), ds->F)
+                        ? ctx->forced_tile
+                        : heuristic_tile_for(*ds);
+    if ((rc = enqueue_hard(ctx, ds.get(), tile_config(tid), bd, s, correct, per_class, preds, stream)))
+        return rc;
+
+    if (ctx->flags & RS_CTX_ASYNC) {
+        k_fold_status<<<1, 1, 0, stream>>>(s.status, ctx->d_sticky);
+        RS_CUDA(cudaGetLastError());
+        count_launch(ctx);
+        return RS_OK;
+    }
+    uint32_t st = 0;
+    RS_CUDA(cudaMemcpyAsync(&st, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    RS_CUDA(cudaStreamSynchronize(stream));
+    if (st) {
+        set_error("batch rejected: %s", status_text(st).c_str());
+        return (st & (ST_WAIT_TIMEOUT | ST_QUEUE_TIMEOUT)) ? RS_ERR_TIMEOUT : RS_ERR_INVALID;
+    }
+    return RS_OK;
+}
+
+}  // namespace rs

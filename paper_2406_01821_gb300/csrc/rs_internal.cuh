@@ -172,6 +172,15 @@ struct PackOut {
 // Returns the number of kernels launched.
 int launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream);
 
+// Per-call scratch of a hard evaluation.
+struct Scratch {
+    Rec *recs = nullptr;
+    SetInfo *sets = nullptr;
+    int32_t *order = nullptr;
+    uint32_t *status = nullptr;
+    int32_t *out_dev = nullptr;   // device outputs when the caller's are host memory
+};
+
 struct HardArgs {
     const Rec *recs;
     const SetInfo *sets;
@@ -191,6 +200,12 @@ struct HardArgs {
 rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,
                       cudaStream_t stream);
 int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P);
+// Enqueue packing + evaluation of a device batch with the given scratch.
+rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
+                       const Scratch &s, int32_t *correct, int32_t *per_class, int32_t *preds,
+                       cudaStream_t stream);
+// The built-in tile choice for a dataset (no autotuned entry).
+int heuristic_tile_for(const Dataset &ds);
 const CUtensorMap *dataset_tmap(Dataset *ds, int S);
 
 struct SoftArgs {
