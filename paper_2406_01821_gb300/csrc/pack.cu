@@ -69,6 +69,58 @@ __device__ inline bool rec_eval_scalar(uint32_t kind, float v0, float v1, float 
     }
 }
 
+// The v2 form of a threshold condition: fl(v0 * x) > v1 with the same truth value for every x.
+// A '<' cut c becomes -x > -c and a '<' product becomes fl(-a * x) > -t (negation is exact).
+__device__ void rewrite_lin(float a, float t, int op, float &v0, float &v1)
+{
+    uint32_t kind;
+    float c0, c1;
+    rewrite_threshold(a, t, op, kind, c0, c1);
+    switch (kind) {
+    case KIND_GT: v0 = 1.f; v1 = c0; break;
+    case KIND_LT: v0 = -1.f; v1 = -c0; break;
+    case KIND_MGT: v0 = c0; v1 = c1; break;
+    case KIND_MLT: v0 = -c0; v1 = -c1; break;
+    default: v0 = 0.f; v1 = __uint_as_float(0x7F800000u); break;   // never true
+    }
+}
+
+// Pack v2 records: one thread per rule.
+__global__ void k_pack_rules2(BatchDev b, int F, int K, int S, Rec *recs_out, uint32_t *status)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= b.R) return;
+    const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
+    if (c0 < 0 || c1 < c0 || c1 > b.C) { atomicOr(status, ST_BAD_OFFSETS); return; }
+    if (c1 - c0 > 0xFFF) { atomicOr(status, ST_TOO_LARGE); return; }
+    int cls = b.rule_class[r];
+    if (cls < 0 || cls >= K) { atomicOr(status, ST_BAD_CLASS); cls = 0; }
+    uint4 *out = reinterpret_cast<uint4 *>(recs_out);
+    const uint32_t len = (uint32_t)(c1 - c0);
+    const uint32_t row16 = (uint32_t)S / 4;   // 16-byte units per feature row
+    for (int c = c0; c < c1; ++c) {
+        const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
+        uint32_t w0 = len << LEN_SHIFT, w1 = (uint32_t)cls << CLS_SHIFT;
+        float v0 = 0.f, v1 = __uint_as_float(0x7F800000u);   // never true
+        if (f < 0 || f >= F || g < -1 || g >= F) {
+            atomicOr(status, ST_BAD_FEATURE);
+        } else if (op != 0 && op != 1) {
+            atomicOr(status, ST_BAD_OP);
+        } else if (g < 0) {
+            rewrite_lin(b.cond_a[c], b.cond_t[c], op, v0, v1);
+            w0 |= (uint32_t)f * row16;
+        } else {
+            const int lf = op == 0 ? f : g, rg = op == 0 ? g : f;
+            v0 = op == 0 ? b.cond_a[c] : b.cond_b[c];
+            v1 = op == 0 ? b.cond_b[c] : b.cond_a[c];
+            w0 |= ((uint32_t)lf * row16) | PAIR_BIT;
+            w1 |= (uint32_t)rg * row16;
+        }
+        out[c] = make_uint4(w0, w1, __float_as_uint(v0), __float_as_uint(v1));
+    }
+}
+
+
 // One thread per set: offsets, default class, first empty rule (an empty rule fires for every
 // sample still unclaimed, so the set effectively ends there with that class as its default).
 __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
@@ -172,11 +224,17 @@ __global__ void k_order(const SetInfo *sets, int P, int32_t *order)
     }
 }
 
-int launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream)
+int launch_pack(const BatchDev &b, int F, int K, int S, int ver, const PackOut &o, cudaStream_t stream)
 {
     int n = 0;
     if (b.P > 0) { k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.status); ++n; }
-    if (b.R > 0) { k_pack_rules<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status); ++n; }
+    if (b.R > 0 && ver == 2) {
+        k_pack_rules2<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, S, o.recs, o.status);
+        ++n;
+    } else if (b.R > 0) {
+        k_pack_rules<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status);
+        ++n;
+    }
     if (b.P > 0 && o.order) { k_order<<<1, 1024, 0, stream>>>(o.sets, b.P, o.order); ++n; }
     return n;
 }

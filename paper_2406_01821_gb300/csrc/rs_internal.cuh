@@ -55,6 +55,14 @@ enum : uint32_t {
     KIND_NEVER = 5,  // never true
 };
 
+// Record format v2 (rule-at-a-time evaluator): w0 = [0,18) feature row offset in 16-byte units |
+// [18] pair | [19,31) rule length; w1 = [0,18) second feature row offset | [18,30) rule class;
+// then v0, v1 with the test fl(v0*x[f]) > v1 (LIN) or fl(v0*x[f]) > fl(v1*x[g]) (pair).
+constexpr uint32_t OFF_MASK = 0x3FFFFu;
+constexpr uint32_t PAIR_BIT = 1u << 18;
+constexpr int LEN_SHIFT = 19;
+constexpr int CLS_SHIFT = 18;
+
 struct __align__(16) Rec {
     uint32_t meta;   // [0,3) kind | [3] last condition of its rule | [4,16) rule class | [16,32) skip
     uint16_t f, g;
@@ -100,6 +108,7 @@ struct TileConfig {
     int id;
     int V;       // samples per lane
     int W;       // warps per CTA
+    int ver;     // 1: condition-at-a-time evaluator, 2: rule-at-a-time evaluator (record v2)
     int S() const { return 32 * V; }
 };
 int tile_config_count();
@@ -170,7 +179,7 @@ struct PackOut {
 
 // Validate + pack (+ order) a device batch. Enqueued on `stream`.
 // Returns the number of kernels launched.
-int launch_pack(const BatchDev &b, int F, int K, const PackOut &o, cudaStream_t stream);
+int launch_pack(const BatchDev &b, int F, int K, int S, int ver, const PackOut &o, cudaStream_t stream);
 
 // Per-call scratch of a hard evaluation.
 struct Scratch {
@@ -200,6 +209,7 @@ struct HardArgs {
 rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,
                       cudaStream_t stream);
 int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P);
+rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream);
 // Enqueue packing + evaluation of a device batch with the given scratch.
 rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
                        const Scratch &s, int32_t *correct, int32_t *per_class, int32_t *preds,
