@@ -162,8 +162,11 @@ def hard_leg(args, rank, dev, ctx_mod, w):
     ctx = rs.Context(dev, flags=rs.CTX_PROFILE)
     ds = ctx.dataset(w.X, w.y, w.K)
     db = rs.DeviceBatch.from_host(w.batch, device=f"cuda:{dev}")
-    tile = 0 if args.no_autotune else ctx.autotune(ds, db, stream=stream)
-    if args.no_autotune:
+    if args.tile is not None:
+        tile = args.tile
+    else:
+        tile = 0 if args.no_autotune else ctx.autotune(ds, db, stream=stream)
+    if args.no_autotune or args.tile is not None:
         ctx.set_tile_config(tile)
     P, K, N = w.batch.P, w.K, w.N
     out = (torch.empty(P, dtype=torch.int32, device=dev),
@@ -337,6 +340,7 @@ def main():
     ap.add_argument("--workload", default="ragged", choices=["ragged", "ragged-small"],
                     help="ragged-small (N=2^19, P=512) is the case used for ncu captures")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile", type=int, default=None, help="force a tile configuration id")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     d = Dist()

@@ -257,7 +257,8 @@ rs_status launch_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t stream
 const TileConfig kConfigs[] = {
     {0, 4, 8, 1}, {1, 4, 4, 1}, {2, 4, 16, 1}, {3, 2, 8, 1}, {4, 2, 16, 1}, {5, 1, 16, 1},
     {6, 8, 8, 1}, {7, 8, 4, 1},
-    {8, 4, 8, 2}, {9, 4, 16, 2}, {10, 8, 8, 2}, {11, 8, 4, 2}, {12, 2, 16, 2},
+    {8, 4, 8, 2}, {9, 4, 16, 2}, {10, 2, 16, 2},
+    {11, 4, 8, 3}, {12, 4, 16, 3}, {13, 2, 16, 3}, {14, 2, 32, 3}, {15, 4, 32, 3},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
@@ -270,7 +271,7 @@ bool tile_config_fits(const TileConfig &tc, int F)
 {
     const int Fb = F < 256 ? F : 256;
     const int Frows = ((F + Fb - 1) / Fb) * Fb;
-    const size_t stage = (size_t)tc.W * (tc.ver == 2 ? 64 : 32) * sizeof(Rec);
+    const size_t stage = (size_t)tc.W * (tc.ver >= 2 ? 64 : 32) * sizeof(Rec);
     const size_t smem = (size_t)Frows * tc.S() * sizeof(float) + stage + 16;
     return smem <= 227 * 1024 && (tc.ver == 1 || (size_t)F * tc.S() / 4 < (1u << 18));
 }
@@ -282,7 +283,7 @@ rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArg
     if (a.P > 0 && a.per_class)
         RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
-    if (tc.ver == 2) return launch_hard2(ctx, ds, tc.V, tc.W, a, stream);
+    if (tc.ver >= 2) return launch_hard2(ctx, ds, tc.V, tc.W, tc.ver == 3, a, stream);
     switch (tc.id) {
     case 0: return launch_t<4, 8>(ctx, ds, a, stream);
     case 1: return launch_t<4, 4>(ctx, ds, a, stream);

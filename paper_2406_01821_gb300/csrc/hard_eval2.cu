@@ -32,6 +32,35 @@ __device__ __forceinline__ void load_v2(const float *p, float (&x)[V])
     }
 }
 
+__device__ __forceinline__ float min_nan(float a, float b)
+{
+    float r;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// Margin form: the condition holds iff m = fl(fl(v0*x) - rhs) > 0 (exact for every input: the
+// difference of two floats is positive iff the first is larger under gradual underflow, and
+// inf - inf and NaN operands give NaN, which is not > 0). A rule fires iff the NaN-propagating
+// minimum of its margins is > 0.
+template <int V>
+__device__ __forceinline__ void eval_rec_m(const uint4 r, const float *xl, float (&mn)[V])
+{
+    float x[V];
+    load_v2<V>(xl + (r.x & OFF_MASK) * 4, x);
+    const float v0 = __uint_as_float(r.z), v1 = __uint_as_float(r.w);
+    if (r.x & PAIR_BIT) {
+        float z[V];
+        load_v2<V>(xl + (r.y & OFF_MASK) * 4, z);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            mn[v] = min_nan(mn[v], __fsub_rn(__fmul_rn(v0, x[v]), __fmul_rn(v1, z[v])));
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) mn[v] = min_nan(mn[v], __fsub_rn(__fmul_rn(v0, x[v]), v1));
+    }
+}
+
 template <int V>
 __device__ __forceinline__ void eval_rec(const uint4 r, const float *xl, bool (&al)[V])
 {
@@ -49,7 +78,7 @@ __device__ __forceinline__ void eval_rec(const uint4 r, const float *xl, bool (&
     }
 }
 
-template <int V, int W>
+template <int V, int W, bool MM>
 __global__ void __launch_bounds__(W * 32) k_hard2(const __grid_constant__ CUtensorMap tmap, HardArgs a)
 {
     constexpr int S = 32 * V;
@@ -144,16 +173,32 @@ __global__ void __launch_bounds__(W * 32) k_hard2(const __grid_constant__ CUtens
             const int nc = (int)((r0.x >> LEN_SHIFT) & 0xFFFu);
             const int cls = (int)(r0.y >> CLS_SHIFT);
             bool al[V];
+            if constexpr (MM) {
+                float mn[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) al[v] = unc[v];
-            if (nc <= 33) {
-                eval_rec<V>(r0, xl, al);
+                for (int v = 0; v < V; ++v) mn[v] = unc[v] ? __uint_as_float(0x7F800000u) : -1.f;
+                if (nc <= 33) {
+                    eval_rec_m<V>(r0, xl, mn);
 #pragma unroll 2
-                for (int k = 1; k < nc; ++k) eval_rec<V>(rp[k], xl, al);
+                    for (int k = 1; k < nc; ++k) eval_rec_m<V>(rp[k], xl, mn);
+                } else {
+                    eval_rec_m<V>(r0, xl, mn);
+                    for (int k = 1; k < nc; ++k) eval_rec_m<V>(__ldg(recs + rb + rel + k), xl, mn);
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = mn[v] > 0.f;
             } else {
-                // long rule: read its records straight from global memory
-                eval_rec<V>(r0, xl, al);
-                for (int k = 1; k < nc; ++k) eval_rec<V>(__ldg(recs + rb + rel + k), xl, al);
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = unc[v];
+                if (nc <= 33) {
+                    eval_rec<V>(r0, xl, al);
+#pragma unroll 2
+                    for (int k = 1; k < nc; ++k) eval_rec<V>(rp[k], xl, al);
+                } else {
+                    // long rule: read its records straight from global memory
+                    eval_rec<V>(r0, xl, al);
+                    for (int k = 1; k < nc; ++k) eval_rec<V>(__ldg(recs + rb + rel + k), xl, al);
+                }
             }
             bool any_unc = false;
 #pragma unroll
@@ -204,7 +249,7 @@ static size_t smem_bytes2(int F)
     return (size_t)Frows * 32 * V * sizeof(float) + (size_t)W * 64 * 16 + 16;
 }
 
-template <int V, int W>
+template <int V, int W, bool MM>
 rs_status launch2_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t stream)
 {
     const size_t smem = smem_bytes2<V, W>(a.F);
@@ -212,7 +257,7 @@ rs_status launch2_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t strea
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(k_hard2<V, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(k_hard2<V, W, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)ctx->smem_optin);
     });
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute(k_hard2)");
@@ -222,24 +267,31 @@ rs_status launch2_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t strea
     dim3 grid(tiles, a.groups);
     {
         TimedLaunch tl(ctx, TK_HARD, stream);
-        k_hard2<V, W><<<grid, W * 32, smem, stream>>>(*tm, a);
+        k_hard2<V, W, MM><<<grid, W * 32, smem, stream>>>(*tm, a);
     }
     RS_CUDA(cudaGetLastError());
     count_launch(ctx);
     return RS_OK;
 }
 
-rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream)
+rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, bool mm, const HardArgs &a,
+                       cudaStream_t stream)
 {
     if (a.P > 0) RS_CUDA(cudaMemsetAsync(a.correct, 0, sizeof(int32_t) * a.P, stream));
     if (a.P > 0 && a.per_class)
         RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
-    if (V == 4 && W == 8) return launch2_t<4, 8>(ctx, ds, a, stream);
-    if (V == 4 && W == 16) return launch2_t<4, 16>(ctx, ds, a, stream);
-    if (V == 8 && W == 8) return launch2_t<8, 8>(ctx, ds, a, stream);
-    if (V == 8 && W == 4) return launch2_t<8, 4>(ctx, ds, a, stream);
-    if (V == 2 && W == 16) return launch2_t<2, 16>(ctx, ds, a, stream);
+    if (!mm) {
+        if (V == 4 && W == 8) return launch2_t<4, 8, false>(ctx, ds, a, stream);
+        if (V == 4 && W == 16) return launch2_t<4, 16, false>(ctx, ds, a, stream);
+        if (V == 2 && W == 16) return launch2_t<2, 16, false>(ctx, ds, a, stream);
+    } else {
+        if (V == 4 && W == 8) return launch2_t<4, 8, true>(ctx, ds, a, stream);
+        if (V == 4 && W == 16) return launch2_t<4, 16, true>(ctx, ds, a, stream);
+        if (V == 2 && W == 16) return launch2_t<2, 16, true>(ctx, ds, a, stream);
+        if (V == 2 && W == 32) return launch2_t<2, 32, true>(ctx, ds, a, stream);
+        if (V == 4 && W == 32) return launch2_t<4, 32, true>(ctx, ds, a, stream);
+    }
     return RS_ERR_INVALID;
 }
 

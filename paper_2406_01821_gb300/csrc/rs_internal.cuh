@@ -108,7 +108,8 @@ struct TileConfig {
     int id;
     int V;       // samples per lane
     int W;       // warps per CTA
-    int ver;     // 1: condition-at-a-time evaluator, 2: rule-at-a-time evaluator (record v2)
+    int ver;     // 1: condition-at-a-time evaluator, 2: rule-at-a-time (record v2),
+                 // 3: rule-at-a-time with the margin-minimum conjunction
     int S() const { return 32 * V; }
 };
 int tile_config_count();
@@ -209,7 +210,8 @@ struct HardArgs {
 rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,
                       cudaStream_t stream);
 int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P);
-rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream);
+rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, bool mm, const HardArgs &a,
+                       cudaStream_t stream);
 // Enqueue packing + evaluation of a device batch with the given scratch.
 rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
                        const Scratch &s, int32_t *correct, int32_t *per_class, int32_t *preds,
