@@ -203,6 +203,64 @@ rs_status rs_eval_soft_bwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, floa
 rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,
                               int32_t *per_class, int32_t *preds, void *stream);
 
+/* ------------------------------------------------------------------------------ evolution */
+
+/*
+ * A population in fixed slots (host arrays): set p has nrule[p] rules; rule r of set p sits at
+ * [p*RMAX + r] and has ncond[...] conditions; condition k of that rule at [(p*RMAX + r)*CMAX + k]
+ * (cond_g = -1 marks a threshold). Slots past nrule / ncond are carried along and never read.
+ */
+typedef struct {
+    int32_t *nrule;    /* [P] 1..RMAX */
+    int32_t *deflt;    /* [P] default class */
+    int32_t *rcls;     /* [P*RMAX] */
+    int32_t *ncond;    /* [P*RMAX] 1..CMAX */
+    int32_t *cf, *cg;  /* [P*RMAX*CMAX] */
+    int8_t *cop;
+    float *ca, *cb, *ct;
+    int32_t *fitness;  /* [P] out: correct counts of the returned population; may be NULL */
+} rs_population;
+
+typedef struct {
+    int32_t P, RMAX, CMAX;    /* population shape; RMAX <= 32, CMAX <= 64 */
+    int32_t generations;
+    int32_t elite;            /* best individuals copied unchanged each generation */
+    int32_t tune_every;       /* fine-tune every this many generations (0 = never) */
+    int32_t tune_top;         /* the best tune_top sets are fine-tuned */
+    int32_t tune_steps;       /* full-batch Adam steps per fine-tuning (lr, 0.9, 0.999, 1e-8) */
+    float tau, lr;            /* sigmoid temperature, Adam learning rate */
+    int32_t lamarckian;       /* 0: the tuned fitness ranks the individual, its genome is kept
+                                 (Baldwin effect, Sec. 3); 1: tuned coefficients are written back */
+    uint64_t seed;
+} rs_evolve_config;
+
+/*
+ * Run `generations` generations of evolution on the device (Sec. 3: tournament selection,
+ * offspring with randomized coefficients, back-propagation fine-tuning guiding evolution through
+ * the Baldwin effect). Each generation: evaluate every set exactly (rs_eval_hard semantics), rank
+ * by (correct desc, index asc), copy the `elite` best, fill the rest with children of two binary
+ * tournaments (uniform rule-list crossover with probability 1/2, one mutation with probability
+ * 9/10: new random coefficients, new feature, flipped comparison, add/delete a condition,
+ * add/delete a rule, new class). Random numbers: Philox4x64-10, counter (i/4, child, generation,
+ * 0), key (seed, 0x65766f6c).
+ * `pop` holds the initial population on entry and the final one (after `generations` steps) on
+ * return. best / mean (host, may be NULL): best and mean correct count of each evaluated
+ * generation, generations + 1 entries.
+ */
+rs_status rs_evolve(rs_ctx *ctx, uint64_t ds, const rs_evolve_config *cfg, rs_population *pop,
+                    int32_t *best, double *mean, void *stream);
+
+/*
+ * Full-batch fine-tuning of one population's coefficients and thresholds (Sec. 3 back-propagation;
+ * Fig. 1c): `steps` Adam steps (lr, beta 0.9 / 0.999, eps 1e-8) on the summed soft loss of all sets,
+ * gradients from rs_eval_soft_bwd. The structure comes from `batch` (device arrays; its cond_a,
+ * cond_b, cond_t are not read); the parameters a, b, t (device float32[C]) are updated in place
+ * (b only for pairs, t only for thresholds). loss_trace (host float32[steps*P], may be NULL)
+ * receives the per-set loss before each step.
+ */
+rs_status rs_finetune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float *a, float *b, float *t,
+                      float tau, float lr, int32_t steps, float *loss_trace, void *stream);
+
 /* ---------------------------------------------------------------------------- tile tuning */
 
 /* Number of compiled tile configurations of the hard evaluator. */

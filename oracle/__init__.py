@@ -66,6 +66,7 @@ def _load(path):
     h.orc_eval_hard.restype = ctypes.c_int
     h.orc_soft.restype = ctypes.c_int
     h.orc_num_threads.restype = ctypes.c_int
+    h.orc_evolve_step.restype = ctypes.c_int
     return h
 
 
@@ -159,3 +160,48 @@ def planted(plant: int):
     h = _load(build(plant=plant))
     return types.SimpleNamespace(eval_hard=functools.partial(eval_hard, _h=h),
                                  soft=functools.partial(soft, _h=h), build=build)
+
+
+# ------------------------------------------------------------------------------ evolution
+
+class _Pop(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int32), ("RMAX", ctypes.c_int32), ("CMAX", ctypes.c_int32)] + \
+               [(n, ctypes.c_void_p) for n in ("nrule", "deflt", "rcls", "ncond", "cf", "cg", "cop",
+                                               "ca", "cb", "ct")]
+
+
+POP_FIELDS = {"nrule": np.int32, "deflt": np.int32, "rcls": np.int32, "ncond": np.int32,
+              "cf": np.int32, "cg": np.int32, "cop": np.int8, "ca": np.float32, "cb": np.float32,
+              "ct": np.float32}
+
+
+def _cpop(pop):
+    arrs = {k: np.ascontiguousarray(pop[k], t) for k, t in POP_FIELDS.items()}
+    P, RMAX, CMAX = arrs["cf"].shape
+    return _Pop(P, RMAX, CMAX, *[_ptr(arrs[k]) for k in POP_FIELDS]), arrs
+
+
+def philox4x64_10(ctr, key):
+    """Philox4x64-10 block for counter[4], key[2] (uint64)."""
+    out = np.zeros(4, np.uint64)
+    c = np.ascontiguousarray(ctr, np.uint64)
+    k = np.ascontiguousarray(key, np.uint64)
+    lib().orc_philox4x64_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def evolve_step(pop, fit, seed, gen, elite, X, K):
+    """One generation (tournament selection, crossover, mutation with randomized coefficients).
+    ``pop`` is a dict of slot arrays (see POP_FIELDS; condition arrays are [P, RMAX, CMAX])."""
+    cin, keep_in = _cpop(pop)
+    out = {k: np.zeros_like(v) for k, v in keep_in.items()}
+    cout, keep_out = _cpop(out)
+    fit = np.ascontiguousarray(fit, np.int32)
+    X = np.ascontiguousarray(X, np.float32)
+    rc = lib().orc_evolve_step(ctypes.byref(cin), _ptr(fit), ctypes.byref(cout), ctypes.c_uint64(seed),
+                               ctypes.c_uint64(gen), ctypes.c_int32(elite), _ptr(X),
+                               ctypes.c_int64(X.shape[0]), ctypes.c_int32(X.shape[1]),
+                               ctypes.c_int32(K))
+    if rc != 0:
+        raise ValueError("population shape not supported by the oracle")
+    return keep_out

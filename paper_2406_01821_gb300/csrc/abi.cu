@@ -21,6 +21,10 @@ rs_status selftest_rewrite(const float *a_h, const float *t_h, const int8_t *op_
 void load_tune_table(Ctx *ctx);
 void server_shutdown(Ctx *ctx);
 rs_status profile_read(Ctx *ctx, rs_profile *out, int reset);
+rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_population *hp,
+                     int32_t *best_out, double *mean_out, cudaStream_t s);
+rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, float *pb, float *pt,
+                       float tau, float lr, int steps, float *loss_trace, cudaStream_t s);
 rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
                            int32_t *per_class, int32_t *preds, cudaStream_t stream);
 }  // namespace rs
@@ -206,6 +210,24 @@ rs_status rs_profile_read(rs_ctx *ctx, rs_profile *out, int32_t reset)
         rs_status rc = device_guard(ctx);
         if (rc) return rc;
         return profile_read(ctx, out, reset);
+    })
+}
+
+rs_status rs_evolve(rs_ctx *ctx, uint64_t ds, const rs_evolve_config *cfg, rs_population *pop,
+                    int32_t *best, double *mean, void *stream)
+{
+    RS_GUARD({
+        if (!ctx || !cfg || !pop) return RS_ERR_INVALID;
+        return evolve_run(ctx, ds, cfg, pop, best, mean, S(stream));
+    })
+}
+
+rs_status rs_finetune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float *a, float *b, float *t,
+                      float tau, float lr, int32_t steps, float *loss_trace, void *stream)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return finetune_run(ctx, ds, batch, a, b, t, tau, lr, steps, loss_trace, S(stream));
     })
 }
 

@@ -200,6 +200,17 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchD
     return launch_hard(ctx, ds, tc, a, stream);
 }
 
+rs_status enqueue_hard_dev_sizes(Ctx *ctx, Dataset *ds, const TileConfig &tc, BatchDev bd,
+                                 const int32_t *dR, const int32_t *dC, const Scratch &s,
+                                 int32_t *correct, int32_t *per_class, int32_t *preds,
+                                 cudaStream_t stream)
+{
+    // R and C are capacities here (packing grids); the kernels read the real counts from dR / dC
+    bd.dR = dR;
+    bd.dC = dC;
+    return enqueue_hard(ctx, ds, tc, bd, s, correct, per_class, preds, stream);
+}
+
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     ~GraphEntry() { if (exec) cudaGraphExecDestroy(exec); }

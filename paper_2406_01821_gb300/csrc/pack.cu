@@ -89,6 +89,7 @@ __device__ void rewrite_lin(float a, float t, int op, float &v0, float &v1)
 __global__ void k_pack_rules2(BatchDev b, int F, int K, int S, Rec *recs_out, uint32_t *status)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
     if (r >= b.R) return;
     const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
     if (c0 < 0 || c1 < c0 || c1 > b.C) { atomicOr(status, ST_BAD_OFFSETS); return; }
@@ -126,6 +127,7 @@ __global__ void k_pack_rules2(BatchDev b, int F, int K, int S, Rec *recs_out, ui
 __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
     if (p == 0) {
         if (b.set_rule_off[0] != 0 || b.set_rule_off[b.P] != b.R ||
             b.rule_cond_off[0] != 0 || b.rule_cond_off[b.R] != b.C)
@@ -167,6 +169,7 @@ __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
 __global__ void k_pack_rules(BatchDev b, int F, int K, Rec *recs, uint32_t *status)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
     if (r >= b.R) return;
     const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
     if (c0 < 0 || c1 < c0 || c1 > b.C) { atomicOr(status, ST_BAD_OFFSETS); return; }

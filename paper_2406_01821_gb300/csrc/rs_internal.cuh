@@ -80,9 +80,12 @@ struct __align__(16) SetInfo {
     int32_t cost;                // rec_end - rec_begin
 };
 
-// Device-side view of a batch (device pointers).
+// Device-side view of a batch (device pointers). When dR / dC are set, the rule and condition
+// counts are read on the device (batches built on the device); R and C then hold capacities that
+// size the packing grids.
 struct BatchDev {
     int32_t P, R, C;
+    const int32_t *dR = nullptr, *dC = nullptr;
     const int32_t *set_rule_off, *rule_cond_off, *rule_class, *set_default;
     const int32_t *cond_f, *cond_g;
     const int8_t *cond_op;
@@ -97,6 +100,7 @@ struct Dataset {
     float *Xt = nullptr;          // [F][n_pad], samples grouped by label (stable), zero padded
     int32_t *y = nullptr;         // [n_pad] labels in that order, -1 for padding
     int32_t *perm = nullptr;      // [N] caller index of sorted position
+    int32_t *inv = nullptr;       // [N] sorted position of caller index
     std::vector<int64_t> class_count;
     std::map<int, CUtensorMap> tmaps;   // keyed by samples per tile
     std::mutex mu;
@@ -221,7 +225,6 @@ int heuristic_tile_for(const Dataset &ds);
 const CUtensorMap *dataset_tmap(Dataset *ds, int S);
 
 struct SoftArgs {
-    const Rec *recs_unused;
     BatchDev b;
     const float *Xt;
     const int32_t *y;
@@ -235,7 +238,16 @@ struct SoftArgs {
     float *grad_a, *grad_b, *grad_t;
     uint32_t *status;
 };
+// Validate (one host readback of the batch's largest set) and run.
 rs_status launch_soft(Ctx *ctx, const SoftArgs &a, cudaStream_t stream);
+// Run with known bounds on rules and conditions per set, no host synchronisation; the kernels
+// skip all work if the status word is non-zero.
+rs_status soft_step_known(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, cudaStream_t stream);
+// Hard evaluation of a device-built batch whose R and C are known only on the device.
+rs_status enqueue_hard_dev_sizes(Ctx *ctx, Dataset *ds, const TileConfig &tc, BatchDev bd,
+                                 const int32_t *dR, const int32_t *dC, const Scratch &s,
+                                 int32_t *correct, int32_t *per_class, int32_t *preds,
+                                 cudaStream_t stream);
 
 }  // namespace rs
 

@@ -194,7 +194,7 @@ __global__ void k_class_start(const int64_t *class_total, int K, int64_t *class_
 
 __global__ void k_label_scatter(const int32_t *y, int64_t N, int K, const int32_t *blk_off,
                                 const int64_t *class_start, const int32_t *rank, int32_t *perm,
-                                int32_t *y_sorted)
+                                int32_t *inv, int32_t *y_sorted)
 {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -203,6 +203,7 @@ __global__ void k_label_scatter(const int32_t *y, int64_t N, int K, const int32_
     const int64_t blk = n / REG_BLOCK;
     const int64_t pos = class_start[lab] + blk_off[blk * K + lab] + rank[n];
     perm[pos] = (int32_t)n;
+    inv[n] = (int32_t)pos;
     y_sorted[pos] = lab;
 }
 
@@ -308,7 +309,7 @@ rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, 
         if (e_ != cudaSuccess) {                            \
             rc = cuda_fail(e_, #call);                      \
             cleanup();                                      \
-            cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm); \
+            cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm); cudaFree(ds->inv); \
             return rc;                                      \
         }                                                   \
     } while (0)
@@ -325,6 +326,7 @@ rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, 
     REG_CUDA(cudaMalloc(&ds->Xt, sizeof(float) * ds->n_pad * F));
     REG_CUDA(cudaMalloc(&ds->y, sizeof(int32_t) * ds->n_pad));
     REG_CUDA(cudaMalloc(&ds->perm, sizeof(int32_t) * N));
+    REG_CUDA(cudaMalloc(&ds->inv, sizeof(int32_t) * N));
     REG_CUDA(cudaMalloc(&blk, sizeof(int32_t) * nblk * K));
     REG_CUDA(cudaMalloc(&rank, sizeof(int32_t) * N));
     REG_CUDA(cudaMalloc(&ctot, sizeof(int64_t) * K));
@@ -342,13 +344,13 @@ rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, 
     if (hst) {
         cleanup();
         set_error("dataset rejected: %s", status_text(hst).c_str());
-        cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm);
+        cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm); cudaFree(ds->inv);
         return RS_ERR_INVALID;
     }
     k_label_offsets<<<(K + 127) / 128, 128, 0, stream>>>(blk, nblk, K, ctot);
     k_class_start<<<1, 32, 0, stream>>>(ctot, K, cstart);
     k_label_scatter<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(yd, N, K, blk, cstart, rank,
-                                                                      ds->perm, ds->y);
+                                                                      ds->perm, ds->inv, ds->y);
     dim3 tg((unsigned)(ds->n_pad / 32), (unsigned)((F + 31) / 32));
     k_transpose_gather<<<tg, dim3(32, 8), 0, stream>>>(Xd, N, F, ds->n_pad, ds->perm, ds->Xt);
     REG_CUDA(cudaGetLastError());
@@ -384,6 +386,7 @@ rs_status dataset_destroy(Ctx *ctx, uint64_t h)
     cudaFree(ds->Xt);
     cudaFree(ds->y);
     cudaFree(ds->perm);
+    cudaFree(ds->inv);
     return RS_OK;
 }
 

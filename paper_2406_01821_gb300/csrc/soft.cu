@@ -44,6 +44,7 @@ struct __align__(16) SoftRec {
 __global__ void k_pack_soft(BatchDev b, int F, int K, SoftRec *recs, uint32_t *status)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
     if (c >= b.C) return;
     const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
     SoftRec r{0, 0, 0, 0.f, 0.f};
@@ -60,9 +61,11 @@ __global__ void k_pack_soft(BatchDev b, int F, int K, SoftRec *recs, uint32_t *s
 }
 
 // Validation of the set/rule structure (one thread per set).
-__global__ void k_check_sets_soft(BatchDev b, int K, uint32_t *status, int32_t *maxima)
+__global__ void k_check_sets_soft(BatchDev b, int K, uint32_t *status, int32_t *maxima, int maxR,
+                                  int maxC)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
     if (p == 0) {
         if (b.set_rule_off[0] != 0 || b.set_rule_off[b.P] != b.R ||
             b.rule_cond_off[0] != 0 || b.rule_cond_off[b.R] != b.C)
@@ -81,7 +84,7 @@ __global__ void k_check_sets_soft(BatchDev b, int K, uint32_t *status, int32_t *
         if (cls < 0 || cls >= K) atomicOr(status, ST_BAD_CLASS);
     }
     const int nc = re > rb ? b.rule_cond_off[re] - b.rule_cond_off[rb] : 0;
-    if (nc > SOFT_MAX_CONDS) atomicOr(status, ST_TOO_LARGE);
+    if (nc > SOFT_MAX_CONDS || re - rb > maxR || nc > maxC) atomicOr(status, ST_TOO_LARGE);
     atomicMax(&maxima[0], re - rb);
     atomicMax(&maxima[1], nc);
 }
@@ -133,6 +136,8 @@ struct SoftKArgs {
     int32_t backward;
     int32_t *next;                   // work counter
     int32_t maxR, maxC;              // shared-memory capacity per warp (rules, conditions)
+    int64_t Ccap;                    // row stride of the gradient partials
+    const uint32_t *status;          // no work if non-zero (malformed batch)
 };
 
 template <bool BWD>
@@ -147,6 +152,7 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
     float(*lq)[32] = reinterpret_cast<float(*)[32]>(base_w);
     float(*lu)[32] = reinterpret_cast<float(*)[32]>(base_w + (size_t)a.maxR * 32);
     float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * 32);
+    if (*a.status) return;
 
     while (true) {
         int64_t task = 0;
@@ -250,10 +256,9 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
         if (lane == 0) a.part_loss[(int64_t)ch * a.P + p] = ls;
         if (BWD) {
             __syncwarp();
-            const int64_t C = a.rule_cond_off[a.set_rule_off[a.P]];
             for (int i = lane; i < (ce - cb); i += 32) {
-                a.part_ga[(int64_t)ch * C + cb + i] = acc[i][0];
-                a.part_gbt[(int64_t)ch * C + cb + i] = acc[i][2];
+                a.part_ga[(int64_t)ch * a.Ccap + cb + i] = acc[i][0];
+                a.part_gbt[(int64_t)ch * a.Ccap + cb + i] = acc[i][2];
             }
             __syncwarp();
         }
@@ -273,10 +278,11 @@ __device__ __forceinline__ float tree_sum_strided(const float *base, int64_t str
     return v[0];
 }
 
-__global__ void k_soft_reduce_loss(const float *part_loss, int nchunks, int P, float inv_n, float *loss)
+__global__ void k_soft_reduce_loss(const float *part_loss, int nchunks, int P, float inv_n, float *loss,
+                                   const uint32_t *status)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
+    if (p >= P || *status) return;
     loss[p] = tree_sum_strided(part_loss + p, P, nchunks) * inv_n;
 }
 
@@ -284,10 +290,11 @@ __global__ void k_soft_reduce_loss(const float *part_loss, int nchunks, int P, f
 __global__ void k_soft_reduce_grad(const float *part_ga, const float *part_gbt, int nchunks,
                                    const int32_t *set_rule_off, const int32_t *rule_cond_off,
                                    const SoftRec *recs, int P, int64_t C, const float *dloss,
-                                   float inv_n, float *grad_a, float *grad_b, float *grad_t)
+                                   float inv_n, float *grad_a, float *grad_b, float *grad_t,
+                                   const uint32_t *status)
 {
     const int p = blockIdx.x;
-    if (p >= P) return;
+    if (p >= P || *status) return;
     const int cb = rule_cond_off[set_rule_off[p]], ce = rule_cond_off[set_rule_off[p + 1]];
     const float scale = dloss[p] * inv_n;
     for (int c = cb + threadIdx.x; c < ce; c += blockDim.x) {
@@ -302,11 +309,12 @@ __global__ void k_soft_reduce_grad(const float *part_ga, const float *part_gbt, 
 
 }  // namespace
 
-rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
+// Shared body of both entry points. `known` = bounds given by the caller (no host readback).
+static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known_maxC, cudaStream_t stream)
 {
     const BatchDev &b = s.b;
     const int P = b.P;
-    const int64_t C = b.C;
+    const int64_t Ccap = std::max<int64_t>(b.C, 1);     // capacity when sizes are device-side
     if (P == 0) return RS_OK;
     int nchunks = (int)std::min<int64_t>(SOFT_MAX_CHUNKS, (s.N + 1023) / 1024);
     if (nchunks < 1) nchunks = 1;
@@ -318,18 +326,20 @@ rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
     float *part_loss = nullptr, *part_ga = nullptr, *part_gbt = nullptr;
     int32_t *next = nullptr;   // [0] work counter, [1..2] max rules / conditions per set
     const bool bwd = s.dloss != nullptr;
-    RS_CUDA(cudaMallocAsync(&recs, sizeof(SoftRec) * std::max<int64_t>(C, 1), stream));
+    RS_CUDA(cudaMallocAsync(&recs, sizeof(SoftRec) * Ccap, stream));
     RS_CUDA(cudaMallocAsync(&part_loss, sizeof(float) * (size_t)nchunks * P, stream));
     RS_CUDA(cudaMallocAsync(&next, sizeof(int32_t) * 4, stream));
     if (bwd) {
-        RS_CUDA(cudaMallocAsync(&part_ga, sizeof(float) * (size_t)nchunks * std::max<int64_t>(C, 1), stream));
-        RS_CUDA(cudaMallocAsync(&part_gbt, sizeof(float) * (size_t)nchunks * std::max<int64_t>(C, 1), stream));
+        RS_CUDA(cudaMallocAsync(&part_ga, sizeof(float) * (size_t)nchunks * Ccap, stream));
+        RS_CUDA(cudaMallocAsync(&part_gbt, sizeof(float) * (size_t)nchunks * Ccap, stream));
     }
     RS_CUDA(cudaMemsetAsync(next, 0, sizeof(int32_t) * 4, stream));
-    k_check_sets_soft<<<(P + 255) / 256, 256, 0, stream>>>(b, s.K, s.status, next + 1);
-    if (C > 0) k_pack_soft<<<(unsigned)((C + 255) / 256), 256, 0, stream>>>(b, s.F, s.K, recs, s.status);
-    count_launch(ctx, 1 + (C > 0 ? 1 : 0));
-    // The main kernel reads only validated structure: skip it when validation failed.
+    const bool known = known_maxR > 0;
+    k_check_sets_soft<<<(P + 255) / 256, 256, 0, stream>>>(b, s.K, s.status, next + 1,
+                                                           known ? known_maxR : SOFT_MAX_RULES,
+                                                           known ? known_maxC : SOFT_MAX_CONDS);
+    k_pack_soft<<<(unsigned)((Ccap + 255) / 256), 256, 0, stream>>>(b, s.F, s.K, recs, s.status);
+    count_launch(ctx, 2);
     SoftKArgs k{};
     k.recs = recs;
     k.set_rule_off = b.set_rule_off;
@@ -352,20 +362,32 @@ rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
     k.probs = s.probs;
     k.backward = bwd;
     k.next = next;
+    k.Ccap = Ccap;
+    k.status = s.status;
     rs_status rc = RS_OK;
-    uint32_t *hs = host_status_slot();
-    // validation must finish before the evaluator trusts the offsets: read the status word
-    RS_CUDA(cudaMemcpyAsync(hs, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
-    RS_CUDA(cudaMemcpyAsync(hs + 1, next + 1, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, stream));
-    RS_CUDA(cudaStreamSynchronize(stream));
-    k.maxR = std::max<int32_t>(1, (int32_t)hs[1]);
-    k.maxC = std::max<int32_t>(1, (int32_t)hs[2]);
-    const size_t smem = sizeof(float) * SOFT_W *
-                        ((size_t)(2 * k.maxR + 1) * 32 + (size_t)k.maxC * 4);
-    if (*hs) {
-        rc = (*hs & ST_TOO_LARGE) ? RS_ERR_TOO_LARGE : RS_ERR_INVALID;
-        set_error("soft evaluation rejected the batch: %s", status_text(*hs).c_str());
+    if (known) {
+        k.maxR = known_maxR;
+        k.maxC = known_maxC;
     } else {
+        // validation must finish before the launch is sized: read the status and the maxima
+        uint32_t *hs = host_status_slot();
+        if (!hs) return RS_ERR_OOM;
+        RS_CUDA(cudaMemcpyAsync(hs, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+        RS_CUDA(cudaMemcpyAsync(hs + 1, next + 1, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, stream));
+        RS_CUDA(cudaStreamSynchronize(stream));
+        k.maxR = std::max<int32_t>(1, (int32_t)hs[1]);
+        k.maxC = std::max<int32_t>(1, (int32_t)hs[2]);
+        if (*hs) {
+            rc = (*hs & ST_TOO_LARGE) ? RS_ERR_TOO_LARGE : RS_ERR_INVALID;
+            set_error("soft evaluation rejected the batch: %s", status_text(*hs).c_str());
+        }
+    }
+    const size_t smem = sizeof(float) * SOFT_W * ((size_t)(2 * k.maxR + 1) * 32 + (size_t)k.maxC * 4);
+    if (rc == RS_OK && smem > ctx->smem_optin) {
+        rc = RS_ERR_TOO_LARGE;
+        set_error("soft evaluation: sets too large for shared memory");
+    }
+    if (rc == RS_OK) {
         static std::once_flag once;
         std::call_once(once, [&] {
             cudaFuncSetAttribute(k_soft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
@@ -380,13 +402,14 @@ rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
             if (bwd) k_soft<true><<<grid, SOFT_W * 32, smem, stream>>>(k);
             else k_soft<false><<<grid, SOFT_W * 32, smem, stream>>>(k);
         }
-        count_launch(ctx, 2 + ((bwd && C > 0) ? 1 : 0));
         k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
-                                                               1.0f / (float)s.N, s.loss);
-        if (bwd && C > 0)
+                                                               1.0f / (float)s.N, s.loss, s.status);
+        if (bwd)
             k_soft_reduce_grad<<<P, 128, 0, stream>>>(part_ga, part_gbt, nchunks, b.set_rule_off,
-                                                     b.rule_cond_off, recs, P, C, s.dloss,
-                                                     1.0f / (float)s.N, s.grad_a, s.grad_b, s.grad_t);
+                                                     b.rule_cond_off, recs, P, Ccap, s.dloss,
+                                                     1.0f / (float)s.N, s.grad_a, s.grad_b, s.grad_t,
+                                                     s.status);
+        count_launch(ctx, 2 + (bwd ? 1 : 0));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "soft kernels");
     }
@@ -395,6 +418,16 @@ rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
     cudaFreeAsync(next, stream);
     if (bwd) { cudaFreeAsync(part_ga, stream); cudaFreeAsync(part_gbt, stream); }
     return rc;
+}
+
+rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
+{
+    return soft_run(ctx, s, 0, 0, stream);
+}
+
+rs_status soft_step_known(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, cudaStream_t stream)
+{
+    return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream);
 }
 
 }  // namespace rs

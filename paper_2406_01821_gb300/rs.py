@@ -48,6 +48,19 @@ class rs_profile(ctypes.Structure):
                 ("soft_ms", ctypes.c_double)]
 
 
+class rs_population(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("nrule", "deflt", "rcls", "ncond", "cf", "cg", "cop",
+                                               "ca", "cb", "ct", "fitness")]
+
+
+class rs_evolve_config(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int32), ("RMAX", ctypes.c_int32), ("CMAX", ctypes.c_int32),
+                ("generations", ctypes.c_int32), ("elite", ctypes.c_int32),
+                ("tune_every", ctypes.c_int32), ("tune_top", ctypes.c_int32),
+                ("tune_steps", ctypes.c_int32), ("tau", ctypes.c_float), ("lr", ctypes.c_float),
+                ("lamarckian", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 _lib = None
 
 _SIGS = {
@@ -78,6 +91,12 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "rs_profile_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rs_profile), ctypes.c_int32]),
+    "rs_evolve": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_evolve_config),
+                                   ctypes.POINTER(rs_population), ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    "rs_finetune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "rs_tile_config_count": (ctypes.c_int32, []),
     "rs_tile_config_info": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -306,6 +325,37 @@ class Context:
         p = rs_profile()
         check(lib().rs_profile_read(self.h, ctypes.byref(p), int(reset)))
         return {f: getattr(p, f) for f, _ in rs_profile._fields_}
+
+    def evolve(self, ds: int, pop: dict, generations: int, elite: int, seed: int, tune_every=0,
+               tune_top=0, tune_steps=0, tau=0.1, lr=1e-2, lamarckian=False, stream=None):
+        """Device-resident evolution. ``pop`` = dict of fixed-slot numpy arrays (nrule [P],
+        deflt [P], rcls/ncond [P,RMAX], cf/cg/cop/ca/cb/ct [P,RMAX,CMAX]); returns
+        (final population dict, fitness [P], best [G+1], mean [G+1])."""
+        kinds = {"nrule": np.int32, "deflt": np.int32, "rcls": np.int32, "ncond": np.int32,
+                 "cf": np.int32, "cg": np.int32, "cop": np.int8, "ca": np.float32, "cb": np.float32,
+                 "ct": np.float32}
+        arr = {k: np.ascontiguousarray(pop[k], t).copy() for k, t in kinds.items()}
+        P, RMAX, CMAX = arr["cf"].shape
+        fitness = np.zeros(P, np.int32)
+        best = np.zeros(generations + 1, np.int32)
+        mean = np.zeros(generations + 1, np.float64)
+        cp = rs_population(*[_ptr(arr[k]) for k in kinds], _ptr(fitness))
+        cfg = rs_evolve_config(P, RMAX, CMAX, generations, elite, tune_every, tune_top, tune_steps,
+                               tau, lr, int(lamarckian), seed)
+        check(lib().rs_evolve(self.h, ds, ctypes.byref(cfg), ctypes.byref(cp), _ptr(best), _ptr(mean),
+                              _stream_ptr(stream)))
+        return arr, fitness, best, mean
+
+    def finetune(self, ds: int, batch: DeviceBatch, tau: float, lr: float, steps: int, stream=None):
+        """Adam fine-tuning of a device batch; returns (a, b, t, loss_trace [steps, P])."""
+        a = batch.t["cond_a"].clone()
+        b = batch.t["cond_b"].clone()
+        t = batch.t["cond_t"].clone()
+        trace = np.zeros((steps, batch.P), np.float32)
+        cb = batch.c()
+        check(lib().rs_finetune(self.h, ds, ctypes.byref(cb), _ptr(a), _ptr(b), _ptr(t), float(tau),
+                                float(lr), int(steps), _ptr(trace), _stream_ptr(stream)))
+        return a, b, t, trace
 
     def check_async(self, stream=None):
         check(lib().rs_check(self.h, _stream_ptr(stream)))

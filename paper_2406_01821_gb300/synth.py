@@ -283,3 +283,61 @@ def boundary_samples(batch: Batch, F: int, N: int, seed: int, frac: float = 0.7,
                 x = np.nextafter(x, direction, dtype=np.float32)
             X[n, f] = x
     return X
+
+
+# ------------------------------------------------------------------------------ populations
+
+POP_FIELDS = ("nrule", "deflt", "rcls", "ncond", "cf", "cg", "cop", "ca", "cb", "ct")
+
+
+def population_from_batch(batch: Batch, RMAX: int, CMAX: int):
+    """Fixed-slot population arrays (rule r of set p at [p, r], condition k at [p, r, k]) from a
+    CSR batch whose sets have <= RMAX rules of 1..CMAX conditions. Unused slots are zero."""
+    P = batch.P
+    pop = {"nrule": np.zeros(P, np.int32), "deflt": batch.set_default.astype(np.int32).copy(),
+           "rcls": np.zeros((P, RMAX), np.int32), "ncond": np.zeros((P, RMAX), np.int32),
+           "cf": np.zeros((P, RMAX, CMAX), np.int32), "cg": np.full((P, RMAX, CMAX), -1, np.int32),
+           "cop": np.zeros((P, RMAX, CMAX), np.int8), "ca": np.zeros((P, RMAX, CMAX), np.float32),
+           "cb": np.zeros((P, RMAX, CMAX), np.float32), "ct": np.zeros((P, RMAX, CMAX), np.float32)}
+    for p in range(P):
+        r0, r1 = batch.set_rule_off[p], batch.set_rule_off[p + 1]
+        assert r1 - r0 <= RMAX
+        pop["nrule"][p] = r1 - r0
+        for j, r in enumerate(range(r0, r1)):
+            c0, c1 = batch.rule_cond_off[r], batch.rule_cond_off[r + 1]
+            assert 1 <= c1 - c0 <= CMAX
+            pop["rcls"][p, j] = batch.rule_class[r]
+            pop["ncond"][p, j] = c1 - c0
+            sl = slice(c0, c1)
+            pop["cf"][p, j, :c1 - c0] = batch.cond_f[sl]
+            pop["cg"][p, j, :c1 - c0] = batch.cond_g[sl]
+            pop["cop"][p, j, :c1 - c0] = batch.cond_op[sl]
+            pop["ca"][p, j, :c1 - c0] = batch.cond_a[sl]
+            pop["cb"][p, j, :c1 - c0] = batch.cond_b[sl]
+            pop["ct"][p, j, :c1 - c0] = batch.cond_t[sl]
+    return pop
+
+
+def batch_from_population(pop) -> Batch:
+    """CSR batch of the live slots of a fixed-slot population."""
+    P, RMAX, CMAX = pop["cf"].shape
+    nrule = pop["nrule"]
+    set_rule_off = np.zeros(P + 1, np.int32)
+    set_rule_off[1:] = np.cumsum(nrule)
+    live = np.arange(RMAX)[None, :] < nrule[:, None]
+    nc = pop["ncond"][live]
+    rule_cond_off = np.zeros(len(nc) + 1, np.int32)
+    rule_cond_off[1:] = np.cumsum(nc)
+    cmask = live[:, :, None] & (np.arange(CMAX)[None, None, :] < pop["ncond"][:, :, None])
+    return Batch(set_rule_off, rule_cond_off, pop["rcls"][live].astype(np.int32),
+                 pop["deflt"].astype(np.int32), pop["cf"][cmask].astype(np.int32),
+                 pop["cg"][cmask].astype(np.int32), pop["cop"][cmask].astype(np.int8),
+                 pop["ca"][cmask].astype(np.float32), pop["cb"][cmask].astype(np.float32),
+                 pop["ct"][cmask].astype(np.float32))
+
+
+def initial_population(X, y, K, P, RMAX=32, CMAX=6, seed=0):
+    """Random initial population: R ~ U{1..RMAX}, C ~ U{1..CMAX}, default = majority class."""
+    b = random_rulesets(quantile_table(X), K, P, (1, RMAX), (1, CMAX), seed,
+                        default=majority_class(y, K))
+    return population_from_batch(b, RMAX, CMAX)

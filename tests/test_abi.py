@@ -53,7 +53,7 @@ def test_tile_configs_describe_themselves(lib):
     assert len(cfgs) >= 4
     for c in cfgs:
         assert c["samples_per_tile"] == 32 * c["samples_per_lane"]
-        assert c["warps"] in (4, 8, 16)
+        assert c["warps"] in (4, 8, 16, 32)
     assert lib.rs_tile_config_info(len(cfgs), None, None, None) == -1
 
 

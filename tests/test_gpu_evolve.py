@@ -1,0 +1,119 @@
+"""GPU parity of the device-resident evolution loop and of fine-tuning.
+
+Without fine-tuning every step is exact (integer fitness, Philox draws, float32 operations that
+both sides perform identically), so the GPU trajectory must equal the oracle's bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2406_01821_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    c = rs.Context(0)
+    yield c
+    c.close()
+
+
+def oracle_run(orc, X, y, K, pop, generations, elite, seed):
+    best, mean = [], []
+    for g in range(generations + 1):
+        fit, _, _ = orc.eval_hard(X, y, K, synth.batch_from_population(pop))
+        best.append(int(fit.max()))
+        mean.append(float(fit.mean()))
+        if g == generations:
+            return pop, fit, np.array(best), np.array(mean)
+        pop = orc.evolve_step(pop, fit, seed, g, elite, X, K)
+
+
+@pytest.mark.parametrize("seed,K", [(3, 2), (4, 3)])
+def test_evolution_matches_oracle_bit_exact(ctx, orc, seed, K):
+    X, y = synth.gaussian_mixture(3001, 9, K, seed)
+    pop = synth.initial_population(X, y, K, 96, RMAX=8, CMAX=4, seed=seed)
+    ds = ctx.dataset(X, y, K)
+    try:
+        got, fit, best, mean = ctx.evolve(ds, pop, generations=4, elite=3, seed=seed)
+    finally:
+        ctx.dataset_destroy(ds)
+    want, wfit, wbest, wmean = oracle_run(orc, X, y, K, pop, 4, 3, seed)
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+    assert np.array_equal(fit, wfit)
+    assert np.array_equal(best, wbest)
+    assert np.allclose(mean, wmean, rtol=0, atol=1e-12)
+
+
+def test_lamarckian_tuning_keeps_best_monotone(ctx, orc):
+    X, y = synth.two_class_gaussian(4000, 8, 5)
+    pop = synth.initial_population(X, y, 2, 64, RMAX=6, CMAX=3, seed=5)
+    ds = ctx.dataset(X, y, 2)
+    try:
+        got, fit, best, mean = ctx.evolve(ds, pop, generations=6, elite=2, seed=5, tune_every=2,
+                                          tune_top=8, tune_steps=5, tau=0.1, lr=1e-2, lamarckian=True)
+    finally:
+        ctx.dataset_destroy(ds)
+    assert (np.diff(best) >= 0).all(), best
+    # the returned fitness is the exact evaluation of the returned genomes
+    wfit, _, _ = orc.eval_hard(X, y, 2, synth.batch_from_population(got))
+    assert np.array_equal(fit, wfit)
+
+
+def test_baldwinian_tuning_runs_and_keeps_valid_genomes(ctx, orc):
+    X, y = synth.two_class_gaussian(4000, 8, 6)
+    pop = synth.initial_population(X, y, 2, 64, RMAX=6, CMAX=3, seed=6)
+    ds = ctx.dataset(X, y, 2)
+    try:
+        got, fit, best, mean = ctx.evolve(ds, pop, generations=4, elite=2, seed=6, tune_every=1,
+                                          tune_top=8, tune_steps=3)
+    finally:
+        ctx.dataset_destroy(ds)
+    wfit, _, _ = orc.eval_hard(X, y, 2, synth.batch_from_population(got))
+    assert np.array_equal(fit, wfit)
+
+
+def test_finetune_matches_float64_adam(ctx, orc):
+    """Three Adam steps of the library against float64 Adam on the oracle's gradients."""
+    import torch
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.two_class_gaussian(3000, 6, 7)
+    b = synth.random_rulesets(synth.quantile_table(X), 2, 6, (1, 5), (1, 3), 7, pair_prob=0.3)
+    b.set_default[:] = np.where(b.rule_class[b.set_rule_off[:-1]] == 0, 1, 0)
+    tau, lr, steps = 0.25, 1e-2, 3
+    ds = ctx.dataset(X, y, 2)
+    try:
+        a, bb, t, trace = ctx.finetune(ds, rs.DeviceBatch.from_host(b), tau, lr, steps)
+        torch.cuda.synchronize()
+        a, bb, t = a.cpu().numpy(), bb.cpu().numpy(), t.cpu().numpy()
+    finally:
+        ctx.dataset_destroy(ds)
+    # float64 reference: Adam on the oracle's gradients
+    pair = b.cond_g >= 0
+    th = [b.cond_a.astype(np.float64), np.where(pair, b.cond_b, b.cond_t).astype(np.float64)]
+    m = [np.zeros(b.C), np.zeros(b.C)]
+    v = [np.zeros(b.C), np.zeros(b.C)]
+    ref_trace = []
+    well = np.ones(b.C, bool)
+    for step in range(1, steps + 1):
+        cur = synth.Batch(**b.arrays())
+        cur.cond_a = th[0].astype(np.float32)
+        cur.cond_b = np.where(pair, th[1], 0).astype(np.float32)
+        cur.cond_t = np.where(pair, 0, th[1]).astype(np.float32)
+        out = orc.soft(X, y, 2, cur, tau, dloss=np.ones(b.P), want_mag=True)
+        ref_trace.append(out["loss"])
+        g = [out["grad_a"], np.where(pair, out["grad_b"], out["grad_t"])]
+        mag = [out["mag_a"], np.where(pair, out["mag_b"], out["mag_t"])]
+        for k in range(2):
+            well &= np.abs(g[k]) > 1e-3 * mag[k]          # the sign of the step is well determined
+            m[k] = 0.9 * m[k] + 0.1 * g[k]
+            v[k] = 0.999 * v[k] + 0.001 * g[k] ** 2
+            mh, vh = m[k] / (1 - 0.9 ** step), v[k] / (1 - 0.999 ** step)
+            th[k] = th[k] - lr * mh / (np.sqrt(vh) + 1e-8)
+    assert np.allclose(trace, np.array(ref_trace), rtol=1e-5, atol=0)
+    got2 = np.where(pair, bb, t)
+    assert well.sum() > 0.5 * b.C
+    assert np.allclose(a[well], th[0][well], rtol=0, atol=1e-5)
+    assert np.allclose(got2[well], th[1][well], rtol=0, atol=1e-5)
