@@ -179,7 +179,8 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchD
                               int32_t *preds, cudaStream_t stream)
 {
     PackOut po{s.recs, s.sets, s.order, s.status};
-    count_launch(ctx, launch_pack(bd, ds->F, ds->K, tc.S(), tc.ver >= 2 ? 2 : 1, po, stream));
+    const int ver = effective_version(tc, *ds, preds != nullptr);
+    count_launch(ctx, launch_pack(bd, ds->F, ds->K, tc.S(), ver == 4 ? 4 : (ver >= 2 ? 2 : 1), po, stream));
     RS_CUDA(cudaGetLastError());
     HardArgs a{};
     a.recs = s.recs;

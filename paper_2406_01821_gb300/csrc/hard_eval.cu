@@ -259,12 +259,19 @@ const TileConfig kConfigs[] = {
     {6, 8, 8, 1}, {7, 8, 4, 1},
     {8, 4, 8, 2}, {9, 4, 16, 2}, {10, 2, 16, 2},
     {11, 4, 8, 3}, {12, 4, 16, 3}, {13, 2, 16, 3}, {14, 2, 32, 3}, {15, 4, 32, 3},
+    {16, 4, 8, 4}, {17, 4, 16, 4}, {18, 4, 32, 4}, {19, 2, 16, 4}, {20, 2, 32, 4},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 }  // namespace
 
 int tile_config_count() { return kNumConfigs; }
+
+int effective_version(const TileConfig &tc, const Dataset &ds, bool preds)
+{
+    if (tc.ver == 4 && (preds || !ds.finite)) return 3;   // same V and W exist for version 3
+    return tc.ver;
+}
 const TileConfig &tile_config(int id) { return kConfigs[id]; }
 
 bool tile_config_fits(const TileConfig &tc, int F)
@@ -283,7 +290,9 @@ rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArg
     if (a.P > 0 && a.per_class)
         RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
-    if (tc.ver >= 2) return launch_hard2(ctx, ds, tc.V, tc.W, tc.ver == 3, a, stream);
+    const int ver = effective_version(tc, *ds, a.preds != nullptr);
+    if (ver == 4) return launch_hard4(ctx, ds, tc.V, tc.W, a, stream);
+    if (ver >= 2) return launch_hard2(ctx, ds, tc.V, tc.W, ver == 3, a, stream);
     switch (tc.id) {
     case 0: return launch_t<4, 8>(ctx, ds, a, stream);
     case 1: return launch_t<4, 4>(ctx, ds, a, stream);

@@ -1,0 +1,259 @@
+// Sign-mask evaluator for datasets with only finite values (record format v4).
+//
+// A threshold condition x > c holds exactly when x >= c' with c' = nextup(c), i.e. when
+// m = fl(x - c') has a clear sign bit: for finite x and c' != +0 the difference is +0 only for
+// x = c', positive above and negative below (gradual underflow), and x - c' never produces -0 or
+// NaN. A '<' cut is the same test on -x. Since the product by +-1 is exact, m is one fused
+// multiply-add, computed for two samples at a time with the packed f32x2 FMA; a rule's
+// conjunction is the OR of its conditions' margin bit patterns (fires iff the sign stays clear),
+// seeded with the "already claimed" sign of each sample. Feature-pair and general-product
+// conditions take an ordinary compare and contribute a sign mask.
+//
+// Per-class counting uses the label grouping of the dataset: in a tile holding one label k, only
+// rules of class k (and the default, if it is k) can add hits, decided once per rule for the whole
+// warp. Predictions are not produced here (the caller then uses the general evaluator).
+#include "rs_internal.cuh"
+#include "tma.cuh"
+
+namespace rs {
+
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr uint32_t SIGN = 0x80000000u;
+constexpr uint64_t TMA_WAIT_LIMIT_NS = 2000000000ull;
+
+template <int V>
+__device__ __forceinline__ void load_x(const float *p, float (&x)[V])
+{
+    if constexpr (V == 2) {
+        float2 t = *reinterpret_cast<const float2 *>(p);
+        x[0] = t.x; x[1] = t.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k += 4) {
+            float4 t = *reinterpret_cast<const float4 *>(p + k);
+            x[k] = t.x; x[k + 1] = t.y; x[k + 2] = t.z; x[k + 3] = t.w;
+        }
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void cond_mask(const uint4 r, const float *xl, uint32_t (&acc)[V])
+{
+    float x[V];
+    load_x<V>(xl + (r.x & OFF_MASK) * 4, x);
+    const float v0 = __uint_as_float(r.z), v1 = __uint_as_float(r.w);
+    if (!(r.x & (PAIR_BIT | GENERAL_BIT))) {
+        const float2 s2 = make_float2(v0, v0), c2 = make_float2(v1, v1);
+#pragma unroll
+        for (int v = 0; v < V; v += 2) {
+            const float2 m = __ffma2_rn(make_float2(x[v], x[v + 1]), s2, c2);
+            acc[v] |= __float_as_uint(m.x);
+            acc[v + 1] |= __float_as_uint(m.y);
+        }
+    } else if (r.x & PAIR_BIT) {
+        float z[V];
+        load_x<V>(xl + (r.y & OFF_MASK) * 4, z);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            acc[v] |= (__fmul_rn(v0, x[v]) > __fmul_rn(v1, z[v])) ? 0u : SIGN;
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] |= (__fmul_rn(v0, x[v]) > v1) ? 0u : SIGN;
+    }
+}
+
+template <int V, int W>
+__global__ void __launch_bounds__(W * 32) k_hard4(const __grid_constant__ CUtensorMap tmap, HardArgs a)
+{
+    constexpr int S = 32 * V;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int F = a.F;
+    const int Fb = F < 256 ? F : 256;
+    const int nbox = (F + Fb - 1) / Fb;
+    const int Frows = nbox * Fb;
+    float *xs = reinterpret_cast<float *>(smem);
+    uint4 *stage_all = reinterpret_cast<uint4 *>(smem + (size_t)Frows * S * sizeof(float));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(stage_all + W * 64);
+    int *next = reinterpret_cast<int *>(bar + 1);
+    const uint4 *recs = reinterpret_cast<const uint4 *>(a.recs);
+
+    const int tile = blockIdx.x, group = blockIdx.y, G = gridDim.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        *next = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(Frows * S * sizeof(float)));
+        for (int b = 0; b < nbox; ++b) tma_load_2d(xs + (size_t)b * Fb * S, &tmap, tile * S, b * Fb, bar);
+    }
+    const int64_t n0 = (int64_t)tile * S + lane * V;
+    int y[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) y[v] = a.y[n0 + v];
+    const int64_t t_last = min((int64_t)tile * S + S, a.N) - 1;
+    const int kmin = a.y[(int64_t)tile * S], kmax = a.y[t_last];
+    const bool uniform = kmin == kmax;
+
+    if (!mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT_NS)) {
+        if (threadIdx.x == 0) atomicOr(a.status, ST_WAIT_TIMEOUT);
+        mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT_NS);
+        return;
+    }
+
+    const int count = (a.P - group + G - 1) / G;
+    uint4 *st = stage_all + warp * 64;
+    const float *xl = xs + lane * V;
+    const uint4 zero4 = make_uint4(0, 0, 0, 0);
+
+    while (true) {
+        int m = 0;
+        if (lane == 0) m = atomicAdd(next, 1);
+        m = __shfl_sync(FULL, m, 0);
+        if (m >= count) break;
+        const int p = a.order[group + m * G];
+        const SetInfo si = a.sets[p];
+        const int rb = si.rec_begin, re = si.rec_end;
+
+        // sign set = claimed (padding samples start claimed and never count)
+        uint32_t claimed[V], hit[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            claimed[v] = y[v] >= 0 ? 0u : SIGN;
+            hit[v] = 0u;
+        }
+        int ck = 0;
+        uint4 pf = zero4;
+        if (rb < re) {
+            __syncwarp();
+            st[lane] = (rb + lane < re) ? __ldg(recs + rb + lane) : zero4;
+            st[32 + lane] = (rb + 32 + lane < re) ? __ldg(recs + rb + 32 + lane) : zero4;
+            pf = (rb + 64 + lane < re) ? __ldg(recs + rb + 64 + lane) : zero4;
+            __syncwarp();
+        }
+        int rel = 0;
+        const int nrec = re - rb;
+        while (rel < nrec) {
+            while ((rel >> 5) > ck) {
+                const uint4 keep = st[32 + lane];
+                __syncwarp();
+                st[lane] = keep;
+                st[32 + lane] = pf;
+                __syncwarp();
+                ++ck;
+                const int nx = rb + 32 * (ck + 2) + lane;
+                pf = (nx < re) ? __ldg(recs + nx) : zero4;
+            }
+            const uint4 *rp = st + (rel - 32 * ck);
+            const uint4 r0 = rp[0];
+            const int nc = (int)((r0.x >> LEN_SHIFT) & 0xFFFu);
+            const int cls = (int)(r0.y >> CLS_SHIFT);
+            uint32_t acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = claimed[v];
+            cond_mask<V>(r0, xl, acc);
+            if (nc <= 33) {
+#pragma unroll 2
+                for (int k = 1; k < nc; ++k) cond_mask<V>(rp[k], xl, acc);
+            } else {
+                for (int k = 1; k < nc; ++k) cond_mask<V>(__ldg(recs + rb + rel + k), xl, acc);
+            }
+            // fired: sign still clear. Claim, and count hits of this rule's class.
+            uint32_t all = SIGN;
+            if (uniform) {
+                const bool mine = cls == kmin;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t fired = ~acc[v] & SIGN;
+                    claimed[v] |= fired;
+                    if (mine) hit[v] |= fired;
+                    all &= claimed[v];
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t fired = ~acc[v] & SIGN;
+                    claimed[v] |= fired;
+                    hit[v] |= (y[v] == cls) ? fired : 0u;
+                    all &= claimed[v];
+                }
+            }
+            if (__all_sync(FULL, all != 0u)) break;
+            rel += nc;
+        }
+        // the default class takes what is left
+        const int d = si.deflt;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t left = ~claimed[v] & SIGN;
+            hit[v] |= (uniform ? (d == kmin) : (y[v] == d)) ? left : 0u;
+        }
+        __syncwarp();
+        int hits = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) hits += __popc(__ballot_sync(FULL, hit[v] != 0u));
+        if (lane == 0 && hits) atomicAdd(&a.correct[p], hits);
+        if (a.per_class) {
+            if (uniform) {
+                if (lane == 0 && hits) atomicAdd(&a.per_class[(int64_t)p * a.K + kmin], hits);
+            } else {
+                for (int k = kmin; k <= kmax; ++k) {
+                    int ckc = 0;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) ckc += __popc(__ballot_sync(FULL, hit[v] != 0u && y[v] == k));
+                    if (lane == 0 && ckc) atomicAdd(&a.per_class[(int64_t)p * a.K + k], ckc);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+template <int V, int W>
+rs_status launch4_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t stream)
+{
+    const int Fb = a.F < 256 ? a.F : 256;
+    const int Frows = ((a.F + Fb - 1) / Fb) * Fb;
+    const size_t smem = (size_t)Frows * 32 * V * sizeof(float) + (size_t)W * 64 * 16 + 16;
+    if (smem > ctx->smem_optin) return RS_ERR_TOO_LARGE;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(k_hard4<V, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ctx->smem_optin);
+    });
+    if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute(k_hard4)");
+    const CUtensorMap *tm = dataset_tmap(ds, 32 * V);
+    if (!tm) return RS_ERR_DEVICE;
+    const int tiles = (int)((a.N + 32 * V - 1) / (32 * V));
+    dim3 grid(tiles, a.groups);
+    {
+        TimedLaunch tl(ctx, TK_HARD, stream);
+        k_hard4<V, W><<<grid, W * 32, smem, stream>>>(*tm, a);
+    }
+    RS_CUDA(cudaGetLastError());
+    count_launch(ctx);
+    return RS_OK;
+}
+
+rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream)
+{
+    if (a.P > 0) RS_CUDA(cudaMemsetAsync(a.correct, 0, sizeof(int32_t) * a.P, stream));
+    if (a.P > 0 && a.per_class)
+        RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
+    if (a.P == 0) return RS_OK;
+    if (V == 4 && W == 8) return launch4_t<4, 8>(ctx, ds, a, stream);
+    if (V == 4 && W == 16) return launch4_t<4, 16>(ctx, ds, a, stream);
+    if (V == 4 && W == 32) return launch4_t<4, 32>(ctx, ds, a, stream);
+    if (V == 2 && W == 16) return launch4_t<2, 16>(ctx, ds, a, stream);
+    if (V == 2 && W == 32) return launch4_t<2, 32>(ctx, ds, a, stream);
+    return RS_ERR_INVALID;
+}
+
+}  // namespace rs

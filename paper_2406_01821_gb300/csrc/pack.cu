@@ -86,7 +86,7 @@ __device__ void rewrite_lin(float a, float t, int op, float &v0, float &v1)
 }
 
 // Pack v2 records: one thread per rule.
-__global__ void k_pack_rules2(BatchDev b, int F, int K, int S, Rec *recs_out, uint32_t *status)
+__global__ void k_pack_rules2(BatchDev b, int F, int K, int S, int form, Rec *recs_out, uint32_t *status)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
@@ -107,6 +107,16 @@ __global__ void k_pack_rules2(BatchDev b, int F, int K, int S, Rec *recs_out, ui
             atomicOr(status, ST_BAD_FEATURE);
         } else if (op != 0 && op != 1) {
             atomicOr(status, ST_BAD_OP);
+        } else if (g < 0 && form == 4) {
+            // cut form: x > c  <=>  sign(fl(+-x - c')) clear with c' = nextup(+-c)
+            uint32_t kind;
+            float c0, c1;
+            rewrite_threshold(b.cond_a[c], b.cond_t[c], op, kind, c0, c1);
+            const float pinf = __uint_as_float(0x7F800000u);
+            if (kind == KIND_GT) { v0 = 1.f; v1 = -nextafterf(c0, pinf); }
+            else if (kind == KIND_LT) { v0 = -1.f; v1 = -nextafterf(-c0, pinf); }
+            else { rewrite_lin(b.cond_a[c], b.cond_t[c], op, v0, v1); w0 |= GENERAL_BIT; }
+            w0 |= (uint32_t)f * row16;
         } else if (g < 0) {
             rewrite_lin(b.cond_a[c], b.cond_t[c], op, v0, v1);
             w0 |= (uint32_t)f * row16;
@@ -231,8 +241,8 @@ int launch_pack(const BatchDev &b, int F, int K, int S, int ver, const PackOut &
 {
     int n = 0;
     if (b.P > 0) { k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.status); ++n; }
-    if (b.R > 0 && ver == 2) {
-        k_pack_rules2<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, S, o.recs, o.status);
+    if (b.R > 0 && ver >= 2) {
+        k_pack_rules2<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, S, ver == 4 ? 4 : 2, o.recs, o.status);
         ++n;
     } else if (b.R > 0) {
         k_pack_rules<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status);

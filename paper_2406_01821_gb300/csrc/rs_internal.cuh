@@ -62,6 +62,8 @@ constexpr uint32_t OFF_MASK = 0x3FFFFu;
 constexpr uint32_t PAIR_BIT = 1u << 18;
 constexpr int LEN_SHIFT = 19;
 constexpr int CLS_SHIFT = 18;
+// v4 only: a threshold condition that is not a +-1 cut (zero or infinite coefficient, never true)
+constexpr uint32_t GENERAL_BIT = 1u << 31;
 
 struct __align__(16) Rec {
     uint32_t meta;   // [0,3) kind | [3] last condition of its rule | [4,16) rule class | [16,32) skip
@@ -97,6 +99,7 @@ struct BatchDev {
 struct Dataset {
     int64_t N = 0, n_pad = 0;
     int32_t F = 0, K = 0;
+    bool finite = false;          // no NaN or infinity in X
     float *Xt = nullptr;          // [F][n_pad], samples grouped by label (stable), zero padded
     int32_t *y = nullptr;         // [n_pad] labels in that order, -1 for padding
     int32_t *perm = nullptr;      // [N] caller index of sorted position
@@ -113,7 +116,8 @@ struct TileConfig {
     int V;       // samples per lane
     int W;       // warps per CTA
     int ver;     // 1: condition-at-a-time evaluator, 2: rule-at-a-time (record v2),
-                 // 3: rule-at-a-time with the margin-minimum conjunction
+                 // 3: rule-at-a-time with the margin-minimum conjunction,
+                 // 4: sign-mask conjunction for finite datasets (falls back to 3 otherwise)
     int S() const { return 32 * V; }
 };
 int tile_config_count();
@@ -216,6 +220,9 @@ rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArg
 int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P);
 rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, bool mm, const HardArgs &a,
                        cudaStream_t stream);
+rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream);
+// The evaluator version a configuration runs as for this dataset and output choice.
+int effective_version(const TileConfig &tc, const Dataset &ds, bool preds);
 // Enqueue packing + evaluation of a device batch with the given scratch.
 rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
                        const Scratch &s, int32_t *correct, int32_t *per_class, int32_t *preds,

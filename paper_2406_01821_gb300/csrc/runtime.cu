@@ -230,6 +230,14 @@ __global__ void k_transpose_gather(const float *X, int64_t N, int F, int64_t n_p
     }
 }
 
+__global__ void k_nonfinite(const float *x, int64_t n, uint32_t *flag)
+{
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -354,12 +362,18 @@ rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, 
     dim3 tg((unsigned)(ds->n_pad / 32), (unsigned)((F + 31) / 32));
     k_transpose_gather<<<tg, dim3(32, 8), 0, stream>>>(Xd, N, F, ds->n_pad, ds->perm, ds->Xt);
     REG_CUDA(cudaGetLastError());
+    REG_CUDA(cudaMemsetAsync(st, 0, sizeof(uint32_t), stream));
+    k_nonfinite<<<1024, 256, 0, stream>>>(ds->Xt, ds->n_pad * F, st);
+    REG_CUDA(cudaGetLastError());
+    uint32_t nonfinite = 0;
+    REG_CUDA(cudaMemcpyAsync(&nonfinite, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
     ds->class_count.resize(K);
     REG_CUDA(cudaMemcpyAsync(ds->class_count.data(), ctot, sizeof(int64_t) * K,
                              cudaMemcpyDeviceToHost, stream));
     REG_CUDA(cudaStreamSynchronize(stream));
     cleanup();
 #undef REG_CUDA
+    ds->finite = nonfinite == 0;
     std::lock_guard<std::mutex> lk(ctx->mu);
     const uint64_t h = ctx->next_ds++;
     ctx->datasets[h] = ds;

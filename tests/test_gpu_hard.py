@@ -73,8 +73,14 @@ def test_every_tile_config_identical(ctx, orc):
         assert_same(got, want)
 
 
+# one configuration of each evaluator form: condition-at-a-time, rule-at-a-time with predicate
+# conjunction, with the margin minimum, and the sign-mask form for finite data
+FORMS = [0, 9, 12, 17]
+
+
+@pytest.mark.parametrize("tile", FORMS)
 @pytest.mark.parametrize("seed", range(4))
-def test_boundary_crowded_inputs(ctx, orc, seed):
+def test_boundary_crowded_inputs(ctx, orc, seed, tile):
     rng = np.random.default_rng(seed)
     F = int(rng.integers(1, 9))
     X0 = rng.standard_normal((4096, F)).astype(np.float32)
@@ -82,6 +88,9 @@ def test_boundary_crowded_inputs(ctx, orc, seed):
                               pair_prob=0.5 if F > 1 else 0.0)
     X = synth.boundary_samples(b, F, 2500, seed, frac=0.9, ulps=2)
     y = rng.integers(0, 3, len(X)).astype(np.int32)
+    got = run_gpu(ctx, X, y, 3, b, preds=False, tile=tile)
+    want = orc.eval_hard(X, y, 3, b)
+    assert_same(got, want, preds=False)
     got = run_gpu(ctx, X, y, 3, b)
     want = orc.eval_hard(X, y, 3, b, want_preds=True)
     assert_same(got, want)
@@ -93,7 +102,8 @@ def special_values(rng, n):
     return pool[rng.integers(0, len(pool), n)]
 
 
-def test_special_values_in_data_and_coefficients(ctx, orc):
+@pytest.mark.parametrize("tile", FORMS)
+def test_special_values_in_data_and_coefficients(ctx, orc, tile):
     rng = np.random.default_rng(11)
     N, F = 1500, 4
     X = rng.standard_normal((N, F)).astype(np.float32)
@@ -105,12 +115,30 @@ def test_special_values_in_data_and_coefficients(ctx, orc):
         m = rng.random(len(arr)) < 0.25
         arr[m] = special_values(rng, int(m.sum()))
     y = rng.integers(0, 2, N).astype(np.int32)
-    got = run_gpu(ctx, X, y, 2, b)
+    got = run_gpu(ctx, X, y, 2, b, tile=tile)
     want = orc.eval_hard(X, y, 2, b, want_preds=True)
     assert_same(got, want)
 
 
-def test_subnormal_products(ctx, orc):
+@pytest.mark.parametrize("tile", FORMS)
+def test_special_coefficients_finite_data(ctx, orc, tile):
+    """Finite data (the sign-mask form applies) with zero, infinite, NaN and extreme
+    coefficients and thresholds."""
+    rng = np.random.default_rng(12)
+    N, F = 2000, 5
+    X = (rng.standard_normal((N, F)) * rng.choice([1e-39, 1.0, 1e30], (N, F))).astype(np.float32)
+    b = synth.random_rulesets(synth.quantile_table(X), 3, 40, (1, 6), (1, 4), 12, pair_prob=0.3)
+    for arr in (b.cond_a, b.cond_b, b.cond_t):
+        m = rng.random(len(arr)) < 0.3
+        arr[m] = special_values(rng, int(m.sum()))
+    y = rng.integers(0, 3, N).astype(np.int32)
+    got = run_gpu(ctx, X, y, 3, b, preds=False, tile=tile)
+    want = orc.eval_hard(X, y, 3, b)
+    assert_same(got, want, preds=False)
+
+
+@pytest.mark.parametrize("tile", FORMS)
+def test_subnormal_products(ctx, orc, tile):
     """Products that land in the subnormal range must not be flushed to zero."""
     rng = np.random.default_rng(3)
     N = 2000
@@ -121,24 +149,29 @@ def test_subnormal_products(ctx, orc):
         rules.append((1, [(1, 0, synth.LT, 3e-21, 2e-19, 0.0)]))
     b = synth.from_lists([rules[i:i + 2] for i in range(0, len(rules), 2)], [0] * (len(rules) // 2))
     y = rng.integers(0, 2, N).astype(np.int32)
-    got = run_gpu(ctx, X, y, 2, b)
+    got = run_gpu(ctx, X, y, 2, b, tile=tile)
     want = orc.eval_hard(X, y, 2, b, want_preds=True)
     assert_same(got, want)
 
 
+@pytest.mark.parametrize("tile", FORMS)
 @pytest.mark.parametrize("N,F,K", [(1, 1, 2), (31, 3, 2), (33, 5, 3), (257, 256, 2), (700, 300, 4),
                                    (129, 7, 40)])
-def test_shapes(ctx, orc, N, F, K):
+def test_shapes(ctx, orc, N, F, K, tile):
     rng = np.random.default_rng(N + F)
     X = rng.standard_normal((N, F)).astype(np.float32)
     y = rng.integers(0, K, N).astype(np.int32)
     b = synth.random_rulesets(synth.quantile_table(X), K, 17, (1, 9), (1, 5), N, pair_prob=0.3 if F > 1 else 0)
+    got = run_gpu(ctx, X, y, K, b, preds=False, tile=tile)
+    want = orc.eval_hard(X, y, K, b)
+    assert_same(got, want, preds=False)
     got = run_gpu(ctx, X, y, K, b)
     want = orc.eval_hard(X, y, K, b, want_preds=True)
     assert_same(got, want)
 
 
-def test_empty_sets_rules_and_degenerate_cases(ctx, orc):
+@pytest.mark.parametrize("tile", FORMS)
+def test_empty_sets_rules_and_degenerate_cases(ctx, orc, tile):
     X, y = synth.two_class_gaussian(999, 4, 2)
     sets = [
         [],                                                    # empty set -> default
@@ -150,7 +183,7 @@ def test_empty_sets_rules_and_degenerate_cases(ctx, orc):
         [(1, [(2, 2, synth.LT, 1.0, 1.0, 0.0)])],              # same feature both sides
     ]
     b = synth.from_lists(sets, [0, 1, 0, 1, 0, 1, 0])
-    got = run_gpu(ctx, X, y, 2, b)
+    got = run_gpu(ctx, X, y, 2, b, tile=tile)
     want = orc.eval_hard(X, y, 2, b, want_preds=True)
     assert_same(got, want)
 
