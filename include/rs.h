@@ -229,8 +229,9 @@ typedef struct {
     int32_t tune_top;         /* the best tune_top sets are fine-tuned */
     int32_t tune_steps;       /* full-batch Adam steps per fine-tuning (lr, 0.9, 0.999, 1e-8) */
     float tau, lr;            /* sigmoid temperature, Adam learning rate */
-    int32_t lamarckian;       /* 0: the tuned fitness ranks the individual, its genome is kept
-                                 (Baldwin effect, Sec. 3); 1: tuned coefficients are written back */
+    int32_t lamarckian;       /* 0: the tuned fitness (the better of before / after tuning)
+                                 ranks the individual, its genome is kept (Baldwin effect, Sec. 3);
+                                 1: tuned coefficients that improved it are written back */
     uint64_t seed;
 } rs_evolve_config;
 

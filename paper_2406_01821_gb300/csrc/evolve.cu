@@ -1,7 +1,8 @@
 // Device-resident evolution of a population of rule sets (tournament selection, uniform rule-list
 // crossover, one mutation with randomized coefficients; Sec. 3), with periodic back-propagation
 // fine-tuning of the best sets (Adam on a, b, t through the soft adjoint) used Baldwin-style: the
-// tuned fitness ranks the individual, its genome is kept unless write-back is requested.
+// tuned fitness (the better of before and after tuning) ranks the individual, its genome is kept
+// unless write-back of improved coefficients is requested.
 //
 // The population lives in fixed slots on the device: rule r of set p at [p*RMAX + r], condition k
 // at [(p*RMAX + r)*CMAX + k]. Per generation: slots -> CSR (two scans) -> packed hard evaluation
@@ -386,19 +387,29 @@ __global__ void k_adam(float *a, float *b, float *t, const int32_t *g_is_pair_sr
     }
 }
 
-__global__ void k_scatter_fit(const int32_t *tuned, const int32_t *subset, int n, int32_t *fit)
+// Fine-tuning refines fitness and never lowers it: a tuned set keeps the better of its fitness
+// before and after tuning; `improved` marks the sets whose tuned coefficients did better.
+__global__ void k_scatter_fit(const int32_t *tuned, const int32_t *subset, int n, int32_t *fit,
+                              int32_t *improved)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) fit[subset[i]] = tuned[i];
+    if (i >= n) return;
+    const int s = subset[i];
+    improved[i] = tuned[i] > fit[s];
+    fit[s] = max(fit[s], tuned[i]);
 }
 
+// Write-back of improved tuned coefficients into the genome (one warp per tuned set).
 __global__ void k_write_back(const float *a, const float *b, const float *t, const int32_t *slot,
-                             const int32_t *dC, PopDev p)
+                             const int32_t *first_cond, const int32_t *improved, int n, PopDev p)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= *dC) return;
-    const int q = slot[c];
-    p.ca[q] = a[c]; p.cb[q] = b[c]; p.ct[q] = t[c];
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n || !improved[i]) return;
+    for (int c = first_cond[i] + lane; c < first_cond[i + 1]; c += 32) {
+        const int q = slot[c];
+        p.ca[q] = a[c]; p.cb[q] = b[c]; p.ct[q] = t[c];
+    }
 }
 
 __global__ void k_stats(const int32_t *fit, int P, int32_t *best, double *mean, int gen)
@@ -513,12 +524,13 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
         (rc = B.get(&w.sub_rule_len, P)) || (rc = B.get(&w.sub_cond_len, P)) ||
         (rc = B.get(&w.first_rule, P + 1)) || (rc = B.get(&w.first_cond, P + 1)))
         return rc;
-    int32_t *fit = nullptr, *order = nullptr, *best = nullptr, *tuned_fit = nullptr;
+    int32_t *fit = nullptr, *order = nullptr, *best = nullptr, *tuned_fit = nullptr, *improved = nullptr;
     double *mean = nullptr;
     Scratch sc;
     const int G = cfg->generations;
     if ((rc = B.get(&fit, P)) || (rc = B.get(&order, P)) || (rc = B.get(&best, G + 1)) ||
-        (rc = B.get(&mean, G + 1)) || (rc = B.get(&tuned_fit, P)) || (rc = B.get(&sc.recs, C)) ||
+        (rc = B.get(&mean, G + 1)) || (rc = B.get(&tuned_fit, P)) || (rc = B.get(&improved, P)) ||
+        (rc = B.get(&sc.recs, C)) ||
         (rc = B.get(&sc.sets, P)) || (rc = B.get(&sc.order, P)) || (rc = B.get(&sc.status, 64)))
         return rc;
     // tuning buffers (a, b, t copies, grads, Adam moments, per-set loss / dloss)
@@ -587,9 +599,10 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
             RS_CUDA(cudaMemcpyAsync(w.o.cond_b, tb, 4 * TC, cudaMemcpyDeviceToDevice, s));
             RS_CUDA(cudaMemcpyAsync(w.o.cond_t, tt, 4 * TC, cudaMemcpyDeviceToDevice, s));
             if ((rc = evaluate(T, tuned_fit))) return rc;
-            k_scatter_fit<<<(T + 255) / 256, 256, 0, s>>>(tuned_fit, order, T, fit);
+            k_scatter_fit<<<(T + 255) / 256, 256, 0, s>>>(tuned_fit, order, T, fit, improved);
             if (cfg->lamarckian)
-                k_write_back<<<(int)((TC + 255) / 256), 256, 0, s>>>(ta, tb, tt, w.o.cond_slot, w.first_cond + T, in);
+                k_write_back<<<(T * 32 + 255) / 256, 256, 0, s>>>(ta, tb, tt, w.o.cond_slot, w.first_cond,
+                                                                improved, T, in);
             count_launch(ctx, 2 + (cfg->lamarckian ? 1 : 0));
         }
         k_stats<<<1, 1024, 0, s>>>(fit, P, best, mean, g);
