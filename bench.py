@@ -261,6 +261,157 @@ def soft_leg(args, dev):
             "what": "forward + adjoint (loss and gradients w.r.t. a, b, t of every condition)"}
 
 
+def evolution_leg(args, dev):
+    """Device-resident evolution: population 10,000 (R <= 32, C <= 6), 200 generations on
+    N=100,000 x F=32 two-class data, the best 64 fine-tuned (50 Adam steps) every 10 generations.
+    Compared with two plain arms per generation: the CPU oracle (evaluation + evolution on the host
+    cores) and host-driven evolution with one GPU evaluation launch per generation."""
+    import torch
+    import oracle
+    from paper_2406_01821_gb300 import rs, synth
+    X, y = synth.evolution_data(seed=0)
+    P, RMAX, CMAX, G = 10000, 32, 6, 200
+    pop = synth.initial_population(X, y, 2, P, RMAX, CMAX, seed=0)
+    ctx = rs.Context(dev)
+    ds = ctx.dataset(X, y, 2)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.evolve(ds, pop, generations=2, elite=100, seed=1, stream=stream)          # warm-up
+    t0 = time.perf_counter()
+    _, fit, best, mean = ctx.evolve(ds, pop, generations=G, elite=100, seed=1, tune_every=10,
+                                    tune_top=64, tune_steps=50, tau=0.1, lr=1e-2, stream=stream)
+    t_tuned = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.evolve(ds, pop, generations=G, elite=100, seed=1, stream=stream)
+    t_plain_gpu = time.perf_counter() - t0
+    # host-driven arm: one evaluation launch per generation, evolution on the host
+    hb_gens = 3
+    t0 = time.perf_counter()
+    cur = pop
+    for g in range(hb_gens):
+        b = synth.batch_from_population(cur)
+        c, _, _ = ctx.eval_hard(ds, rs.HostBatch(b), 2, per_class=False)
+        cur = oracle.evolve_step(cur, c, 1, g, 100, X, 2)
+    t_host = (time.perf_counter() - t0) / hb_gens
+    # CPU arm: the oracle evaluates and evolves (one generation, all host cores)
+    t0 = time.perf_counter()
+    c, _, _ = oracle.eval_hard(X, y, 2, synth.batch_from_population(pop), want_per_class=False)
+    oracle.evolve_step(pop, c, 1, 0, 100, X, 2)
+    t_cpu = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": f"evolution P={P} R<=32 C<=6 N={len(X)} F=32 K=2 generations={G} "
+                        "tune top-64 x 50 Adam steps every 10",
+            "generations_per_s": G / t_tuned, "seconds": t_tuned,
+            "generations_per_s_without_tuning": G / t_plain_gpu,
+            "best_first_last": [int(best[0]), int(best[-1])], "mean_last": float(mean[-1]),
+            "plain_host_driven_gpu_generations_per_s": 1.0 / t_host,
+            "plain_cpu_oracle_generations_per_s": 1.0 / t_cpu,
+            "cpu_cores": oracle.num_threads(0)}
+
+
+def serving_leg(args, dev):
+    """Continuous batching of fitness requests from 256 concurrent evolution runs (each with its own
+    resident dataset: N log-uniform [500, 500000], F ~ U{8..256}, K ~ U{2..10}); request
+    populations P log-uniform [16, 2048], R ~ U{1..64}, C ~ U{1..8}; Poisson arrivals at 0.7 of the
+    measured capacity of the plain one-request-per-launch evaluator; 40 GB budget. Latency =
+    completion - arrival, for the served path and for the plain evaluator (FIFO, one launch per
+    request) on the same GPU."""
+    import queue
+    import torch
+    from paper_2406_01821_gb300 import rs, synth
+    runs_N, runs_F, runs_K = synth.serving_runs(seed=0, runs=256)
+    ctx = rs.Context(dev, mem_budget_bytes=40 << 30)
+    dss, qtabs = [], []
+    for i in range(len(runs_N)):
+        X, y = synth.gaussian_mixture(int(runs_N[i]), int(runs_F[i]), int(runs_K[i]), 1000 + i)
+        dss.append(ctx.dataset(X, y, int(runs_K[i])))
+        qtabs.append(synth.quantile_table(X, m=4096))
+        del X, y
+    M = args.serve_requests
+    rng = np.random.default_rng(7)
+    Ps = synth.serving_request_sizes(seed=0, count=M)
+    reqs = []
+    for j in range(M):
+        i = int(rng.integers(0, len(runs_N)))
+        b = synth.random_rulesets(qtabs[i], int(runs_K[i]), int(Ps[j]), (1, 64), (1, 8), 5000 + j)
+        reqs.append((i, rs.HostBatch(b), b.nominal_conditions() * int(runs_N[i])))
+    # plain capacity: mean service time of one-launch evaluation, back to back
+    for j in range(8):
+        i, hb, _ = reqs[j]
+        ctx.eval_hard(dss[i], hb, int(runs_K[i]))
+    t0 = time.perf_counter()
+    for j in range(min(M, 64)):
+        i, hb, _ = reqs[j]
+        ctx.eval_hard(dss[i], hb, int(runs_K[i]))
+    service = (time.perf_counter() - t0) / min(M, 64)
+    rate = 0.7 / service
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=M))
+
+    def drive(submit, finish_all):
+        t_start = time.perf_counter() + 0.05
+        for j in range(M):
+            wait = t_start + arrivals[j] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            submit(j, t_start + arrivals[j])
+        return finish_all(), t_start
+
+    # plain: FIFO worker, one rs_eval_hard launch per request
+    q = queue.Queue()
+    lat_plain = [0.0] * M
+
+    def worker():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            j, t_arr = item
+            i, hb, _ = reqs[j]
+            ctx.eval_hard(dss[i], hb, int(runs_K[i]))
+            lat_plain[j] = time.perf_counter() - t_arr
+    th = threading.Thread(target=worker)
+    th.start()
+
+    def fin_plain():
+        q.put(None)
+        th.join()
+        return time.perf_counter()
+    t_end, t_start = drive(lambda j, ta: q.put((j, ta)), fin_plain)
+    dur_plain = t_end - t_start
+    # served: rs_submit at arrival, completion times from the library's ticket info
+    tickets = [0] * M
+    t_arr_ns = [0] * M
+
+    def submit(j, ta):
+        i, hb, _ = reqs[j]
+        tickets[j] = ctx.submit(dss[i], hb)
+        t_arr_ns[j] = time.monotonic_ns() - int((time.perf_counter() - ta) * 1e9)
+
+    lat_srv = [0.0] * M
+
+    def fin_served():
+        last = 0
+        for j in range(M):
+            i, hb, _ = reqs[j]
+            out = ctx.poll(tickets[j], hb.P, int(runs_K[i]), timeout_us=120_000_000)
+            lat_srv[j] = (out[2]["done_ns"] - t_arr_ns[j]) / 1e9
+            last = max(last, out[2]["done_ns"])
+        return time.perf_counter()
+    t_end, t_start = drive(submit, fin_served)
+    dur_srv = t_end - t_start
+    stats = ctx.serving_stats()
+    ctx.close()
+    total = float(sum(r[2] for r in reqs))
+
+    def summ(lat, dur):
+        a = np.array(lat) * 1e3
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "mean_ms": float(a.mean()), "requests_per_s": M / dur, "condition_evals_per_s": total / dur}
+    return {"workload": f"serving {M} requests from 256 runs, Poisson arrivals at 0.7 x plain capacity, "
+                        "40 GB budget",
+            "served": summ(lat_srv, dur_srv), "plain_one_launch_per_request": summ(lat_plain, dur_plain),
+            "plain_service_ms": service * 1e3, "persistent_kernel_launches": stats["kernel_launches"]}
+
+
 # ----------------------------------------------------------------------------- distributed
 
 class Dist:
@@ -341,6 +492,8 @@ def main():
                     help="ragged-small (N=2^19, P=512) is the case used for ncu captures")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="force a tile configuration id")
+    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving)")
+    ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     d = Dist()
@@ -377,10 +530,13 @@ def main():
     traffic = profiled_traffic()
     extras = {}
     if not args.no_extras and d.rank == 0:
-        try:
-            extras["soft"] = soft_leg(args, dev)
-        except Exception as e:     # an extra leg never hides the headline number
-            extras["soft"] = {"error": repr(e)}
+        for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("serving", serving_leg)):
+            if name in args.skip:
+                continue
+            try:
+                extras[name] = leg(args, dev)
+            except Exception as e:     # an extra leg never hides the headline number
+                extras[name] = {"error": repr(e)}
 
     if d.rank == 0:
         cb = cpu_baseline(w, args.cpu_sample)

@@ -203,6 +203,47 @@ rs_status rs_eval_soft_bwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, floa
 rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,
                               int32_t *per_class, int32_t *preds, void *stream);
 
+/* ------------------------------------------------------------------------------- serving */
+
+#define RS_KIND_HARD 0
+
+/*
+ * Continuous batching of fitness-evaluation requests (hard evaluation). rs_submit copies the batch
+ * (host or device arrays per batch->mem) into pinned staging -- the caller may free it on return --
+ * and queues the request. Requests are admitted in arrival order while the context's memory budget
+ * (rs_config.mem_budget_bytes) and the request slots allow; admitted requests share one persistent
+ * kernel: each 64-sample tile of a request's dataset is a work unit, and units of requests admitted
+ * while others run interleave with theirs on the device. Results equal rs_eval_hard's exactly.
+ *   kind    RS_KIND_HARD (the only kind served)
+ *   errors  RS_ERR_TOO_LARGE if the request alone exceeds the budget; RS_ERR_UNSUPPORTED for
+ *           datasets with more than 256 features; RS_ERR_NOT_FOUND (ds)
+ * Thread-safe. *ticket receives a non-zero id.
+ */
+rs_status rs_submit(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t kind, uint64_t *ticket);
+
+typedef struct {
+    int64_t submit_ns, admit_ns, done_ns;   /* host steady-clock times of the request */
+} rs_ticket_info;
+
+/*
+ * Wait up to timeout_us (0 = do not wait) for a request. Returns RS_PENDING while it runs; on
+ * completion writes correct (host int32[P]) and per_class (host int32[P*K], may be NULL) and the
+ * request's times (info, may be NULL), releases the ticket and returns its status (RS_OK,
+ * RS_ERR_INVALID for a malformed batch, RS_ERR_CANCELLED).
+ */
+rs_status rs_poll(rs_ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct,
+                  int32_t *per_class, rs_ticket_info *info);
+/* Cancel a request that has not been admitted yet (RS_ERR_INVALID once it runs). */
+rs_status rs_cancel(rs_ctx *ctx, uint64_t ticket);
+
+typedef struct {
+    int64_t queued, active;          /* requests waiting for admission / admitted */
+    uint64_t device_bytes_in_use;    /* charged against the budget */
+    uint64_t units_published;        /* work units published since start */
+    int64_t kernel_launches;         /* persistent-kernel launches since start */
+} rs_serving_stats;
+rs_status rs_serving_stats_read(rs_ctx *ctx, rs_serving_stats *out);
+
 /* ------------------------------------------------------------------------------ evolution */
 
 /*

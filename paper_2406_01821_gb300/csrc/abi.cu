@@ -21,6 +21,11 @@ rs_status selftest_rewrite(const float *a_h, const float *t_h, const int8_t *op_
 void load_tune_table(Ctx *ctx);
 void server_shutdown(Ctx *ctx);
 rs_status profile_read(Ctx *ctx, rs_profile *out, int reset);
+rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint64_t *ticket);
+rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, int32_t *per_class,
+               rs_ticket_info *info);
+rs_status cancel(Ctx *ctx, uint64_t ticket);
+rs_status server_stats(Ctx *ctx, rs_serving_stats *out);
 rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_population *hp,
                      int32_t *best_out, double *mean_out, cudaStream_t s);
 rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, float *pb, float *pt,
@@ -228,6 +233,39 @@ rs_status rs_finetune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float *a,
     RS_GUARD({
         if (!ctx) return RS_ERR_INVALID;
         return finetune_run(ctx, ds, batch, a, b, t, tau, lr, steps, loss_trace, S(stream));
+    })
+}
+
+rs_status rs_submit(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t kind, uint64_t *ticket)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return submit(ctx, ds, batch, kind, ticket);
+    })
+}
+
+rs_status rs_poll(rs_ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct,
+                  int32_t *per_class, rs_ticket_info *info)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return poll(ctx, ticket, timeout_us, correct, per_class, info);
+    })
+}
+
+rs_status rs_cancel(rs_ctx *ctx, uint64_t ticket)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return cancel(ctx, ticket);
+    })
+}
+
+rs_status rs_serving_stats_read(rs_ctx *ctx, rs_serving_stats *out)
+{
+    RS_GUARD({
+        if (!ctx || !out) return RS_ERR_INVALID;
+        return server_stats(ctx, out);
     })
 }
 

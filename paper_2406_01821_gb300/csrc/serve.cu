@@ -1,6 +1,618 @@
-// Serving: continuous batching of fitness-evaluation requests (filled in below).
+// Serving: continuous batching of fitness-evaluation requests from many concurrent evolution runs.
+//
+// rs_submit copies a request's population into pinned host staging and queues it. A scheduler
+// thread admits queued requests in arrival order while the memory budget and the request slots
+// allow, uploads and packs each one on its own stream, writes its descriptor into a device table
+// and publishes its work units (one per 64-sample tile of its dataset) into a device ring. One
+// persistent kernel, kept alive while work arrives, lets each CTA claim units from the ring: load
+// the tile of that request's dataset into shared memory, evaluate all of the request's sets on it
+// and add exact counts. The CTA that finishes a request's last unit raises the request's flag in
+// mapped host memory; the scheduler then copies the counts back and frees the slot and its memory.
+// Requests that arrive while others run are admitted as soon as budget and slots allow and their
+// units interleave with the running ones on the device.
+//
+// Waits are bounded: an idle persistent kernel exits after a short idle limit (the scheduler
+// relaunches it when work is published), and every host wait has a timeout.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+#include "eval_core.cuh"
 #include "rs_internal.cuh"
 
 namespace rs {
-void server_shutdown(Ctx *ctx) { (void)ctx; }
+
+namespace {
+
+constexpr int SV = 2;                 // samples per lane
+constexpr int SW = 8;                 // warps per CTA
+constexpr int SS = 32 * SV;           // samples per tile (unit)
+constexpr int SERVE_MAX_F = 256;      // shared x tile [F][64]: 64 KB
+constexpr int MAX_SLOTS = 2048;
+constexpr uint32_t QCAP = 1u << 23;   // unit ring entries
+constexpr uint64_t IDLE_NS = 20000000ull;   // persistent kernel idle limit: 20 ms
+
+struct __align__(16) ReqDesc {
+    const float *Xt;
+    const int32_t *y;
+    int64_t N, n_pad;
+    int32_t F, K;
+    const uint4 *recs;
+    const SetInfo *sets;
+    const int32_t *order;
+    int32_t P, tiles;
+    int32_t *correct, *per_class;
+    uint64_t epoch;
+};
+
+struct ServeArgs {
+    const ReqDesc *table;
+    const int2 *ring;                       // (slot, tile)
+    unsigned long long *head;               // device: next unit to claim
+    const volatile unsigned long long *tail;  // device: units published
+    int32_t *done;                          // [MAX_SLOTS] units finished per slot
+    volatile unsigned long long *host_flag; // mapped host memory [MAX_SLOTS]: finished epoch
+    const volatile int32_t *stop;           // mapped host memory
+};
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(SW * 32) k_serve(ServeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *xs = reinterpret_cast<float *>(smem);                                   // [256][SS]
+    uint4 *stage_all = reinterpret_cast<uint4 *>(smem + SERVE_MAX_F * SS * sizeof(float));
+    __shared__ long long s_unit;
+    __shared__ int s_next;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *st = stage_all + warp * 64;
+
+    while (true) {
+        if (threadIdx.x == 0) {
+            long long unit = -1;
+            uint64_t idle0 = 0;
+            while (true) {
+                if (*a.stop) break;
+                const unsigned long long h = *reinterpret_cast<volatile unsigned long long *>(a.head);
+                const unsigned long long t = *a.tail;
+                if (h < t) {
+                    if (atomicCAS(a.head, h, h + 1) == h) { unit = (long long)h; break; }
+                    continue;
+                }
+                const uint64_t tn = now_ns();
+                if (idle0 == 0) idle0 = tn;
+                else if (tn - idle0 > IDLE_NS) break;
+                __nanosleep(2000);
+            }
+            s_unit = unit;
+            s_next = 0;
+        }
+        __syncthreads();
+        const long long unit = s_unit;
+        if (unit < 0) return;
+        __threadfence();
+        // Ring entries, descriptors and per-request buffers are reused while this kernel lives:
+        // read them through L2 (.cg), never from a possibly stale L1 line.
+        const int2 u = __ldcg(a.ring + unit % QCAP);
+        ReqDesc d;
+        {
+            const int4 *src = reinterpret_cast<const int4 *>(a.table + u.x);
+            int4 *dst = reinterpret_cast<int4 *>(&d);
+#pragma unroll
+            for (int i = 0; i < (int)(sizeof(ReqDesc) / 16); ++i) dst[i] = __ldcg(src + i);
+        }
+        // stage the tile x[0..F)[tile*SS .. +SS) (n_pad is a multiple of 256)
+        const int64_t col0 = (int64_t)u.y * SS;
+        const int nvec = d.F * (SS / 4);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+            const int f = i / (SS / 4), c4 = i % (SS / 4);
+            reinterpret_cast<float4 *>(xs)[i] =
+                *reinterpret_cast<const float4 *>(d.Xt + (int64_t)f * d.n_pad + col0 + 4 * c4);
+        }
+        const int64_t n0 = col0 + lane * SV;
+        int y[SV];
+        bool valid[SV];
+#pragma unroll
+        for (int v = 0; v < SV; ++v) {
+            y[v] = d.y[n0 + v];
+            valid[v] = y[v] >= 0;
+        }
+        const int64_t t_last = min(col0 + SS, d.N) - 1;
+        const int kmin = d.y[col0], kmax = d.y[t_last];
+        __syncthreads();
+        const float *xl = xs + lane * SV;
+        while (true) {
+            int m = 0;
+            if (lane == 0) m = atomicAdd(&s_next, 1);
+            m = __shfl_sync(core::FULL, m, 0);
+            if (m >= d.P) break;
+            const int p = __ldcg(d.order + m);
+            SetInfo si;
+            {
+                const int4 t = __ldcg(reinterpret_cast<const int4 *>(d.sets + p));
+                si.rec_begin = t.x; si.rec_end = t.y; si.deflt = t.z; si.cost = t.w;
+            }
+            int pred[SV];
+            core::eval_set<SV>(d.recs, si.rec_begin, si.rec_end, st, xl, lane, si.deflt, valid, pred);
+            int hits = 0;
+            bool hit[SV];
+#pragma unroll
+            for (int v = 0; v < SV; ++v) {
+                hit[v] = pred[v] == y[v];
+                hits += __popc(__ballot_sync(core::FULL, hit[v]));
+            }
+            if (lane == 0 && hits) atomicAdd(&d.correct[p], hits);
+            if (d.per_class) {
+                if (kmin == kmax) {
+                    if (lane == 0 && hits) atomicAdd(&d.per_class[(int64_t)p * d.K + kmin], hits);
+                } else {
+                    for (int k = kmin; k <= kmax; ++k) {
+                        int c = 0;
+#pragma unroll
+                        for (int v = 0; v < SV; ++v) c += __popc(__ballot_sync(core::FULL, hit[v] && y[v] == k));
+                        if (lane == 0 && c) atomicAdd(&d.per_class[(int64_t)p * d.K + k], c);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const int fin = atomicAdd(&a.done[u.x], 1) + 1;
+            if (fin == d.tiles) {
+                __threadfence_system();
+                a.host_flag[u.x] = d.epoch;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_publish(int2 *ring, unsigned long long base, int slot, int units)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < units) ring[(base + i) % QCAP] = make_int2(slot, i);
+}
+
+__global__ void k_set_tail(unsigned long long *tail, unsigned long long v)
+{
+    __threadfence();
+    *reinterpret_cast<volatile unsigned long long *>(tail) = v;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ host side
+
+struct Request {
+    uint64_t ticket = 0;
+    std::shared_ptr<Dataset> ds;
+    int32_t P = 0, R = 0, C = 0, K = 0;
+    int32_t kind = 0;
+    void *h_stage = nullptr;              // pinned copy of the batch arrays
+    size_t stage_bytes = 0;
+    size_t off[10] = {};
+    size_t device_bytes = 0;
+    void *d_buf = nullptr;
+    int slot = -1;
+    int state = 0;                        // 0 queued, 1 preparing, 2 running, 3 copying, 4 done
+    rs_status status = RS_OK;
+    cudaEvent_t ev = nullptr;
+    int32_t *h_correct = nullptr, *h_pc = nullptr;   // pinned results
+    int32_t *d_correct = nullptr, *d_pc = nullptr;
+    uint32_t *d_status = nullptr;
+    uint32_t *h_status = nullptr;
+    std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
+};
+
+struct Server {
+    Ctx *ctx = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queued;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
+    std::vector<std::shared_ptr<Request>> active;
+    std::thread thread;
+    bool quit = false;
+    uint64_t next_ticket = 1;
+    size_t used = 0;
+    std::vector<int> free_slots;
+    cudaStream_t sstream = nullptr, kstream = nullptr;
+    cudaEvent_t kevent = nullptr;
+    bool kernel_live = false;
+    ReqDesc *d_table = nullptr;
+    int2 *d_ring = nullptr;
+    unsigned long long *d_head = nullptr, *d_tail = nullptr;
+    int32_t *d_done = nullptr;
+    unsigned long long *h_flag = nullptr;
+    int32_t *h_stop = nullptr;
+    unsigned long long published = 0, retired = 0;
+    rs_status fatal = RS_OK;
+    int grid = 0;
+    size_t smem = 0;
+    int64_t launches = 0;
+};
+
+static rs_status server_start(Ctx *ctx, Server **out);
+static void server_loop(Server *s);
+
+static rs_status server_get(Ctx *ctx, Server **out)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->server) {
+        rs_status rc = server_start(ctx, &ctx->server);
+        if (rc) return rc;
+    }
+    *out = ctx->server;
+    return RS_OK;
+}
+
+static rs_status server_start(Ctx *ctx, Server **out)
+{
+    auto *s = new Server();
+    s->ctx = ctx;
+    auto fail = [&](cudaError_t e, const char *w) {
+        rs_status rc = cuda_fail(e, w);
+        delete s;
+        return rc;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&s->sstream, cudaStreamNonBlocking))) return fail(e, "stream");
+    if ((e = cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking))) return fail(e, "stream");
+    if ((e = cudaEventCreateWithFlags(&s->kevent, cudaEventDisableTiming))) return fail(e, "event");
+    if ((e = cudaMalloc(&s->d_table, sizeof(ReqDesc) * MAX_SLOTS))) return fail(e, "table");
+    if ((e = cudaMalloc(&s->d_ring, sizeof(int2) * QCAP))) return fail(e, "ring");
+    if ((e = cudaMalloc(&s->d_head, 2 * sizeof(unsigned long long)))) return fail(e, "head");
+    s->d_tail = s->d_head + 1;
+    if ((e = cudaMemset(s->d_head, 0, 2 * sizeof(unsigned long long)))) return fail(e, "head");
+    if ((e = cudaMalloc(&s->d_done, sizeof(int32_t) * MAX_SLOTS))) return fail(e, "done");
+    if ((e = cudaHostAlloc(&s->h_flag, sizeof(unsigned long long) * MAX_SLOTS, cudaHostAllocMapped))) return fail(e, "flags");
+    if ((e = cudaHostAlloc(&s->h_stop, sizeof(int32_t), cudaHostAllocMapped))) return fail(e, "stop");
+    memset(s->h_flag, 0, sizeof(unsigned long long) * MAX_SLOTS);
+    *s->h_stop = 0;
+    for (int i = MAX_SLOTS - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->smem = SERVE_MAX_F * SS * sizeof(float) + SW * 64 * sizeof(uint4);
+    if ((e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem)))
+        return fail(e, "k_serve attribute");
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, SW * 32, s->smem);
+    // leave room on every SM for the packing and publishing kernels of new requests
+    s->grid = ctx->sm_count * std::max(1, per_sm - 1 > 0 ? per_sm - 1 : 1);
+    s->thread = std::thread(server_loop, s);
+    *out = s;
+    return RS_OK;
+}
+
+void server_shutdown(Ctx *ctx)
+{
+    Server *s = ctx->server;
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->quit = true;
+    }
+    s->cv_work.notify_all();
+    if (s->thread.joinable()) s->thread.join();
+    *(volatile int32_t *)s->h_stop = 1;
+    cudaStreamSynchronize(s->kstream);
+    cudaStreamSynchronize(s->sstream);
+    for (auto &kv : s->all) {
+        Request &r = *kv.second;
+        if (r.h_stage) cudaFreeHost(r.h_stage);
+        if (r.h_correct) cudaFreeHost(r.h_correct);
+        if (r.d_buf) cudaFree(r.d_buf);
+        if (r.ev) cudaEventDestroy(r.ev);
+    }
+    cudaFree(s->d_table);
+    cudaFree(s->d_ring);
+    cudaFree(s->d_head);
+    cudaFree(s->d_done);
+    cudaFreeHost(s->h_flag);
+    cudaFreeHost(s->h_stop);
+    cudaEventDestroy(s->kevent);
+    cudaStreamDestroy(s->sstream);
+    cudaStreamDestroy(s->kstream);
+    delete s;
+    ctx->server = nullptr;
+}
+
+static size_t request_device_bytes(int64_t P, int64_t R, int64_t C, int64_t K)
+{
+    size_t b = 0;
+    b += align256(4 * (P + 1)) + align256(4 * (R + 1)) + align256(4 * R) + align256(4 * P);
+    b += 3 * align256(4 * C) + align256(C) + 3 * align256(4 * C);       // condition arrays
+    b += align256(16 * std::max<int64_t>(C, 1)) + align256(16 * std::max<int64_t>(P, 1)) +
+         align256(4 * std::max<int64_t>(P, 1));                          // records, sets, order
+    b += align256(4 * P) + align256(4 * P * K) + 256;                   // outputs, status
+    return b;
+}
+
+rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint64_t *ticket)
+{
+    if (!b || !ticket) { set_error("NULL batch or ticket"); return RS_ERR_INVALID; }
+    if (kind != 0) { set_error("only hard evaluation requests are served"); return RS_ERR_UNSUPPORTED; }
+    if (b->P < 0 || b->R < 0 || b->C < 0 || (b->mem != RS_MEM_HOST && b->mem != RS_MEM_DEVICE)) {
+        set_error("bad batch");
+        return RS_ERR_INVALID;
+    }
+    auto ds = find_dataset(ctx, ds_h);
+    if (!ds) { set_error("unknown dataset"); return RS_ERR_NOT_FOUND; }
+    if (ds->F > SERVE_MAX_F) { set_error("served datasets have at most %d features", SERVE_MAX_F); return RS_ERR_UNSUPPORTED; }
+    rs_status rc = device_guard(ctx);
+    if (rc) return rc;
+    Server *s = nullptr;
+    if ((rc = server_get(ctx, &s))) return rc;
+    auto r = std::make_shared<Request>();
+    r->ds = ds;
+    r->P = b->P; r->R = b->R; r->C = b->C; r->K = ds->K; r->kind = kind;
+    r->device_bytes = request_device_bytes(b->P, b->R, b->C, ds->K);
+    if (r->device_bytes > ctx->budget) {
+        set_error("request needs %zu bytes of device memory; the budget is %llu", r->device_bytes,
+                  (unsigned long long)ctx->budget);
+        return RS_ERR_TOO_LARGE;
+    }
+    const int64_t units = (ds->N + SS - 1) / SS;
+    if (units > (int64_t)QCAP / 2) { set_error("dataset too large to serve"); return RS_ERR_TOO_LARGE; }
+    // copy the batch into pinned staging: the caller may free its arrays on return
+    const size_t P = b->P, R = b->R, C = b->C;
+    const size_t sz[10] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C};
+    const void *src[10] = {b->set_rule_off, b->rule_cond_off, b->rule_class, b->set_default,
+                           b->cond_f, b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t};
+    size_t tot = 0;
+    for (int i = 0; i < 10; ++i) { r->off[i] = tot; tot = align256(tot + sz[i]); }
+    r->stage_bytes = tot;
+    RS_CUDA(cudaHostAlloc(&r->h_stage, std::max<size_t>(tot, 256), cudaHostAllocDefault));
+    for (int i = 0; i < 10; ++i) {
+        if (!sz[i]) continue;
+        if (!src[i]) { cudaFreeHost(r->h_stage); set_error("NULL batch array"); return RS_ERR_INVALID; }
+        if (b->mem == RS_MEM_HOST) memcpy((char *)r->h_stage + r->off[i], src[i], sz[i]);
+        else RS_CUDA(cudaMemcpy((char *)r->h_stage + r->off[i], src[i], sz[i], cudaMemcpyDeviceToHost));
+    }
+    RS_CUDA(cudaHostAlloc(&r->h_correct, align256(4 * std::max<size_t>(P, 1)) + 4 * std::max<size_t>(P * r->K, 1) + 256,
+                          cudaHostAllocDefault));
+    r->h_pc = (int32_t *)((char *)r->h_correct + align256(4 * std::max<size_t>(P, 1)));
+    r->h_status = (uint32_t *)((char *)r->h_pc + 4 * std::max<size_t>(P * r->K, 1));
+    *r->h_status = 0;
+    RS_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+    r->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->fatal) { set_error("serving stopped after a device error"); return s->fatal; }
+        r->ticket = s->next_ticket++;
+        s->queued.push_back(r);
+        s->all[r->ticket] = r;
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_all();
+    return RS_OK;
+}
+
+// Scheduler-thread helpers (called with s->mu held) ------------------------------------------
+
+static bool try_admit(Server *s, Request &r)
+{
+    const int64_t units = (r.ds->N + SS - 1) / SS;
+    if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget ||
+        (s->published - s->retired) + (unsigned long long)units > QCAP / 2)
+        return false;
+    char *base = nullptr;
+    if (cudaMallocAsync(&base, r.device_bytes, s->sstream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;                      // retry later, when memory is back
+    }
+    r.d_buf = base;
+    r.slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    s->used += r.device_bytes;
+    r.t_admit = std::chrono::steady_clock::now();
+    // batch arrays
+    for (int i = 0; i < 10; ++i)
+        cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
+                        (i + 1 < 10 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
+                        s->sstream);
+    char *p = base + r.stage_bytes;
+    BatchDev bd{};
+    bd.P = r.P; bd.R = r.R; bd.C = r.C;
+    bd.set_rule_off = (int32_t *)(base + r.off[0]); bd.rule_cond_off = (int32_t *)(base + r.off[1]);
+    bd.rule_class = (int32_t *)(base + r.off[2]); bd.set_default = (int32_t *)(base + r.off[3]);
+    bd.cond_f = (int32_t *)(base + r.off[4]); bd.cond_g = (int32_t *)(base + r.off[5]);
+    bd.cond_op = (int8_t *)(base + r.off[6]); bd.cond_a = (float *)(base + r.off[7]);
+    bd.cond_b = (float *)(base + r.off[8]); bd.cond_t = (float *)(base + r.off[9]);
+    PackOut po;
+    po.recs = (Rec *)p; p += align256(16 * std::max(r.C, 1));
+    po.sets = (SetInfo *)p; p += align256(16 * std::max(r.P, 1));
+    po.order = (int32_t *)p; p += align256(4 * std::max(r.P, 1));
+    r.d_correct = (int32_t *)p; p += align256(4 * r.P);
+    r.d_pc = (int32_t *)p; p += align256(4 * (size_t)r.P * r.K);
+    r.d_status = (uint32_t *)p;
+    po.status = r.d_status;
+    cudaMemsetAsync(r.d_status, 0, 4, s->sstream);
+    if (r.P > 0) {
+        cudaMemsetAsync(r.d_correct, 0, 4 * (size_t)r.P, s->sstream);
+        cudaMemsetAsync(r.d_pc, 0, 4 * (size_t)r.P * r.K, s->sstream);
+    }
+    count_launch(s->ctx, launch_pack(bd, r.ds->F, r.K, SS, 2, po, s->sstream));
+    ReqDesc d{};
+    d.Xt = r.ds->Xt; d.y = r.ds->y; d.N = r.ds->N; d.n_pad = r.ds->n_pad; d.F = r.ds->F; d.K = r.K;
+    d.recs = reinterpret_cast<const uint4 *>(po.recs); d.sets = po.sets; d.order = po.order;
+    d.P = r.P; d.tiles = (int32_t)units; d.correct = r.d_correct; d.per_class = r.d_pc;
+    d.epoch = r.ticket;
+    // a copy from pageable memory is staged before the call returns, so `d` may go out of scope
+    cudaMemcpyAsync(&s->d_table[r.slot], &d, sizeof(d), cudaMemcpyHostToDevice, s->sstream);
+    cudaMemsetAsync(&s->d_done[r.slot], 0, 4, s->sstream);
+    if (units > 0 && r.P > 0) {
+        k_publish<<<(unsigned)((units + 255) / 256), 256, 0, s->sstream>>>(s->d_ring, s->published, r.slot, (int)units);
+        s->published += units;
+        k_set_tail<<<1, 1, 0, s->sstream>>>(s->d_tail, s->published);
+        count_launch(s->ctx, 2);
+    }
+    cudaEventRecord(r.ev, s->sstream);
+    r.state = (units > 0 && r.P > 0) ? 2 : 3;
+    if (r.state == 3) {        // nothing to evaluate: results are the zeros just written
+        cudaMemcpyAsync(r.h_correct, r.d_correct, 4 * (size_t)r.P, cudaMemcpyDeviceToHost, s->sstream);
+        cudaMemcpyAsync(r.h_status, r.d_status, 4, cudaMemcpyDeviceToHost, s->sstream);
+        cudaEventRecord(r.ev, s->sstream);
+    }
+    return true;
+}
+
+static void server_loop(Server *s)
+{
+    cudaSetDevice(s->ctx->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        if (s->quit && s->queued.empty() && s->active.empty()) break;
+        bool progress = false;
+        // admit in arrival order
+        while (!s->queued.empty()) {
+            auto r = s->queued.front();
+            if (r->state >= 4) { s->queued.pop_front(); continue; }   // cancelled
+            if (!try_admit(s, *r)) break;
+            s->queued.pop_front();
+            s->active.push_back(r);
+            progress = true;
+        }
+        // (re)launch the persistent kernel when units wait and it is not running
+        bool pending_units = false;
+        for (auto &r : s->active) pending_units |= r->state == 2;
+        if (pending_units && s->kernel_live) {
+            if (cudaEventQuery(s->kevent) == cudaSuccess) s->kernel_live = false;
+            else cudaGetLastError();
+        }
+        if (pending_units && !s->kernel_live) {
+            // the descriptors and ring entries must be in place before the kernel starts
+            cudaStreamWaitEvent(s->kstream, s->active.back()->ev, 0);
+            ServeArgs a{s->d_table, s->d_ring, s->d_head, s->d_tail, s->d_done,
+                        (volatile unsigned long long *)s->h_flag, (volatile int32_t *)s->h_stop};
+            k_serve<<<s->grid, SW * 32, s->smem, s->kstream>>>(a);
+            cudaEventRecord(s->kevent, s->kstream);
+            count_launch(s->ctx);
+            ++s->launches;
+            s->kernel_live = true;
+            progress = true;
+        }
+        // completions
+        for (auto &r : s->active) {
+            if (r->state == 2 && ((volatile unsigned long long *)s->h_flag)[r->slot] == r->ticket) {
+                cudaMemcpyAsync(r->h_correct, r->d_correct, 4 * (size_t)r->P, cudaMemcpyDeviceToHost, s->sstream);
+                cudaMemcpyAsync(r->h_pc, r->d_pc, 4 * (size_t)r->P * r->K, cudaMemcpyDeviceToHost, s->sstream);
+                cudaMemcpyAsync(r->h_status, r->d_status, 4, cudaMemcpyDeviceToHost, s->sstream);
+                cudaEventRecord(r->ev, s->sstream);
+                s->retired += (r->ds->N + SS - 1) / SS;
+                r->state = 3;
+                progress = true;
+            }
+            if (r->state == 3) {
+                cudaError_t q = cudaEventQuery(r->ev);
+                if (q == cudaSuccess) {
+                    r->t_done = std::chrono::steady_clock::now();
+                    r->status = *r->h_status ? RS_ERR_INVALID : RS_OK;
+                    cudaFreeAsync(r->d_buf, s->sstream);
+                    r->d_buf = nullptr;
+                    s->used -= r->device_bytes;
+                    s->free_slots.push_back(r->slot);
+                    r->state = 4;
+                    progress = true;
+                } else if (q != cudaErrorNotReady) {
+                    s->fatal = cuda_fail(q, "serving");
+                    r->status = s->fatal;
+                    r->state = 4;
+                }
+            }
+        }
+        s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
+                                       [](const std::shared_ptr<Request> &r) { return r->state == 4; }),
+                        s->active.end());
+        if (progress) s->cv_done.notify_all();
+        if (!progress) {
+            if (s->active.empty() && s->queued.empty()) {
+                if (s->quit) break;
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            } else {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                lk.lock();
+            }
+        }
+    }
+}
+
+rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, int32_t *per_class,
+               rs_ticket_info *info)
+{
+    Server *s = ctx->server;
+    if (!s) { set_error("no request was submitted"); return RS_ERR_NOT_FOUND; }
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return RS_ERR_NOT_FOUND; }
+    auto r = it->second;
+    auto done = [&] { return r->state >= 4; };
+    if (!done()) {
+        if (timeout_us <= 0) return RS_PENDING;
+        if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done)) return RS_PENDING;
+    }
+    if (info) {
+        info->submit_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(r->t_submit.time_since_epoch()).count();
+        info->admit_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(r->t_admit.time_since_epoch()).count();
+        info->done_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(r->t_done.time_since_epoch()).count();
+    }
+    rs_status rc = r->status;
+    if (rc == RS_OK) {
+        if (correct) memcpy(correct, r->h_correct, 4 * (size_t)r->P);
+        if (per_class) memcpy(per_class, r->h_pc, 4 * (size_t)r->P * r->K);
+    } else if (rc == RS_ERR_CANCELLED) {
+        set_error("request cancelled");
+    } else {
+        set_error("request rejected by the device checks (malformed batch)");
+    }
+    // results are released at the first successful poll
+    if (r->h_stage) cudaFreeHost(r->h_stage);
+    if (r->h_correct) cudaFreeHost(r->h_correct);
+    if (r->ev) cudaEventDestroy(r->ev);
+    r->h_stage = nullptr; r->h_correct = nullptr; r->ev = nullptr;
+    s->all.erase(it);
+    return rc;
+}
+
+rs_status cancel(Ctx *ctx, uint64_t ticket)
+{
+    Server *s = ctx->server;
+    if (!s) return RS_ERR_NOT_FOUND;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return RS_ERR_NOT_FOUND;
+    Request &r = *it->second;
+    if (r.state != 0) { set_error("request already admitted"); return RS_ERR_INVALID; }
+    r.status = RS_ERR_CANCELLED;
+    r.t_done = std::chrono::steady_clock::now();
+    r.state = 4;
+    s->cv_done.notify_all();
+    return RS_OK;
+}
+
+rs_status server_stats(Ctx *ctx, rs_serving_stats *out)
+{
+    Server *s = ctx->server;
+    memset(out, 0, sizeof(*out));
+    if (!s) return RS_OK;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->queued = (int64_t)s->queued.size();
+    out->active = (int64_t)s->active.size();
+    out->device_bytes_in_use = s->used;
+    out->units_published = s->published;
+    out->kernel_launches = s->launches;
+    return RS_OK;
+}
+
 }  // namespace rs

@@ -53,6 +53,16 @@ class rs_population(ctypes.Structure):
                                                "ca", "cb", "ct", "fitness")]
 
 
+class rs_ticket_info(ctypes.Structure):
+    _fields_ = [("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+class rs_serving_stats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("device_bytes_in_use", ctypes.c_uint64), ("units_published", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
 class rs_evolve_config(ctypes.Structure):
     _fields_ = [("P", ctypes.c_int32), ("RMAX", ctypes.c_int32), ("CMAX", ctypes.c_int32),
                 ("generations", ctypes.c_int32), ("elite", ctypes.c_int32),
@@ -91,6 +101,12 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "rs_profile_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rs_profile), ctypes.c_int32]),
+    "rs_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
+                                   ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
+    "rs_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.POINTER(rs_ticket_info)]),
+    "rs_cancel": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rs_serving_stats_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rs_serving_stats)]),
     "rs_evolve": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_evolve_config),
                                    ctypes.POINTER(rs_population), ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
@@ -325,6 +341,33 @@ class Context:
         p = rs_profile()
         check(lib().rs_profile_read(self.h, ctypes.byref(p), int(reset)))
         return {f: getattr(p, f) for f, _ in rs_profile._fields_}
+
+    # serving
+    def submit(self, ds: int, batch) -> int:
+        """Queue a hard-evaluation request (HostBatch or DeviceBatch); returns its ticket."""
+        t = ctypes.c_uint64()
+        cb = batch.c()
+        check(lib().rs_submit(self.h, ds, ctypes.byref(cb), 0, ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, P: int, K: int, timeout_us: int = 0):
+        """Returns None while pending, else (correct[P], per_class[P,K], info dict)."""
+        c = np.zeros(P, np.int32)
+        pc = np.zeros((P, K), np.int32)
+        info = rs_ticket_info()
+        rc = lib().rs_poll(self.h, ticket, int(timeout_us), _ptr(c), _ptr(pc), ctypes.byref(info))
+        if rc == PENDING:
+            return None
+        check(rc)
+        return c, pc, {"submit_ns": info.submit_ns, "admit_ns": info.admit_ns, "done_ns": info.done_ns}
+
+    def cancel(self, ticket: int) -> int:
+        return lib().rs_cancel(self.h, ticket)
+
+    def serving_stats(self) -> dict:
+        st = rs_serving_stats()
+        check(lib().rs_serving_stats_read(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in rs_serving_stats._fields_}
 
     def evolve(self, ds: int, pop: dict, generations: int, elite: int, seed: int, tune_every=0,
                tune_top=0, tune_steps=0, tau=0.1, lr=1e-2, lamarckian=False, stream=None):

@@ -1,0 +1,121 @@
+"""Serving (continuous batching): every result of a request served in a mix of concurrent requests
+of uneven sizes over several resident datasets equals the result of the same request evaluated
+alone with rs_eval_hard (exact integer counts); budget admission, rejection and cancellation."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2406_01821_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def make_runs(seed, n_runs=5):
+    rng = np.random.default_rng(seed)
+    runs = []
+    for i in range(n_runs):
+        N = int(rng.integers(500, 40000))
+        F = int(rng.integers(8, 257))
+        K = int(rng.integers(2, 11))
+        X, y = synth.gaussian_mixture(N, F, K, seed * 100 + i)
+        runs.append((X, y, K, synth.quantile_table(X)))
+    return runs
+
+
+def test_mix_equals_alone(orc):
+    import torch
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    ctx = rs.Context(0, mem_budget_bytes=1 << 30)
+    try:
+        runs = make_runs(1)
+        dss = [ctx.dataset(X, y, K) for (X, y, K, _) in runs]
+        rng = np.random.default_rng(2)
+        reqs = []
+        for j in range(24):
+            i = int(rng.integers(0, len(runs)))
+            X, y, K, q = runs[i]
+            P = int(np.exp(rng.uniform(np.log(16), np.log(300))))
+            b = synth.random_rulesets(q, K, P, (1, 64), (1, 8), 1000 + j)
+            reqs.append((i, b))
+        # alone
+        alone = []
+        for i, b in reqs:
+            c, pc, _ = ctx.eval_hard(dss[i], rs.HostBatch(b), runs[i][2])
+            alone.append((c.copy(), pc.copy()))
+        # mixed: submitted from several threads, polled in any order
+        tickets = [None] * len(reqs)
+
+        def submitter(idx):
+            for j in idx:
+                i, b = reqs[j]
+                tickets[j] = ctx.submit(dss[i], rs.HostBatch(b) if j % 2 else rs.DeviceBatch.from_host(b))
+        th = [threading.Thread(target=submitter, args=(list(range(k, len(reqs), 4)),)) for k in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for j in reversed(range(len(reqs))):
+            i, b = reqs[j]
+            out = ctx.poll(tickets[j], b.P, runs[i][2], timeout_us=60_000_000)
+            assert out is not None, "request did not finish"
+            assert np.array_equal(out[0], alone[j][0]), j
+            assert np.array_equal(out[1], alone[j][1]), j
+            assert out[2]["submit_ns"] <= out[2]["admit_ns"] <= out[2]["done_ns"]
+        # spot-check one against the oracle
+        i, b = reqs[0]
+        X, y, K, _ = runs[i]
+        want = orc.eval_hard(X, y, K, b)
+        assert np.array_equal(alone[0][0], want[0])
+        st = ctx.serving_stats()
+        assert st["active"] == 0 and st["queued"] == 0 and st["device_bytes_in_use"] == 0
+        assert st["kernel_launches"] >= 1
+    finally:
+        ctx.close()
+
+
+def test_budget_admission_and_errors():
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    X, y = synth.gaussian_mixture(20000, 32, 3, 5)
+    q = synth.quantile_table(X)
+    big = synth.random_rulesets(q, 3, 2000, (60, 64), (8, 8), 5)          # ~1M conditions
+    small = [synth.random_rulesets(q, 3, 40, (1, 10), (1, 4), 6 + j) for j in range(6)]
+    # a budget that holds one small request at a time (and not the big one)
+    ctx = rs.Context(0, mem_budget_bytes=4 << 20)
+    try:
+        ds = ctx.dataset(X, y, 3)
+        with pytest.raises(rs.RsError) as ei:
+            ctx.submit(ds, rs.HostBatch(big))
+        assert ei.value.code == -2
+        ts = [ctx.submit(ds, rs.HostBatch(b)) for b in small]
+        for t, b in zip(ts, small):
+            out = ctx.poll(t, b.P, 3, timeout_us=60_000_000)
+            c, _, _ = ctx.eval_hard(ds, rs.HostBatch(b), 3)
+            assert np.array_equal(out[0], c)
+        bad = synth.random_rulesets(q, 3, 5, 2, 2, 9)
+        bad.cond_f[0] = 99
+        t = ctx.submit(ds, rs.HostBatch(bad))
+        with pytest.raises(rs.RsError) as ei:
+            ctx.poll(t, bad.P, 3, timeout_us=60_000_000)
+        assert ei.value.code == -1
+        # cancellation of a request still waiting for admission
+        ctx2 = rs.Context(0, mem_budget_bytes=(12 << 20))
+        try:
+            ds2 = ctx2.dataset(X, y, 3)
+            mid = synth.random_rulesets(q, 3, 600, (40, 64), (6, 8), 11)
+            t1 = ctx2.submit(ds2, rs.HostBatch(mid))
+            t2 = ctx2.submit(ds2, rs.HostBatch(mid))
+            rc = ctx2.cancel(t2)
+            if rc == 0:
+                with pytest.raises(rs.RsError) as ei:
+                    ctx2.poll(t2, mid.P, 3, timeout_us=60_000_000)
+                assert ei.value.code == -8
+            else:
+                assert ctx2.poll(t2, mid.P, 3, timeout_us=60_000_000) is not None
+            assert ctx2.poll(t1, mid.P, 3, timeout_us=60_000_000) is not None
+        finally:
+            ctx2.close()
+    finally:
+        ctx.close()
