@@ -121,7 +121,7 @@ rs_status rs_dataset_info(rs_ctx *ctx, uint64_t ds, int64_t *N, int32_t *F, int3
  *   cond_g        int32[C]    -1: threshold condition a*x[f] op t; else 0..F-1: a*x[f] op b*x[g]
  *   cond_op       int8[C]     0: '>', 1: '<'
  *   cond_a, cond_b, cond_t  float32[C]   (b unused for thresholds, t unused for pairs)
- * P >= 0, R >= 0, C >= 0; P, R, C < 2^31 - 1.
+ * P >= 0, R >= 0, C >= 0; P, R, C < 2^31 - 1; a rule has at most 4095 conditions.
  */
 typedef struct {
     int32_t P, R, C;

@@ -90,7 +90,7 @@ __device__ void eval_set(const uint4 *recs, int rb, int re, uint4 *st, const flo
         }
         const uint4 *rp = st + (rel - 32 * ck);
         const uint4 r0 = rp[0];
-        const int nc = (int)((r0.x >> LEN_SHIFT) & 0xFFFu);
+        const int nc = max(1, (int)((r0.x >> LEN_SHIFT) & 0xFFFu));   // >= 1: progress
         const int cls = (int)(r0.y >> CLS_SHIFT);
         float mn[V];
 #pragma unroll

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(W * 32) k_hard4(const __grid_constant__ CUtens
             }
             const uint4 *rp = st + (rel - 32 * ck);
             const uint4 r0 = rp[0];
-            const int nc = (int)((r0.x >> LEN_SHIFT) & 0xFFFu);
+            const int nc = max(1, (int)((r0.x >> LEN_SHIFT) & 0xFFFu));   // >= 1: progress
             const int cls = (int)(r0.y >> CLS_SHIFT);
             uint32_t acc[V];
 #pragma unroll

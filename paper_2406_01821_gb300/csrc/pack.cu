@@ -158,7 +158,8 @@ __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
     bool ok = true;
     for (int r = rb; r < re; ++r) {
         const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
-        if (c0 < 0 || c1 < c0 || c1 > b.C || c1 - c0 > 0xFFFF) { ok = false; break; }
+        if (c0 < 0 || c1 < c0 || c1 > b.C) { ok = false; break; }
+        if (c1 - c0 > 0xFFF) { atomicOr(status, ST_TOO_LARGE); ok = false; break; }
         if (r == rb) { c_begin = c0; c_end = c0; }
         const int cls = b.rule_class[r];
         if (cls < 0 || cls >= K) { atomicOr(status, ST_BAD_CLASS); ok = false; break; }
@@ -183,7 +184,7 @@ __global__ void k_pack_rules(BatchDev b, int F, int K, Rec *recs, uint32_t *stat
     if (r >= b.R) return;
     const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
     if (c0 < 0 || c1 < c0 || c1 > b.C) { atomicOr(status, ST_BAD_OFFSETS); return; }
-    if (c1 - c0 > 0xFFFF) { atomicOr(status, ST_TOO_LARGE); return; }   // skip field is 16 bits
+    if (c1 - c0 > 0xFFF) { atomicOr(status, ST_TOO_LARGE); return; }    // rule length is 12 bits
     int cls = b.rule_class[r];
     if (cls < 0 || cls >= K) { atomicOr(status, ST_BAD_CLASS); cls = 0; }
     for (int c = c0; c < c1; ++c) {
