@@ -88,9 +88,10 @@ static std::string tune_key(const Dataset &ds, const rs_batch *b)
 
 static int heuristic_tile(const Dataset &ds)
 {
-    // 128-sample tiles with 8 warps when the feature tile fits three CTAs per SM; smaller tiles
-    // for wide data.
-    static const int prefs[] = {0, 3, 5};
+    // The sign-mask evaluator with 128-sample tiles and 32 warps (fastest measured on the ragged
+    // workload; it runs as the margin-minimum form on non-finite data), then smaller tiles for
+    // wide data.
+    static const int prefs[] = {18, 16, 20, 3, 5};
     for (int id : prefs)
         if (tile_config_fits(tile_config(id), ds.F)) return id;
     return 5;
