@@ -13,6 +13,7 @@
 // rules of class k (and the default, if it is k) can add hits, decided once per rule for the whole
 // warp. Predictions are not produced here (the caller then uses the general evaluator).
 #include "rs_internal.cuh"
+#include "eval_core.cuh"
 #include "tma.cuh"
 
 namespace rs {
@@ -20,49 +21,7 @@ namespace rs {
 namespace {
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
-constexpr uint32_t SIGN = 0x80000000u;
 constexpr uint64_t TMA_WAIT_LIMIT_NS = 2000000000ull;
-
-template <int V>
-__device__ __forceinline__ void load_x(const float *p, float (&x)[V])
-{
-    if constexpr (V == 2) {
-        float2 t = *reinterpret_cast<const float2 *>(p);
-        x[0] = t.x; x[1] = t.y;
-    } else {
-#pragma unroll
-        for (int k = 0; k < V; k += 4) {
-            float4 t = *reinterpret_cast<const float4 *>(p + k);
-            x[k] = t.x; x[k + 1] = t.y; x[k + 2] = t.z; x[k + 3] = t.w;
-        }
-    }
-}
-
-template <int V>
-__device__ __forceinline__ void cond_mask(const uint4 r, const float *xl, uint32_t (&acc)[V])
-{
-    float x[V];
-    load_x<V>(xl + (r.x & OFF_MASK) * 4, x);
-    const float v0 = __uint_as_float(r.z), v1 = __uint_as_float(r.w);
-    if (!(r.x & (PAIR_BIT | GENERAL_BIT))) {
-        const float2 s2 = make_float2(v0, v0), c2 = make_float2(v1, v1);
-#pragma unroll
-        for (int v = 0; v < V; v += 2) {
-            const float2 m = __ffma2_rn(make_float2(x[v], x[v + 1]), s2, c2);
-            acc[v] |= __float_as_uint(m.x);
-            acc[v + 1] |= __float_as_uint(m.y);
-        }
-    } else if (r.x & PAIR_BIT) {
-        float z[V];
-        load_x<V>(xl + (r.y & OFF_MASK) * 4, z);
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            acc[v] |= (__fmul_rn(v0, x[v]) > __fmul_rn(v1, z[v])) ? 0u : SIGN;
-    } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] |= (__fmul_rn(v0, x[v]) > v1) ? 0u : SIGN;
-    }
-}
 
 template <int V, int W>
 __global__ void __launch_bounds__(W * 32) k_hard4(const __grid_constant__ CUtensorMap tmap, HardArgs a)
@@ -109,7 +68,6 @@ __global__ void __launch_bounds__(W * 32) k_hard4(const __grid_constant__ CUtens
     const int count = (a.P - group + G - 1) / G;
     uint4 *st = stage_all + warp * 64;
     const float *xl = xs + lane * V;
-    const uint4 zero4 = make_uint4(0, 0, 0, 0);
 
     while (true) {
         int m = 0;
@@ -120,80 +78,8 @@ __global__ void __launch_bounds__(W * 32) k_hard4(const __grid_constant__ CUtens
         const SetInfo si = a.sets[p];
         const int rb = si.rec_begin, re = si.rec_end;
 
-        // sign set = claimed (padding samples start claimed and never count)
-        uint32_t claimed[V], hit[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            claimed[v] = y[v] >= 0 ? 0u : SIGN;
-            hit[v] = 0u;
-        }
-        int ck = 0;
-        uint4 pf = zero4;
-        if (rb < re) {
-            __syncwarp();
-            st[lane] = (rb + lane < re) ? __ldg(recs + rb + lane) : zero4;
-            st[32 + lane] = (rb + 32 + lane < re) ? __ldg(recs + rb + 32 + lane) : zero4;
-            pf = (rb + 64 + lane < re) ? __ldg(recs + rb + 64 + lane) : zero4;
-            __syncwarp();
-        }
-        int rel = 0;
-        const int nrec = re - rb;
-        while (rel < nrec) {
-            while ((rel >> 5) > ck) {
-                const uint4 keep = st[32 + lane];
-                __syncwarp();
-                st[lane] = keep;
-                st[32 + lane] = pf;
-                __syncwarp();
-                ++ck;
-                const int nx = rb + 32 * (ck + 2) + lane;
-                pf = (nx < re) ? __ldg(recs + nx) : zero4;
-            }
-            const uint4 *rp = st + (rel - 32 * ck);
-            const uint4 r0 = rp[0];
-            const int nc = max(1, (int)((r0.x >> LEN_SHIFT) & 0xFFFu));   // >= 1: progress
-            const int cls = (int)(r0.y >> CLS_SHIFT);
-            uint32_t acc[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = claimed[v];
-            cond_mask<V>(r0, xl, acc);
-            if (nc <= 33) {
-#pragma unroll 2
-                for (int k = 1; k < nc; ++k) cond_mask<V>(rp[k], xl, acc);
-            } else {
-                for (int k = 1; k < nc; ++k) cond_mask<V>(__ldg(recs + rb + rel + k), xl, acc);
-            }
-            // fired: sign still clear. Claim, and count hits of this rule's class.
-            uint32_t all = SIGN;
-            if (uniform) {
-                const bool mine = cls == kmin;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const uint32_t fired = ~acc[v] & SIGN;
-                    claimed[v] |= fired;
-                    if (mine) hit[v] |= fired;
-                    all &= claimed[v];
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const uint32_t fired = ~acc[v] & SIGN;
-                    claimed[v] |= fired;
-                    hit[v] |= (y[v] == cls) ? fired : 0u;
-                    all &= claimed[v];
-                }
-            }
-            if (__all_sync(FULL, all != 0u)) break;
-            rel += nc;
-        }
-        // the default class takes what is left
-        const int d = si.deflt;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint32_t left = ~claimed[v] & SIGN;
-            hit[v] |= (uniform ? (d == kmin) : (y[v] == d)) ? left : 0u;
-        }
-        __syncwarp();
+        uint32_t hit[V];
+        core::eval_set_sign<V>(recs, rb, re, st, xl, lane, si.deflt, y, uniform, kmin, hit);
         int hits = 0;
 #pragma unroll
         for (int v = 0; v < V; ++v) hits += __popc(__ballot_sync(FULL, hit[v] != 0u));

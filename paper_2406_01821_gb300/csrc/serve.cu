@@ -2,17 +2,19 @@
 //
 // rs_submit copies a request's population into pinned host staging and queues it. A scheduler
 // thread admits queued requests in arrival order while the memory budget and the request slots
-// allow, uploads and packs each one on its own stream, writes its descriptor into a device table
-// and publishes its work units (one per 64-sample tile of its dataset) into a device ring. One
-// persistent kernel, kept alive while work arrives, lets each CTA claim units from the ring: load
-// the tile of that request's dataset into shared memory, evaluate all of the request's sets on it
-// and add exact counts. The CTA that finishes a request's last unit raises the request's flag in
-// mapped host memory; the scheduler then copies the counts back and frees the slot and its memory.
-// Requests that arrive while others run are admitted as soon as budget and slots allow and their
-// units interleave with the running ones on the device.
+// allow, uploads and packs each one, writes its descriptor into a device table and publishes it in
+// the device list of active requests with a claim word (epoch | next unit | units). One persistent
+// kernel, kept alive while work arrives, lets each CTA claim a unit -- a 64-sample tile of the
+// request's dataset times a group of up to 256 of its sets -- from the active requests in
+// round-robin order (processor sharing: a small request does not wait behind a large one), load
+// the tile into shared memory, evaluate those sets on it and add exact counts. The CTA finishing
+// a request's last unit raises the request's flag in mapped host memory; the scheduler then copies
+// the counts back on its own stream and frees the slot and its memory. Requests admitted while
+// others run join the rotation at once, so their work overlaps on the device.
 //
-// Waits are bounded: an idle persistent kernel exits after a short idle limit (the scheduler
-// relaunches it when work is published), and every host wait has a timeout.
+// Claims are compare-and-swap on the 64-bit claim word, so a CTA holding a stale view of the
+// active list can only claim real, unclaimed units. Waits are bounded: an idle persistent kernel
+// exits after a short idle limit (the scheduler relaunches it when work is published).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -33,8 +35,11 @@ constexpr int SW = 8;                 // warps per CTA
 constexpr int SS = 32 * SV;           // samples per tile (unit)
 constexpr int SERVE_MAX_F = 256;      // shared x tile [F][64]: 64 KB
 constexpr int MAX_SLOTS = 2048;
-constexpr uint32_t QCAP = 1u << 23;   // unit ring entries
+constexpr int GROUP_SETS = 256;       // sets per unit
 constexpr uint64_t IDLE_NS = 20000000ull;   // persistent kernel idle limit: 20 ms
+// claim word: epoch (24 bits) | next unit (20 bits) | units (20 bits)
+constexpr int CW_NEXT = 20, CW_EPOCH = 40;
+constexpr unsigned long long CW_MASK = (1ull << 20) - 1;
 
 struct __align__(16) ReqDesc {
     const float *Xt;
@@ -44,16 +49,17 @@ struct __align__(16) ReqDesc {
     const uint4 *recs;
     const SetInfo *sets;
     const int32_t *order;
-    int32_t P, tiles;
+    int32_t P, tiles, groups, finite;
     int32_t *correct, *per_class;
     uint64_t epoch;
 };
 
 struct ServeArgs {
     const ReqDesc *table;
-    const int2 *ring;                       // (slot, tile)
-    unsigned long long *head;               // device: next unit to claim
-    const volatile unsigned long long *tail;  // device: units published
+    unsigned long long *claims;             // [MAX_SLOTS] claim words
+    const volatile int32_t *active;         // [MAX_SLOTS] active slots (a hint; claims decide)
+    const volatile int32_t *nactive;
+    unsigned int *rr;                       // round-robin cursor
     int32_t *done;                          // [MAX_SLOTS] units finished per slot
     volatile unsigned long long *host_flag; // mapped host memory [MAX_SLOTS]: finished epoch
     const volatile int32_t *stop;           // mapped host memory
@@ -71,47 +77,59 @@ __global__ void __launch_bounds__(SW * 32) k_serve(ServeArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     float *xs = reinterpret_cast<float *>(smem);                                   // [256][SS]
     uint4 *stage_all = reinterpret_cast<uint4 *>(smem + SERVE_MAX_F * SS * sizeof(float));
-    __shared__ long long s_unit;
-    __shared__ int s_next;
+    __shared__ int s_slot, s_unit, s_next;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint4 *st = stage_all + warp * 64;
 
     while (true) {
         if (threadIdx.x == 0) {
-            long long unit = -1;
+            int slot = -1, unit = -1;
             uint64_t idle0 = 0;
+            int misses = 0;
             while (true) {
                 if (*a.stop) break;
-                const unsigned long long h = *reinterpret_cast<volatile unsigned long long *>(a.head);
-                const unsigned long long t = *a.tail;
-                if (h < t) {
-                    if (atomicCAS(a.head, h, h + 1) == h) { unit = (long long)h; break; }
-                    continue;
+                const int n = *a.nactive;
+                if (n > 0) {
+                    const int i = (int)(atomicAdd(a.rr, 1u) % (unsigned)n);
+                    const int sl = a.active[i];
+                    if (sl >= 0 && sl < MAX_SLOTS) {
+                        unsigned long long w = *reinterpret_cast<volatile unsigned long long *>(a.claims + sl);
+                        while (((w >> CW_NEXT) & CW_MASK) < (w & CW_MASK)) {
+                            const unsigned long long old = atomicCAS(a.claims + sl, w, w + (1ull << CW_NEXT));
+                            if (old == w) { slot = sl; unit = (int)((w >> CW_NEXT) & CW_MASK); break; }
+                            w = old;
+                        }
+                        if (slot >= 0) break;
+                    }
+                    if (++misses < 2 * n) continue;     // try the other active requests first
                 }
+                misses = 0;
                 const uint64_t tn = now_ns();
                 if (idle0 == 0) idle0 = tn;
                 else if (tn - idle0 > IDLE_NS) break;
                 __nanosleep(2000);
             }
+            s_slot = slot;
             s_unit = unit;
             s_next = 0;
         }
         __syncthreads();
-        const long long unit = s_unit;
-        if (unit < 0) return;
+        const int slot = s_slot, unit = s_unit;
+        if (slot < 0) return;
         __threadfence();
-        // Ring entries, descriptors and per-request buffers are reused while this kernel lives:
-        // read them through L2 (.cg), never from a possibly stale L1 line.
-        const int2 u = __ldcg(a.ring + unit % QCAP);
+        // Descriptors and per-request buffers are reused while this kernel lives: read them
+        // through L2 (.cg), never from a possibly stale L1 line.
         ReqDesc d;
         {
-            const int4 *src = reinterpret_cast<const int4 *>(a.table + u.x);
+            const int4 *src = reinterpret_cast<const int4 *>(a.table + slot);
             int4 *dst = reinterpret_cast<int4 *>(&d);
 #pragma unroll
             for (int i = 0; i < (int)(sizeof(ReqDesc) / 16); ++i) dst[i] = __ldcg(src + i);
         }
+        const int tile = unit / d.groups, grp = unit % d.groups;
+        const int set0 = grp * GROUP_SETS, set1 = min(d.P, set0 + GROUP_SETS);
         // stage the tile x[0..F)[tile*SS .. +SS) (n_pad is a multiple of 256)
-        const int64_t col0 = (int64_t)u.y * SS;
+        const int64_t col0 = (int64_t)tile * SS;
         const int nvec = d.F * (SS / 4);
         for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
             const int f = i / (SS / 4), c4 = i % (SS / 4);
@@ -128,31 +146,39 @@ __global__ void __launch_bounds__(SW * 32) k_serve(ServeArgs a)
         }
         const int64_t t_last = min(col0 + SS, d.N) - 1;
         const int kmin = d.y[col0], kmax = d.y[t_last];
+        const bool uniform = kmin == kmax;
         __syncthreads();
         const float *xl = xs + lane * SV;
         while (true) {
             int m = 0;
             if (lane == 0) m = atomicAdd(&s_next, 1);
             m = __shfl_sync(core::FULL, m, 0);
-            if (m >= d.P) break;
-            const int p = __ldcg(d.order + m);
+            if (set0 + m >= set1) break;
+            const int p = __ldcg(d.order + set0 + m);
             SetInfo si;
             {
                 const int4 t = __ldcg(reinterpret_cast<const int4 *>(d.sets + p));
                 si.rec_begin = t.x; si.rec_end = t.y; si.deflt = t.z; si.cost = t.w;
             }
-            int pred[SV];
-            core::eval_set<SV>(d.recs, si.rec_begin, si.rec_end, st, xl, lane, si.deflt, valid, pred);
-            int hits = 0;
             bool hit[SV];
+            if (d.finite) {
+                uint32_t h[SV];
+                core::eval_set_sign<SV>(d.recs, si.rec_begin, si.rec_end, st, xl, lane, si.deflt, y,
+                                        uniform, kmin, h);
 #pragma unroll
-            for (int v = 0; v < SV; ++v) {
-                hit[v] = pred[v] == y[v];
-                hits += __popc(__ballot_sync(core::FULL, hit[v]));
+                for (int v = 0; v < SV; ++v) hit[v] = h[v] != 0u;
+            } else {
+                int pred[SV];
+                core::eval_set<SV>(d.recs, si.rec_begin, si.rec_end, st, xl, lane, si.deflt, valid, pred);
+#pragma unroll
+                for (int v = 0; v < SV; ++v) hit[v] = pred[v] == y[v];
             }
+            int hits = 0;
+#pragma unroll
+            for (int v = 0; v < SV; ++v) hits += __popc(__ballot_sync(core::FULL, hit[v]));
             if (lane == 0 && hits) atomicAdd(&d.correct[p], hits);
             if (d.per_class) {
-                if (kmin == kmax) {
+                if (uniform) {
                     if (lane == 0 && hits) atomicAdd(&d.per_class[(int64_t)p * d.K + kmin], hits);
                 } else {
                     for (int k = kmin; k <= kmax; ++k) {
@@ -167,26 +193,20 @@ __global__ void __launch_bounds__(SW * 32) k_serve(ServeArgs a)
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            const int fin = atomicAdd(&a.done[u.x], 1) + 1;
-            if (fin == d.tiles) {
+            const int fin = atomicAdd(&a.done[slot], 1) + 1;
+            if (fin == d.tiles * d.groups) {
                 __threadfence_system();
-                a.host_flag[u.x] = d.epoch;
+                a.host_flag[slot] = d.epoch;
             }
         }
         __syncthreads();
     }
 }
 
-__global__ void k_publish(int2 *ring, unsigned long long base, int slot, int units)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < units) ring[(base + i) % QCAP] = make_int2(slot, i);
-}
-
-__global__ void k_set_tail(unsigned long long *tail, unsigned long long v)
+__global__ void k_set_claim(unsigned long long *claims, int slot, unsigned long long word)
 {
     __threadfence();
-    *reinterpret_cast<volatile unsigned long long *>(tail) = v;
+    atomicExch(claims + slot, word);
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -232,12 +252,15 @@ struct Server {
     cudaEvent_t kevent = nullptr;
     bool kernel_live = false;
     ReqDesc *d_table = nullptr;
-    int2 *d_ring = nullptr;
-    unsigned long long *d_head = nullptr, *d_tail = nullptr;
+    unsigned long long *d_claims = nullptr;
+    int32_t *d_active = nullptr;           // [MAX_SLOTS + 1]: list, then its length
+    unsigned int *d_rr = nullptr;
+    std::vector<int32_t> h_active;         // host copy of the active list
+    cudaStream_t cstream = nullptr;        // completion copies
     int32_t *d_done = nullptr;
     unsigned long long *h_flag = nullptr;
     int32_t *h_stop = nullptr;
-    unsigned long long published = 0, retired = 0;
+    unsigned long long published = 0;
     rs_status fatal = RS_OK;
     int grid = 0;
     size_t smem = 0;
@@ -272,10 +295,13 @@ static rs_status server_start(Ctx *ctx, Server **out)
     if ((e = cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking))) return fail(e, "stream");
     if ((e = cudaEventCreateWithFlags(&s->kevent, cudaEventDisableTiming))) return fail(e, "event");
     if ((e = cudaMalloc(&s->d_table, sizeof(ReqDesc) * MAX_SLOTS))) return fail(e, "table");
-    if ((e = cudaMalloc(&s->d_ring, sizeof(int2) * QCAP))) return fail(e, "ring");
-    if ((e = cudaMalloc(&s->d_head, 2 * sizeof(unsigned long long)))) return fail(e, "head");
-    s->d_tail = s->d_head + 1;
-    if ((e = cudaMemset(s->d_head, 0, 2 * sizeof(unsigned long long)))) return fail(e, "head");
+    if ((e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking))) return fail(e, "stream");
+    if ((e = cudaMalloc(&s->d_claims, sizeof(unsigned long long) * MAX_SLOTS))) return fail(e, "claims");
+    if ((e = cudaMemset(s->d_claims, 0, sizeof(unsigned long long) * MAX_SLOTS))) return fail(e, "claims");
+    if ((e = cudaMalloc(&s->d_active, sizeof(int32_t) * (MAX_SLOTS + 1)))) return fail(e, "active");
+    if ((e = cudaMemset(s->d_active, 0, sizeof(int32_t) * (MAX_SLOTS + 1)))) return fail(e, "active");
+    if ((e = cudaMalloc(&s->d_rr, sizeof(unsigned int)))) return fail(e, "rr");
+    if ((e = cudaMemset(s->d_rr, 0, sizeof(unsigned int)))) return fail(e, "rr");
     if ((e = cudaMalloc(&s->d_done, sizeof(int32_t) * MAX_SLOTS))) return fail(e, "done");
     if ((e = cudaHostAlloc(&s->h_flag, sizeof(unsigned long long) * MAX_SLOTS, cudaHostAllocMapped))) return fail(e, "flags");
     if ((e = cudaHostAlloc(&s->h_stop, sizeof(int32_t), cudaHostAllocMapped))) return fail(e, "stop");
@@ -307,6 +333,7 @@ void server_shutdown(Ctx *ctx)
     *(volatile int32_t *)s->h_stop = 1;
     cudaStreamSynchronize(s->kstream);
     cudaStreamSynchronize(s->sstream);
+    cudaStreamSynchronize(s->cstream);
     for (auto &kv : s->all) {
         Request &r = *kv.second;
         if (r.h_stage) cudaFreeHost(r.h_stage);
@@ -315,14 +342,16 @@ void server_shutdown(Ctx *ctx)
         if (r.ev) cudaEventDestroy(r.ev);
     }
     cudaFree(s->d_table);
-    cudaFree(s->d_ring);
-    cudaFree(s->d_head);
+    cudaFree(s->d_claims);
+    cudaFree(s->d_active);
+    cudaFree(s->d_rr);
     cudaFree(s->d_done);
     cudaFreeHost(s->h_flag);
     cudaFreeHost(s->h_stop);
     cudaEventDestroy(s->kevent);
     cudaStreamDestroy(s->sstream);
     cudaStreamDestroy(s->kstream);
+    cudaStreamDestroy(s->cstream);
     delete s;
     ctx->server = nullptr;
 }
@@ -362,8 +391,8 @@ rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint6
                   (unsigned long long)ctx->budget);
         return RS_ERR_TOO_LARGE;
     }
-    const int64_t units = (ds->N + SS - 1) / SS;
-    if (units > (int64_t)QCAP / 2) { set_error("dataset too large to serve"); return RS_ERR_TOO_LARGE; }
+    const int64_t units = ((ds->N + SS - 1) / SS) * std::max<int64_t>(1, (b->P + GROUP_SETS - 1) / GROUP_SETS);
+    if (units > (int64_t)CW_MASK) { set_error("request too large to serve (%lld work units)", (long long)units); return RS_ERR_TOO_LARGE; }
     // copy the batch into pinned staging: the caller may free its arrays on return
     const size_t P = b->P, R = b->R, C = b->C;
     const size_t sz[10] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C};
@@ -400,12 +429,21 @@ rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint6
 
 // Scheduler-thread helpers (called with s->mu held) ------------------------------------------
 
+static void push_active(Server *s)
+{
+    // list, then its length, in one copy (pageable source: staged before the call returns)
+    std::vector<int32_t> buf(s->h_active);
+    buf.resize(MAX_SLOTS + 1, -1);
+    buf[MAX_SLOTS] = (int32_t)s->h_active.size();
+    cudaMemcpyAsync(s->d_active, buf.data(), sizeof(int32_t) * (MAX_SLOTS + 1), cudaMemcpyHostToDevice,
+                    s->sstream);
+}
+
 static bool try_admit(Server *s, Request &r)
 {
-    const int64_t units = (r.ds->N + SS - 1) / SS;
-    if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget ||
-        (s->published - s->retired) + (unsigned long long)units > QCAP / 2)
-        return false;
+    const int64_t tiles = (r.ds->N + SS - 1) / SS;
+    const int64_t groups = std::max<int64_t>(1, (r.P + GROUP_SETS - 1) / GROUP_SETS);
+    if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
     if (cudaMallocAsync(&base, r.device_bytes, s->sstream) != cudaSuccess) {
         cudaGetLastError();
@@ -442,28 +480,33 @@ static bool try_admit(Server *s, Request &r)
         cudaMemsetAsync(r.d_correct, 0, 4 * (size_t)r.P, s->sstream);
         cudaMemsetAsync(r.d_pc, 0, 4 * (size_t)r.P * r.K, s->sstream);
     }
-    count_launch(s->ctx, launch_pack(bd, r.ds->F, r.K, SS, 2, po, s->sstream));
+    const bool finite = r.ds->finite;
+    count_launch(s->ctx, launch_pack(bd, r.ds->F, r.K, SS, finite ? 4 : 2, po, s->sstream));
     ReqDesc d{};
     d.Xt = r.ds->Xt; d.y = r.ds->y; d.N = r.ds->N; d.n_pad = r.ds->n_pad; d.F = r.ds->F; d.K = r.K;
     d.recs = reinterpret_cast<const uint4 *>(po.recs); d.sets = po.sets; d.order = po.order;
-    d.P = r.P; d.tiles = (int32_t)units; d.correct = r.d_correct; d.per_class = r.d_pc;
-    d.epoch = r.ticket;
+    d.P = r.P; d.tiles = (int32_t)tiles; d.groups = (int32_t)groups; d.finite = finite ? 1 : 0;
+    d.correct = r.d_correct; d.per_class = r.d_pc;
+    d.epoch = r.ticket & 0xFFFFFFull;
     // a copy from pageable memory is staged before the call returns, so `d` may go out of scope
     cudaMemcpyAsync(&s->d_table[r.slot], &d, sizeof(d), cudaMemcpyHostToDevice, s->sstream);
     cudaMemsetAsync(&s->d_done[r.slot], 0, 4, s->sstream);
+    const unsigned long long units = (unsigned long long)(tiles * groups);
     if (units > 0 && r.P > 0) {
-        k_publish<<<(unsigned)((units + 255) / 256), 256, 0, s->sstream>>>(s->d_ring, s->published, r.slot, (int)units);
+        // the descriptor is in place before the claim word opens the request to the kernel
+        const unsigned long long word = (d.epoch << CW_EPOCH) | units;
+        k_set_claim<<<1, 1, 0, s->sstream>>>(s->d_claims, r.slot, word);
+        count_launch(s->ctx);
+        s->h_active.push_back(r.slot);
+        push_active(s);
         s->published += units;
-        k_set_tail<<<1, 1, 0, s->sstream>>>(s->d_tail, s->published);
-        count_launch(s->ctx, 2);
-    }
-    cudaEventRecord(r.ev, s->sstream);
-    r.state = (units > 0 && r.P > 0) ? 2 : 3;
-    if (r.state == 3) {        // nothing to evaluate: results are the zeros just written
+        r.state = 2;
+    } else {                   // nothing to evaluate: results are the zeros just written
         cudaMemcpyAsync(r.h_correct, r.d_correct, 4 * (size_t)r.P, cudaMemcpyDeviceToHost, s->sstream);
         cudaMemcpyAsync(r.h_status, r.d_status, 4, cudaMemcpyDeviceToHost, s->sstream);
-        cudaEventRecord(r.ev, s->sstream);
+        r.state = 3;
     }
+    cudaEventRecord(r.ev, s->sstream);
     return true;
 }
 
@@ -493,7 +536,7 @@ static void server_loop(Server *s)
         if (pending_units && !s->kernel_live) {
             // the descriptors and ring entries must be in place before the kernel starts
             cudaStreamWaitEvent(s->kstream, s->active.back()->ev, 0);
-            ServeArgs a{s->d_table, s->d_ring, s->d_head, s->d_tail, s->d_done,
+            ServeArgs a{s->d_table, s->d_claims, s->d_active, s->d_active + MAX_SLOTS, s->d_rr, s->d_done,
                         (volatile unsigned long long *)s->h_flag, (volatile int32_t *)s->h_stop};
             k_serve<<<s->grid, SW * 32, s->smem, s->kstream>>>(a);
             cudaEventRecord(s->kevent, s->kstream);
@@ -504,12 +547,15 @@ static void server_loop(Server *s)
         }
         // completions
         for (auto &r : s->active) {
-            if (r->state == 2 && ((volatile unsigned long long *)s->h_flag)[r->slot] == r->ticket) {
-                cudaMemcpyAsync(r->h_correct, r->d_correct, 4 * (size_t)r->P, cudaMemcpyDeviceToHost, s->sstream);
-                cudaMemcpyAsync(r->h_pc, r->d_pc, 4 * (size_t)r->P * r->K, cudaMemcpyDeviceToHost, s->sstream);
-                cudaMemcpyAsync(r->h_status, r->d_status, 4, cudaMemcpyDeviceToHost, s->sstream);
-                cudaEventRecord(r->ev, s->sstream);
-                s->retired += (r->ds->N + SS - 1) / SS;
+            if (r->state == 2 &&
+                ((volatile unsigned long long *)s->h_flag)[r->slot] == (r->ticket & 0xFFFFFFull)) {
+                cudaMemcpyAsync(r->h_correct, r->d_correct, 4 * (size_t)r->P, cudaMemcpyDeviceToHost, s->cstream);
+                cudaMemcpyAsync(r->h_pc, r->d_pc, 4 * (size_t)r->P * r->K, cudaMemcpyDeviceToHost, s->cstream);
+                cudaMemcpyAsync(r->h_status, r->d_status, 4, cudaMemcpyDeviceToHost, s->cstream);
+                cudaEventRecord(r->ev, s->cstream);
+                s->h_active.erase(std::remove(s->h_active.begin(), s->h_active.end(), r->slot),
+                                  s->h_active.end());
+                push_active(s);
                 r->state = 3;
                 progress = true;
             }
@@ -518,7 +564,7 @@ static void server_loop(Server *s)
                 if (q == cudaSuccess) {
                     r->t_done = std::chrono::steady_clock::now();
                     r->status = *r->h_status ? RS_ERR_INVALID : RS_OK;
-                    cudaFreeAsync(r->d_buf, s->sstream);
+                    cudaFreeAsync(r->d_buf, s->sstream);   // the copies out have completed
                     r->d_buf = nullptr;
                     s->used -= r->device_bytes;
                     s->free_slots.push_back(r->slot);
