@@ -181,7 +181,7 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchD
 {
     PackOut po{s.recs, s.sets, s.order, s.status};
     const int ver = effective_version(tc, *ds, preds != nullptr);
-    count_launch(ctx, launch_pack(bd, ds->F, ds->K, tc.S(), ver == 4 ? 4 : (ver >= 2 ? 2 : 1), po, stream));
+    count_launch(ctx, launch_pack(bd, ds->F, ds->K, tc.S(), ver >= 4 ? 4 : (ver >= 2 ? 2 : 1), po, stream));
     RS_CUDA(cudaGetLastError());
     HardArgs a{};
     a.recs = s.recs;
