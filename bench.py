@@ -398,6 +398,17 @@ def serving_leg(args, dev):
         return time.perf_counter()
     t_end, t_start = drive(submit, fin_served)
     dur_srv = t_end - t_start
+    # capacity: every request at once (served) / back to back (plain)
+    t0 = time.perf_counter()
+    ts = [ctx.submit(dss[i], hb) for (i, hb, _) in reqs]
+    for j, t in enumerate(ts):
+        i, hb, _ = reqs[j]
+        ctx.poll(t, hb.P, int(runs_K[i]), timeout_us=300_000_000)
+    burst_srv = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for (i, hb, _) in reqs:
+        ctx.eval_hard(dss[i], hb, int(runs_K[i]))
+    burst_plain = time.perf_counter() - t0
     stats = ctx.serving_stats()
     ctx.close()
     total = float(sum(r[2] for r in reqs))
@@ -409,7 +420,9 @@ def serving_leg(args, dev):
     return {"workload": f"serving {M} requests from 256 runs, Poisson arrivals at 0.7 x plain capacity, "
                         "40 GB budget",
             "served": summ(lat_srv, dur_srv), "plain_one_launch_per_request": summ(lat_plain, dur_plain),
-            "plain_service_ms": service * 1e3, "persistent_kernel_launches": stats["kernel_launches"]}
+            "plain_service_ms": service * 1e3, "persistent_kernel_launches": stats["kernel_launches"],
+            "capacity_condition_evals_per_s": {"served_all_at_once": total / burst_srv,
+                                               "plain_back_to_back": total / burst_plain}}
 
 
 # ----------------------------------------------------------------------------- distributed

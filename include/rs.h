@@ -212,9 +212,9 @@ rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, i
  * (host or device arrays per batch->mem) into pinned staging -- the caller may free it on return --
  * and queues the request. Requests are admitted in arrival order while the context's memory budget
  * (rs_config.mem_budget_bytes) and the request slots allow; admitted requests share one persistent
- * kernel: each 128-sample tile of a request's dataset times up to 512 of its sets is a work unit, and
- * units of requests admitted
- * while others run interleave with theirs on the device. Results equal rs_eval_hard's exactly.
+ * kernel: a 64-sample tile of a request's dataset times up to 64 of its sets is a work unit, and
+ * CTAs claim units from the active requests in turn, so units of requests admitted while others
+ * run interleave with theirs on the device. Results equal rs_eval_hard's exactly.
  *   kind    RS_KIND_HARD (the only kind served)
  *   errors  RS_ERR_TOO_LARGE if the request alone exceeds the budget; RS_ERR_UNSUPPORTED for
  *           datasets with more than 256 features; RS_ERR_NOT_FOUND (ds)

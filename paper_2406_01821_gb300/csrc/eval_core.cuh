@@ -147,46 +147,14 @@ __device__ __forceinline__ void cond_mask(const uint4 r, const float *xl, uint32
     }
 }
 
-// The same test for V = 4 written out in PTX (one 128-bit shared load, four FMAs, four ORs),
-// for the hot path of the evaluator; `xs_addr` is the shared-memory address of the lane's samples.
-template <int V>
-__device__ __forceinline__ void cond_mask_asm(const uint4 r, const float *xl, uint32_t xs_addr,
-                                              uint32_t (&acc)[V])
-{
-    if constexpr (V == 4) {
-        if (!(r.x & (PAIR_BIT | GENERAL_BIT))) {
-            asm("{\n\t"
-                ".reg .u32 ad;\n\t"
-                ".reg .f32 x0, x1, x2, x3, m0, m1, m2, m3;\n\t"
-                "and.b32 ad, %4, 262143;\n\t"
-                "mad.lo.u32 ad, ad, 16, %5;\n\t"
-                "ld.shared.v4.f32 {x0, x1, x2, x3}, [ad];\n\t"
-                "fma.rn.f32 m0, x0, %6, %7;\n\t"
-                "fma.rn.f32 m1, x1, %6, %7;\n\t"
-                "fma.rn.f32 m2, x2, %6, %7;\n\t"
-                "fma.rn.f32 m3, x3, %6, %7;\n\t"
-                "or.b32 %0, %0, m0;\n\t"
-                "or.b32 %1, %1, m1;\n\t"
-                "or.b32 %2, %2, m2;\n\t"
-                "or.b32 %3, %3, m3;\n\t"
-                "}"
-                : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3])
-                : "r"(r.x), "r"(xs_addr), "f"(__uint_as_float(r.z)), "f"(__uint_as_float(r.w)));
-            return;
-        }
-    }
-    cond_mask<V>(r, xl, acc);
-}
-
 // Evaluate one set (records [rb, re), format v4) on this lane's V samples. hit[v] gets its sign
 // bit set when the sample's prediction equals its label: in a tile of one label (`uniform`, label
 // kmin) only rules of that class count; otherwise the per-sample label y[v] decides. y[v] < 0
 // marks padding. All lanes of the warp call this together.
-template <int V, bool ASM = false>
+template <int V>
 __device__ void eval_set_sign(const uint4 *recs, int rb, int re, uint4 *st, const float *xl, int lane,
                               int deflt, const int (&y)[V], bool uniform, int kmin, uint32_t (&hit)[V])
 {
-    const uint32_t xs_addr = (uint32_t)__cvta_generic_to_shared(xl);
     const uint4 zero4 = make_uint4(0, 0, 0, 0);
     uint32_t claimed[V];
 #pragma unroll
@@ -223,22 +191,12 @@ __device__ void eval_set_sign(const uint4 *recs, int rb, int re, uint4 *st, cons
         uint32_t acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = claimed[v];
-        if constexpr (ASM) {
-            cond_mask_asm<V>(r0, xl, xs_addr, acc);
-            if (nc <= 33) {
+        cond_mask<V>(r0, xl, acc);
+        if (nc <= 33) {
 #pragma unroll 2
-                for (int k = 1; k < nc; ++k) cond_mask_asm<V>(rp[k], xl, xs_addr, acc);
-            } else {
-                for (int k = 1; k < nc; ++k) cond_mask_asm<V>(__ldcg(recs + rb + rel + k), xl, xs_addr, acc);
-            }
+            for (int k = 1; k < nc; ++k) cond_mask<V>(rp[k], xl, acc);
         } else {
-            cond_mask<V>(r0, xl, acc);
-            if (nc <= 33) {
-#pragma unroll 2
-                for (int k = 1; k < nc; ++k) cond_mask<V>(rp[k], xl, acc);
-            } else {
-                for (int k = 1; k < nc; ++k) cond_mask<V>(__ldcg(recs + rb + rel + k), xl, acc);
-            }
+            for (int k = 1; k < nc; ++k) cond_mask<V>(__ldcg(recs + rb + rel + k), xl, acc);
         }
         uint32_t all = SIGN;
         if (uniform) {

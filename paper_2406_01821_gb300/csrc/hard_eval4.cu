@@ -23,7 +23,7 @@ namespace {
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr uint64_t TMA_WAIT_LIMIT_NS = 2000000000ull;
 
-template <int V, int W, bool ASM>
+template <int V, int W>
 __global__ void __launch_bounds__(W * 32) k_hard4(const __grid_constant__ CUtensorMap tmap, HardArgs a)
 {
     constexpr int S = 32 * V;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(W * 32) k_hard4(const __grid_constant__ CUtens
         const int rb = si.rec_begin, re = si.rec_end;
 
         uint32_t hit[V];
-        core::eval_set_sign<V, ASM>(recs, rb, re, st, xl, lane, si.deflt, y, uniform, kmin, hit);
+        core::eval_set_sign<V>(recs, rb, re, st, xl, lane, si.deflt, y, uniform, kmin, hit);
         int hits = 0;
 #pragma unroll
         for (int v = 0; v < V; ++v) hits += __popc(__ballot_sync(FULL, hit[v] != 0u));
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(W * 32) k_hard4(const __grid_constant__ CUtens
 
 }  // namespace
 
-template <int V, int W, bool ASM>
+template <int V, int W>
 rs_status launch4_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t stream)
 {
     const int Fb = a.F < 256 ? a.F : 256;
@@ -111,7 +111,7 @@ rs_status launch4_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t strea
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(k_hard4<V, W, ASM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(k_hard4<V, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)ctx->smem_optin);
     });
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute(k_hard4)");
@@ -121,30 +121,24 @@ rs_status launch4_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t strea
     dim3 grid(tiles, a.groups);
     {
         TimedLaunch tl(ctx, TK_HARD, stream);
-        k_hard4<V, W, ASM><<<grid, W * 32, smem, stream>>>(*tm, a);
+        k_hard4<V, W><<<grid, W * 32, smem, stream>>>(*tm, a);
     }
     RS_CUDA(cudaGetLastError());
     count_launch(ctx);
     return RS_OK;
 }
 
-rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, bool asm_path, const HardArgs &a,
-                       cudaStream_t stream)
+rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream)
 {
     if (a.P > 0) RS_CUDA(cudaMemsetAsync(a.correct, 0, sizeof(int32_t) * a.P, stream));
     if (a.P > 0 && a.per_class)
         RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
-    if (asm_path) {
-        if (V == 4 && W == 8) return launch4_t<4, 8, true>(ctx, ds, a, stream);
-        if (V == 4 && W == 16) return launch4_t<4, 16, true>(ctx, ds, a, stream);
-        if (V == 4 && W == 32) return launch4_t<4, 32, true>(ctx, ds, a, stream);
-    }
-    if (V == 4 && W == 8) return launch4_t<4, 8, false>(ctx, ds, a, stream);
-    if (V == 4 && W == 16) return launch4_t<4, 16, false>(ctx, ds, a, stream);
-    if (V == 4 && W == 32) return launch4_t<4, 32, false>(ctx, ds, a, stream);
-    if (V == 2 && W == 16) return launch4_t<2, 16, false>(ctx, ds, a, stream);
-    if (V == 2 && W == 32) return launch4_t<2, 32, false>(ctx, ds, a, stream);
+    if (V == 4 && W == 8) return launch4_t<4, 8>(ctx, ds, a, stream);
+    if (V == 4 && W == 16) return launch4_t<4, 16>(ctx, ds, a, stream);
+    if (V == 4 && W == 32) return launch4_t<4, 32>(ctx, ds, a, stream);
+    if (V == 2 && W == 16) return launch4_t<2, 16>(ctx, ds, a, stream);
+    if (V == 2 && W == 32) return launch4_t<2, 32>(ctx, ds, a, stream);
     return RS_ERR_INVALID;
 }
 

@@ -117,8 +117,7 @@ struct TileConfig {
     int W;       // warps per CTA
     int ver;     // 1: condition-at-a-time evaluator, 2: rule-at-a-time (record v2),
                  // 3: rule-at-a-time with the margin-minimum conjunction,
-                 // 4: sign-mask conjunction for finite datasets (falls back to 3 otherwise),
-                 // 5: as 4 with the threshold test written in PTX (V = 4)
+                 // 4: sign-mask conjunction for finite datasets (falls back to 3 otherwise)
     int S() const { return 32 * V; }
 };
 int tile_config_count();
@@ -221,8 +220,7 @@ rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArg
 int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P);
 rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, bool mm, const HardArgs &a,
                        cudaStream_t stream);
-rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, bool asm_path, const HardArgs &a,
-                       cudaStream_t stream);
+rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream);
 // The evaluator version a configuration runs as for this dataset and output choice.
 int effective_version(const TileConfig &tc, const Dataset &ds, bool preds);
 // Enqueue packing + evaluation of a device batch with the given scratch.
