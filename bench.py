@@ -233,7 +233,10 @@ def hb_nbytes(hb):
 def soft_leg(args, dev):
     import torch
     from paper_2406_01821_gb300 import rs, synth
-    w = synth.soft_tune(seed=0)
+    if args.workload == "soft-small":
+        w = synth.soft_tune(seed=0, N=65536, P=256)
+    else:
+        w = synth.soft_tune(seed=0)
     ctx = rs.Context(dev, flags=rs.CTX_PROFILE)
     stream = torch.cuda.Stream(device=dev)
     ds = ctx.dataset(w.X, w.y, w.K)
@@ -501,8 +504,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=131072)
-    ap.add_argument("--workload", default="ragged", choices=["ragged", "ragged-small"],
-                    help="ragged-small (N=2^19, P=512) is the case used for ncu captures")
+    ap.add_argument("--workload", default="ragged", choices=["ragged", "ragged-small", "soft-small"],
+                    help="ragged-small (N=2^19, P=512) and soft-small (soft leg only, N=65536, "
+                         "P=256) are the cases used for ncu captures")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="force a tile configuration id")
     ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving)")
@@ -522,6 +526,10 @@ def main():
     d.barrier()
     dev = d.local
     torch.cuda.set_device(dev)
+    if args.workload == "soft-small":
+        print(json.dumps({"soft": soft_leg(args, dev)}), flush=True)
+        d.close()
+        return
     if args.workload == "ragged-small":
         w = synth.ragged_hard(seed=d.rank, N=1 << 19, P=512)
     else:

@@ -212,7 +212,7 @@ rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, i
  * (host or device arrays per batch->mem) into pinned staging -- the caller may free it on return --
  * and queues the request. Requests are admitted in arrival order while the context's memory budget
  * (rs_config.mem_budget_bytes) and the request slots allow; admitted requests share one persistent
- * kernel: a 64-sample tile of a request's dataset times up to 64 of its sets is a work unit, and
+ * kernel: a 128-sample tile of a request's dataset times up to 128 of its sets is a work unit, and
  * CTAs claim units from the active requests in turn, so units of requests admitted while others
  * run interleave with theirs on the device. Results equal rs_eval_hard's exactly.
  *   kind    RS_KIND_HARD (the only kind served)

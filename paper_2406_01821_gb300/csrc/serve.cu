@@ -4,8 +4,8 @@
 // thread admits queued requests in arrival order while the memory budget and the request slots
 // allow, uploads and packs each one, writes its descriptor into a device table and publishes it in
 // the device list of active requests with a claim word (epoch | next unit | units). One persistent
-// kernel, kept alive while work arrives, lets each CTA claim a unit -- a 64-sample tile of the
-// request's dataset times a group of up to 64 of its sets -- from the active requests in
+// kernel, kept alive while work arrives, lets each CTA claim a unit -- a 128-sample tile of the
+// request's dataset times a group of up to 128 of its sets -- from the active requests in
 // round-robin order (processor sharing: a small request does not wait behind a large one), load
 // the tile into shared memory, evaluate those sets on it and add exact counts. The CTA finishing
 // a request's last unit raises the request's flag in mapped host memory; the scheduler then copies
@@ -30,13 +30,14 @@ namespace rs {
 
 namespace {
 
-constexpr int SV = 2;                 // samples per lane
-constexpr int SW = 8;                 // warps per CTA
+constexpr int SV = 4;                 // samples per lane
+constexpr int SW = 16;                // warps per CTA (one CTA per SM; registers and shared
+                                      // memory are left for the packing kernels of new requests)
 constexpr int SS = 32 * SV;           // samples per tile (unit)
-constexpr int SERVE_MAX_F = 256;      // shared x tile [F][64]: 64 KB
+constexpr int SERVE_MAX_F = 256;      // shared x tile [F][128]: 128 KB
 constexpr int MAX_SLOTS = 2048;
-constexpr int GROUP_SETS = 64;        // sets per unit: eight per warp, small units balance well
-constexpr int SPARE_SMS = 4;          // SMs left free for the packing kernels of new requests
+constexpr int GROUP_SETS = 128;       // sets per unit: eight per warp
+constexpr int SPARE_SMS = 0;
 constexpr uint64_t IDLE_NS = 20000000ull;   // persistent kernel idle limit: 20 ms
 // claim word: epoch (24 bits) | next unit (20 bits) | units (20 bits)
 constexpr int CW_NEXT = 20, CW_EPOCH = 40;
@@ -312,11 +313,8 @@ static rs_status server_start(Ctx *ctx, Server **out)
     s->smem = SERVE_MAX_F * SS * sizeof(float) + SW * 64 * sizeof(uint4);
     if ((e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem)))
         return fail(e, "k_serve attribute");
-    // as many CTAs per SM as fit, on all but a few SMs, which stay free so that new requests can
-    // be packed while the kernel runs
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, SW * 32, s->smem);
-    s->grid = std::max(1, ctx->sm_count - SPARE_SMS) * std::max(1, per_sm);
+    // one CTA per SM: the rest of each SM stays available to the packing kernels of new requests
+    s->grid = std::max(1, ctx->sm_count - SPARE_SMS);
     s->thread = std::thread(server_loop, s);
     *out = s;
     return RS_OK;
