@@ -118,7 +118,7 @@ def hard_algorithmic_ops(batch, N):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("hard_eval.cu", "pack.cu", "rs_internal.cuh", "tma.cuh"):
+    for f in ("hard_eval.cu", "hard_eval4.cu", "eval_core.cuh", "pack.cu", "rs_internal.cuh", "tma.cuh"):
         with open(os.path.join(ROOT, "paper_2406_01821_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
