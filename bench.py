@@ -107,6 +107,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# evaluator kernel of each tile-configuration version (finite, ranked datasets)
+KERNEL_OF_VERSION = {1: "k_hard", 2: "k_hard2", 3: "k_hard2", 4: "k_hard4", 5: "k_hard5"}
+
+
 def hard_algorithmic_ops(batch, N):
     """Algorithmic lane operations of one evaluation: 1 compare per threshold condition-eval,
     2 multiplies + 1 compare per pair condition-eval, and per rule 3 word operations (AND,
@@ -118,7 +122,8 @@ def hard_algorithmic_ops(batch, N):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("hard_eval.cu", "hard_eval4.cu", "eval_core.cuh", "pack.cu", "rs_internal.cuh", "tma.cuh"):
+    for f in ("hard_eval.cu", "hard_eval4.cu", "hard_eval5.cu", "eval_core.cuh", "pack.cu",
+              "rs_internal.cuh", "tma.cuh"):
         with open(os.path.join(ROOT, "paper_2406_01821_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -576,7 +581,8 @@ def main():
             "roofline": {"bound": "alu", "achieved": ops / (kern_ms / 1e3) / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s",
                          "frac": (ops / (kern_ms / 1e3)) / peak_ops, "traffic": traffic,
-                         "kernel": "k_hard", "kernel_ms": kern_ms,
+                         "kernel": KERNEL_OF_VERSION.get(rs.tile_configs()[res["tile"]]["form"], "k_hard"),
+                         "kernel_ms": kern_ms,
                          "ops_per_launch": ops,
                          "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                         f"({peak_src} max clock)"},

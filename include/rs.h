@@ -311,6 +311,11 @@ int32_t rs_tile_config_count(void);
 /* Describe configuration `id`: samples per CTA tile, warps per CTA, samples per lane. */
 rs_status rs_tile_config_info(int32_t id, int32_t *samples_per_tile, int32_t *warps,
                               int32_t *samples_per_lane);
+/* Evaluator form of configuration `id`: 1 condition at a time; 2 rule at a time; 3 rule at a
+ * time with the margin minimum; 4 sign-mask conjunction (finite datasets, else runs as 3);
+ * 5 rank-coded cuts (datasets with rank tables: finite and at most 160 features; else runs as
+ * 4, then 3). Forms 4 and 5 produce counts only: a call that asks for predictions runs as 3. */
+rs_status rs_tile_config_form(int32_t id, int32_t *form);
 /* Force configuration `id` for every following hard evaluation of the context (-1 = automatic:
  * autotuned table, else heuristic). */
 rs_status rs_set_tile_config(rs_ctx *ctx, int32_t id);

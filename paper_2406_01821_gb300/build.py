@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "--expt-relaxed-constexpr"]
-NO_FMA = {"hard_eval.cu", "pack.cu", "serve.cu", "evolve.cu"}
+NO_FMA = {"hard_eval.cu", "hard_eval5.cu", "pack.cu", "serve.cu", "evolve.cu"}
 
 
 def sources():

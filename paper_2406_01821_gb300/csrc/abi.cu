@@ -282,6 +282,13 @@ rs_status rs_tile_config_info(int32_t id, int32_t *samples_per_tile, int32_t *wa
     return RS_OK;
 }
 
+rs_status rs_tile_config_form(int32_t id, int32_t *form)
+{
+    if (id < 0 || id >= tile_config_count() || !form) { set_error("bad tile config %d", id); return RS_ERR_INVALID; }
+    *form = tile_config(id).ver;
+    return RS_OK;
+}
+
 rs_status rs_set_tile_config(rs_ctx *ctx, int32_t id)
 {
     if (!ctx) return RS_ERR_INVALID;

@@ -88,10 +88,10 @@ static std::string tune_key(const Dataset &ds, const rs_batch *b)
 
 static int heuristic_tile(const Dataset &ds)
 {
-    // The sign-mask evaluator with 128-sample tiles and 32 warps (fastest measured on the ragged
-    // workload; it runs as the margin-minimum form on non-finite data), then smaller tiles for
-    // wide data.
-    static const int prefs[] = {18, 16, 20, 3, 5};
+    // The rank-coded evaluator with 32 warps (it runs as the sign-mask form on datasets without
+    // rank tables and as the margin-minimum form on non-finite data), then smaller tiles for wide
+    // data.
+    static const int prefs[] = {22, 21, 18, 16, 20, 3, 5};
     for (int id : prefs)
         if (tile_config_fits(tile_config(id), ds.F)) return id;
     return 5;
@@ -181,7 +181,8 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchD
 {
     PackOut po{s.recs, s.sets, s.order, s.status};
     const int ver = effective_version(tc, *ds, preds != nullptr);
-    count_launch(ctx, launch_pack(bd, ds->F, ds->K, tc.S(), ver >= 4 ? 4 : (ver >= 2 ? 2 : 1), po, stream));
+    const int pack_ver = ver == 5 ? 5 : (ver == 4 ? 4 : (ver >= 2 ? 2 : 1));
+    count_launch(ctx, launch_pack(bd, ds->F, ds->K, tc.S(), pack_ver, po, stream));
     RS_CUDA(cudaGetLastError());
     HardArgs a{};
     a.recs = s.recs;

@@ -260,6 +260,7 @@ const TileConfig kConfigs[] = {
     {8, 4, 8, 2}, {9, 4, 16, 2}, {10, 2, 16, 2},
     {11, 4, 8, 3}, {12, 4, 16, 3}, {13, 2, 16, 3}, {14, 2, 32, 3}, {15, 4, 32, 3},
     {16, 4, 8, 4}, {17, 4, 16, 4}, {18, 4, 32, 4}, {19, 2, 16, 4}, {20, 2, 32, 4},
+    {21, 4, 16, 5}, {22, 4, 32, 5},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
@@ -270,8 +271,10 @@ int tile_config_count() { return kNumConfigs; }
 int effective_version(const TileConfig &tc, const Dataset &ds, bool preds)
 {
     if (tc.ver >= 4 && (preds || !ds.finite)) return 3;   // same V and W exist for version 3
+    if (tc.ver == 5 && (!ds.ranked || hard5_smem_bytes(ds.F, tc.W) > 227 * 1024)) return 4;
     return tc.ver;
 }
+
 const TileConfig &tile_config(int id) { return kConfigs[id]; }
 
 bool tile_config_fits(const TileConfig &tc, int F)
@@ -291,6 +294,7 @@ rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArg
         RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
     const int ver = effective_version(tc, *ds, a.preds != nullptr);
+    if (ver == 5) return launch_hard5(ctx, ds, tc.W, a, stream);
     if (ver == 4) return launch_hard4(ctx, ds, tc.V, tc.W, a, stream);
     if (ver >= 2) return launch_hard2(ctx, ds, tc.V, tc.W, ver == 3, a, stream);
     switch (tc.id) {

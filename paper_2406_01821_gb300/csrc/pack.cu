@@ -176,6 +176,78 @@ __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
     sets[p] = si;
 }
 
+// Kind of a condition in format v5, decided with the same tests as rewrite_threshold (without its
+// search): R5_CUT_GT / R5_CUT_LT for a +-cut, R5_PAIR, or R5_GEN for everything else (zero or
+// infinite coefficient, never-true conditions, invalid input).
+__device__ uint32_t kind5(const BatchDev &b, int c, int F)
+{
+    const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
+    if (f < 0 || f >= F || g < -1 || g >= F || (op != 0 && op != 1)) return R5_GEN;
+    if (g >= 0) return R5_PAIR;
+    const float a = b.cond_a[c], t = b.cond_t[c];
+    if (isnan(a) || isnan(t) || a == 0.f || isinf(a)) return R5_GEN;
+    const bool up = (a > 0.f) == (op == 0);
+    const float end = up ? __uint_as_float(0x7F800000u) : __uint_as_float(0xFF800000u);
+    if (!thr_true(a, end, t, op)) return R5_GEN;
+    return up ? R5_CUT_GT : R5_CUT_LT;
+}
+
+// Pack v5 records, one thread per rule: the cuts, the pairs and the remaining conditions (a
+// conjunction does not depend on the order of its conditions); the rule's last record carries
+// the end-of-rule flag and the rule class.
+__global__ void k_pack_rules5(BatchDev b, int F, int K, Rec *recs_out, uint32_t *status)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
+    if (r >= b.R) return;
+    const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
+    if (c0 < 0 || c1 < c0 || c1 > b.C) { atomicOr(status, ST_BAD_OFFSETS); return; }
+    if (c1 - c0 > 0xFFF) { atomicOr(status, ST_TOO_LARGE); return; }
+    int cls = b.rule_class[r];
+    if (cls < 0 || cls >= K) { atomicOr(status, ST_BAD_CLASS); cls = 0; }
+    uint4 *out = reinterpret_cast<uint4 *>(recs_out);
+    int ncut = 0, npair = 0;
+    for (int c = c0; c < c1; ++c) {
+        const uint32_t k = kind5(b, c, F);
+        ncut += (k == R5_CUT_GT || k == R5_CUT_LT);
+        npair += (k == R5_PAIR);
+    }
+    int qc = c0, qp = c0 + ncut, qg = c0 + ncut + npair;
+    const float pinf = __uint_as_float(0x7F800000u);
+    for (int c = c0; c < c1; ++c) {
+        const uint32_t k = kind5(b, c, F);
+        const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
+        int q;
+        uint4 rec;
+        if (k == R5_CUT_GT || k == R5_CUT_LT) {
+            uint32_t kind;
+            float cut, unused;
+            rewrite_threshold(b.cond_a[c], b.cond_t[c], op, kind, cut, unused);
+            // x < c  <=>  x <= nextdown(c) for non-NaN x: both cut kinds then count tile values <= w2
+            if (k == R5_CUT_LT) cut = nextafterf(cut, __uint_as_float(0xFF800000u));
+            rec = make_uint4((k << R5_TAG_SHIFT) | (uint32_t)f, 0u, __float_as_uint(cut), 0u);
+            q = qc++;
+        } else if (k == R5_PAIR) {
+            const int lf = op == 0 ? f : g, rg = op == 0 ? g : f;
+            const float a = op == 0 ? b.cond_a[c] : b.cond_b[c];
+            const float bb = op == 0 ? b.cond_b[c] : b.cond_a[c];
+            rec = make_uint4((R5_PAIR << R5_TAG_SHIFT) | (uint32_t)lf, (uint32_t)rg, __float_as_uint(a),
+                             __float_as_uint(bb));
+            q = qp++;
+        } else {
+            float v0 = 0.f, v1 = pinf;   // never true
+            uint32_t rf = 0;
+            if (f < 0 || f >= F || g < -1 || g >= F) atomicOr(status, ST_BAD_FEATURE);
+            else if (op != 0 && op != 1) atomicOr(status, ST_BAD_OP);
+            else { rewrite_lin(b.cond_a[c], b.cond_t[c], op, v0, v1); rf = (uint32_t)f; }
+            rec = make_uint4((R5_GEN << R5_TAG_SHIFT) | rf, 0u, __float_as_uint(v0), __float_as_uint(v1));
+            q = qg++;
+        }
+        if (q == c1 - 1) rec.x |= R5_END_BIT | ((uint32_t)cls << R5_CLS_SHIFT);
+        out[q] = rec;
+    }
+}
+
 // One thread per rule: build the records of its conditions.
 __global__ void k_pack_rules(BatchDev b, int F, int K, Rec *recs, uint32_t *status)
 {
@@ -242,7 +314,10 @@ int launch_pack(const BatchDev &b, int F, int K, int S, int ver, const PackOut &
 {
     int n = 0;
     if (b.P > 0) { k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.status); ++n; }
-    if (b.R > 0 && ver >= 2) {
+    if (b.R > 0 && ver == 5) {
+        k_pack_rules5<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status);
+        ++n;
+    } else if (b.R > 0 && ver >= 2) {
         k_pack_rules2<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, S, ver == 4 ? 4 : 2, o.recs, o.status);
         ++n;
     } else if (b.R > 0) {

@@ -65,6 +65,18 @@ constexpr int CLS_SHIFT = 18;
 // v4 only: a threshold condition that is not a +-1 cut (zero or infinite coefficient, never true)
 constexpr uint32_t GENERAL_BIT = 1u << 31;
 
+// Record format v5 (rank-coded evaluator): per rule its threshold cuts, its pair conditions and
+// its remaining product conditions, one record per condition (same positions as the conditions).
+// w0 = tag << 29 | end-of-rule << 28 | rule class << 16 (last record of a rule) | feature.
+//   cut:     x[f] > w2 (R5_CUT_GT) or x[f] <= w2 (R5_CUT_LT: x[f] < c stored as w2 = nextdown(c))
+//   pair:    fl(w2 * x[f]) > fl(w3 * x[w1])
+//   product: fl(w2 * x[f]) > w3
+enum : uint32_t { R5_NONE = 0, R5_CUT_GT = 2, R5_CUT_LT = 3, R5_PAIR = 4, R5_GEN = 5 };
+constexpr int R5_TAG_SHIFT = 29;
+constexpr uint32_t R5_END_BIT = 1u << 28;
+constexpr int R5_CLS_SHIFT = 16;
+constexpr uint32_t R5_F_MASK = 0xFFFFu;
+
 struct __align__(16) Rec {
     uint32_t meta;   // [0,3) kind | [3] last condition of its rule | [4,16) rule class | [16,32) skip
     uint16_t f, g;
@@ -106,6 +118,14 @@ struct Dataset {
     int32_t *inv = nullptr;       // [N] sorted position of caller index
     std::vector<int64_t> class_count;
     std::map<int, CUtensorMap> tmaps;   // keyed by samples per tile
+    // Rank tables (finite datasets with F <= RANK_MAX_F), per 128-sample tile t and feature f:
+    // Rk[f][n] = number of values of the tile's column f strictly below x[f][n] (0..127), and
+    // Us[t][f][j ^ (f & 31)] = the tile's column f in ascending order.
+    uint8_t *Rk = nullptr;
+    float *Us = nullptr;
+    bool ranked = false;
+    bool rmap_ok = false;
+    CUtensorMap rmap;
     std::mutex mu;
 };
 
@@ -118,8 +138,11 @@ struct TileConfig {
     int ver;     // 1: condition-at-a-time evaluator, 2: rule-at-a-time (record v2),
                  // 3: rule-at-a-time with the margin-minimum conjunction,
                  // 4: sign-mask conjunction for finite datasets (falls back to 3 otherwise)
+                 // 5: rank-coded cuts for ranked datasets (falls back to 4, then 3)
     int S() const { return 32 * V; }
 };
+constexpr int RANK_TILE = 128;    // samples per rank tile (ranks fit in 7 bits)
+constexpr int RANK_MAX_F = 160;   // widest dataset given rank tables
 int tile_config_count();
 const TileConfig &tile_config(int id);
 // Largest F a configuration can stage (its x tile must fit in shared memory).
@@ -221,6 +244,9 @@ int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P);
 rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, bool mm, const HardArgs &a,
                        cudaStream_t stream);
 rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream);
+rs_status launch_hard5(Ctx *ctx, Dataset *ds, int W, const HardArgs &a, cudaStream_t stream);
+// Shared memory of the v5 evaluator for F features and W warps.
+size_t hard5_smem_bytes(int F, int W);
 // The evaluator version a configuration runs as for this dataset and output choice.
 int effective_version(const TileConfig &tc, const Dataset &ds, bool preds);
 // Enqueue packing + evaluation of a device batch with the given scratch.
@@ -230,6 +256,7 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchD
 // The built-in tile choice for a dataset (no autotuned entry).
 int heuristic_tile_for(const Dataset &ds);
 const CUtensorMap *dataset_tmap(Dataset *ds, int S);
+const CUtensorMap *dataset_rank_tmap(Dataset *ds);
 
 struct SoftArgs {
     BatchDev b;

@@ -116,6 +116,7 @@ _SIGS = {
     "rs_tile_config_count": (ctypes.c_int32, []),
     "rs_tile_config_info": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "rs_tile_config_form": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "rs_set_tile_config": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "rs_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
@@ -416,9 +417,11 @@ class Context:
 def tile_configs():
     out = []
     for i in range(lib().rs_tile_config_count()):
-        s, w, v = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        s, w, v, f = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         check(lib().rs_tile_config_info(i, ctypes.byref(s), ctypes.byref(w), ctypes.byref(v)))
-        out.append({"id": i, "samples_per_tile": s.value, "warps": w.value, "samples_per_lane": v.value})
+        check(lib().rs_tile_config_form(i, ctypes.byref(f)))
+        out.append({"id": i, "samples_per_tile": s.value, "warps": w.value, "samples_per_lane": v.value,
+                    "form": f.value})
     return out
 
 

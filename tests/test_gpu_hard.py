@@ -74,8 +74,10 @@ def test_every_tile_config_identical(ctx, orc):
 
 
 # one configuration of each evaluator form: condition-at-a-time, rule-at-a-time with predicate
-# conjunction, with the margin minimum, and the sign-mask form for finite data
-FORMS = [0, 9, 12, 17]
+# conjunction, with the margin minimum, the sign-mask form for finite data, and the rank-coded
+# form (16 and 32 warps) for datasets with rank tables
+FORMS = [0, 9, 12, 17, 21, 22]
+RANKED = [21, 22]
 
 
 @pytest.mark.parametrize("tile", FORMS)
@@ -286,3 +288,70 @@ def test_ragged_full_size_sampled(ctx, orc):
     want_c, want_pc, _ = orc.eval_hard(w.X, w.y, w.K, sub)
     assert np.array_equal(correct[sample], want_c)
     assert np.array_equal(pc[sample], want_pc)
+
+
+@pytest.mark.parametrize("tile", RANKED + [17])
+@pytest.mark.parametrize("seed", range(3))
+def test_rank_ties_and_thresholds_at_data_values(ctx, orc, tile, seed):
+    """Tiles full of equal values (small integers, +0 and -0) and thresholds placed exactly on data
+    values and one ulp either side: the per-tile rank counts must treat ties exactly."""
+    rng = np.random.default_rng(100 + seed)
+    N, F = 3000, 6
+    X = rng.integers(-3, 4, (N, F)).astype(np.float32)
+    X[:, 1] = np.where(rng.random(N) < 0.5, np.float32(0.0), np.float32(-0.0))
+    X[:, 2] = rng.standard_normal(N).astype(np.float32)
+    b = synth.random_rulesets(synth.quantile_table(X), 3, 48, (1, 12), (1, 6), seed, pair_prob=0.25)
+    thr = b.cond_g < 0
+    idx = np.flatnonzero(thr)
+    vals = X[rng.integers(0, N, len(idx)), b.cond_f[idx]]
+    a = rng.choice(np.array([1.0, -1.0, 0.5, -2.0], np.float32), len(idx))
+    t = (a * vals).astype(np.float32)
+    shift = rng.integers(-1, 2, len(idx))
+    t = np.where(shift < 0, np.nextafter(t, np.float32(-np.inf)),
+                 np.where(shift > 0, np.nextafter(t, np.float32(np.inf)), t)).astype(np.float32)
+    b.cond_a[idx], b.cond_t[idx] = a, t
+    y = rng.integers(0, 3, N).astype(np.int32)
+    got = run_gpu(ctx, X, y, 3, b, preds=False, tile=tile)
+    want = orc.eval_hard(X, y, 3, b)
+    assert_same(got, want, preds=False)
+
+
+@pytest.mark.parametrize("tile", RANKED + [17])
+def test_long_rules_cross_the_record_window(ctx, orc, tile):
+    """Rules of 30..150 conditions (longer than the 64-record stage) mixed with short ones."""
+    X, y = synth.gaussian_mixture(2000, 24, 4, 7)
+    b = synth.random_rulesets(synth.quantile_table(X), 4, 30, (1, 12), (30, 150), 7, pair_prob=0.05)
+    # loosen the thresholds so that long rules still fire on some samples
+    thr = b.cond_g < 0
+    b.cond_t[thr] = np.where(b.cond_op[thr] == synth.GT, np.float32(-2.5), np.float32(2.5)) * np.abs(b.cond_a[thr])
+    got = run_gpu(ctx, X, y, 4, b, preds=False, tile=tile)
+    want = orc.eval_hard(X, y, 4, b)
+    assert_same(got, want, preds=False)
+    assert want[0].max() > 0
+
+
+@pytest.mark.parametrize("tile", RANKED)
+def test_many_labels_per_tile(ctx, orc, tile):
+    """40 classes over 3001 samples: most 128-sample tiles hold several labels."""
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((3001, 9)).astype(np.float32)
+    y = rng.integers(0, 40, 3001).astype(np.int32)
+    b = synth.random_rulesets(synth.quantile_table(X), 40, 64, (1, 20), (1, 5), 9, pair_prob=0.2)
+    got = run_gpu(ctx, X, y, 40, b, preds=False, tile=tile)
+    want = orc.eval_hard(X, y, 40, b)
+    assert_same(got, want, preds=False)
+
+
+def test_wide_and_nonfinite_data_fall_back_from_ranks(ctx, orc):
+    """Datasets without rank tables (F > 168, or NaN/inf present) run the rank-coded
+    configuration as its sign-mask / margin-minimum twin, still exact."""
+    rng = np.random.default_rng(4)
+    for F, poison in ((200, False), (12, True)):
+        X = rng.standard_normal((1500, F)).astype(np.float32)
+        if poison:
+            X[rng.integers(0, 1500, 20), rng.integers(0, F, 20)] = np.nan
+        y = rng.integers(0, 2, 1500).astype(np.int32)
+        b = synth.random_rulesets(synth.quantile_table(np.nan_to_num(X)), 2, 24, (1, 8), (1, 4), 4)
+        got = run_gpu(ctx, X, y, 2, b, preds=False, tile=22)
+        want = orc.eval_hard(X, y, 2, b)
+        assert_same(got, want, preds=False)
