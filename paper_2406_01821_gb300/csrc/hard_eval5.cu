@@ -46,7 +46,8 @@ __device__ __forceinline__ int count_below(const float *row, int sw, float c)
     return pos;
 }
 
-constexpr int VSLOTS = 8;                    // pass rows per warp for pair / product conditions
+// pass rows per warp for pair / product conditions of one chunk
+template <int W> __host__ __device__ constexpr int vslots() { return W >= 32 ? 12 : 16; }
 constexpr uint32_t NOOP_K = 127u * ONES;     // constant - rank never has bit 7 set: never fails
 
 // The staged form of a cut for this tile: {rank-table byte offset of the row, per-byte constant}.
@@ -67,24 +68,6 @@ __device__ __forceinline__ uint32_t gt_bytes(const float (&p)[4], const float (&
     return __byte_perm(__byte_perm(s[0], s[1], 0x0040), __byte_perm(s[2], s[3], 0x0040), 0x5410);
 }
 
-// Pass bits (0x80 in byte v where the condition holds for the lane's sample v) of a pair
-// condition fl(a * x[f]) > fl(b * x[g]) or a product condition fl(a * x[f]) > b.
-__device__ __forceinline__ uint32_t pass_bytes(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
-                                               const unsigned char *xl, int F)
-{
-    const uint32_t f = min(w0 & R5_F_MASK, (uint32_t)(F - 1));
-    const float4 x = *reinterpret_cast<const float4 *>(xl + f * T * 4u);
-    const float a = __uint_as_float(w2), b = __uint_as_float(w3);
-    const float p[4] = {__fmul_rn(a, x.x), __fmul_rn(a, x.y), __fmul_rn(a, x.z), __fmul_rn(a, x.w)};
-    float q[4] = {b, b, b, b};
-    if ((w0 >> R5_TAG_SHIFT) == R5_PAIR) {
-        const uint32_t g = min(w1, (uint32_t)(F - 1));
-        const float4 z = *reinterpret_cast<const float4 *>(xl + g * T * 4u);
-        q[0] = __fmul_rn(b, z.x); q[1] = __fmul_rn(b, z.y); q[2] = __fmul_rn(b, z.z); q[3] = __fmul_rn(b, z.w);
-    }
-    return gt_bytes(p, q) & HIGH;
-}
-
 // Bit 7 of byte v where the lane's sample v (labels yl[0..3]) has label k. Only tiles that hold
 // more than one label need it, so the labels are read again instead of kept in registers.
 __device__ __forceinline__ uint32_t class_bytes(const int32_t *yl, int k)
@@ -92,6 +75,46 @@ __device__ __forceinline__ uint32_t class_bytes(const int32_t *yl, int k)
     const int4 y = __ldg(reinterpret_cast<const int4 *>(yl));
     return ((y.x == k) ? 0x80u : 0u) | ((y.y == k) ? 0x8000u : 0u) | ((y.z == k) ? 0x800000u : 0u) |
            ((y.w == k) ? 0x80000000u : 0u);
+}
+
+// Pass bits (0x80 in byte v where the condition holds for the lane's sample v) of a pair
+// condition fl(a * x[f]) > fl(b * x[g]) or a product condition fl(a * x[f]) > b. The products are
+// separately rounded (packed two-lane multiplies).
+__device__ __forceinline__ uint32_t pass_bytes(uint4 r, const unsigned char *xl, int F)
+{
+    const uint32_t f = min(r.x & R5_F_MASK, (uint32_t)(F - 1));
+    const float4 x = *reinterpret_cast<const float4 *>(xl + f * T * 4u);
+    const float a = __uint_as_float(r.z), b = __uint_as_float(r.w);
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    const float2 p01 = __fmul2_rn(make_float2(x.x, x.y), a2), p23 = __fmul2_rn(make_float2(x.z, x.w), a2);
+    float2 q01 = b2, q23 = b2;
+    if ((r.x >> R5_TAG_SHIFT) == R5_PAIR) {
+        const uint32_t g = min(r.y, (uint32_t)(F - 1));
+        const float4 z = *reinterpret_cast<const float4 *>(xl + g * T * 4u);
+        q01 = __fmul2_rn(make_float2(z.x, z.y), b2);
+        q23 = __fmul2_rn(make_float2(z.z, z.w), b2);
+    }
+    const float p[4] = {p01.x, p01.y, p23.x, p23.y}, q[4] = {q01.x, q01.y, q23.x, q23.y};
+    return gt_bytes(p, q) & HIGH;
+}
+
+// One group of four staged records with end-of-rule flags M (bit u: record u ends its rule).
+template <uint32_t M, bool UNI>
+__device__ __forceinline__ void group4(const uint32_t (&e)[4], const uint32_t *sw, const int32_t *yl,
+                                       uint32_t &fail, uint32_t &claimed, uint32_t &hit)
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        fail |= e[u];
+        if (M & (1u << u)) {
+            const uint32_t w = sw[u];
+            const uint32_t newly = ~fail & HIGH;
+            if (UNI) hit |= newly & w;
+            else hit |= newly & class_bytes(yl, (int)w);
+            claimed |= newly;
+            fail = claimed;
+        }
+    }
 }
 
 // Walk the rules of one set (records [rb, rb + nrec)) over the lane's four samples; returns the
@@ -104,7 +127,7 @@ __device__ __forceinline__ uint32_t class_bytes(const int32_t *yl, int k)
 // (0x80 / 0x00 per sample, constant 0x80808080) in the warp's `vrow` slots; padding records are
 // no-ops. The chunk is then one straight run of identical steps, with the first-fire claim
 // applied after each rule's last record (a warp vote gives their positions).
-template <bool UNI>
+template <bool UNI, int VS>
 __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t vrow_off, int lane,
                                              const uint4 *recs, int rb, int nrec, const float *us,
                                              uint32_t rev_off, int F, int kmine, const unsigned char *rl,
@@ -123,9 +146,9 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
         const uint32_t tag = raw.x >> R5_TAG_SHIFT;
         int cnt = min(32, nrec - c0);
         uint32_t pm = __ballot_sync(FULL, lane < cnt && (tag == R5_PAIR || tag == R5_GEN));
-        if (__popc(pm) > VSLOTS) {          // end the chunk before the pair that finds no slot
+        if (__popc(pm) > VS) {              // end the chunk before the pair that finds no slot
             uint32_t m = pm;
-            for (int k = 0; k < VSLOTS; ++k) m &= m - 1u;
+            for (int k = 0; k < VS; ++k) m &= m - 1u;
             cnt = __ffs(m) - 1;
             pm &= (1u << cnt) - 1u;
         }
@@ -134,21 +157,30 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
 
         __syncwarp();
         st[lane] = raw;                     // raw records, read back by the pass-row loop
-        uint2 sr = make_uint2(0u, NOOP_K);
+        // every lane runs the cut search (branch-free staging); other records then take their form
         const uint32_t cls = (raw.x >> R5_CLS_SHIFT) & 0xFFFu;
         const uint32_t ew = UNI ? ((int)cls == kmine ? 0xFFFFFFFFu : 0u) : cls;
-        if (lane < cnt) {
-            if (tag == R5_CUT_GT || tag == R5_CUT_LT) {
-                sr = stage_cut(raw, us, rev_off, F);
-            } else if (tag == R5_PAIR || tag == R5_GEN) {
-                sr = make_uint2(vrow_off + 128u * (uint32_t)__popc(pm & ((1u << lane) - 1u)), HIGH);
-            }
-        }
+        uint2 sr = stage_cut(raw, us, rev_off, F);
+        if ((pm >> lane) & 1u) sr = make_uint2(vrow_off + 128u * (uint32_t)__popc(pm & ((1u << lane) - 1u)), HIGH);
+        else if (lane >= cnt || tag == R5_NONE) sr = make_uint2(0u, NOOP_K);
         __syncwarp();
-        for (uint32_t m = pm; m; m &= m - 1u) {      // pass rows, one warp-wide evaluation each
-            const int j = __ffs(m) - 1;
-            const uint4 pr = st[j];
-            vrow[32 * __popc(pm & ((1u << j) - 1u)) + lane] = pass_bytes(pr.x, pr.y, pr.z, pr.w, xl, F);
+        {                                             // pass rows, one warp-wide evaluation each
+            uint32_t m = pm;
+            uint32_t *vr = vrow + lane;
+            while (m) {
+                const uint4 p0 = st[__ffs(m) - 1];
+                m &= m - 1u;
+                if (m) {
+                    const uint4 p1 = st[__ffs(m) - 1];
+                    m &= m - 1u;
+                    const uint32_t v0 = pass_bytes(p0, xl, F), v1 = pass_bytes(p1, xl, F);
+                    vr[0] = v0;
+                    vr[32] = v1;
+                    vr += 64;
+                } else {
+                    vr[0] = pass_bytes(p0, xl, F);
+                }
+            }
         }
         __syncwarp();
         s8[lane] = sr;
@@ -162,24 +194,16 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
             const uint32_t e1 = ra.w - *reinterpret_cast<const uint32_t *>(rl + ra.z);
             const uint32_t e2 = rc.y - *reinterpret_cast<const uint32_t *>(rl + rc.x);
             const uint32_t e3 = rc.w - *reinterpret_cast<const uint32_t *>(rl + rc.z);
-            const uint32_t e4 = (ends >> g) & 0xFu;
-            if (e4 == 0u) {
-                fail |= e0 | e1 | e2 | e3;
-            } else {
-                const uint32_t e[4] = {e0, e1, e2, e3};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    fail |= e[u];
-                    if (e4 & (1u << u)) {
-                        const uint32_t w = sw[g + u];
-                        const uint32_t newly = ~fail & HIGH;
-                        hit |= newly & (UNI ? w : class_bytes(yl, (int)w));
-                        claimed |= newly;
-                        fail = claimed;
-                    }
-                }
-                if (__all_sync(FULL, claimed == HIGH)) { done = true; break; }
+            const uint32_t e[4] = {e0, e1, e2, e3};
+            const uint32_t *swg = sw + g;
+            switch ((ends >> g) & 0xFu) {
+#define RS_GROUP4(M) case M: group4<M, UNI>(e, swg, yl, fail, claimed, hit); break;
+            RS_GROUP4(0) RS_GROUP4(1) RS_GROUP4(2) RS_GROUP4(3) RS_GROUP4(4) RS_GROUP4(5) RS_GROUP4(6)
+            RS_GROUP4(7) RS_GROUP4(8) RS_GROUP4(9) RS_GROUP4(10) RS_GROUP4(11) RS_GROUP4(12)
+            RS_GROUP4(13) RS_GROUP4(14) RS_GROUP4(15)
+#undef RS_GROUP4
             }
+            if (((ends >> g) & 0xFu) && __all_sync(FULL, claimed == HIGH)) { done = true; break; }
         }
         c0 += cnt;
     }
@@ -203,8 +227,9 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
     unsigned char *rs = xs + (size_t)Frows * T * 4;                   // u8 [Frows][T], then reversed
     float *us = reinterpret_cast<float *>(rs + (size_t)Frows * T * 2);  // float [F][T] sorted
     uint4 *stage_all = reinterpret_cast<uint4 *>(us + (size_t)Frows * T);
-    uint32_t *vrows = reinterpret_cast<uint32_t *>(stage_all + W * 32);     // [W][VSLOTS][32]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(vrows + W * VSLOTS * 32);
+    constexpr int VS = vslots<W>();
+    uint32_t *vrows = reinterpret_cast<uint32_t *>(stage_all + W * 32);     // [W][VS][32]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(vrows + W * VS * 32);
     int *next = reinterpret_cast<int *>(bar + 1);
     const uint4 *recs = reinterpret_cast<const uint4 *>(a.recs);
 
@@ -260,12 +285,12 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
         const SetInfo si = a.sets[p];
         const int rb = si.rec_begin, nrec = si.rec_end - si.rec_begin;
 
-        uint32_t *vr = vrows + warp * VSLOTS * 32;
+        uint32_t *vr = vrows + warp * VS * 32;
         const uint32_t vr_off = (uint32_t)(reinterpret_cast<unsigned char *>(vr) - rs);
         const uint32_t hit =
-            uniform ? walk_set<true>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, kmin, rl, xl, yl,
+            uniform ? walk_set<true, VS>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, kmin, rl, xl, yl,
                                      claimed0, si.deflt)
-                    : walk_set<false>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, -2, rl, xl, yl,
+                    : walk_set<false, VS>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, -2, rl, xl, yl,
                                       claimed0, si.deflt);
         const int hits = __reduce_add_sync(FULL, __popc(hit));
         if (lane == 0 && hits) atomicAdd(&a.correct[p], hits);
@@ -288,7 +313,8 @@ size_t hard5_smem_bytes(int F, int W)
 {
     const int Fb = F < 256 ? F : 256;
     const size_t Frows = (size_t)((F + Fb - 1) / Fb) * Fb;
-    return Frows * T * (4 + 2 + 4) + (size_t)W * 32 * 16 + (size_t)W * VSLOTS * 32 * 4 + 16;
+    const size_t vs = W >= 32 ? vslots<32>() : vslots<16>();
+    return Frows * T * (4 + 2 + 4) + (size_t)W * 32 * 16 + (size_t)W * vs * 32 * 4 + 16;
 }
 
 template <int W>
