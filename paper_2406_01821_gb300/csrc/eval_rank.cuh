@@ -1,0 +1,216 @@
+// Device code of the rank-coded evaluator (record format v5), shared by the batch evaluator and
+// the serving kernel.
+//
+// A threshold condition has been rewritten exactly as x > c or x < c (pack.cu). Within one
+// 128-sample tile, let rank(x) be the number of the tile's values (same feature) strictly below
+// x. Because x is itself one of the tile's values,
+//     x >  c  <=>  rank(x) >= L,   L = #{tile values <= c}
+//     x <= c  <=>  rank(x) <  L
+// (a '<' cut x < c arrives as x <= nextdown(c)). L is counted once per tile and condition, by a
+// binary search over the tile's sorted values, when the condition's record is staged. The test
+// of a lane's four samples is then one 32-bit subtraction on four rank bytes (0..127), with the
+// failure in bit 7 of each byte:
+//     '>':  byte (L + 127) - rank          >= 128  <=>  rank <  L   (fails)
+//     '<=': byte (255 - L) - (127 - rank)  >= 128  <=>  rank >= L   (fails)
+// Each byte difference lies in [0, 255], so no borrow crosses a byte. The second form reads a
+// table of reversed ranks (127 - rank), built in shared memory from the first, so that both
+// forms are "constant minus table word". A rule's failures are ORed into one word per lane; pair
+// and product conditions are compared on the float tile and packed into the same byte layout.
+// Claims, per-class hits and the all-claimed exit work on these words (bit 7 of byte v belongs
+// to the lane's sample v). A set's records are one flat stream (each rule's conditions, the last
+// one flagged) walked 32 records at a time. Predictions are not produced here.
+#pragma once
+#include "rs_internal.cuh"
+
+namespace rs {
+namespace rank {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr uint32_t HIGH = 0x80808080u;          // bit 7 of every byte
+constexpr uint32_t ONES = 0x01010101u;
+constexpr int T = RANK_TILE;                     // samples per tile (= one warp, four per lane)
+
+// #{j : row[j] <= c} (or < c) over the 128 ascending values of a row stored at j ^ sw.
+template <bool LE>
+__device__ __forceinline__ int count_below(const float *row, int sw, float c)
+{
+    int pos = 0;
+#pragma unroll
+    for (int step = 64; step >= 1; step >>= 1) {
+        const float u = row[(pos + step - 1) ^ sw];
+        if (LE ? (u <= c) : (u < c)) pos += step;
+    }
+    const float u = row[pos ^ sw];               // pos <= 127: one more for a full count
+    if (LE ? (u <= c) : (u < c)) pos += 1;
+    return pos;
+}
+
+// pass rows per warp for pair / product conditions of one chunk
+template <int W> __host__ __device__ constexpr int vslots() { return W >= 32 ? 12 : 16; }
+constexpr uint32_t NOOP_K = 127u * ONES;     // constant - rank never has bit 7 set: never fails
+
+// The staged form of a cut for this tile: {rank-table byte offset of the row, per-byte constant}.
+__device__ __forceinline__ uint2 stage_cut(uint4 r, const float *us, uint32_t rev_off, int F)
+{
+    const uint32_t f = min(r.x & R5_F_MASK, (uint32_t)(F - 1));
+    const bool le = (r.x >> R5_TAG_SHIFT) == R5_CUT_LT;
+    const int L = count_below<true>(us + f * T, (int)(f & 31u), __uint_as_float(r.z));
+    return make_uint2((le ? rev_off : 0u) + f * T, (uint32_t)(le ? 255 - L : L + 127) * ONES);
+}
+
+// 0xFF in byte v where p[v] > q[v] (IEEE compare: false with NaN), 0 elsewhere.
+__device__ __forceinline__ uint32_t gt_bytes(const float (&p)[4], const float (&q)[4])
+{
+    uint32_t s[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(s[v]) : "f"(p[v]), "f"(q[v]));
+    return __byte_perm(__byte_perm(s[0], s[1], 0x0040), __byte_perm(s[2], s[3], 0x0040), 0x5410);
+}
+
+// Bit 7 of byte v where the lane's sample v (labels yl[0..3]) has label k. Only tiles that hold
+// more than one label need it, so the labels are read again instead of kept in registers.
+__device__ __forceinline__ uint32_t class_bytes(const int32_t *yl, int k)
+{
+    const int4 y = __ldg(reinterpret_cast<const int4 *>(yl));
+    return ((y.x == k) ? 0x80u : 0u) | ((y.y == k) ? 0x8000u : 0u) | ((y.z == k) ? 0x800000u : 0u) |
+           ((y.w == k) ? 0x80000000u : 0u);
+}
+
+// Pass bits (0x80 in byte v where the condition holds for the lane's sample v) of a pair
+// condition fl(a * x[f]) > fl(b * x[g]) or a product condition fl(a * x[f]) > b. The products are
+// separately rounded (packed two-lane multiplies).
+__device__ __forceinline__ uint32_t pass_bytes(uint4 r, const unsigned char *xl, int F)
+{
+    const uint32_t f = min(r.x & R5_F_MASK, (uint32_t)(F - 1));
+    const float4 x = *reinterpret_cast<const float4 *>(xl + f * T * 4u);
+    const float a = __uint_as_float(r.z), b = __uint_as_float(r.w);
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    const float2 p01 = __fmul2_rn(make_float2(x.x, x.y), a2), p23 = __fmul2_rn(make_float2(x.z, x.w), a2);
+    float2 q01 = b2, q23 = b2;
+    if ((r.x >> R5_TAG_SHIFT) == R5_PAIR) {
+        const uint32_t g = min(r.y, (uint32_t)(F - 1));
+        const float4 z = *reinterpret_cast<const float4 *>(xl + g * T * 4u);
+        q01 = __fmul2_rn(make_float2(z.x, z.y), b2);
+        q23 = __fmul2_rn(make_float2(z.z, z.w), b2);
+    }
+    const float p[4] = {p01.x, p01.y, p23.x, p23.y}, q[4] = {q01.x, q01.y, q23.x, q23.y};
+    return gt_bytes(p, q) & HIGH;
+}
+
+// One group of four staged records with end-of-rule flags M (bit u: record u ends its rule).
+template <uint32_t M, bool UNI>
+__device__ __forceinline__ void group4(const uint32_t (&e)[4], const uint32_t *sw, const int32_t *yl,
+                                       uint32_t &fail, uint32_t &claimed, uint32_t &hit)
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        fail |= e[u];
+        if (M & (1u << u)) {
+            const uint32_t w = sw[u];
+            const uint32_t newly = ~fail & HIGH;
+            if (UNI) hit |= newly & w;
+            else hit |= newly & class_bytes(yl, (int)w);
+            claimed |= newly;
+            fail = claimed;
+        }
+    }
+}
+
+// Walk the rules of one set (records [rb, rb + nrec)) over the lane's four samples; returns the
+// hit bits (bit 7 of byte v: sample v predicted correctly, default included). UNI: the tile holds
+// one label (kmine) and end records carry the class mask.
+//
+// The set is walked in chunks of up to 32 records. Staging turns every record of a chunk into the
+// same form {byte offset from the lane's rank word, per-byte constant}: a cut points at its rank
+// row; a pair or product condition is first evaluated by the whole warp into a pass row
+// (0x80 / 0x00 per sample, constant 0x80808080) in the warp's `vrow` slots; padding records are
+// no-ops. The chunk is then one straight run of identical steps, with the first-fire claim
+// applied after each rule's last record (a warp vote gives their positions).
+template <bool UNI, int VS>
+__device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t vrow_off, int lane,
+                                             const uint4 *recs, int rb, int nrec, const float *us,
+                                             uint32_t rev_off, int F, int kmine, const unsigned char *rl,
+                                             const unsigned char *xl, const int32_t *yl, uint32_t claimed,
+                                             int deflt)
+{
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    uint2 *s8 = reinterpret_cast<uint2 *>(st);            // staged {offset, constant}, 32 entries
+    uint32_t *sw = reinterpret_cast<uint32_t *>(st) + 64;  // end-of-rule class mask / class
+    uint4 pf = lane < nrec ? __ldcg(recs + rb + lane) : zero4;
+    uint32_t hit = 0, fail = claimed;
+    bool done = false;
+    int c0 = 0;
+    while (c0 < nrec && !done) {
+        const uint4 raw = pf;
+        const uint32_t tag = raw.x >> R5_TAG_SHIFT;
+        int cnt = min(32, nrec - c0);
+        uint32_t pm = __ballot_sync(FULL, lane < cnt && (tag == R5_PAIR || tag == R5_GEN));
+        if (__popc(pm) > VS) {              // end the chunk before the pair that finds no slot
+            uint32_t m = pm;
+            for (int k = 0; k < VS; ++k) m &= m - 1u;
+            cnt = __ffs(m) - 1;
+            pm &= (1u << cnt) - 1u;
+        }
+        const uint32_t ends = __ballot_sync(FULL, lane < cnt && (raw.x & R5_END_BIT) != 0u);
+        pf = (c0 + cnt + lane < nrec) ? __ldcg(recs + rb + c0 + cnt + lane) : zero4;
+
+        __syncwarp();
+        st[lane] = raw;                     // raw records, read back by the pass-row loop
+        // every lane runs the cut search (branch-free staging); other records then take their form
+        const uint32_t cls = (raw.x >> R5_CLS_SHIFT) & 0xFFFu;
+        const uint32_t ew = UNI ? ((int)cls == kmine ? 0xFFFFFFFFu : 0u) : cls;
+        uint2 sr = stage_cut(raw, us, rev_off, F);
+        if ((pm >> lane) & 1u) sr = make_uint2(vrow_off + 128u * (uint32_t)__popc(pm & ((1u << lane) - 1u)), HIGH);
+        else if (lane >= cnt || tag == R5_NONE) sr = make_uint2(0u, NOOP_K);
+        __syncwarp();
+        {                                             // pass rows, one warp-wide evaluation each
+            uint32_t m = pm;
+            uint32_t *vr = vrow + lane;
+            while (m) {
+                const uint4 p0 = st[__ffs(m) - 1];
+                m &= m - 1u;
+                if (m) {
+                    const uint4 p1 = st[__ffs(m) - 1];
+                    m &= m - 1u;
+                    const uint32_t v0 = pass_bytes(p0, xl, F), v1 = pass_bytes(p1, xl, F);
+                    vr[0] = v0;
+                    vr[32] = v1;
+                    vr += 64;
+                } else {
+                    vr[0] = pass_bytes(p0, xl, F);
+                }
+            }
+        }
+        __syncwarp();
+        s8[lane] = sr;
+        sw[lane] = ew;
+        __syncwarp();
+
+        for (int g = 0; g < cnt; g += 4) {
+            const uint4 ra = *reinterpret_cast<const uint4 *>(s8 + g);
+            const uint4 rc = *reinterpret_cast<const uint4 *>(s8 + g + 2);
+            const uint32_t e0 = ra.y - *reinterpret_cast<const uint32_t *>(rl + ra.x);
+            const uint32_t e1 = ra.w - *reinterpret_cast<const uint32_t *>(rl + ra.z);
+            const uint32_t e2 = rc.y - *reinterpret_cast<const uint32_t *>(rl + rc.x);
+            const uint32_t e3 = rc.w - *reinterpret_cast<const uint32_t *>(rl + rc.z);
+            const uint32_t e[4] = {e0, e1, e2, e3};
+            const uint32_t *swg = sw + g;
+            switch ((ends >> g) & 0xFu) {
+#define RS_GROUP4(M) case M: group4<M, UNI>(e, swg, yl, fail, claimed, hit); break;
+            RS_GROUP4(0) RS_GROUP4(1) RS_GROUP4(2) RS_GROUP4(3) RS_GROUP4(4) RS_GROUP4(5) RS_GROUP4(6)
+            RS_GROUP4(7) RS_GROUP4(8) RS_GROUP4(9) RS_GROUP4(10) RS_GROUP4(11) RS_GROUP4(12)
+            RS_GROUP4(13) RS_GROUP4(14) RS_GROUP4(15)
+#undef RS_GROUP4
+            }
+            if (((ends >> g) & 0xFu) && __all_sync(FULL, claimed == HIGH)) { done = true; break; }
+        }
+        c0 += cnt;
+    }
+    const uint32_t left = ~claimed & HIGH;
+    if (UNI) hit |= (deflt == kmine) ? left : 0u;
+    else hit |= left & class_bytes(yl, deflt);
+    return hit;
+}
+
+}  // namespace rank
+}  // namespace rs

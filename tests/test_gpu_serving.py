@@ -63,11 +63,12 @@ def test_mix_equals_alone(orc):
             assert np.array_equal(out[0], alone[j][0]), j
             assert np.array_equal(out[1], alone[j][1]), j
             assert out[2]["submit_ns"] <= out[2]["admit_ns"] <= out[2]["done_ns"]
-        # spot-check one against the oracle
-        i, b = reqs[0]
-        X, y, K, _ = runs[i]
-        want = orc.eval_hard(X, y, K, b)
-        assert np.array_equal(alone[0][0], want[0])
+        # and every result against the oracle
+        for j, (i, b) in enumerate(reqs):
+            X, y, K, _ = runs[i]
+            want = orc.eval_hard(X, y, K, b)
+            assert np.array_equal(alone[j][0], want[0]), j
+            assert np.array_equal(alone[j][1], want[1]), j
         st = ctx.serving_stats()
         assert st["active"] == 0 and st["queued"] == 0 and st["device_bytes_in_use"] == 0
         assert st["kernel_launches"] >= 1
