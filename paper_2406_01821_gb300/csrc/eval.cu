@@ -157,6 +157,7 @@ static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t 
     size_t set_b = align_up(sizeof(SetInfo) * std::max(b.P, 1), 256);
     size_t ord_b = align_up(sizeof(int32_t) * std::max(b.P, 1), 256);
     size_t st_b = 256;
+    const size_t le_b = K <= LAST_END_MAX_K ? align_up(sizeof(int32_t) * std::max(b.P, 1) * (size_t)K, 256) : 0;
     size_t out_b = 0;
     if (host_out) {
         out_b = align_up(sizeof(int32_t) * b.P, 256);
@@ -164,12 +165,13 @@ static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t 
         if (preds) out_b += align_up(sizeof(int32_t) * (size_t)b.P * N, 256);
     }
     char *base = nullptr;
-    RS_CUDA(cudaMallocAsync(&base, rec_b + set_b + ord_b + st_b + out_b, stream));
+    RS_CUDA(cudaMallocAsync(&base, rec_b + set_b + ord_b + st_b + le_b + out_b, stream));
     s.recs = (Rec *)base;
     s.sets = (SetInfo *)(base + rec_b);
     s.order = (int32_t *)(base + rec_b + set_b);
     s.status = (uint32_t *)(base + rec_b + set_b + ord_b);
-    s.out_dev = host_out ? (int32_t *)(base + rec_b + set_b + ord_b + st_b) : nullptr;
+    s.last_end = le_b ? (int32_t *)(base + rec_b + set_b + ord_b + st_b) : nullptr;
+    s.out_dev = host_out ? (int32_t *)(base + rec_b + set_b + ord_b + st_b + le_b) : nullptr;
     RS_CUDA(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream));
     return RS_OK;
 }
@@ -179,7 +181,9 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchD
                               const Scratch &s, int32_t *correct, int32_t *per_class,
                               int32_t *preds, cudaStream_t stream)
 {
-    PackOut po{s.recs, s.sets, s.order, s.status};
+    PackOut po;
+    po.recs = s.recs; po.sets = s.sets; po.order = s.order; po.status = s.status;
+    po.last_end = ds->K <= LAST_END_MAX_K ? s.last_end : nullptr;
     const int ver = effective_version(tc, *ds, preds != nullptr);
     const int pack_ver = ver == 5 ? 5 : (ver == 4 ? 4 : (ver >= 2 ? 2 : 1));
     count_launch(ctx, launch_pack(bd, ds->F, ds->K, tc.S(), pack_ver, po, stream));
@@ -200,6 +204,7 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchD
     a.preds = preds;
     a.groups = choose_groups(ctx, ds, tc, bd.P);
     a.status = s.status;
+    a.last_end = po.last_end;
     return launch_hard(ctx, ds, tc, a, stream);
 }
 

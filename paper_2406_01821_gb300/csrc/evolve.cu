@@ -533,6 +533,7 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
         (rc = B.get(&sc.recs, C)) ||
         (rc = B.get(&sc.sets, P)) || (rc = B.get(&sc.order, P)) || (rc = B.get(&sc.status, 64)))
         return rc;
+    if (ds.K <= LAST_END_MAX_K && (rc = B.get(&sc.last_end, (size_t)P * ds.K))) return rc;
     // tuning buffers (a, b, t copies, grads, Adam moments, per-set loss / dloss)
     const int T = cfg->tune_top;
     const size_t TC = (size_t)std::max(1, T) * RMAX * CMAX;

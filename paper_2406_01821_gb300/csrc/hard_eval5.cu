@@ -81,7 +81,12 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
         if (m >= count) break;
         const int p = a.order[group + m * G];
         const SetInfo si = a.sets[p];
-        const int rb = si.rec_begin, nrec = si.rec_end - si.rec_begin;
+        const int rb = si.rec_begin;
+        // one label in the tile and a default of another class: records after the set's last
+        // rule of that class cannot change its count
+        const int nrec = (uniform && a.last_end && si.deflt != kmin)
+                             ? min(a.last_end[(int64_t)p * a.K + kmin], si.rec_end - si.rec_begin)
+                             : si.rec_end - si.rec_begin;
 
         uint32_t *vr = vrows + warp * VS * 32;
         const uint32_t vr_off = (uint32_t)(reinterpret_cast<unsigned char *>(vr) - rs);

@@ -134,7 +134,7 @@ __global__ void k_pack_rules2(BatchDev b, int F, int K, int S, int form, Rec *re
 
 // One thread per set: offsets, default class, first empty rule (an empty rule fires for every
 // sample still unclaimed, so the set effectively ends there with that class as its default).
-__global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
+__global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, int32_t *last_end, uint32_t *status)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
@@ -156,6 +156,8 @@ __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
     }
     int c_begin = 0, c_end = 0;
     bool ok = true;
+    if (last_end)
+        for (int k = 0; k < K; ++k) last_end[(int64_t)p * K + k] = 0;
     for (int r = rb; r < re; ++r) {
         const int c0 = b.rule_cond_off[r], c1 = b.rule_cond_off[r + 1];
         if (c0 < 0 || c1 < c0 || c1 > b.C) { ok = false; break; }
@@ -165,10 +167,13 @@ __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, uint32_t *status)
         if (cls < 0 || cls >= K) { atomicOr(status, ST_BAD_CLASS); ok = false; break; }
         if (c1 == c0) { si.deflt = cls; break; }   // empty rule: fires on everything left
         c_end = c1;
+        if (last_end) last_end[(int64_t)p * K + cls] = c1 - c_begin;
     }
     if (!ok) {
         atomicOr(status, ST_BAD_OFFSETS);
         c_begin = c_end = 0;
+        if (last_end)
+            for (int k = 0; k < K; ++k) last_end[(int64_t)p * K + k] = 0;
     }
     si.rec_begin = c_begin;
     si.rec_end = c_end;
@@ -313,7 +318,7 @@ __global__ void k_order(const SetInfo *sets, int P, int32_t *order)
 int launch_pack(const BatchDev &b, int F, int K, int S, int ver, const PackOut &o, cudaStream_t stream)
 {
     int n = 0;
-    if (b.P > 0) { k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.status); ++n; }
+    if (b.P > 0) { k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.last_end, o.status); ++n; }
     if (b.R > 0 && ver == 5) {
         k_pack_rules5<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status);
         ++n;

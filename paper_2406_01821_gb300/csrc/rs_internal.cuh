@@ -202,11 +202,17 @@ uint32_t *host_status_slot();
 
 // ------------------------------------------------------------------------------ kernels / launchers
 
+// Sets of at most LAST_END_MAX_K classes also get, per class k, the end (relative to the set's
+// first record) of the set's last rule of class k: in a tile whose samples all have label k, no
+// record after it can change the count when the default is another class.
+constexpr int LAST_END_MAX_K = 64;
+
 struct PackOut {
-    Rec *recs;          // [C]
-    SetInfo *sets;      // [P]
-    int32_t *order;     // [P] set ids, most expensive first
-    uint32_t *status;   // device status word
+    Rec *recs = nullptr;          // [C]
+    SetInfo *sets = nullptr;      // [P]
+    int32_t *order = nullptr;     // [P] set ids, most expensive first
+    uint32_t *status = nullptr;   // device status word
+    int32_t *last_end = nullptr;  // [P*K] or null
 };
 
 // Validate + pack (+ order) a device batch. Enqueued on `stream`.
@@ -220,6 +226,7 @@ struct Scratch {
     int32_t *order = nullptr;
     uint32_t *status = nullptr;
     int32_t *out_dev = nullptr;   // device outputs when the caller's are host memory
+    int32_t *last_end = nullptr;  // [P*K] (K <= LAST_END_MAX_K) or null
 };
 
 struct HardArgs {
@@ -236,6 +243,7 @@ struct HardArgs {
     int32_t *preds;          // [P*N] or null
     int32_t groups;          // set groups (grid.y)
     uint32_t *status;
+    const int32_t *last_end; // [P*K] or null (see PackOut)
 };
 // Zero outputs and run the evaluator with tile configuration `tc`.
 rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,
