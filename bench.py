@@ -122,16 +122,16 @@ def hard_algorithmic_ops(batch, N):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("hard_eval.cu", "hard_eval4.cu", "hard_eval5.cu", "eval_core.cuh", "pack.cu",
+    for f in ("hard_eval.cu", "hard_eval4.cu", "hard_eval5.cu", "eval_rank.cuh", "eval_core.cuh", "pack.cu",
               "rs_internal.cuh", "tma.cuh"):
         with open(os.path.join(ROOT, "paper_2406_01821_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the evaluator from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def profiled_counters():
+    """The committed ncu summary of the evaluator if it was taken on the current kernel source
+    (else None): DRAM bytes per launch and the utilisation of its bottleneck pipes."""
     try:
         with open(PROFILE_SUMMARY) as fh:
             d = json.load(fh)
@@ -139,7 +139,7 @@ def profiled_traffic():
         return None
     if d.get("source_hash") != source_hash():
         return None
-    return d.get("dram_bytes_per_launch_full")
+    return d
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -553,7 +553,11 @@ def main():
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_ops = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
-    traffic = profiled_traffic()
+    counters = profiled_counters()
+    traffic = counters.get("dram_bytes_per_launch_full") if counters else None
+    pipes = ({"issue_active": counters["issue_active_pct"] / 100, "l1tex_throughput": counters["l1tex_throughput_pct"] / 100,
+              "alu_pipe": counters["alu_pipe_pct"] / 100, "source": "profiles/hard_eval_k_hard5_full.md (N=2^19)"}
+             if counters and "issue_active_pct" in counters else None)
     extras = {}
     if not args.no_extras and d.rank == 0:
         for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("serving", serving_leg)):
@@ -583,7 +587,7 @@ def main():
                          "frac": (ops / (kern_ms / 1e3)) / peak_ops, "traffic": traffic,
                          "kernel": KERNEL_OF_VERSION.get(rs.tile_configs()[res["tile"]]["form"], "k_hard"),
                          "kernel_ms": kern_ms,
-                         "ops_per_launch": ops,
+                         "ops_per_launch": ops, "bottleneck_pipes": pipes,
                          "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                         f"({peak_src} max clock)"},
             "cpu_baseline": cb,

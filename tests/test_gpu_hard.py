@@ -355,3 +355,17 @@ def test_wide_and_nonfinite_data_fall_back_from_ranks(ctx, orc):
         got = run_gpu(ctx, X, y, 2, b, preds=False, tile=22)
         want = orc.eval_hard(X, y, 2, b)
         assert_same(got, want, preds=False)
+
+
+@pytest.mark.parametrize("tile", RANKED)
+@pytest.mark.parametrize("K", [3, 100])
+def test_walk_stops_after_last_rule_of_tile_label(ctx, orc, tile, K):
+    """One-label tiles whose set defaults to another class stop after the set's last rule of that
+    label (K <= 64); with more classes the per-class table is not built."""
+    X, y = synth.gaussian_mixture(6000, 16, K, 3)
+    b = synth.random_rulesets(synth.quantile_table(X), K, 48, (1, 40), (1, 4), 3)
+    # a few sets with no rule of some classes, and sets whose only rules of a class come first
+    b.rule_class[: b.set_rule_off[4]] = 0
+    got = run_gpu(ctx, X, y, K, b, preds=False, tile=tile)
+    want = orc.eval_hard(X, y, K, b)
+    assert_same(got, want, preds=False)
