@@ -140,6 +140,113 @@ struct SoftKArgs {
     const uint32_t *status;          // no work if non-zero (malformed batch)
 };
 
+// Feature access for one 32-sample group: the lane's sample column either in global memory
+// (x[f] at col[f * stride]) or in a staged shared-memory tile [F][32] (stride 32).
+struct XView {
+    const float *col;
+    int64_t stride;
+    __device__ __forceinline__ float operator()(int f) const { return col[(int64_t)f * stride]; }
+};
+
+// Forward (and adjoint) of set p over one group of 32 samples, lane = sample n (valid: n < N).
+// lq/lu: the warp's per-rule log-probabilities; acc: its per-condition gradient sums.
+template <bool BWD>
+__device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, int R, int cb, int deflt,
+                                           int64_t n, bool valid, const XView &x, float (*lq)[32],
+                                           float (*lu)[32], float (*acc)[4], int lane, float &loss_s,
+                                           float &loss_c)
+{
+    const int yn = valid ? a.y[n] : -1;
+    // ---------------- forward
+    float lu_r = 0.f, lpy = -INFINITY;
+    for (int j = 0; j < R; ++j) {
+        const int r = rb + j;
+        const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
+        float s = 0.f;
+        for (int c = c0; c < c1; ++c) {
+            const SoftRec rc = a.recs[c];
+            const float lhs = rc.a * x(rc.f);
+            const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g) : rc.bt;
+            float u = (lhs - rhs) * a.inv_tau;
+            if (rc.meta & 2u) u = -u;
+            s += log_sigmoid(u);
+        }
+        lq[j][lane] = s;
+        lu[j][lane] = lu_r;
+        if (a.rule_class[r] == yn) lpy = log_add(lpy, s + lu_r);
+        lu_r += logf(-expm1f(s));
+    }
+    lu[R][lane] = lu_r;
+    if (deflt == yn) lpy = log_add(lpy, lu_r);
+    if (valid) kadd(loss_s, loss_c, -lpy);
+    if (a.probs && valid) {
+        const int64_t orig = a.perm[n];
+        for (int k = 0; k < a.K; ++k) {
+            float lpk = (deflt == k) ? lu_r : -INFINITY;
+            for (int j = 0; j < R; ++j)
+                if (a.rule_class[rb + j] == k) lpk = log_add(lpk, lq[j][lane] + lu[j][lane]);
+            a.probs[((int64_t)p * a.N + orig) * a.K + k] = expf(lpk);
+        }
+    }
+    if (!BWD) return;
+    // ---------------- adjoint
+    float lS = (deflt == yn) ? 0.f : -INFINITY;
+    float lT = (deflt == yn) ? -INFINITY : 0.f;
+    for (int j = R - 1; j >= 0; --j) {
+        const int r = rb + j;
+        const float lqj = lq[j][lane], luj = lu[j][lane];
+        const bool same = a.rule_class[r] == yn;
+        float gq = same ? -expf(lqj + luj + lT - lpy) : expf(lqj + luj + lS - lpy);
+        if (!valid) gq = 0.f;
+        const float l1q = logf(-expm1f(lqj));
+        lS = log_add(same ? lqj : -INFINITY, l1q + lS);
+        lT = log_add(same ? -INFINITY : lqj, l1q + lT);
+        const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
+        for (int c = c0; c < c1; ++c) {
+            const SoftRec rc = a.recs[c];
+            const float xf = x(rc.f);
+            const bool pair = rc.meta & 1u;
+            const float xg = pair ? x(rc.g) : 0.f;
+            const float lhs = rc.a * xf;
+            const float rhs = pair ? rc.bt * xg : rc.bt;
+            const float sg = (rc.meta & 2u) ? -1.f : 1.f;
+            const float u = sg * (lhs - rhs) * a.inv_tau;
+            const float du = gq * sigmoid_neg(u) * sg * a.inv_tau;
+            float ga = du * xf;
+            float gbt = pair ? -du * xg : -du;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ga += __shfl_xor_sync(FULL, ga, o);
+                gbt += __shfl_xor_sync(FULL, gbt, o);
+            }
+            const int ci = c - cb;
+            if (lane == (ci & 31)) {
+                kadd(acc[ci][0], acc[ci][1], ga);
+                kadd(acc[ci][2], acc[ci][3], gbt);
+            }
+        }
+    }
+}
+
+// Write a task's chunk partials (loss; gradient sums when BWD).
+template <bool BWD>
+__device__ __forceinline__ void soft_flush(const SoftKArgs &a, int p, int ch, int cb, int ce, float loss_s,
+                                           float (*acc)[4], int lane)
+{
+    float ls = loss_s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(FULL, ls, o);
+    if (lane == 0) a.part_loss[(int64_t)ch * a.P + p] = ls;
+    if (BWD) {
+        __syncwarp();
+        for (int i = lane; i < (ce - cb); i += 32) {
+            a.part_ga[(int64_t)ch * a.Ccap + cb + i] = acc[i][0];
+            a.part_gbt[(int64_t)ch * a.Ccap + cb + i] = acc[i][2];
+        }
+        __syncwarp();
+    }
+}
+
 template <bool BWD>
 __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
 {
@@ -162,9 +269,7 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
         const int p = (int)(task / a.nchunks);
         const int ch = (int)(task % a.nchunks);
         const int rb = a.set_rule_off[p], re = a.set_rule_off[p + 1];
-        const int R = re - rb;
         const int cb = a.rule_cond_off[rb], ce = a.rule_cond_off[re];
-        const int deflt = a.set_default[p];
         if (BWD) {
             for (int i = lane; i < (ce - cb); i += 32) {
                 acc[i][0] = 0.f; acc[i][1] = 0.f; acc[i][2] = 0.f; acc[i][3] = 0.f;
@@ -177,91 +282,97 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
         for (int64_t nb = s0; nb < s1; nb += 32) {
             const int64_t n = nb + lane;
             const bool valid = n < a.N;
-            const int yn = valid ? a.y[n] : -1;
-            const float *xcol = a.Xt + (valid ? n : 0);   // x[f] at xcol[f * n_pad]
-            // ---------------- forward
-            float lu_r = 0.f, lpy = -INFINITY;
-            for (int j = 0; j < R; ++j) {
-                const int r = rb + j;
-                const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
-                float s = 0.f;
-                for (int c = c0; c < c1; ++c) {
-                    const SoftRec rc = a.recs[c];
-                    const float lhs = rc.a * xcol[(int64_t)rc.f * a.n_pad];
-                    const float rhs = (rc.meta & 1u) ? rc.bt * xcol[(int64_t)rc.g * a.n_pad] : rc.bt;
-                    float u = (lhs - rhs) * a.inv_tau;
-                    if (rc.meta & 2u) u = -u;
-                    s += log_sigmoid(u);
+            const XView x{a.Xt + (valid ? n : 0), a.n_pad};
+            soft_group<BWD>(a, p, rb, re - rb, cb, a.set_default[p], n, valid, x, lq, lu, acc, lane, loss_s,
+                            loss_c);
+        }
+        soft_flush<BWD>(a, p, ch, cb, ce, loss_s, acc, lane);
+    }
+}
+
+// The same evaluation with the warps of a CTA on SOFT_TW consecutive sets over the same chunk:
+// the features of each 32-sample group are staged once per CTA in shared memory (double-buffered
+// asynchronous copies), so condition loads are shared-memory reads. Per-set results are identical
+// to k_soft (same per-sample arithmetic and summation order).
+constexpr int SOFT_TW = 8;
+constexpr int SOFT_TILE_STATIC = 256;   // bytes kept for the kernel's static shared memory
+
+__device__ __forceinline__ void stage_group(float *dst, const float *Xt, int64_t n_pad, int F, int64_t nb)
+{
+    // F rows x 32 samples, 16-byte pieces
+    for (int i = threadIdx.x; i < F * 8; i += blockDim.x) {
+        const int f = i >> 3, q = i & 7;
+        const float *src = Xt + (int64_t)f * n_pad + nb + 4 * q;
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + f * 32 + 4 * q);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <bool BWD>
+__global__ void __launch_bounds__(SOFT_TW * 32) k_soft_tile(SoftKArgs a, int F)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int64_t s_task;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t set_groups = (a.P + SOFT_TW - 1) / SOFT_TW;
+    const int64_t tasks = set_groups * a.nchunks;
+    const size_t per_warp = (size_t)(2 * a.maxR + 1) * 32 + (size_t)a.maxC * 4;
+    float *base_w = sm + per_warp * w;
+    float(*lq)[32] = reinterpret_cast<float(*)[32]>(base_w);
+    float(*lu)[32] = reinterpret_cast<float(*)[32]>(base_w + (size_t)a.maxR * 32);
+    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * 32);
+    float *xbuf = sm + per_warp * SOFT_TW;            // [2][F][32]
+    if (*a.status) return;
+
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_task = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int64_t task = s_task;
+        if (task >= tasks) break;
+        const int g = (int)(task / a.nchunks);
+        const int ch = (int)(task % a.nchunks);
+        const int p = g * SOFT_TW + w;
+        const bool active = p < a.P;
+        int rb = 0, R = 0, cb = 0, ce = 0, deflt = 0;
+        if (active) {
+            rb = a.set_rule_off[p];
+            const int re = a.set_rule_off[p + 1];
+            R = re - rb;
+            cb = a.rule_cond_off[rb];
+            ce = a.rule_cond_off[re];
+            deflt = a.set_default[p];
+            if (BWD) {
+                for (int i = lane; i < (ce - cb); i += 32) {
+                    acc[i][0] = 0.f; acc[i][1] = 0.f; acc[i][2] = 0.f; acc[i][3] = 0.f;
                 }
-                lq[j][lane] = s;
-                lu[j][lane] = lu_r;
-                if (a.rule_class[r] == yn) lpy = log_add(lpy, s + lu_r);
-                lu_r += logf(-expm1f(s));
-            }
-            lu[R][lane] = lu_r;
-            if (deflt == yn) lpy = log_add(lpy, lu_r);
-            if (valid) kadd(loss_s, loss_c, -lpy);
-            if (a.probs && valid) {
-                const int64_t orig = a.perm[n];
-                for (int k = 0; k < a.K; ++k) {
-                    float lpk = (deflt == k) ? lu_r : -INFINITY;
-                    for (int j = 0; j < R; ++j)
-                        if (a.rule_class[rb + j] == k) lpk = log_add(lpk, lq[j][lane] + lu[j][lane]);
-                    a.probs[((int64_t)p * a.N + orig) * a.K + k] = expf(lpk);
-                }
-            }
-            if (!BWD) continue;
-            // ---------------- adjoint
-            float lS = (deflt == yn) ? 0.f : -INFINITY;
-            float lT = (deflt == yn) ? -INFINITY : 0.f;
-            for (int j = R - 1; j >= 0; --j) {
-                const int r = rb + j;
-                const float lqj = lq[j][lane], luj = lu[j][lane];
-                const bool same = a.rule_class[r] == yn;
-                float gq = same ? -expf(lqj + luj + lT - lpy) : expf(lqj + luj + lS - lpy);
-                if (!valid) gq = 0.f;
-                const float l1q = logf(-expm1f(lqj));
-                lS = log_add(same ? lqj : -INFINITY, l1q + lS);
-                lT = log_add(same ? -INFINITY : lqj, l1q + lT);
-                const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
-                for (int c = c0; c < c1; ++c) {
-                    const SoftRec rc = a.recs[c];
-                    const float xf = xcol[(int64_t)rc.f * a.n_pad];
-                    const bool pair = rc.meta & 1u;
-                    const float xg = pair ? xcol[(int64_t)rc.g * a.n_pad] : 0.f;
-                    const float lhs = rc.a * xf;
-                    const float rhs = pair ? rc.bt * xg : rc.bt;
-                    const float sg = (rc.meta & 2u) ? -1.f : 1.f;
-                    const float u = sg * (lhs - rhs) * a.inv_tau;
-                    const float du = gq * sigmoid_neg(u) * sg * a.inv_tau;
-                    float ga = du * xf;
-                    float gbt = pair ? -du * xg : -du;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        ga += __shfl_xor_sync(FULL, ga, o);
-                        gbt += __shfl_xor_sync(FULL, gbt, o);
-                    }
-                    const int ci = c - cb;
-                    if (lane == (ci & 31)) {
-                        kadd(acc[ci][0], acc[ci][1], ga);
-                        kadd(acc[ci][2], acc[ci][3], gbt);
-                    }
-                }
+                __syncwarp();
             }
         }
-        // chunk partials
-        float ls = loss_s;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(FULL, ls, o);
-        if (lane == 0) a.part_loss[(int64_t)ch * a.P + p] = ls;
-        if (BWD) {
-            __syncwarp();
-            for (int i = lane; i < (ce - cb); i += 32) {
-                a.part_ga[(int64_t)ch * a.Ccap + cb + i] = acc[i][0];
-                a.part_gbt[(int64_t)ch * a.Ccap + cb + i] = acc[i][2];
+        float loss_s = 0.f, loss_c = 0.f;
+        const int64_t s0 = (int64_t)ch * a.chunk;
+        const int64_t s1 = min(s0 + a.chunk, a.N);
+        const int ngroups = (int)((s1 - s0 + 31) / 32);
+        stage_group(xbuf, a.Xt, a.n_pad, F, s0);
+        for (int gi = 0; gi < ngroups; ++gi) {
+            const int64_t nb = s0 + 32 * (int64_t)gi;
+            if (gi + 1 < ngroups) {
+                stage_group(xbuf + ((gi + 1) & 1) * F * 32, a.Xt, a.n_pad, F, nb + 32);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
-            __syncwarp();
+            __syncthreads();
+            if (active) {
+                const int64_t n = nb + lane;
+                const bool valid = n < a.N;
+                const XView x{xbuf + (gi & 1) * F * 32 + lane, 32};
+                soft_group<BWD>(a, p, rb, R, cb, deflt, n, valid, x, lq, lu, acc, lane, loss_s, loss_c);
+            }
+            __syncthreads();              // the buffer is restaged two groups later
         }
+        if (active) soft_flush<BWD>(a, p, ch, cb, ce, loss_s, acc, lane);
     }
 }
 
@@ -382,7 +493,11 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
             set_error("soft evaluation rejected the batch: %s", status_text(*hs).c_str());
         }
     }
-    const size_t smem = sizeof(float) * SOFT_W * ((size_t)(2 * k.maxR + 1) * 32 + (size_t)k.maxC * 4);
+    const size_t per_warp = sizeof(float) * ((size_t)(2 * k.maxR + 1) * 32 + (size_t)k.maxC * 4);
+    const size_t smem = per_warp * SOFT_W;
+    // the staged-tile kernel when its per-CTA footprint (8 warps + two feature tiles) fits
+    const size_t smem_tile = per_warp * SOFT_TW + sizeof(float) * 2 * 32 * (size_t)s.F;
+    const bool tiled = s.F <= 128 && smem_tile + SOFT_TILE_STATIC <= ctx->smem_optin;
     if (rc == RS_OK && smem > ctx->smem_optin) {
         rc = RS_ERR_TOO_LARGE;
         set_error("soft evaluation: sets too large for shared memory");
@@ -392,15 +507,31 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
         std::call_once(once, [&] {
             cudaFuncSetAttribute(k_soft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
             cudaFuncSetAttribute(k_soft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
+            // the staged-tile kernel has a little static shared memory of its own
+            cudaFuncSetAttribute(k_soft_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ctx->smem_optin - SOFT_TILE_STATIC);
+            cudaFuncSetAttribute(k_soft_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ctx->smem_optin - SOFT_TILE_STATIC);
+            cudaGetLastError();
         });
         int per_sm = 1;
-        if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true>, SOFT_W * 32, smem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false>, SOFT_W * 32, smem);
+        if (tiled) {
+            if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<true>, SOFT_TW * 32, smem_tile);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<false>, SOFT_TW * 32, smem_tile);
+        } else {
+            if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true>, SOFT_W * 32, smem);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false>, SOFT_W * 32, smem);
+        }
         const int grid = ctx->sm_count * std::max(1, per_sm);
         {
             TimedLaunch tl(ctx, TK_SOFT, stream);
-            if (bwd) k_soft<true><<<grid, SOFT_W * 32, smem, stream>>>(k);
-            else k_soft<false><<<grid, SOFT_W * 32, smem, stream>>>(k);
+            if (tiled) {
+                if (bwd) k_soft_tile<true><<<grid, SOFT_TW * 32, smem_tile, stream>>>(k, s.F);
+                else k_soft_tile<false><<<grid, SOFT_TW * 32, smem_tile, stream>>>(k, s.F);
+            } else {
+                if (bwd) k_soft<true><<<grid, SOFT_W * 32, smem, stream>>>(k);
+                else k_soft<false><<<grid, SOFT_W * 32, smem, stream>>>(k);
+            }
         }
         k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
                                                                1.0f / (float)s.N, s.loss, s.status);

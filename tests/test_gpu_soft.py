@@ -65,6 +65,18 @@ def test_soft_small_vs_oracle(ctx, orc, seed):
     check_against_oracle(got, ref)
 
 
+@pytest.mark.parametrize("F,P", [(160, 12), (33, 29)])
+def test_soft_wide_and_odd_shapes_vs_oracle(ctx, orc, F, P):
+    """F > 128 runs the per-warp kernel (features read from global memory); F <= 128 the
+    staged-tile kernel, here with a set count that leaves idle warps in the last CTA group."""
+    X, y = synth.two_class_gaussian(2333, F, 5)
+    b = reachable(synth.random_rulesets(synth.quantile_table(X), 2, P, (1, 8), (1, 4), 5, pair_prob=0.3))
+    dl = np.random.default_rng(5).uniform(-1, 2, b.P)
+    got = soft_gpu(ctx, X, y, 2, b, 0.1, dl)
+    ref = orc.soft(X, y, 2, b, 0.1, dloss=dl, want_mag=True)
+    check_against_oracle(got, ref)
+
+
 def test_soft_multiclass_probs(ctx, orc):
     rng = np.random.default_rng(4)
     X, _ = synth.gaussian_mixture(777, 6, 4, 4)
