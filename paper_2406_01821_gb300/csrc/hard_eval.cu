@@ -260,7 +260,7 @@ const TileConfig kConfigs[] = {
     {8, 4, 8, 2}, {9, 4, 16, 2}, {10, 2, 16, 2},
     {11, 4, 8, 3}, {12, 4, 16, 3}, {13, 2, 16, 3}, {14, 2, 32, 3}, {15, 4, 32, 3},
     {16, 4, 8, 4}, {17, 4, 16, 4}, {18, 4, 32, 4}, {19, 2, 16, 4}, {20, 2, 32, 4},
-    {21, 4, 16, 5}, {22, 4, 32, 5}, {23, 4, 24, 5},
+    {21, 4, 16, 5}, {22, 4, 32, 5},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 

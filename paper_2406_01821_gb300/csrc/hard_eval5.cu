@@ -116,7 +116,7 @@ size_t hard5_smem_bytes(int F, int W)
 {
     const int Fb = F < 256 ? F : 256;
     const size_t Frows = (size_t)((F + Fb - 1) / Fb) * Fb;
-    const size_t vs = W >= 32 ? vslots<32>() : vslots<16>();   // 16 slots below 32 warps
+    const size_t vs = W >= 32 ? vslots<32>() : vslots<16>();
     return Frows * T * (4 + 2 + 4) + (size_t)W * 32 * 16 + (size_t)W * vs * 32 * 4 + 16;
 }
 
@@ -153,7 +153,6 @@ rs_status launch_hard5(Ctx *ctx, Dataset *ds, int W, const HardArgs &a, cudaStre
         RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
     if (W == 16) return launch5_t<16>(ctx, ds, a, stream);
-    if (W == 24) return launch5_t<24>(ctx, ds, a, stream);
     if (W == 32) return launch5_t<32>(ctx, ds, a, stream);
     return RS_ERR_INVALID;
 }
