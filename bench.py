@@ -263,10 +263,29 @@ def soft_leg(args, dev):
     prof = ctx.profile(reset=True)
     ctx.close()
     cs = w.batch.nominal_conditions() * w.N
+    kern_ms = prof["soft_ms"] / max(1, prof["soft_launches"])
+    xu = soft_transcendentals(w.batch, w.N)
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    xu_peak = sms * 16 * peaks.get("sm_max_mhz", 2070.0) * 1e6
     return {"workload": w.name, "ms_per_step": ms, "condition_samples_per_s": cs / (ms / 1e3),
             "rule_set_samples_per_s": w.batch.P * w.N / (ms / 1e3),
-            "kernel_ms": prof["soft_ms"] / max(1, prof["soft_launches"]), "steps": steps,
-            "what": "forward + adjoint (loss and gradients w.r.t. a, b, t of every condition)"}
+            "kernel_ms": kern_ms, "steps": steps,
+            "what": "forward + adjoint (loss and gradients w.r.t. a, b, t of every condition)",
+            "roofline": {"bound": "xu", "achieved": xu / (kern_ms / 1e3) / 1e12, "peak": xu_peak / 1e12,
+                         "unit": "T transcendentals/s", "frac": xu / (kern_ms / 1e3) / xu_peak,
+                         "transcendentals_per_pass": xu,
+                         "peak_source": f"{sms} SMs x 16 XU lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                        f"({peak_src} max clock)"}}
+
+
+def soft_transcendentals(batch, N):
+    """Algorithmic transcendentals of one forward + adjoint pass: per condition and sample an
+    exp and a log1p (log-sigmoid) and an exp (sigmoid of -u); per rule and sample an expm1 and a
+    log (log(1 - q)) forward and again in the adjoint, an exp (the gradient of lq), two
+    log-sum-exps (exp + log1p each) in the adjoint and one forward for rules of the sample's
+    class (counted for every rule: an upper bound on the forward share)."""
+    return N * (3 * batch.C + 11 * batch.R)
 
 
 def evolution_leg(args, dev):
