@@ -414,6 +414,7 @@ def serving_leg(args, dev):
         t_arr_ns[j] = time.monotonic_ns() - int((time.perf_counter() - ta) * 1e9)
 
     lat_srv = [0.0] * M
+    split = np.zeros((M, 3))      # arrival -> submit returned, -> admitted, -> done (seconds)
 
     def fin_served():
         last = 0
@@ -421,6 +422,8 @@ def serving_leg(args, dev):
             i, hb, _ = reqs[j]
             out = ctx.poll(tickets[j], hb.P, int(runs_K[i]), timeout_us=120_000_000)
             lat_srv[j] = (out[2]["done_ns"] - t_arr_ns[j]) / 1e9
+            split[j] = [(out[2]["submit_ns"] - t_arr_ns[j]) / 1e9, (out[2]["admit_ns"] - out[2]["submit_ns"]) / 1e9,
+                        (out[2]["done_ns"] - out[2]["admit_ns"]) / 1e9]
             last = max(last, out[2]["done_ns"])
         return time.perf_counter()
     t_end, t_start = drive(submit, fin_served)
@@ -447,6 +450,9 @@ def serving_leg(args, dev):
     return {"workload": f"serving {M} requests from 256 runs, Poisson arrivals at 0.7 x plain capacity, "
                         "40 GB budget",
             "served": summ(lat_srv, dur_srv), "plain_one_launch_per_request": summ(lat_plain, dur_plain),
+            "served_p50_split_ms": {"arrival_to_queued": float(np.percentile(split[:, 0], 50) * 1e3),
+                                    "queued_to_admitted": float(np.percentile(split[:, 1], 50) * 1e3),
+                                    "admitted_to_done": float(np.percentile(split[:, 2], 50) * 1e3)},
             "plain_service_ms": service * 1e3, "persistent_kernel_launches": stats["kernel_launches"],
             "capacity_condition_evals_per_s": {"served_all_at_once": total / burst_srv,
                                                "plain_back_to_back": total / burst_plain}}

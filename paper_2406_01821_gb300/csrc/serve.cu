@@ -20,10 +20,12 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <thread>
 #include <unordered_map>
 
 #include "eval_core.cuh"
+#include "eval_rank.cuh"
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -31,13 +33,20 @@ namespace rs {
 namespace {
 
 constexpr int SV = 4;                 // samples per lane
-constexpr int SW = 16;                // warps per CTA (one CTA per SM; registers and shared
-                                      // memory are left for the packing kernels of new requests)
+constexpr int SW = 32;                // warps per CTA: one CTA per SM on all but SPARE_SMS SMs
 constexpr int SS = 32 * SV;           // samples per tile (unit)
 constexpr int SERVE_MAX_F = 256;      // shared x tile [F][128]: 128 KB
+constexpr int SERVE_RANK_MAX_F = 128; // rank-coded units: x, ranks, reversed ranks, sorted [F][128]
+constexpr int SVS = 8;                // pass-row slots per warp of rank-coded units
+constexpr size_t TILE_BYTES = (size_t)SERVE_MAX_F * SS * 4 > (size_t)SERVE_RANK_MAX_F * SS * 10
+                                  ? (size_t)SERVE_MAX_F * SS * 4
+                                  : (size_t)SERVE_RANK_MAX_F * SS * 10;
+constexpr size_t SERVE_SMEM = TILE_BYTES + (size_t)SW * 64 * 16 + (size_t)SW * SVS * 32 * 4;
 constexpr int MAX_SLOTS = 2048;
-constexpr int GROUP_SETS = 128;       // sets per unit: eight per warp
-constexpr int SPARE_SMS = 0;
+constexpr int GROUP_SETS = 128;       // sets per unit: four per warp
+constexpr int GROUP_SETS_RANKED = 256;  // rank-coded units: their tile staging is heavier
+constexpr int SERVE_RANK_MIN_P = 64;    // smaller requests keep the sign-mask units
+constexpr int SPARE_SMS = 4;          // left to the packing kernels of new requests
 constexpr uint64_t IDLE_NS = 20000000ull;   // persistent kernel idle limit: 20 ms
 // claim word: epoch (24 bits) | next unit (20 bits) | units (20 bits)
 constexpr int CW_NEXT = 20, CW_EPOCH = 40;
@@ -54,6 +63,10 @@ struct __align__(16) ReqDesc {
     int32_t P, tiles, groups, finite;
     int32_t *correct, *per_class;
     uint64_t epoch;
+    const uint8_t *Rk;                  // rank tables (rank-coded units), or null
+    const float *Us;
+    const int32_t *last_end;            // [P*K] per-class last rule ends, or null
+    int32_t ranked, gsets;              // gsets: sets per unit
 };
 
 struct ServeArgs {
@@ -74,46 +87,126 @@ __device__ __forceinline__ uint64_t now_ns()
     return t;
 }
 
-__global__ void __launch_bounds__(SW * 32) k_serve(ServeArgs a)
+// One unit on a dataset with rank tables: stage x, ranks, reversed ranks and the sorted columns
+// of the tile, then walk sets [set0, set1) with the rank-coded evaluator.
+__device__ __forceinline__ void serve_unit_ranked(const ReqDesc &d, int tile, int set0, int set1,
+                                                  unsigned char *smem, uint4 *st, uint32_t *vr, int *s_next)
+{
+    using namespace rank;
+    const int F = d.F, lane = threadIdx.x & 31;
+    unsigned char *xs = smem;                                  // float [F][T]
+    unsigned char *rs = xs + (size_t)F * T * 4;                // u8 [F][T], reversed after it
+    float *us = reinterpret_cast<float *>(rs + (size_t)F * T * 2);
+    const int64_t col0 = (int64_t)tile * T;
+    for (int i = threadIdx.x; i < F * (T / 4); i += blockDim.x) {
+        const int f = i / (T / 4), c4 = i % (T / 4);
+        reinterpret_cast<float4 *>(xs)[i] = *reinterpret_cast<const float4 *>(d.Xt + (int64_t)f * d.n_pad + col0 + 4 * c4);
+    }
+    for (int i = threadIdx.x; i < F * (T / 16); i += blockDim.x) {
+        const int f = i / (T / 16), c16 = i % (T / 16);
+        const uint4 w = *reinterpret_cast<const uint4 *>(d.Rk + (int64_t)f * d.n_pad + col0 + 16 * c16);
+        reinterpret_cast<uint4 *>(rs)[i] = w;
+        reinterpret_cast<uint4 *>(rs + (size_t)F * T)[i] =
+            make_uint4(w.x ^ 0x7F7F7F7Fu, w.y ^ 0x7F7F7F7Fu, w.z ^ 0x7F7F7F7Fu, w.w ^ 0x7F7F7F7Fu);
+    }
+    const float4 *usrc = reinterpret_cast<const float4 *>(d.Us + (int64_t)tile * F * T);
+    for (int i = threadIdx.x; i < F * (T / 4); i += blockDim.x) reinterpret_cast<float4 *>(us)[i] = usrc[i];
+    const int32_t *yl = d.y + col0 + lane * 4;
+    const int64_t t_last = min(col0 + T, d.N) - 1;
+    const int kmin = d.y[col0], kmax = d.y[t_last];
+    const bool uniform = kmin == kmax;
+    const uint32_t claimed0 = class_bytes(yl, -1);
+    const uint32_t rev_off = (uint32_t)F * T;
+    const uint32_t vr_off = (uint32_t)(reinterpret_cast<unsigned char *>(vr) - rs);
+    const unsigned char *rl = rs + lane * 4, *xl = xs + lane * 16;
+    __syncthreads();
+    while (true) {
+        int m = 0;
+        if (lane == 0) m = atomicAdd(s_next, 1);
+        m = __shfl_sync(FULL, m, 0);
+        if (set0 + m >= set1) break;
+        const int p = __ldcg(d.order + set0 + m);
+        const int4 t = __ldcg(reinterpret_cast<const int4 *>(d.sets + p));
+        const int rb = t.x, deflt = t.z;
+        // one label in the tile and a default of another class: records after the set's last
+        // rule of that class cannot change its count
+        const int nrec = (uniform && d.last_end && deflt != kmin)
+                             ? min(__ldcg(d.last_end + (int64_t)p * d.K + kmin), t.y - t.x)
+                             : t.y - t.x;
+        const uint32_t hit =
+            uniform ? walk_set<true, SVS>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, kmin, rl, xl, yl,
+                                          claimed0, deflt)
+                    : walk_set<false, SVS>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, -2, rl, xl, yl,
+                                           claimed0, deflt);
+        const int hits = __reduce_add_sync(FULL, __popc(hit));
+        if (lane == 0 && hits) atomicAdd(&d.correct[p], hits);
+        if (d.per_class) {
+            if (uniform) {
+                if (lane == 0 && hits) atomicAdd(&d.per_class[(int64_t)p * d.K + kmin], hits);
+            } else {
+                for (int k = kmin; k <= kmax; ++k) {
+                    const int c = __reduce_add_sync(FULL, __popc(hit & class_bytes(yl, k)));
+                    if (lane == 0 && c) atomicAdd(&d.per_class[(int64_t)p * d.K + k], c);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SW * 32, 1) k_serve(ServeArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     float *xs = reinterpret_cast<float *>(smem);                                   // [F][SS]
-    uint4 *stage_all = reinterpret_cast<uint4 *>(smem + SERVE_MAX_F * SS * sizeof(float));
+    uint4 *stage_all = reinterpret_cast<uint4 *>(smem + TILE_BYTES);
+    uint32_t *vrows = reinterpret_cast<uint32_t *>(stage_all + SW * 64);            // [SW][SVS][32]
     __shared__ int s_slot, s_unit, s_next;
+    __shared__ ReqDesc sd;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint4 *st = stage_all + warp * 64;
 
     while (true) {
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
+            // Warp 0 claims the next unit, oldest admitted request first (requests drain in
+            // arrival order while the tail of one overlaps the start of the next). The lanes read
+            // 32 claim words at a time; the first open request wins a compare-and-swap.
             int slot = -1, unit = -1;
             uint64_t idle0 = 0;
-            int misses = 0;
             while (true) {
-                if (*a.stop) break;
-                const int n = *a.nactive;
-                if (n > 0) {
-                    const int i = (int)(atomicAdd(a.rr, 1u) % (unsigned)n);
-                    const int sl = a.active[i];
-                    if (sl >= 0 && sl < MAX_SLOTS) {
-                        unsigned long long w = *reinterpret_cast<volatile unsigned long long *>(a.claims + sl);
-                        while (((w >> CW_NEXT) & CW_MASK) < (w & CW_MASK)) {
-                            const unsigned long long old = atomicCAS(a.claims + sl, w, w + (1ull << CW_NEXT));
-                            if (old == w) { slot = sl; unit = (int)((w >> CW_NEXT) & CW_MASK); break; }
-                            w = old;
+                // host-written words: lane 0 reads them, so every lane takes the same branches
+                if (__shfl_sync(core::FULL, lane == 0 ? *a.stop : 0, 0)) break;
+                const int n = __shfl_sync(core::FULL, lane == 0 ? *a.nactive : 0, 0);
+                for (int base = 0; base < n && slot < 0; base += 32) {
+                    const int i = base + lane;
+                    const int sl = i < n ? a.active[i] : -1;
+                    const bool ok = sl >= 0 && sl < MAX_SLOTS;
+                    unsigned long long w = ok ? *reinterpret_cast<volatile unsigned long long *>(a.claims + sl) : 0ull;
+                    uint32_t open = __ballot_sync(core::FULL, ok && ((w >> CW_NEXT) & CW_MASK) < (w & CW_MASK));
+                    while (open && slot < 0) {
+                        const int j = __ffs(open) - 1;
+                        int got = -1;
+                        if (lane == j) {
+                            while (((w >> CW_NEXT) & CW_MASK) < (w & CW_MASK)) {
+                                const unsigned long long old = atomicCAS(a.claims + sl, w, w + (1ull << CW_NEXT));
+                                if (old == w) { got = (int)((w >> CW_NEXT) & CW_MASK); break; }
+                                w = old;
+                            }
                         }
-                        if (slot >= 0) break;
+                        got = __shfl_sync(core::FULL, got, j);
+                        if (got >= 0) { slot = __shfl_sync(core::FULL, sl, j); unit = got; }
+                        open &= ~(1u << j);
                     }
-                    if (++misses < 2 * n) continue;     // try the other active requests first
                 }
-                misses = 0;
-                const uint64_t tn = now_ns();
+                if (slot >= 0) break;
+                const uint64_t tn = __shfl_sync(core::FULL, now_ns(), 0);
                 if (idle0 == 0) idle0 = tn;
                 else if (tn - idle0 > IDLE_NS) break;
                 __nanosleep(2000);
             }
-            s_slot = slot;
-            s_unit = unit;
-            s_next = 0;
+            if (lane == 0) {
+                s_slot = slot;
+                s_unit = unit;
+                s_next = 0;
+            }
         }
         __syncthreads();
         const int slot = s_slot, unit = s_unit;
@@ -121,15 +214,27 @@ __global__ void __launch_bounds__(SW * 32) k_serve(ServeArgs a)
         __threadfence();
         // Descriptors and per-request buffers are reused while this kernel lives: read them
         // through L2 (.cg), never from a possibly stale L1 line.
-        ReqDesc d;
-        {
-            const int4 *src = reinterpret_cast<const int4 *>(a.table + slot);
-            int4 *dst = reinterpret_cast<int4 *>(&d);
-#pragma unroll
-            for (int i = 0; i < (int)(sizeof(ReqDesc) / 16); ++i) dst[i] = __ldcg(src + i);
-        }
+        if (threadIdx.x < (int)(sizeof(ReqDesc) / 16))
+            reinterpret_cast<int4 *>(&sd)[threadIdx.x] =
+                __ldcg(reinterpret_cast<const int4 *>(a.table + slot) + threadIdx.x);
+        __syncthreads();
+        const ReqDesc &d = sd;       // shared: keeps the descriptor out of registers
         const int tile = unit / d.groups, grp = unit % d.groups;
-        const int set0 = grp * GROUP_SETS, set1 = min(d.P, set0 + GROUP_SETS);
+        const int set0 = grp * d.gsets, set1 = min(d.P, set0 + d.gsets);
+        if (d.ranked) {
+            serve_unit_ranked(d, tile, set0, set1, smem, st, vrows + warp * SVS * 32, &s_next);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const int fin = atomicAdd(&a.done[slot], 1) + 1;
+                if (fin == d.tiles * d.groups) {
+                    __threadfence_system();
+                    a.host_flag[slot] = d.epoch;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         // stage the tile x[0..F)[tile*SS .. +SS) (n_pad is a multiple of 256)
         const int64_t col0 = (int64_t)tile * SS;
         const int nvec = d.F * (SS / 4);
@@ -213,6 +318,18 @@ __global__ void k_set_claim(unsigned long long *claims, int slot, unsigned long 
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Requests on datasets with rank tables use the rank-coded evaluator when they have enough sets
+// to amortise its tile staging (x, ranks and sorted columns, and one search per cut and tile).
+bool serve_ranked(const Dataset &ds, int P)
+{
+    return ds.ranked && ds.F <= SERVE_RANK_MAX_F && P >= SERVE_RANK_MIN_P;
+}
+int64_t serve_groups(const Dataset &ds, int P)
+{
+    const int g = serve_ranked(ds, P) ? GROUP_SETS_RANKED : GROUP_SETS;
+    return std::max<int64_t>(1, (P + g - 1) / g);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ host side
@@ -223,7 +340,7 @@ struct Request {
     int32_t P = 0, R = 0, C = 0, K = 0;
     int32_t kind = 0;
     void *h_stage = nullptr;              // pinned copy of the batch arrays
-    size_t stage_bytes = 0;
+    size_t stage_bytes = 0, stage_cap = 0, result_cap = 0;   // pinned buffer capacities
     size_t off[10] = {};
     size_t device_bytes = 0;
     void *d_buf = nullptr;
@@ -267,9 +384,42 @@ struct Server {
     int grid = 0;
     size_t smem = 0;
     int64_t launches = 0;
+    // pinned host buffers of finished requests, reused by new ones (pinning memory is slow and
+    // can stall other CUDA calls): capacity -> buffer
+    std::mutex pool_mu;
+    std::multimap<size_t, void *> pinned_free;
 };
 
 static rs_status server_start(Ctx *ctx, Server **out);
+// Pinned staging pool -------------------------------------------------------------------------
+
+static void *pinned_get(Server *s, size_t bytes, size_t *cap)
+{
+    {
+        std::lock_guard<std::mutex> lk(s->pool_mu);
+        auto it = s->pinned_free.lower_bound(bytes);
+        if (it != s->pinned_free.end() && it->first <= 4 * bytes + 65536) {
+            void *p = it->second;
+            *cap = it->first;
+            s->pinned_free.erase(it);
+            return p;
+        }
+    }
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    *cap = c;
+    return p;
+}
+
+static void pinned_put(Server *s, void *p, size_t cap)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(s->pool_mu);
+    s->pinned_free.emplace(cap, p);
+}
+
 static void server_loop(Server *s);
 
 static rs_status server_get(Ctx *ctx, Server **out)
@@ -310,7 +460,7 @@ static rs_status server_start(Ctx *ctx, Server **out)
     memset(s->h_flag, 0, sizeof(unsigned long long) * MAX_SLOTS);
     *s->h_stop = 0;
     for (int i = MAX_SLOTS - 1; i >= 0; --i) s->free_slots.push_back(i);
-    s->smem = SERVE_MAX_F * SS * sizeof(float) + SW * 64 * sizeof(uint4);
+    s->smem = SERVE_SMEM;
     if ((e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem)))
         return fail(e, "k_serve attribute");
     // one CTA per SM: the rest of each SM stays available to the packing kernels of new requests
@@ -338,6 +488,8 @@ void server_shutdown(Ctx *ctx)
         Request &r = *kv.second;
         if (r.h_stage) cudaFreeHost(r.h_stage);
         if (r.h_correct) cudaFreeHost(r.h_correct);
+        r.h_stage = nullptr;
+        r.h_correct = nullptr;
         if (r.d_buf) cudaFree(r.d_buf);
         if (r.ev) cudaEventDestroy(r.ev);
     }
@@ -346,6 +498,7 @@ void server_shutdown(Ctx *ctx)
     cudaFree(s->d_active);
     cudaFree(s->d_rr);
     cudaFree(s->d_done);
+    for (auto &kv : s->pinned_free) cudaFreeHost(kv.second);
     cudaFreeHost(s->h_flag);
     cudaFreeHost(s->h_stop);
     cudaEventDestroy(s->kevent);
@@ -364,6 +517,7 @@ static size_t request_device_bytes(int64_t P, int64_t R, int64_t C, int64_t K)
     b += align256(16 * std::max<int64_t>(C, 1)) + align256(16 * std::max<int64_t>(P, 1)) +
          align256(4 * std::max<int64_t>(P, 1));                          // records, sets, order
     b += align256(4 * P) + align256(4 * P * K) + 256;                   // outputs, status
+    if (K <= LAST_END_MAX_K) b += align256(4 * P * K);                  // per-class last rule ends
     return b;
 }
 
@@ -391,7 +545,7 @@ rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint6
                   (unsigned long long)ctx->budget);
         return RS_ERR_TOO_LARGE;
     }
-    const int64_t units = ((ds->N + SS - 1) / SS) * std::max<int64_t>(1, (b->P + GROUP_SETS - 1) / GROUP_SETS);
+    const int64_t units = ((ds->N + SS - 1) / SS) * serve_groups(*ds, b->P);
     if (units > (int64_t)CW_MASK) { set_error("request too large to serve (%lld work units)", (long long)units); return RS_ERR_TOO_LARGE; }
     // copy the batch into pinned staging: the caller may free its arrays on return
     const size_t P = b->P, R = b->R, C = b->C;
@@ -401,15 +555,35 @@ rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint6
     size_t tot = 0;
     for (int i = 0; i < 10; ++i) { r->off[i] = tot; tot = align256(tot + sz[i]); }
     r->stage_bytes = tot;
-    RS_CUDA(cudaHostAlloc(&r->h_stage, std::max<size_t>(tot, 256), cudaHostAllocDefault));
+    r->h_stage = pinned_get(s, std::max<size_t>(tot, 256), &r->stage_cap);
+    if (!r->h_stage) { set_error("pinned host memory exhausted"); return RS_ERR_OOM; }
     for (int i = 0; i < 10; ++i) {
         if (!sz[i]) continue;
-        if (!src[i]) { cudaFreeHost(r->h_stage); set_error("NULL batch array"); return RS_ERR_INVALID; }
-        if (b->mem == RS_MEM_HOST) memcpy((char *)r->h_stage + r->off[i], src[i], sz[i]);
-        else RS_CUDA(cudaMemcpy((char *)r->h_stage + r->off[i], src[i], sz[i], cudaMemcpyDeviceToHost));
+        if (!src[i]) {
+            pinned_put(s, r->h_stage, r->stage_cap);
+            r->h_stage = nullptr;
+            set_error("NULL batch array");
+            return RS_ERR_INVALID;
+        }
+        if (b->mem == RS_MEM_HOST) {
+            memcpy((char *)r->h_stage + r->off[i], src[i], sz[i]);
+        } else {
+            const cudaError_t e = cudaMemcpy((char *)r->h_stage + r->off[i], src[i], sz[i], cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                pinned_put(s, r->h_stage, r->stage_cap);
+                r->h_stage = nullptr;
+                return cuda_fail(e, "rs_submit copy");
+            }
+        }
     }
-    RS_CUDA(cudaHostAlloc(&r->h_correct, align256(4 * std::max<size_t>(P, 1)) + 4 * std::max<size_t>(P * r->K, 1) + 256,
-                          cudaHostAllocDefault));
+    r->h_correct = (int32_t *)pinned_get(
+        s, align256(4 * std::max<size_t>(P, 1)) + 4 * std::max<size_t>(P * r->K, 1) + 256, &r->result_cap);
+    if (!r->h_correct) {
+        pinned_put(s, r->h_stage, r->stage_cap);
+        r->h_stage = nullptr;
+        set_error("pinned host memory exhausted");
+        return RS_ERR_OOM;
+    }
     r->h_pc = (int32_t *)((char *)r->h_correct + align256(4 * std::max<size_t>(P, 1)));
     r->h_status = (uint32_t *)((char *)r->h_pc + 4 * std::max<size_t>(P * r->K, 1));
     *r->h_status = 0;
@@ -442,7 +616,7 @@ static void push_active(Server *s)
 static bool try_admit(Server *s, Request &r)
 {
     const int64_t tiles = (r.ds->N + SS - 1) / SS;
-    const int64_t groups = std::max<int64_t>(1, (r.P + GROUP_SETS - 1) / GROUP_SETS);
+    const int64_t groups = serve_groups(*r.ds, r.P);
     if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
     if (cudaMallocAsync(&base, r.device_bytes, s->sstream) != cudaSuccess) {
@@ -474,20 +648,28 @@ static bool try_admit(Server *s, Request &r)
     r.d_correct = (int32_t *)p; p += align256(4 * r.P);
     r.d_pc = (int32_t *)p; p += align256(4 * (size_t)r.P * r.K);
     r.d_status = (uint32_t *)p;
+    p += 256;
     po.status = r.d_status;
+    if (r.K <= LAST_END_MAX_K) po.last_end = (int32_t *)p;
     cudaMemsetAsync(r.d_status, 0, 4, s->sstream);
     if (r.P > 0) {
         cudaMemsetAsync(r.d_correct, 0, 4 * (size_t)r.P, s->sstream);
         cudaMemsetAsync(r.d_pc, 0, 4 * (size_t)r.P * r.K, s->sstream);
     }
     const bool finite = r.ds->finite;
-    count_launch(s->ctx, launch_pack(bd, r.ds->F, r.K, SS, finite ? 4 : 2, po, s->sstream));
+    const bool ranked = serve_ranked(*r.ds, r.P);
+    count_launch(s->ctx, launch_pack(bd, r.ds->F, r.K, SS, ranked ? 5 : (finite ? 4 : 2), po, s->sstream));
     ReqDesc d{};
     d.Xt = r.ds->Xt; d.y = r.ds->y; d.N = r.ds->N; d.n_pad = r.ds->n_pad; d.F = r.ds->F; d.K = r.K;
     d.recs = reinterpret_cast<const uint4 *>(po.recs); d.sets = po.sets; d.order = po.order;
     d.P = r.P; d.tiles = (int32_t)tiles; d.groups = (int32_t)groups; d.finite = finite ? 1 : 0;
     d.correct = r.d_correct; d.per_class = r.d_pc;
     d.epoch = r.ticket & 0xFFFFFFull;
+    d.Rk = ranked ? r.ds->Rk : nullptr;
+    d.Us = ranked ? r.ds->Us : nullptr;
+    d.ranked = ranked ? 1 : 0;
+    d.gsets = ranked ? GROUP_SETS_RANKED : GROUP_SETS;
+    d.last_end = po.last_end;
     // a copy from pageable memory is staged before the call returns, so `d` may go out of scope
     cudaMemcpyAsync(&s->d_table[r.slot], &d, sizeof(d), cudaMemcpyHostToDevice, s->sstream);
     cudaMemsetAsync(&s->d_done[r.slot], 0, 4, s->sstream);
@@ -623,8 +805,8 @@ rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, 
         set_error("request rejected by the device checks (malformed batch)");
     }
     // results are released at the first successful poll
-    if (r->h_stage) cudaFreeHost(r->h_stage);
-    if (r->h_correct) cudaFreeHost(r->h_correct);
+    pinned_put(s, r->h_stage, r->stage_cap);
+    pinned_put(s, r->h_correct, r->result_cap);
     if (r->ev) cudaEventDestroy(r->ev);
     r->h_stage = nullptr; r->h_correct = nullptr; r->ev = nullptr;
     s->all.erase(it);
