@@ -149,6 +149,7 @@ typedef struct {
  * Outputs live in the memory space given by batch->mem (host buffers: the library copies).
  * Results are bit-identical to the plain definition (no FMA, no flush-to-zero).
  * Errors: RS_ERR_INVALID (malformed batch: nothing is counted, outputs undefined),
+ *         RS_ERR_TOO_LARGE (a rule of more than 4095 conditions; outputs undefined),
  *         RS_ERR_NOT_FOUND (ds), RS_ERR_OOM, RS_ERR_DEVICE.
  */
 rs_status rs_eval_hard(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,
@@ -314,7 +315,9 @@ rs_status rs_tile_config_info(int32_t id, int32_t *samples_per_tile, int32_t *wa
 /* Evaluator form of configuration `id`: 1 condition at a time; 2 rule at a time; 3 rule at a
  * time with the margin minimum; 4 sign-mask conjunction (finite datasets, else runs as 3);
  * 5 rank-coded cuts (datasets with rank tables: finite and at most 160 features; else runs as
- * 4, then 3). Forms 4 and 5 produce counts only: a call that asks for predictions runs as 3. */
+ * 4, then 3). Forms 4 and 5 produce counts only: a call that asks for predictions runs as 3.
+ * The other configurations stage a feature tile in shared memory and need F small enough for
+ * it; configuration 23 (form 1) reads the features from global memory and takes any F. */
 rs_status rs_tile_config_form(int32_t id, int32_t *form);
 /* Force configuration `id` for every following hard evaluation of the context (-1 = automatic:
  * autotuned table, else heuristic). */

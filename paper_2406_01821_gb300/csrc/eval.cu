@@ -90,8 +90,8 @@ static int heuristic_tile(const Dataset &ds)
 {
     // The rank-coded evaluator with 32 warps (it runs as the sign-mask form on datasets without
     // rank tables and as the margin-minimum form on non-finite data), then smaller tiles for wide
-    // data.
-    static const int prefs[] = {22, 21, 18, 16, 20, 3, 5};
+    // data, and for data too wide for any shared tile the configuration reading global memory.
+    static const int prefs[] = {22, 21, 18, 16, 20, 3, 5, 23};
     for (int id : prefs)
         if (tile_config_fits(tile_config(id), ds.F)) return id;
     return 5;
@@ -205,6 +205,7 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchD
     a.groups = choose_groups(ctx, ds, tc, bd.P);
     a.status = s.status;
     a.last_end = po.last_end;
+    a.Xt = ds->Xt;
     return launch_hard(ctx, ds, tc, a, stream);
 }
 
@@ -333,7 +334,8 @@ rs_status finish_status(Ctx *ctx, const uint32_t *d_status, cudaStream_t stream)
     RS_CUDA(cudaStreamSynchronize(stream));
     if (*hs) {
         set_error("batch rejected: %s", status_text(*hs).c_str());
-        return (*hs & (ST_WAIT_TIMEOUT | ST_QUEUE_TIMEOUT)) ? RS_ERR_TIMEOUT : RS_ERR_INVALID;
+        if (*hs & (ST_WAIT_TIMEOUT | ST_QUEUE_TIMEOUT)) return RS_ERR_TIMEOUT;
+        return (*hs & ST_TOO_LARGE) ? RS_ERR_TOO_LARGE : RS_ERR_INVALID;
     }
     return RS_OK;
 }

@@ -45,7 +45,9 @@ __device__ __forceinline__ uint4 ldg_rec(const Rec *p)
     return __ldg(reinterpret_cast<const uint4 *>(p));
 }
 
-template <int V, int W>
+// GM: features are read from global memory (x[f][n] at Xt[f * n_pad + n]) instead of a staged
+// shared tile, for datasets too wide for any tile.
+template <int V, int W, bool GM = false>
 __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtensorMap tmap, HardArgs a)
 {
     constexpr int S = 32 * V;
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtenso
     const int F = a.F;
     const int Fb = F < 256 ? F : 256;
     const int nbox = (F + Fb - 1) / Fb;
-    const int Frows = nbox * Fb;
+    const int Frows = GM ? 0 : nbox * Fb;
     float *xs = reinterpret_cast<float *>(smem);
     Rec *stage = reinterpret_cast<Rec *>(smem + (size_t)Frows * S * sizeof(float));
     uint64_t *bar = reinterpret_cast<uint64_t *>(stage + W * 32);
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtenso
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (!GM && threadIdx.x == 0) {
         mbar_arrive_expect_tx(bar, (uint32_t)(Frows * S * sizeof(float)));
         for (int b = 0; b < nbox; ++b) tma_load_2d(xs + (size_t)b * Fb * S, &tmap, tile * S, b * Fb, bar);
     }
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtenso
     const int64_t t_last = min((int64_t)tile * S + S, a.N) - 1;
     const int kmin = a.y[t_first], kmax = a.y[t_last];   // labels are sorted within the dataset
 
-    if (!mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT_NS)) {
+    if (!GM && !mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT_NS)) {
         if (threadIdx.x == 0) atomicOr(a.status, ST_WAIT_TIMEOUT);
         mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT_NS);   // let copies in flight land before exit
         return;
@@ -95,7 +97,8 @@ __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtenso
 
     const int count = (a.P - group + G - 1) / G;
     Rec *st = stage + warp * 32;
-    const float *xl = xs + lane * V;
+    const float *xl = GM ? a.Xt + n0 : xs + lane * V;     // x[f] of the lane's samples at xl + f * xstride
+    const int64_t xstride = GM ? a.n_pad : S;
 
     while (true) {
         int m = 0;
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtenso
             const float v0 = __uint_as_float(raw.z), v1 = __uint_as_float(raw.w);
             const uint32_t kind = rec_kind(meta);
             float x[V];
-            load_v<V>(xl + f * S, x);
+            load_v<V>(xl + f * xstride, x);
             if (kind == KIND_GT) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) al[v] = al[v] && (x[v] > v0);
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtenso
                 for (int v = 0; v < V; ++v) al[v] = al[v] && (x[v] < v0);
             } else if (kind == KIND_PAIR) {
                 float z[V];
-                load_v<V>(xl + g * S, z);
+                load_v<V>(xl + g * xstride, z);
 #pragma unroll
                 for (int v = 0; v < V; ++v) al[v] = al[v] && (__fmul_rn(v0, x[v]) > __fmul_rn(v1, z[v]));
             } else if (kind == KIND_MGT) {
@@ -220,33 +223,35 @@ __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtenso
     }
 }
 
-template <int V, int W>
+template <int V, int W, bool GM = false>
 size_t smem_bytes(int F)
 {
+    if (GM) return (size_t)W * 32 * sizeof(Rec) + 16;
     const int Fb = F < 256 ? F : 256;
     const int Frows = ((F + Fb - 1) / Fb) * Fb;
     return (size_t)Frows * 32 * V * sizeof(float) + (size_t)W * 32 * sizeof(Rec) + 16;
 }
 
-template <int V, int W>
+template <int V, int W, bool GM = false>
 rs_status launch_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t stream)
 {
-    const size_t smem = smem_bytes<V, W>(a.F);
+    const size_t smem = smem_bytes<V, W, GM>(a.F);
     if (smem > ctx->smem_optin) return RS_ERR_TOO_LARGE;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(k_hard<V, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(k_hard<V, W, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)ctx->smem_optin);
     });
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute(k_hard)");
-    const CUtensorMap *tm = dataset_tmap(ds, 32 * V);
+    CUtensorMap none{};
+    const CUtensorMap *tm = GM ? &none : dataset_tmap(ds, 32 * V);
     if (!tm) return RS_ERR_DEVICE;
     const int tiles = (int)((a.N + 32 * V - 1) / (32 * V));
     dim3 grid(tiles, a.groups);
     {
         TimedLaunch tl(ctx, TK_HARD, stream);
-        k_hard<V, W><<<grid, W * 32, smem, stream>>>(*tm, a);
+        k_hard<V, W, GM><<<grid, W * 32, smem, stream>>>(*tm, a);
     }
     RS_CUDA(cudaGetLastError());
     count_launch(ctx);
@@ -261,6 +266,7 @@ const TileConfig kConfigs[] = {
     {11, 4, 8, 3}, {12, 4, 16, 3}, {13, 2, 16, 3}, {14, 2, 32, 3}, {15, 4, 32, 3},
     {16, 4, 8, 4}, {17, 4, 16, 4}, {18, 4, 32, 4}, {19, 2, 16, 4}, {20, 2, 32, 4},
     {21, 4, 16, 5}, {22, 4, 32, 5},
+    {23, 4, 8, 1, true},
 };
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
@@ -279,6 +285,7 @@ const TileConfig &tile_config(int id) { return kConfigs[id]; }
 
 bool tile_config_fits(const TileConfig &tc, int F)
 {
+    if (tc.gmem) return true;
     const int Fb = F < 256 ? F : 256;
     const int Frows = ((F + Fb - 1) / Fb) * Fb;
     const size_t stage = (size_t)tc.W * (tc.ver >= 2 ? 64 : 32) * sizeof(Rec);
@@ -306,6 +313,7 @@ rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArg
     case 5: return launch_t<1, 16>(ctx, ds, a, stream);
     case 6: return launch_t<8, 8>(ctx, ds, a, stream);
     case 7: return launch_t<8, 4>(ctx, ds, a, stream);
+    case 23: return launch_t<4, 8, true>(ctx, ds, a, stream);
     default: return RS_ERR_INVALID;
     }
 }

@@ -139,6 +139,7 @@ struct TileConfig {
                  // 3: rule-at-a-time with the margin-minimum conjunction,
                  // 4: sign-mask conjunction for finite datasets (falls back to 3 otherwise)
                  // 5: rank-coded cuts for ranked datasets (falls back to 4, then 3)
+    bool gmem = false;   // form 1 reading features from global memory (no shared tile: any F)
     int S() const { return 32 * V; }
 };
 constexpr int RANK_TILE = 128;    // samples per rank tile (ranks fit in 7 bits)
@@ -244,6 +245,7 @@ struct HardArgs {
     int32_t groups;          // set groups (grid.y)
     uint32_t *status;
     const int32_t *last_end; // [P*K] or null (see PackOut)
+    const float *Xt;         // [F][n_pad] (read directly by the global-memory configuration)
 };
 // Zero outputs and run the evaluator with tile configuration `tc`.
 rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,

@@ -369,3 +369,32 @@ def test_walk_stops_after_last_rule_of_tile_label(ctx, orc, tile, K):
     got = run_gpu(ctx, X, y, K, b, preds=False, tile=tile)
     want = orc.eval_hard(X, y, K, b)
     assert_same(got, want, preds=False)
+
+
+def test_maximum_sizes(ctx, orc):
+    """The widest dataset (4096 features: only the configuration reading global memory fits) with
+    the most classes (4096), predictions included; the longest rule (4095 conditions) in every
+    evaluator form; and one condition more is refused."""
+    from paper_2406_01821_gb300 import rs
+    rng = np.random.default_rng(8)
+    N, F, K = 700, 4096, 4096
+    X = rng.standard_normal((N, F)).astype(np.float32)
+    y = rng.integers(0, K, N).astype(np.int32)
+    b = synth.random_rulesets(synth.quantile_table(X), K, 12, (1, 6), (1, 4), 8, pair_prob=0.3)
+    got = run_gpu(ctx, X, y, K, b)
+    want = orc.eval_hard(X, y, K, b, want_preds=True)
+    assert_same(got, want)
+
+    X, y = synth.two_class_gaussian(3000, 8, 9)
+    def long_rule(n):
+        conds = [(j % 8, -1, synth.GT, 1.0, 0.0, -3.0 - j * 1e-3) for j in range(n)]   # nearly always true
+        return [[(1, conds), (0, [(0, -1, synth.GT, 1.0, 0.0, 0.0)])]]
+    b = synth.from_lists(long_rule(4095), [0])
+    want = orc.eval_hard(X, y, 2, b, want_preds=True)
+    assert want[0][0] > 0
+    for tile in FORMS:
+        assert_same(run_gpu(ctx, X, y, 2, b, preds=False, tile=tile), want, preds=False)
+    b = synth.from_lists(long_rule(4096), [0])
+    with pytest.raises(rs.RsError) as ei:
+        run_gpu(ctx, X, y, 2, b, preds=False)
+    assert ei.value.code == -2                     # RS_ERR_TOO_LARGE
