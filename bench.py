@@ -461,41 +461,51 @@ def serving_leg(args, dev):
 # ----------------------------------------------------------------------------- distributed
 
 class Dist:
+    """Ranks of a torchrun launch (one per GPU, NCCL); a single process otherwise. Without CUDA
+    (multi-rank tests on the CPU) the ranks use gloo and CPU tensors."""
+
     def __init__(self):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
+        self.dev = "cpu"
         if self.world > 1:
             import torch
             import torch.distributed as dist
-            torch.cuda.set_device(self.local)
-            dist.init_process_group("nccl", device_id=torch.device(f"cuda:{self.local}"))
+            if torch.cuda.is_available():
+                torch.cuda.set_device(self.local)
+                self.dev = f"cuda:{self.local}"
+                dist.init_process_group("nccl", device_id=torch.device(self.dev))
+            else:
+                dist.init_process_group("gloo")
             self.pg = dist
 
     def barrier(self):
         if self.pg:
             self.pg.barrier()
 
-    def max(self, v: float) -> float:
-        if not self.pg:
-            return v
+    def _reduce(self, v: float, op) -> float:
         import torch
-        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{self.local}")
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        t = torch.tensor([v], dtype=torch.float64, device=self.dev)
+        self.pg.all_reduce(t, op=op)
         return float(t.item())
 
+    def max(self, v: float) -> float:
+        return self._reduce(v, self.pg.ReduceOp.MAX) if self.pg else v
+
     def sum(self, v: float) -> float:
-        if not self.pg:
-            return v
-        import torch
-        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{self.local}")
-        self.pg.all_reduce(t)
-        return float(t.item())
+        return self._reduce(v, self.pg.ReduceOp.SUM) if self.pg else v
 
     def close(self):
         if self.pg:
             self.pg.destroy_process_group()
+
+
+def whole_job_rate(d: Dist, units: float, ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank (weak scaling: every rank
+    evaluates its own population)."""
+    return d.sum(units) / (d.max(ms) / 1e3)
 
 
 # ----------------------------------------------------------------------------- main
@@ -570,7 +580,7 @@ def main():
     nominal = w.batch.nominal_conditions() * w.N
     total_nominal = d.sum(float(nominal))
     total_sets = d.sum(float(w.batch.P))
-    value = total_nominal / (ms_max / 1e3)
+    value = whole_job_rate(d, float(nominal), res["ms"])
 
     prof = res["prof"]
     kern_ms = prof["hard_ms"] / max(1, prof["hard_launches"])
