@@ -166,37 +166,47 @@ __global__ void __launch_bounds__(SW * 32, 1) k_serve(ServeArgs a)
 
     while (true) {
         if (warp == 0) {
-            // Warp 0 claims the next unit, oldest admitted request first (requests drain in
-            // arrival order while the tail of one overlaps the start of the next). The lanes read
-            // 32 claim words at a time; the first open request wins a compare-and-swap.
+            // Warp 0 claims the next unit from the active request with the fewest unclaimed
+            // units (the oldest among equals): shortest remaining work first, so a small request
+            // is not held behind a large one. The lanes read 32 claim words at a time; the chosen
+            // request is taken by compare-and-swap (a lost race rescans).
             int slot = -1, unit = -1;
             uint64_t idle0 = 0;
             while (true) {
                 // host-written words: lane 0 reads them, so every lane takes the same branches
                 if (__shfl_sync(core::FULL, lane == 0 ? *a.stop : 0, 0)) break;
                 const int n = __shfl_sync(core::FULL, lane == 0 ? *a.nactive : 0, 0);
-                for (int base = 0; base < n && slot < 0; base += 32) {
+                // best = (remaining units << 11) | list index, minimised over the active list
+                uint32_t best = 0xFFFFFFFFu;
+                for (int base = 0; base < n; base += 32) {
                     const int i = base + lane;
                     const int sl = i < n ? a.active[i] : -1;
-                    const bool ok = sl >= 0 && sl < MAX_SLOTS;
-                    unsigned long long w = ok ? *reinterpret_cast<volatile unsigned long long *>(a.claims + sl) : 0ull;
-                    uint32_t open = __ballot_sync(core::FULL, ok && ((w >> CW_NEXT) & CW_MASK) < (w & CW_MASK));
-                    while (open && slot < 0) {
-                        const int j = __ffs(open) - 1;
-                        int got = -1;
-                        if (lane == j) {
+                    uint32_t key = 0xFFFFFFFFu;
+                    if (sl >= 0 && sl < MAX_SLOTS) {
+                        const unsigned long long w = *reinterpret_cast<volatile unsigned long long *>(a.claims + sl);
+                        const uint32_t next = (uint32_t)((w >> CW_NEXT) & CW_MASK), units = (uint32_t)(w & CW_MASK);
+                        if (next < units) key = ((units - next) << 11) | (uint32_t)i;
+                    }
+                    best = min(best, __reduce_min_sync(core::FULL, key));
+                }
+                if (best != 0xFFFFFFFFu) {
+                    const int i = (int)(best & 0x7FFu);
+                    int got = -1, sl = -1;
+                    if (lane == 0) {
+                        sl = a.active[i];
+                        if (sl >= 0 && sl < MAX_SLOTS) {
+                            unsigned long long w = *reinterpret_cast<volatile unsigned long long *>(a.claims + sl);
                             while (((w >> CW_NEXT) & CW_MASK) < (w & CW_MASK)) {
                                 const unsigned long long old = atomicCAS(a.claims + sl, w, w + (1ull << CW_NEXT));
                                 if (old == w) { got = (int)((w >> CW_NEXT) & CW_MASK); break; }
                                 w = old;
                             }
                         }
-                        got = __shfl_sync(core::FULL, got, j);
-                        if (got >= 0) { slot = __shfl_sync(core::FULL, sl, j); unit = got; }
-                        open &= ~(1u << j);
                     }
+                    got = __shfl_sync(core::FULL, got, 0);
+                    if (got >= 0) { slot = __shfl_sync(core::FULL, sl, 0); unit = got; break; }
+                    continue;                   // the request filled up meanwhile: rescan
                 }
-                if (slot >= 0) break;
                 const uint64_t tn = __shfl_sync(core::FULL, now_ns(), 0);
                 if (idle0 == 0) idle0 = tn;
                 else if (tn - idle0 > IDLE_NS) break;
@@ -345,7 +355,7 @@ struct Request {
     size_t device_bytes = 0;
     void *d_buf = nullptr;
     int slot = -1;
-    int state = 0;                        // 0 queued, 1 preparing, 2 running, 3 copying, 4 done
+    int state = 0;                        // 0 queued, 1 preparing, 2 running, 3 copying, 4 done, 5 released
     rs_status status = RS_OK;
     cudaEvent_t ev = nullptr;
     int32_t *h_correct = nullptr, *h_pc = nullptr;   // pinned results
@@ -357,14 +367,21 @@ struct Request {
 
 struct Server {
     Ctx *ctx = nullptr;
-    std::mutex mu;
+    std::mutex mu;                         // scheduler state (held by the scheduler thread while it works)
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<Request>> queued;
-    std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
     std::vector<std::shared_ptr<Request>> active;
     std::thread thread;
     bool quit = false;
-    uint64_t next_ticket = 1;
+    // Submissions go through an inbox under their own lock, so rs_submit never waits for the
+    // scheduler's device work; the scheduler moves them to `queued`. Lock order: mu, then in_mu.
+    std::mutex in_mu;
+    std::condition_variable in_cv;
+    std::vector<std::shared_ptr<Request>> inbox;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> all;   // under in_mu
+    uint64_t next_ticket = 1;                                       // under in_mu
+    std::atomic<bool> quit_flag{false};
+    std::atomic<int> fatal_flag{0};
     size_t used = 0;
     std::vector<int> free_slots;
     cudaStream_t sstream = nullptr, kstream = nullptr;
@@ -478,6 +495,11 @@ void server_shutdown(Ctx *ctx)
         std::lock_guard<std::mutex> lk(s->mu);
         s->quit = true;
     }
+    s->quit_flag = true;
+    {
+        std::lock_guard<std::mutex> il(s->in_mu);
+    }
+    s->in_cv.notify_all();
     s->cv_work.notify_all();
     if (s->thread.joinable()) s->thread.join();
     *(volatile int32_t *)s->h_stop = 1;
@@ -590,14 +612,17 @@ rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint6
     RS_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
     r->t_submit = std::chrono::steady_clock::now();
     {
-        std::lock_guard<std::mutex> lk(s->mu);
-        if (s->fatal) { set_error("serving stopped after a device error"); return s->fatal; }
+        std::lock_guard<std::mutex> il(s->in_mu);
+        if (s->fatal_flag.load()) {
+            set_error("serving stopped after a device error");
+            return (rs_status)s->fatal_flag.load();
+        }
         r->ticket = s->next_ticket++;
-        s->queued.push_back(r);
+        s->inbox.push_back(r);
         s->all[r->ticket] = r;
         *ticket = r->ticket;
     }
-    s->cv_work.notify_all();
+    s->in_cv.notify_one();
     return RS_OK;
 }
 
@@ -697,6 +722,11 @@ static void server_loop(Server *s)
     cudaSetDevice(s->ctx->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
+        {
+            std::lock_guard<std::mutex> il(s->in_mu);
+            for (auto &r : s->inbox) s->queued.push_back(r);
+            s->inbox.clear();
+        }
         if (s->quit && s->queued.empty() && s->active.empty()) break;
         bool progress = false;
         // admit in arrival order
@@ -754,6 +784,7 @@ static void server_loop(Server *s)
                     progress = true;
                 } else if (q != cudaErrorNotReady) {
                     s->fatal = cuda_fail(q, "serving");
+                    s->fatal_flag = (int)s->fatal;
                     r->status = s->fatal;
                     r->state = 4;
                 }
@@ -766,7 +797,13 @@ static void server_loop(Server *s)
         if (!progress) {
             if (s->active.empty() && s->queued.empty()) {
                 if (s->quit) break;
-                s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+                lk.unlock();
+                {
+                    std::unique_lock<std::mutex> il(s->in_mu);
+                    s->in_cv.wait_for(il, std::chrono::milliseconds(50),
+                                      [&] { return !s->inbox.empty() || s->quit_flag.load(); });
+                }
+                lk.lock();
             } else {
                 lk.unlock();
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -781,10 +818,14 @@ rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, 
 {
     Server *s = ctx->server;
     if (!s) { set_error("no request was submitted"); return RS_ERR_NOT_FOUND; }
+    std::shared_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> il(s->in_mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return RS_ERR_NOT_FOUND; }
+        r = it->second;
+    }
     std::unique_lock<std::mutex> lk(s->mu);
-    auto it = s->all.find(ticket);
-    if (it == s->all.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return RS_ERR_NOT_FOUND; }
-    auto r = it->second;
     auto done = [&] { return r->state >= 4; };
     if (!done()) {
         if (timeout_us <= 0) return RS_PENDING;
@@ -804,12 +845,21 @@ rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, 
     } else {
         set_error("request rejected by the device checks (malformed batch)");
     }
+    if (r->state == 5) {            // another poll took the results first
+        set_error("unknown ticket %llu", (unsigned long long)ticket);
+        return RS_ERR_NOT_FOUND;
+    }
     // results are released at the first successful poll
     pinned_put(s, r->h_stage, r->stage_cap);
     pinned_put(s, r->h_correct, r->result_cap);
     if (r->ev) cudaEventDestroy(r->ev);
     r->h_stage = nullptr; r->h_correct = nullptr; r->ev = nullptr;
-    s->all.erase(it);
+    r->state = 5;
+    lk.unlock();
+    {
+        std::lock_guard<std::mutex> il(s->in_mu);
+        s->all.erase(ticket);
+    }
     return rc;
 }
 
@@ -817,10 +867,15 @@ rs_status cancel(Ctx *ctx, uint64_t ticket)
 {
     Server *s = ctx->server;
     if (!s) return RS_ERR_NOT_FOUND;
+    std::shared_ptr<Request> rp;
+    {
+        std::lock_guard<std::mutex> il(s->in_mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) return RS_ERR_NOT_FOUND;
+        rp = it->second;
+    }
     std::lock_guard<std::mutex> lk(s->mu);
-    auto it = s->all.find(ticket);
-    if (it == s->all.end()) return RS_ERR_NOT_FOUND;
-    Request &r = *it->second;
+    Request &r = *rp;
     if (r.state != 0) { set_error("request already admitted"); return RS_ERR_INVALID; }
     r.status = RS_ERR_CANCELLED;
     r.t_done = std::chrono::steady_clock::now();
@@ -835,7 +890,8 @@ rs_status server_stats(Ctx *ctx, rs_serving_stats *out)
     memset(out, 0, sizeof(*out));
     if (!s) return RS_OK;
     std::lock_guard<std::mutex> lk(s->mu);
-    out->queued = (int64_t)s->queued.size();
+    std::lock_guard<std::mutex> il(s->in_mu);
+    out->queued = (int64_t)(s->queued.size() + s->inbox.size());
     out->active = (int64_t)s->active.size();
     out->device_bytes_in_use = s->used;
     out->units_published = s->published;
