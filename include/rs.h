@@ -207,16 +207,18 @@ rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, i
 /* ------------------------------------------------------------------------------- serving */
 
 #define RS_KIND_HARD 0
+#define RS_KIND_SOFT 1
 
 /*
  * Continuous batching of fitness-evaluation requests (hard evaluation). rs_submit copies the batch
  * (host or device arrays per batch->mem) into pinned staging -- the caller may free it on return --
  * and queues the request. Requests are admitted in arrival order while the context's memory budget
  * (rs_config.mem_budget_bytes) and the request slots allow; admitted requests share one persistent
- * kernel: a 128-sample tile of a request's dataset times up to 128 of its sets is a work unit, and
- * CTAs claim units from the active requests in turn, so units of requests admitted while others
- * run interleave with theirs on the device. Results equal rs_eval_hard's exactly.
- *   kind    RS_KIND_HARD (the only kind served)
+ * kernel: a 128-sample tile of a request's dataset times a group of its sets is a work unit, and
+ * CTAs claim units from the request with the fewest unclaimed units (the oldest among equals), so
+ * units of requests admitted while others run interleave with theirs on the device. Results equal
+ * rs_eval_hard's exactly.
+ *   kind    RS_KIND_HARD (soft requests carry a temperature: rs_submit_soft)
  *   errors  RS_ERR_TOO_LARGE if the request alone exceeds the budget; RS_ERR_UNSUPPORTED for
  *           datasets with more than 256 features; RS_ERR_NOT_FOUND (ds)
  * Thread-safe. *ticket receives a non-zero id.
@@ -235,6 +237,15 @@ typedef struct {
  */
 rs_status rs_poll(rs_ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct,
                   int32_t *per_class, rs_ticket_info *info);
+/*
+ * Soft-loss requests (Sec. 3 sigmoid relaxation, the forward of rs_eval_soft_fwd at temperature
+ * tau > 0): queued, admitted under the same budget and run as their own kernels next to the
+ * persistent kernel. rs_poll_soft writes loss (host float[P], may be NULL) and the times, releases
+ * the ticket and returns its status (RS_ERR_INVALID for a malformed batch or a hard ticket).
+ * Losses equal rs_eval_soft_fwd's bit for bit.
+ */
+rs_status rs_submit_soft(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float tau, uint64_t *ticket);
+rs_status rs_poll_soft(rs_ctx *ctx, uint64_t ticket, int64_t timeout_us, float *loss, rs_ticket_info *info);
 /* Cancel a request that has not been admitted yet (RS_ERR_INVALID once it runs). */
 rs_status rs_cancel(rs_ctx *ctx, uint64_t ticket);
 

@@ -25,6 +25,8 @@ rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint6
 rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, int32_t *per_class,
                rs_ticket_info *info);
 rs_status cancel(Ctx *ctx, uint64_t ticket);
+rs_status submit_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, uint64_t *ticket);
+rs_status poll_soft(Ctx *ctx, uint64_t ticket, int64_t timeout_us, float *loss, rs_ticket_info *info);
 rs_status server_stats(Ctx *ctx, rs_serving_stats *out);
 rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_population *hp,
                      int32_t *best_out, double *mean_out, cudaStream_t s);
@@ -250,6 +252,22 @@ rs_status rs_poll(rs_ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *cor
     RS_GUARD({
         if (!ctx) return RS_ERR_INVALID;
         return poll(ctx, ticket, timeout_us, correct, per_class, info);
+    })
+}
+
+rs_status rs_submit_soft(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float tau, uint64_t *ticket)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return submit_soft(ctx, ds, batch, tau, ticket);
+    })
+}
+
+rs_status rs_poll_soft(rs_ctx *ctx, uint64_t ticket, int64_t timeout_us, float *loss, rs_ticket_info *info)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return poll_soft(ctx, ticket, timeout_us, loss, info);
     })
 }
 

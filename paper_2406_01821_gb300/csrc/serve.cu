@@ -348,7 +348,9 @@ struct Request {
     uint64_t ticket = 0;
     std::shared_ptr<Dataset> ds;
     int32_t P = 0, R = 0, C = 0, K = 0;
-    int32_t kind = 0;
+    int32_t kind = 0;                     // RS_KIND_HARD or RS_KIND_SOFT
+    float tau = 0.f;                      // soft requests: temperature
+    int32_t maxR = 0, maxC = 0;           // soft requests: largest set (rules, conditions)
     void *h_stage = nullptr;              // pinned copy of the batch arrays
     size_t stage_bytes = 0, stage_cap = 0, result_cap = 0;   // pinned buffer capacities
     size_t off[10] = {};
@@ -543,24 +545,28 @@ static size_t request_device_bytes(int64_t P, int64_t R, int64_t C, int64_t K)
     return b;
 }
 
-rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint64_t *ticket)
+rs_status submit_impl(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, float tau, uint64_t *ticket)
 {
     if (!b || !ticket) { set_error("NULL batch or ticket"); return RS_ERR_INVALID; }
-    if (kind != 0) { set_error("only hard evaluation requests are served"); return RS_ERR_UNSUPPORTED; }
+    if (kind != RS_KIND_HARD && kind != RS_KIND_SOFT) { set_error("unknown request kind %d", kind); return RS_ERR_INVALID; }
+    if (kind == RS_KIND_SOFT && !(tau > 0.f)) { set_error("tau must be positive"); return RS_ERR_INVALID; }
     if (b->P < 0 || b->R < 0 || b->C < 0 || (b->mem != RS_MEM_HOST && b->mem != RS_MEM_DEVICE)) {
         set_error("bad batch");
         return RS_ERR_INVALID;
     }
     auto ds = find_dataset(ctx, ds_h);
     if (!ds) { set_error("unknown dataset"); return RS_ERR_NOT_FOUND; }
-    if (ds->F > SERVE_MAX_F) { set_error("served datasets have at most %d features", SERVE_MAX_F); return RS_ERR_UNSUPPORTED; }
+    if (kind == RS_KIND_HARD && ds->F > SERVE_MAX_F) {
+        set_error("hard requests are served on datasets of at most %d features", SERVE_MAX_F);
+        return RS_ERR_UNSUPPORTED;
+    }
     rs_status rc = device_guard(ctx);
     if (rc) return rc;
     Server *s = nullptr;
     if ((rc = server_get(ctx, &s))) return rc;
     auto r = std::make_shared<Request>();
     r->ds = ds;
-    r->P = b->P; r->R = b->R; r->C = b->C; r->K = ds->K; r->kind = kind;
+    r->P = b->P; r->R = b->R; r->C = b->C; r->K = ds->K; r->kind = kind; r->tau = tau;
     r->device_bytes = request_device_bytes(b->P, b->R, b->C, ds->K);
     if (r->device_bytes > ctx->budget) {
         set_error("request needs %zu bytes of device memory; the budget is %llu", r->device_bytes,
@@ -568,7 +574,10 @@ rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint6
         return RS_ERR_TOO_LARGE;
     }
     const int64_t units = ((ds->N + SS - 1) / SS) * serve_groups(*ds, b->P);
-    if (units > (int64_t)CW_MASK) { set_error("request too large to serve (%lld work units)", (long long)units); return RS_ERR_TOO_LARGE; }
+    if (kind == RS_KIND_HARD && units > (int64_t)CW_MASK) {
+        set_error("request too large to serve (%lld work units)", (long long)units);
+        return RS_ERR_TOO_LARGE;
+    }
     // copy the batch into pinned staging: the caller may free its arrays on return
     const size_t P = b->P, R = b->R, C = b->C;
     const size_t sz[10] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C};
@@ -597,6 +606,22 @@ rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint6
                 return cuda_fail(e, "rs_submit copy");
             }
         }
+    }
+    if (kind == RS_KIND_SOFT) {
+        // the largest set bounds the soft kernels' shared memory; malformed offsets are left to
+        // the device checks, which see the same arrays
+        const int32_t *sro = (const int32_t *)((char *)r->h_stage + r->off[0]);
+        const int32_t *rco = (const int32_t *)((char *)r->h_stage + r->off[1]);
+        int32_t mr = 1, mc = 1;
+        for (size_t p = 0; p < P; ++p) {
+            const int32_t rb = sro[p], re = sro[p + 1];
+            if (rb < 0 || re < rb || (size_t)re > R) continue;
+            mr = std::max(mr, re - rb);
+            const int32_t cb = rco[rb], ce = rco[re];
+            if (cb >= 0 && ce >= cb && (size_t)ce <= C) mc = std::max(mc, ce - cb);
+        }
+        r->maxR = mr;
+        r->maxC = mc;
     }
     r->h_correct = (int32_t *)pinned_get(
         s, align256(4 * std::max<size_t>(P, 1)) + 4 * std::max<size_t>(P * r->K, 1) + 256, &r->result_cap);
@@ -638,8 +663,48 @@ static void push_active(Server *s)
                     s->sstream);
 }
 
+// A soft-loss request runs as its own kernels on the staging stream (next to the persistent
+// kernel): upload, the soft forward, and the copy of the per-set losses and the status word.
+static bool admit_soft(Server *s, Request &r)
+{
+    if (s->used + r.device_bytes > s->ctx->budget) return false;
+    char *base = nullptr;
+    if (cudaMallocAsync(&base, r.device_bytes, s->sstream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    r.d_buf = base;
+    s->used += r.device_bytes;
+    r.t_admit = std::chrono::steady_clock::now();
+    for (int i = 0; i < 10; ++i)
+        cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
+                        (i + 1 < 10 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
+                        s->sstream);
+    char *p = base + r.stage_bytes;
+    SoftArgs a{};
+    a.b.P = r.P; a.b.R = r.R; a.b.C = r.C;
+    a.b.set_rule_off = (int32_t *)(base + r.off[0]); a.b.rule_cond_off = (int32_t *)(base + r.off[1]);
+    a.b.rule_class = (int32_t *)(base + r.off[2]); a.b.set_default = (int32_t *)(base + r.off[3]);
+    a.b.cond_f = (int32_t *)(base + r.off[4]); a.b.cond_g = (int32_t *)(base + r.off[5]);
+    a.b.cond_op = (int8_t *)(base + r.off[6]); a.b.cond_a = (float *)(base + r.off[7]);
+    a.b.cond_b = (float *)(base + r.off[8]); a.b.cond_t = (float *)(base + r.off[9]);
+    float *d_loss = (float *)p; p += align256(4 * std::max<size_t>(r.P, 1));
+    r.d_status = (uint32_t *)p;
+    a.Xt = r.ds->Xt; a.y = r.ds->y; a.perm = r.ds->perm; a.N = r.ds->N; a.n_pad = r.ds->n_pad;
+    a.F = r.ds->F; a.K = r.K; a.tau = r.tau; a.loss = d_loss; a.status = r.d_status;
+    cudaMemsetAsync(r.d_status, 0, 4, s->sstream);
+    if (r.P > 0) soft_step_known(s->ctx, a, r.maxR, r.maxC, s->sstream);
+    cudaGetLastError();
+    if (r.P > 0) cudaMemcpyAsync(r.h_correct, d_loss, 4 * (size_t)r.P, cudaMemcpyDeviceToHost, s->sstream);
+    cudaMemcpyAsync(r.h_status, r.d_status, 4, cudaMemcpyDeviceToHost, s->sstream);
+    cudaEventRecord(r.ev, s->sstream);
+    r.state = 3;
+    return true;
+}
+
 static bool try_admit(Server *s, Request &r)
 {
+    if (r.kind == RS_KIND_SOFT) return admit_soft(s, r);
     const int64_t tiles = (r.ds->N + SS - 1) / SS;
     const int64_t groups = serve_groups(*r.ds, r.P);
     if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget) return false;
@@ -779,7 +844,7 @@ static void server_loop(Server *s)
                     cudaFreeAsync(r->d_buf, s->sstream);   // the copies out have completed
                     r->d_buf = nullptr;
                     s->used -= r->device_bytes;
-                    s->free_slots.push_back(r->slot);
+                    if (r->slot >= 0) s->free_slots.push_back(r->slot);
                     r->state = 4;
                     progress = true;
                 } else if (q != cudaErrorNotReady) {
@@ -813,8 +878,8 @@ static void server_loop(Server *s)
     }
 }
 
-rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, int32_t *per_class,
-               rs_ticket_info *info)
+rs_status poll_impl(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t kind, int32_t *correct,
+                    int32_t *per_class, float *loss, rs_ticket_info *info)
 {
     Server *s = ctx->server;
     if (!s) { set_error("no request was submitted"); return RS_ERR_NOT_FOUND; }
@@ -824,6 +889,10 @@ rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, 
         auto it = s->all.find(ticket);
         if (it == s->all.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return RS_ERR_NOT_FOUND; }
         r = it->second;
+    }
+    if (r->kind != kind) {
+        set_error("ticket %llu is a %s request", (unsigned long long)ticket, r->kind == RS_KIND_SOFT ? "soft" : "hard");
+        return RS_ERR_INVALID;
     }
     std::unique_lock<std::mutex> lk(s->mu);
     auto done = [&] { return r->state >= 4; };
@@ -840,6 +909,7 @@ rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, 
     if (rc == RS_OK) {
         if (correct) memcpy(correct, r->h_correct, 4 * (size_t)r->P);
         if (per_class) memcpy(per_class, r->h_pc, 4 * (size_t)r->P * r->K);
+        if (loss) memcpy(loss, r->h_correct, 4 * (size_t)r->P);
     } else if (rc == RS_ERR_CANCELLED) {
         set_error("request cancelled");
     } else {
@@ -897,6 +967,28 @@ rs_status server_stats(Ctx *ctx, rs_serving_stats *out)
     out->units_published = s->published;
     out->kernel_launches = s->launches;
     return RS_OK;
+}
+
+rs_status submit(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, uint64_t *ticket)
+{
+    if (kind == RS_KIND_SOFT) {
+        set_error("soft requests carry a temperature: use rs_submit_soft");
+        return RS_ERR_INVALID;
+    }
+    return submit_impl(ctx, ds_h, b, kind, 0.f, ticket);
+}
+rs_status submit_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, uint64_t *ticket)
+{
+    return submit_impl(ctx, ds_h, b, RS_KIND_SOFT, tau, ticket);
+}
+rs_status poll(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t *correct, int32_t *per_class,
+               rs_ticket_info *info)
+{
+    return poll_impl(ctx, ticket, timeout_us, RS_KIND_HARD, correct, per_class, nullptr, info);
+}
+rs_status poll_soft(Ctx *ctx, uint64_t ticket, int64_t timeout_us, float *loss, rs_ticket_info *info)
+{
+    return poll_impl(ctx, ticket, timeout_us, RS_KIND_SOFT, nullptr, nullptr, loss, info);
 }
 
 }  // namespace rs

@@ -115,7 +115,7 @@ __device__ __forceinline__ void kadd(float &s, float &c, float v)
 {
     const float y = v - c;
     const float t = s + y;
-    c = (t - s) - y;
+    c = isinf(t) ? 0.f : (t - s) - y;   // an infinite sum stays infinite rather than turning NaN
     s = t;
 }
 

@@ -118,6 +118,10 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "rs_tile_config_form": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "rs_set_tile_config": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "rs_submit_soft": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch), ctypes.c_float,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "rs_poll_soft": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.POINTER(rs_ticket_info)]),
     "rs_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "rs_selftest_threshold_rewrite": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
@@ -361,6 +365,23 @@ class Context:
             return None
         check(rc)
         return c, pc, {"submit_ns": info.submit_ns, "admit_ns": info.admit_ns, "done_ns": info.done_ns}
+
+    def submit_soft(self, ds: int, batch, tau: float) -> int:
+        """Queue a soft-loss request (forward at temperature tau); returns its ticket."""
+        t = ctypes.c_uint64()
+        cb = batch.c()
+        check(lib().rs_submit_soft(self.h, ds, ctypes.byref(cb), float(tau), ctypes.byref(t)))
+        return t.value
+
+    def poll_soft(self, ticket: int, P: int, timeout_us: int = 0):
+        """Returns None while pending, else (loss[P] float32, info dict)."""
+        loss = np.zeros(P, np.float32)
+        info = rs_ticket_info()
+        rc = lib().rs_poll_soft(self.h, ticket, int(timeout_us), _ptr(loss), ctypes.byref(info))
+        if rc == PENDING:
+            return None
+        check(rc)
+        return loss, {"submit_ns": info.submit_ns, "admit_ns": info.admit_ns, "done_ns": info.done_ns}
 
     def cancel(self, ticket: int) -> int:
         return lib().rs_cancel(self.h, ticket)

@@ -120,3 +120,44 @@ def test_budget_admission_and_errors():
             ctx2.close()
     finally:
         ctx.close()
+
+
+def test_soft_requests_in_the_mix(orc):
+    """Soft-loss requests served next to hard ones: each loss equals rs_eval_soft_fwd's bit for bit
+    and the float64 oracle's within the soft tolerance; hard results stay exact; kinds are kept
+    apart (a soft ticket cannot be polled as hard) and a soft request needs tau > 0."""
+    import torch
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    ctx = rs.Context(0, mem_budget_bytes=1 << 30)
+    try:
+        runs = make_runs(3, n_runs=3)
+        dss = [ctx.dataset(X, y, K) for (X, y, K, _) in runs]
+        rng = np.random.default_rng(4)
+        jobs = []
+        for j in range(12):
+            i = int(rng.integers(0, len(runs)))
+            X, y, K, q = runs[i]
+            b = synth.random_rulesets(q, K, int(rng.integers(8, 120)), (1, 16), (1, 6), 300 + j)
+            soft = j % 2 == 0
+            t = ctx.submit_soft(dss[i], rs.HostBatch(b), 0.1) if soft else ctx.submit(dss[i], rs.HostBatch(b))
+            jobs.append((i, b, soft, t))
+        for i, b, soft, t in jobs:
+            X, y, K, _ = runs[i]
+            if soft:
+                with pytest.raises(rs.RsError):
+                    ctx.poll(t, b.P, K, timeout_us=60_000_000)      # wrong kind
+                loss, info = ctx.poll_soft(t, b.P, timeout_us=60_000_000)
+                direct, _ = ctx.soft_fwd(dss[i], rs.DeviceBatch.from_host(b), 0.1, N=len(X), K=K)
+                torch.cuda.synchronize()
+                assert np.array_equal(loss.view(np.uint32), direct.cpu().numpy().view(np.uint32))
+                ref = orc.soft(X, y, K, b, 0.1)
+                assert np.allclose(loss, ref["loss"], rtol=1e-5, atol=0)
+            else:
+                c, pc, _ = ctx.poll(t, b.P, K, timeout_us=60_000_000)
+                want = orc.eval_hard(X, y, K, b)
+                assert np.array_equal(c, want[0]) and np.array_equal(pc, want[1])
+        with pytest.raises(rs.RsError):
+            ctx.submit_soft(dss[0], rs.HostBatch(jobs[0][1]), 0.0)
+    finally:
+        ctx.close()

@@ -101,6 +101,32 @@ def test_soft_ragged_and_pairs(ctx, orc):
     check_against_oracle(got, ref)
 
 
+@pytest.mark.parametrize("F", [8, 160])
+def test_unreachable_label_gives_infinite_loss(ctx, orc, F):
+    """Sets where some sample's label has no rule and is not the default: the loss is +inf, as
+    in the oracle (not NaN), in both the staged-tile (F <= 128) and the per-warp kernel; the other
+    sets of the batch are unaffected."""
+    import torch
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.gaussian_mixture(4000, F, 3, 9)
+    b = synth.random_rulesets(synth.quantile_table(X), 2, 40, (2, 8), (1, 4), 9)   # classes 0, 1 only
+    for p in range(b.P):
+        r0 = b.set_rule_off[p]
+        b.rule_class[r0:r0 + 2] = (0, 1)
+    b.set_default[::2] = 2                                 # even sets: every label reachable
+    ref = orc.soft(X, y, 3, b, 0.1)
+    ds = ctx.dataset(X, y, 3)
+    try:
+        loss, _ = ctx.soft_fwd(ds, rs.DeviceBatch.from_host(b), 0.1)
+        torch.cuda.synchronize()
+        loss = loss.cpu().numpy()
+    finally:
+        ctx.dataset_destroy(ds)
+    assert np.isposinf(ref["loss"][1::2]).all() and np.isfinite(ref["loss"][::2]).all()
+    assert np.isposinf(loss[1::2]).all()
+    assert np.allclose(loss[::2], ref["loss"][::2], rtol=RTOL, atol=0)
+
+
 def test_soft_is_deterministic(ctx):
     X, y = synth.two_class_gaussian(5000, 8, 1)
     b = reachable(synth.random_rulesets(synth.quantile_table(X), 2, 16, (1, 8), (1, 4), 1))

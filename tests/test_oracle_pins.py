@@ -349,6 +349,20 @@ def test_soft_probabilities_sum_to_one(orc):
         assert np.allclose(out["loss"], (-np.log(py)).mean(axis=1), rtol=1e-12, atol=0)
 
 
+def test_unreachable_label_has_infinite_loss(orc):
+    """A label with no rule of its class and another default class has probability exactly 0 in
+    the ordered mixture of Sec. 3 (every path ends in a rule or the default), so -log p is +inf;
+    a set where every label is reachable stays finite."""
+    X, _ = synth.two_class_gaussian(50, 2, 3)
+    y = np.zeros(len(X), np.int32)
+    y[7] = 2                                                   # class 2 appears in no set below
+    cond = (0, -1, synth.GT, 1.0, 0.0, 0.0)
+    b = synth.from_lists([[(0, [cond])], [(2, [cond])]], [1, 0])
+    out = orc.soft(X, y, 3, b, 0.5, want_probs=True)
+    assert np.isposinf(out["loss"][0]) and out["probs"][0, 7, 2] == 0.0
+    assert np.isfinite(out["loss"][1])
+
+
 @pytest.mark.parametrize("op", [synth.GT, synth.LT])
 @pytest.mark.parametrize("pair", [False, True])
 def test_one_rule_one_condition_is_logistic_regression(orc, op, pair):
