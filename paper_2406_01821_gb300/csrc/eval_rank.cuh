@@ -76,25 +76,20 @@ __device__ __forceinline__ uint32_t class_bytes(const int32_t *yl, int k)
            ((y.w == k) ? 0x80000000u : 0u);
 }
 
-// Pass bits (0x80 in byte v where the condition holds for the lane's sample v) of a pair
-// condition fl(a * x[f]) > fl(b * x[g]) or a product condition fl(a * x[f]) > b. The products are
-// separately rounded (packed two-lane multiplies).
-__device__ __forceinline__ uint32_t pass_bytes(uint4 r, const unsigned char *xl, int F)
+// Pass row of a pair condition fl(a * x[f]) > fl(b * x[g]) or a product condition
+// fl(a * x[f]) > b, staged as {byte offset of row f, byte offset of row g (a row of 1.0 for a
+// product: fl(b * 1) = b), a, b}: 0xFF in byte v where the condition holds for the lane's sample v.
+// The products are separately rounded (packed two-lane multiplies).
+__device__ __forceinline__ uint32_t pass_row(uint4 q, const unsigned char *xl)
 {
-    const uint32_t f = min(r.x & R5_F_MASK, (uint32_t)(F - 1));
-    const float4 x = *reinterpret_cast<const float4 *>(xl + f * T * 4u);
-    const float a = __uint_as_float(r.z), b = __uint_as_float(r.w);
-    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    const float4 x = *reinterpret_cast<const float4 *>(xl + q.x);
+    const float4 z = *reinterpret_cast<const float4 *>(xl + q.y);
+    const float2 a2 = make_float2(__uint_as_float(q.z), __uint_as_float(q.z));
+    const float2 b2 = make_float2(__uint_as_float(q.w), __uint_as_float(q.w));
     const float2 p01 = __fmul2_rn(make_float2(x.x, x.y), a2), p23 = __fmul2_rn(make_float2(x.z, x.w), a2);
-    float2 q01 = b2, q23 = b2;
-    if ((r.x >> R5_TAG_SHIFT) == R5_PAIR) {
-        const uint32_t g = min(r.y, (uint32_t)(F - 1));
-        const float4 z = *reinterpret_cast<const float4 *>(xl + g * T * 4u);
-        q01 = __fmul2_rn(make_float2(z.x, z.y), b2);
-        q23 = __fmul2_rn(make_float2(z.z, z.w), b2);
-    }
-    const float p[4] = {p01.x, p01.y, p23.x, p23.y}, q[4] = {q01.x, q01.y, q23.x, q23.y};
-    return gt_bytes(p, q) & HIGH;
+    const float2 q01 = __fmul2_rn(make_float2(z.x, z.y), b2), q23 = __fmul2_rn(make_float2(z.z, z.w), b2);
+    const float p[4] = {p01.x, p01.y, p23.x, p23.y}, r[4] = {q01.x, q01.y, q23.x, q23.y};
+    return gt_bytes(p, r);
 }
 
 // One group of four staged records with end-of-rule flags M (bit u: record u ends its rule).
@@ -102,11 +97,14 @@ template <uint32_t M, bool UNI>
 __device__ __forceinline__ void group4(const uint32_t (&e)[4], const uint32_t *sw, const int32_t *yl,
                                        uint32_t &fail, uint32_t &claimed, uint32_t &hit)
 {
+    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+    if (M) w4 = *reinterpret_cast<const uint4 *>(sw);       // the group's four class words at once
+    const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         fail |= e[u];
         if (M & (1u << u)) {
-            const uint32_t w = sw[u];
+            const uint32_t w = ws[u];
             const uint32_t newly = ~fail & HIGH;
             if (UNI) hit |= newly & w;
             else hit |= newly & class_bytes(yl, (int)w);
@@ -123,16 +121,18 @@ __device__ __forceinline__ void group4(const uint32_t (&e)[4], const uint32_t *s
 // The set is walked in chunks of up to 32 records. Staging turns every record of a chunk into the
 // same form {byte offset from the lane's rank word, per-byte constant}: a cut points at its rank
 // row; a pair or product condition is first evaluated by the whole warp into a pass row
-// (0x80 / 0x00 per sample, constant 0x80808080) in the warp's `vrow` slots; padding records are
-// no-ops. The chunk is then one straight run of identical steps, with the first-fire claim
-// applied after each rule's last record (a warp vote gives their positions).
+// (0xFF / 0x00 per sample, constant 0xFFFFFFFF) in the warp's `vrow` slots, from a table of the
+// chunk's pairs that the lanes build in parallel; padding records are no-ops. The chunk is then one
+// straight run of identical steps, with the first-fire claim applied after each rule's last record
+// (a warp vote gives their positions); the all-claimed exit is tested once per chunk.
 template <bool UNI, int VS>
 __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t vrow_off, int lane,
                                              const uint4 *recs, int rb, int nrec, const float *us,
                                              uint32_t rev_off, int F, int kmine, const unsigned char *rl,
-                                             const unsigned char *xl, const int32_t *yl, uint32_t claimed,
-                                             int deflt)
+                                             const unsigned char *xl, uint32_t ones_off, const int32_t *yl,
+                                             uint32_t claimed, int deflt)
 {
+    static_assert(VS <= 16, "pair table and staged records share the warp's 512-byte stage");
     const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
     uint2 *s8 = reinterpret_cast<uint2 *>(st);            // staged {offset, constant}, 32 entries
     uint32_t *sw = reinterpret_cast<uint32_t *>(st) + 64;  // end-of-rule class mask / class
@@ -154,31 +154,30 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
         const uint32_t ends = __ballot_sync(FULL, lane < cnt && (raw.x & R5_END_BIT) != 0u);
         pf = (c0 + cnt + lane < nrec) ? __ldcg(recs + rb + c0 + cnt + lane) : zero4;
 
-        __syncwarp();
-        st[lane] = raw;                     // raw records, read back by the pass-row loop
-        // every lane runs the cut search (branch-free staging); other records then take their form
+        __syncwarp();                       // the previous chunk's readers of the stage are done
+        // every lane runs the cut search (branch-free staging); other records then take their form.
+        // A pair or product condition gets a pass-row slot and a pair-table entry.
         const uint32_t cls = (raw.x >> R5_CLS_SHIFT) & 0xFFFu;
         const uint32_t ew = UNI ? ((int)cls == kmine ? 0xFFFFFFFFu : 0u) : cls;
         uint2 sr = stage_cut(raw, us, rev_off, F);
-        if ((pm >> lane) & 1u) sr = make_uint2(vrow_off + 128u * (uint32_t)__popc(pm & ((1u << lane) - 1u)), HIGH);
-        else if (lane >= cnt || tag == R5_NONE) sr = make_uint2(0u, NOOP_K);
+        if ((pm >> lane) & 1u) {
+            const uint32_t slot = __popc(pm & ((1u << lane) - 1u));
+            const uint32_t f = min(raw.x & R5_F_MASK, (uint32_t)(F - 1));
+            const uint32_t g = min(raw.y, (uint32_t)(F - 1));
+            st[slot] = make_uint4(f * (T * 4u), tag == R5_PAIR ? g * (T * 4u) : ones_off, raw.z, raw.w);
+            sr = make_uint2(vrow_off + 128u * slot, FULL);
+        } else if (lane >= cnt || tag == R5_NONE) {
+            sr = make_uint2(0u, NOOP_K);
+        }
         __syncwarp();
         {                                             // pass rows, one warp-wide evaluation each
-            uint32_t m = pm;
+            const int np = __popc(pm);
             uint32_t *vr = vrow + lane;
-            while (m) {
-                const uint4 p0 = st[__ffs(m) - 1];
-                m &= m - 1u;
-                if (m) {
-                    const uint4 p1 = st[__ffs(m) - 1];
-                    m &= m - 1u;
-                    const uint32_t v0 = pass_bytes(p0, xl, F), v1 = pass_bytes(p1, xl, F);
-                    vr[0] = v0;
-                    vr[32] = v1;
-                    vr += 64;
-                } else {
-                    vr[0] = pass_bytes(p0, xl, F);
-                }
+            for (int j = 0; j < np; j += 2) {
+                const uint32_t v0 = pass_row(st[j], xl);
+                if (j + 1 < np) vr[32] = pass_row(st[j + 1], xl);
+                vr[0] = v0;
+                vr += 64;
             }
         }
         __syncwarp();
@@ -202,8 +201,8 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
             RS_GROUP4(13) RS_GROUP4(14) RS_GROUP4(15)
 #undef RS_GROUP4
             }
-            if (((ends >> g) & 0xFu) && __all_sync(FULL, claimed == HIGH)) { done = true; break; }
         }
+        done = __all_sync(FULL, claimed == HIGH);     // all 128 samples claimed: the set is decided
         c0 += cnt;
     }
     const uint32_t left = ~claimed & HIGH;

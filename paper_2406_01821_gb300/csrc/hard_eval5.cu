@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
     uint4 *stage_all = reinterpret_cast<uint4 *>(us + (size_t)Frows * T);
     constexpr int VS = vslots<W>();
     uint32_t *vrows = reinterpret_cast<uint32_t *>(stage_all + W * 32);     // [W][VS][32]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(vrows + W * VS * 32);
+    float *ones = reinterpret_cast<float *>(vrows + W * VS * 32);             // [T] of 1.0 (products)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ones + T);
     int *next = reinterpret_cast<int *>(bar + 1);
     const uint4 *recs = reinterpret_cast<const uint4 *>(a.recs);
 
@@ -66,11 +67,13 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
         const uint32_t *r32 = reinterpret_cast<const uint32_t *>(rs);
         uint32_t *rr32 = reinterpret_cast<uint32_t *>(rs + rev_off);
         for (int i = threadIdx.x; i < Frows * T / 4; i += W * 32) rr32[i] = r32[i] ^ 0x7F7F7F7Fu;
+        if (threadIdx.x < T) ones[threadIdx.x] = 1.f;
     }
     __syncthreads();
 
     const unsigned char *rl = rs + lane * 4;       // this lane's four rank bytes of row 0
     const unsigned char *xl = xs + lane * 16;      // this lane's four floats of row 0
+    const uint32_t ones_off = (uint32_t)(reinterpret_cast<unsigned char *>(ones) - xs);
     const int count = (a.P - group + G - 1) / G;
     uint4 *st = stage_all + warp * 32;
 
@@ -91,10 +94,10 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
         uint32_t *vr = vrows + warp * VS * 32;
         const uint32_t vr_off = (uint32_t)(reinterpret_cast<unsigned char *>(vr) - rs);
         const uint32_t hit =
-            uniform ? walk_set<true, VS>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, kmin, rl, xl, yl,
-                                     claimed0, si.deflt)
-                    : walk_set<false, VS>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, -2, rl, xl, yl,
-                                      claimed0, si.deflt);
+            uniform ? walk_set<true, VS>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, kmin, rl, xl,
+                                         ones_off, yl, claimed0, si.deflt)
+                    : walk_set<false, VS>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, -2, rl, xl,
+                                          ones_off, yl, claimed0, si.deflt);
         const int hits = __reduce_add_sync(FULL, __popc(hit));
         if (lane == 0 && hits) atomicAdd(&a.correct[p], hits);
         if (a.per_class) {
@@ -117,7 +120,7 @@ size_t hard5_smem_bytes(int F, int W)
     const int Fb = F < 256 ? F : 256;
     const size_t Frows = (size_t)((F + Fb - 1) / Fb) * Fb;
     const size_t vs = W >= 32 ? vslots<32>() : vslots<16>();
-    return Frows * T * (4 + 2 + 4) + (size_t)W * 32 * 16 + (size_t)W * vs * 32 * 4 + 16;
+    return Frows * T * (4 + 2 + 4) + (size_t)W * 32 * 16 + (size_t)W * vs * 32 * 4 + T * 4 + 16;
 }
 
 template <int W>

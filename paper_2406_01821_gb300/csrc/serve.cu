@@ -41,7 +41,8 @@ constexpr int SVS = 8;                // pass-row slots per warp of rank-coded u
 constexpr size_t TILE_BYTES = (size_t)SERVE_MAX_F * SS * 4 > (size_t)SERVE_RANK_MAX_F * SS * 10
                                   ? (size_t)SERVE_MAX_F * SS * 4
                                   : (size_t)SERVE_RANK_MAX_F * SS * 10;
-constexpr size_t SERVE_SMEM = TILE_BYTES + (size_t)SW * 64 * 16 + (size_t)SW * SVS * 32 * 4;
+constexpr size_t ONES_BYTES = (size_t)SS * 4;   // a row of 1.0: the right side of product conditions
+constexpr size_t SERVE_SMEM = TILE_BYTES + (size_t)SW * 64 * 16 + (size_t)SW * SVS * 32 * 4 + ONES_BYTES;
 constexpr int MAX_SLOTS = 2048;
 constexpr int GROUP_SETS = 128;       // sets per unit: four per warp
 constexpr int GROUP_SETS_RANKED = 256;  // rank-coded units: their tile staging is heavier
@@ -90,7 +91,8 @@ __device__ __forceinline__ uint64_t now_ns()
 // One unit on a dataset with rank tables: stage x, ranks, reversed ranks and the sorted columns
 // of the tile, then walk sets [set0, set1) with the rank-coded evaluator.
 __device__ __forceinline__ void serve_unit_ranked(const ReqDesc &d, int tile, int set0, int set1,
-                                                  unsigned char *smem, uint4 *st, uint32_t *vr, int *s_next)
+                                                  unsigned char *smem, uint4 *st, uint32_t *vr, uint32_t ones_off,
+                                                  int *s_next)
 {
     using namespace rank;
     const int F = d.F, lane = threadIdx.x & 31;
@@ -134,10 +136,10 @@ __device__ __forceinline__ void serve_unit_ranked(const ReqDesc &d, int tile, in
                              ? min(__ldcg(d.last_end + (int64_t)p * d.K + kmin), t.y - t.x)
                              : t.y - t.x;
         const uint32_t hit =
-            uniform ? walk_set<true, SVS>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, kmin, rl, xl, yl,
-                                          claimed0, deflt)
-                    : walk_set<false, SVS>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, -2, rl, xl, yl,
-                                           claimed0, deflt);
+            uniform ? walk_set<true, SVS>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, kmin, rl, xl,
+                                          ones_off, yl, claimed0, deflt)
+                    : walk_set<false, SVS>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, -2, rl, xl,
+                                           ones_off, yl, claimed0, deflt);
         const int hits = __reduce_add_sync(FULL, __popc(hit));
         if (lane == 0 && hits) atomicAdd(&d.correct[p], hits);
         if (d.per_class) {
@@ -159,6 +161,9 @@ __global__ void __launch_bounds__(SW * 32, 1) k_serve(ServeArgs a)
     float *xs = reinterpret_cast<float *>(smem);                                   // [F][SS]
     uint4 *stage_all = reinterpret_cast<uint4 *>(smem + TILE_BYTES);
     uint32_t *vrows = reinterpret_cast<uint32_t *>(stage_all + SW * 64);            // [SW][SVS][32]
+    float *ones = reinterpret_cast<float *>(vrows + SW * SVS * 32);                  // [SS] of 1.0
+    const uint32_t ones_off = (uint32_t)(reinterpret_cast<unsigned char *>(ones) - smem);
+    if (threadIdx.x < SS) ones[threadIdx.x] = 1.f;                                   // read after a barrier
     __shared__ int s_slot, s_unit, s_next;
     __shared__ ReqDesc sd;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(SW * 32, 1) k_serve(ServeArgs a)
         const int tile = unit / d.groups, grp = unit % d.groups;
         const int set0 = grp * d.gsets, set1 = min(d.P, set0 + d.gsets);
         if (d.ranked) {
-            serve_unit_ranked(d, tile, set0, set1, smem, st, vrows + warp * SVS * 32, &s_next);
+            serve_unit_ranked(d, tile, set0, set1, smem, st, vrows + warp * SVS * 32, ones_off, &s_next);
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
