@@ -8,13 +8,15 @@ generators in ``paper_2406_01821_gb300.synth`` (which hold none of the method's 
 Functions (each follows the paper, "GPU-Accelerated Rule Evaluation and Evolution"):
   eval_hard   Sec. 3 / Fig. 1a-b: inequalities with a strict sign activation, conjunction per
               rule, first firing rule of the ordered list (Sec. 1 list grammar), default class
-              otherwise; fitness = correct counts (Sec. 1). float32 products, no FMA.
+              otherwise; fitness = correct counts (Sec. 1). float32 products, no FMA. Categorical
+              membership conditions (Sec. 5 future work): x[f] an integer code 0..63 in a set.
   soft        Sec. 3: sigmoid relaxation for back-propagation of coefficients and thresholds
               (Fig. 1c). float64, log domain. Loss, class probabilities and the adjoint.
   evolve_step Sec. 3: tournament selection and offspring with randomized coefficients.
 
 Parity status: eval_hard and soft are pinned by tests (worked example of Fig. 1, a second
-dense formulation, brute force, closed forms, invariants, finite differences). The paper's
+dense formulation, brute force, closed forms, invariants, finite differences; membership tests
+by hand-written edge values, numpy's isin and the band form of a single code). The paper's
 example accuracies (21.05% -> 92.40%) are parity unpinned: the dataset and optimizer behind
 them are not available.
 """
@@ -58,7 +60,8 @@ class _Batch(ctypes.Structure):
                 ("rule_class", ctypes.c_void_p), ("set_default", ctypes.c_void_p),
                 ("cond_f", ctypes.c_void_p), ("cond_g", ctypes.c_void_p),
                 ("cond_op", ctypes.c_void_p), ("cond_a", ctypes.c_void_p),
-                ("cond_b", ctypes.c_void_p), ("cond_t", ctypes.c_void_p)]
+                ("cond_b", ctypes.c_void_p), ("cond_t", ctypes.c_void_p),
+                ("cond_set", ctypes.c_void_p)]
 
 
 def _load(path):
@@ -93,10 +96,12 @@ def _cbatch(b):
         "cond_a": np.ascontiguousarray(b.cond_a, np.float32),
         "cond_b": np.ascontiguousarray(b.cond_b, np.float32),
         "cond_t": np.ascontiguousarray(b.cond_t, np.float32),
+        "cond_set": (np.ascontiguousarray(b.cond_set, np.uint64)
+                     if getattr(b, "cond_set", None) is not None else None),
     }
     cb = _Batch(int(keep["set_default"].shape[0]), *[_ptr(keep[k]) for k in
                 ("set_rule_off", "rule_cond_off", "rule_class", "set_default", "cond_f", "cond_g",
-                 "cond_op", "cond_a", "cond_b", "cond_t")])
+                 "cond_op", "cond_a", "cond_b", "cond_t", "cond_set")])
     return cb, keep
 
 

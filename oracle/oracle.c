@@ -26,6 +26,11 @@
  *  - soft relaxation: q_r = prod_c sigmoid(s*(lhs-rhs)/tau), first-fire probability
  *    q_r * prod_{j<r} (1-q_j), the default class takes prod_j (1-q_j), loss = mean_n -log p(y_n),
  *    all in float64 in the log domain.
+ *  - categorical features (Sec. 5 names them as future work): a feature may hold integer category
+ *    codes stored as floats; a membership condition (op 2) on feature f with category set S
+ *    (a 64-bit mask, bit k = code k) is true iff x[f] is an integer k with 0 <= k <= 63 and k is
+ *    in S, false otherwise (other values, NaN). It has no coefficient, so the soft relaxation
+ *    keeps it as its exact indicator (a factor 1 or 0 of q_r) and it has no gradient.
  */
 #include <math.h>
 #include <stdint.h>
@@ -48,6 +53,7 @@ typedef struct {
     const int32_t *cond_f, *cond_g;
     const int8_t *cond_op;
     const float *cond_a, *cond_b, *cond_t;
+    const uint64_t *cond_set;    /* category sets of op-2 conditions; NULL if there are none */
 } orc_batch;
 
 int orc_num_threads(int requested)
@@ -61,9 +67,28 @@ int orc_num_threads(int requested)
 #endif
 }
 
-/* One condition on one sample, exactly as defined: two rounded float32 products, one compare. */
+/* Membership of one value in a category set: an integer code 0..63 whose bit is set. */
+static int in_set(float x, uint64_t set)
+{
+    if (!(x >= 0.0f && x <= 63.0f)) return 0;      /* also false for NaN */
+    const int k = (int)x;
+#if ORC_PLANT == 8
+    (void)0;                                       /* planted: a fractional value keeps its code */
+#else
+    if ((float)k != x) return 0;                   /* not an integer code */
+#endif
+#if ORC_PLANT == 9
+    return (int)((set >> (63 - k)) & 1u);          /* planted: bits read from the top */
+#else
+    return (int)((set >> k) & 1u);
+#endif
+}
+
+/* One condition on one sample, exactly as defined: two rounded float32 products, one compare
+ * (or, for op 2, the category membership of x[f]). */
 static int cond_true(const orc_batch *b, int64_t c, const float *xrow)
 {
+    if (b->cond_op[c] == 2) return b->cond_set ? in_set(xrow[b->cond_f[c]], b->cond_set[c]) : 0;
     float lhs = b->cond_a[c] * xrow[b->cond_f[c]];
     float rhs = (b->cond_g[c] < 0) ? b->cond_t[c] : b->cond_b[c] * xrow[b->cond_g[c]];
 #if ORC_PLANT == 1
@@ -204,7 +229,8 @@ int orc_soft(const float *X, int64_t N, int32_t F, const int32_t *y, int32_t K,
                     int32_t r = r0 + j;
                     double s = 0.0;
                     for (int32_t c = b->rule_cond_off[r]; c < b->rule_cond_off[r + 1]; ++c)
-                        s += log_sigmoid(margin(b, c, xrow, tau));
+                        s += (b->cond_op[c] == 2) ? (cond_true(b, c, xrow) ? 0.0 : -INFINITY)
+                                                  : log_sigmoid(margin(b, c, xrow, tau));
                     lq[j] = s;
                     l1q[j] = log(-expm1(s));
                 }
@@ -245,6 +271,7 @@ int orc_soft(const float *X, int64_t N, int32_t F, const int32_t *y, int32_t K,
                     lS = log_add(same ? lq[j] : -INFINITY, l1q[j] + lS);
                     lT = log_add(same ? -INFINITY : lq[j], l1q[j] + lT);
                     for (int32_t c = b->rule_cond_off[r]; c < b->rule_cond_off[r + 1]; ++c) {
+                        if (b->cond_op[c] == 2) continue;           /* an indicator: no gradient */
                         const double u = margin(b, c, xrow, tau);
                         const double du = gq * exp(log_sigmoid(-u));      /* d ell / d u */
                         const double s = (b->cond_op[c] == 0) ? 1.0 : -1.0;

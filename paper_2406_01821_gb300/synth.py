@@ -14,17 +14,19 @@ Rule-set batch layout (the C-ABI ``rs_batch`` layout, all arrays contiguous):
   rule_class    int32[R]     class named by rule r
   set_default   int32[P]     class assigned when no rule of set p fires
   cond_f, cond_g int32[C]    feature indices; cond_g = -1 marks a threshold condition
-  cond_op       int8[C]      0: '>' , 1: '<'
+  cond_op       int8[C]      0: '>' , 1: '<', 2: category membership
   cond_a, cond_b, cond_t float32[C]
+  cond_set      uint64[C] or None   category sets of membership conditions (bit k: code k)
 A threshold condition reads  a*x[f] op t ; a feature-pair condition reads  a*x[f] op b*x[g]
-(Sec. 3, Fig. 1a/1b).
+(Sec. 3, Fig. 1a/1b). A membership condition (categorical features, named as future work in
+Sec. 5) reads  x[f] in S : x[f] is an integer code k in 0..63 with bit k of cond_set set.
 """
 from __future__ import annotations
 
 import dataclasses
 import numpy as np
 
-GT, LT = 0, 1
+GT, LT, IN = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -39,6 +41,7 @@ class Batch:
     cond_a: np.ndarray
     cond_b: np.ndarray
     cond_t: np.ndarray
+    cond_set: np.ndarray | None = None
 
     @property
     def P(self) -> int:
@@ -57,7 +60,8 @@ class Batch:
         return int(self.rule_cond_off[-1])
 
     def arrays(self):
-        return {f.name: getattr(self, f.name) for f in dataclasses.fields(self)}
+        return {f.name: getattr(self, f.name) for f in dataclasses.fields(self)
+                if getattr(self, f.name) is not None}
 
     def nbytes(self) -> int:
         return sum(a.nbytes for a in self.arrays().values())
@@ -77,29 +81,50 @@ class Batch:
                      self.rule_class[rules].astype(np.int32), self.set_default[sets].astype(np.int32),
                      self.cond_f[conds].astype(np.int32), self.cond_g[conds].astype(np.int32),
                      self.cond_op[conds].astype(np.int8), self.cond_a[conds].astype(np.float32),
-                     self.cond_b[conds].astype(np.float32), self.cond_t[conds].astype(np.float32))
+                     self.cond_b[conds].astype(np.float32), self.cond_t[conds].astype(np.float32),
+                     None if self.cond_set is None else self.cond_set[conds].astype(np.uint64))
 
 
 def from_lists(sets, defaults) -> Batch:
     """Build a batch from nested python lists.
 
     ``sets[p]`` is a list of rules; a rule is ``(cls, [cond, ...])`` and a condition is
-    ``(f, g, op, a, b, t)`` with ``g = -1`` for a threshold condition.
+    ``(f, g, op, a, b, t)`` with ``g = -1`` for a threshold condition, or
+    ``(f, -1, IN, 0, 0, 0, codes)`` for a membership condition on the category codes ``codes``.
+    The batch carries ``cond_set`` only when some condition is a membership test.
     """
     set_rule_off = [0]
     rule_cond_off = [0]
-    rule_class, cf, cg, cop, ca, cb, ct = [], [], [], [], [], [], []
+    rule_class, cf, cg, cop, ca, cb, ct, cs = [], [], [], [], [], [], [], []
     for rules in sets:
         for cls, conds in rules:
             rule_class.append(cls)
-            for (f, g, op, a, b, t) in conds:
+            for cond in conds:
+                f, g, op, a, b, t = cond[:6]
                 cf.append(f); cg.append(g); cop.append(op); ca.append(a); cb.append(b); ct.append(t)
+                cs.append(category_mask(cond[6]) if len(cond) > 6 else 0)
             rule_cond_off.append(len(cf))
         set_rule_off.append(len(rule_class))
     return Batch(np.array(set_rule_off, np.int32), np.array(rule_cond_off, np.int32),
                  np.array(rule_class, np.int32), np.array(defaults, np.int32),
                  np.array(cf, np.int32), np.array(cg, np.int32), np.array(cop, np.int8),
-                 np.array(ca, np.float32), np.array(cb, np.float32), np.array(ct, np.float32))
+                 np.array(ca, np.float32), np.array(cb, np.float32), np.array(ct, np.float32),
+                 np.array(cs, np.uint64) if any(op == IN for op in cop) else None)
+
+
+def category_mask(codes) -> int:
+    """64-bit set of category codes (each 0..63)."""
+    m = 0
+    for k in codes:
+        if not 0 <= int(k) <= 63:
+            raise ValueError("category codes are 0..63")
+        m |= 1 << int(k)
+    return m
+
+
+def category_codes(mask: int):
+    """Sorted codes of a 64-bit category set."""
+    return [k for k in range(64) if (int(mask) >> k) & 1]
 
 
 # ----------------------------------------------------------------------------------- datasets
@@ -125,6 +150,21 @@ def gaussian_mixture(N: int, F: int, K: int, seed: int):
     return X, y
 
 
+def categorical_mixture(N: int, F: int, K: int, seed: int, n_cat: int, n_codes: int = 16):
+    """The K-class Gaussian mixture with its last ``n_cat`` features categorical: feature j holds
+    integer codes 0..n_codes-1 (as float32) drawn per class from a category distribution that
+    is itself drawn from a symmetric Dirichlet(1) law, so the codes carry class information."""
+    X, y = gaussian_mixture(N, F, K, seed)
+    rng = np.random.default_rng([seed, 13])
+    probs = rng.dirichlet(np.ones(n_codes), size=(n_cat, K))           # [n_cat, K, n_codes]
+    for j in range(n_cat):
+        cdf = np.cumsum(probs[j], axis=1)
+        u = rng.random(N)
+        codes = np.minimum((u[:, None] > cdf[y]).sum(axis=1), n_codes - 1)
+        X[:, F - n_cat + j] = codes.astype(np.float32)
+    return X, y
+
+
 def quantile_table(X: np.ndarray, m: int = 65536) -> np.ndarray:
     """Per-feature sorted sample (F x m') used to draw thresholds at empirical quantiles."""
     sub = X[: min(len(X), m)]
@@ -134,14 +174,17 @@ def quantile_table(X: np.ndarray, m: int = 65536) -> np.ndarray:
 # ---------------------------------------------------------------------------------- rule sets
 
 def random_rulesets(qtab: np.ndarray, K: int, P: int, R, C, seed: int, pair_prob: float = 0.2,
-                    default=None) -> Batch:
+                    default=None, cat_from: int | None = None, n_codes: int = 16) -> Batch:
     """Random ordered rule sets.
 
     R and C are either an int (fixed) or an inclusive (lo, hi) range drawn uniformly per set / rule.
     Conditions: PAIR with probability ``pair_prob``; op uniform over {'>', '<'}; a, b ~ U[-1, 1];
     a threshold t = fl32(a * Q_f(q)) with q ~ U(0.05, 0.95) and Q_f the lower empirical quantile
     of feature f.  Rule class ~ U{0..K-1}.  ``default`` is an int (one class for all sets) or None
-    (uniform per set).
+    (uniform per set).  With ``cat_from``, features f >= cat_from are categorical (codes
+    0..n_codes-1): a condition on such a feature is a membership test of a random non-empty set
+    of codes (each code in with probability 1/2), and a pair whose second feature is categorical
+    becomes a threshold condition on its first.
     """
     rng = np.random.default_rng([seed, 21])
     F, m = qtab.shape
@@ -178,8 +221,22 @@ def random_rulesets(qtab: np.ndarray, K: int, P: int, R, C, seed: int, pair_prob
     qidx = np.floor(q * (m - 1)).astype(np.int64)
     Q = qtab[cond_f, qidx]
     cond_t = np.where(is_pair, np.float32(0), cond_a * Q).astype(np.float32)
+    cond_set = None
+    if cat_from is not None:
+        is_cat = cond_f >= cat_from
+        to_thr = ~is_cat & (cond_g >= cat_from)
+        cond_g = np.where(is_cat | to_thr, -1, cond_g).astype(np.int32)
+        cond_b = np.where(is_cat | to_thr, 0.0, cond_b).astype(np.float32)
+        cond_t = np.where(to_thr, cond_a * Q, cond_t).astype(np.float32)
+        cond_t = np.where(is_cat, 0.0, cond_t).astype(np.float32)
+        cond_a = np.where(is_cat, 0.0, cond_a).astype(np.float32)
+        cond_op = np.where(is_cat, IN, cond_op).astype(np.int8)
+        bits = rng.random((C_tot, n_codes)) < 0.5
+        bits[np.arange(C_tot), rng.integers(0, n_codes, size=C_tot)] = True      # non-empty
+        masks = (bits.astype(np.uint64) << np.arange(n_codes, dtype=np.uint64)).sum(axis=1, dtype=np.uint64)
+        cond_set = np.where(is_cat, masks, np.uint64(0)).astype(np.uint64)
     return Batch(set_rule_off, rule_cond_off, rule_class, set_default, cond_f, cond_g, cond_op,
-                 cond_a, cond_b, cond_t)
+                 cond_a, cond_b, cond_t, cond_set)
 
 
 def majority_class(y: np.ndarray, K: int) -> int:

@@ -3,6 +3,7 @@ compile-time switch in the oracle source, built only here) has to fail at least 
 import pytest
 
 import oracle
+import test_oracle_categorical as cat
 import test_oracle_pins as pins
 
 # plant id -> (description, pin calls that must not all pass)
@@ -17,6 +18,11 @@ PLANTS = {
     5: ("later rules not discounted", [lambda o: pins.test_soft_probabilities_sum_to_one(o)]),
     6: ("threshold gradient sign", [lambda o: pins.test_one_rule_one_condition_is_logistic_regression(o, 0, False)]),
     7: ("S used where 1 - S belongs in the adjoint", [lambda o: pins.test_adjoint_matches_central_differences(o, 0)]),
+    8: ("a fractional category value keeps its code",
+        [lambda o: cat.test_membership_edge_values(o, range(64), [1, 1, 1, 0, 1, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0]),
+         lambda o: cat.test_mixed_rulesets_match_isin_formulation(o, 0)]),
+    9: ("category bits read in the wrong order", [lambda o: cat.test_membership_bit_order(o),
+                                                   lambda o: cat.test_single_code_equals_band(o)]),
 }
 
 
