@@ -197,10 +197,12 @@ def hard_leg(args, rank, dev, ctx_mod, w):
     hb = rs.HostBatch(w.batch)
     pinned = {}
     for f, a in hb.a.items():
+        if a is None:
+            continue
         t = torch.empty(a.shape, dtype=torch.from_numpy(a).dtype, pin_memory=True)
         t.numpy()[...] = a
         pinned[f] = t
-    hb.a = {f: t.numpy() for f, t in pinned.items()}
+    hb.a = {f: (pinned[f].numpy() if f in pinned else None) for f in hb.a}
     hc = torch.empty(P, dtype=torch.int32, pin_memory=True).numpy()
     hpc = torch.empty((P, K), dtype=torch.int32, pin_memory=True).numpy()
     ctx2 = rs.Context(dev)
@@ -232,7 +234,7 @@ def hard_leg(args, rank, dev, ctx_mod, w):
 
 
 def hb_nbytes(hb):
-    return int(sum(a.nbytes for a in hb.a.values()))
+    return int(sum(a.nbytes for a in hb.a.values() if a is not None))
 
 
 def soft_leg(args, dev):
@@ -277,6 +279,51 @@ def soft_leg(args, dev):
                          "transcendentals_per_pass": xu,
                          "peak_source": f"{sms} SMs x 16 XU lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                         f"({peak_src} max clock)"}}
+
+
+def categorical_leg(args, dev):
+    """The ragged workload's shape with a quarter of the features categorical (48 codes): every
+    condition on those features is a membership test. Hard evaluation, device-resident inputs."""
+    import torch
+    import oracle
+    from paper_2406_01821_gb300 import rs, synth
+    N = (1 << 19) if args.workload == "ragged-small" else (1 << 20)
+    P = 512 if args.workload == "ragged-small" else 4096
+    F, K, n_cat = 128, 10, 32
+    X, y = synth.categorical_mixture(N, F, K, 0, n_cat=n_cat, n_codes=48)
+    b = synth.random_rulesets(synth.quantile_table(X), K, P, (1, 64), (1, 8), 0, cat_from=F - n_cat, n_codes=48)
+    ctx = rs.Context(dev, flags=rs.CTX_PROFILE)
+    stream = torch.cuda.Stream(device=dev)
+    ds = ctx.dataset(X, y, K)
+    db = rs.DeviceBatch.from_host(b, device=f"cuda:{dev}")
+    out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty((P, K), dtype=torch.int32, device=dev), None)
+    for _ in range(max(1, args.warmup)):
+        ctx.eval_hard(ds, db, K, out=out, stream=stream)
+    stream.synchronize()
+    ctx.profile(reset=True)
+    steps = max(1, args.steps // 2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.eval_hard(ds, db, K, out=out, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = ctx.profile(reset=True)
+    ctx.close()
+    nominal = b.nominal_conditions() * N
+    n_s = 1024
+    nt = oracle.num_threads(0)
+    t0 = time.perf_counter()
+    oracle.eval_hard(X[:n_s], y[:n_s], K, b, nthreads=nt)
+    dt = time.perf_counter() - t0
+    return {"workload": f"categorical P={P} R=1..64 C=1..8 N={N} F={F} ({n_cat} categorical, 48 codes) K={K}",
+            "metric": METRIC, "value": nominal / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "membership_conditions": int((b.cond_op == synth.IN).sum()), "conditions": int(b.C),
+            "kernel_ms": prof["hard_ms"] / max(1, prof["hard_launches"]),
+            "cpu_baseline": {"value": b.nominal_conditions() * n_s / dt, "unit": UNIT, "cores": nt,
+                             "kind": "oracle", "sample": f"all {P} sets on the first {n_s} samples ({dt:.2f} s)"}}
 
 
 def soft_transcendentals(batch, N):
@@ -549,7 +596,7 @@ def main():
                          "P=256) are the cases used for ncu captures")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="force a tile configuration id")
-    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving)")
+    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving,categorical)")
     ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -595,7 +642,8 @@ def main():
              if counters and "issue_active_pct" in counters else None)
     extras = {}
     if not args.no_extras and d.rank == 0:
-        for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("serving", serving_leg)):
+        for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("serving", serving_leg),
+                          ("categorical", categorical_leg)):
             if name in args.skip:
                 continue
             try:

@@ -119,10 +119,21 @@ rs_status rs_dataset_info(rs_ctx *ctx, uint64_t ds, int64_t *N, int32_t *F, int3
  *   set_default   int32[P]    class of set p when no rule fires, 0..K-1
  *   cond_f        int32[C]    feature of the left-hand product, 0..F-1
  *   cond_g        int32[C]    -1: threshold condition a*x[f] op t; else 0..F-1: a*x[f] op b*x[g]
- *   cond_op       int8[C]     0: '>', 1: '<'
- *   cond_a, cond_b, cond_t  float32[C]   (b unused for thresholds, t unused for pairs)
+ *   cond_op       int8[C]     RS_OP_GT '>', RS_OP_LT '<', RS_OP_IN category membership
+ *   cond_a, cond_b, cond_t  float32[C]   (b unused for thresholds, t unused for pairs; all
+ *                             three unused by membership conditions)
+ *   cond_set      uint64[C]   category set of each RS_OP_IN condition (bit k: code k), read only
+ *                             for those; NULL when no condition has op RS_OP_IN
+ * A membership condition (categorical features, the future work of Sec. 5) has cond_g = -1 and is
+ * true iff x[f] is an integer category code k, 0 <= k <= 63, whose bit is set in cond_set[c]
+ * (fractions, negatives, codes above 63, NaN and infinities are in no set). The soft path keeps it
+ * as its exact 0/1 indicator (no gradient). Evolution (rs_evolve) works on inequalities only.
  * P >= 0, R >= 0, C >= 0; P, R, C < 2^31 - 1; a rule has at most 4095 conditions.
  */
+#define RS_OP_GT 0
+#define RS_OP_LT 1
+#define RS_OP_IN 2
+
 typedef struct {
     int32_t P, R, C;
     int32_t mem;
@@ -136,6 +147,7 @@ typedef struct {
     const float *cond_a;
     const float *cond_b;
     const float *cond_t;
+    const uint64_t *cond_set;
 } rs_batch;
 
 /* ------------------------------------------------------------------------ hard evaluation */

@@ -49,17 +49,19 @@ static rs_status stage_batch(const rs_batch *b, cudaStream_t stream, StagedBatch
         out.d.rule_class = b->rule_class; out.d.set_default = b->set_default;
         out.d.cond_f = b->cond_f; out.d.cond_g = b->cond_g; out.d.cond_op = b->cond_op;
         out.d.cond_a = b->cond_a; out.d.cond_b = b->cond_b; out.d.cond_t = b->cond_t;
+        out.d.cond_set = b->cond_set;
         return RS_OK;
     }
     const size_t P = b->P, R = b->R, C = b->C;
-    size_t off[10], sz[10] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C};
-    const void *src[10] = {b->set_rule_off, b->rule_cond_off, b->rule_class, b->set_default,
-                           b->cond_f, b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t};
+    const size_t cs = b->cond_set ? 8 * C : 0;
+    size_t off[11], sz[11] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C, cs};
+    const void *src[11] = {b->set_rule_off, b->rule_cond_off, b->rule_class, b->set_default,
+                           b->cond_f, b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t, b->cond_set};
     size_t total = 0;
-    for (int i = 0; i < 10; ++i) { off[i] = total; total = align_up(total + sz[i], 256); }
+    for (int i = 0; i < 11; ++i) { off[i] = total; total = align_up(total + sz[i], 256); }
     RS_CUDA(cudaMallocAsync(&out.buf, std::max<size_t>(total, 256), stream));
     char *base = static_cast<char *>(out.buf);
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < 11; ++i)
         if (sz[i]) RS_CUDA(cudaMemcpyAsync(base + off[i], src[i], sz[i], cudaMemcpyHostToDevice, stream));
     out.d.set_rule_off = (const int32_t *)(base + off[0]);
     out.d.rule_cond_off = (const int32_t *)(base + off[1]);
@@ -71,6 +73,7 @@ static rs_status stage_batch(const rs_batch *b, cudaStream_t stream, StagedBatch
     out.d.cond_a = (const float *)(base + off[7]);
     out.d.cond_b = (const float *)(base + off[8]);
     out.d.cond_t = (const float *)(base + off[9]);
+    out.d.cond_set = b->cond_set ? (const uint64_t *)(base + off[10]) : nullptr;
     return RS_OK;
 }
 
@@ -82,7 +85,7 @@ static std::string tune_key(const Dataset &ds, const rs_batch *b)
     const int cb = (int)std::lround(std::min(meanC, 16.0) * 2);   // half-condition buckets
     const int nb = (int)std::floor(std::log2((double)ds.N));
     std::ostringstream k;
-    k << "F" << ds.F << "|K" << ds.K << "|C" << cb << "|N" << nb;
+    k << "F" << ds.F << "|K" << ds.K << "|C" << cb << "|N" << nb << (b->cond_set ? "|cat" : "");
     return k.str();
 }
 
@@ -177,13 +180,15 @@ static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t 
 }
 
 // Enqueue pack + evaluation (the part a graph captures).
-rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
+rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc_in, const BatchDev &bd,
                               const Scratch &s, int32_t *correct, int32_t *per_class,
                               int32_t *preds, cudaStream_t stream)
 {
     PackOut po;
     po.recs = s.recs; po.sets = s.sets; po.order = s.order; po.status = s.status;
     po.last_end = ds->K <= LAST_END_MAX_K ? s.last_end : nullptr;
+    // batches with membership conditions run the forms that evaluate them (rank-coded or v1)
+    const TileConfig &tc = bd.cond_set ? categorical_config(tc_in, *ds, preds != nullptr) : tc_in;
     const int ver = effective_version(tc, *ds, preds != nullptr);
     const int pack_ver = ver == 5 ? 5 : (ver == 4 ? 4 : (ver >= 2 ? 2 : 1));
     count_launch(ctx, launch_pack(bd, ds->F, ds->K, tc.S(), pack_ver, po, stream));
@@ -273,7 +278,8 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
         // (same topology -> in-place parameter update; otherwise re-instantiate).
         std::ostringstream key;
         key << "ds" << ds_h << "|t" << tid << "|s" << (uintptr_t)stream << "|pc" << (per_class != nullptr)
-            << "|pr" << (preds != nullptr) << "|P" << (b->P > 0) << "|R" << (b->R > 0);
+            << "|pr" << (preds != nullptr) << "|P" << (b->P > 0) << "|R" << (b->R > 0)
+            << "|cat" << (b->cond_set != nullptr);
         cudaGraph_t g = nullptr;
         RS_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
         rs_status erc = enqueue_hard(ctx, ds.get(), tc, sb.d, s, d_correct, d_pc, d_preds, stream);

@@ -92,6 +92,15 @@ __device__ __forceinline__ uint32_t pass_row(uint4 q, const unsigned char *xl)
     return gt_bytes(p, r);
 }
 
+// Pass row of a membership condition, staged as {byte offset of row f, -, set bits 0..31, set
+// bits 32..63}: 0xFF in byte v where the lane's sample v holds a category code in the set.
+__device__ __forceinline__ uint32_t set_row(uint4 q, const unsigned char *xl)
+{
+    const float4 x = *reinterpret_cast<const float4 *>(xl + q.x);
+    return (category_member(x.x, q.z, q.w) ? 0x000000FFu : 0u) | (category_member(x.y, q.z, q.w) ? 0x0000FF00u : 0u) |
+           (category_member(x.z, q.z, q.w) ? 0x00FF0000u : 0u) | (category_member(x.w, q.z, q.w) ? 0xFF000000u : 0u);
+}
+
 // One group of four staged records with end-of-rule flags M (bit u: record u ends its rule).
 template <uint32_t M, bool UNI>
 __device__ __forceinline__ void group4(const uint32_t (&e)[4], const uint32_t *sw, const int32_t *yl,
@@ -145,11 +154,13 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
         const uint32_t tag = raw.x >> R5_TAG_SHIFT;
         int cnt = min(32, nrec - c0);
         uint32_t pm = __ballot_sync(FULL, lane < cnt && (tag == R5_PAIR || tag == R5_GEN));
-        if (__popc(pm) > VS) {              // end the chunk before the pair that finds no slot
-            uint32_t m = pm;
+        uint32_t sm = __ballot_sync(FULL, lane < cnt && tag == R5_SET);       // membership tests
+        if (__popc(pm | sm) > VS) {         // end the chunk before the pass row that finds no slot
+            uint32_t m = pm | sm;
             for (int k = 0; k < VS; ++k) m &= m - 1u;
             cnt = __ffs(m) - 1;
             pm &= (1u << cnt) - 1u;
+            sm &= (1u << cnt) - 1u;
         }
         const uint32_t ends = __ballot_sync(FULL, lane < cnt && (raw.x & R5_END_BIT) != 0u);
         pf = (c0 + cnt + lane < nrec) ? __ldcg(recs + rb + c0 + cnt + lane) : zero4;
@@ -160,18 +171,23 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
         const uint32_t cls = (raw.x >> R5_CLS_SHIFT) & 0xFFFu;
         const uint32_t ew = UNI ? ((int)cls == kmine ? 0xFFFFFFFFu : 0u) : cls;
         uint2 sr = stage_cut(raw, us, rev_off, F);
+        const int np = __popc(pm);
         if ((pm >> lane) & 1u) {
             const uint32_t slot = __popc(pm & ((1u << lane) - 1u));
             const uint32_t f = min(raw.x & R5_F_MASK, (uint32_t)(F - 1));
             const uint32_t g = min(raw.y, (uint32_t)(F - 1));
             st[slot] = make_uint4(f * (T * 4u), tag == R5_PAIR ? g * (T * 4u) : ones_off, raw.z, raw.w);
             sr = make_uint2(vrow_off + 128u * slot, FULL);
+        } else if ((sm >> lane) & 1u) {
+            const uint32_t slot = np + __popc(sm & ((1u << lane) - 1u));
+            const uint32_t f = min(raw.x & R5_F_MASK, (uint32_t)(F - 1));
+            st[slot] = make_uint4(f * (T * 4u), 0u, raw.z, raw.w);
+            sr = make_uint2(vrow_off + 128u * slot, FULL);
         } else if (lane >= cnt || tag == R5_NONE) {
             sr = make_uint2(0u, NOOP_K);
         }
         __syncwarp();
         {                                             // pass rows, one warp-wide evaluation each
-            const int np = __popc(pm);
             uint32_t *vr = vrow + lane;
             for (int j = 0; j < np; j += 2) {
                 const uint32_t v0 = pass_row(st[j], xl);
@@ -179,6 +195,7 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
                 vr[0] = v0;
                 vr += 64;
             }
+            for (int j = np; j < np + __popc(sm); ++j) vrow[j * 32 + lane] = set_row(st[j], xl);
         }
         __syncwarp();
         s8[lane] = sr;

@@ -676,6 +676,7 @@ rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, fl
     sa.b.rule_class = b->rule_class; sa.b.set_default = b->set_default;
     sa.b.cond_f = b->cond_f; sa.b.cond_g = b->cond_g; sa.b.cond_op = b->cond_op;
     sa.b.cond_a = pa; sa.b.cond_b = pb; sa.b.cond_t = pt;
+    sa.b.cond_set = b->cond_set;          // membership tests: indicators, no gradient, unchanged
     sa.Xt = ds.Xt; sa.y = ds.y; sa.perm = ds.perm; sa.N = ds.N; sa.n_pad = ds.n_pad;
     sa.F = ds.F; sa.K = ds.K; sa.tau = tau; sa.loss = loss; sa.dloss = dl;
     sa.grad_a = ga; sa.grad_b = gb; sa.grad_t = gt; sa.status = status;

@@ -163,6 +163,9 @@ __global__ void __launch_bounds__(W * 32) k_hard(const __grid_constant__ CUtenso
             } else if (kind == KIND_MLT) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) al[v] = al[v] && (__fmul_rn(v0, x[v]) < v1);
+            } else if (kind == KIND_IN) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) al[v] = al[v] && category_member(x[v], raw.z, raw.w);
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) al[v] = false;
@@ -282,6 +285,16 @@ int effective_version(const TileConfig &tc, const Dataset &ds, bool preds)
 }
 
 const TileConfig &tile_config(int id) { return kConfigs[id]; }
+
+// Membership conditions are evaluated by the rank-coded form and by v1; a configuration of
+// another form is replaced by the first v1 configuration that fits the dataset.
+const TileConfig &categorical_config(const TileConfig &tc, const Dataset &ds, bool preds)
+{
+    if (tc.ver == 1 || effective_version(tc, ds, preds) == 5) return tc;
+    for (int id : {0, 5, 23})
+        if (tile_config_fits(kConfigs[id], ds.F)) return kConfigs[id];
+    return kConfigs[23];
+}
 
 bool tile_config_fits(const TileConfig &tc, int F)
 {

@@ -101,6 +101,7 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
     bd.rule_class = b->rule_class; bd.set_default = b->set_default;
     bd.cond_f = b->cond_f; bd.cond_g = b->cond_g; bd.cond_op = b->cond_op;
     bd.cond_a = b->cond_a; bd.cond_b = b->cond_b; bd.cond_t = b->cond_t;
+    bd.cond_set = b->cond_set;
 
     const int tid = ctx->forced_tile >= 0 && tile_config_fits(tile_config(ctx->forced_tile), ds->F)
                         ? ctx->forced_tile

@@ -182,11 +182,13 @@ __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, int32_t *last_end,
 }
 
 // Kind of a condition in format v5, decided with the same tests as rewrite_threshold (without its
-// search): R5_CUT_GT / R5_CUT_LT for a +-cut, R5_PAIR, or R5_GEN for everything else (zero or
-// infinite coefficient, never-true conditions, invalid input).
+// search): R5_CUT_GT / R5_CUT_LT for a +-cut, R5_PAIR, R5_SET for a category membership test,
+// or R5_GEN for everything else (zero or infinite coefficient, never-true conditions, invalid
+// input).
 __device__ uint32_t kind5(const BatchDev &b, int c, int F)
 {
     const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
+    if (op == RS_OP_IN && b.cond_set && g == -1 && f >= 0 && f < F) return R5_SET;
     if (f < 0 || f >= F || g < -1 || g >= F || (op != 0 && op != 1)) return R5_GEN;
     if (g >= 0) return R5_PAIR;
     const float a = b.cond_a[c], t = b.cond_t[c];
@@ -239,6 +241,10 @@ __global__ void k_pack_rules5(BatchDev b, int F, int K, Rec *recs_out, uint32_t 
             rec = make_uint4((R5_PAIR << R5_TAG_SHIFT) | (uint32_t)lf, (uint32_t)rg, __float_as_uint(a),
                              __float_as_uint(bb));
             q = qp++;
+        } else if (k == R5_SET) {
+            const uint64_t set = b.cond_set[c];
+            rec = make_uint4((R5_SET << R5_TAG_SHIFT) | (uint32_t)f, 0u, (uint32_t)set, (uint32_t)(set >> 32));
+            q = qg++;
         } else {
             float v0 = 0.f, v1 = pinf;   // never true
             uint32_t rf = 0;
@@ -272,6 +278,12 @@ __global__ void k_pack_rules(BatchDev b, int F, int K, Rec *recs, uint32_t *stat
         int rf = 0, rg = 0;
         if (f < 0 || f >= F || g < -1 || g >= F) {
             atomicOr(status, ST_BAD_FEATURE);
+        } else if (op == RS_OP_IN && b.cond_set && g == -1) {
+            const uint64_t set = b.cond_set[c];
+            kind = KIND_IN;
+            v0 = __uint_as_float((uint32_t)set);
+            v1 = __uint_as_float((uint32_t)(set >> 32));
+            rf = f;
         } else if (op != 0 && op != 1) {
             atomicOr(status, ST_BAD_OP);
         } else if (g < 0) {

@@ -53,6 +53,7 @@ enum : uint32_t {
     KIND_MGT = 3,    // fl(v0 * x[f]) > v1  (coefficient 0 / inf: kept as the plain product)
     KIND_MLT = 4,    // fl(v0 * x[f]) < v1
     KIND_NEVER = 5,  // never true
+    KIND_IN = 6,     // x[f] an integer category code k in 0..63 with bit k of (v1 bits : v0 bits)
 };
 
 // Record format v2 (rule-at-a-time evaluator): w0 = [0,18) feature row offset in 16-byte units |
@@ -71,7 +72,8 @@ constexpr uint32_t GENERAL_BIT = 1u << 31;
 //   cut:     x[f] > w2 (R5_CUT_GT) or x[f] <= w2 (R5_CUT_LT: x[f] < c stored as w2 = nextdown(c))
 //   pair:    fl(w2 * x[f]) > fl(w3 * x[w1])
 //   product: fl(w2 * x[f]) > w3
-enum : uint32_t { R5_NONE = 0, R5_CUT_GT = 2, R5_CUT_LT = 3, R5_PAIR = 4, R5_GEN = 5 };
+//   set:     x[f] an integer category code k in 0..63 with bit k of the 64-bit set (w3 : w2)
+enum : uint32_t { R5_NONE = 0, R5_CUT_GT = 2, R5_CUT_LT = 3, R5_PAIR = 4, R5_GEN = 5, R5_SET = 6 };
 constexpr int R5_TAG_SHIFT = 29;
 constexpr uint32_t R5_END_BIT = 1u << 28;
 constexpr int R5_CLS_SHIFT = 16;
@@ -104,7 +106,18 @@ struct BatchDev {
     const int32_t *cond_f, *cond_g;
     const int8_t *cond_op;
     const float *cond_a, *cond_b, *cond_t;
+    const uint64_t *cond_set = nullptr;   // category sets (membership conditions), or null
 };
+
+// Membership of one value in a 64-bit category set: an integer code 0..63 whose bit is set
+// (false for fractions, negatives, codes above 63, NaN and infinities).
+__host__ __device__ __forceinline__ bool category_member(float x, uint32_t lo, uint32_t hi)
+{
+    if (!(x >= 0.f && x <= 63.f)) return false;
+    const int k = (int)x;
+    if ((float)k != x) return false;
+    return ((k < 32 ? lo : hi) >> (k & 31)) & 1u;
+}
 
 // ------------------------------------------------------------------------------ datasets
 
@@ -259,6 +272,7 @@ rs_status launch_hard5(Ctx *ctx, Dataset *ds, int W, const HardArgs &a, cudaStre
 size_t hard5_smem_bytes(int F, int W);
 // The evaluator version a configuration runs as for this dataset and output choice.
 int effective_version(const TileConfig &tc, const Dataset &ds, bool preds);
+const TileConfig &categorical_config(const TileConfig &tc, const Dataset &ds, bool preds);
 // Enqueue packing + evaluation of a device batch with the given scratch.
 rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const BatchDev &bd,
                        const Scratch &s, int32_t *correct, int32_t *per_class, int32_t *preds,

@@ -335,13 +335,15 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Requests on datasets with rank tables use the rank-coded evaluator when they have enough sets
 // to amortise its tile staging (x, ranks and sorted columns, and one search per cut and tile).
-bool serve_ranked(const Dataset &ds, int P)
+// Requests with membership conditions always take them (the sign-mask units have no membership
+// test).
+bool serve_ranked(const Dataset &ds, int P, bool cat)
 {
-    return ds.ranked && ds.F <= SERVE_RANK_MAX_F && P >= SERVE_RANK_MIN_P;
+    return ds.ranked && ds.F <= SERVE_RANK_MAX_F && (P >= SERVE_RANK_MIN_P || cat);
 }
-int64_t serve_groups(const Dataset &ds, int P)
+int64_t serve_groups(const Dataset &ds, int P, bool cat)
 {
-    const int g = serve_ranked(ds, P) ? GROUP_SETS_RANKED : GROUP_SETS;
+    const int g = serve_ranked(ds, P, cat) ? GROUP_SETS_RANKED : GROUP_SETS;
     return std::max<int64_t>(1, (P + g - 1) / g);
 }
 
@@ -358,7 +360,8 @@ struct Request {
     int32_t maxR = 0, maxC = 0;           // soft requests: largest set (rules, conditions)
     void *h_stage = nullptr;              // pinned copy of the batch arrays
     size_t stage_bytes = 0, stage_cap = 0, result_cap = 0;   // pinned buffer capacities
-    size_t off[10] = {};
+    size_t off[11] = {};
+    bool cat = false;                     // the batch carries category sets
     size_t device_bytes = 0;
     void *d_buf = nullptr;
     int slot = -1;
@@ -538,11 +541,12 @@ void server_shutdown(Ctx *ctx)
     ctx->server = nullptr;
 }
 
-static size_t request_device_bytes(int64_t P, int64_t R, int64_t C, int64_t K)
+static size_t request_device_bytes(int64_t P, int64_t R, int64_t C, int64_t K, bool cat)
 {
     size_t b = 0;
     b += align256(4 * (P + 1)) + align256(4 * (R + 1)) + align256(4 * R) + align256(4 * P);
     b += 3 * align256(4 * C) + align256(C) + 3 * align256(4 * C);       // condition arrays
+    if (cat) b += align256(8 * C);                                       // category sets
     b += align256(16 * std::max<int64_t>(C, 1)) + align256(16 * std::max<int64_t>(P, 1)) +
          align256(4 * std::max<int64_t>(P, 1));                          // records, sets, order
     b += align256(4 * P) + align256(4 * P * K) + 256;                   // outputs, status
@@ -565,35 +569,42 @@ rs_status submit_impl(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, 
         set_error("hard requests are served on datasets of at most %d features", SERVE_MAX_F);
         return RS_ERR_UNSUPPORTED;
     }
+    const bool cat = b->cond_set != nullptr;
+    if (kind == RS_KIND_HARD && cat && !serve_ranked(*ds, b->P, true)) {
+        set_error("hard requests with membership conditions are served on finite datasets of at most %d "
+                  "features", SERVE_RANK_MAX_F);
+        return RS_ERR_UNSUPPORTED;
+    }
     rs_status rc = device_guard(ctx);
     if (rc) return rc;
     Server *s = nullptr;
     if ((rc = server_get(ctx, &s))) return rc;
     auto r = std::make_shared<Request>();
     r->ds = ds;
-    r->P = b->P; r->R = b->R; r->C = b->C; r->K = ds->K; r->kind = kind; r->tau = tau;
-    r->device_bytes = request_device_bytes(b->P, b->R, b->C, ds->K);
+    r->P = b->P; r->R = b->R; r->C = b->C; r->K = ds->K; r->kind = kind; r->tau = tau; r->cat = cat;
+    r->device_bytes = request_device_bytes(b->P, b->R, b->C, ds->K, cat);
     if (r->device_bytes > ctx->budget) {
         set_error("request needs %zu bytes of device memory; the budget is %llu", r->device_bytes,
                   (unsigned long long)ctx->budget);
         return RS_ERR_TOO_LARGE;
     }
-    const int64_t units = ((ds->N + SS - 1) / SS) * serve_groups(*ds, b->P);
+    const int64_t units = ((ds->N + SS - 1) / SS) * serve_groups(*ds, b->P, cat);
     if (kind == RS_KIND_HARD && units > (int64_t)CW_MASK) {
         set_error("request too large to serve (%lld work units)", (long long)units);
         return RS_ERR_TOO_LARGE;
     }
     // copy the batch into pinned staging: the caller may free its arrays on return
     const size_t P = b->P, R = b->R, C = b->C;
-    const size_t sz[10] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C};
-    const void *src[10] = {b->set_rule_off, b->rule_cond_off, b->rule_class, b->set_default,
-                           b->cond_f, b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t};
+    const size_t sz[11] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C,
+                           cat ? 8 * C : 0};
+    const void *src[11] = {b->set_rule_off, b->rule_cond_off, b->rule_class, b->set_default,
+                           b->cond_f, b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t, b->cond_set};
     size_t tot = 0;
-    for (int i = 0; i < 10; ++i) { r->off[i] = tot; tot = align256(tot + sz[i]); }
+    for (int i = 0; i < 11; ++i) { r->off[i] = tot; tot = align256(tot + sz[i]); }
     r->stage_bytes = tot;
     r->h_stage = pinned_get(s, std::max<size_t>(tot, 256), &r->stage_cap);
     if (!r->h_stage) { set_error("pinned host memory exhausted"); return RS_ERR_OOM; }
-    for (int i = 0; i < 10; ++i) {
+    for (int i = 0; i < 11; ++i) {
         if (!sz[i]) continue;
         if (!src[i]) {
             pinned_put(s, r->h_stage, r->stage_cap);
@@ -681,10 +692,11 @@ static bool admit_soft(Server *s, Request &r)
     r.d_buf = base;
     s->used += r.device_bytes;
     r.t_admit = std::chrono::steady_clock::now();
-    for (int i = 0; i < 10; ++i)
-        cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
-                        (i + 1 < 10 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
-                        s->sstream);
+    for (int i = 0; i < 11; ++i)
+        if ((i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) > r.off[i])
+            cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
+                            (i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
+                            s->sstream);
     char *p = base + r.stage_bytes;
     SoftArgs a{};
     a.b.P = r.P; a.b.R = r.R; a.b.C = r.C;
@@ -693,6 +705,7 @@ static bool admit_soft(Server *s, Request &r)
     a.b.cond_f = (int32_t *)(base + r.off[4]); a.b.cond_g = (int32_t *)(base + r.off[5]);
     a.b.cond_op = (int8_t *)(base + r.off[6]); a.b.cond_a = (float *)(base + r.off[7]);
     a.b.cond_b = (float *)(base + r.off[8]); a.b.cond_t = (float *)(base + r.off[9]);
+    a.b.cond_set = r.cat ? (uint64_t *)(base + r.off[10]) : nullptr;
     float *d_loss = (float *)p; p += align256(4 * std::max<size_t>(r.P, 1));
     r.d_status = (uint32_t *)p;
     a.Xt = r.ds->Xt; a.y = r.ds->y; a.perm = r.ds->perm; a.N = r.ds->N; a.n_pad = r.ds->n_pad;
@@ -711,7 +724,7 @@ static bool try_admit(Server *s, Request &r)
 {
     if (r.kind == RS_KIND_SOFT) return admit_soft(s, r);
     const int64_t tiles = (r.ds->N + SS - 1) / SS;
-    const int64_t groups = serve_groups(*r.ds, r.P);
+    const int64_t groups = serve_groups(*r.ds, r.P, r.cat);
     if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
     if (cudaMallocAsync(&base, r.device_bytes, s->sstream) != cudaSuccess) {
@@ -724,10 +737,11 @@ static bool try_admit(Server *s, Request &r)
     s->used += r.device_bytes;
     r.t_admit = std::chrono::steady_clock::now();
     // batch arrays
-    for (int i = 0; i < 10; ++i)
-        cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
-                        (i + 1 < 10 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
-                        s->sstream);
+    for (int i = 0; i < 11; ++i)
+        if ((i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) > r.off[i])
+            cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
+                            (i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
+                            s->sstream);
     char *p = base + r.stage_bytes;
     BatchDev bd{};
     bd.P = r.P; bd.R = r.R; bd.C = r.C;
@@ -736,6 +750,7 @@ static bool try_admit(Server *s, Request &r)
     bd.cond_f = (int32_t *)(base + r.off[4]); bd.cond_g = (int32_t *)(base + r.off[5]);
     bd.cond_op = (int8_t *)(base + r.off[6]); bd.cond_a = (float *)(base + r.off[7]);
     bd.cond_b = (float *)(base + r.off[8]); bd.cond_t = (float *)(base + r.off[9]);
+    bd.cond_set = r.cat ? (uint64_t *)(base + r.off[10]) : nullptr;
     PackOut po;
     po.recs = (Rec *)p; p += align256(16 * std::max(r.C, 1));
     po.sets = (SetInfo *)p; p += align256(16 * std::max(r.P, 1));
@@ -752,7 +767,7 @@ static bool try_admit(Server *s, Request &r)
         cudaMemsetAsync(r.d_pc, 0, 4 * (size_t)r.P * r.K, s->sstream);
     }
     const bool finite = r.ds->finite;
-    const bool ranked = serve_ranked(*r.ds, r.P);
+    const bool ranked = serve_ranked(*r.ds, r.P, r.cat);
     count_launch(s->ctx, launch_pack(bd, r.ds->F, r.K, SS, ranked ? 5 : (finite ? 4 : 2), po, s->sstream));
     ReqDesc d{};
     d.Xt = r.ds->Xt; d.y = r.ds->y; d.N = r.ds->N; d.n_pad = r.ds->n_pad; d.F = r.ds->F; d.K = r.K;

@@ -36,9 +36,10 @@ constexpr int SOFT_MAX_CONDS = 512;       // conditions per set accumulated in s
 constexpr int SOFT_MAX_CHUNKS = 64;
 
 struct __align__(16) SoftRec {
-    uint32_t meta;    // bit 0: pair condition, bit 1: '<'
+    uint32_t meta;    // bit 0: pair condition, bit 1: '<', bit 2: category membership
     uint16_t f, g;
-    float a, bt;      // bt = threshold t, or the pair coefficient b
+    float a, bt;      // bt = threshold t, or the pair coefficient b; a membership test holds the
+                      // bits of its category set (0..31 in a, 32..63 in bt)
 };
 
 __global__ void k_pack_soft(BatchDev b, int F, int K, SoftRec *recs, uint32_t *status)
@@ -49,7 +50,13 @@ __global__ void k_pack_soft(BatchDev b, int F, int K, SoftRec *recs, uint32_t *s
     const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
     SoftRec r{0, 0, 0, 0.f, 0.f};
     if (f < 0 || f >= F || g < -1 || g >= F) atomicOr(status, ST_BAD_FEATURE);
-    else if (op != 0 && op != 1) atomicOr(status, ST_BAD_OP);
+    else if (op == RS_OP_IN && b.cond_set && g == -1) {
+        const uint64_t set = b.cond_set[c];
+        r.meta = 4u;
+        r.f = (uint16_t)f;
+        r.a = __uint_as_float((uint32_t)set);
+        r.bt = __uint_as_float((uint32_t)(set >> 32));
+    } else if (op != 0 && op != 1) atomicOr(status, ST_BAD_OP);
     else {
         r.meta = (g >= 0 ? 1u : 0u) | (op == 1 ? 2u : 0u);
         r.f = (uint16_t)f;
@@ -165,6 +172,10 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         float s = 0.f;
         for (int c = c0; c < c1; ++c) {
             const SoftRec rc = a.recs[c];
+            if (rc.meta & 4u) {          // membership: its exact indicator, a factor 1 or 0 of q_r
+                if (!category_member(x(rc.f), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s = -INFINITY;
+                continue;
+            }
             const float lhs = rc.a * x(rc.f);
             const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g) : rc.bt;
             float u = (lhs - rhs) * a.inv_tau;
@@ -204,6 +215,7 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
         for (int c = c0; c < c1; ++c) {
             const SoftRec rc = a.recs[c];
+            if (rc.meta & 4u) continue;   // membership tests have no gradient
             const float xf = x(rc.f);
             const bool pair = rc.meta & 1u;
             const float xg = pair ? x(rc.g) : 0.f;

@@ -18,6 +18,7 @@ OK, PENDING = 0, 1
 ERR = {-1: "RS_ERR_INVALID", -2: "RS_ERR_TOO_LARGE", -3: "RS_ERR_OOM", -4: "RS_ERR_TIMEOUT",
        -5: "RS_ERR_DEVICE", -6: "RS_ERR_UNSUPPORTED", -7: "RS_ERR_NOT_FOUND", -8: "RS_ERR_CANCELLED"}
 MEM_HOST, MEM_DEVICE = 0, 1
+OP_GT, OP_LT, OP_IN = 0, 1, 2          # cond_op values (OP_IN: category membership)
 CTX_ASYNC, CTX_NO_GRAPH, CTX_NO_AUTOTUNE, CTX_PROFILE = 1, 2, 4, 8
 
 
@@ -39,7 +40,8 @@ class rs_batch(ctypes.Structure):
                 ("rule_class", ctypes.c_void_p), ("set_default", ctypes.c_void_p),
                 ("cond_f", ctypes.c_void_p), ("cond_g", ctypes.c_void_p),
                 ("cond_op", ctypes.c_void_p), ("cond_a", ctypes.c_void_p),
-                ("cond_b", ctypes.c_void_p), ("cond_t", ctypes.c_void_p)]
+                ("cond_b", ctypes.c_void_p), ("cond_t", ctypes.c_void_p),
+                ("cond_set", ctypes.c_void_p)]
 
 
 class rs_profile(ctypes.Structure):
@@ -197,6 +199,9 @@ class DeviceBatch:
         for f in _FIELDS:
             a = np.ascontiguousarray(getattr(batch, f), _DTYPES.get(f, np.int32))
             t[f] = torch.from_numpy(a).to(device)
+        cs = getattr(batch, "cond_set", None)
+        if cs is not None:        # 64-bit category sets, carried as int64 bit patterns
+            t["cond_set"] = torch.from_numpy(np.ascontiguousarray(cs, np.uint64).view(np.int64)).to(device)
         return cls(t)
 
     def with_params(self, a=None, b=None, t=None) -> "DeviceBatch":
@@ -210,7 +215,8 @@ class DeviceBatch:
         return DeviceBatch(d)
 
     def c(self) -> rs_batch:
-        return rs_batch(self.P, self.R, self.C, MEM_DEVICE, *[_ptr(self.t[f]) for f in _FIELDS])
+        return rs_batch(self.P, self.R, self.C, MEM_DEVICE, *[_ptr(self.t[f]) for f in _FIELDS],
+                        _ptr(self.t.get("cond_set")))
 
 
 class HostBatch:
@@ -218,12 +224,15 @@ class HostBatch:
 
     def __init__(self, batch):
         self.a = {f: np.ascontiguousarray(getattr(batch, f), _DTYPES.get(f, np.int32)) for f in _FIELDS}
+        cs = getattr(batch, "cond_set", None)
+        self.a["cond_set"] = None if cs is None else np.ascontiguousarray(cs, np.uint64)
         self.P = int(self.a["set_default"].shape[0])
         self.R = int(self.a["rule_class"].shape[0])
         self.C = int(self.a["cond_f"].shape[0])
 
     def c(self) -> rs_batch:
-        return rs_batch(self.P, self.R, self.C, MEM_HOST, *[_ptr(self.a[f]) for f in _FIELDS])
+        return rs_batch(self.P, self.R, self.C, MEM_HOST, *[_ptr(self.a[f]) for f in _FIELDS],
+                        _ptr(self.a["cond_set"]))
 
 
 # ------------------------------------------------------------------------------- context

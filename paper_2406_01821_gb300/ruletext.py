@@ -4,7 +4,8 @@
   ``1. (mean radius > 2.02) & (fractal dimension error > 0.38 x worst compactness) -> malignant``,
   plus, in this library's format, a final ``else -> <class>`` line for the default class.
   A condition is ``(lhs op rhs)`` with op ``>`` or ``<``; ``lhs`` is ``name`` (a = 1), ``-name``
-  (a = -1) or ``a x name``; ``rhs`` is a threshold ``t`` or ``b x name``.
+  (a = -1) or ``a x name``; ``rhs`` is a threshold ``t`` or ``b x name``. A membership test on a
+  categorical feature reads ``(name in {0, 2, 5})`` (its category codes).
 * Tensor form (Fig. 1a): one row per condition, ``sum_j w_j x_j + bias > 0``. A threshold
   condition ``a x_f > t`` is the row w_f = a, bias = -t; a feature pair ``a x_f > b x_g`` is
   w_f = a, w_g = -b, bias 0. A ``<`` condition is written as the row of the negated ``>`` form
@@ -22,7 +23,7 @@ import numpy as np
 
 from . import synth
 
-Cond = Tuple[int, int, int, float, float, float]      # (f, g, op, a, b, t), g = -1: threshold
+Cond = tuple                                          # (f, g, op, a, b, t[, codes]), g = -1: threshold
 Rule = Tuple[int, List[Cond]]                          # (class, conditions)
 
 
@@ -48,13 +49,17 @@ def _term(coef: float, name: str, digits: Optional[int]) -> str:
 
 
 def set_rules(batch: synth.Batch, p: int) -> Tuple[List[Rule], int]:
-    """Rules of set p as (class, [(f, g, op, a, b, t), ...]) and its default class."""
+    """Rules of set p as (class, [(f, g, op, a, b, t), ...]) and its default class; a membership
+    condition carries its category codes as a seventh element."""
     rules = []
     for r in range(batch.set_rule_off[p], batch.set_rule_off[p + 1]):
         conds = []
         for c in range(batch.rule_cond_off[r], batch.rule_cond_off[r + 1]):
-            conds.append((int(batch.cond_f[c]), int(batch.cond_g[c]), int(batch.cond_op[c]),
-                          float(batch.cond_a[c]), float(batch.cond_b[c]), float(batch.cond_t[c])))
+            cond = (int(batch.cond_f[c]), int(batch.cond_g[c]), int(batch.cond_op[c]),
+                    float(batch.cond_a[c]), float(batch.cond_b[c]), float(batch.cond_t[c]))
+            if cond[2] == synth.IN:
+                cond += (synth.category_codes(int(batch.cond_set[c])),)
+            conds.append(cond)
         rules.append((int(batch.rule_class[r]), conds))
     return rules, int(batch.set_default[p])
 
@@ -65,7 +70,11 @@ def render_rules(rules: Sequence[Rule], features: Sequence[str], classes: Sequen
     out = []
     for i, (cls, conds) in enumerate(rules):
         parts = []
-        for f, g, op, a, b, t in conds:
+        for cond in conds:
+            f, g, op, a, b, t = cond[:6]
+            if op == synth.IN:
+                parts.append(f"({features[f]} in {{" + ", ".join(str(k) for k in cond[6]) + "})")
+                continue
             sym = ">" if op == synth.GT else "<"
             rhs = _num(t, digits) if g < 0 else _term(b, features[g], digits)
             parts.append(f"({_term(a, features[f], digits)} {sym} {rhs})")
@@ -79,7 +88,7 @@ def render(batch: synth.Batch, p: int, features: Optional[Sequence[str]] = None,
            classes: Optional[Sequence[str]] = None, digits: Optional[int] = None) -> List[str]:
     """Readable lines of set p of a batch, default class included."""
     rules, default = set_rules(batch, p)
-    nf = 1 + max([max(f, g) for _, cs in rules for f, g, *_ in cs], default=0)
+    nf = 1 + max([max(cd[0], cd[1]) for _, cs in rules for cd in cs], default=0)
     nk = 1 + max([cls for cls, _ in rules] + [default])
     features = features or [f"x{j}" for j in range(nf)]
     classes = classes or [f"class{k}" for k in range(nk)]
@@ -111,8 +120,13 @@ def parse_rules(lines: Sequence[str], features: Sequence[str],
             continue
         body = body.split(". ", 1)[1]
         conds: List[Cond] = []
-        for part in body.split(" & "):
+        for part in _split_conditions(body):
             part = part.strip()[1:-1]
+            if " in {" in part:
+                name, codes = part.split(" in {", 1)
+                ks = [int(v) for v in codes.rstrip("}").split(",") if v.strip()]
+                conds.append((list(features).index(name.strip()), -1, synth.IN, 0.0, 0.0, 0.0, ks))
+                continue
             op = synth.GT if " > " in part else synth.LT
             lhs, rhs = part.split(" > " if op == synth.GT else " < ")
             a, f = _parse_term(lhs, features)
@@ -124,6 +138,19 @@ def parse_rules(lines: Sequence[str], features: Sequence[str],
                 conds.append((f, g, op, a, b, 0.0))
         rules.append((k, conds))
     return rules, default
+
+
+def _split_conditions(body: str) -> List[str]:
+    """The parenthesised conditions of a rule body, split at the top-level ' & '."""
+    out, depth, start = [], 0, 0
+    for i, ch in enumerate(body):
+        depth += ch == "("
+        depth -= ch == ")"
+        if depth == 0 and body.startswith(" & ", i):
+            out.append(body[start:i])
+            start = i + 3
+    out.append(body[start:])
+    return out
 
 
 def parse(texts: Sequence[Sequence[str]], features: Sequence[str], classes: Sequence[str],
@@ -145,7 +172,10 @@ def tensor_rows(rules: Sequence[Rule], F: int) -> List[Tuple[int, np.ndarray, fl
     where x_g is NaN); a pair on one feature and a zero threshold coefficient have no row."""
     rows = []
     for cls, conds in rules:
-        for f, g, op, a, b, t in conds:
+        for cond in conds:
+            f, g, op, a, b, t = cond[:6]
+            if op == synth.IN:
+                raise ValueError("a membership test has no row form")
             if g == f or (g < 0 and a == 0.0):
                 raise ValueError("a pair on one feature or a zero threshold coefficient has no row form")
             w = np.zeros(F, np.float32)
