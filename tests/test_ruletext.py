@@ -107,3 +107,27 @@ def test_tensor_rows_keep_the_evaluation(orc):
     w1, w2 = orc.eval_hard(X, y, 2, b1, want_preds=True), orc.eval_hard(X, y, 2, b2, want_preds=True)
     for u, v in zip(w1, w2):
         assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_membership_conditions_round_trip(seed, orc):
+    """'(name in {codes})' reads back to the same category set; the predictions are unchanged;
+    a membership test has no Fig. 1a row."""
+    X, y = synth.categorical_mixture(800, 9, 3, seed, n_cat=3, n_codes=40)
+    b = synth.random_rulesets(synth.quantile_table(X), 3, 7, (1, 5), (1, 4), seed, cat_from=6, n_codes=40)
+    assert (b.cond_op == synth.IN).any()
+    feats = [f"f{j}" for j in range(9)]
+    classes = ["a", "b", "c"]
+    texts = [ruletext.render(b, p, feats, classes) for p in range(b.P)]
+    assert any(" in {" in ln for t in texts for ln in t)
+    back = ruletext.parse(texts, feats, classes)
+    m = b.cond_op == synth.IN
+    assert np.array_equal(back.cond_op, b.cond_op)
+    assert np.array_equal(back.cond_set[m], b.cond_set[m])
+    for u, v in zip(orc.eval_hard(X, y, 3, b, want_preds=True), orc.eval_hard(X, y, 3, back, want_preds=True)):
+        assert np.array_equal(u, v)
+    p = int(np.flatnonzero(m)[0])
+    rule = int(np.searchsorted(b.rule_cond_off, p, side="right") - 1)
+    s = int(np.searchsorted(b.set_rule_off, rule, side="right") - 1)
+    with pytest.raises(ValueError):
+        ruletext.tensor_rows(ruletext.set_rules(b, s)[0], 9)
