@@ -122,7 +122,17 @@ __device__ __forceinline__ void kadd(float &s, float &c, float v)
 {
     const float y = v - c;
     const float t = s + y;
-    c = isinf(t) ? 0.f : (t - s) - y;   // an infinite sum stays infinite rather than turning NaN
+    c = (t - s) - y;
+    s = t;
+}
+
+// The same for the loss, whose terms may be +inf (a label no path reaches): an infinite sum stays
+// infinite rather than turning NaN.
+__device__ __forceinline__ void kadd_loss(float &s, float &c, float v)
+{
+    const float y = v - c;
+    const float t = s + y;
+    c = isinf(t) ? 0.f : (t - s) - y;
     s = t;
 }
 
@@ -156,8 +166,9 @@ struct XView {
 };
 
 // Forward (and adjoint) of set p over one group of 32 samples, lane = sample n (valid: n < N).
-// lq/lu: the warp's per-rule log-probabilities; acc: its per-condition gradient sums.
-template <bool BWD>
+// lq/lu: the warp's per-rule log-probabilities; acc: its per-condition gradient sums. CAT: the
+// batch may hold membership conditions.
+template <bool BWD, bool CAT>
 __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, int R, int cb, int deflt,
                                            int64_t n, bool valid, const XView &x, float (*lq)[32],
                                            float (*lu)[32], float (*acc)[4], int lane, float &loss_s,
@@ -172,7 +183,7 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         float s = 0.f;
         for (int c = c0; c < c1; ++c) {
             const SoftRec rc = a.recs[c];
-            if (rc.meta & 4u) {          // membership: its exact indicator, a factor 1 or 0 of q_r
+            if (CAT && (rc.meta & 4u)) {   // membership: its exact indicator, a factor 1 or 0 of q_r
                 if (!category_member(x(rc.f), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s = -INFINITY;
                 continue;
             }
@@ -189,7 +200,7 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
     }
     lu[R][lane] = lu_r;
     if (deflt == yn) lpy = log_add(lpy, lu_r);
-    if (valid) kadd(loss_s, loss_c, -lpy);
+    if (valid) kadd_loss(loss_s, loss_c, -lpy);
     if (a.probs && valid) {
         const int64_t orig = a.perm[n];
         for (int k = 0; k < a.K; ++k) {
@@ -215,7 +226,7 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
         for (int c = c0; c < c1; ++c) {
             const SoftRec rc = a.recs[c];
-            if (rc.meta & 4u) continue;   // membership tests have no gradient
+            if (CAT && (rc.meta & 4u)) continue;   // membership tests have no gradient
             const float xf = x(rc.f);
             const bool pair = rc.meta & 1u;
             const float xg = pair ? x(rc.g) : 0.f;
@@ -259,7 +270,7 @@ __device__ __forceinline__ void soft_flush(const SoftKArgs &a, int p, int ch, in
     }
 }
 
-template <bool BWD>
+template <bool BWD, bool CAT>
 __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
 {
     // per warp: lq[maxR][32], lu[maxR+1][32], acc[maxC][4] (ga sum/comp, gbt sum/comp)
@@ -295,7 +306,7 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
             const int64_t n = nb + lane;
             const bool valid = n < a.N;
             const XView x{a.Xt + (valid ? n : 0), a.n_pad};
-            soft_group<BWD>(a, p, rb, re - rb, cb, a.set_default[p], n, valid, x, lq, lu, acc, lane, loss_s,
+            soft_group<BWD, CAT>(a, p, rb, re - rb, cb, a.set_default[p], n, valid, x, lq, lu, acc, lane, loss_s,
                             loss_c);
         }
         soft_flush<BWD>(a, p, ch, cb, ce, loss_s, acc, lane);
@@ -321,7 +332,7 @@ __device__ __forceinline__ void stage_group(float *dst, const float *Xt, int64_t
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-template <bool BWD>
+template <bool BWD, bool CAT>
 __global__ void __launch_bounds__(SOFT_TW * 32) k_soft_tile(SoftKArgs a, int F)
 {
     extern __shared__ __align__(16) float sm[];
@@ -380,7 +391,7 @@ __global__ void __launch_bounds__(SOFT_TW * 32) k_soft_tile(SoftKArgs a, int F)
                 const int64_t n = nb + lane;
                 const bool valid = n < a.N;
                 const XView x{xbuf + (gi & 1) * F * 32 + lane, 32};
-                soft_group<BWD>(a, p, rb, R, cb, deflt, n, valid, x, lq, lu, acc, lane, loss_s, loss_c);
+                soft_group<BWD, CAT>(a, p, rb, R, cb, deflt, n, valid, x, lq, lu, acc, lane, loss_s, loss_c);
             }
             __syncthreads();              // the buffer is restaged two groups later
         }
@@ -433,6 +444,43 @@ __global__ void k_soft_reduce_grad(const float *part_ga, const float *part_gbt, 
 }  // namespace
 
 // Shared body of both entry points. `known` = bounds given by the caller (no host readback).
+template <bool CAT>
+static void set_soft_attributes(Ctx *ctx)
+{
+    cudaFuncSetAttribute(k_soft<true, CAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
+    cudaFuncSetAttribute(k_soft<false, CAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
+    // the staged-tile kernel has a little static shared memory of its own
+    cudaFuncSetAttribute(k_soft_tile<true, CAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ctx->smem_optin - SOFT_TILE_STATIC);
+    cudaFuncSetAttribute(k_soft_tile<false, CAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ctx->smem_optin - SOFT_TILE_STATIC);
+    cudaGetLastError();
+}
+
+// One persistent wave of the soft kernel: the staged-tile form or the per-warp form, forward only
+// or forward + adjoint, with or without membership conditions (CAT).
+template <bool CAT>
+static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bwd, int F, size_t smem,
+                               size_t smem_tile, cudaStream_t stream)
+{
+    int per_sm = 1;
+    if (tiled) {
+        if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<true, CAT>, SOFT_TW * 32, smem_tile);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<false, CAT>, SOFT_TW * 32, smem_tile);
+    } else {
+        if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true, CAT>, SOFT_W * 32, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false, CAT>, SOFT_W * 32, smem);
+    }
+    const int grid = ctx->sm_count * std::max(1, per_sm);
+    if (tiled) {
+        if (bwd) k_soft_tile<true, CAT><<<grid, SOFT_TW * 32, smem_tile, stream>>>(k, F);
+        else k_soft_tile<false, CAT><<<grid, SOFT_TW * 32, smem_tile, stream>>>(k, F);
+    } else {
+        if (bwd) k_soft<true, CAT><<<grid, SOFT_W * 32, smem, stream>>>(k);
+        else k_soft<false, CAT><<<grid, SOFT_W * 32, smem, stream>>>(k);
+    }
+}
+
 static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known_maxC, cudaStream_t stream)
 {
     const BatchDev &b = s.b;
@@ -517,33 +565,13 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     if (rc == RS_OK) {
         static std::once_flag once;
         std::call_once(once, [&] {
-            cudaFuncSetAttribute(k_soft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
-            cudaFuncSetAttribute(k_soft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
-            // the staged-tile kernel has a little static shared memory of its own
-            cudaFuncSetAttribute(k_soft_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ctx->smem_optin - SOFT_TILE_STATIC);
-            cudaFuncSetAttribute(k_soft_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ctx->smem_optin - SOFT_TILE_STATIC);
-            cudaGetLastError();
+            set_soft_attributes<false>(ctx);
+            set_soft_attributes<true>(ctx);
         });
-        int per_sm = 1;
-        if (tiled) {
-            if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<true>, SOFT_TW * 32, smem_tile);
-            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<false>, SOFT_TW * 32, smem_tile);
-        } else {
-            if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true>, SOFT_W * 32, smem);
-            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false>, SOFT_W * 32, smem);
-        }
-        const int grid = ctx->sm_count * std::max(1, per_sm);
         {
             TimedLaunch tl(ctx, TK_SOFT, stream);
-            if (tiled) {
-                if (bwd) k_soft_tile<true><<<grid, SOFT_TW * 32, smem_tile, stream>>>(k, s.F);
-                else k_soft_tile<false><<<grid, SOFT_TW * 32, smem_tile, stream>>>(k, s.F);
-            } else {
-                if (bwd) k_soft<true><<<grid, SOFT_W * 32, smem, stream>>>(k);
-                else k_soft<false><<<grid, SOFT_W * 32, smem, stream>>>(k);
-            }
+            if (b.cond_set) launch_soft_kernel<true>(ctx, k, tiled, bwd, s.F, smem, smem_tile, stream);
+            else launch_soft_kernel<false>(ctx, k, tiled, bwd, s.F, smem, smem_tile, stream);
         }
         k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
                                                                1.0f / (float)s.N, s.loss, s.status);
