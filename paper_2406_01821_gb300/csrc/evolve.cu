@@ -659,8 +659,9 @@ rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, fl
     Dataset &ds = *dsp;
     EvolveBuffers B;
     const size_t C = std::max(b->C, 1), P = b->P;
-    float *ga, *gb, *gt, *mo, *ve, *loss, *dl;
-    uint32_t *status;
+    float *ga = nullptr, *gb = nullptr, *gt = nullptr, *mo = nullptr, *ve = nullptr, *loss = nullptr,
+          *dl = nullptr;
+    uint32_t *status = nullptr;
     if ((rc = B.get(&ga, C)) || (rc = B.get(&gb, C)) || (rc = B.get(&gt, C)) || (rc = B.get(&mo, 2 * C)) ||
         (rc = B.get(&ve, 2 * C)) || (rc = B.get(&loss, P)) || (rc = B.get(&dl, P)) ||
         (rc = B.get(&status, 64)))
