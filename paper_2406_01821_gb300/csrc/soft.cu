@@ -181,6 +181,7 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         const int r = rb + j;
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
         float s = 0.f;
+#pragma unroll 4
         for (int c = c0; c < c1; ++c) {
             const SoftRec rc = a.recs[c];
             if (CAT && (rc.meta & 4u)) {   // membership: its exact indicator, a factor 1 or 0 of q_r
@@ -224,6 +225,7 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         lS = log_add(same ? lqj : -INFINITY, l1q + lS);
         lT = log_add(same ? -INFINITY : lqj, l1q + lT);
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
+#pragma unroll 4
         for (int c = c0; c < c1; ++c) {
             const SoftRec rc = a.recs[c];
             if (CAT && (rc.meta & 4u)) continue;   // membership tests have no gradient
