@@ -68,6 +68,35 @@ __global__ void k_pack_soft(BatchDev b, int F, int K, SoftRec *recs, uint32_t *s
 }
 
 // Validation of the set/rule structure (one thread per set).
+// Single-CTA counting sort of the sets by size (rules + conditions, most first), so that the
+// warps of one CTA group walk sets of similar length. Malformed offsets count as size 0 (the
+// check kernel rejects the batch).
+constexpr int SOFT_ORDER_BUCKETS = 1024;
+__global__ void k_soft_order(BatchDev b, int32_t *order)
+{
+    __shared__ int hist[SOFT_ORDER_BUCKETS];
+    const int R = b.dR ? *b.dR : b.R, C = b.dC ? *b.dC : b.C;
+    for (int i = threadIdx.x; i < SOFT_ORDER_BUCKETS; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    auto bucket = [&](int p) {
+        const int rb = b.set_rule_off[p], re = b.set_rule_off[p + 1];
+        int cost = 0;
+        if (rb >= 0 && re >= rb && re <= R) {
+            const int cb = b.rule_cond_off[rb], ce = b.rule_cond_off[re];
+            if (cb >= 0 && ce >= cb && ce <= C) cost = (re - rb) + (ce - cb);
+        }
+        return SOFT_ORDER_BUCKETS - 1 - min(cost, SOFT_ORDER_BUCKETS - 1);
+    };
+    for (int p = threadIdx.x; p < b.P; p += blockDim.x) atomicAdd(&hist[bucket(p)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < SOFT_ORDER_BUCKETS; ++i) { const int h = hist[i]; hist[i] = run; run += h; }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < b.P; p += blockDim.x) order[atomicAdd(&hist[bucket(p)], 1)] = p;
+}
+
 __global__ void k_check_sets_soft(BatchDev b, int K, uint32_t *status, int32_t *maxima, int maxR,
                                   int maxC)
 {
@@ -155,6 +184,7 @@ struct SoftKArgs {
     int32_t maxR, maxC;              // shared-memory capacity per warp (rules, conditions)
     int64_t Ccap;                    // row stride of the gradient partials
     const uint32_t *status;          // no work if non-zero (malformed batch)
+    const int32_t *order;            // sets by decreasing size (schedule only; results do not depend on it)
 };
 
 // Feature access for one 32-sample group: the lane's sample column either in global memory
@@ -291,7 +321,7 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
         if (lane == 0) task = atomicAdd(a.next, 1);
         task = __shfl_sync(FULL, task, 0);
         if (task >= tasks) break;
-        const int p = (int)(task / a.nchunks);
+        const int p = a.order[task / a.nchunks];
         const int ch = (int)(task % a.nchunks);
         const int rb = a.set_rule_off[p], re = a.set_rule_off[p + 1];
         const int cb = a.rule_cond_off[rb], ce = a.rule_cond_off[re];
@@ -358,8 +388,9 @@ __global__ void __launch_bounds__(SOFT_TW * 32) k_soft_tile(SoftKArgs a, int F)
         if (task >= tasks) break;
         const int g = (int)(task / a.nchunks);
         const int ch = (int)(task % a.nchunks);
-        const int p = g * SOFT_TW + w;
-        const bool active = p < a.P;
+        // the CTA's warps move through the chunk in step: sets of one group have similar sizes
+        const bool active = g * SOFT_TW + w < a.P;
+        const int p = active ? a.order[g * SOFT_TW + w] : 0;
         int rb = 0, R = 0, cb = 0, ce = 0, deflt = 0;
         if (active) {
             rb = a.set_rule_off[p];
@@ -498,8 +529,10 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     SoftRec *recs = nullptr;
     float *part_loss = nullptr, *part_ga = nullptr, *part_gbt = nullptr;
     int32_t *next = nullptr;   // [0] work counter, [1..2] max rules / conditions per set
+    int32_t *order = nullptr;
     const bool bwd = s.dloss != nullptr;
     RS_CUDA(cudaMallocAsync(&recs, sizeof(SoftRec) * Ccap, stream));
+    RS_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * (size_t)P, stream));
     RS_CUDA(cudaMallocAsync(&part_loss, sizeof(float) * (size_t)nchunks * P, stream));
     RS_CUDA(cudaMallocAsync(&next, sizeof(int32_t) * 4, stream));
     if (bwd) {
@@ -512,7 +545,8 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
                                                            known ? known_maxR : SOFT_MAX_RULES,
                                                            known ? known_maxC : SOFT_MAX_CONDS);
     k_pack_soft<<<(unsigned)((Ccap + 255) / 256), 256, 0, stream>>>(b, s.F, s.K, recs, s.status);
-    count_launch(ctx, 2);
+    k_soft_order<<<1, 1024, 0, stream>>>(b, order);
+    count_launch(ctx, 3);
     SoftKArgs k{};
     k.recs = recs;
     k.set_rule_off = b.set_rule_off;
@@ -532,6 +566,7 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     k.part_loss = part_loss;
     k.part_ga = part_ga;
     k.part_gbt = part_gbt;
+    k.order = order;
     k.probs = s.probs;
     k.backward = bwd;
     k.next = next;
@@ -587,6 +622,7 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
         if (e != cudaSuccess) rc = cuda_fail(e, "soft kernels");
     }
     cudaFreeAsync(recs, stream);
+    cudaFreeAsync(order, stream);
     cudaFreeAsync(part_loss, stream);
     cudaFreeAsync(next, stream);
     if (bwd) { cudaFreeAsync(part_ga, stream); cudaFreeAsync(part_gbt, stream); }
