@@ -211,6 +211,7 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc_in, const Bat
     a.status = s.status;
     a.last_end = po.last_end;
     a.Xt = ds->Xt;
+    a.cat = bd.cond_set != nullptr;
     return launch_hard(ctx, ds, tc, a, stream);
 }
 

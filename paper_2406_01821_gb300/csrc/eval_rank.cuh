@@ -125,7 +125,8 @@ __device__ __forceinline__ void group4(const uint32_t (&e)[4], const uint32_t *s
 
 // Walk the rules of one set (records [rb, rb + nrec)) over the lane's four samples; returns the
 // hit bits (bit 7 of byte v: sample v predicted correctly, default included). UNI: the tile holds
-// one label (kmine) and end records carry the class mask.
+// one label (kmine) and end records carry the class mask. CAT: the records may hold membership
+// tests (without it, a membership record is never packed: the packer rejects op 2 without sets).
 //
 // The set is walked in chunks of up to 32 records. Staging turns every record of a chunk into the
 // same form {byte offset from the lane's rank word, per-byte constant}: a cut points at its rank
@@ -134,7 +135,7 @@ __device__ __forceinline__ void group4(const uint32_t (&e)[4], const uint32_t *s
 // chunk's pairs that the lanes build in parallel; padding records are no-ops. The chunk is then one
 // straight run of identical steps, with the first-fire claim applied after each rule's last record
 // (a warp vote gives their positions); the all-claimed exit is tested once per chunk.
-template <bool UNI, int VS>
+template <bool UNI, int VS, bool CAT>
 __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t vrow_off, int lane,
                                              const uint4 *recs, int rb, int nrec, const float *us,
                                              uint32_t rev_off, int F, int kmine, const unsigned char *rl,
@@ -154,7 +155,7 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
         const uint32_t tag = raw.x >> R5_TAG_SHIFT;
         int cnt = min(32, nrec - c0);
         uint32_t pm = __ballot_sync(FULL, lane < cnt && (tag == R5_PAIR || tag == R5_GEN));
-        uint32_t sm = __ballot_sync(FULL, lane < cnt && tag == R5_SET);       // membership tests
+        uint32_t sm = CAT ? __ballot_sync(FULL, lane < cnt && tag == R5_SET) : 0u;   // membership tests
         if (__popc(pm | sm) > VS) {         // end the chunk before the pass row that finds no slot
             uint32_t m = pm | sm;
             for (int k = 0; k < VS; ++k) m &= m - 1u;
@@ -178,7 +179,7 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
             const uint32_t g = min(raw.y, (uint32_t)(F - 1));
             st[slot] = make_uint4(f * (T * 4u), tag == R5_PAIR ? g * (T * 4u) : ones_off, raw.z, raw.w);
             sr = make_uint2(vrow_off + 128u * slot, FULL);
-        } else if ((sm >> lane) & 1u) {
+        } else if (CAT && ((sm >> lane) & 1u)) {
             const uint32_t slot = np + __popc(sm & ((1u << lane) - 1u));
             const uint32_t f = min(raw.x & R5_F_MASK, (uint32_t)(F - 1));
             st[slot] = make_uint4(f * (T * 4u), 0u, raw.z, raw.w);
@@ -195,7 +196,8 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
                 vr[0] = v0;
                 vr += 64;
             }
-            for (int j = np; j < np + __popc(sm); ++j) vrow[j * 32 + lane] = set_row(st[j], xl);
+            if (CAT)
+                for (int j = np; j < np + __popc(sm); ++j) vrow[j * 32 + lane] = set_row(st[j], xl);
         }
         __syncwarp();
         s8[lane] = sr;

@@ -11,7 +11,7 @@ namespace {
 using namespace rank;
 constexpr uint64_t TMA_WAIT_LIMIT_NS = 2000000000ull;
 
-template <int W>
+template <int W, bool CAT>
 __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUtensorMap tmx,
                                                   const __grid_constant__ CUtensorMap tmr, HardArgs a,
                                                   const float *__restrict__ Us)
@@ -94,10 +94,10 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
         uint32_t *vr = vrows + warp * VS * 32;
         const uint32_t vr_off = (uint32_t)(reinterpret_cast<unsigned char *>(vr) - rs);
         const uint32_t hit =
-            uniform ? walk_set<true, VS>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, kmin, rl, xl,
-                                         ones_off, yl, claimed0, si.deflt)
-                    : walk_set<false, VS>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, -2, rl, xl,
-                                          ones_off, yl, claimed0, si.deflt);
+            uniform ? walk_set<true, VS, CAT>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, kmin, rl, xl,
+                                              ones_off, yl, claimed0, si.deflt)
+                    : walk_set<false, VS, CAT>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, -2, rl, xl,
+                                               ones_off, yl, claimed0, si.deflt);
         const int hits = __reduce_add_sync(FULL, __popc(hit));
         if (lane == 0 && hits) atomicAdd(&a.correct[p], hits);
         if (a.per_class) {
@@ -123,7 +123,7 @@ size_t hard5_smem_bytes(int F, int W)
     return Frows * T * (4 + 2 + 4) + (size_t)W * 32 * 16 + (size_t)W * vs * 32 * 4 + T * 4 + 16;
 }
 
-template <int W>
+template <int W, bool CAT>
 static rs_status launch5_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t stream)
 {
     const size_t smem = hard5_smem_bytes(a.F, W);
@@ -131,7 +131,7 @@ static rs_status launch5_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(k_hard5<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(k_hard5<W, CAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)ctx->smem_optin);
     });
     if (attr_err != cudaSuccess) return cuda_fail(attr_err, "cudaFuncSetAttribute(k_hard5)");
@@ -142,7 +142,7 @@ static rs_status launch5_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_
     dim3 grid(tiles, a.groups);
     {
         TimedLaunch tl(ctx, TK_HARD, stream);
-        k_hard5<W><<<grid, W * 32, smem, stream>>>(*tmx, *tmr, a, ds->Us);
+        k_hard5<W, CAT><<<grid, W * 32, smem, stream>>>(*tmx, *tmr, a, ds->Us);
     }
     RS_CUDA(cudaGetLastError());
     count_launch(ctx);
@@ -155,8 +155,8 @@ rs_status launch_hard5(Ctx *ctx, Dataset *ds, int W, const HardArgs &a, cudaStre
     if (a.P > 0 && a.per_class)
         RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
-    if (W == 16) return launch5_t<16>(ctx, ds, a, stream);
-    if (W == 32) return launch5_t<32>(ctx, ds, a, stream);
+    if (W == 16) return a.cat ? launch5_t<16, true>(ctx, ds, a, stream) : launch5_t<16, false>(ctx, ds, a, stream);
+    if (W == 32) return a.cat ? launch5_t<32, true>(ctx, ds, a, stream) : launch5_t<32, false>(ctx, ds, a, stream);
     return RS_ERR_INVALID;
 }
 

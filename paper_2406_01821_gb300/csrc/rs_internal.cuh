@@ -259,6 +259,7 @@ struct HardArgs {
     uint32_t *status;
     const int32_t *last_end; // [P*K] or null (see PackOut)
     const float *Xt;         // [F][n_pad] (read directly by the global-memory configuration)
+    bool cat;                // the records may hold membership tests
 };
 // Zero outputs and run the evaluator with tile configuration `tc`.
 rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,

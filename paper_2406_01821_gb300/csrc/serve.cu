@@ -68,6 +68,7 @@ struct __align__(16) ReqDesc {
     const float *Us;
     const int32_t *last_end;            // [P*K] per-class last rule ends, or null
     int32_t ranked, gsets;              // gsets: sets per unit
+    int32_t cat;                        // the records may hold membership tests
 };
 
 struct ServeArgs {
@@ -135,11 +136,17 @@ __device__ __forceinline__ void serve_unit_ranked(const ReqDesc &d, int tile, in
         const int nrec = (uniform && d.last_end && deflt != kmin)
                              ? min(__ldcg(d.last_end + (int64_t)p * d.K + kmin), t.y - t.x)
                              : t.y - t.x;
-        const uint32_t hit =
-            uniform ? walk_set<true, SVS>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, kmin, rl, xl,
-                                          ones_off, yl, claimed0, deflt)
-                    : walk_set<false, SVS>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, -2, rl, xl,
-                                           ones_off, yl, claimed0, deflt);
+        uint32_t hit;
+        if (d.cat)
+            hit = uniform ? walk_set<true, SVS, true>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, kmin,
+                                                      rl, xl, ones_off, yl, claimed0, deflt)
+                          : walk_set<false, SVS, true>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, -2,
+                                                       rl, xl, ones_off, yl, claimed0, deflt);
+        else
+            hit = uniform ? walk_set<true, SVS, false>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, kmin,
+                                                       rl, xl, ones_off, yl, claimed0, deflt)
+                          : walk_set<false, SVS, false>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, -2,
+                                                        rl, xl, ones_off, yl, claimed0, deflt);
         const int hits = __reduce_add_sync(FULL, __popc(hit));
         if (lane == 0 && hits) atomicAdd(&d.correct[p], hits);
         if (d.per_class) {
@@ -780,6 +787,7 @@ static bool try_admit(Server *s, Request &r)
     d.ranked = ranked ? 1 : 0;
     d.gsets = ranked ? GROUP_SETS_RANKED : GROUP_SETS;
     d.last_end = po.last_end;
+    d.cat = r.cat ? 1 : 0;
     // a copy from pageable memory is staged before the call returns, so `d` may go out of scope
     cudaMemcpyAsync(&s->d_table[r.slot], &d, sizeof(d), cudaMemcpyHostToDevice, s->sstream);
     cudaMemsetAsync(&s->d_done[r.slot], 0, 4, s->sstream);
