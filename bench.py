@@ -563,7 +563,7 @@ def run_reference(args, d: Dist):
         return
     from paper_2406_01821_gb300 import synth
     w = synth.ragged_hard(seed=0)
-    n_sample = args.cpu_sample
+    n_sample = min(args.cpu_sample, 131072)      # about 2.5 s of oracle work per step on 16 cores
     for _ in range(args.warmup):
         cpu_baseline(w, min(n_sample, 4096))
     vals = []
@@ -590,7 +590,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=131072)
+    ap.add_argument("--cpu-sample", type=int, default=524288)
     ap.add_argument("--workload", default="ragged", choices=["ragged", "ragged-small", "soft-small"],
                     help="ragged-small (N=2^19, P=512) and soft-small (soft leg only, N=65536, "
                          "P=256) are the cases used for ncu captures")
