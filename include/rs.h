@@ -373,6 +373,23 @@ rs_status rs_profile_read(rs_ctx *ctx, rs_profile *out, int32_t reset);
 rs_status rs_selftest_threshold_rewrite(rs_ctx *ctx, const float *a, const float *t,
                                         const int8_t *op, int32_t n, uint64_t *mismatches);
 
+/*
+ * Fault injection on the host: of the per-call device allocations of the evaluation paths
+ * (rs_eval_hard, rs_eval_soft_fwd/bwd, serving admission), the next `skip` succeed and the `count`
+ * after them fail as if the device were out of memory (process-wide; count 0 disarms). A call
+ * whose allocation fails returns RS_ERR_OOM having released whatever it had taken; serving keeps
+ * the request queued and admits it once allocations succeed again.
+ */
+rs_status rs_inject_alloc_failures(int32_t skip, int32_t count);
+
+/*
+ * Bounded device wait: runs the bounded mbarrier wait that guards every asynchronous copy of the
+ * evaluators on a barrier that nothing completes, with a limit of limit_ns (clamped to 1 ms ..
+ * 2 s). The wait gives up, the kernel records a timeout in its status word and returns, and the
+ * call returns RS_ERR_TIMEOUT; the context stays usable.
+ */
+rs_status rs_selftest_bounded_wait(rs_ctx *ctx, int64_t limit_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

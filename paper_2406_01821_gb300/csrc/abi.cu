@@ -32,6 +32,8 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
                      int32_t *best_out, double *mean_out, cudaStream_t s);
 rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, float *pb, float *pt,
                        float tau, float lr, int steps, float *loss_trace, cudaStream_t s);
+void set_injected_alloc_failures(int32_t skip, int32_t count);
+rs_status selftest_bounded_wait(Ctx *ctx, int64_t limit_ns, cudaStream_t stream);
 rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
                            int32_t *per_class, int32_t *preds, cudaStream_t stream);
 }  // namespace rs
@@ -331,6 +333,25 @@ rs_status rs_selftest_threshold_rewrite(rs_ctx *ctx, const float *a, const float
         rs_status rc = device_guard(ctx);
         if (rc) return rc;
         return selftest_rewrite(a, t, op, n, mismatches, ctx->sm_count);
+    })
+}
+
+rs_status rs_inject_alloc_failures(int32_t skip, int32_t count)
+{
+    RS_GUARD({
+        if (skip < 0 || count < 0) return RS_ERR_INVALID;
+        set_injected_alloc_failures(skip, count);
+        return RS_OK;
+    })
+}
+
+rs_status rs_selftest_bounded_wait(rs_ctx *ctx, int64_t limit_ns, void *stream)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return selftest_bounded_wait(ctx, limit_ns, S(stream));
     })
 }
 

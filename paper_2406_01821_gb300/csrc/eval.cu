@@ -59,7 +59,7 @@ static rs_status stage_batch(const rs_batch *b, cudaStream_t stream, StagedBatch
                            b->cond_f, b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t, b->cond_set};
     size_t total = 0;
     for (int i = 0; i < 11; ++i) { off[i] = total; total = align_up(total + sz[i], 256); }
-    RS_CUDA(cudaMallocAsync(&out.buf, std::max<size_t>(total, 256), stream));
+    RS_CUDA(dev_alloc_async(&out.buf, std::max<size_t>(total, 256), stream));
     char *base = static_cast<char *>(out.buf);
     for (int i = 0; i < 11; ++i)
         if (sz[i]) RS_CUDA(cudaMemcpyAsync(base + off[i], src[i], sz[i], cudaMemcpyHostToDevice, stream));
@@ -168,7 +168,7 @@ static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t 
         if (preds) out_b += align_up(sizeof(int32_t) * (size_t)b.P * N, 256);
     }
     char *base = nullptr;
-    RS_CUDA(cudaMallocAsync(&base, rec_b + set_b + ord_b + st_b + le_b + out_b, stream));
+    RS_CUDA(dev_alloc_async(&base, rec_b + set_b + ord_b + st_b + le_b + out_b, stream));
     s.recs = (Rec *)base;
     s.sets = (SetInfo *)(base + rec_b);
     s.order = (int32_t *)(base + rec_b + set_b);
@@ -438,7 +438,11 @@ rs_status eval_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, float
             if (probs) need += align_up(4 * P * ds->N * ds->K, 256);
             if (bwd) need += align_up(4 * std::max<size_t>(C, 1), 256) * 3;
         }
-        RS_CUDA(cudaMallocAsync(&obuf, need, stream));
+        const cudaError_t ae = dev_alloc_async(&obuf, need, stream);
+        if (ae != cudaSuccess) {
+            if (sb.buf) cudaFreeAsync(sb.buf, stream);
+            return cuda_fail(ae, "soft outputs");
+        }
         d_status = (uint32_t *)obuf;
         char *p = obuf + 256;
         if (host) {
@@ -457,7 +461,12 @@ rs_status eval_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, float
     }
     float *tmp_loss = nullptr;
     if (!d_loss) {   // the backward call may omit the loss output
-        RS_CUDA(cudaMallocAsync(&tmp_loss, 4 * std::max<size_t>(P, 1), stream));
+        const cudaError_t ae = dev_alloc_async(&tmp_loss, 4 * std::max<size_t>(P, 1), stream);
+        if (ae != cudaSuccess) {
+            cudaFreeAsync(obuf, stream);
+            if (sb.buf) cudaFreeAsync(sb.buf, stream);
+            return cuda_fail(ae, "soft loss scratch");
+        }
         d_loss = tmp_loss;
     }
     SoftArgs a{};

@@ -27,6 +27,21 @@ rs_status cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return ::rs::cuda_fail(e_, #call);             \
     } while (0)
 
+// Host-side fault injection (tests): rs_inject_alloc_failures(skip, count) lets the next `skip`
+// per-call device allocations of the evaluation paths succeed and makes the `count` after them
+// fail as if the device were out of memory.
+bool take_injected_alloc_failure();
+inline cudaError_t dev_alloc_async(void **p, size_t bytes, cudaStream_t stream)
+{
+    if (take_injected_alloc_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMallocAsync(p, bytes, stream);
+}
+template <typename T>
+inline cudaError_t dev_alloc_async(T **p, size_t bytes, cudaStream_t stream)
+{
+    return dev_alloc_async(reinterpret_cast<void **>(p), bytes, stream);
+}
+
 // Device status word bits (set with atomicOr by kernels that find a problem).
 enum : uint32_t {
     ST_BAD_OFFSETS = 1u << 0,

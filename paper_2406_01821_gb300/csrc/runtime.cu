@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include "rs_internal.cuh"
+#include "tma.cuh"
 
 namespace rs {
 
@@ -22,6 +23,64 @@ void set_error(const char *fmt, ...)
 }
 
 const char *last_error() { return g_last_error.c_str(); }
+
+static std::mutex g_inject_mu;
+static int32_t g_inject_skip = 0, g_inject_fail = 0;
+static std::atomic<bool> g_inject_armed{false};
+
+void set_injected_alloc_failures(int32_t skip, int32_t count)
+{
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_inject_skip = skip;
+    g_inject_fail = count;
+    g_inject_armed.store(count > 0);
+}
+
+bool take_injected_alloc_failure()
+{
+    if (!g_inject_armed.load(std::memory_order_relaxed)) return false;
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    if (g_inject_skip > 0) { --g_inject_skip; return false; }
+    if (g_inject_fail > 0) {
+        if (--g_inject_fail == 0) g_inject_armed.store(false);
+        return true;
+    }
+    return false;
+}
+
+// A bounded wait on an mbarrier that nothing completes: the wait must give up within limit_ns.
+__global__ void k_bounded_wait_selftest(uint64_t limit_ns, uint32_t *status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool landed = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (!__syncthreads_and(landed) && threadIdx.x == 0) atomicOr(status, ST_WAIT_TIMEOUT);
+}
+
+rs_status selftest_bounded_wait(Ctx *ctx, int64_t limit_ns, cudaStream_t stream)
+{
+    const uint64_t lim = (uint64_t)std::min<int64_t>(std::max<int64_t>(limit_ns, 1000000), 2000000000);
+    uint32_t *d = nullptr;
+    RS_CUDA(cudaMallocAsync(&d, sizeof(uint32_t), stream));
+    RS_CUDA(cudaMemsetAsync(d, 0, sizeof(uint32_t), stream));
+    k_bounded_wait_selftest<<<1, 32, 0, stream>>>(lim, d);
+    count_launch(ctx);
+    uint32_t h = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+    cudaFreeAsync(d, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+    if (h & ST_WAIT_TIMEOUT) {
+        set_error("device wait gave up after %.1f ms (self-test)", (double)lim / 1e6);
+        return RS_ERR_TIMEOUT;
+    }
+    return RS_OK;
+}
 
 rs_status cuda_fail(cudaError_t e, const char *what)
 {

@@ -692,7 +692,7 @@ static bool admit_soft(Server *s, Request &r)
 {
     if (s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
-    if (cudaMallocAsync(&base, r.device_bytes, s->sstream) != cudaSuccess) {
+    if (dev_alloc_async(&base, r.device_bytes, s->sstream) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -734,7 +734,7 @@ static bool try_admit(Server *s, Request &r)
     const int64_t groups = serve_groups(*r.ds, r.P, r.cat);
     if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
-    if (cudaMallocAsync(&base, r.device_bytes, s->sstream) != cudaSuccess) {
+    if (dev_alloc_async(&base, r.device_bytes, s->sstream) != cudaSuccess) {
         cudaGetLastError();
         return false;                      // retry later, when memory is back
     }

@@ -531,13 +531,16 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     int32_t *next = nullptr;   // [0] work counter, [1..2] max rules / conditions per set
     int32_t *order = nullptr;
     const bool bwd = s.dloss != nullptr;
-    RS_CUDA(cudaMallocAsync(&recs, sizeof(SoftRec) * Ccap, stream));
-    RS_CUDA(cudaMallocAsync(&order, sizeof(int32_t) * (size_t)P, stream));
-    RS_CUDA(cudaMallocAsync(&part_loss, sizeof(float) * (size_t)nchunks * P, stream));
-    RS_CUDA(cudaMallocAsync(&next, sizeof(int32_t) * 4, stream));
-    if (bwd) {
-        RS_CUDA(cudaMallocAsync(&part_ga, sizeof(float) * (size_t)nchunks * Ccap, stream));
-        RS_CUDA(cudaMallocAsync(&part_gbt, sizeof(float) * (size_t)nchunks * Ccap, stream));
+    cudaError_t ae = dev_alloc_async(&recs, sizeof(SoftRec) * Ccap, stream);
+    if (ae == cudaSuccess) ae = dev_alloc_async(&order, sizeof(int32_t) * (size_t)P, stream);
+    if (ae == cudaSuccess) ae = dev_alloc_async(&part_loss, sizeof(float) * (size_t)nchunks * P, stream);
+    if (ae == cudaSuccess) ae = dev_alloc_async(&next, sizeof(int32_t) * 4, stream);
+    if (ae == cudaSuccess && bwd) ae = dev_alloc_async(&part_ga, sizeof(float) * (size_t)nchunks * Ccap, stream);
+    if (ae == cudaSuccess && bwd) ae = dev_alloc_async(&part_gbt, sizeof(float) * (size_t)nchunks * Ccap, stream);
+    if (ae != cudaSuccess) {         // release what was taken before the failure
+        for (void *q : {(void *)recs, (void *)order, (void *)part_loss, (void *)next, (void *)part_ga, (void *)part_gbt})
+            if (q) cudaFreeAsync(q, stream);
+        return cuda_fail(ae, "soft scratch");
     }
     RS_CUDA(cudaMemsetAsync(next, 0, sizeof(int32_t) * 4, stream));
     const bool known = known_maxR > 0;

@@ -129,6 +129,8 @@ _SIGS = {
     "rs_selftest_threshold_rewrite": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                        ctypes.c_void_p, ctypes.c_void_p,
                                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
+    "rs_inject_alloc_failures": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
+    "rs_selftest_bounded_wait": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
 }
 
 
