@@ -299,6 +299,11 @@ typedef struct {
                                  ranks the individual, its genome is kept (Baldwin effect, Sec. 3);
                                  1: tuned coefficients that improved it are written back */
     uint64_t seed;
+    int32_t first_generation; /* index of the first generation of this call (0 for a new run): a
+                                 run resumed from a saved population with the same seed and
+                                 first_generation = generations done so far continues exactly as
+                                 an uninterrupted run (random counters and the tuning schedule
+                                 use the absolute index) */
 } rs_evolve_config;
 
 /*

@@ -491,7 +491,7 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
     Dataset &ds = *dsp;
     const int P = cfg->P, RMAX = cfg->RMAX, CMAX = cfg->CMAX;
     if (P < 2 || RMAX < 1 || RMAX > 32 || CMAX < 1 || CMAX > 64 || cfg->generations < 0 ||
-        cfg->elite < 0 || cfg->elite > P || cfg->tune_top < 0 || cfg->tune_top > P ||
+        cfg->first_generation < 0 || cfg->elite < 0 || cfg->elite > P || cfg->tune_top < 0 || cfg->tune_top > P ||
         cfg->tune_steps < 0 || !(cfg->tau > 0.f) || !hp) {
         set_error("bad evolution configuration");
         return RS_ERR_INVALID;
@@ -567,7 +567,7 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
         build_csr(in, nullptr, P, w, s);
         if ((rc = evaluate(P, fit))) return rc;
         const bool tune = cfg->tune_every > 0 && T > 0 && cfg->tune_steps > 0 && g < G &&
-                          (g % cfg->tune_every) == cfg->tune_every - 1;
+                          ((cfg->first_generation + g) % cfg->tune_every) == cfg->tune_every - 1;
         if (tune) {
             k_rank<<<(P + 255) / 256, 256, 0, s>>>(fit, P, order);
             build_csr(in, order, T, w, s);                     // the T best, in rank order
@@ -611,7 +611,8 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
         if (g == G) break;
         k_rank<<<(P + 255) / 256, 256, 0, s>>>(fit, P, order);
         k_next_generation<<<(P * 32 + 255) / 256, 256, 0, s>>>(in, fit, order, pop[cur ^ 1], cfg->seed,
-                                                               (uint64_t)g, cfg->elite, dv);
+                                                               (uint64_t)(cfg->first_generation + g), cfg->elite,
+                                                               dv);
         count_launch(ctx, 2);
         RS_CUDA(cudaGetLastError());
         cur ^= 1;

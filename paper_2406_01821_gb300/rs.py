@@ -70,7 +70,8 @@ class rs_evolve_config(ctypes.Structure):
                 ("generations", ctypes.c_int32), ("elite", ctypes.c_int32),
                 ("tune_every", ctypes.c_int32), ("tune_top", ctypes.c_int32),
                 ("tune_steps", ctypes.c_int32), ("tau", ctypes.c_float), ("lr", ctypes.c_float),
-                ("lamarckian", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("lamarckian", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("first_generation", ctypes.c_int32)]
 
 
 _lib = None
@@ -403,7 +404,8 @@ class Context:
         return {f: getattr(st, f) for f, _ in rs_serving_stats._fields_}
 
     def evolve(self, ds: int, pop: dict, generations: int, elite: int, seed: int, tune_every=0,
-               tune_top=0, tune_steps=0, tau=0.1, lr=1e-2, lamarckian=False, stream=None):
+               tune_top=0, tune_steps=0, tau=0.1, lr=1e-2, lamarckian=False, first_generation=0,
+               stream=None):
         """Device-resident evolution. ``pop`` = dict of fixed-slot numpy arrays (nrule [P],
         deflt [P], rcls/ncond [P,RMAX], cf/cg/cop/ca/cb/ct [P,RMAX,CMAX]); returns
         (final population dict, fitness [P], best [G+1], mean [G+1])."""
@@ -417,10 +419,25 @@ class Context:
         mean = np.zeros(generations + 1, np.float64)
         cp = rs_population(*[_ptr(arr[k]) for k in kinds], _ptr(fitness))
         cfg = rs_evolve_config(P, RMAX, CMAX, generations, elite, tune_every, tune_top, tune_steps,
-                               tau, lr, int(lamarckian), seed)
+                               tau, lr, int(lamarckian), seed, int(first_generation))
         check(lib().rs_evolve(self.h, ds, ctypes.byref(cfg), ctypes.byref(cp), _ptr(best), _ptr(mean),
                               _stream_ptr(stream)))
         return arr, fitness, best, mean
+
+    @staticmethod
+    def save_population(path: str, pop: dict, seed: int, next_generation: int):
+        """Checkpoint of an evolution run: the fixed-slot population, the seed and the index of
+        the next generation (a plain numpy .npz file)."""
+        np.savez(path, seed=np.uint64(seed), next_generation=np.int64(next_generation),
+                 **{k: np.asarray(v) for k, v in pop.items()})
+
+    @staticmethod
+    def load_population(path: str):
+        """(population dict, seed, next generation) of a checkpoint; resume with
+        evolve(..., seed=seed, first_generation=next_generation)."""
+        with np.load(path) as z:
+            pop = {k: z[k].copy() for k in z.files if k not in ("seed", "next_generation")}
+            return pop, int(z["seed"]), int(z["next_generation"])
 
     def finetune(self, ds: int, batch: DeviceBatch, tau: float, lr: float, steps: int, stream=None):
         """Adam fine-tuning of a device batch; returns (a, b, t, loss_trace [steps, P])."""

@@ -117,3 +117,31 @@ def test_finetune_matches_float64_adam(ctx, orc):
     assert well.sum() > 0.5 * b.C
     assert np.allclose(a[well], th[0][well], rtol=0, atol=1e-5)
     assert np.allclose(got2[well], th[1][well], rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_checkpoint_resume_continues_exactly(ctx, tmp_path, tune):
+    """A run of 7 generations equals 3 generations, a checkpoint written and read back, and 4 more
+    generations resumed from it (random counters and the tuning schedule use the absolute
+    generation index)."""
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.two_class_gaussian(3000, 8, 9)
+    pop = synth.initial_population(X, y, 2, 80, RMAX=6, CMAX=3, seed=9)
+    kw = dict(elite=2, seed=9)
+    if tune:
+        kw.update(tune_every=2, tune_top=6, tune_steps=3, tau=0.2, lr=1e-2)
+    ds = ctx.dataset(X, y, 2)
+    try:
+        full, ffit, fbest, _ = ctx.evolve(ds, pop, generations=7, **kw)
+        part, _, pbest, _ = ctx.evolve(ds, pop, generations=3, **kw)
+        path = str(tmp_path / "ckpt.npz")
+        rs.Context.save_population(path, part, 9, 3)
+        pop2, seed2, g2 = rs.Context.load_population(path)
+        assert seed2 == 9 and g2 == 3
+        rest, rfit, rbest, _ = ctx.evolve(ds, pop2, generations=4, first_generation=g2, **kw)
+    finally:
+        ctx.dataset_destroy(ds)
+    for k in full:
+        assert np.array_equal(rest[k], full[k]), k
+    assert np.array_equal(rfit, ffit)
+    assert np.array_equal(np.concatenate([pbest[:3], rbest]), fbest)
