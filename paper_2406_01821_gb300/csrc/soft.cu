@@ -363,11 +363,12 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
     }
 }
 
-// The same evaluation with the warps of a CTA on SOFT_TW consecutive sets over the same chunk:
+// The same evaluation with the warps of a CTA on as many neighbouring sets (in size order) over
+// the same chunk:
 // the features of each 32-sample group are staged once per CTA in shared memory (double-buffered
 // asynchronous copies), so condition loads are shared-memory reads. Per-set results are identical
 // to k_soft (same per-sample arithmetic and summation order).
-constexpr int SOFT_TW = 8;
+constexpr int SOFT_TW_MIN = 4, SOFT_TW_MAX = 16;   // warps (sets) per CTA of the staged-tile kernel
 constexpr int SOFT_TILE_STATIC = 256;   // bytes kept for the kernel's static shared memory
 
 __device__ __forceinline__ void stage_group(float *dst, const float *Xt, int64_t n_pad, int F, int64_t nb)
@@ -383,19 +384,20 @@ __device__ __forceinline__ void stage_group(float *dst, const float *Xt, int64_t
 }
 
 template <bool BWD, bool CAT>
-__global__ void __launch_bounds__(SOFT_TW * 32) k_soft_tile(SoftKArgs a, int F)
+__global__ void __launch_bounds__(SOFT_TW_MAX * 32) k_soft_tile(SoftKArgs a, int F)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ int64_t s_task;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t set_groups = (a.P + SOFT_TW - 1) / SOFT_TW;
+    const int TW = blockDim.x >> 5;                   // sets per CTA group
+    const int64_t set_groups = (a.P + TW - 1) / TW;
     const int64_t tasks = set_groups * a.nchunks;
     const size_t per_warp = (size_t)(2 * a.maxR + 1) * 32 + (size_t)a.maxC * 4;
     float *base_w = sm + per_warp * w;
     float(*lq)[32] = reinterpret_cast<float(*)[32]>(base_w);
     float(*lu)[32] = reinterpret_cast<float(*)[32]>(base_w + (size_t)a.maxR * 32);
     float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * 32);
-    float *xbuf = sm + per_warp * SOFT_TW;            // [2][F][32]
+    float *xbuf = sm + per_warp * TW;                 // [2][F][32]
     if (*a.status) return;
 
     while (true) {
@@ -407,8 +409,8 @@ __global__ void __launch_bounds__(SOFT_TW * 32) k_soft_tile(SoftKArgs a, int F)
         const int g = (int)(task / a.nchunks);
         const int ch = (int)(task % a.nchunks);
         // the CTA's warps move through the chunk in step: sets of one group have similar sizes
-        const bool active = g * SOFT_TW + w < a.P;
-        const int p = active ? a.order[g * SOFT_TW + w] : 0;
+        const bool active = g * TW + w < a.P;
+        const int p = active ? a.order[g * TW + w] : 0;
         int rb = 0, R = 0, cb = 0, ce = 0, deflt = 0;
         if (active) {
             rb = a.set_rule_off[p];
@@ -508,24 +510,48 @@ static void set_soft_attributes(Ctx *ctx)
     cudaGetLastError();
 }
 
+// Resident CTAs per SM of the staged-tile kernel with tw warps and per-warp arrays of
+// per_warp bytes (0 when it does not fit).
+template <bool BWD, bool CAT>
+static int soft_tile_per_sm(Ctx *ctx, int tw, size_t per_warp, int F)
+{
+    const size_t bytes = per_warp * tw + sizeof(float) * 2 * 32 * (size_t)F;
+    if (bytes + SOFT_TILE_STATIC > ctx->smem_optin) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<BWD, CAT>, tw * 32, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
 // One persistent wave of the soft kernel: the staged-tile form or the per-warp form, forward only
-// or forward + adjoint, with or without membership conditions (CAT).
+// or forward + adjoint, with or without membership conditions (CAT). The staged-tile form takes
+// the number of warps per CTA that keeps the most warps resident for this batch's per-warp
+// arrays (ties: fewer warps per CTA, so that a CTA's sets are closer in size).
 template <bool CAT>
 static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bwd, int F, size_t smem,
-                               size_t smem_tile, cudaStream_t stream)
+                               size_t per_warp, cudaStream_t stream)
 {
     int per_sm = 1;
+    int tw = SOFT_TW_MIN;
+    size_t smem_tile = 0;
     if (tiled) {
-        if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<true, CAT>, SOFT_TW * 32, smem_tile);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<false, CAT>, SOFT_TW * 32, smem_tile);
+        int best = 0;
+        for (int t = SOFT_TW_MIN; t <= SOFT_TW_MAX; ++t) {
+            const int c = bwd ? soft_tile_per_sm<true, CAT>(ctx, t, per_warp, F)
+                              : soft_tile_per_sm<false, CAT>(ctx, t, per_warp, F);
+            if (c * t > best) { best = c * t; tw = t; per_sm = c; }
+        }
+        smem_tile = per_warp * tw + sizeof(float) * 2 * 32 * (size_t)F;
     } else {
         if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true, CAT>, SOFT_W * 32, smem);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false, CAT>, SOFT_W * 32, smem);
     }
     const int grid = ctx->sm_count * std::max(1, per_sm);
     if (tiled) {
-        if (bwd) k_soft_tile<true, CAT><<<grid, SOFT_TW * 32, smem_tile, stream>>>(k, F);
-        else k_soft_tile<false, CAT><<<grid, SOFT_TW * 32, smem_tile, stream>>>(k, F);
+        if (bwd) k_soft_tile<true, CAT><<<grid, tw * 32, smem_tile, stream>>>(k, F);
+        else k_soft_tile<false, CAT><<<grid, tw * 32, smem_tile, stream>>>(k, F);
     } else {
         if (bwd) k_soft<true, CAT><<<grid, SOFT_W * 32, smem, stream>>>(k);
         else k_soft<false, CAT><<<grid, SOFT_W * 32, smem, stream>>>(k);
@@ -614,7 +640,7 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     const size_t per_warp = sizeof(float) * ((size_t)(2 * k.maxR + 1) * 32 + (size_t)k.maxC * 4);
     const size_t smem = per_warp * SOFT_W;
     // the staged-tile kernel when its per-CTA footprint (8 warps + two feature tiles) fits
-    const size_t smem_tile = per_warp * SOFT_TW + sizeof(float) * 2 * 32 * (size_t)s.F;
+    const size_t smem_tile = per_warp * SOFT_TW_MIN + sizeof(float) * 2 * 32 * (size_t)s.F;
     const bool tiled = s.F <= 128 && smem_tile + SOFT_TILE_STATIC <= ctx->smem_optin;
     if (rc == RS_OK && smem > ctx->smem_optin) {
         rc = RS_ERR_TOO_LARGE;
@@ -628,8 +654,8 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
         });
         {
             TimedLaunch tl(ctx, TK_SOFT, stream);
-            if (b.cond_set) launch_soft_kernel<true>(ctx, k, tiled, bwd, s.F, smem, smem_tile, stream);
-            else launch_soft_kernel<false>(ctx, k, tiled, bwd, s.F, smem, smem_tile, stream);
+            if (b.cond_set) launch_soft_kernel<true>(ctx, k, tiled, bwd, s.F, smem, per_warp, stream);
+            else launch_soft_kernel<false>(ctx, k, tiled, bwd, s.F, smem, per_warp, stream);
         }
         k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
                                                                1.0f / (float)s.N, s.loss, s.status);
