@@ -213,6 +213,20 @@ struct XView {
     __device__ __forceinline__ float operator()(int f) const { return col[(int64_t)f * stride]; }
 };
 
+// This lane's (d ell / d a, d ell / d b or d t) of condition rc, given d ell / d log q of its rule.
+__device__ __forceinline__ float2 cond_grad(const SoftKArgs &a, const SoftRec &rc, const XView &x, float gq)
+{
+    const float xf = x(rc.f);
+    const bool pair = rc.meta & 1u;
+    const float xg = pair ? x(rc.g) : 0.f;
+    const float lhs = rc.a * xf;
+    const float rhs = pair ? rc.bt * xg : rc.bt;
+    const float sg = (rc.meta & 2u) ? -1.f : 1.f;
+    const float u = sg * (lhs - rhs) * a.inv_tau;
+    const float du = gq * sigmoid_neg(u) * sg * a.inv_tau;
+    return make_float2(du * xf, pair ? -du * xg : -du);
+}
+
 // Forward (and adjoint) of set p over one group of 32 samples, lane = sample n (valid: n < N).
 // lq/lu: the warp's per-rule log-probabilities; acc: its per-condition gradient sums. CAT: the
 // batch may hold membership conditions.
@@ -273,29 +287,28 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         lS = log_add(same ? lqj : -INFINITY, l1q + lS);
         lT = log_add(same ? -INFINITY : lqj, l1q + lT);
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
-#pragma unroll 4
-        for (int c = c0; c < c1; ++c) {
-            const SoftRec rc = a.recs[c];
-            if (CAT && (rc.meta & 4u)) continue;   // membership tests have no gradient
-            const float xf = x(rc.f);
-            const bool pair = rc.meta & 1u;
-            const float xg = pair ? x(rc.g) : 0.f;
-            const float lhs = rc.a * xf;
-            const float rhs = pair ? rc.bt * xg : rc.bt;
-            const float sg = (rc.meta & 2u) ? -1.f : 1.f;
-            const float u = sg * (lhs - rhs) * a.inv_tau;
-            const float du = gq * sigmoid_neg(u) * sg * a.inv_tau;
-            float ga = du * xf;
-            float gbt = pair ? -du * xg : -du;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                ga += __shfl_xor_sync(FULL, ga, o);
-                gbt += __shfl_xor_sync(FULL, gbt, o);
-            }
-            const int ci = c - cb;
-            if (lane == (ci & 31)) {
-                kadd(acc[ci][0], acc[ci][1], ga);
-                kadd(acc[ci][2], acc[ci][3], gbt);
+        // conditions two at a time: the four sums (d/da, d/db-or-dt of both) share one butterfly
+#pragma unroll 2
+        for (int c = c0; c < c1; c += 2) {
+            const bool has1 = c + 1 < c1;
+            const SoftRec r0 = a.recs[c];
+            const SoftRec r1 = a.recs[has1 ? c + 1 : c];
+            const float2 g0 = (CAT && (r0.meta & 4u)) ? make_float2(0.f, 0.f) : cond_grad(a, r0, x, gq);
+            const float2 g1 = (!has1 || (CAT && (r1.meta & 4u))) ? make_float2(0.f, 0.f) : cond_grad(a, r1, x, gq);
+            const bool b4 = lane & 16, b3 = lane & 8;
+            // lanes 0..15 gather the first condition's two sums, lanes 16..31 the second's
+            float k0 = b4 ? g1.x : g0.x, k1 = b4 ? g1.y : g0.y;
+            k0 += __shfl_xor_sync(FULL, b4 ? g0.x : g1.x, 16);
+            k1 += __shfl_xor_sync(FULL, b4 ? g0.y : g1.y, 16);
+            // then lanes with bit 3 clear the d/da sum, set the other
+            float t = (b3 ? k1 : k0) + __shfl_xor_sync(FULL, b3 ? k0 : k1, 8);
+            t += __shfl_xor_sync(FULL, t, 4);
+            t += __shfl_xor_sync(FULL, t, 2);
+            t += __shfl_xor_sync(FULL, t, 1);
+            // lanes 0, 8, 16, 24 hold the totals; each condition's sums always land in the same lanes
+            if ((lane & 7) == 0 && (!b4 || has1)) {
+                const int ci = c - cb + (b4 ? 1 : 0), k = b3 ? 2 : 0;
+                kadd(acc[ci][k], acc[ci][k + 1], t);
             }
         }
     }
