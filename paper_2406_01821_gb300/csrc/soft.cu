@@ -34,6 +34,14 @@ constexpr int SOFT_W = 4;                 // warps per CTA
 constexpr int SOFT_MAX_RULES = 64;        // rules per set held in shared memory
 constexpr int SOFT_MAX_CONDS = 512;       // conditions per set accumulated in shared memory
 constexpr int SOFT_MAX_CHUNKS = 64;
+constexpr int SOFT_V = 2;                 // samples per lane; a group is 32 * SOFT_V samples
+constexpr int SOFT_G = 32 * SOFT_V;
+
+// Floats of a warp's shared arrays: lq [maxR][G], lu [maxR + 1][G], acc [maxC][4].
+__host__ __device__ constexpr size_t soft_per_warp(int maxR, int maxC)
+{
+    return (size_t)(2 * maxR + 1) * SOFT_G + (size_t)maxC * 4;
+}
 
 struct __align__(16) SoftRec {
     uint32_t meta;    // bit 0: pair condition, bit 1: '<', bit 2: category membership
@@ -210,15 +218,17 @@ struct SoftKArgs {
 struct XView {
     const float *col;
     int64_t stride;
-    __device__ __forceinline__ float operator()(int f) const { return col[(int64_t)f * stride]; }
+    // x[f] of the lane's sample v (32 v samples after its first)
+    __device__ __forceinline__ float operator()(int f, int v) const { return col[(int64_t)f * stride + 32 * v]; }
 };
 
-// This lane's (d ell / d a, d ell / d b or d t) of condition rc, given d ell / d log q of its rule.
-__device__ __forceinline__ float2 cond_grad(const SoftKArgs &a, const SoftRec &rc, const XView &x, float gq)
+// The lane's sample v: (d ell / d a, d ell / d b or d t) of condition rc, given d ell / d log q of
+// its rule.
+__device__ __forceinline__ float2 cond_grad(const SoftKArgs &a, const SoftRec &rc, const XView &x, int v, float gq)
 {
-    const float xf = x(rc.f);
+    const float xf = x(rc.f, v);
     const bool pair = rc.meta & 1u;
-    const float xg = pair ? x(rc.g) : 0.f;
+    const float xg = pair ? x(rc.g, v) : 0.f;
     const float lhs = rc.a * xf;
     const float rhs = pair ? rc.bt * xg : rc.bt;
     const float sg = (rc.meta & 2u) ? -1.f : 1.f;
@@ -227,74 +237,112 @@ __device__ __forceinline__ float2 cond_grad(const SoftKArgs &a, const SoftRec &r
     return make_float2(du * xf, pair ? -du * xg : -du);
 }
 
-// Forward (and adjoint) of set p over one group of 32 samples, lane = sample n (valid: n < N).
-// lq/lu: the warp's per-rule log-probabilities; acc: its per-condition gradient sums. CAT: the
-// batch may hold membership conditions.
-template <bool BWD, bool CAT>
+// Forward (and adjoint) of set p over one group of 32 * V samples: lane l holds samples
+// n0 + l + 32 v (v < V; bit v of valid: the sample exists), whose independent chains interleave.
+// lq/lu: the warp's per-rule log-probabilities [rule][32 V]; acc: its per-condition gradient sums.
+// CAT: the batch may hold membership conditions.
+template <bool BWD, bool CAT, int V>
 __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, int R, int cb, int deflt,
-                                           int64_t n, bool valid, const XView &x, float (*lq)[32],
-                                           float (*lu)[32], float (*acc)[4], int lane, float &loss_s,
-                                           float &loss_c)
+                                           int64_t n0, uint32_t valid, const XView &x,
+                                           float (*lq)[32 * V], float (*lu)[32 * V], float (*acc)[4], int lane,
+                                           float &loss_s, float &loss_c)
 {
-    const int yn = valid ? a.y[n] : -1;
+    int yn[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) yn[v] = ((valid >> v) & 1u) ? a.y[n0 + lane + 32 * v] : -1;
     // ---------------- forward
-    float lu_r = 0.f, lpy = -INFINITY;
+    float lu_r[V], lpy[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) { lu_r[v] = 0.f; lpy[v] = -INFINITY; }
     for (int j = 0; j < R; ++j) {
         const int r = rb + j;
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
-        float s = 0.f;
-#pragma unroll 4
+        float s[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) s[v] = 0.f;
+#pragma unroll 2
         for (int c = c0; c < c1; ++c) {
             const SoftRec rc = a.recs[c];
             if (CAT && (rc.meta & 4u)) {   // membership: its exact indicator, a factor 1 or 0 of q_r
-                if (!category_member(x(rc.f), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s = -INFINITY;
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (!category_member(x(rc.f, v), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s[v] = -INFINITY;
                 continue;
             }
-            const float lhs = rc.a * x(rc.f);
-            const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g) : rc.bt;
-            float u = (lhs - rhs) * a.inv_tau;
-            if (rc.meta & 2u) u = -u;
-            s += log_sigmoid(u);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float lhs = rc.a * x(rc.f, v);
+                const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g, v) : rc.bt;
+                float u = (lhs - rhs) * a.inv_tau;
+                if (rc.meta & 2u) u = -u;
+                s[v] += log_sigmoid(u);
+            }
         }
-        lq[j][lane] = s;
-        lu[j][lane] = lu_r;
-        if (a.rule_class[r] == yn) lpy = log_add(lpy, s + lu_r);
-        lu_r += logf(-expm1f(s));
+        const int cls = a.rule_class[r];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            lq[j][lane + 32 * v] = s[v];
+            lu[j][lane + 32 * v] = lu_r[v];
+            if (cls == yn[v]) lpy[v] = log_add(lpy[v], s[v] + lu_r[v]);
+            lu_r[v] += logf(-expm1f(s[v]));
+        }
     }
-    lu[R][lane] = lu_r;
-    if (deflt == yn) lpy = log_add(lpy, lu_r);
-    if (valid) kadd_loss(loss_s, loss_c, -lpy);
-    if (a.probs && valid) {
-        const int64_t orig = a.perm[n];
-        for (int k = 0; k < a.K; ++k) {
-            float lpk = (deflt == k) ? lu_r : -INFINITY;
-            for (int j = 0; j < R; ++j)
-                if (a.rule_class[rb + j] == k) lpk = log_add(lpk, lq[j][lane] + lu[j][lane]);
-            a.probs[((int64_t)p * a.N + orig) * a.K + k] = expf(lpk);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        lu[R][lane + 32 * v] = lu_r[v];
+        if (deflt == yn[v]) lpy[v] = log_add(lpy[v], lu_r[v]);
+        if (((valid >> v) & 1u)) kadd_loss(loss_s, loss_c, -lpy[v]);
+    }
+    if (a.probs) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (!((valid >> v) & 1u)) continue;
+            const int64_t orig = a.perm[n0 + lane + 32 * v];
+            for (int k = 0; k < a.K; ++k) {
+                float lpk = (deflt == k) ? lu_r[v] : -INFINITY;
+                for (int j = 0; j < R; ++j)
+                    if (a.rule_class[rb + j] == k) lpk = log_add(lpk, lq[j][lane + 32 * v] + lu[j][lane + 32 * v]);
+                a.probs[((int64_t)p * a.N + orig) * a.K + k] = expf(lpk);
+            }
         }
     }
     if (!BWD) return;
     // ---------------- adjoint
-    float lS = (deflt == yn) ? 0.f : -INFINITY;
-    float lT = (deflt == yn) ? -INFINITY : 0.f;
+    float lS[V], lT[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        lS[v] = (deflt == yn[v]) ? 0.f : -INFINITY;
+        lT[v] = (deflt == yn[v]) ? -INFINITY : 0.f;
+    }
     for (int j = R - 1; j >= 0; --j) {
         const int r = rb + j;
-        const float lqj = lq[j][lane], luj = lu[j][lane];
-        const bool same = a.rule_class[r] == yn;
-        float gq = same ? -expf(lqj + luj + lT - lpy) : expf(lqj + luj + lS - lpy);
-        if (!valid) gq = 0.f;
-        const float l1q = logf(-expm1f(lqj));
-        lS = log_add(same ? lqj : -INFINITY, l1q + lS);
-        lT = log_add(same ? -INFINITY : lqj, l1q + lT);
+        const int cls = a.rule_class[r];
+        float gq[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float lqj = lq[j][lane + 32 * v], luj = lu[j][lane + 32 * v];
+            const bool same = cls == yn[v];
+            gq[v] = same ? -expf(lqj + luj + lT[v] - lpy[v]) : expf(lqj + luj + lS[v] - lpy[v]);
+            if (!((valid >> v) & 1u)) gq[v] = 0.f;
+            const float l1q = logf(-expm1f(lqj));
+            lS[v] = log_add(same ? lqj : -INFINITY, l1q + lS[v]);
+            lT[v] = log_add(same ? -INFINITY : lqj, l1q + lT[v]);
+        }
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
-        // conditions two at a time: the four sums (d/da, d/db-or-dt of both) share one butterfly
+        // conditions two at a time: the four sums (d/da, d/db-or-dt of both, over all 32 V samples)
+        // share one butterfly
 #pragma unroll 2
         for (int c = c0; c < c1; c += 2) {
             const bool has1 = c + 1 < c1;
             const SoftRec r0 = a.recs[c];
             const SoftRec r1 = a.recs[has1 ? c + 1 : c];
-            const float2 g0 = (CAT && (r0.meta & 4u)) ? make_float2(0.f, 0.f) : cond_grad(a, r0, x, gq);
-            const float2 g1 = (!has1 || (CAT && (r1.meta & 4u))) ? make_float2(0.f, 0.f) : cond_grad(a, r1, x, gq);
+            const bool use0 = !(CAT && (r0.meta & 4u)), use1 = has1 && !(CAT && (r1.meta & 4u));
+            float2 g0 = make_float2(0.f, 0.f), g1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (use0) { const float2 t = cond_grad(a, r0, x, v, gq[v]); g0.x += t.x; g0.y += t.y; }
+                if (use1) { const float2 t = cond_grad(a, r1, x, v, gq[v]); g1.x += t.x; g1.y += t.y; }
+            }
             const bool b4 = lane & 16, b3 = lane & 8;
             // lanes 0..15 gather the first condition's two sums, lanes 16..31 the second's
             float k0 = b4 ? g1.x : g0.x, k1 = b4 ? g1.y : g0.y;
@@ -336,15 +384,15 @@ __device__ __forceinline__ void soft_flush(const SoftKArgs &a, int p, int ch, in
 template <bool BWD, bool CAT>
 __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
 {
-    // per warp: lq[maxR][32], lu[maxR+1][32], acc[maxC][4] (ga sum/comp, gbt sum/comp)
+    // per warp: lq[maxR][G], lu[maxR+1][G], acc[maxC][4] (ga sum/comp, gbt sum/comp)
     extern __shared__ __align__(16) float sm[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t tasks = (int64_t)a.P * a.nchunks;
-    const size_t per_warp = (size_t)(2 * a.maxR + 1) * 32 + (size_t)a.maxC * 4;
+    const size_t per_warp = soft_per_warp(a.maxR, a.maxC);
     float *base_w = sm + per_warp * w;
-    float(*lq)[32] = reinterpret_cast<float(*)[32]>(base_w);
-    float(*lu)[32] = reinterpret_cast<float(*)[32]>(base_w + (size_t)a.maxR * 32);
-    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * 32);
+    float(*lq)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w);
+    float(*lu)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w + (size_t)a.maxR * SOFT_G);
+    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * SOFT_G);
     if (*a.status) return;
 
     while (true) {
@@ -365,12 +413,14 @@ __global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
         float loss_s = 0.f, loss_c = 0.f;
         const int64_t s0 = (int64_t)ch * a.chunk;
         const int64_t s1 = min(s0 + a.chunk, a.N);
-        for (int64_t nb = s0; nb < s1; nb += 32) {
-            const int64_t n = nb + lane;
-            const bool valid = n < a.N;
-            const XView x{a.Xt + (valid ? n : 0), a.n_pad};
-            soft_group<BWD, CAT>(a, p, rb, re - rb, cb, a.set_default[p], n, valid, x, lq, lu, acc, lane, loss_s,
-                            loss_c);
+        for (int64_t nb = s0; nb < s1; nb += SOFT_G) {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int v = 0; v < SOFT_V; ++v) valid |= (nb + lane + 32 * v < s1 ? 1u : 0u) << v;
+            // the dataset is padded to a multiple of 128 samples: every read stays inside it
+            const XView x{a.Xt + nb + lane, a.n_pad};
+            soft_group<BWD, CAT, SOFT_V>(a, p, rb, re - rb, cb, a.set_default[p], nb, valid, x, lq, lu, acc, lane,
+                                         loss_s, loss_c);
         }
         soft_flush<BWD>(a, p, ch, cb, ce, loss_s, acc, lane);
     }
@@ -386,18 +436,21 @@ constexpr int SOFT_TILE_STATIC = 256;   // bytes kept for the kernel's static sh
 
 __device__ __forceinline__ void stage_group(float *dst, const float *Xt, int64_t n_pad, int F, int64_t nb)
 {
-    // F rows x 32 samples, 16-byte pieces
-    for (int i = threadIdx.x; i < F * 8; i += blockDim.x) {
-        const int f = i >> 3, q = i & 7;
+    // F rows x G samples, 16-byte pieces
+    constexpr int PR = SOFT_G / 4;   // pieces per row
+    for (int i = threadIdx.x; i < F * PR; i += blockDim.x) {
+        const int f = i / PR, q = i % PR;
         const float *src = Xt + (int64_t)f * n_pad + nb + 4 * q;
-        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + f * 32 + 4 * q);
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + f * SOFT_G + 4 * q);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// Launched with at most SOFT_TW_MAX warps: 80 registers per thread keep the two samples' chains
+// of the adjoint in registers and fit 512 threads (a launch bound of 512 capped it at 64 and spilled).
 template <bool BWD, bool CAT>
-__global__ void __launch_bounds__(SOFT_TW_MAX * 32) k_soft_tile(SoftKArgs a, int F)
+__global__ void __maxnreg__(80) k_soft_tile(SoftKArgs a, int F)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ int64_t s_task;
@@ -405,12 +458,12 @@ __global__ void __launch_bounds__(SOFT_TW_MAX * 32) k_soft_tile(SoftKArgs a, int
     const int TW = blockDim.x >> 5;                   // sets per CTA group
     const int64_t set_groups = (a.P + TW - 1) / TW;
     const int64_t tasks = set_groups * a.nchunks;
-    const size_t per_warp = (size_t)(2 * a.maxR + 1) * 32 + (size_t)a.maxC * 4;
+    const size_t per_warp = soft_per_warp(a.maxR, a.maxC);
     float *base_w = sm + per_warp * w;
-    float(*lq)[32] = reinterpret_cast<float(*)[32]>(base_w);
-    float(*lu)[32] = reinterpret_cast<float(*)[32]>(base_w + (size_t)a.maxR * 32);
-    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * 32);
-    float *xbuf = sm + per_warp * TW;                 // [2][F][32]
+    float(*lq)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w);
+    float(*lu)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w + (size_t)a.maxR * SOFT_G);
+    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * SOFT_G);
+    float *xbuf = sm + per_warp * TW;                 // [2][F][G]
     if (*a.status) return;
 
     while (true) {
@@ -442,22 +495,24 @@ __global__ void __launch_bounds__(SOFT_TW_MAX * 32) k_soft_tile(SoftKArgs a, int
         float loss_s = 0.f, loss_c = 0.f;
         const int64_t s0 = (int64_t)ch * a.chunk;
         const int64_t s1 = min(s0 + a.chunk, a.N);
-        const int ngroups = (int)((s1 - s0 + 31) / 32);
+        const int ngroups = (int)((s1 - s0 + SOFT_G - 1) / SOFT_G);
         stage_group(xbuf, a.Xt, a.n_pad, F, s0);
         for (int gi = 0; gi < ngroups; ++gi) {
-            const int64_t nb = s0 + 32 * (int64_t)gi;
+            const int64_t nb = s0 + SOFT_G * (int64_t)gi;
             if (gi + 1 < ngroups) {
-                stage_group(xbuf + ((gi + 1) & 1) * F * 32, a.Xt, a.n_pad, F, nb + 32);
+                stage_group(xbuf + ((gi + 1) & 1) * F * SOFT_G, a.Xt, a.n_pad, F, nb + SOFT_G);
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
             } else {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
             __syncthreads();
             if (active) {
-                const int64_t n = nb + lane;
-                const bool valid = n < a.N;
-                const XView x{xbuf + (gi & 1) * F * 32 + lane, 32};
-                soft_group<BWD, CAT>(a, p, rb, R, cb, deflt, n, valid, x, lq, lu, acc, lane, loss_s, loss_c);
+                uint32_t valid = 0;
+#pragma unroll
+                for (int v = 0; v < SOFT_V; ++v) valid |= (nb + lane + 32 * v < s1 ? 1u : 0u) << v;
+                const XView x{xbuf + (gi & 1) * F * SOFT_G + lane, SOFT_G};
+                soft_group<BWD, CAT, SOFT_V>(a, p, rb, R, cb, deflt, nb, valid, x, lq, lu, acc, lane, loss_s,
+                                             loss_c);
             }
             __syncthreads();              // the buffer is restaged two groups later
         }
@@ -528,7 +583,7 @@ static void set_soft_attributes(Ctx *ctx)
 template <bool BWD, bool CAT>
 static int soft_tile_per_sm(Ctx *ctx, int tw, size_t per_warp, int F)
 {
-    const size_t bytes = per_warp * tw + sizeof(float) * 2 * 32 * (size_t)F;
+    const size_t bytes = per_warp * tw + sizeof(float) * 2 * SOFT_G * (size_t)F;
     if (bytes + SOFT_TILE_STATIC > ctx->smem_optin) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft_tile<BWD, CAT>, tw * 32, bytes) != cudaSuccess) {
@@ -556,7 +611,7 @@ static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bw
                               : soft_tile_per_sm<false, CAT>(ctx, t, per_warp, F);
             if (c * t > best) { best = c * t; tw = t; per_sm = c; }
         }
-        smem_tile = per_warp * tw + sizeof(float) * 2 * 32 * (size_t)F;
+        smem_tile = per_warp * tw + sizeof(float) * 2 * SOFT_G * (size_t)F;
     } else {
         if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true, CAT>, SOFT_W * 32, smem);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false, CAT>, SOFT_W * 32, smem);
@@ -580,7 +635,7 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     int nchunks = (int)std::min<int64_t>(SOFT_MAX_CHUNKS, (s.N + 1023) / 1024);
     if (nchunks < 1) nchunks = 1;
     int64_t chunk = (s.N + nchunks - 1) / nchunks;
-    chunk = (chunk + 31) / 32 * 32;
+    chunk = (chunk + SOFT_G - 1) / SOFT_G * SOFT_G;
     nchunks = (int)((s.N + chunk - 1) / chunk);
 
     SoftRec *recs = nullptr;
@@ -650,10 +705,10 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
             set_error("soft evaluation rejected the batch: %s", status_text(*hs).c_str());
         }
     }
-    const size_t per_warp = sizeof(float) * ((size_t)(2 * k.maxR + 1) * 32 + (size_t)k.maxC * 4);
+    const size_t per_warp = sizeof(float) * soft_per_warp(k.maxR, k.maxC);
     const size_t smem = per_warp * SOFT_W;
     // the staged-tile kernel when its per-CTA footprint (8 warps + two feature tiles) fits
-    const size_t smem_tile = per_warp * SOFT_TW_MIN + sizeof(float) * 2 * 32 * (size_t)s.F;
+    const size_t smem_tile = per_warp * SOFT_TW_MIN + sizeof(float) * 2 * SOFT_G * (size_t)s.F;
     const bool tiled = s.F <= 128 && smem_tile + SOFT_TILE_STATIC <= ctx->smem_optin;
     if (rc == RS_OK && smem > ctx->smem_optin) {
         rc = RS_ERR_TOO_LARGE;
