@@ -41,6 +41,12 @@ inline cudaError_t dev_alloc_async(T **p, size_t bytes, cudaStream_t stream)
 {
     return dev_alloc_async(reinterpret_cast<void **>(p), bytes, stream);
 }
+template <typename T>
+inline cudaError_t dev_alloc_pool_async(T **p, size_t bytes, cudaMemPool_t pool, cudaStream_t stream)
+{
+    if (take_injected_alloc_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMallocFromPoolAsync(reinterpret_cast<void **>(p), bytes, pool, stream);
+}
 
 // Device status word bits (set with atomicOr by kernels that find a problem).
 enum : uint32_t {

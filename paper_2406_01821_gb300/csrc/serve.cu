@@ -402,6 +402,9 @@ struct Server {
     size_t used = 0;
     std::vector<int> free_slots;
     cudaStream_t sstream = nullptr, kstream = nullptr;
+    // request memory: a pool of the server's own that keeps what it has mapped (up to the budget),
+    // so that admissions do not wait for the driver to map memory again
+    cudaMemPool_t pool = nullptr;
     cudaEvent_t kevent = nullptr;
     bool kernel_live = false;
     ReqDesc *d_table = nullptr;
@@ -480,6 +483,16 @@ static rs_status server_start(Ctx *ctx, Server **out)
     if ((e = cudaStreamCreateWithFlags(&s->sstream, cudaStreamNonBlocking))) return fail(e, "stream");
     if ((e = cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking))) return fail(e, "stream");
     if ((e = cudaEventCreateWithFlags(&s->kevent, cudaEventDisableTiming))) return fail(e, "event");
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        if ((e = cudaMemPoolCreate(&s->pool, &props))) return fail(e, "memory pool");
+        uint64_t keep = ctx->budget;
+        if ((e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep)))
+            return fail(e, "pool attribute");
+    }
     if ((e = cudaMalloc(&s->d_table, sizeof(ReqDesc) * MAX_SLOTS))) return fail(e, "table");
     if ((e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking))) return fail(e, "stream");
     if ((e = cudaMalloc(&s->d_claims, sizeof(unsigned long long) * MAX_SLOTS))) return fail(e, "claims");
@@ -541,6 +554,7 @@ void server_shutdown(Ctx *ctx)
     cudaFreeHost(s->h_flag);
     cudaFreeHost(s->h_stop);
     cudaEventDestroy(s->kevent);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     cudaStreamDestroy(s->sstream);
     cudaStreamDestroy(s->kstream);
     cudaStreamDestroy(s->cstream);
@@ -692,7 +706,7 @@ static bool admit_soft(Server *s, Request &r)
 {
     if (s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
-    if (dev_alloc_async(&base, r.device_bytes, s->sstream) != cudaSuccess) {
+    if (dev_alloc_pool_async(&base, r.device_bytes, s->pool, s->sstream) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -734,7 +748,7 @@ static bool try_admit(Server *s, Request &r)
     const int64_t groups = serve_groups(*r.ds, r.P, r.cat);
     if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
-    if (dev_alloc_async(&base, r.device_bytes, s->sstream) != cudaSuccess) {
+    if (dev_alloc_pool_async(&base, r.device_bytes, s->pool, s->sstream) != cudaSuccess) {
         cudaGetLastError();
         return false;                      // retry later, when memory is back
     }
