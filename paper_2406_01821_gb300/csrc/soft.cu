@@ -37,10 +37,11 @@ constexpr int SOFT_MAX_CHUNKS = 64;
 constexpr int SOFT_V = 2;                 // samples per lane; a group is 32 * SOFT_V samples
 constexpr int SOFT_G = 32 * SOFT_V;
 
-// Floats of a warp's shared arrays: lq [maxR][G], lu [maxR + 1][G], acc [maxC][4].
-__host__ __device__ constexpr size_t soft_per_warp(int maxR, int maxC)
+// Floats of a warp's shared arrays: lu [maxR + 1][G], acc [maxC][4], and lq [maxR][G] when the
+// class probabilities are written.
+__host__ __device__ constexpr size_t soft_per_warp(int maxR, int maxC, bool with_lq)
 {
-    return (size_t)(2 * maxR + 1) * SOFT_G + (size_t)maxC * 4;
+    return (size_t)(maxR + 1) * SOFT_G + (size_t)maxC * 4 + (with_lq ? (size_t)maxR * SOFT_G : 0);
 }
 
 struct __align__(16) SoftRec {
@@ -237,9 +238,38 @@ __device__ __forceinline__ float2 cond_grad(const SoftKArgs &a, const SoftRec &r
     return make_float2(du * xf, pair ? -du * xg : -du);
 }
 
+// log q of one rule (its conditions [c0, c1)) for the lane's V samples: the sum of the
+// conditions' log-sigmoids (membership tests: 0 or -inf). The forward and the adjoint both call it.
+template <bool CAT, int V>
+__device__ __forceinline__ void rule_logq(const SoftKArgs &a, int c0, int c1, const XView &x, float (&s)[V])
+{
+#pragma unroll
+    for (int v = 0; v < V; ++v) s[v] = 0.f;
+#pragma unroll 2
+    for (int c = c0; c < c1; ++c) {
+        const SoftRec rc = a.recs[c];
+        if (CAT && (rc.meta & 4u)) {   // membership: its exact indicator, a factor 1 or 0 of q_r
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (!category_member(x(rc.f, v), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s[v] = -INFINITY;
+            continue;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float lhs = rc.a * x(rc.f, v);
+            const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g, v) : rc.bt;
+            float u = (lhs - rhs) * a.inv_tau;
+            if (rc.meta & 2u) u = -u;
+            s[v] += log_sigmoid(u);
+        }
+    }
+}
+
 // Forward (and adjoint) of set p over one group of 32 * V samples: lane l holds samples
 // n0 + l + 32 v (v < V; bit v of valid: the sample exists), whose independent chains interleave.
-// lq/lu: the warp's per-rule log-probabilities [rule][32 V]; acc: its per-condition gradient sums.
+// lu: the warp's per-rule log-probabilities that no earlier rule fired [rule][32 V]; lq: the
+// rules' log q, kept only when class probabilities are written (null otherwise: the adjoint
+// computes them again); acc: the per-condition gradient sums.
 // CAT: the batch may hold membership conditions.
 template <bool BWD, bool CAT, int V>
 __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, int R, int cb, int deflt,
@@ -258,30 +288,11 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         const int r = rb + j;
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
         float s[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) s[v] = 0.f;
-#pragma unroll 2
-        for (int c = c0; c < c1; ++c) {
-            const SoftRec rc = a.recs[c];
-            if (CAT && (rc.meta & 4u)) {   // membership: its exact indicator, a factor 1 or 0 of q_r
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (!category_member(x(rc.f, v), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s[v] = -INFINITY;
-                continue;
-            }
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const float lhs = rc.a * x(rc.f, v);
-                const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g, v) : rc.bt;
-                float u = (lhs - rhs) * a.inv_tau;
-                if (rc.meta & 2u) u = -u;
-                s[v] += log_sigmoid(u);
-            }
-        }
+        rule_logq<CAT, V>(a, c0, c1, x, s);
         const int cls = a.rule_class[r];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            lq[j][lane + 32 * v] = s[v];
+            if (lq) lq[j][lane + 32 * v] = s[v];      // kept only for the class probabilities
             lu[j][lane + 32 * v] = lu_r[v];
             if (cls == yn[v]) lpy[v] = log_add(lpy[v], s[v] + lu_r[v]);
             lu_r[v] += logf(-expm1f(s[v]));
@@ -317,10 +328,13 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
     for (int j = R - 1; j >= 0; --j) {
         const int r = rb + j;
         const int cls = a.rule_class[r];
+        const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
+        float lqr[V];
+        rule_logq<CAT, V>(a, c0, c1, x, lqr);        // log q again: cheaper than keeping it per sample
         float gq[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const float lqj = lq[j][lane + 32 * v], luj = lu[j][lane + 32 * v];
+            const float lqj = lqr[v], luj = lu[j][lane + 32 * v];
             const bool same = cls == yn[v];
             gq[v] = same ? -expf(lqj + luj + lT[v] - lpy[v]) : expf(lqj + luj + lS[v] - lpy[v]);
             if (!((valid >> v) & 1u)) gq[v] = 0.f;
@@ -328,7 +342,6 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
             lS[v] = log_add(same ? lqj : -INFINITY, l1q + lS[v]);
             lT[v] = log_add(same ? -INFINITY : lqj, l1q + lT[v]);
         }
-        const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
         // conditions two at a time: the four sums (d/da, d/db-or-dt of both, over all 32 V samples)
         // share one butterfly
 #pragma unroll 2
@@ -382,17 +395,19 @@ __device__ __forceinline__ void soft_flush(const SoftKArgs &a, int p, int ch, in
 }
 
 template <bool BWD, bool CAT>
-__global__ void __launch_bounds__(SOFT_W * 32) k_soft(SoftKArgs a)
+__global__ void __maxnreg__(80) k_soft(SoftKArgs a)     // launched with SOFT_W warps
 {
-    // per warp: lq[maxR][G], lu[maxR+1][G], acc[maxC][4] (ga sum/comp, gbt sum/comp)
+    // per warp: lu[maxR+1][G], acc[maxC][4] (ga sum/comp, gbt sum/comp), lq[maxR][G] (probabilities)
     extern __shared__ __align__(16) float sm[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t tasks = (int64_t)a.P * a.nchunks;
-    const size_t per_warp = soft_per_warp(a.maxR, a.maxC);
+    const size_t per_warp = soft_per_warp(a.maxR, a.maxC, a.probs != nullptr);
     float *base_w = sm + per_warp * w;
-    float(*lq)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w);
-    float(*lu)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w + (size_t)a.maxR * SOFT_G);
-    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * SOFT_G);
+    float(*lu)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w);
+    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(a.maxR + 1) * SOFT_G);
+    float(*lq)[SOFT_G] = a.probs ? reinterpret_cast<float(*)[SOFT_G]>(base_w + (size_t)(a.maxR + 1) * SOFT_G +
+                                                                    (size_t)a.maxC * 4)
+                                 : nullptr;
     if (*a.status) return;
 
     while (true) {
@@ -458,11 +473,13 @@ __global__ void __maxnreg__(80) k_soft_tile(SoftKArgs a, int F)
     const int TW = blockDim.x >> 5;                   // sets per CTA group
     const int64_t set_groups = (a.P + TW - 1) / TW;
     const int64_t tasks = set_groups * a.nchunks;
-    const size_t per_warp = soft_per_warp(a.maxR, a.maxC);
+    const size_t per_warp = soft_per_warp(a.maxR, a.maxC, a.probs != nullptr);
     float *base_w = sm + per_warp * w;
-    float(*lq)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w);
-    float(*lu)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w + (size_t)a.maxR * SOFT_G);
-    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(2 * a.maxR + 1) * SOFT_G);
+    float(*lu)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w);
+    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(a.maxR + 1) * SOFT_G);
+    float(*lq)[SOFT_G] = a.probs ? reinterpret_cast<float(*)[SOFT_G]>(base_w + (size_t)(a.maxR + 1) * SOFT_G +
+                                                                    (size_t)a.maxC * 4)
+                                 : nullptr;
     float *xbuf = sm + per_warp * TW;                 // [2][F][G]
     if (*a.status) return;
 
@@ -705,7 +722,7 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
             set_error("soft evaluation rejected the batch: %s", status_text(*hs).c_str());
         }
     }
-    const size_t per_warp = sizeof(float) * soft_per_warp(k.maxR, k.maxC);
+    const size_t per_warp = sizeof(float) * soft_per_warp(k.maxR, k.maxC, k.probs != nullptr);
     const size_t smem = per_warp * SOFT_W;
     // the staged-tile kernel when its per-CTA footprint (8 warps + two feature tiles) fits
     const size_t smem_tile = per_warp * SOFT_TW_MIN + sizeof(float) * 2 * SOFT_G * (size_t)s.F;
