@@ -19,8 +19,9 @@
 // Everything is evaluated in float32 in the log domain, which keeps 1 - q_r and the products of
 // many sigmoids representable where the linear form underflows.
 //
-// Work: one warp owns a (rule set, sample chunk) pair and walks the chunk 32 samples at a time
-// (lane = sample), so each partial sum has a fixed summation order. Chunks are a function of N
+// Work: one warp owns a (rule set, sample chunk) pair and walks the chunk 64 samples at a time
+// (two per lane), so each partial sum has a fixed summation order. The forward keeps lu_r per
+// rule and sample; the adjoint computes lq_r again from the conditions. Chunks are a function of N
 // only; partial losses and gradients per chunk are reduced in a second kernel in a fixed order,
 // which makes results bit-reproducible run to run and independent of scheduling.
 #include "rs_internal.cuh"
@@ -214,8 +215,9 @@ struct SoftKArgs {
     const int32_t *order;            // sets by decreasing size (schedule only; results do not depend on it)
 };
 
-// Feature access for one 32-sample group: the lane's sample column either in global memory
-// (x[f] at col[f * stride]) or in a staged shared-memory tile [F][32] (stride 32).
+// Feature access for one group of 64 samples: the lane's first sample column either in global
+// memory (x[f] at col[f * stride]) or in a staged shared-memory tile [F][64] (stride 64); its
+// second sample is 32 columns further.
 struct XView {
     const float *col;
     int64_t stride;
@@ -442,10 +444,9 @@ __global__ void __maxnreg__(80) k_soft(SoftKArgs a)     // launched with SOFT_W 
 }
 
 // The same evaluation with the warps of a CTA on as many neighbouring sets (in size order) over
-// the same chunk:
-// the features of each 32-sample group are staged once per CTA in shared memory (double-buffered
-// asynchronous copies), so condition loads are shared-memory reads. Per-set results are identical
-// to k_soft (same per-sample arithmetic and summation order).
+// the same chunk: the features of each 64-sample group are staged once per CTA in shared memory
+// (double-buffered asynchronous copies), so condition loads are shared-memory reads. Per-set
+// results are identical to k_soft (same per-sample arithmetic and summation order).
 constexpr int SOFT_TW_MIN = 4, SOFT_TW_MAX = 16;   // warps (sets) per CTA of the staged-tile kernel
 constexpr int SOFT_TILE_STATIC = 256;   // bytes kept for the kernel's static shared memory
 
