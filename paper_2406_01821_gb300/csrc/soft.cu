@@ -267,6 +267,89 @@ __device__ __forceinline__ void rule_logq(const SoftKArgs &a, int c0, int c1, co
     }
 }
 
+// rule_logq for the adjoint, which also keeps u and e^-|u| of the rule's first SOFT_CACHE
+// conditions (same arithmetic and order, so the same log q) for their gradients.
+constexpr int SOFT_CACHE = 4;
+template <bool CAT, int V>
+__device__ __forceinline__ void rule_logq_cached(const SoftKArgs &a, int c0, int c1, const XView &x, float (&s)[V],
+                                                 float (&cu)[SOFT_CACHE][V], float (&ce)[SOFT_CACHE][V])
+{
+#pragma unroll
+    for (int v = 0; v < V; ++v) s[v] = 0.f;
+#pragma unroll
+    for (int k = 0; k < SOFT_CACHE; ++k) {
+        if (c0 + k >= c1) break;
+        const SoftRec rc = a.recs[c0 + k];
+        if (CAT && (rc.meta & 4u)) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (!category_member(x(rc.f, v), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s[v] = -INFINITY;
+            continue;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float lhs = rc.a * x(rc.f, v);
+            const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g, v) : rc.bt;
+            float u = (lhs - rhs) * a.inv_tau;
+            if (rc.meta & 2u) u = -u;
+            const float e = expf(-fabsf(u));
+            cu[k][v] = u;
+            ce[k][v] = e;
+            s[v] += -(fmaxf(-u, 0.f) + log1p_unit(e));
+        }
+    }
+#pragma unroll 2
+    for (int c = c0 + SOFT_CACHE; c < c1; ++c) {
+        const SoftRec rc = a.recs[c];
+        if (CAT && (rc.meta & 4u)) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (!category_member(x(rc.f, v), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s[v] = -INFINITY;
+            continue;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float lhs = rc.a * x(rc.f, v);
+            const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g, v) : rc.bt;
+            float u = (lhs - rhs) * a.inv_tau;
+            if (rc.meta & 2u) u = -u;
+            s[v] += log_sigmoid(u);
+        }
+    }
+}
+
+// cond_grad from the condition's u (already signed) and e = e^-|u|.
+__device__ __forceinline__ float2 cond_grad_cached(const SoftKArgs &a, const SoftRec &rc, const XView &x, int v,
+                                                   float gq, float u, float e)
+{
+    const float xf = x(rc.f, v);
+    const bool pair = rc.meta & 1u;
+    const float sg = (rc.meta & 2u) ? -1.f : 1.f;
+    const float du = gq * __fdividef(u >= 0.f ? e : 1.f, 1.f + e) * sg * a.inv_tau;
+    return make_float2(du * xf, pair ? -du * x(rc.g, v) : -du);
+}
+
+// The four gradient sums of conditions c and c + 1 (g0, g1: this lane's d/da, d/db-or-dt) reduced
+// over the warp in one butterfly and added to the warp's accumulators.
+__device__ __forceinline__ void reduce_pair(float2 g0, float2 g1, int ci0, bool has1, float (*acc)[4], int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8;
+    // lanes 0..15 gather the first condition's two sums, lanes 16..31 the second's
+    float k0 = b4 ? g1.x : g0.x, k1 = b4 ? g1.y : g0.y;
+    k0 += __shfl_xor_sync(FULL, b4 ? g0.x : g1.x, 16);
+    k1 += __shfl_xor_sync(FULL, b4 ? g0.y : g1.y, 16);
+    // then lanes with bit 3 clear the d/da sum, set the other
+    float t = (b3 ? k1 : k0) + __shfl_xor_sync(FULL, b3 ? k0 : k1, 8);
+    t += __shfl_xor_sync(FULL, t, 4);
+    t += __shfl_xor_sync(FULL, t, 2);
+    t += __shfl_xor_sync(FULL, t, 1);
+    // lanes 0, 8, 16, 24 hold the totals; each condition's sums always land in the same lanes
+    if ((lane & 7) == 0 && (!b4 || has1)) {
+        const int ci = ci0 + (b4 ? 1 : 0), k = b3 ? 2 : 0;
+        kadd(acc[ci][k], acc[ci][k + 1], t);
+    }
+}
+
 // Forward (and adjoint) of set p over one group of 32 * V samples: lane l holds samples
 // n0 + l + 32 v (v < V; bit v of valid: the sample exists), whose independent chains interleave.
 // lu: the warp's per-rule log-probabilities that no earlier rule fired [rule][32 V]; lq: the
@@ -331,8 +414,8 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
         const int r = rb + j;
         const int cls = a.rule_class[r];
         const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
-        float lqr[V];
-        rule_logq<CAT, V>(a, c0, c1, x, lqr);        // log q again: cheaper than keeping it per sample
+        float lqr[V], cu[SOFT_CACHE][V], ce[SOFT_CACHE][V];
+        rule_logq_cached<CAT, V>(a, c0, c1, x, lqr, cu, ce);   // log q again: cheaper than keeping it
         float gq[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -345,9 +428,31 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
             lT[v] = log_add(same ? -INFINITY : lqj, l1q + lT[v]);
         }
         // conditions two at a time: the four sums (d/da, d/db-or-dt of both, over all 32 V samples)
-        // share one butterfly
+        // share one butterfly; the first SOFT_CACHE conditions reuse u and e^-|u| from above
+#pragma unroll
+        for (int k = 0; k < SOFT_CACHE; k += 2) {
+            const int c = c0 + k;
+            if (c >= c1) break;
+            const bool has1 = c + 1 < c1;
+            const SoftRec r0 = a.recs[c];
+            const SoftRec r1 = a.recs[has1 ? c + 1 : c];
+            const bool use0 = !(CAT && (r0.meta & 4u)), use1 = has1 && !(CAT && (r1.meta & 4u));
+            float2 g0 = make_float2(0.f, 0.f), g1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (use0) {
+                    const float2 t = cond_grad_cached(a, r0, x, v, gq[v], cu[k][v], ce[k][v]);
+                    g0.x += t.x; g0.y += t.y;
+                }
+                if (use1) {
+                    const float2 t = cond_grad_cached(a, r1, x, v, gq[v], cu[k + 1][v], ce[k + 1][v]);
+                    g1.x += t.x; g1.y += t.y;
+                }
+            }
+            reduce_pair(g0, g1, c - cb, has1, acc, lane);
+        }
 #pragma unroll 2
-        for (int c = c0; c < c1; c += 2) {
+        for (int c = c0 + SOFT_CACHE; c < c1; c += 2) {
             const bool has1 = c + 1 < c1;
             const SoftRec r0 = a.recs[c];
             const SoftRec r1 = a.recs[has1 ? c + 1 : c];
@@ -358,21 +463,7 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
                 if (use0) { const float2 t = cond_grad(a, r0, x, v, gq[v]); g0.x += t.x; g0.y += t.y; }
                 if (use1) { const float2 t = cond_grad(a, r1, x, v, gq[v]); g1.x += t.x; g1.y += t.y; }
             }
-            const bool b4 = lane & 16, b3 = lane & 8;
-            // lanes 0..15 gather the first condition's two sums, lanes 16..31 the second's
-            float k0 = b4 ? g1.x : g0.x, k1 = b4 ? g1.y : g0.y;
-            k0 += __shfl_xor_sync(FULL, b4 ? g0.x : g1.x, 16);
-            k1 += __shfl_xor_sync(FULL, b4 ? g0.y : g1.y, 16);
-            // then lanes with bit 3 clear the d/da sum, set the other
-            float t = (b3 ? k1 : k0) + __shfl_xor_sync(FULL, b3 ? k0 : k1, 8);
-            t += __shfl_xor_sync(FULL, t, 4);
-            t += __shfl_xor_sync(FULL, t, 2);
-            t += __shfl_xor_sync(FULL, t, 1);
-            // lanes 0, 8, 16, 24 hold the totals; each condition's sums always land in the same lanes
-            if ((lane & 7) == 0 && (!b4 || has1)) {
-                const int ci = c - cb + (b4 ? 1 : 0), k = b3 ? 2 : 0;
-                kadd(acc[ci][k], acc[ci][k + 1], t);
-            }
+            reduce_pair(g0, g1, c - cb, has1, acc, lane);
         }
     }
 }
@@ -397,7 +488,7 @@ __device__ __forceinline__ void soft_flush(const SoftKArgs &a, int p, int ch, in
 }
 
 template <bool BWD, bool CAT>
-__global__ void __maxnreg__(80) k_soft(SoftKArgs a)     // launched with SOFT_W warps
+__global__ void __maxnreg__(96) k_soft(SoftKArgs a)     // launched with SOFT_W warps
 {
     // per warp: lu[maxR+1][G], acc[maxC][4] (ga sum/comp, gbt sum/comp), lq[maxR][G] (probabilities)
     extern __shared__ __align__(16) float sm[];
@@ -463,10 +554,10 @@ __device__ __forceinline__ void stage_group(float *dst, const float *Xt, int64_t
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Launched with at most SOFT_TW_MAX warps: 80 registers per thread keep the two samples' chains
+// Launched with at most SOFT_TW_MAX warps: 96 registers per thread keep the two samples' chains
 // of the adjoint in registers and fit 512 threads (a launch bound of 512 capped it at 64 and spilled).
 template <bool BWD, bool CAT>
-__global__ void __maxnreg__(80) k_soft_tile(SoftKArgs a, int F)
+__global__ void __maxnreg__(96) k_soft_tile(SoftKArgs a, int F)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ int64_t s_task;
