@@ -538,7 +538,7 @@ __global__ void __maxnreg__(96) k_soft(SoftKArgs a)     // launched with SOFT_W 
 // the same chunk: the features of each 64-sample group are staged once per CTA in shared memory
 // (double-buffered asynchronous copies), so condition loads are shared-memory reads. Per-set
 // results are identical to k_soft (same per-sample arithmetic and summation order).
-constexpr int SOFT_TW_MIN = 4, SOFT_TW_MAX = 16;   // warps (sets) per CTA of the staged-tile kernel
+constexpr int SOFT_TW_MIN = 4, SOFT_TW_MAX = 24;   // warps (sets) per CTA of the staged-tile kernel
 constexpr int SOFT_TILE_STATIC = 256;   // bytes kept for the kernel's static shared memory
 
 __device__ __forceinline__ void stage_group(float *dst, const float *Xt, int64_t n_pad, int F, int64_t nb)
@@ -705,7 +705,9 @@ static int soft_tile_per_sm(Ctx *ctx, int tw, size_t per_warp, int F)
 // One persistent wave of the soft kernel: the staged-tile form or the per-warp form, forward only
 // or forward + adjoint, with or without membership conditions (CAT). The staged-tile form takes
 // the number of warps per CTA that keeps the most warps resident for this batch's per-warp
-// arrays (ties: fewer warps per CTA, so that a CTA's sets are closer in size).
+// arrays (ties: fewer warps per CTA, so that a CTA's sets are closer in size); small populations
+// keep at most P / 8 warps per CTA, since a CTA walks its sets in step and a wide CTA over few
+// sets of uneven size waits for the longest.
 template <bool CAT>
 static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bwd, int F, size_t smem,
                                size_t per_warp, cudaStream_t stream)
@@ -715,7 +717,8 @@ static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bw
     size_t smem_tile = 0;
     if (tiled) {
         int best = 0;
-        for (int t = SOFT_TW_MIN; t <= SOFT_TW_MAX; ++t) {
+        const int tw_max = std::max(SOFT_TW_MIN, std::min(SOFT_TW_MAX, k.P / 8));
+        for (int t = SOFT_TW_MIN; t <= tw_max; ++t) {
             const int c = bwd ? soft_tile_per_sm<true, CAT>(ctx, t, per_warp, F)
                               : soft_tile_per_sm<false, CAT>(ctx, t, per_warp, F);
             if (c * t > best) { best = c * t; tw = t; per_sm = c; }
