@@ -232,7 +232,10 @@ rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, i
  * rs_eval_hard's exactly.
  *   kind    RS_KIND_HARD (soft requests carry a temperature: rs_submit_soft)
  *   errors  RS_ERR_TOO_LARGE if the request alone exceeds the budget; RS_ERR_UNSUPPORTED for
- *           datasets with more than 256 features; RS_ERR_NOT_FOUND (ds)
+ *           datasets with more than 256 features, and for batches with category sets (membership
+ *           tests) unless the dataset is finite with at most 128 features; RS_ERR_NOT_FOUND (ds)
+ * Request memory comes from a pool of the scheduler's own that keeps what it has mapped, up to the
+ * budget, until the context is destroyed.
  * Thread-safe. *ticket receives a non-zero id.
  */
 rs_status rs_submit(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t kind, uint64_t *ticket);
