@@ -8,8 +8,8 @@
  *   condition  a*x[f] op t           (threshold)       Sec. 3 / Fig. 1a rows with one weight
  *              a*x[f] op b*x[g]      (feature pair)    Sec. 3 / Fig. 1a row [0, 1.0, -0.38, ...]
  *              op is '>' or '<'; each product is one correctly rounded float32 multiply and the
- *              compare is strict and IEEE-ordered (NaN compares false, a zero margin is false,
- *              Sec. 3: "clips negative values to zero ... rounds positives to one").
+ *              compare is strict and IEEE-ordered (NaN compares false, a zero margin is false:
+ *              the hard activation of Sec. 3 maps negative margins to false, positive to true).
  *   rule       conjunction of its conditions naming one class (Fig. 1b "&" and "->"); an empty
  *              rule fires.
  *   rule set   ordered list of rules (Sec. 1, list-based grammar): the first rule that fires gives
@@ -91,8 +91,8 @@ rs_status rs_check(rs_ctx *ctx, void *stream);
 #define RS_MEM_DEVICE 1          /* arrays are device memory of the context's device */
 
 /*
- * Register a dataset (Sec. 3: "GPU experiments loading candidates" -- the data stays resident
- * while any number of populations is evaluated against it).
+ * Register a dataset (Sec. 3: the candidates are evaluated on the GPU against data loaded there;
+ * here the data stays resident while any number of populations is evaluated against it).
  *   X      float32, row-major N x F (sample n, feature f at X[n*F + f]); host or device per `mem`
  *   y      int32[N], labels in 0..K-1
  *   N >= 1, 1 <= F <= RS_MAX_FEATURES, 1 <= K <= RS_MAX_CLASSES
@@ -170,7 +170,8 @@ rs_status rs_eval_hard(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t 
 /* ------------------------------------------------------------------------- soft evaluation */
 
 /*
- * Sigmoid-relaxed forward (Sec. 3, "a differentiable activation function (e.g., sigmoid)").
+ * Sigmoid-relaxed forward (Sec. 3: a sigmoid replaces the hard activation to make evaluation
+ * differentiable).
  * Per condition u = s*(a*x[f] - rhs)/tau with s = +1 for '>' and -1 for '<', rhs = t or b*x[g];
  * rule firing probability q_r = prod_c sigmoid(u_c); rule r decides with probability
  * q_r * prod_{j<r} (1 - q_j); the default class takes prod_j (1 - q_j);

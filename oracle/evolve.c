@@ -12,7 +12,7 @@
  *      position j that B also has takes B's rule with probability 1/2 (uniform rule-list
  *      crossover);
  *   3. with probability 9/10 one mutation, chosen uniformly among: new random coefficients of a
- *      condition (the "randomized coefficients" of Sec. 3), a new feature for a condition, flipped
+ *      condition (offspring with coefficients drawn at random, Sec. 3), a new feature for a condition, flipped
  *      comparison, add a condition, delete a condition, add a random rule, delete a rule, new class
  *      of a rule. A threshold is drawn as t = fl32(a * x[n][f]) for a uniformly drawn sample n
  *      (an empirical quantile of feature f); a new condition is a feature pair with probability
