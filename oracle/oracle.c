@@ -187,7 +187,7 @@ static double margin(const orc_batch *b, int64_t c, const float *xrow, double ta
  *   probs[(p*N+n)*K+k] (optional) = p_k(n)
  *   If dloss != NULL: grad_{a,b,t}[c] = dloss[p] * dloss_p/dtheta_c, and (optional) mag_{a,b,t}[c]
  *   = |dloss[p]| * (1/N) sum_n |d ell_n / d theta_c|, the scale against which float32 round-off of
- *   a cancelling sum over samples is judged.
+ *   a cancelling sum over samples is measured.
  */
 int orc_soft(const float *X, int64_t N, int32_t F, const int32_t *y, int32_t K,
              const orc_batch *b, double tau, double *loss, double *probs,

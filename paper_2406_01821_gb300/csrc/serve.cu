@@ -403,7 +403,7 @@ struct Server {
     std::vector<int> free_slots;
     cudaStream_t sstream = nullptr, kstream = nullptr;
     // request memory: a pool of the server's own that keeps what it has mapped (up to the budget),
-    // so that admissions do not wait for the driver to map memory again
+    // so that admissions do not wait for the CUDA driver to map memory again
     cudaMemPool_t pool = nullptr;
     cudaEvent_t kevent = nullptr;
     bool kernel_live = false;
