@@ -1,5 +1,6 @@
 // extern "C" entry points declared in include/rs.h. Every function converts exceptions and CUDA
 // errors into rs_status and never lets a C++ exception cross the boundary.
+#include <nvtx3/nvToolsExt.h>
 #include <new>
 
 #include "rs_internal.cuh"
@@ -40,8 +41,15 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
 
 using namespace rs;
 
+// Every entry point is an NVTX range named after it (no cost unless a profiler attaches).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 #define RS_GUARD(...)                                                    \
     try {                                                                \
+        NvtxRange nvtx_range_(__func__);                                 \
         __VA_ARGS__                                                      \
     } catch (const std::bad_alloc &) {                                   \
         set_error("host allocation failed");                             \
