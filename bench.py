@@ -144,7 +144,7 @@ def profiled_counters():
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def cpu_baseline(w, n_sample: int, threads: int = 0):
+def cpu_baseline(w, n_sample: int, threads: int = 0, single_thread: bool = False):
     import oracle
     Xs, ys = w.X[:n_sample], w.y[:n_sample]
     nt = oracle.num_threads(threads)
@@ -153,9 +153,17 @@ def cpu_baseline(w, n_sample: int, threads: int = 0):
     oracle.eval_hard(Xs, ys, w.K, w.batch, nthreads=nt)
     dt = time.perf_counter() - t0
     v = w.batch.nominal_conditions() * n_sample / dt
-    return {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle",
-            "sample": f"all {w.batch.P} sets on the first {n_sample} of {w.N} samples "
-                      f"({dt:.2f} s wall, OpenMP over sets)"}
+    out = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle",
+           "sample": f"all {w.batch.P} sets on the first {n_sample} of {w.N} samples "
+                     f"({dt:.2f} s wall, OpenMP over sets)"}
+    if single_thread and nt > 1:        # the same oracle on one core, on a sample a sixteenth the size
+        n1 = max(256, n_sample // 16)
+        t0 = time.perf_counter()
+        oracle.eval_hard(Xs[:n1], ys[:n1], w.K, w.batch, nthreads=1)
+        d1 = time.perf_counter() - t0
+        out["single_thread"] = {"value": w.batch.nominal_conditions() * n1 / d1, "cores": 1,
+                                "sample": f"all {w.batch.P} sets on the first {n1} samples ({d1:.2f} s wall)"}
+    return out
 
 
 # ----------------------------------------------------------------------------- legs
@@ -324,6 +332,37 @@ def categorical_leg(args, dev):
             "kernel_ms": prof["hard_ms"] / max(1, prof["hard_launches"]),
             "cpu_baseline": {"value": b.nominal_conditions() * n_s / dt, "unit": UNIT, "cores": nt,
                              "kind": "oracle", "sample": f"all {P} sets on the first {n_s} samples ({dt:.2f} s)"}}
+
+
+def plain_leg(args, dev):
+    """The paper's experiment shape (569 samples x 30 features, 64 sets x 8 rules x 1..3
+    conditions): launch-bound, so reported as time per call and evaluations per second, with no
+    roofline fraction."""
+    import torch
+    from paper_2406_01821_gb300 import rs, synth
+    w = synth.plain_hard(seed=0)
+    ctx = rs.Context(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ds = ctx.dataset(w.X, w.y, w.K)
+    db = rs.DeviceBatch.from_host(w.batch, device=f"cuda:{dev}")
+    P, K = w.batch.P, w.K
+    out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty((P, K), dtype=torch.int32, device=dev), None)
+    for _ in range(20):
+        ctx.eval_hard(ds, db, K, out=out, stream=stream)
+    stream.synchronize()
+    reps = 200
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.eval_hard(ds, db, K, out=out, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    ctx.close()
+    return {"workload": w.name, "us_per_call": us, "condition_evals_per_s": w.nominal_cond_evals() / (us * 1e-6),
+            "rule_set_samples_per_s": P * w.N / (us * 1e-6), "calls": reps,
+            "note": "launch-bound (pack + validate + evaluate in one captured graph per call); no roofline fraction"}
 
 
 def soft_transcendentals(batch, N):
@@ -602,7 +641,7 @@ def main():
                          "P=256) are the cases used for ncu captures")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="force a tile configuration id")
-    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving,categorical)")
+    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving,categorical,plain)")
     ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -649,7 +688,7 @@ def main():
     extras = {}
     if not args.no_extras and d.rank == 0:
         for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("serving", serving_leg),
-                          ("categorical", categorical_leg)):
+                          ("categorical", categorical_leg), ("plain", plain_leg)):
             if name in args.skip:
                 continue
             try:
@@ -658,7 +697,7 @@ def main():
                 extras[name] = {"error": repr(e)}
 
     if d.rank == 0:
-        cb = cpu_baseline(w, args.cpu_sample)
+        cb = cpu_baseline(w, args.cpu_sample, single_thread=True)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,

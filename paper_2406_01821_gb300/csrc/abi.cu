@@ -34,6 +34,14 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
 rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, float *pb, float *pt,
                        float tau, float lr, int steps, float *loss_trace, cudaStream_t s);
 void set_injected_alloc_failures(int32_t skip, int32_t count);
+void preload_hard_kernels();
+void preload_hard2_kernels();
+void preload_hard4_kernels();
+void preload_hard5_kernels();
+void preload_pack_kernels();
+void preload_soft_kernels();
+void preload_serve_kernels();
+void preload_dataset_kernels();
 rs_status selftest_bounded_wait(Ctx *ctx, int64_t limit_ns, cudaStream_t stream);
 rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
                            int32_t *per_class, int32_t *preds, cudaStream_t stream);
@@ -108,6 +116,17 @@ rs_status rs_create(const rs_config *cfg, rs_ctx **out)
             uint64_t thr = UINT64_MAX;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
+        cudaGetLastError();
+        // load every kernel now rather than at the first launch that needs it (lazy loading would
+        // put that cost on the first requests)
+        preload_dataset_kernels();
+        preload_pack_kernels();
+        preload_hard_kernels();
+        preload_hard2_kernels();
+        preload_hard4_kernels();
+        preload_hard5_kernels();
+        preload_soft_kernels();
+        preload_serve_kernels();
         cudaGetLastError();
         if (!(ctx->flags & RS_CTX_NO_AUTOTUNE)) load_tune_table(ctx);
         *out = ctx;

@@ -345,4 +345,20 @@ int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P)
     return (int)g;
 }
 
+// Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
+// otherwise land on the first request that needs it).
+void preload_hard_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_hard<4, 8>);
+    cudaFuncGetAttributes(&fa, k_hard<4, 4>);
+    cudaFuncGetAttributes(&fa, k_hard<4, 16>);
+    cudaFuncGetAttributes(&fa, k_hard<2, 8>);
+    cudaFuncGetAttributes(&fa, k_hard<2, 16>);
+    cudaFuncGetAttributes(&fa, k_hard<1, 16>);
+    cudaFuncGetAttributes(&fa, k_hard<8, 8>);
+    cudaFuncGetAttributes(&fa, k_hard<8, 4>);
+    cudaFuncGetAttributes(&fa, k_hard<4, 8, true>);
+}
+
 }  // namespace rs

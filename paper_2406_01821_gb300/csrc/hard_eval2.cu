@@ -295,4 +295,19 @@ rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, bool mm, const HardA
     return RS_ERR_INVALID;
 }
 
+// Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
+// otherwise land on the first request that needs it).
+void preload_hard2_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_hard2<4, 8, false>);
+    cudaFuncGetAttributes(&fa, k_hard2<4, 16, false>);
+    cudaFuncGetAttributes(&fa, k_hard2<2, 16, false>);
+    cudaFuncGetAttributes(&fa, k_hard2<4, 8, true>);
+    cudaFuncGetAttributes(&fa, k_hard2<4, 16, true>);
+    cudaFuncGetAttributes(&fa, k_hard2<2, 16, true>);
+    cudaFuncGetAttributes(&fa, k_hard2<2, 32, true>);
+    cudaFuncGetAttributes(&fa, k_hard2<4, 32, true>);
+}
+
 }  // namespace rs

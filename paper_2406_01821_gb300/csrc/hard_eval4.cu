@@ -142,4 +142,16 @@ rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, c
     return RS_ERR_INVALID;
 }
 
+// Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
+// otherwise land on the first request that needs it).
+void preload_hard4_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_hard4<4, 8>);
+    cudaFuncGetAttributes(&fa, k_hard4<4, 16>);
+    cudaFuncGetAttributes(&fa, k_hard4<4, 32>);
+    cudaFuncGetAttributes(&fa, k_hard4<2, 16>);
+    cudaFuncGetAttributes(&fa, k_hard4<2, 32>);
+}
+
 }  // namespace rs

@@ -160,4 +160,15 @@ rs_status launch_hard5(Ctx *ctx, Dataset *ds, int W, const HardArgs &a, cudaStre
     return RS_ERR_INVALID;
 }
 
+// Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
+// otherwise land on the first request that needs it).
+void preload_hard5_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_hard5<16, false>);
+    cudaFuncGetAttributes(&fa, k_hard5<16, true>);
+    cudaFuncGetAttributes(&fa, k_hard5<32, false>);
+    cudaFuncGetAttributes(&fa, k_hard5<32, true>);
+}
+
 }  // namespace rs

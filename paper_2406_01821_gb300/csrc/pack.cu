@@ -399,4 +399,16 @@ rs_status selftest_rewrite(const float *a_h, const float *t_h, const int8_t *op_
     return RS_OK;
 }
 
+// Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
+// otherwise land on the first request that needs it).
+void preload_pack_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_pack_rules);
+    cudaFuncGetAttributes(&fa, k_pack_rules2);
+    cudaFuncGetAttributes(&fa, k_pack_rules5);
+    cudaFuncGetAttributes(&fa, k_pack_sets);
+    cudaFuncGetAttributes(&fa, k_order);
+}
+
 }  // namespace rs

@@ -529,4 +529,19 @@ rs_status dataset_destroy(Ctx *ctx, uint64_t h)
     return RS_OK;
 }
 
+// Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
+// otherwise land on the first request that needs it).
+void preload_dataset_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_label_rank);
+    cudaFuncGetAttributes(&fa, k_label_offsets);
+    cudaFuncGetAttributes(&fa, k_class_start);
+    cudaFuncGetAttributes(&fa, k_label_scatter);
+    cudaFuncGetAttributes(&fa, k_transpose_gather);
+    cudaFuncGetAttributes(&fa, k_nonfinite);
+    cudaFuncGetAttributes(&fa, k_rank_tiles);
+    cudaFuncGetAttributes(&fa, k_fill_i32);
+}
+
 }  // namespace rs

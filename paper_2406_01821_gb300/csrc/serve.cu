@@ -1033,4 +1033,13 @@ rs_status poll_soft(Ctx *ctx, uint64_t ticket, int64_t timeout_us, float *loss, 
     return poll_impl(ctx, ticket, timeout_us, RS_KIND_SOFT, nullptr, nullptr, loss, info);
 }
 
+// Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
+// otherwise land on the first request that needs it).
+void preload_serve_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_serve);
+    cudaFuncGetAttributes(&fa, k_set_claim);
+}
+
 }  // namespace rs

@@ -866,4 +866,24 @@ rs_status soft_step_known(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, cudaS
     return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream);
 }
 
+// Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
+// otherwise land on the first request that needs it).
+void preload_soft_kernels()
+{
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_soft<false, false>);
+    cudaFuncGetAttributes(&fa, k_soft<true, false>);
+    cudaFuncGetAttributes(&fa, k_soft<false, true>);
+    cudaFuncGetAttributes(&fa, k_soft<true, true>);
+    cudaFuncGetAttributes(&fa, k_soft_tile<false, false>);
+    cudaFuncGetAttributes(&fa, k_soft_tile<true, false>);
+    cudaFuncGetAttributes(&fa, k_soft_tile<false, true>);
+    cudaFuncGetAttributes(&fa, k_soft_tile<true, true>);
+    cudaFuncGetAttributes(&fa, k_check_sets_soft);
+    cudaFuncGetAttributes(&fa, k_pack_soft);
+    cudaFuncGetAttributes(&fa, k_soft_order);
+    cudaFuncGetAttributes(&fa, k_soft_reduce_grad);
+    cudaFuncGetAttributes(&fa, k_soft_reduce_loss);
+}
+
 }  // namespace rs
