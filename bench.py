@@ -362,7 +362,7 @@ def plain_leg(args, dev):
     ctx.close()
     return {"workload": w.name, "us_per_call": us, "condition_evals_per_s": w.nominal_cond_evals() / (us * 1e-6),
             "rule_set_samples_per_s": P * w.N / (us * 1e-6), "calls": reps,
-            "note": "launch-bound (pack + validate + evaluate in one captured graph per call); no roofline fraction"}
+            "note": "launch-bound (pack + validate + evaluate: one cached graph replayed per call); no roofline fraction"}
 
 
 def soft_transcendentals(batch, N):

@@ -41,40 +41,61 @@ struct StagedBatch {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static rs_status stage_batch(const rs_batch *b, cudaStream_t stream, StagedBatch &out)
+// Byte offsets of the eleven arrays of a host batch inside one staging buffer; returns its size.
+static size_t staging_layout(const rs_batch *b, size_t off[11], size_t sz[11])
 {
-    out.d.P = b->P; out.d.R = b->R; out.d.C = b->C;
-    if (b->mem == RS_MEM_DEVICE) {
-        out.d.set_rule_off = b->set_rule_off; out.d.rule_cond_off = b->rule_cond_off;
-        out.d.rule_class = b->rule_class; out.d.set_default = b->set_default;
-        out.d.cond_f = b->cond_f; out.d.cond_g = b->cond_g; out.d.cond_op = b->cond_op;
-        out.d.cond_a = b->cond_a; out.d.cond_b = b->cond_b; out.d.cond_t = b->cond_t;
-        out.d.cond_set = b->cond_set;
-        return RS_OK;
-    }
     const size_t P = b->P, R = b->R, C = b->C;
     const size_t cs = b->cond_set ? 8 * C : 0;
-    size_t off[11], sz[11] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C, cs};
+    const size_t s[11] = {4 * (P + 1), 4 * (R + 1), 4 * R, 4 * P, 4 * C, 4 * C, C, 4 * C, 4 * C, 4 * C, cs};
+    size_t total = 0;
+    for (int i = 0; i < 11; ++i) { sz[i] = s[i]; off[i] = total; total = align_up(total + s[i], 256); }
+    return std::max<size_t>(total, 256);
+}
+
+// Copy a host batch into a staging buffer laid out by staging_layout (stream-ordered).
+static rs_status stage_into(const rs_batch *b, char *base, cudaStream_t stream, BatchDev &d)
+{
+    size_t off[11], sz[11];
+    staging_layout(b, off, sz);
     const void *src[11] = {b->set_rule_off, b->rule_cond_off, b->rule_class, b->set_default,
                            b->cond_f, b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t, b->cond_set};
-    size_t total = 0;
-    for (int i = 0; i < 11; ++i) { off[i] = total; total = align_up(total + sz[i], 256); }
-    RS_CUDA(dev_alloc_async(&out.buf, std::max<size_t>(total, 256), stream));
-    char *base = static_cast<char *>(out.buf);
     for (int i = 0; i < 11; ++i)
         if (sz[i]) RS_CUDA(cudaMemcpyAsync(base + off[i], src[i], sz[i], cudaMemcpyHostToDevice, stream));
-    out.d.set_rule_off = (const int32_t *)(base + off[0]);
-    out.d.rule_cond_off = (const int32_t *)(base + off[1]);
-    out.d.rule_class = (const int32_t *)(base + off[2]);
-    out.d.set_default = (const int32_t *)(base + off[3]);
-    out.d.cond_f = (const int32_t *)(base + off[4]);
-    out.d.cond_g = (const int32_t *)(base + off[5]);
-    out.d.cond_op = (const int8_t *)(base + off[6]);
-    out.d.cond_a = (const float *)(base + off[7]);
-    out.d.cond_b = (const float *)(base + off[8]);
-    out.d.cond_t = (const float *)(base + off[9]);
-    out.d.cond_set = b->cond_set ? (const uint64_t *)(base + off[10]) : nullptr;
+    d.P = b->P; d.R = b->R; d.C = b->C;
+    d.set_rule_off = (const int32_t *)(base + off[0]);
+    d.rule_cond_off = (const int32_t *)(base + off[1]);
+    d.rule_class = (const int32_t *)(base + off[2]);
+    d.set_default = (const int32_t *)(base + off[3]);
+    d.cond_f = (const int32_t *)(base + off[4]);
+    d.cond_g = (const int32_t *)(base + off[5]);
+    d.cond_op = (const int8_t *)(base + off[6]);
+    d.cond_a = (const float *)(base + off[7]);
+    d.cond_b = (const float *)(base + off[8]);
+    d.cond_t = (const float *)(base + off[9]);
+    d.cond_set = b->cond_set ? (const uint64_t *)(base + off[10]) : nullptr;
     return RS_OK;
+}
+
+// The caller's device arrays, unchanged.
+static BatchDev device_view(const rs_batch *b)
+{
+    BatchDev d{};
+    d.P = b->P; d.R = b->R; d.C = b->C;
+    d.set_rule_off = b->set_rule_off; d.rule_cond_off = b->rule_cond_off;
+    d.rule_class = b->rule_class; d.set_default = b->set_default;
+    d.cond_f = b->cond_f; d.cond_g = b->cond_g; d.cond_op = b->cond_op;
+    d.cond_a = b->cond_a; d.cond_b = b->cond_b; d.cond_t = b->cond_t;
+    d.cond_set = b->cond_set;
+    return d;
+}
+
+static rs_status stage_batch(const rs_batch *b, cudaStream_t stream, StagedBatch &out)
+{
+    if (b->mem == RS_MEM_DEVICE) { out.d = device_view(b); return RS_OK; }
+    size_t off[11], sz[11];
+    const size_t total = staging_layout(b, off, sz);
+    RS_CUDA(dev_alloc_async(&out.buf, total, stream));
+    return stage_into(b, static_cast<char *>(out.buf), stream, out.d);
 }
 
 // ------------------------------------------------------------------------ tile configuration
@@ -153,13 +174,17 @@ static void save_tune_table(Ctx *ctx)
 
 // ------------------------------------------------------------------------ the call
 
-static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t N, bool per_class,
-                               bool preds, cudaStream_t stream, Scratch &s)
+// Scratch of one call in one buffer: packed records, set descriptors, evaluation order, the
+// status word, per-(set, class) last rule ends (K <= LAST_END_MAX_K) and, for host outputs,
+// the device copies of the outputs. scratch_layout returns the size; with a base it also
+// fills in the pointers.
+static size_t scratch_layout(const BatchDev &b, bool host_out, int K, int64_t N, bool per_class,
+                             bool preds, char *base, Scratch *s)
 {
-    size_t rec_b = align_up(sizeof(Rec) * std::max(b.C, 1), 256);
-    size_t set_b = align_up(sizeof(SetInfo) * std::max(b.P, 1), 256);
-    size_t ord_b = align_up(sizeof(int32_t) * std::max(b.P, 1), 256);
-    size_t st_b = 256;
+    const size_t rec_b = align_up(sizeof(Rec) * std::max(b.C, 1), 256);
+    const size_t set_b = align_up(sizeof(SetInfo) * std::max(b.P, 1), 256);
+    const size_t ord_b = align_up(sizeof(int32_t) * std::max(b.P, 1), 256);
+    const size_t st_b = 256;
     const size_t le_b = K <= LAST_END_MAX_K ? align_up(sizeof(int32_t) * std::max(b.P, 1) * (size_t)K, 256) : 0;
     size_t out_b = 0;
     if (host_out) {
@@ -167,14 +192,24 @@ static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t 
         if (per_class) out_b += align_up(sizeof(int32_t) * (size_t)b.P * K, 256);
         if (preds) out_b += align_up(sizeof(int32_t) * (size_t)b.P * N, 256);
     }
+    if (base && s) {
+        s->recs = (Rec *)base;
+        s->sets = (SetInfo *)(base + rec_b);
+        s->order = (int32_t *)(base + rec_b + set_b);
+        s->status = (uint32_t *)(base + rec_b + set_b + ord_b);
+        s->last_end = le_b ? (int32_t *)(base + rec_b + set_b + ord_b + st_b) : nullptr;
+        s->out_dev = host_out ? (int32_t *)(base + rec_b + set_b + ord_b + st_b + le_b) : nullptr;
+    }
+    return rec_b + set_b + ord_b + st_b + le_b + out_b;
+}
+
+static rs_status alloc_scratch(const BatchDev &b, bool host_out, int K, int64_t N, bool per_class,
+                               bool preds, cudaStream_t stream, Scratch &s)
+{
     char *base = nullptr;
-    RS_CUDA(dev_alloc_async(&base, rec_b + set_b + ord_b + st_b + le_b + out_b, stream));
-    s.recs = (Rec *)base;
-    s.sets = (SetInfo *)(base + rec_b);
-    s.order = (int32_t *)(base + rec_b + set_b);
-    s.status = (uint32_t *)(base + rec_b + set_b + ord_b);
-    s.last_end = le_b ? (int32_t *)(base + rec_b + set_b + ord_b + st_b) : nullptr;
-    s.out_dev = host_out ? (int32_t *)(base + rec_b + set_b + ord_b + st_b + le_b) : nullptr;
+    const size_t bytes = scratch_layout(b, host_out, K, N, per_class, preds, nullptr, nullptr);
+    RS_CUDA(dev_alloc_async(&base, bytes, stream));
+    scratch_layout(b, host_out, K, N, per_class, preds, base, &s);
     RS_CUDA(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream));
     return RS_OK;
 }
@@ -226,16 +261,171 @@ rs_status enqueue_hard_dev_sizes(Ctx *ctx, Dataset *ds, const TileConfig &tc, Ba
     return enqueue_hard(ctx, ds, tc, bd, s, correct, per_class, preds, stream);
 }
 
+// A cached executable graph for one call shape (dataset, tile, stream, output kinds) with the
+// staging and scratch buffers it was captured against. A call whose pointers and sizes equal
+// those of the last capture launches it as it is; any other call captures again and updates
+// the executable in place (same topology) or instantiates it anew. The buffers only grow and
+// are released with the entry (dataset destroyed or context closed). One call at a time runs
+// on an entry (its mutex), so calls on one stream from several host threads stay correct.
 struct GraphEntry {
+    std::mutex mu;
     cudaGraphExec_t exec = nullptr;
-    ~GraphEntry() { if (exec) cudaGraphExecDestroy(exec); }
+    int kernels = 0;                 // kernel nodes of the executable (launch accounting on replay)
+    char *stage = nullptr;           // host batches: device copy of the eleven arrays
+    size_t stage_cap = 0;
+    char *scratch = nullptr;
+    size_t scratch_cap = 0;
+    // the arguments the executable was captured with
+    BatchDev bd{};
+    const int32_t *correct = nullptr, *per_class = nullptr, *preds = nullptr;
+    const char *scratch_at = nullptr;
+    ~GraphEntry()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (stage) cudaFree(stage);
+        if (scratch) cudaFree(scratch);
+    }
 };
+
+static bool same_batch(const BatchDev &a, const BatchDev &b)
+{
+    return a.P == b.P && a.R == b.R && a.C == b.C && a.dR == b.dR && a.dC == b.dC &&
+           a.set_rule_off == b.set_rule_off && a.rule_cond_off == b.rule_cond_off &&
+           a.rule_class == b.rule_class && a.set_default == b.set_default && a.cond_f == b.cond_f &&
+           a.cond_g == b.cond_g && a.cond_op == b.cond_op && a.cond_a == b.cond_a &&
+           a.cond_b == b.cond_b && a.cond_t == b.cond_t && a.cond_set == b.cond_set;
+}
+
+// Grow a buffer owned by a graph entry to at least `need` bytes. cudaFree of the old buffer
+// waits for the device, so work still reading it (asynchronous contexts) has finished.
+static rs_status grow_buffer(char *&p, size_t &cap, size_t need)
+{
+    if (need <= cap) return RS_OK;
+    if (p) { RS_CUDA(cudaFree(p)); p = nullptr; cap = 0; }
+    need = align_up(need + need / 8, 4096);   // headroom: a slowly growing batch does not re-allocate every call
+    if (take_injected_alloc_failure()) return cuda_fail(cudaErrorMemoryAllocation, "cudaMalloc");
+    RS_CUDA(cudaMalloc(&p, need));
+    cap = need;
+    return RS_OK;
+}
+
+static int kernel_nodes(cudaGraph_t g)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
 
 rs_status finish_status(Ctx *ctx, const uint32_t *d_status, cudaStream_t stream);
 
 __global__ void k_merge_status(const uint32_t *src, uint32_t *dst)
 {
     if (*src) atomicOr(dst, *src);
+}
+
+static rs_status copy_outputs_to_host(const rs_batch *b, const Dataset &ds, int32_t *correct,
+                                      int32_t *per_class, int32_t *preds, const int32_t *d_correct,
+                                      const int32_t *d_pc, const int32_t *d_preds, cudaStream_t stream)
+{
+    RS_CUDA(cudaMemcpyAsync(correct, d_correct, sizeof(int32_t) * b->P, cudaMemcpyDeviceToHost, stream));
+    if (per_class)
+        RS_CUDA(cudaMemcpyAsync(per_class, d_pc, sizeof(int32_t) * (size_t)b->P * ds.K,
+                                cudaMemcpyDeviceToHost, stream));
+    if (preds)
+        RS_CUDA(cudaMemcpyAsync(preds, d_preds, sizeof(int32_t) * (size_t)b->P * ds.N,
+                                cudaMemcpyDeviceToHost, stream));
+    return RS_OK;
+}
+
+// Device output pointers of a call: the caller's, or (host outputs) the scratch copies.
+static void device_outputs(const Scratch &s, const rs_batch *b, const Dataset &ds, bool host,
+                           int32_t *&d_correct, int32_t *&d_pc, int32_t *&d_preds)
+{
+    if (!host) return;
+    d_correct = s.out_dev;
+    char *p = (char *)(s.out_dev) + align_up(sizeof(int32_t) * b->P, 256);
+    if (d_pc) { d_pc = (int32_t *)p; p += align_up(sizeof(int32_t) * (size_t)b->P * ds.K, 256); }
+    if (d_preds) d_preds = (int32_t *)p;
+}
+
+// The graph path of eval_hard: staging and scratch live in the cached entry, and a call with
+// the same arguments as the last capture is a single graph launch.
+static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, const rs_batch *b,
+                                 int32_t *correct, int32_t *per_class, int32_t *preds,
+                                 cudaStream_t stream)
+{
+    const bool host = b->mem == RS_MEM_HOST;
+    std::ostringstream key;
+    key << "ds" << ds_h << "|t" << tid << "|s" << (uintptr_t)stream << "|pc" << (per_class != nullptr)
+        << "|pr" << (preds != nullptr) << "|P" << (b->P > 0) << "|R" << (b->R > 0)
+        << "|cat" << (b->cond_set != nullptr) << "|h" << host;
+    std::shared_ptr<GraphEntry> ge;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto &slot = ctx->graphs[key.str()];
+        if (!slot) slot = std::make_shared<GraphEntry>();
+        ge = slot;
+    }
+    std::lock_guard<std::mutex> call(ge->mu);
+    rs_status rc;
+    BatchDev bd;
+    if (host) {
+        size_t off[11], sz[11];
+        if ((rc = grow_buffer(ge->stage, ge->stage_cap, staging_layout(b, off, sz)))) return rc;
+        if ((rc = stage_into(b, ge->stage, stream, bd))) return rc;
+    } else {
+        bd = device_view(b);
+    }
+    const bool pc = per_class != nullptr, pr = preds != nullptr;
+    if ((rc = grow_buffer(ge->scratch, ge->scratch_cap, scratch_layout(bd, host, ds->K, ds->N, pc, pr, nullptr, nullptr))))
+        return rc;
+    Scratch s;
+    scratch_layout(bd, host, ds->K, ds->N, pc, pr, ge->scratch, &s);
+    RS_CUDA(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream));
+    int32_t *d_correct = correct, *d_pc = per_class, *d_preds = preds;
+    device_outputs(s, b, *ds, host, d_correct, d_pc, d_preds);
+
+    const bool same = ge->exec && same_batch(ge->bd, bd) && ge->correct == d_correct &&
+                      ge->per_class == d_pc && ge->preds == d_preds && ge->scratch_at == ge->scratch;
+    if (same) {
+        RS_CUDA(cudaGraphLaunch(ge->exec, stream));
+        count_launch(ctx, ge->kernels);
+    } else {
+        cudaGraph_t g = nullptr;
+        RS_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        rs_status erc = enqueue_hard(ctx, ds, tile_config(tid), bd, s, d_correct, d_pc, d_preds, stream);
+        cudaError_t ce = cudaStreamEndCapture(stream, &g);
+        if (erc) { if (g) cudaGraphDestroy(g); return erc; }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        bool ok = false;
+        if (ge->exec) {
+            cudaGraphExecUpdateResultInfo info;
+            ok = cudaGraphExecUpdate(ge->exec, g, &info) == cudaSuccess;
+            if (!ok) cudaGetLastError();
+        }
+        if (!ok) {
+            if (ge->exec) { cudaGraphExecDestroy(ge->exec); ge->exec = nullptr; }
+            cudaError_t ie = cudaGraphInstantiate(&ge->exec, g, 0);
+            if (ie != cudaSuccess) { ge->exec = nullptr; cudaGraphDestroy(g); return cuda_fail(ie, "cudaGraphInstantiate"); }
+        }
+        ge->kernels = kernel_nodes(g);
+        cudaGraphDestroy(g);
+        // remember the arguments only once the executable holds them
+        ge->bd = bd;
+        ge->correct = d_correct; ge->per_class = d_pc; ge->preds = d_preds;
+        ge->scratch_at = ge->scratch;
+        RS_CUDA(cudaGraphLaunch(ge->exec, stream));
+    }
+    if (host && (rc = copy_outputs_to_host(b, *ds, correct, per_class, preds, d_correct, d_pc, d_preds, stream)))
+        return rc;
+    return finish_status(ctx, s.status, stream);
 }
 
 rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
@@ -249,6 +439,15 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
     if ((rc = device_guard(ctx))) return rc;
     if (b->R > 0 && ds->K > 4096) return RS_ERR_UNSUPPORTED;
 
+    const int tid = tile_override >= 0 ? tile_override : pick_tile(ctx, *ds, b);
+    // Graph replay needs a capturable stream: not the legacy default stream, and not a stream the
+    // caller is capturing already (then the work simply joins the caller's graph).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (stream) RS_CUDA(cudaStreamIsCapturing(stream, &cap));
+    const bool use_graph = !(ctx->flags & (RS_CTX_NO_GRAPH | RS_CTX_PROFILE)) && tile_override < 0 &&
+                           stream != nullptr && cap == cudaStreamCaptureStatusNone;
+    if (use_graph) return eval_hard_graph(ctx, ds_h, ds.get(), tid, b, correct, per_class, preds, stream);
+
     const bool host = b->mem == RS_MEM_HOST;
     StagedBatch sb;
     if ((rc = stage_batch(b, stream, sb))) return rc;
@@ -258,68 +457,10 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
         return rc;
     }
     int32_t *d_correct = correct, *d_pc = per_class, *d_preds = preds;
-    if (host) {
-        d_correct = s.out_dev;
-        char *p = (char *)(s.out_dev) + align_up(sizeof(int32_t) * b->P, 256);
-        if (per_class) { d_pc = (int32_t *)p; p += align_up(sizeof(int32_t) * (size_t)b->P * ds->K, 256); }
-        if (preds) d_preds = (int32_t *)p;
-    }
-    const int tid = tile_override >= 0 ? tile_override : pick_tile(ctx, *ds, b);
-    const TileConfig &tc = tile_config(tid);
-
-    // Graph replay needs a capturable stream: not the legacy default stream, and not a stream the
-    // caller is capturing already (then the work simply joins the caller's graph).
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (stream) RS_CUDA(cudaStreamIsCapturing(stream, &cap));
-    const bool use_graph = !(ctx->flags & (RS_CTX_NO_GRAPH | RS_CTX_PROFILE)) && tile_override < 0 &&
-                           stream != nullptr &&
-                           cap == cudaStreamCaptureStatusNone;
-    if (use_graph) {
-        // Capture pack + evaluate, then update the cached executable for this shape bucket
-        // (same topology -> in-place parameter update; otherwise re-instantiate).
-        std::ostringstream key;
-        key << "ds" << ds_h << "|t" << tid << "|s" << (uintptr_t)stream << "|pc" << (per_class != nullptr)
-            << "|pr" << (preds != nullptr) << "|P" << (b->P > 0) << "|R" << (b->R > 0)
-            << "|cat" << (b->cond_set != nullptr);
-        cudaGraph_t g = nullptr;
-        RS_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        rs_status erc = enqueue_hard(ctx, ds.get(), tc, sb.d, s, d_correct, d_pc, d_preds, stream);
-        cudaError_t ce = cudaStreamEndCapture(stream, &g);
-        if (erc) { if (g) cudaGraphDestroy(g); return erc; }
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-        std::shared_ptr<GraphEntry> ge;
-        {
-            std::lock_guard<std::mutex> lk(ctx->mu);
-            auto &slot = ctx->graphs[key.str()];
-            if (!slot) slot = std::make_shared<GraphEntry>();
-            ge = slot;
-        }
-        bool ok = false;
-        if (ge->exec) {
-            cudaGraphExecUpdateResultInfo info;
-            ok = cudaGraphExecUpdate(ge->exec, g, &info) == cudaSuccess;
-            if (!ok) cudaGetLastError();
-        }
-        if (!ok) {
-            if (ge->exec) { cudaGraphExecDestroy(ge->exec); ge->exec = nullptr; }
-            cudaError_t ie = cudaGraphInstantiate(&ge->exec, g, 0);
-            if (ie != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ie, "cudaGraphInstantiate"); }
-        }
-        cudaGraphDestroy(g);
-        RS_CUDA(cudaGraphLaunch(ge->exec, stream));
-    } else {
-        if ((rc = enqueue_hard(ctx, ds.get(), tc, sb.d, s, d_correct, d_pc, d_preds, stream))) return rc;
-    }
-    if (host) {
-        RS_CUDA(cudaMemcpyAsync(correct, d_correct, sizeof(int32_t) * b->P, cudaMemcpyDeviceToHost, stream));
-        if (per_class)
-            RS_CUDA(cudaMemcpyAsync(per_class, d_pc, sizeof(int32_t) * (size_t)b->P * ds->K,
-                                    cudaMemcpyDeviceToHost, stream));
-        if (preds)
-            RS_CUDA(cudaMemcpyAsync(preds, d_preds, sizeof(int32_t) * (size_t)b->P * ds->N,
-                                    cudaMemcpyDeviceToHost, stream));
-    }
-    rc = finish_status(ctx, s.status, stream);
+    device_outputs(s, b, *ds, host, d_correct, d_pc, d_preds);
+    rc = enqueue_hard(ctx, ds.get(), tile_config(tid), sb.d, s, d_correct, d_pc, d_preds, stream);
+    if (!rc && host) rc = copy_outputs_to_host(b, *ds, correct, per_class, preds, d_correct, d_pc, d_preds, stream);
+    if (!rc) rc = finish_status(ctx, s.status, stream);
     cudaFreeAsync(s.recs, stream);
     if (sb.buf) cudaFreeAsync(sb.buf, stream);
     return rc;

@@ -398,3 +398,53 @@ def test_maximum_sizes(ctx, orc):
     with pytest.raises(rs.RsError) as ei:
         run_gpu(ctx, X, y, 2, b, preds=False)
     assert ei.value.code == -2                     # RS_ERR_TOO_LARGE
+
+
+def test_graph_replay_reads_current_contents(ctx, orc):
+    """A call whose pointers and sizes equal the previous call's on the same stream replays the
+    cached graph without capturing again; it must still read the batch's current contents (device
+    arrays rewritten in place, host arrays staged again) and write the current outputs. Then a
+    batch of another size (captured again) and the first one once more."""
+    import copy
+    import torch
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.gaussian_mixture(7001, 12, 3, 31)
+    K = 3
+    ds = ctx.dataset(X, y, K)
+    s = torch.cuda.Stream()
+    rng = np.random.default_rng(31)
+    b0 = synth.random_rulesets(synth.quantile_table(X), K, 40, (1, 10), (1, 4), 31, pair_prob=0.3)
+    variants = [b0]
+    for _ in range(3):
+        bv = copy.deepcopy(b0)
+        bv.cond_t = rng.permutation(bv.cond_t).astype(np.float32)
+        bv.set_default = rng.integers(0, K, size=b0.P).astype(np.int32)
+        variants.append(bv)
+    try:
+        db = rs.DeviceBatch.from_host(b0)
+        out = (torch.empty(b0.P, dtype=torch.int32, device="cuda"),
+               torch.empty((b0.P, K), dtype=torch.int32, device="cuda"), None)
+        launches = []
+        for bv in variants:                       # device arrays rewritten in place
+            db.t["cond_t"].copy_(torch.from_numpy(bv.cond_t))
+            db.t["set_default"].copy_(torch.from_numpy(bv.set_default))
+            before = ctx.profile()["launches"]
+            with torch.cuda.stream(s):
+                c, pc, _ = ctx.eval_hard(ds, db, K, out=out, stream=s)
+            s.synchronize()
+            launches.append(ctx.profile()["launches"] - before)
+            want = orc.eval_hard(X, y, K, bv)
+            assert np.array_equal(c.cpu().numpy(), want[0])
+            assert np.array_equal(pc.cpu().numpy(), want[1])
+        assert len(set(launches)) == 1 and launches[0] > 0   # a replay counts the kernels it runs
+        for bv in variants:                       # host arrays, host outputs
+            c, pc, _ = ctx.eval_hard(ds, rs.HostBatch(bv), K, stream=s)
+            want = orc.eval_hard(X, y, K, bv)
+            assert np.array_equal(c, want[0]) and np.array_equal(pc, want[1])
+        b1 = synth.random_rulesets(synth.quantile_table(X), K, 9, (1, 30), (1, 6), 32)
+        for bv in (b1, variants[2], b1):          # other sizes: captured again, same entry
+            c, pc, _ = ctx.eval_hard(ds, rs.HostBatch(bv), K, stream=s)
+            want = orc.eval_hard(X, y, K, bv)
+            assert np.array_equal(c, want[0]) and np.array_equal(pc, want[1])
+    finally:
+        ctx.dataset_destroy(ds)
