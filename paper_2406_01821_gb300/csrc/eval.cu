@@ -222,6 +222,8 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc_in, const Bat
     PackOut po;
     po.recs = s.recs; po.sets = s.sets; po.order = s.order; po.status = s.status;
     po.last_end = ds->K <= LAST_END_MAX_K ? s.last_end : nullptr;
+    po.correct = correct;
+    po.per_class = per_class;
     // batches with membership conditions run the forms that evaluate them (rank-coded or v1)
     const TileConfig &tc = bd.cond_set ? categorical_config(tc_in, *ds, preds != nullptr) : tc_in;
     const int ver = effective_version(tc, *ds, preds != nullptr);
@@ -275,6 +277,7 @@ struct GraphEntry {
     size_t stage_cap = 0;
     char *scratch = nullptr;
     size_t scratch_cap = 0;
+    uint32_t *status_host = nullptr; // synchronous contexts: pinned copy of the status word
     // the arguments the executable was captured with
     BatchDev bd{};
     const int32_t *correct = nullptr, *per_class = nullptr, *preds = nullptr;
@@ -284,6 +287,7 @@ struct GraphEntry {
         if (exec) cudaGraphExecDestroy(exec);
         if (stage) cudaFree(stage);
         if (scratch) cudaFree(scratch);
+        if (status_host) cudaFreeHost(status_host);
     }
 };
 
@@ -324,6 +328,7 @@ static int kernel_nodes(cudaGraph_t g)
 }
 
 rs_status finish_status(Ctx *ctx, const uint32_t *d_status, cudaStream_t stream);
+rs_status report_status(uint32_t h);
 
 __global__ void k_merge_status(const uint32_t *src, uint32_t *dst)
 {
@@ -386,9 +391,10 @@ static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, 
     const bool pc = per_class != nullptr, pr = preds != nullptr;
     if ((rc = grow_buffer(ge->scratch, ge->scratch_cap, scratch_layout(bd, host, ds->K, ds->N, pc, pr, nullptr, nullptr))))
         return rc;
+    const bool async = ctx->flags & RS_CTX_ASYNC;
+    if (!async && !ge->status_host) RS_CUDA(cudaHostAlloc(&ge->status_host, sizeof(uint32_t), cudaHostAllocDefault));
     Scratch s;
     scratch_layout(bd, host, ds->K, ds->N, pc, pr, ge->scratch, &s);
-    RS_CUDA(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream));
     int32_t *d_correct = correct, *d_pc = per_class, *d_preds = preds;
     device_outputs(s, b, *ds, host, d_correct, d_pc, d_preds);
 
@@ -398,9 +404,23 @@ static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, 
         RS_CUDA(cudaGraphLaunch(ge->exec, stream));
         count_launch(ctx, ge->kernels);
     } else {
+        // The graph resets the status word, evaluates, and hands the status on: into the
+        // context's sticky word (asynchronous contexts) or into the entry's pinned word.
         cudaGraph_t g = nullptr;
         RS_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        rs_status erc = enqueue_hard(ctx, ds, tile_config(tid), bd, s, d_correct, d_pc, d_preds, stream);
+        rs_status erc = RS_OK;
+        cudaError_t me = cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream);
+        if (me != cudaSuccess) erc = cuda_fail(me, "cudaMemsetAsync");
+        if (!erc) erc = enqueue_hard(ctx, ds, tile_config(tid), bd, s, d_correct, d_pc, d_preds, stream);
+        if (!erc && async) {
+            k_merge_status<<<1, 1, 0, stream>>>(s.status, ctx->d_sticky);
+            me = cudaGetLastError();
+            if (me != cudaSuccess) erc = cuda_fail(me, "k_merge_status");
+            else count_launch(ctx);
+        } else if (!erc) {
+            me = cudaMemcpyAsync(ge->status_host, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+            if (me != cudaSuccess) erc = cuda_fail(me, "cudaMemcpyAsync");
+        }
         cudaError_t ce = cudaStreamEndCapture(stream, &g);
         if (erc) { if (g) cudaGraphDestroy(g); return erc; }
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
@@ -425,7 +445,9 @@ static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, 
     }
     if (host && (rc = copy_outputs_to_host(b, *ds, correct, per_class, preds, d_correct, d_pc, d_preds, stream)))
         return rc;
-    return finish_status(ctx, s.status, stream);
+    if (async) return RS_OK;
+    RS_CUDA(cudaStreamSynchronize(stream));
+    return report_status(*ge->status_host);
 }
 
 rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
@@ -480,12 +502,16 @@ rs_status finish_status(Ctx *ctx, const uint32_t *d_status, cudaStream_t stream)
     if (!hs) return RS_ERR_OOM;
     RS_CUDA(cudaMemcpyAsync(hs, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
     RS_CUDA(cudaStreamSynchronize(stream));
-    if (*hs) {
-        set_error("batch rejected: %s", status_text(*hs).c_str());
-        if (*hs & (ST_WAIT_TIMEOUT | ST_QUEUE_TIMEOUT)) return RS_ERR_TIMEOUT;
-        return (*hs & ST_TOO_LARGE) ? RS_ERR_TOO_LARGE : RS_ERR_INVALID;
-    }
-    return RS_OK;
+    return report_status(*hs);
+}
+
+// The call's result from its device status word (0: accepted).
+rs_status report_status(uint32_t h)
+{
+    if (!h) return RS_OK;
+    set_error("batch rejected: %s", status_text(h).c_str());
+    if (h & (ST_WAIT_TIMEOUT | ST_QUEUE_TIMEOUT)) return RS_ERR_TIMEOUT;
+    return (h & ST_TOO_LARGE) ? RS_ERR_TOO_LARGE : RS_ERR_INVALID;
 }
 
 rs_status check_async(Ctx *ctx, cudaStream_t stream)

@@ -309,9 +309,7 @@ bool tile_config_fits(const TileConfig &tc, int F)
 rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,
                       cudaStream_t stream)
 {
-    if (a.P > 0) RS_CUDA(cudaMemsetAsync(a.correct, 0, sizeof(int32_t) * a.P, stream));
-    if (a.P > 0 && a.per_class)
-        RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
+    // correct and per_class were zeroed by the packing (k_pack_sets), which every call runs first
     if (a.P == 0) return RS_OK;
     const int ver = effective_version(tc, *ds, a.preds != nullptr);
     if (ver == 5) return launch_hard5(ctx, ds, tc.W, a, stream);
@@ -338,8 +336,10 @@ int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P)
     const int64_t want = (int64_t)ctx->sm_count * 4;
     int64_t g = (want + tiles - 1) / tiles;
     if (g < 1) g = 1;
-    // keep >= 2 sets per warp in a group so the dynamic counter can balance within the CTA
-    const int64_t gmax = std::max<int64_t>(1, P / (2 * tc.W));
+    // keep >= 2 sets per warp in a group so the dynamic counter can balance within the CTA, unless
+    // that leaves SMs idle (small launches): then down to one set per warp
+    int64_t gmax = std::max<int64_t>(1, P / (2 * tc.W));
+    if (tiles * gmax < ctx->sm_count) gmax = std::max<int64_t>(1, (P + tc.W - 1) / tc.W);
     if (g > gmax) g = gmax;
     if (g > 65535) g = 65535;
     return (int)g;

@@ -277,9 +277,6 @@ rs_status launch2_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t strea
 rs_status launch_hard2(Ctx *ctx, Dataset *ds, int V, int W, bool mm, const HardArgs &a,
                        cudaStream_t stream)
 {
-    if (a.P > 0) RS_CUDA(cudaMemsetAsync(a.correct, 0, sizeof(int32_t) * a.P, stream));
-    if (a.P > 0 && a.per_class)
-        RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
     if (!mm) {
         if (V == 4 && W == 8) return launch2_t<4, 8, false>(ctx, ds, a, stream);

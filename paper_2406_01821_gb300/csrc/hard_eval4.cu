@@ -130,9 +130,6 @@ rs_status launch4_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_t strea
 
 rs_status launch_hard4(Ctx *ctx, Dataset *ds, int V, int W, const HardArgs &a, cudaStream_t stream)
 {
-    if (a.P > 0) RS_CUDA(cudaMemsetAsync(a.correct, 0, sizeof(int32_t) * a.P, stream));
-    if (a.P > 0 && a.per_class)
-        RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
     if (V == 4 && W == 8) return launch4_t<4, 8>(ctx, ds, a, stream);
     if (V == 4 && W == 16) return launch4_t<4, 16>(ctx, ds, a, stream);

@@ -151,9 +151,6 @@ static rs_status launch5_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_
 
 rs_status launch_hard5(Ctx *ctx, Dataset *ds, int W, const HardArgs &a, cudaStream_t stream)
 {
-    if (a.P > 0) RS_CUDA(cudaMemsetAsync(a.correct, 0, sizeof(int32_t) * a.P, stream));
-    if (a.P > 0 && a.per_class)
-        RS_CUDA(cudaMemsetAsync(a.per_class, 0, sizeof(int32_t) * (size_t)a.P * a.K, stream));
     if (a.P == 0) return RS_OK;
     if (W == 16) return a.cat ? launch5_t<16, true>(ctx, ds, a, stream) : launch5_t<16, false>(ctx, ds, a, stream);
     if (W == 32) return a.cat ? launch5_t<32, true>(ctx, ds, a, stream) : launch5_t<32, false>(ctx, ds, a, stream);

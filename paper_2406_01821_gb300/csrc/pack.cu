@@ -132,18 +132,51 @@ __global__ void k_pack_rules2(BatchDev b, int F, int K, int S, int form, Rec *re
 }
 
 
-// One thread per set: offsets, default class, first empty rule (an empty rule fires for every
-// sample still unclaimed, so the set effectively ends there with that class as its default).
-__global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, int32_t *last_end, uint32_t *status)
+// Order buckets of the counting sort of sets by cost (k_order, and k_pack_sets for one-block batches).
+constexpr int ORDER_BUCKETS = 1024;
+__device__ __forceinline__ int order_bucket(int cost) { return ORDER_BUCKETS - 1 - min(cost, ORDER_BUCKETS - 1); }
+
+// Exclusive prefix sum over the bucket counts in place, by the whole block (blockDim.x a multiple
+// of 32 that divides ORDER_BUCKETS; every thread of the block calls it).
+__device__ void scan_buckets(int *hist)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
-    if (p == 0) {
-        if (b.set_rule_off[0] != 0 || b.set_rule_off[b.P] != b.R ||
-            b.rule_cond_off[0] != 0 || b.rule_cond_off[b.R] != b.C)
-            atomicOr(status, ST_BAD_OFFSETS);
+    __shared__ int warp_sums[32];
+    const int per = ORDER_BUCKETS / blockDim.x;
+    const int base = threadIdx.x * per;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int local = 0;
+    for (int i = 0; i < per; ++i) local += hist[base + i];
+    int x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
     }
-    if (p >= b.P) return;
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int w = lane < nw ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int run = x - local + (warp ? warp_sums[warp - 1] : 0);
+    for (int i = 0; i < per; ++i) {
+        const int h = hist[base + i];
+        hist[base + i] = run;
+        run += h;
+    }
+    __syncthreads();
+}
+
+// Offsets, default class and first empty rule of set p (an empty rule fires for every sample
+// still unclaimed, so the set effectively ends there with that class as its default). Returns
+// the set's cost (its record count).
+__device__ int pack_one_set(const BatchDev &b, int K, int p, SetInfo *sets, int32_t *last_end, uint32_t *status)
+{
     SetInfo si{0, 0, 0, 0};
     const int rb = b.set_rule_off[p], re = b.set_rule_off[p + 1];
     int d = b.set_default[p];
@@ -152,7 +185,7 @@ __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, int32_t *last_end,
     if (rb < 0 || re < rb || re > b.R) {
         atomicOr(status, ST_BAD_OFFSETS);
         sets[p] = si;
-        return;
+        return 0;
     }
     int c_begin = 0, c_end = 0;
     bool ok = true;
@@ -179,6 +212,36 @@ __global__ void k_pack_sets(BatchDev b, int K, SetInfo *sets, int32_t *last_end,
     si.rec_end = c_end;
     si.cost = c_end - c_begin;
     sets[p] = si;
+    return si.cost;
+}
+
+// One thread per set: the set's descriptor, and zeroed counts (correct[p], per_class[p][*]) when
+// the output pointers are given. With `order_here` (a batch of at most one block) the block also
+// sorts the sets by cost, which otherwise k_order does in a launch of its own.
+__global__ void k_pack_sets(BatchDev b, int K, PackOut o, bool order_here)
+{
+    __shared__ int hist[ORDER_BUCKETS];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
+    if (p == 0) {
+        if (b.set_rule_off[0] != 0 || b.set_rule_off[b.P] != b.R ||
+            b.rule_cond_off[0] != 0 || b.rule_cond_off[b.R] != b.C)
+            atomicOr(o.status, ST_BAD_OFFSETS);
+    }
+    int cost = 0;
+    if (p < b.P) {
+        if (o.correct) o.correct[p] = 0;
+        if (o.per_class)
+            for (int k = 0; k < K; ++k) o.per_class[(int64_t)p * K + k] = 0;
+        cost = pack_one_set(b, K, p, o.sets, o.last_end, o.status);
+    }
+    if (!order_here) return;   // uniform over the launch
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    if (p < b.P) atomicAdd(&hist[order_bucket(cost)], 1);
+    __syncthreads();
+    scan_buckets(hist);
+    if (p < b.P) o.order[atomicAdd(&hist[order_bucket(cost)], 1)] = p;
 }
 
 // Kind of a condition in format v5, decided with the same tests as rewrite_threshold (without its
@@ -307,22 +370,16 @@ __global__ void k_pack_rules(BatchDev b, int F, int K, Rec *recs, uint32_t *stat
 
 // Single-CTA counting sort of sets by cost, most expensive first (bucketed; the order only
 // schedules work, results do not depend on it).
-constexpr int ORDER_BUCKETS = 1024;
 __global__ void k_order(const SetInfo *sets, int P, int32_t *order)
 {
     __shared__ int hist[ORDER_BUCKETS];
     for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    auto bucket = [](int cost) { return ORDER_BUCKETS - 1 - min(cost, ORDER_BUCKETS - 1); };
-    for (int p = threadIdx.x; p < P; p += blockDim.x) atomicAdd(&hist[bucket(sets[p].cost)], 1);
+    for (int p = threadIdx.x; p < P; p += blockDim.x) atomicAdd(&hist[order_bucket(sets[p].cost)], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int i = 0; i < ORDER_BUCKETS; ++i) { int h = hist[i]; hist[i] = run; run += h; }
-    }
-    __syncthreads();
+    scan_buckets(hist);
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        int pos = atomicAdd(&hist[bucket(sets[p].cost)], 1);
+        int pos = atomicAdd(&hist[order_bucket(sets[p].cost)], 1);
         order[pos] = p;
     }
 }
@@ -330,7 +387,9 @@ __global__ void k_order(const SetInfo *sets, int P, int32_t *order)
 int launch_pack(const BatchDev &b, int F, int K, int S, int ver, const PackOut &o, cudaStream_t stream)
 {
     int n = 0;
-    if (b.P > 0) { k_pack_sets<<<(b.P + 255) / 256, 256, 0, stream>>>(b, K, o.sets, o.last_end, o.status); ++n; }
+    constexpr int SET_BLOCK = 256;
+    const bool order_here = o.order && b.P <= SET_BLOCK;
+    if (b.P > 0) { k_pack_sets<<<(b.P + SET_BLOCK - 1) / SET_BLOCK, SET_BLOCK, 0, stream>>>(b, K, o, order_here); ++n; }
     if (b.R > 0 && ver == 5) {
         k_pack_rules5<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status);
         ++n;
@@ -341,7 +400,7 @@ int launch_pack(const BatchDev &b, int F, int K, int S, int ver, const PackOut &
         k_pack_rules<<<(b.R + 127) / 128, 128, 0, stream>>>(b, F, K, o.recs, o.status);
         ++n;
     }
-    if (b.P > 0 && o.order) { k_order<<<1, 1024, 0, stream>>>(o.sets, b.P, o.order); ++n; }
+    if (b.P > 0 && o.order && !order_here) { k_order<<<1, 1024, 0, stream>>>(o.sets, b.P, o.order); ++n; }
     return n;
 }
 

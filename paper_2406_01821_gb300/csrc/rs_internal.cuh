@@ -248,9 +248,12 @@ struct PackOut {
     int32_t *order = nullptr;     // [P] set ids, most expensive first
     uint32_t *status = nullptr;   // device status word
     int32_t *last_end = nullptr;  // [P*K] or null
+    int32_t *correct = nullptr;   // [P] zeroed by the packing when given
+    int32_t *per_class = nullptr; // [P*K] zeroed by the packing when given
 };
 
-// Validate + pack (+ order) a device batch. Enqueued on `stream`.
+// Validate + pack (+ order) a device batch, zeroing the count outputs named in `o`. Enqueued on
+// `stream`.
 // Returns the number of kernels launched.
 int launch_pack(const BatchDev &b, int F, int K, int S, int ver, const PackOut &o, cudaStream_t stream);
 

@@ -782,11 +782,9 @@ static bool try_admit(Server *s, Request &r)
     p += 256;
     po.status = r.d_status;
     if (r.K <= LAST_END_MAX_K) po.last_end = (int32_t *)p;
+    po.correct = r.d_correct;     // zeroed by the packing
+    po.per_class = r.d_pc;
     cudaMemsetAsync(r.d_status, 0, 4, s->sstream);
-    if (r.P > 0) {
-        cudaMemsetAsync(r.d_correct, 0, 4 * (size_t)r.P, s->sstream);
-        cudaMemsetAsync(r.d_pc, 0, 4 * (size_t)r.P * r.K, s->sstream);
-    }
     const bool finite = r.ds->finite;
     const bool ranked = serve_ranked(*r.ds, r.P, r.cat);
     count_launch(s->ctx, launch_pack(bd, r.ds->F, r.K, SS, ranked ? 5 : (finite ? 4 : 2), po, s->sstream));

@@ -184,6 +184,7 @@ def _ptr(t):
 _FIELDS = ("set_rule_off", "rule_cond_off", "rule_class", "set_default", "cond_f", "cond_g",
            "cond_op", "cond_a", "cond_b", "cond_t")
 _DTYPES = {"cond_op": np.int8, "cond_a": np.float32, "cond_b": np.float32, "cond_t": np.float32}
+_ALL_FIELDS = _FIELDS + ("cond_set",)
 
 
 class DeviceBatch:
@@ -194,6 +195,7 @@ class DeviceBatch:
         self.P = int(tensors["set_default"].numel())
         self.R = int(tensors["rule_class"].numel())
         self.C = int(tensors["cond_f"].numel())
+        self._c = None
 
     @classmethod
     def from_host(cls, batch, device="cuda"):
@@ -218,8 +220,13 @@ class DeviceBatch:
         return DeviceBatch(d)
 
     def c(self) -> rs_batch:
-        return rs_batch(self.P, self.R, self.C, MEM_DEVICE, *[_ptr(self.t[f]) for f in _FIELDS],
-                        _ptr(self.t.get("cond_set")))
+        # Building the ctypes structure is most of the host time of a small call, so it is kept
+        # and rebuilt only when an array's address has changed.
+        addrs = tuple(0 if x is None else x.data_ptr() for x in map(self.t.get, _ALL_FIELDS))
+        key = (self.P, self.R, self.C, addrs)
+        if self._c is None or self._c[0] != key:
+            self._c = (key, rs_batch(self.P, self.R, self.C, MEM_DEVICE, *addrs))
+        return self._c[1]
 
 
 class HostBatch:

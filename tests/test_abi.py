@@ -72,3 +72,27 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert rc == -6                                  # RS_ERR_UNSUPPORTED
     assert h.value is None
     assert b"device" in lib.rs_last_error()
+
+
+def test_device_batch_struct_follows_its_arrays():
+    """DeviceBatch keeps its ctypes structure between calls and rebuilds it when an array is
+    replaced or a size changes (CPU tensors stand in for device ones: only addresses are read)."""
+    import numpy as np
+    import torch
+    from paper_2406_01821_gb300 import rs, synth
+    b = synth.random_rulesets(synth.quantile_table(np.random.default_rng(0).normal(size=(50, 4))),
+                              2, 5, 3, 2, 0)
+    t = {f: torch.from_numpy(np.ascontiguousarray(getattr(b, f), rs._DTYPES.get(f, np.int32)))
+         for f in rs._FIELDS}
+    db = rs.DeviceBatch(t)
+    c1 = db.c()
+    assert db.c() is c1
+    assert (c1.P, c1.R, c1.C, c1.mem) == (b.P, b.R, b.C, rs.MEM_DEVICE)
+    assert c1.cond_t == t["cond_t"].data_ptr() and not c1.cond_set
+    t["cond_t"] = t["cond_t"].clone()
+    c2 = db.c()
+    assert c2 is not c1 and c2.cond_t == t["cond_t"].data_ptr()
+    t["cond_set"] = torch.zeros(b.C, dtype=torch.int64)
+    assert db.c().cond_set == t["cond_set"].data_ptr()
+    db.P -= 1
+    assert db.c().P == b.P - 1
