@@ -268,9 +268,12 @@ rs_status enqueue_hard_dev_sizes(Ctx *ctx, Dataset *ds, const TileConfig &tc, Ba
 // those of the last capture launches it as it is; any other call captures again and updates
 // the executable in place (same topology) or instantiates it anew. The buffers only grow and
 // are released with the entry (dataset destroyed or context closed). One call at a time runs
-// on an entry (its mutex), so calls on one stream from several host threads stay correct.
+// on an entry (its mutex), so calls on one stream from several host threads stay correct. The
+// capture runs on a stream of the entry's own, never on the caller's: a stream in capture mode
+// would take in whatever another host thread enqueues on it meanwhile.
 struct GraphEntry {
     std::mutex mu;
+    cudaStream_t capture = nullptr;
     cudaGraphExec_t exec = nullptr;
     int kernels = 0;                 // kernel nodes of the executable (launch accounting on replay)
     char *stage = nullptr;           // host batches: device copy of the eleven arrays
@@ -285,6 +288,7 @@ struct GraphEntry {
     ~GraphEntry()
     {
         if (exec) cudaGraphExecDestroy(exec);
+        if (capture) cudaStreamDestroy(capture);
         if (stage) cudaFree(stage);
         if (scratch) cudaFree(scratch);
         if (status_host) cudaFreeHost(status_host);
@@ -406,22 +410,24 @@ static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, 
     } else {
         // The graph resets the status word, evaluates, and hands the status on: into the
         // context's sticky word (asynchronous contexts) or into the entry's pinned word.
+        if (!ge->capture) RS_CUDA(cudaStreamCreateWithFlags(&ge->capture, cudaStreamNonBlocking));
+        cudaStream_t cs = ge->capture;
         cudaGraph_t g = nullptr;
-        RS_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        RS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         rs_status erc = RS_OK;
-        cudaError_t me = cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream);
+        cudaError_t me = cudaMemsetAsync(s.status, 0, sizeof(uint32_t), cs);
         if (me != cudaSuccess) erc = cuda_fail(me, "cudaMemsetAsync");
-        if (!erc) erc = enqueue_hard(ctx, ds, tile_config(tid), bd, s, d_correct, d_pc, d_preds, stream);
+        if (!erc) erc = enqueue_hard(ctx, ds, tile_config(tid), bd, s, d_correct, d_pc, d_preds, cs);
         if (!erc && async) {
-            k_merge_status<<<1, 1, 0, stream>>>(s.status, ctx->d_sticky);
+            k_merge_status<<<1, 1, 0, cs>>>(s.status, ctx->d_sticky);
             me = cudaGetLastError();
             if (me != cudaSuccess) erc = cuda_fail(me, "k_merge_status");
             else count_launch(ctx);
         } else if (!erc) {
-            me = cudaMemcpyAsync(ge->status_host, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+            me = cudaMemcpyAsync(ge->status_host, s.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs);
             if (me != cudaSuccess) erc = cuda_fail(me, "cudaMemcpyAsync");
         }
-        cudaError_t ce = cudaStreamEndCapture(stream, &g);
+        cudaError_t ce = cudaStreamEndCapture(cs, &g);
         if (erc) { if (g) cudaGraphDestroy(g); return erc; }
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
         bool ok = false;
@@ -462,12 +468,13 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
     if (b->R > 0 && ds->K > 4096) return RS_ERR_UNSUPPORTED;
 
     const int tid = tile_override >= 0 ? tile_override : pick_tile(ctx, *ds, b);
-    // Graph replay needs a capturable stream: not the legacy default stream, and not a stream the
-    // caller is capturing already (then the work simply joins the caller's graph).
+    // The cached graph (captured on a stream of its own, launched on the caller's, the legacy
+    // default stream included) unless the caller is capturing this stream: then the work is
+    // enqueued directly and joins the caller's graph.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (stream) RS_CUDA(cudaStreamIsCapturing(stream, &cap));
     const bool use_graph = !(ctx->flags & (RS_CTX_NO_GRAPH | RS_CTX_PROFILE)) && tile_override < 0 &&
-                           stream != nullptr && cap == cudaStreamCaptureStatusNone;
+                           cap == cudaStreamCaptureStatusNone;
     if (use_graph) return eval_hard_graph(ctx, ds_h, ds.get(), tid, b, correct, per_class, preds, stream);
 
     const bool host = b->mem == RS_MEM_HOST;
