@@ -421,6 +421,73 @@ def evolution_leg(args, dev):
             "cpu_cores": oracle.num_threads(0)}
 
 
+def paper_evolution_leg(args, dev):
+    """The paper's experiment shape (Sec. 4): a population of 100 rule sets (R <= 8, C <= 3) evolved
+    on N=569 x F=30 two-class data for 100 generations, without and with back-propagation
+    fine-tuning of every set each generation (50 Adam steps, Baldwinian selection), on the GPU.
+    The CPU arm does the same work per generation with the oracle on the host cores (hard
+    evaluation and the evolution step; with fine-tuning, per step a float64 soft forward + adjoint
+    of all sets and an Adam update), timed over a few generations. The paper reports the CPU/GPU
+    wall-clock ratio on this shape: at least five-fold on a T4, with and without fine-tuning."""
+    import dataclasses
+    import torch
+    import oracle
+    from paper_2406_01821_gb300 import rs, synth
+    w = synth.plain_hard(seed=0)
+    X, y, K = w.X, w.y, w.K
+    P, RMAX, CMAX, G, STEPS, TAU, LR = 100, 8, 3, 100, 50, 0.1, 1e-2
+    pop = synth.initial_population(X, y, K, P, RMAX, CMAX, seed=0)
+    ctx = rs.Context(dev)
+    ds = ctx.dataset(X, y, K)
+    stream = torch.cuda.Stream(device=dev)
+    tuned = dict(tune_every=1, tune_top=P, tune_steps=STEPS, tau=TAU, lr=LR)
+    ctx.evolve(ds, pop, generations=2, elite=1, seed=1, stream=stream)                # warm-up
+    ctx.evolve(ds, pop, generations=2, elite=1, seed=1, stream=stream, **tuned)
+    t0 = time.perf_counter()
+    ctx.evolve(ds, pop, generations=G, elite=1, seed=1, stream=stream)
+    t_gpu = (time.perf_counter() - t0) / G
+    t0 = time.perf_counter()
+    _, _, best, _ = ctx.evolve(ds, pop, generations=G, elite=1, seed=1, stream=stream, **tuned)
+    t_gpu_tuned = (time.perf_counter() - t0) / G
+    ctx.close()
+
+    def cpu_generations(gens, finetune):
+        cur = pop
+        t0 = time.perf_counter()
+        for g in range(gens):
+            b = synth.batch_from_population(cur)
+            fit, _, _ = oracle.eval_hard(X, y, K, b, want_per_class=False)
+            if finetune:
+                theta = [b.cond_a.astype(np.float64), b.cond_b.astype(np.float64), b.cond_t.astype(np.float64)]
+                m1 = [np.zeros_like(v) for v in theta]
+                m2 = [np.zeros_like(v) for v in theta]
+                for step in range(1, STEPS + 1):
+                    bt = dataclasses.replace(b, cond_a=theta[0].astype(np.float32),
+                                             cond_b=theta[1].astype(np.float32), cond_t=theta[2].astype(np.float32))
+                    r = oracle.soft(X, y, K, bt, TAU, dloss=np.ones(P))
+                    for i, gr in enumerate((r["grad_a"], r["grad_b"], r["grad_t"])):
+                        m1[i] = 0.9 * m1[i] + 0.1 * gr
+                        m2[i] = 0.999 * m2[i] + 0.001 * gr * gr
+                        theta[i] -= LR * (m1[i] / (1 - 0.9 ** step)) / (np.sqrt(m2[i] / (1 - 0.999 ** step)) + 1e-8)
+                bt = dataclasses.replace(b, cond_a=theta[0].astype(np.float32),
+                                         cond_b=theta[1].astype(np.float32), cond_t=theta[2].astype(np.float32))
+                fit2, _, _ = oracle.eval_hard(X, y, K, bt, want_per_class=False)
+                fit = np.maximum(fit, fit2)
+            cur = oracle.evolve_step(cur, fit, 1, g, 1, X, K)
+        return (time.perf_counter() - t0) / gens
+
+    t_cpu = cpu_generations(10, False)
+    t_cpu_tuned = cpu_generations(2, True)
+    return {"workload": f"paper-shape evolution P={P} R<=8 C<=3 N={len(X)} F=30 K=2 generations={G}; "
+                        f"fine-tuned arm: all {P} sets x {STEPS} Adam steps every generation",
+            "gpu_generations_per_s": 1.0 / t_gpu, "gpu_generations_per_s_finetuned": 1.0 / t_gpu_tuned,
+            "cpu_oracle_generations_per_s": 1.0 / t_cpu, "cpu_oracle_generations_per_s_finetuned": 1.0 / t_cpu_tuned,
+            "cpu_over_gpu_time": t_cpu / t_gpu, "cpu_over_gpu_time_finetuned": t_cpu_tuned / t_gpu_tuned,
+            "best_first_last_finetuned": [int(best[0]), int(best[-1])],
+            "cpu_cores": oracle.num_threads(0), "cpu_sample": "10 generations (2 with fine-tuning)",
+            "paper": "CPU/GPU wall-clock ratio at least 5x on a T4 with and without fine-tuning (Sec. 4)"}
+
+
 def serving_leg(args, dev):
     """Continuous batching of fitness requests from 256 concurrent evolution runs (each with its own
     resident dataset: N log-uniform [500, 500000], F ~ U{8..256}, K ~ U{2..10}); request
@@ -641,7 +708,7 @@ def main():
                          "P=256) are the cases used for ncu captures")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="force a tile configuration id")
-    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving,categorical,plain)")
+    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,paper_evolution,serving,categorical,plain)")
     ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -687,9 +754,10 @@ def main():
              if counters and "issue_active_pct" in counters else None)
     extras = {}
     if not args.no_extras and d.rank == 0:
-        for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("serving", serving_leg),
-                          ("categorical", categorical_leg), ("plain", plain_leg)):
-            if name in args.skip:
+        skip = {x.strip() for x in args.skip.split(",") if x.strip()}
+        for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("paper_evolution", paper_evolution_leg),
+                          ("serving", serving_leg), ("categorical", categorical_leg), ("plain", plain_leg)):
+            if name in skip:
                 continue
             try:
                 extras[name] = leg(args, dev)
