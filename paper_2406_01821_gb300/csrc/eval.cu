@@ -7,6 +7,7 @@
 #include <sstream>
 
 #include "rs_internal.cuh"
+#include "graph_util.cuh"
 
 namespace rs {
 
@@ -317,20 +318,6 @@ static rs_status grow_buffer(char *&p, size_t &cap, size_t need)
     return RS_OK;
 }
 
-static int kernel_nodes(cudaGraph_t g)
-{
-    size_t n = 0;
-    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
-    std::vector<cudaGraphNode_t> nodes(n);
-    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
-    int k = 0;
-    for (size_t i = 0; i < n; ++i) {
-        cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
-    }
-    return k;
-}
-
 rs_status finish_status(Ctx *ctx, const uint32_t *d_status, cudaStream_t stream);
 rs_status report_status(uint32_t h);
 
@@ -441,7 +428,7 @@ static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, 
             cudaError_t ie = cudaGraphInstantiate(&ge->exec, g, 0);
             if (ie != cudaSuccess) { ge->exec = nullptr; cudaGraphDestroy(g); return cuda_fail(ie, "cudaGraphInstantiate"); }
         }
-        ge->kernels = kernel_nodes(g);
+        ge->kernels = graph_kernel_nodes(g);
         cudaGraphDestroy(g);
         // remember the arguments only once the executable holds them
         ge->bd = bd;

@@ -15,6 +15,8 @@
 #include <vector>
 
 #include "rs_internal.cuh"
+#include "graph_util.cuh"
+#include "soft_step.cuh"
 
 namespace rs {
 
@@ -239,9 +241,12 @@ __device__ void mutate(Rng &r, const PopDev &o, int c, const DataView &d)
 }
 
 // One warp per child: copies in parallel, random decisions on lane 0.
+// gen = gen0 + *gidx: the generation index is read on the device, so that one captured graph
+// serves every generation.
 __global__ void k_next_generation(PopDev in, const int32_t *fit, const int32_t *order, PopDev out,
-                                  uint64_t seed, uint64_t gen, int elite, DataView d)
+                                  uint64_t seed, uint64_t gen0, const int64_t *gidx, int elite, DataView d)
 {
+    const uint64_t gen = gen0 + (uint64_t)*gidx;
     const int lane = threadIdx.x & 31;
     const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (c >= in.P) return;
@@ -412,7 +417,9 @@ __global__ void k_write_back(const float *a, const float *b, const float *t, con
     }
 }
 
-__global__ void k_stats(const int32_t *fit, int P, int32_t *best, double *mean, int gen)
+// best[g] and mean[g] for g = *gidx; writes g + 1 to *gnext when given.
+__global__ void k_stats(const int32_t *fit, int P, int32_t *best, double *mean, const int64_t *gidx,
+                        int64_t *gnext)
 {
     __shared__ long long ssum[1024];
     __shared__ int smax[1024];
@@ -430,8 +437,10 @@ __global__ void k_stats(const int32_t *fit, int P, int32_t *best, double *mean, 
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        const int64_t gen = *gidx;
         best[gen] = smax[0];
         mean[gen] = (double)ssum[0] / (double)P;
+        if (gnext) *gnext = gen + 1;
     }
 }
 
@@ -548,7 +557,7 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
 
     DataView dv{ds.Xt, ds.inv, ds.N, ds.n_pad, ds.F, ds.K};
     const TileConfig &tc = tile_config(heuristic_tile_for(ds));
-    auto evaluate = [&](int nsub, int32_t *out_fit) -> rs_status {
+    auto evaluate = [&](int nsub, int32_t *out_fit, cudaStream_t st) -> rs_status {
         BatchDev bd{};
         bd.P = nsub;
         bd.R = (int32_t)((size_t)nsub * RMAX);          // capacities; real sizes are on the device
@@ -558,24 +567,34 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
         bd.cond_f = w.o.cond_f; bd.cond_g = w.o.cond_g; bd.cond_op = w.o.cond_op;
         bd.cond_a = w.o.cond_a; bd.cond_b = w.o.cond_b; bd.cond_t = w.o.cond_t;
         return enqueue_hard_dev_sizes(ctx, &ds, tc, bd, w.first_rule + nsub, w.first_cond + nsub, sc,
-                                      out_fit, nullptr, nullptr, s);
+                                      out_fit, nullptr, nullptr, st);
     };
 
-    int cur = 0;
-    for (int g = 0; g <= G; ++g) {
-        PopDev &in = pop[cur];
-        build_csr(in, nullptr, P, w, s);
-        if ((rc = evaluate(P, fit))) return rc;
-        const bool tune = cfg->tune_every > 0 && T > 0 && cfg->tune_steps > 0 && g < G &&
-                          ((cfg->first_generation + g) % cfg->tune_every) == cfg->tune_every - 1;
+    // The generation index lives on the device: while generation g runs, slot g & 1 holds g and
+    // k_stats writes g + 1 into the other slot. With the population buffers also alternating by
+    // the parity of g, a generation's work depends on the host only through (parity, tuning), so
+    // one captured graph per pair serves every generation.
+    int64_t *gslot = nullptr;
+    void *soft_scratch = nullptr;
+    const int64_t soft_cap_c = (int64_t)TC;
+    if ((rc = B.get(&gslot, 2)) ||
+        (T > 0 && (rc = B.get(reinterpret_cast<char **>(&soft_scratch), soft_scratch_bytes(soft_cap_c, T)))))
+        return rc;
+    RS_CUDA(cudaMemsetAsync(gslot, 0, 2 * sizeof(int64_t), s));
+
+    auto generation = [&](int par, bool tune, bool last, cudaStream_t st) -> rs_status {
+        PopDev &in = pop[par];
+        rs_status grc;
+        build_csr(in, nullptr, P, w, st);
+        if ((grc = evaluate(P, fit, st))) return grc;
         if (tune) {
-            k_rank<<<(P + 255) / 256, 256, 0, s>>>(fit, P, order);
-            build_csr(in, order, T, w, s);                     // the T best, in rank order
-            RS_CUDA(cudaMemcpyAsync(ta, w.o.cond_a, 4 * TC, cudaMemcpyDeviceToDevice, s));
-            RS_CUDA(cudaMemcpyAsync(tb, w.o.cond_b, 4 * TC, cudaMemcpyDeviceToDevice, s));
-            RS_CUDA(cudaMemcpyAsync(tt, w.o.cond_t, 4 * TC, cudaMemcpyDeviceToDevice, s));
-            RS_CUDA(cudaMemsetAsync(mo, 0, 8 * TC, s));
-            RS_CUDA(cudaMemsetAsync(ve, 0, 8 * TC, s));
+            k_rank<<<(P + 255) / 256, 256, 0, st>>>(fit, P, order);
+            build_csr(in, order, T, w, st);                    // the T best, in rank order
+            RS_CUDA(cudaMemcpyAsync(ta, w.o.cond_a, 4 * TC, cudaMemcpyDeviceToDevice, st));
+            RS_CUDA(cudaMemcpyAsync(tb, w.o.cond_b, 4 * TC, cudaMemcpyDeviceToDevice, st));
+            RS_CUDA(cudaMemcpyAsync(tt, w.o.cond_t, 4 * TC, cudaMemcpyDeviceToDevice, st));
+            RS_CUDA(cudaMemsetAsync(mo, 0, 8 * TC, st));
+            RS_CUDA(cudaMemsetAsync(ve, 0, 8 * TC, st));
             SoftArgs sa{};
             sa.b.P = T;
             sa.b.R = (int32_t)((size_t)T * RMAX);
@@ -590,33 +609,76 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
             sa.F = ds.F; sa.K = ds.K; sa.tau = cfg->tau; sa.loss = loss; sa.dloss = dl;
             sa.grad_a = ga; sa.grad_b = gb; sa.grad_t = gt; sa.status = sc.status;
             for (int step = 1; step <= cfg->tune_steps; ++step) {
-                if ((rc = soft_step_known(ctx, sa, RMAX, RMAX * CMAX, s))) return rc;
-                k_adam<<<(int)((TC + 255) / 256), 256, 0, s>>>(ta, tb, tt, w.o.cond_g, ga, gb, gt, mo, ve,
-                                                              (int)TC, step, cfg->lr, 0.9f, 0.999f, 1e-8f);
+                if ((grc = soft_step_scratch(ctx, sa, RMAX, RMAX * CMAX, soft_scratch, soft_cap_c, T, st))) return grc;
+                k_adam<<<(int)((TC + 255) / 256), 256, 0, st>>>(ta, tb, tt, w.o.cond_g, ga, gb, gt, mo, ve,
+                                                               (int)TC, step, cfg->lr, 0.9f, 0.999f, 1e-8f);
                 count_launch(ctx);
             }
             // tuned fitness of the T sets (hard evaluation with the tuned coefficients)
-            RS_CUDA(cudaMemcpyAsync(w.o.cond_a, ta, 4 * TC, cudaMemcpyDeviceToDevice, s));
-            RS_CUDA(cudaMemcpyAsync(w.o.cond_b, tb, 4 * TC, cudaMemcpyDeviceToDevice, s));
-            RS_CUDA(cudaMemcpyAsync(w.o.cond_t, tt, 4 * TC, cudaMemcpyDeviceToDevice, s));
-            if ((rc = evaluate(T, tuned_fit))) return rc;
-            k_scatter_fit<<<(T + 255) / 256, 256, 0, s>>>(tuned_fit, order, T, fit, improved);
+            RS_CUDA(cudaMemcpyAsync(w.o.cond_a, ta, 4 * TC, cudaMemcpyDeviceToDevice, st));
+            RS_CUDA(cudaMemcpyAsync(w.o.cond_b, tb, 4 * TC, cudaMemcpyDeviceToDevice, st));
+            RS_CUDA(cudaMemcpyAsync(w.o.cond_t, tt, 4 * TC, cudaMemcpyDeviceToDevice, st));
+            if ((grc = evaluate(T, tuned_fit, st))) return grc;
+            k_scatter_fit<<<(T + 255) / 256, 256, 0, st>>>(tuned_fit, order, T, fit, improved);
             if (cfg->lamarckian)
-                k_write_back<<<(T * 32 + 255) / 256, 256, 0, s>>>(ta, tb, tt, w.o.cond_slot, w.first_cond,
-                                                                improved, T, in);
+                k_write_back<<<(T * 32 + 255) / 256, 256, 0, st>>>(ta, tb, tt, w.o.cond_slot, w.first_cond,
+                                                                 improved, T, in);
             count_launch(ctx, 2 + (cfg->lamarckian ? 1 : 0));
         }
-        k_stats<<<1, 1024, 0, s>>>(fit, P, best, mean, g);
+        k_stats<<<1, 1024, 0, st>>>(fit, P, best, mean, gslot + par, last ? nullptr : gslot + (par ^ 1));
         count_launch(ctx, 8);
-        if (g == G) break;
-        k_rank<<<(P + 255) / 256, 256, 0, s>>>(fit, P, order);
-        k_next_generation<<<(P * 32 + 255) / 256, 256, 0, s>>>(in, fit, order, pop[cur ^ 1], cfg->seed,
-                                                               (uint64_t)(cfg->first_generation + g), cfg->elite,
-                                                               dv);
+        if (last) return RS_OK;
+        k_rank<<<(P + 255) / 256, 256, 0, st>>>(fit, P, order);
+        k_next_generation<<<(P * 32 + 255) / 256, 256, 0, st>>>(in, fit, order, pop[par ^ 1], cfg->seed,
+                                                                (uint64_t)cfg->first_generation, gslot + par,
+                                                                cfg->elite, dv);
         count_launch(ctx, 2);
         RS_CUDA(cudaGetLastError());
-        cur ^= 1;
+        return RS_OK;
+    };
+
+    // Captured generations (on a stream of their own), unless the context launches directly.
+    struct GenGraphs {
+        cudaStream_t cs = nullptr;
+        cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+        int kernels[2][2] = {{0, 0}, {0, 0}};
+        ~GenGraphs()
+        {
+            for (auto &row : exec)
+                for (auto e : row)
+                    if (e) cudaGraphExecDestroy(e);
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } gg;
+    const bool graphs = !(ctx->flags & (RS_CTX_NO_GRAPH | RS_CTX_PROFILE));
+    for (int g = 0; g <= G; ++g) {
+        const int par = g & 1;
+        const bool last = g == G;
+        const bool tune = cfg->tune_every > 0 && T > 0 && cfg->tune_steps > 0 && !last &&
+                          ((cfg->first_generation + g) % cfg->tune_every) == cfg->tune_every - 1;
+        if (!graphs || last) {
+            if ((rc = generation(par, tune, last, s))) return rc;
+            continue;
+        }
+        cudaGraphExec_t &ex = gg.exec[par][tune];
+        if (!ex) {
+            if (!gg.cs) RS_CUDA(cudaStreamCreateWithFlags(&gg.cs, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            RS_CUDA(cudaStreamBeginCapture(gg.cs, cudaStreamCaptureModeThreadLocal));
+            const rs_status crc = generation(par, tune, false, gg.cs);
+            const cudaError_t ce = cudaStreamEndCapture(gg.cs, &graph);
+            if (crc) { if (graph) cudaGraphDestroy(graph); return crc; }
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture(generation)");
+            const cudaError_t ie = cudaGraphInstantiate(&ex, graph, 0);
+            gg.kernels[par][tune] = graph_kernel_nodes(graph);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) { ex = nullptr; return cuda_fail(ie, "cudaGraphInstantiate(generation)"); }
+        } else {
+            count_launch(ctx, gg.kernels[par][tune]);
+        }
+        RS_CUDA(cudaGraphLaunch(ex, s));
     }
+    const int cur = (G & 1);
     // results
     PopDev &fin = pop[cur];
     RS_CUDA(cudaMemcpyAsync(hp->nrule, fin.nrule, 4 * P, cudaMemcpyDeviceToHost, s));

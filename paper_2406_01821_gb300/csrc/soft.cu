@@ -25,6 +25,7 @@
 // only; partial losses and gradients per chunk are reduced in a second kernel in a fixed order,
 // which makes results bit-reproducible run to run and independent of scheduling.
 #include "rs_internal.cuh"
+#include "soft_step.cuh"
 
 namespace rs {
 
@@ -738,7 +739,34 @@ static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bw
     }
 }
 
-static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known_maxC, cudaStream_t stream)
+// Scratch layout of one soft call: records [C], order [P], per-chunk losses [chunks][P], the work
+// counter and maxima [4], per-chunk gradient sums [chunks][C] twice (adjoint only).
+struct SoftScratchLayout {
+    size_t recs, order, part_loss, next, part_ga, part_gbt, total;
+};
+
+static SoftScratchLayout soft_layout(int64_t C, int P, int nchunks, bool bwd)
+{
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    SoftScratchLayout L{};
+    size_t o = 0;
+    L.recs = o; o += up(sizeof(SoftRec) * (size_t)C);
+    L.order = o; o += up(sizeof(int32_t) * (size_t)P);
+    L.part_loss = o; o += up(sizeof(float) * (size_t)nchunks * P);
+    L.next = o; o += 256;
+    L.part_ga = o; o += bwd ? up(sizeof(float) * (size_t)nchunks * C) : 0;
+    L.part_gbt = o; o += bwd ? up(sizeof(float) * (size_t)nchunks * C) : 0;
+    L.total = o;
+    return L;
+}
+
+size_t soft_scratch_bytes(int64_t cap_c, int cap_p)
+{
+    return soft_layout(std::max<int64_t>(cap_c, 1), std::max(cap_p, 1), SOFT_MAX_CHUNKS, true).total;
+}
+
+static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known_maxC, cudaStream_t stream,
+                          char *pre = nullptr)
 {
     const BatchDev &b = s.b;
     const int P = b.P;
@@ -760,12 +788,23 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     int32_t *next = nullptr;   // [0] work counter, [1..2] max rules / conditions per set
     int32_t *order = nullptr;
     const bool bwd = s.dloss != nullptr;
-    cudaError_t ae = dev_alloc_async(&recs, sizeof(SoftRec) * Ccap, stream);
-    if (ae == cudaSuccess) ae = dev_alloc_async(&order, sizeof(int32_t) * (size_t)P, stream);
-    if (ae == cudaSuccess) ae = dev_alloc_async(&part_loss, sizeof(float) * (size_t)nchunks * P, stream);
-    if (ae == cudaSuccess) ae = dev_alloc_async(&next, sizeof(int32_t) * 4, stream);
-    if (ae == cudaSuccess && bwd) ae = dev_alloc_async(&part_ga, sizeof(float) * (size_t)nchunks * Ccap, stream);
-    if (ae == cudaSuccess && bwd) ae = dev_alloc_async(&part_gbt, sizeof(float) * (size_t)nchunks * Ccap, stream);
+    cudaError_t ae = cudaSuccess;
+    if (pre) {                       // the caller's scratch, laid out for at most SOFT_MAX_CHUNKS chunks
+        const SoftScratchLayout L = soft_layout(Ccap, P, SOFT_MAX_CHUNKS, bwd);
+        recs = reinterpret_cast<SoftRec *>(pre + L.recs);
+        order = reinterpret_cast<int32_t *>(pre + L.order);
+        part_loss = reinterpret_cast<float *>(pre + L.part_loss);
+        next = reinterpret_cast<int32_t *>(pre + L.next);
+        part_ga = bwd ? reinterpret_cast<float *>(pre + L.part_ga) : nullptr;
+        part_gbt = bwd ? reinterpret_cast<float *>(pre + L.part_gbt) : nullptr;
+    } else {
+        ae = dev_alloc_async(&recs, sizeof(SoftRec) * Ccap, stream);
+        if (ae == cudaSuccess) ae = dev_alloc_async(&order, sizeof(int32_t) * (size_t)P, stream);
+        if (ae == cudaSuccess) ae = dev_alloc_async(&part_loss, sizeof(float) * (size_t)nchunks * P, stream);
+        if (ae == cudaSuccess) ae = dev_alloc_async(&next, sizeof(int32_t) * 4, stream);
+        if (ae == cudaSuccess && bwd) ae = dev_alloc_async(&part_ga, sizeof(float) * (size_t)nchunks * Ccap, stream);
+        if (ae == cudaSuccess && bwd) ae = dev_alloc_async(&part_gbt, sizeof(float) * (size_t)nchunks * Ccap, stream);
+    }
     if (ae != cudaSuccess) {         // release what was taken before the failure
         for (void *q : {(void *)recs, (void *)order, (void *)part_loss, (void *)next, (void *)part_ga, (void *)part_gbt})
             if (q) cudaFreeAsync(q, stream);
@@ -853,11 +892,13 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "soft kernels");
     }
-    cudaFreeAsync(recs, stream);
-    cudaFreeAsync(order, stream);
-    cudaFreeAsync(part_loss, stream);
-    cudaFreeAsync(next, stream);
-    if (bwd) { cudaFreeAsync(part_ga, stream); cudaFreeAsync(part_gbt, stream); }
+    if (!pre) {
+        cudaFreeAsync(recs, stream);
+        cudaFreeAsync(order, stream);
+        cudaFreeAsync(part_loss, stream);
+        cudaFreeAsync(next, stream);
+        if (bwd) { cudaFreeAsync(part_ga, stream); cudaFreeAsync(part_gbt, stream); }
+    }
     return rc;
 }
 
@@ -869,6 +910,16 @@ rs_status launch_soft(Ctx *ctx, const SoftArgs &s, cudaStream_t stream)
 rs_status soft_step_known(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, cudaStream_t stream)
 {
     return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream);
+}
+
+rs_status soft_step_scratch(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, void *scratch, int64_t cap_c,
+                            int cap_p, cudaStream_t stream)
+{
+    if (!scratch || a.b.P > cap_p || std::max<int64_t>(a.b.C, 1) > std::max<int64_t>(cap_c, 1)) {
+        set_error("soft step: scratch smaller than the batch");
+        return RS_ERR_INVALID;
+    }
+    return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream, static_cast<char *>(scratch));
 }
 
 // Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would

@@ -1,0 +1,17 @@
+// A soft step (forward + adjoint) on scratch the caller allocated once: for loops that run many
+// steps of one shape (the evolution loop's fine-tuning), with no allocation per step, so that the
+// steps can be captured in a CUDA graph.
+#pragma once
+#include "rs_internal.cuh"
+
+namespace rs {
+
+// Bytes of scratch for a soft step over at most `cap_p` sets and `cap_c` conditions.
+size_t soft_scratch_bytes(int64_t cap_c, int cap_p);
+
+// soft_step_known on `scratch` (soft_scratch_bytes(cap_c, cap_p) bytes, 256-byte aligned);
+// a.b.P <= cap_p and the batch's condition capacity <= cap_c.
+rs_status soft_step_scratch(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, void *scratch, int64_t cap_c,
+                            int cap_p, cudaStream_t stream);
+
+}  // namespace rs

@@ -145,3 +145,31 @@ def test_checkpoint_resume_continues_exactly(ctx, tmp_path, tune):
         assert np.array_equal(rest[k], full[k]), k
     assert np.array_equal(rfit, ffit)
     assert np.array_equal(np.concatenate([pbest[:3], rbest]), fbest)
+
+
+@pytest.mark.parametrize("lamarckian", [False, True])
+def test_captured_generations_equal_direct_launches(ctx, lamarckian):
+    """Generations replayed from captured graphs (the generation index read on the device) give
+    the same populations, fitness and statistics as generations launched one kernel at a time,
+    with fine-tuning every third generation (generations 2, 5 and 8 of 10, counted from 3): each
+    (parity, tuning) graph is used, and all but (odd, tuned) are replayed."""
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.two_class_gaussian(3000, 8, 11)
+    pop = synth.initial_population(X, y, 2, 48, RMAX=6, CMAX=3, seed=11)
+    direct = rs.Context(0, flags=rs.CTX_NO_GRAPH)
+    kw = dict(generations=9, elite=2, seed=11, tune_every=3, tune_top=8, tune_steps=4, tau=0.1, lr=1e-2,
+              lamarckian=lamarckian, first_generation=3)
+    try:
+        results = []
+        for c in (ctx, direct):
+            ds = c.dataset(X, y, 2)
+            try:
+                results.append(c.evolve(ds, pop, **kw))
+            finally:
+                c.dataset_destroy(ds)
+    finally:
+        direct.close()
+    (ga, gfit, gbest, gmean), (da, dfit, dbest, dmean) = results
+    for k in ga:
+        assert np.array_equal(ga[k], da[k]), k
+    assert np.array_equal(gfit, dfit) and np.array_equal(gbest, dbest) and np.array_equal(gmean, dmean)
