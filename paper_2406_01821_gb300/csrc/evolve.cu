@@ -295,25 +295,72 @@ __global__ void k_count_conds(PopDev p, int32_t *rule_len, int32_t *set_len)
     rule_len[i] = nr;
 }
 
+// Exclusive prefix of one int per thread over the block (blockDim.x a multiple of 32, at most
+// 1024; every thread calls it); the block's total goes to *total.
+__device__ int block_exclusive_scan(int v, int *total)
+{
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nw ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_sums[lane] = t;
+    }
+    __syncthreads();
+    const int excl = x - v + (warp ? warp_sums[warp - 1] : 0);
+    *total = warp_sums[nw - 1];
+    __syncthreads();                  // warp_sums is reused by the next call
+    return excl;
+}
+
 // Exclusive scan of n ints with one CTA (n up to a few million: strided chunks).
 __global__ void k_scan1(const int32_t *in, int n, int32_t *out /*n+1*/)
 {
-    __shared__ int32_t part[1024];
     const int t = threadIdx.x, T = blockDim.x;
     const int chunk = (n + T - 1) / T;
     const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
     int s = 0;
     for (int i = lo; i < hi; ++i) s += in[i];
-    part[t] = s;
-    __syncthreads();
-    if (t == 0) {
-        int run = 0;
-        for (int i = 0; i < T; ++i) { int v = part[i]; part[i] = run; run += v; }
-        out[n] = run;
-    }
-    __syncthreads();
-    int run = part[t];
+    int total = 0;
+    int run = block_exclusive_scan(s, &total);
+    if (t == 0) out[n] = total;
     for (int i = lo; i < hi; ++i) { out[i] = run; run += in[i]; }
+}
+
+// CSR offsets of at most blockDim.x (<= 1024) sets in one CTA: the rule and condition counts of
+// set subset[i] (or i), scanned into first_rule / first_cond [nsub + 1]. Replaces the counting,
+// gathering and the two scans of the general path for small populations.
+__global__ void k_csr_offsets_small(PopDev p, const int32_t *subset, int nsub, int32_t *first_rule,
+                                    int32_t *first_cond)
+{
+    const int i = threadIdx.x;
+    int nr = 0, nc = 0;
+    if (i < nsub) {
+        const int src = subset ? subset[i] : i;
+        nr = p.nrule[src];
+        for (int j = 0; j < nr; ++j) nc += p.ncond[(int64_t)src * p.RMAX + j];
+    }
+    int tr = 0, tc = 0;
+    const int er = block_exclusive_scan(nr, &tr);
+    const int ec = block_exclusive_scan(nc, &tc);
+    if (i < nsub) {
+        first_rule[i] = er;
+        first_cond[i] = ec;
+    }
+    if (i == 0) {
+        first_rule[nsub] = tr;
+        first_cond[nsub] = tc;
+    }
 }
 
 struct CsrDev {
@@ -323,12 +370,17 @@ struct CsrDev {
     int32_t *cond_slot;    // flat slot index of each CSR condition (for parameter write-back)
 };
 
-// One warp per set: write its rules and conditions at the scanned offsets.
+// One warp per set: write its rules and conditions at the scanned offsets; the first thread also
+// closes the offset arrays.
 __global__ void k_scatter_csr(PopDev p, const int32_t *set_first_rule, const int32_t *set_first_cond,
                               const int32_t *subset, int nsub, CsrDev o)
 {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        o.set_rule_off[nsub] = set_first_rule[nsub];
+        o.rule_cond_off[set_first_rule[nsub]] = set_first_cond[nsub];
+    }
     if (w >= nsub) return;
     const int i = subset ? subset[w] : w;
     const int nr = p.nrule[i];
@@ -352,14 +404,6 @@ __global__ void k_scatter_csr(PopDev p, const int32_t *set_first_rule, const int
             if (o.cond_slot) o.cond_slot[c + k] = (int32_t)q;
         }
         c += nc;
-    }
-}
-
-__global__ void k_close_csr(const int32_t *set_first_rule, const int32_t *set_first_cond, int nsub, CsrDev o)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        o.set_rule_off[nsub] = set_first_rule[nsub];
-        o.rule_cond_off[set_first_rule[nsub]] = set_first_cond[nsub];
     }
 }
 
@@ -481,15 +525,25 @@ struct CsrWork {
     int32_t *rule_len, *cond_len, *sub_rule_len, *sub_cond_len, *first_rule, *first_cond;
 };
 
-static void build_csr(const PopDev &p, const int32_t *subset, int nsub, CsrWork &w, cudaStream_t s)
+// Slots -> CSR batch of nsub sets (subset[i], or the first nsub); returns the kernels launched.
+static int build_csr(const PopDev &p, const int32_t *subset, int nsub, CsrWork &w, cudaStream_t s)
 {
-    k_count_conds<<<(p.P + 255) / 256, 256, 0, s>>>(p, w.rule_len, w.cond_len);
-    k_gather_len<<<(nsub + 255) / 256, 256, 0, s>>>(w.rule_len, subset, nsub, w.sub_rule_len);
-    k_gather_len<<<(nsub + 255) / 256, 256, 0, s>>>(w.cond_len, subset, nsub, w.sub_cond_len);
-    k_scan1<<<1, 1024, 0, s>>>(w.sub_rule_len, nsub, w.first_rule);
-    k_scan1<<<1, 1024, 0, s>>>(w.sub_cond_len, nsub, w.first_cond);
-    k_scatter_csr<<<(nsub * 32 + 255) / 256, 256, 0, s>>>(p, w.first_rule, w.first_cond, subset, nsub, w.o);
-    k_close_csr<<<1, 32, 0, s>>>(w.first_rule, w.first_cond, nsub, w.o);
+    int n = 0;
+    if (nsub <= 1024) {
+        k_csr_offsets_small<<<1, std::max(32, (nsub + 31) / 32 * 32), 0, s>>>(p, subset, nsub, w.first_rule,
+                                                                             w.first_cond);
+        n = 1;
+    } else {
+        k_count_conds<<<(p.P + 255) / 256, 256, 0, s>>>(p, w.rule_len, w.cond_len);
+        k_gather_len<<<(nsub + 255) / 256, 256, 0, s>>>(w.rule_len, subset, nsub, w.sub_rule_len);
+        k_gather_len<<<(nsub + 255) / 256, 256, 0, s>>>(w.cond_len, subset, nsub, w.sub_cond_len);
+        k_scan1<<<1, 1024, 0, s>>>(w.sub_rule_len, nsub, w.first_rule);
+        k_scan1<<<1, 1024, 0, s>>>(w.sub_cond_len, nsub, w.first_cond);
+        n = 5;
+    }
+    k_scatter_csr<<<std::max(1, (nsub * 32 + 255) / 256), 256, 0, s>>>(p, w.first_rule, w.first_cond, subset,
+                                                                      nsub, w.o);
+    return n + 1;
 }
 
 rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_population *hp,
@@ -585,11 +639,11 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
     auto generation = [&](int par, bool tune, bool last, cudaStream_t st) -> rs_status {
         PopDev &in = pop[par];
         rs_status grc;
-        build_csr(in, nullptr, P, w, st);
+        count_launch(ctx, build_csr(in, nullptr, P, w, st));
         if ((grc = evaluate(P, fit, st))) return grc;
         if (tune) {
             k_rank<<<(P + 255) / 256, 256, 0, st>>>(fit, P, order);
-            build_csr(in, order, T, w, st);                    // the T best, in rank order
+            count_launch(ctx, 1 + build_csr(in, order, T, w, st));   // the T best, in rank order
             RS_CUDA(cudaMemcpyAsync(ta, w.o.cond_a, 4 * TC, cudaMemcpyDeviceToDevice, st));
             RS_CUDA(cudaMemcpyAsync(tb, w.o.cond_b, 4 * TC, cudaMemcpyDeviceToDevice, st));
             RS_CUDA(cudaMemcpyAsync(tt, w.o.cond_t, 4 * TC, cudaMemcpyDeviceToDevice, st));
@@ -626,7 +680,7 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
             count_launch(ctx, 2 + (cfg->lamarckian ? 1 : 0));
         }
         k_stats<<<1, 1024, 0, st>>>(fit, P, best, mean, gslot + par, last ? nullptr : gslot + (par ^ 1));
-        count_launch(ctx, 8);
+        count_launch(ctx);
         if (last) return RS_OK;
         k_rank<<<(P + 255) / 256, 256, 0, st>>>(fit, P, order);
         k_next_generation<<<(P * 32 + 255) / 256, 256, 0, st>>>(in, fit, order, pop[par ^ 1], cfg->seed,
