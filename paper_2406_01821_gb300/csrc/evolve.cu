@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "rs_internal.cuh"
+#include "block_scan.cuh"
 #include "graph_util.cuh"
 #include "soft_step.cuh"
 
@@ -293,34 +294,6 @@ __global__ void k_count_conds(PopDev p, int32_t *rule_len, int32_t *set_len)
     for (int j = 0; j < nr; ++j) tot += p.ncond[(int64_t)i * p.RMAX + j];
     set_len[i] = tot;
     rule_len[i] = nr;
-}
-
-// Exclusive prefix of one int per thread over the block (blockDim.x a multiple of 32, at most
-// 1024; every thread calls it); the block's total goes to *total.
-__device__ int block_exclusive_scan(int v, int *total)
-{
-    __shared__ int warp_sums[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int t = lane < nw ? warp_sums[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, t, o);
-            if (lane >= o) t += y;
-        }
-        if (lane < nw) warp_sums[lane] = t;
-    }
-    __syncthreads();
-    const int excl = x - v + (warp ? warp_sums[warp - 1] : 0);
-    *total = warp_sums[nw - 1];
-    __syncthreads();                  // warp_sums is reused by the next call
-    return excl;
 }
 
 // Exclusive scan of n ints with one CTA (n up to a few million: strided chunks).
@@ -663,7 +636,8 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
             sa.F = ds.F; sa.K = ds.K; sa.tau = cfg->tau; sa.loss = loss; sa.dloss = dl;
             sa.grad_a = ga; sa.grad_b = gb; sa.grad_t = gt; sa.status = sc.status;
             for (int step = 1; step <= cfg->tune_steps; ++step) {
-                if ((grc = soft_step_scratch(ctx, sa, RMAX, RMAX * CMAX, soft_scratch, soft_cap_c, T, st))) return grc;
+                if ((grc = soft_step_scratch(ctx, sa, RMAX, RMAX * CMAX, soft_scratch, soft_cap_c, T, step > 1, st)))
+                    return grc;
                 k_adam<<<(int)((TC + 255) / 256), 256, 0, st>>>(ta, tb, tt, w.o.cond_g, ga, gb, gt, mo, ve,
                                                                (int)TC, step, cfg->lr, 0.9f, 0.999f, 1e-8f);
                 count_launch(ctx);

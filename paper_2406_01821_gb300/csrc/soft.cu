@@ -26,6 +26,7 @@
 // which makes results bit-reproducible run to run and independent of scheduling.
 #include "rs_internal.cuh"
 #include "soft_step.cuh"
+#include "block_scan.cuh"
 
 namespace rs {
 
@@ -53,9 +54,10 @@ struct __align__(16) SoftRec {
                       // bits of its category set (0..31 in a, 32..63 in bt)
 };
 
-__global__ void k_pack_soft(BatchDev b, int F, int K, SoftRec *recs, uint32_t *status)
+__global__ void k_pack_soft(BatchDev b, int F, int K, SoftRec *recs, uint32_t *status, int32_t *work_counter)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) *work_counter = 0;            // the soft kernel's task counter
     if (b.dR) { b.R = *b.dR; b.C = *b.dC; }
     if (c >= b.C) return;
     const int f = b.cond_f[c], g = b.cond_g[c], op = b.cond_op[c];
@@ -100,11 +102,7 @@ __global__ void k_soft_order(BatchDev b, int32_t *order)
     };
     for (int p = threadIdx.x; p < b.P; p += blockDim.x) atomicAdd(&hist[bucket(p)], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int i = 0; i < SOFT_ORDER_BUCKETS; ++i) { const int h = hist[i]; hist[i] = run; run += h; }
-    }
-    __syncthreads();
+    block_exclusive_scan_array(hist, SOFT_ORDER_BUCKETS);
     for (int p = threadIdx.x; p < b.P; p += blockDim.x) order[atomicAdd(&hist[bucket(p)], 1)] = p;
 }
 
@@ -651,15 +649,17 @@ __global__ void k_soft_reduce_loss(const float *part_loss, int nchunks, int P, f
     loss[p] = tree_sum_strided(part_loss + p, P, nchunks) * inv_n;
 }
 
-// One thread per set, looping over its conditions (grads scaled by dloss[p] / N).
-__global__ void k_soft_reduce_grad(const float *part_ga, const float *part_gbt, int nchunks,
-                                   const int32_t *set_rule_off, const int32_t *rule_cond_off,
+// One CTA per set, its threads looping over the set's conditions (grads scaled by dloss[p] / N);
+// thread 0 also writes the set's loss when `loss` is given.
+__global__ void k_soft_reduce_grad(const float *part_ga, const float *part_gbt, const float *part_loss,
+                                   int nchunks, const int32_t *set_rule_off, const int32_t *rule_cond_off,
                                    const SoftRec *recs, int P, int64_t C, const float *dloss,
-                                   float inv_n, float *grad_a, float *grad_b, float *grad_t,
+                                   float inv_n, float *grad_a, float *grad_b, float *grad_t, float *loss,
                                    const uint32_t *status)
 {
     const int p = blockIdx.x;
     if (p >= P || *status) return;
+    if (loss && threadIdx.x == 0) loss[p] = tree_sum_strided(part_loss + p, P, nchunks) * inv_n;
     const int cb = rule_cond_off[set_rule_off[p]], ce = rule_cond_off[set_rule_off[p + 1]];
     const float scale = dloss[p] * inv_n;
     for (int c = cb + threadIdx.x; c < ce; c += blockDim.x) {
@@ -765,8 +765,10 @@ size_t soft_scratch_bytes(int64_t cap_c, int cap_p)
     return soft_layout(std::max<int64_t>(cap_c, 1), std::max(cap_p, 1), SOFT_MAX_CHUNKS, true).total;
 }
 
+// `repeat`: a later step on the caller's scratch over the same structure as the step before it
+// (only coefficients and thresholds changed), whose validation and set order still stand.
 static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known_maxC, cudaStream_t stream,
-                          char *pre = nullptr)
+                          char *pre = nullptr, bool repeat = false)
 {
     const BatchDev &b = s.b;
     const int P = b.P;
@@ -810,14 +812,21 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
             if (q) cudaFreeAsync(q, stream);
         return cuda_fail(ae, "soft scratch");
     }
-    RS_CUDA(cudaMemsetAsync(next, 0, sizeof(int32_t) * 4, stream));
     const bool known = known_maxR > 0;
-    k_check_sets_soft<<<(P + 255) / 256, 256, 0, stream>>>(b, s.K, s.status, next + 1,
-                                                           known ? known_maxR : SOFT_MAX_RULES,
-                                                           known ? known_maxC : SOFT_MAX_CONDS);
-    k_pack_soft<<<(unsigned)((Ccap + 255) / 256), 256, 0, stream>>>(b, s.F, s.K, recs, s.status);
-    k_soft_order<<<1, 1024, 0, stream>>>(b, order);
-    count_launch(ctx, 3);
+    repeat = repeat && pre && known;
+    if (!repeat) {
+        RS_CUDA(cudaMemsetAsync(next, 0, sizeof(int32_t) * 4, stream));
+        k_check_sets_soft<<<(P + 255) / 256, 256, 0, stream>>>(b, s.K, s.status, next + 1,
+                                                               known ? known_maxR : SOFT_MAX_RULES,
+                                                               known ? known_maxC : SOFT_MAX_CONDS);
+        count_launch(ctx);
+    }
+    k_pack_soft<<<(unsigned)((Ccap + 255) / 256), 256, 0, stream>>>(b, s.F, s.K, recs, s.status, next);
+    count_launch(ctx);
+    if (!repeat) {
+        k_soft_order<<<1, 1024, 0, stream>>>(b, order);
+        count_launch(ctx);
+    }
     SoftKArgs k{};
     k.recs = recs;
     k.set_rule_off = b.set_rule_off;
@@ -881,14 +890,15 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
             if (b.cond_set) launch_soft_kernel<true>(ctx, k, tiled, bwd, s.F, smem, per_warp, stream);
             else launch_soft_kernel<false>(ctx, k, tiled, bwd, s.F, smem, per_warp, stream);
         }
-        k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
-                                                               1.0f / (float)s.N, s.loss, s.status);
-        if (bwd)
-            k_soft_reduce_grad<<<P, 128, 0, stream>>>(part_ga, part_gbt, nchunks, b.set_rule_off,
+        if (bwd)                      // the gradients and (when asked) the loss in one launch
+            k_soft_reduce_grad<<<P, 128, 0, stream>>>(part_ga, part_gbt, part_loss, nchunks, b.set_rule_off,
                                                      b.rule_cond_off, recs, P, Ccap, s.dloss,
                                                      1.0f / (float)s.N, s.grad_a, s.grad_b, s.grad_t,
-                                                     s.status);
-        count_launch(ctx, 2 + (bwd ? 1 : 0));
+                                                     s.loss, s.status);
+        else
+            k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
+                                                                   1.0f / (float)s.N, s.loss, s.status);
+        count_launch(ctx, 2);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "soft kernels");
     }
@@ -913,13 +923,13 @@ rs_status soft_step_known(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, cudaS
 }
 
 rs_status soft_step_scratch(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, void *scratch, int64_t cap_c,
-                            int cap_p, cudaStream_t stream)
+                            int cap_p, bool repeat, cudaStream_t stream)
 {
     if (!scratch || a.b.P > cap_p || std::max<int64_t>(a.b.C, 1) > std::max<int64_t>(cap_c, 1)) {
         set_error("soft step: scratch smaller than the batch");
         return RS_ERR_INVALID;
     }
-    return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream, static_cast<char *>(scratch));
+    return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream, static_cast<char *>(scratch), repeat);
 }
 
 // Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would

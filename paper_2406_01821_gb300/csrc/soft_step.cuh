@@ -10,8 +10,10 @@ namespace rs {
 size_t soft_scratch_bytes(int64_t cap_c, int cap_p);
 
 // soft_step_known on `scratch` (soft_scratch_bytes(cap_c, cap_p) bytes, 256-byte aligned);
-// a.b.P <= cap_p and the batch's condition capacity <= cap_c.
+// a.b.P <= cap_p and the batch's condition capacity <= cap_c. `repeat`: the previous step on this
+// scratch had the same structure (sets, rules, features, classes; only a, b, t differ), so its
+// validation and set order are reused.
 rs_status soft_step_scratch(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, void *scratch, int64_t cap_c,
-                            int cap_p, cudaStream_t stream);
+                            int cap_p, bool repeat, cudaStream_t stream);
 
 }  // namespace rs
