@@ -310,32 +310,6 @@ __global__ void k_scan1(const int32_t *in, int n, int32_t *out /*n+1*/)
     for (int i = lo; i < hi; ++i) { out[i] = run; run += in[i]; }
 }
 
-// CSR offsets of at most blockDim.x (<= 1024) sets in one CTA: the rule and condition counts of
-// set subset[i] (or i), scanned into first_rule / first_cond [nsub + 1]. Replaces the counting,
-// gathering and the two scans of the general path for small populations.
-__global__ void k_csr_offsets_small(PopDev p, const int32_t *subset, int nsub, int32_t *first_rule,
-                                    int32_t *first_cond)
-{
-    const int i = threadIdx.x;
-    int nr = 0, nc = 0;
-    if (i < nsub) {
-        const int src = subset ? subset[i] : i;
-        nr = p.nrule[src];
-        for (int j = 0; j < nr; ++j) nc += p.ncond[(int64_t)src * p.RMAX + j];
-    }
-    int tr = 0, tc = 0;
-    const int er = block_exclusive_scan(nr, &tr);
-    const int ec = block_exclusive_scan(nc, &tc);
-    if (i < nsub) {
-        first_rule[i] = er;
-        first_cond[i] = ec;
-    }
-    if (i == 0) {
-        first_rule[nsub] = tr;
-        first_cond[nsub] = tc;
-    }
-}
-
 struct CsrDev {
     int32_t *set_rule_off, *rule_cond_off, *rule_class, *set_default, *cond_f, *cond_g;
     int8_t *cond_op;
@@ -343,18 +317,10 @@ struct CsrDev {
     int32_t *cond_slot;    // flat slot index of each CSR condition (for parameter write-back)
 };
 
-// One warp per set: write its rules and conditions at the scanned offsets; the first thread also
-// closes the offset arrays.
-__global__ void k_scatter_csr(PopDev p, const int32_t *set_first_rule, const int32_t *set_first_cond,
-                              const int32_t *subset, int nsub, CsrDev o)
+// Set w of the batch (slot subset[w], or w) written by one warp at its scanned offsets.
+__device__ void scatter_set(const PopDev &p, const int32_t *set_first_rule, const int32_t *set_first_cond,
+                            const int32_t *subset, int w, const CsrDev &o, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        o.set_rule_off[nsub] = set_first_rule[nsub];
-        o.rule_cond_off[set_first_rule[nsub]] = set_first_cond[nsub];
-    }
-    if (w >= nsub) return;
     const int i = subset ? subset[w] : w;
     const int nr = p.nrule[i];
     const int r0 = set_first_rule[w];
@@ -377,6 +343,47 @@ __global__ void k_scatter_csr(PopDev p, const int32_t *set_first_rule, const int
             if (o.cond_slot) o.cond_slot[c + k] = (int32_t)q;
         }
         c += nc;
+    }
+}
+
+// One warp per set: write its rules and conditions at the scanned offsets; the first thread also
+// closes the offset arrays.
+__global__ void k_scatter_csr(PopDev p, const int32_t *set_first_rule, const int32_t *set_first_cond,
+                              const int32_t *subset, int nsub, CsrDev o)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        o.set_rule_off[nsub] = set_first_rule[nsub];
+        o.rule_cond_off[set_first_rule[nsub]] = set_first_cond[nsub];
+    }
+    if (w < nsub) scatter_set(p, set_first_rule, set_first_cond, subset, w, o, threadIdx.x & 31);
+}
+
+// CSR offsets of at most 1024 sets in one CTA of 1024 threads: the rule and condition counts of
+// set subset[i] (or i) scanned into first_rule / first_cond [nsub + 1] (and the closing offsets).
+// Replaces the counting, gathering and the two scans of the general path for small populations;
+// the sets themselves are written by k_scatter_csr, a warp each across the GPU (writing them with
+// this one CTA's warps in turn was slower).
+__global__ void k_csr_offsets_small(PopDev p, const int32_t *subset, int nsub, int32_t *first_rule,
+                                    int32_t *first_cond)
+{
+    const int i = threadIdx.x;
+    int nr = 0, nc = 0;
+    if (i < nsub) {
+        const int src = subset ? subset[i] : i;
+        nr = p.nrule[src];
+        for (int j = 0; j < nr; ++j) nc += p.ncond[(int64_t)src * p.RMAX + j];
+    }
+    int tr = 0, tc = 0;
+    const int er = block_exclusive_scan(nr, &tr);
+    const int ec = block_exclusive_scan(nc, &tc);
+    if (i < nsub) {
+        first_rule[i] = er;
+        first_cond[i] = ec;
+    }
+    if (i == 0) {
+        first_rule[nsub] = tr;
+        first_cond[nsub] = tc;
     }
 }
 
@@ -434,9 +441,9 @@ __global__ void k_write_back(const float *a, const float *b, const float *t, con
     }
 }
 
-// best[g] and mean[g] for g = *gidx; writes g + 1 to *gnext when given.
-__global__ void k_stats(const int32_t *fit, int P, int32_t *best, double *mean, const int64_t *gidx,
-                        int64_t *gnext)
+// best[g] and mean[g] for g = *gidx; writes g + 1 to *gnext when given (one CTA of 1024 threads).
+__device__ void stats_block(const int32_t *fit, int P, int32_t *best, double *mean, const int64_t *gidx,
+                            int64_t *gnext)
 {
     __shared__ long long ssum[1024];
     __shared__ int smax[1024];
@@ -458,6 +465,32 @@ __global__ void k_stats(const int32_t *fit, int P, int32_t *best, double *mean, 
         best[gen] = smax[0];
         mean[gen] = (double)ssum[0] / (double)P;
         if (gnext) *gnext = gen + 1;
+    }
+}
+
+__global__ void k_stats(const int32_t *fit, int P, int32_t *best, double *mean, const int64_t *gidx,
+                        int64_t *gnext)
+{
+    stats_block(fit, P, best, mean, gidx, gnext);
+}
+
+// k_stats and k_rank in one CTA of 1024 threads, for P <= 1024: the same statistics and the same
+// order (fitness descending, index ascending among equals).
+__global__ void k_stats_rank_small(const int32_t *fit, int P, int32_t *best, double *mean, const int64_t *gidx,
+                                   int64_t *gnext, int32_t *order)
+{
+    __shared__ int32_t sf[1024];
+    const int i = threadIdx.x;
+    if (i < P) sf[i] = fit[i];
+    stats_block(fit, P, best, mean, gidx, gnext);      // synchronises the block
+    if (i < P) {
+        const int fi = sf[i];
+        int pos = 0;
+        for (int j = 0; j < P; ++j) {
+            const int fj = sf[j];
+            pos += (fj > fi) || (fj == fi && j < i);
+        }
+        order[pos] = i;
     }
 }
 
@@ -501,11 +534,9 @@ struct CsrWork {
 // Slots -> CSR batch of nsub sets (subset[i], or the first nsub); returns the kernels launched.
 static int build_csr(const PopDev &p, const int32_t *subset, int nsub, CsrWork &w, cudaStream_t s)
 {
-    int n = 0;
+    int n = 1;
     if (nsub <= 1024) {
-        k_csr_offsets_small<<<1, std::max(32, (nsub + 31) / 32 * 32), 0, s>>>(p, subset, nsub, w.first_rule,
-                                                                             w.first_cond);
-        n = 1;
+        k_csr_offsets_small<<<1, 1024, 0, s>>>(p, subset, nsub, w.first_rule, w.first_cond);
     } else {
         k_count_conds<<<(p.P + 255) / 256, 256, 0, s>>>(p, w.rule_len, w.cond_len);
         k_gather_len<<<(nsub + 255) / 256, 256, 0, s>>>(w.rule_len, subset, nsub, w.sub_rule_len);
@@ -653,14 +684,20 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
                                                                  improved, T, in);
             count_launch(ctx, 2 + (cfg->lamarckian ? 1 : 0));
         }
-        k_stats<<<1, 1024, 0, st>>>(fit, P, best, mean, gslot + par, last ? nullptr : gslot + (par ^ 1));
-        count_launch(ctx);
-        if (last) return RS_OK;
-        k_rank<<<(P + 255) / 256, 256, 0, st>>>(fit, P, order);
+        if (!last && P <= 1024) {
+            k_stats_rank_small<<<1, 1024, 0, st>>>(fit, P, best, mean, gslot + par, gslot + (par ^ 1), order);
+            count_launch(ctx);
+        } else {
+            k_stats<<<1, 1024, 0, st>>>(fit, P, best, mean, gslot + par, last ? nullptr : gslot + (par ^ 1));
+            count_launch(ctx);
+            if (last) return RS_OK;
+            k_rank<<<(P + 255) / 256, 256, 0, st>>>(fit, P, order);
+            count_launch(ctx);
+        }
         k_next_generation<<<(P * 32 + 255) / 256, 256, 0, st>>>(in, fit, order, pop[par ^ 1], cfg->seed,
                                                                 (uint64_t)cfg->first_generation, gslot + par,
                                                                 cfg->elite, dv);
-        count_launch(ctx, 2);
+        count_launch(ctx);
         RS_CUDA(cudaGetLastError());
         return RS_OK;
     };
@@ -772,17 +809,32 @@ rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, fl
     sa.Xt = ds.Xt; sa.y = ds.y; sa.perm = ds.perm; sa.N = ds.N; sa.n_pad = ds.n_pad;
     sa.F = ds.F; sa.K = ds.K; sa.tau = tau; sa.loss = loss; sa.dloss = dl;
     sa.grad_a = ga; sa.grad_b = gb; sa.grad_t = gt; sa.status = status;
+    // validate once (the structure does not change between steps), then run the steps back to back
+    // on scratch allocated once, the per-step losses kept on the device until the end
+    int maxR = 1, maxC = 1;
+    if ((rc = soft_validate(ctx, sa, &maxR, &maxC, s))) return rc;
+    void *scratch = nullptr;
+    float *trace = nullptr;
+    if ((rc = B.get(reinterpret_cast<char **>(&scratch), soft_scratch_bytes((int64_t)C, (int)P))) ||
+        (loss_trace && (rc = B.get(&trace, (size_t)steps * P))))
+        return rc;
     for (int step = 1; step <= steps; ++step) {
-        if ((rc = launch_soft(ctx, sa, s))) return rc;     // validates the structure every step
-        if (loss_trace)
-            RS_CUDA(cudaMemcpyAsync(loss_trace + (size_t)(step - 1) * P, loss, 4 * P, cudaMemcpyDeviceToHost, s));
+        sa.loss = trace ? trace + (size_t)(step - 1) * P : loss;
+        if ((rc = soft_step_scratch(ctx, sa, maxR, maxC, scratch, (int64_t)C, (int)P, step > 1, s))) return rc;
         if (b->C > 0) {
             k_adam<<<(int)((b->C + 255) / 256), 256, 0, s>>>(pa, pb, pt, b->cond_g, ga, gb, gt, mo, ve, b->C,
                                                              step, lr, 0.9f, 0.999f, 1e-8f);
             count_launch(ctx);
         }
     }
+    if (trace) RS_CUDA(cudaMemcpyAsync(loss_trace, trace, sizeof(float) * (size_t)steps * P, cudaMemcpyDeviceToHost, s));
+    uint32_t st = 0;
+    RS_CUDA(cudaMemcpyAsync(&st, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     RS_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        set_error("fine-tuning: %s", status_text(st).c_str());
+        return (st & ST_TOO_LARGE) ? RS_ERR_TOO_LARGE : RS_ERR_INVALID;
+    }
     return RS_OK;
 }
 

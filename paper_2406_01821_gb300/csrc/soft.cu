@@ -922,6 +922,30 @@ rs_status soft_step_known(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, cudaS
     return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream);
 }
 
+rs_status soft_validate(Ctx *ctx, const SoftArgs &a, int *maxR, int *maxC, cudaStream_t stream)
+{
+    const BatchDev &b = a.b;
+    if (b.P == 0) { *maxR = *maxC = 1; return RS_OK; }
+    int32_t *maxima = nullptr;
+    RS_CUDA(dev_alloc_async(&maxima, sizeof(int32_t) * 4, stream));
+    RS_CUDA(cudaMemsetAsync(maxima, 0, sizeof(int32_t) * 4, stream));
+    k_check_sets_soft<<<(b.P + 255) / 256, 256, 0, stream>>>(b, a.K, a.status, maxima, SOFT_MAX_RULES, SOFT_MAX_CONDS);
+    count_launch(ctx);
+    uint32_t *hs = host_status_slot();
+    if (!hs) { cudaFreeAsync(maxima, stream); return RS_ERR_OOM; }
+    RS_CUDA(cudaMemcpyAsync(hs, a.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    RS_CUDA(cudaMemcpyAsync(hs + 1, maxima, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, stream));
+    cudaFreeAsync(maxima, stream);
+    RS_CUDA(cudaStreamSynchronize(stream));
+    *maxR = std::max<int32_t>(1, (int32_t)hs[1]);
+    *maxC = std::max<int32_t>(1, (int32_t)hs[2]);
+    if (*hs) {
+        set_error("soft evaluation rejected the batch: %s", status_text(*hs).c_str());
+        return (*hs & ST_TOO_LARGE) ? RS_ERR_TOO_LARGE : RS_ERR_INVALID;
+    }
+    return RS_OK;
+}
+
 rs_status soft_step_scratch(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, void *scratch, int64_t cap_c,
                             int cap_p, bool repeat, cudaStream_t stream)
 {

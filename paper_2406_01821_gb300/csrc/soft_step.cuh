@@ -16,4 +16,9 @@ size_t soft_scratch_bytes(int64_t cap_c, int cap_p);
 rs_status soft_step_scratch(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, void *scratch, int64_t cap_c,
                             int cap_p, bool repeat, cudaStream_t stream);
 
+// Validation of a soft batch once, before a run of steps: the status word (RS_ERR_INVALID /
+// RS_ERR_TOO_LARGE as rs_eval_soft_fwd gives them) and the largest rule and condition counts of a
+// set, which size the steps. Waits for the stream.
+rs_status soft_validate(Ctx *ctx, const SoftArgs &a, int *maxR, int *maxC, cudaStream_t stream);
+
 }  // namespace rs

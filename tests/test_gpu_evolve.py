@@ -119,6 +119,24 @@ def test_finetune_matches_float64_adam(ctx, orc):
     assert np.allclose(got2[well], th[1][well], rtol=0, atol=1e-5)
 
 
+def test_finetune_rejects_malformed_batch_before_any_step(ctx):
+    """A batch naming a class outside 0..K-1 is refused by the one validation before the steps."""
+    import torch
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.two_class_gaussian(500, 4, 9)
+    b = synth.random_rulesets(synth.quantile_table(X), 2, 5, (1, 4), (1, 3), 9, pair_prob=0.3)
+    b.rule_class[2] = 2
+    ds = ctx.dataset(X, y, 2)
+    try:
+        db = rs.DeviceBatch.from_host(b)
+        with pytest.raises(rs.RsError) as e:
+            ctx.finetune(ds, db, 0.2, 1e-2, 5)
+        assert e.value.code == -1
+        torch.cuda.synchronize()
+    finally:
+        ctx.dataset_destroy(ds)
+
+
 @pytest.mark.parametrize("tune", [False, True])
 def test_checkpoint_resume_continues_exactly(ctx, tmp_path, tune):
     """A run of 7 generations equals 3 generations, a checkpoint written and read back, and 4 more
