@@ -329,6 +329,9 @@ typedef struct {
  * `pop` holds the initial population on entry and the final one (after `generations` steps) on
  * return. best / mean (host, may be NULL): best and mean correct count of each evaluated
  * generation, generations + 1 entries.
+ * Launch: a generation is captured once as a CUDA graph per (parity of the generation, fine-tuning
+ * or not) and replayed (RS_CTX_NO_GRAPH / RS_CTX_PROFILE: launched kernel by kernel, with the same
+ * results). Device memory for the run is allocated at entry and released at return.
  */
 rs_status rs_evolve(rs_ctx *ctx, uint64_t ds, const rs_evolve_config *cfg, rs_population *pop,
                     int32_t *best, double *mean, void *stream);
@@ -339,7 +342,9 @@ rs_status rs_evolve(rs_ctx *ctx, uint64_t ds, const rs_evolve_config *cfg, rs_po
  * gradients from rs_eval_soft_bwd. The structure comes from `batch` (device arrays; its cond_a,
  * cond_b, cond_t are not read); the parameters a, b, t (device float32[C]) are updated in place
  * (b only for pairs, t only for thresholds). loss_trace (host float32[steps*P], may be NULL)
- * receives the per-set loss before each step.
+ * receives the per-set loss before each step. The batch is validated once, before the first step
+ * (RS_ERR_INVALID / RS_ERR_TOO_LARGE as rs_eval_soft_fwd gives them, nothing updated); the steps
+ * then run without waiting for the host, which reads the trace and the status at the end.
  */
 rs_status rs_finetune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, float *a, float *b, float *t,
                       float tau, float lr, int32_t steps, float *loss_trace, void *stream);
