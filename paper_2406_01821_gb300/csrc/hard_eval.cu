@@ -341,6 +341,19 @@ int choose_groups(Ctx *ctx, const Dataset *ds, const TileConfig &tc, int P)
     int64_t gmax = std::max<int64_t>(1, P / (2 * tc.W));
     if (tiles * gmax < ctx->sm_count) gmax = std::max<int64_t>(1, (P + tc.W - 1) / tc.W);
     if (g > gmax) g = gmax;
+    // a launch of a few waves loses its last wave's idle SMs: among g .. 4g groups take the count
+    // whose last wave is fullest (one resident CTA per SM, as for the 32-warp evaluators)
+    const int64_t slots = ctx->sm_count;
+    if (tiles * g < 16 * slots) {
+        auto fill = [&](int64_t c) {
+            const int64_t ctas = tiles * c;
+            return (double)ctas / (double)(((ctas + slots - 1) / slots) * slots);
+        };
+        int64_t best = g;
+        for (int64_t c = g + 1; c <= std::min(gmax, 4 * g); ++c)
+            if (fill(c) > fill(best) + 1e-9) best = c;
+        g = best;
+    }
     if (g > 65535) g = 65535;
     return (int)g;
 }
