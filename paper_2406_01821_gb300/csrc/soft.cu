@@ -703,36 +703,47 @@ static int soft_tile_per_sm(Ctx *ctx, int tw, size_t per_warp, int F)
     return per_sm;
 }
 
-// One persistent wave of the soft kernel: the staged-tile form or the per-warp form, forward only
-// or forward + adjoint, with or without membership conditions (CAT). The staged-tile form takes
-// the number of warps per CTA that keeps the most warps resident for this batch's per-warp
-// arrays (ties: fewer warps per CTA, so that a CTA's sets are closer in size); small populations
-// keep at most P / 8 warps per CTA, since a CTA walks its sets in step and a wide CTA over few
-// sets of uneven size waits for the longest.
-template <bool CAT>
-static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bwd, int F, size_t smem,
-                               size_t per_warp, cudaStream_t stream)
-{
-    int per_sm = 1;
+// Launch shape of the soft kernel: warps per CTA (staged-tile form) and resident CTAs per SM.
+struct SoftShape {
     int tw = SOFT_TW_MIN;
-    size_t smem_tile = 0;
+    int per_sm = 1;
+};
+
+// The staged-tile form takes the number of warps per CTA that keeps the most warps resident for
+// this batch's per-warp arrays (ties: fewer warps per CTA, so that a CTA's sets are closer in
+// size); small populations keep at most P / 8 warps per CTA, since a CTA walks its sets in step
+// and a wide CTA over few sets of uneven size waits for the longest.
+template <bool CAT>
+static SoftShape soft_shape(Ctx *ctx, bool tiled, bool bwd, int F, size_t smem, size_t per_warp, int P)
+{
+    SoftShape sh;
     if (tiled) {
         int best = 0;
-        const int tw_max = std::max(SOFT_TW_MIN, std::min(SOFT_TW_MAX, k.P / 8));
+        const int tw_max = std::max(SOFT_TW_MIN, std::min(SOFT_TW_MAX, P / 8));
         for (int t = SOFT_TW_MIN; t <= tw_max; ++t) {
             const int c = bwd ? soft_tile_per_sm<true, CAT>(ctx, t, per_warp, F)
                               : soft_tile_per_sm<false, CAT>(ctx, t, per_warp, F);
-            if (c * t > best) { best = c * t; tw = t; per_sm = c; }
+            if (c * t > best) { best = c * t; sh.tw = t; sh.per_sm = c; }
         }
-        smem_tile = per_warp * tw + sizeof(float) * 2 * SOFT_G * (size_t)F;
     } else {
-        if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<true, CAT>, SOFT_W * 32, smem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_soft<false, CAT>, SOFT_W * 32, smem);
+        if (bwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh.per_sm, k_soft<true, CAT>, SOFT_W * 32, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh.per_sm, k_soft<false, CAT>, SOFT_W * 32, smem);
     }
-    const int grid = ctx->sm_count * std::max(1, per_sm);
+    sh.per_sm = std::max(1, sh.per_sm);
+    return sh;
+}
+
+// One persistent wave of the soft kernel: the staged-tile form or the per-warp form, forward only
+// or forward + adjoint, with or without membership conditions (CAT).
+template <bool CAT>
+static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bwd, int F, size_t smem,
+                               size_t per_warp, const SoftShape &sh, cudaStream_t stream)
+{
+    const int grid = ctx->sm_count * sh.per_sm;
     if (tiled) {
-        if (bwd) k_soft_tile<true, CAT><<<grid, tw * 32, smem_tile, stream>>>(k, F);
-        else k_soft_tile<false, CAT><<<grid, tw * 32, smem_tile, stream>>>(k, F);
+        const size_t smem_tile = per_warp * sh.tw + sizeof(float) * 2 * SOFT_G * (size_t)F;
+        if (bwd) k_soft_tile<true, CAT><<<grid, sh.tw * 32, smem_tile, stream>>>(k, F);
+        else k_soft_tile<false, CAT><<<grid, sh.tw * 32, smem_tile, stream>>>(k, F);
     } else {
         if (bwd) k_soft<true, CAT><<<grid, SOFT_W * 32, smem, stream>>>(k);
         else k_soft<false, CAT><<<grid, SOFT_W * 32, smem, stream>>>(k);
@@ -885,10 +896,34 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
             set_soft_attributes<false>(ctx);
             set_soft_attributes<true>(ctx);
         });
+        const SoftShape sh = b.cond_set ? soft_shape<true>(ctx, tiled, bwd, s.F, smem, per_warp, P)
+                                        : soft_shape<false>(ctx, tiled, bwd, s.F, smem, per_warp, P);
+        if (tiled) {
+            // The staged-tile kernel's CTAs take (set group, chunk) tasks until none is left. When
+            // the tasks make only a few rounds of the resident CTAs, the last round decides the
+            // time: take the chunk count (at most the one chosen above, whose partial sums the
+            // scratch holds) that minimises rounds x samples per chunk, preferring more chunks.
+            const int64_t set_groups = (P + sh.tw - 1) / sh.tw;
+            const int64_t workers = (int64_t)ctx->sm_count * sh.per_sm;
+            int64_t best_cost = INT64_MAX;
+            for (int n = 1; n <= k.nchunks; ++n) {
+                int64_t ch = (s.N + n - 1) / n;
+                ch = (ch + SOFT_G - 1) / SOFT_G * SOFT_G;
+                const int64_t nc = (s.N + ch - 1) / ch;
+                const int64_t cost = (set_groups * nc + workers - 1) / workers * ch;
+                if (cost < best_cost || (cost == best_cost && nc > nchunks)) {
+                    best_cost = cost;
+                    nchunks = (int)nc;
+                    chunk = ch;
+                }
+            }
+            k.nchunks = nchunks;
+            k.chunk = (int32_t)chunk;
+        }
         {
             TimedLaunch tl(ctx, TK_SOFT, stream);
-            if (b.cond_set) launch_soft_kernel<true>(ctx, k, tiled, bwd, s.F, smem, per_warp, stream);
-            else launch_soft_kernel<false>(ctx, k, tiled, bwd, s.F, smem, per_warp, stream);
+            if (b.cond_set) launch_soft_kernel<true>(ctx, k, tiled, bwd, s.F, smem, per_warp, sh, stream);
+            else launch_soft_kernel<false>(ctx, k, tiled, bwd, s.F, smem, per_warp, sh, stream);
         }
         if (bwd)                      // the gradients and (when asked) the loss in one launch
             k_soft_reduce_grad<<<P, 128, 0, stream>>>(part_ga, part_gbt, part_loss, nchunks, b.set_rule_off,
