@@ -160,13 +160,14 @@ typedef struct {
  *   preds      int32[P*N]   pred_p(n) at [p*N + n] in the caller's sample order; may be NULL
  * Outputs live in the memory space given by batch->mem (host buffers: the library copies).
  * Results are bit-identical to the plain definition (no FMA, no flush-to-zero).
- * Launch: packing and evaluation run as one CUDA graph cached per (dataset, tile configuration,
- * stream, output kinds); a call with the same pointers and sizes as the previous one on that
- * stream launches it again as it is, reading the arrays' current contents. Staging and scratch
- * memory belong to the cached graph and are kept until the dataset or the context is destroyed.
- * Calls from several host threads are safe, on one stream or on several. When the caller is
- * capturing `stream` (or the context has RS_CTX_NO_GRAPH / RS_CTX_PROFILE) the kernels are
- * enqueued directly instead.
+ * Launch: on a stream the caller created, packing and evaluation run as one CUDA graph cached per
+ * (dataset, tile configuration, stream, output kinds); a call with the same pointers and sizes as
+ * the previous one on that stream launches it again as it is, reading the arrays' current
+ * contents. Staging and scratch memory belong to the cached graph and are kept until the dataset
+ * or the context is destroyed. On the legacy default stream (NULL), on a stream the caller is
+ * capturing, and in RS_CTX_NO_GRAPH / RS_CTX_PROFILE contexts the kernels are enqueued directly
+ * with per-call scratch from the stream-ordered pool. Calls from several host threads are safe,
+ * on one stream or on several.
  * Errors: RS_ERR_INVALID (malformed batch: nothing is counted, outputs undefined),
  *         RS_ERR_TOO_LARGE (a rule of more than 4095 conditions; outputs undefined),
  *         RS_ERR_NOT_FOUND (ds), RS_ERR_OOM, RS_ERR_DEVICE.

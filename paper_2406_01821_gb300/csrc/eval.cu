@@ -455,13 +455,15 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
     if (b->R > 0 && ds->K > 4096) return RS_ERR_UNSUPPORTED;
 
     const int tid = tile_override >= 0 ? tile_override : pick_tile(ctx, *ds, b);
-    // The cached graph (captured on a stream of its own, launched on the caller's, the legacy
-    // default stream included) unless the caller is capturing this stream: then the work is
-    // enqueued directly and joins the caller's graph.
+    // The cached graph (captured on a stream of its own, launched on the caller's) on streams the
+    // caller created. Calls on the legacy default stream launch directly with scratch from the
+    // stream-ordered pool: callers that use it for one-off calls of ever-changing shapes would pay
+    // a capture per call and hold per-dataset buffers. A stream the caller is capturing also gets
+    // the direct launches, which then join the caller's graph.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (stream) RS_CUDA(cudaStreamIsCapturing(stream, &cap));
     const bool use_graph = !(ctx->flags & (RS_CTX_NO_GRAPH | RS_CTX_PROFILE)) && tile_override < 0 &&
-                           cap == cudaStreamCaptureStatusNone;
+                           stream != nullptr && cap == cudaStreamCaptureStatusNone;
     if (use_graph) return eval_hard_graph(ctx, ds_h, ds.get(), tid, b, correct, per_class, preds, stream);
 
     const bool host = b->mem == RS_MEM_HOST;
