@@ -161,9 +161,10 @@ typedef struct {
  * Outputs live in the memory space given by batch->mem (host buffers: the library copies).
  * Results are bit-identical to the plain definition (no FMA, no flush-to-zero).
  * Launch: on a stream the caller created, packing and evaluation run as one CUDA graph cached per
- * (dataset, tile configuration, stream, output kinds); a call with the same pointers and sizes as
- * the previous one on that stream launches it again as it is, reading the arrays' current
- * contents. Staging and scratch memory belong to the cached graph and are kept until the dataset
+ * (dataset, tile configuration, stream, output kinds). A call whose sizes and device pointers
+ * repeat the previous call's on that stream is captured, and later calls with them launch the
+ * graph as it is, reading the arrays' current contents; a shape seen for the first time runs
+ * directly. Staging and scratch memory of the graph belong to it and are kept until the dataset
  * or the context is destroyed. On the legacy default stream (NULL), on a stream the caller is
  * capturing, and in RS_CTX_NO_GRAPH / RS_CTX_PROFILE contexts the kernels are enqueued directly
  * with per-call scratch from the stream-ordered pool. Calls from several host threads are safe,

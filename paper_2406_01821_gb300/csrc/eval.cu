@@ -272,8 +272,46 @@ rs_status enqueue_hard_dev_sizes(Ctx *ctx, Dataset *ds, const TileConfig &tc, Ba
 // on an entry (its mutex), so calls on one stream from several host threads stay correct. The
 // capture runs on a stream of the entry's own, never on the caller's: a stream in capture mode
 // would take in whatever another host thread enqueues on it meanwhile.
+// What a call passes that a captured graph bakes in, apart from the entry's own buffers: sizes,
+// and the caller's device pointers (device batches and device outputs; host arrays are staged
+// through the entry's buffers, so only their sizes count).
+struct CallShape {
+    int32_t P = 0, R = 0, C = 0;
+    bool host = false;
+    const void *arrays[11] = {};
+    const void *outputs[3] = {};
+    bool operator==(const CallShape &o) const
+    {
+        if (P != o.P || R != o.R || C != o.C || host != o.host) return false;
+        for (int i = 0; i < 11; ++i)
+            if (arrays[i] != o.arrays[i]) return false;
+        for (int i = 0; i < 3; ++i)
+            if (outputs[i] != o.outputs[i]) return false;
+        return true;
+    }
+};
+
+static CallShape call_shape(const rs_batch *b, const int32_t *correct, const int32_t *per_class,
+                            const int32_t *preds)
+{
+    CallShape c;
+    c.P = b->P; c.R = b->R; c.C = b->C;
+    c.host = b->mem == RS_MEM_HOST;
+    if (!c.host) {
+        const void *a[11] = {b->set_rule_off, b->rule_cond_off, b->rule_class, b->set_default, b->cond_f,
+                             b->cond_g, b->cond_op, b->cond_a, b->cond_b, b->cond_t, b->cond_set};
+        for (int i = 0; i < 11; ++i) c.arrays[i] = a[i];
+        c.outputs[0] = correct; c.outputs[1] = per_class; c.outputs[2] = preds;
+    }
+    return c;
+}
+
 struct GraphEntry {
     std::mutex mu;
+    CallShape last{};                // the previous call's shape on this entry
+    bool has_last = false;
+    CallShape captured{};            // the shape the executable holds
+    bool has_captured = false;
     cudaStream_t capture = nullptr;
     cudaGraphExec_t exec = nullptr;
     int kernels = 0;                 // kernel nodes of the executable (launch accounting on replay)
@@ -351,6 +389,30 @@ static void device_outputs(const Scratch &s, const rs_batch *b, const Dataset &d
     if (d_preds) d_preds = (int32_t *)p;
 }
 
+// Kernels enqueued directly on the caller's stream, staging and scratch from the stream-ordered
+// pool for this call only.
+static rs_status eval_hard_direct(Ctx *ctx, Dataset *ds, int tid, const rs_batch *b, int32_t *correct,
+                                  int32_t *per_class, int32_t *preds, cudaStream_t stream)
+{
+    rs_status rc;
+    const bool host = b->mem == RS_MEM_HOST;
+    StagedBatch sb;
+    if ((rc = stage_batch(b, stream, sb))) return rc;
+    Scratch s;
+    if ((rc = alloc_scratch(sb.d, host, ds->K, ds->N, per_class != nullptr, preds != nullptr, stream, s))) {
+        if (sb.buf) cudaFreeAsync(sb.buf, stream);
+        return rc;
+    }
+    int32_t *d_correct = correct, *d_pc = per_class, *d_preds = preds;
+    device_outputs(s, b, *ds, host, d_correct, d_pc, d_preds);
+    rc = enqueue_hard(ctx, ds, tile_config(tid), sb.d, s, d_correct, d_pc, d_preds, stream);
+    if (!rc && host) rc = copy_outputs_to_host(b, *ds, correct, per_class, preds, d_correct, d_pc, d_preds, stream);
+    if (!rc) rc = finish_status(ctx, s.status, stream);
+    cudaFreeAsync(s.recs, stream);
+    if (sb.buf) cudaFreeAsync(sb.buf, stream);
+    return rc;
+}
+
 // The graph path of eval_hard: staging and scratch live in the cached entry, and a call with
 // the same arguments as the last capture is a single graph launch.
 static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, const rs_batch *b,
@@ -370,6 +432,15 @@ static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, 
         ge = slot;
     }
     std::lock_guard<std::mutex> call(ge->mu);
+    // A shape seen for the first time (not the captured one, not the previous call's) runs
+    // directly; it is captured when the next call repeats it. Callers whose shapes change from
+    // call to call so never pay for a capture.
+    const CallShape shape = call_shape(b, correct, per_class, preds);
+    const bool known = ge->exec && ge->has_captured && ge->captured == shape;
+    const bool repeated = ge->has_last && ge->last == shape;
+    ge->last = shape;
+    ge->has_last = true;
+    if (!known && !repeated) return eval_hard_direct(ctx, ds, tid, b, correct, per_class, preds, stream);
     rs_status rc;
     BatchDev bd;
     if (host) {
@@ -434,6 +505,8 @@ static rs_status eval_hard_graph(Ctx *ctx, uint64_t ds_h, Dataset *ds, int tid, 
         ge->bd = bd;
         ge->correct = d_correct; ge->per_class = d_pc; ge->preds = d_preds;
         ge->scratch_at = ge->scratch;
+        ge->captured = shape;
+        ge->has_captured = true;
         RS_CUDA(cudaGraphLaunch(ge->exec, stream));
     }
     if (host && (rc = copy_outputs_to_host(b, *ds, correct, per_class, preds, d_correct, d_pc, d_preds, stream)))
@@ -466,22 +539,7 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
                            stream != nullptr && cap == cudaStreamCaptureStatusNone;
     if (use_graph) return eval_hard_graph(ctx, ds_h, ds.get(), tid, b, correct, per_class, preds, stream);
 
-    const bool host = b->mem == RS_MEM_HOST;
-    StagedBatch sb;
-    if ((rc = stage_batch(b, stream, sb))) return rc;
-    Scratch s;
-    if ((rc = alloc_scratch(sb.d, host, ds->K, ds->N, per_class != nullptr, preds != nullptr, stream, s))) {
-        if (sb.buf) cudaFreeAsync(sb.buf, stream);
-        return rc;
-    }
-    int32_t *d_correct = correct, *d_pc = per_class, *d_preds = preds;
-    device_outputs(s, b, *ds, host, d_correct, d_pc, d_preds);
-    rc = enqueue_hard(ctx, ds.get(), tile_config(tid), sb.d, s, d_correct, d_pc, d_preds, stream);
-    if (!rc && host) rc = copy_outputs_to_host(b, *ds, correct, per_class, preds, d_correct, d_pc, d_preds, stream);
-    if (!rc) rc = finish_status(ctx, s.status, stream);
-    cudaFreeAsync(s.recs, stream);
-    if (sb.buf) cudaFreeAsync(sb.buf, stream);
-    return rc;
+    return eval_hard_direct(ctx, ds.get(), tid, b, correct, per_class, preds, stream);
 }
 
 // Synchronous contexts: wait and report the device status word of this call. Asynchronous

@@ -401,10 +401,10 @@ def test_maximum_sizes(ctx, orc):
 
 
 def test_graph_replay_reads_current_contents(ctx, orc):
-    """A call whose pointers and sizes equal the previous call's on the same stream replays the
-    cached graph without capturing again; it must still read the batch's current contents (device
-    arrays rewritten in place, host arrays staged again) and write the current outputs. Then a
-    batch of another size (captured again) and the first one once more."""
+    """On a caller's stream a call shape runs directly the first time, is captured when the next
+    call repeats it, and is replayed after that; every path must read the batch's current contents
+    (device arrays rewritten in place, host arrays staged again) and write the current outputs, and
+    count the same kernels. Then batches of other sizes and the first one again."""
     import copy
     import torch
     from paper_2406_01821_gb300 import rs
