@@ -395,26 +395,6 @@ __global__ void k_gather_len(const int32_t *len, const int32_t *subset, int n, i
 
 // ---------------------------------------------------------------- tuning
 
-// Adam on the trainable parameters of each condition: a always, b for pairs, t for thresholds.
-__global__ void k_adam(float *a, float *b, float *t, const int32_t *g_is_pair_src, const float *ga,
-                       const float *gb, const float *gt, float *m, float *v, int C, int step,
-                       float lr, float b1, float b2, float eps)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    const bool pair = g_is_pair_src[c] >= 0;
-    const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
-    float *ps[2] = {a, pair ? b : t};
-    const float gs[2] = {ga[c], pair ? gb[c] : gt[c]};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        float &mk = m[2 * c + k], &vk = v[2 * c + k];
-        mk = b1 * mk + (1.0f - b1) * gs[k];
-        vk = b2 * vk + (1.0f - b2) * gs[k] * gs[k];
-        const float mh = mk / bc1, vh = vk / bc2;
-        ps[k][c] -= lr * mh / (sqrtf(vh) + eps);
-    }
-}
 
 // Fine-tuning refines fitness and never lowers it: a tuned set keeps the better of its fitness
 // before and after tuning; `improved` marks the sets whose tuned coefficients did better.
@@ -666,12 +646,13 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
             sa.Xt = ds.Xt; sa.y = ds.y; sa.perm = ds.perm; sa.N = ds.N; sa.n_pad = ds.n_pad;
             sa.F = ds.F; sa.K = ds.K; sa.tau = cfg->tau; sa.loss = loss; sa.dloss = dl;
             sa.grad_a = ga; sa.grad_b = gb; sa.grad_t = gt; sa.status = sc.status;
+            SoftAdam adam;                                      // applied by the gradient reduction
+            adam.a = ta; adam.b = tb; adam.t = tt; adam.m = mo; adam.v = ve; adam.lr = cfg->lr;
             for (int step = 1; step <= cfg->tune_steps; ++step) {
-                if ((grc = soft_step_scratch(ctx, sa, RMAX, RMAX * CMAX, soft_scratch, soft_cap_c, T, step > 1, st)))
+                adam.step = step;
+                if ((grc = soft_step_scratch(ctx, sa, RMAX, RMAX * CMAX, soft_scratch, soft_cap_c, T, step > 1,
+                                             &adam, st)))
                     return grc;
-                k_adam<<<(int)((TC + 255) / 256), 256, 0, st>>>(ta, tb, tt, w.o.cond_g, ga, gb, gt, mo, ve,
-                                                               (int)TC, step, cfg->lr, 0.9f, 0.999f, 1e-8f);
-                count_launch(ctx);
             }
             // tuned fitness of the T sets (hard evaluation with the tuned coefficients)
             RS_CUDA(cudaMemcpyAsync(w.o.cond_a, ta, 4 * TC, cudaMemcpyDeviceToDevice, st));
@@ -818,14 +799,14 @@ rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, fl
     if ((rc = B.get(reinterpret_cast<char **>(&scratch), soft_scratch_bytes((int64_t)C, (int)P))) ||
         (loss_trace && (rc = B.get(&trace, (size_t)steps * P))))
         return rc;
+    SoftAdam adam;                                              // applied by the gradient reduction
+    adam.a = pa; adam.b = pb; adam.t = pt; adam.m = mo; adam.v = ve; adam.lr = lr;
     for (int step = 1; step <= steps; ++step) {
         sa.loss = trace ? trace + (size_t)(step - 1) * P : loss;
-        if ((rc = soft_step_scratch(ctx, sa, maxR, maxC, scratch, (int64_t)C, (int)P, step > 1, s))) return rc;
-        if (b->C > 0) {
-            k_adam<<<(int)((b->C + 255) / 256), 256, 0, s>>>(pa, pb, pt, b->cond_g, ga, gb, gt, mo, ve, b->C,
-                                                             step, lr, 0.9f, 0.999f, 1e-8f);
-            count_launch(ctx);
-        }
+        adam.step = step;
+        if ((rc = soft_step_scratch(ctx, sa, maxR, maxC, scratch, (int64_t)C, (int)P, step > 1,
+                                    b->C > 0 ? &adam : nullptr, s)))
+            return rc;
     }
     if (trace) RS_CUDA(cudaMemcpyAsync(loss_trace, trace, sizeof(float) * (size_t)steps * P, cudaMemcpyDeviceToHost, s));
     uint32_t st = 0;

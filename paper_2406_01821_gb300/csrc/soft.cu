@@ -649,17 +649,32 @@ __global__ void k_soft_reduce_loss(const float *part_loss, int nchunks, int P, f
     loss[p] = tree_sum_strided(part_loss + p, P, nchunks) * inv_n;
 }
 
+// One Adam update of parameter *p with gradient g and moments *m, *v; every operation separately
+// rounded, so that the result does not depend on the file's contraction setting.
+__device__ __forceinline__ void adam_one(float *p, float g, float *m, float *v, float bc1, float bc2,
+                                         const SoftAdam &ad)
+{
+    const float mk = __fadd_rn(__fmul_rn(ad.b1, *m), __fmul_rn(1.0f - ad.b1, g));
+    const float vk = __fadd_rn(__fmul_rn(ad.b2, *v), __fmul_rn(__fmul_rn(1.0f - ad.b2, g), g));
+    *m = mk;
+    *v = vk;
+    const float mh = __fdiv_rn(mk, bc1), vh = __fdiv_rn(vk, bc2);
+    *p = __fsub_rn(*p, __fdiv_rn(__fmul_rn(ad.lr, mh), __fadd_rn(sqrtf(vh), ad.eps)));
+}
+
 // One CTA per set, its threads looping over the set's conditions (grads scaled by dloss[p] / N);
-// thread 0 also writes the set's loss when `loss` is given.
+// thread 0 also writes the set's loss when `loss` is given; with adam.a the Adam update of the
+// set's conditions follows at once.
 __global__ void k_soft_reduce_grad(const float *part_ga, const float *part_gbt, const float *part_loss,
                                    int nchunks, const int32_t *set_rule_off, const int32_t *rule_cond_off,
                                    const SoftRec *recs, int P, int64_t C, const float *dloss,
                                    float inv_n, float *grad_a, float *grad_b, float *grad_t, float *loss,
-                                   const uint32_t *status)
+                                   SoftAdam adam, const uint32_t *status)
 {
     const int p = blockIdx.x;
     if (p >= P || *status) return;
     if (loss && threadIdx.x == 0) loss[p] = tree_sum_strided(part_loss + p, P, nchunks) * inv_n;
+    const float bc1 = 1.0f - powf(adam.b1, (float)adam.step), bc2 = 1.0f - powf(adam.b2, (float)adam.step);
     const int cb = rule_cond_off[set_rule_off[p]], ce = rule_cond_off[set_rule_off[p + 1]];
     const float scale = dloss[p] * inv_n;
     for (int c = cb + threadIdx.x; c < ce; c += blockDim.x) {
@@ -669,6 +684,10 @@ __global__ void k_soft_reduce_grad(const float *part_ga, const float *part_gbt, 
         grad_a[c] = ga;
         grad_b[c] = pair ? gbt : 0.f;
         grad_t[c] = pair ? 0.f : gbt;
+        if (adam.a) {
+            adam_one(adam.a + c, ga, adam.m + 2 * c, adam.v + 2 * c, bc1, bc2, adam);
+            adam_one((pair ? adam.b : adam.t) + c, gbt, adam.m + 2 * c + 1, adam.v + 2 * c + 1, bc1, bc2, adam);
+        }
     }
 }
 
@@ -779,7 +798,7 @@ size_t soft_scratch_bytes(int64_t cap_c, int cap_p)
 // `repeat`: a later step on the caller's scratch over the same structure as the step before it
 // (only coefficients and thresholds changed), whose validation and set order still stand.
 static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known_maxC, cudaStream_t stream,
-                          char *pre = nullptr, bool repeat = false)
+                          char *pre = nullptr, bool repeat = false, const SoftAdam *adam = nullptr)
 {
     const BatchDev &b = s.b;
     const int P = b.P;
@@ -929,7 +948,7 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
             k_soft_reduce_grad<<<P, 128, 0, stream>>>(part_ga, part_gbt, part_loss, nchunks, b.set_rule_off,
                                                      b.rule_cond_off, recs, P, Ccap, s.dloss,
                                                      1.0f / (float)s.N, s.grad_a, s.grad_b, s.grad_t,
-                                                     s.loss, s.status);
+                                                     s.loss, adam ? *adam : SoftAdam{}, s.status);
         else
             k_soft_reduce_loss<<<(P + 255) / 256, 256, 0, stream>>>(part_loss, nchunks, P,
                                                                    1.0f / (float)s.N, s.loss, s.status);
@@ -982,13 +1001,18 @@ rs_status soft_validate(Ctx *ctx, const SoftArgs &a, int *maxR, int *maxC, cudaS
 }
 
 rs_status soft_step_scratch(Ctx *ctx, const SoftArgs &a, int maxR, int maxC, void *scratch, int64_t cap_c,
-                            int cap_p, bool repeat, cudaStream_t stream)
+                            int cap_p, bool repeat, const SoftAdam *adam, cudaStream_t stream)
 {
+    if (adam && !a.dloss) {
+        set_error("soft step: an Adam update needs the adjoint");
+        return RS_ERR_INVALID;
+    }
     if (!scratch || a.b.P > cap_p || std::max<int64_t>(a.b.C, 1) > std::max<int64_t>(cap_c, 1)) {
         set_error("soft step: scratch smaller than the batch");
         return RS_ERR_INVALID;
     }
-    return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream, static_cast<char *>(scratch), repeat);
+    return soft_run(ctx, a, std::max(1, maxR), std::max(1, maxC), stream, static_cast<char *>(scratch), repeat,
+                    adam);
 }
 
 // Load the kernels of this file now (CUDA loads a kernel lazily at its first launch, which would
