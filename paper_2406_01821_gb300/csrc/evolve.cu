@@ -52,9 +52,12 @@ struct Rng {
     uint64_t seed, gen, child, i;
     uint64_t blk[4];
     uint64_t cached = ~0ull;
+    const uint64_t *pre = nullptr;   // blocks 0 .. npre-1 of this stream, computed ahead (4 words each)
+    uint64_t npre = 0;
     __device__ uint64_t next()
     {
         const uint64_t b = i >> 2;
+        if (b < npre) return pre[4 * b + (i++ & 3)];
         if (b != cached) {
             philox4x64_10(b, child, gen, 0, seed, 0x65766f6cull, blk);
             cached = b;
@@ -244,9 +247,13 @@ __device__ void mutate(Rng &r, const PopDev &o, int c, const DataView &d)
 // One warp per child: copies in parallel, random decisions on lane 0.
 // gen = gen0 + *gidx: the generation index is read on the device, so that one captured graph
 // serves every generation.
-__global__ void k_next_generation(PopDev in, const int32_t *fit, const int32_t *order, PopDev out,
-                                  uint64_t seed, uint64_t gen0, const int64_t *gidx, int elite, DataView d)
+constexpr int NEXT_GEN_THREADS = 256;   // k_next_generation's block: 8 warps, one child each
+
+__global__ void __launch_bounds__(NEXT_GEN_THREADS) k_next_generation(PopDev in, const int32_t *fit, const int32_t *order,
+                                                                     PopDev out, uint64_t seed, uint64_t gen0,
+                                                                     const int64_t *gidx, int elite, DataView d)
 {
+    __shared__ uint64_t pre_all[NEXT_GEN_THREADS / 32][32 * 4];
     const uint64_t gen = gen0 + (uint64_t)*gidx;
     const int lane = threadIdx.x & 31;
     const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -254,7 +261,20 @@ __global__ void k_next_generation(PopDev in, const int32_t *fit, const int32_t *
     const int P = in.P;
     int A = 0, B = 0;
     uint32_t take_b = 0;
+    // The child's draws are made by lane 0 one after another; the first 32 Philox blocks of its
+    // stream (128 draws, more than a child usually takes) are computed ahead by the 32 lanes at
+    // once. Same numbers, same order of use.
+    uint64_t *pre = pre_all[threadIdx.x >> 5];
+    {
+        uint64_t blk[4];
+        philox4x64_10((uint64_t)lane, (uint64_t)c, gen, 0, seed, 0x65766f6cull, blk);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pre[4 * lane + k] = blk[k];
+    }
+    __syncwarp();
     Rng r{seed, gen, (uint64_t)c, 0};
+    r.pre = pre;
+    r.npre = 32;
     if (c < elite) {
         A = order[c];
     } else if (lane == 0) {
@@ -675,9 +695,8 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
             k_rank<<<(P + 255) / 256, 256, 0, st>>>(fit, P, order);
             count_launch(ctx);
         }
-        k_next_generation<<<(P * 32 + 255) / 256, 256, 0, st>>>(in, fit, order, pop[par ^ 1], cfg->seed,
-                                                                (uint64_t)cfg->first_generation, gslot + par,
-                                                                cfg->elite, dv);
+        k_next_generation<<<(P * 32 + NEXT_GEN_THREADS - 1) / NEXT_GEN_THREADS, NEXT_GEN_THREADS, 0, st>>>(
+            in, fit, order, pop[par ^ 1], cfg->seed, (uint64_t)cfg->first_generation, gslot + par, cfg->elite, dv);
         count_launch(ctx);
         RS_CUDA(cudaGetLastError());
         return RS_OK;
