@@ -337,32 +337,36 @@ struct CsrDev {
     int32_t *cond_slot;    // flat slot index of each CSR condition (for parameter write-back)
 };
 
-// Set w of the batch (slot subset[w], or w) written by one warp at its scanned offsets.
+// Set w of the batch (slot subset[w], or w) written by one warp at its scanned offsets: lane j
+// takes rule j (a set has at most 32 rules), the rules' condition offsets from a warp scan of
+// their counts, so that no lane waits on another's loads. The whole warp calls it.
 __device__ void scatter_set(const PopDev &p, const int32_t *set_first_rule, const int32_t *set_first_cond,
                             const int32_t *subset, int w, const CsrDev &o, int lane)
 {
     const int i = subset ? subset[w] : w;
     const int nr = p.nrule[i];
     const int r0 = set_first_rule[w];
-    int c = set_first_cond[w];
     if (lane == 0) {
         o.set_rule_off[w] = r0;
         o.set_default[w] = p.deflt[i];
     }
-    for (int j = 0; j < nr; ++j) {
-        const int64_t rj = (int64_t)i * p.RMAX + j;
-        const int nc = p.ncond[rj];
-        if (lane == 0) {
-            o.rule_cond_off[r0 + j] = c;
-            o.rule_class[r0 + j] = p.rcls[rj];
-        }
-        for (int k = lane; k < nc; k += 32) {
+    const int64_t rj = (int64_t)i * p.RMAX + lane;
+    const int nc = lane < nr ? p.ncond[rj] : 0;
+    int x = nc;
+    for (int s = 1; s < 32; s <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, s);
+        if (lane >= s) x += y;
+    }
+    if (lane < nr) {
+        const int c = set_first_cond[w] + x - nc;
+        o.rule_cond_off[r0 + lane] = c;
+        o.rule_class[r0 + lane] = p.rcls[rj];
+        for (int k = 0; k < nc; ++k) {
             const int64_t q = rj * p.CMAX + k;
             o.cond_f[c + k] = p.cf[q]; o.cond_g[c + k] = p.cg[q]; o.cond_op[c + k] = p.cop[q];
             o.cond_a[c + k] = p.ca[q]; o.cond_b[c + k] = p.cb[q]; o.cond_t[c + k] = p.ct[q];
             if (o.cond_slot) o.cond_slot[c + k] = (int32_t)q;
         }
-        c += nc;
     }
 }
 
@@ -565,6 +569,25 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
     }
     rs_status rc = device_guard(ctx);
     if (rc) return rc;
+    // the slot counts bound every read of the slot arrays: check them before anything runs (the
+    // rest of a genome, features, classes and operators, is validated by the packing)
+    if (!hp->nrule || !hp->deflt || !hp->rcls || !hp->ncond || !hp->cf || !hp->cg || !hp->cop || !hp->ca ||
+        !hp->cb || !hp->ct) {
+        set_error("evolution: a population array is NULL");
+        return RS_ERR_INVALID;
+    }
+    for (int q = 0; q < P; ++q) {
+        const int32_t nr = hp->nrule[q];
+        bool ok = nr >= 0 && nr <= RMAX;
+        for (int j = 0; ok && j < nr; ++j) {
+            const int32_t nc = hp->ncond[(size_t)q * RMAX + j];
+            ok = nc >= 0 && nc <= CMAX;
+        }
+        if (!ok) {
+            set_error("evolution: set %d has a rule or condition count outside 0..RMAX / 0..CMAX", q);
+            return RS_ERR_INVALID;
+        }
+    }
     EvolveBuffers B;
     PopDev pop[2];
     if ((rc = alloc_pop(B, pop[0], P, RMAX, CMAX)) || (rc = alloc_pop(B, pop[1], P, RMAX, CMAX))) return rc;

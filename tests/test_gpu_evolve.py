@@ -191,3 +191,23 @@ def test_captured_generations_equal_direct_launches(ctx, lamarckian):
     for k in ga:
         assert np.array_equal(ga[k], da[k]), k
     assert np.array_equal(gfit, dfit) and np.array_equal(gbest, dbest) and np.array_equal(gmean, dmean)
+
+
+@pytest.mark.parametrize("what", ["nrule", "ncond"])
+def test_population_counts_checked_before_any_kernel(ctx, what):
+    """A slot count beyond RMAX / CMAX (which would send the slot readers past a set's row) is
+    refused with RS_ERR_INVALID before anything runs."""
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.two_class_gaussian(400, 4, 12)
+    pop = synth.initial_population(X, y, 2, 16, RMAX=4, CMAX=3, seed=12)
+    if what == "nrule":
+        pop["nrule"][15] = 5
+    else:
+        pop["ncond"][15, 0] = 4
+    ds = ctx.dataset(X, y, 2)
+    try:
+        with pytest.raises(rs.RsError) as e:
+            ctx.evolve(ds, pop, generations=2, elite=1, seed=12)
+        assert e.value.code == -1
+    finally:
+        ctx.dataset_destroy(ds)
