@@ -334,6 +334,10 @@ typedef struct {
  * Launch: a generation is captured once as a CUDA graph per (parity of the generation, fine-tuning
  * or not) and replayed (RS_CTX_NO_GRAPH / RS_CTX_PROFILE: launched kernel by kernel, with the same
  * results). Device memory for the run is allocated at entry and released at return.
+ * Errors: RS_ERR_INVALID for a bad configuration, a NULL population array or a set whose rule
+ * count is outside 0..RMAX or a live rule's condition count outside 0..CMAX (checked on the host
+ * before anything runs); features, classes and operators out of range are reported by the
+ * device validation at the end of the run.
  */
 rs_status rs_evolve(rs_ctx *ctx, uint64_t ds, const rs_evolve_config *cfg, rs_population *pop,
                     int32_t *best, double *mean, void *stream);
