@@ -703,6 +703,11 @@ def run_reference(args, d: Dist):
     print(json.dumps(line), flush=True)
 
 
+def parse_skip(text: str) -> set:
+    """Names of the extra legs to skip, from a comma-separated list (whole names only)."""
+    return {x.strip() for x in (text or "").split(",") if x.strip()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -762,7 +767,7 @@ def main():
              if counters and "issue_active_pct" in counters else None)
     extras = {}
     if not args.no_extras and d.rank == 0:
-        skip = {x.strip() for x in args.skip.split(",") if x.strip()}
+        skip = parse_skip(args.skip)
         for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("paper_evolution", paper_evolution_leg),
                           ("serving", serving_leg), ("categorical", categorical_leg), ("plain", plain_leg)):
             if name in skip:

@@ -40,3 +40,11 @@ def test_operation_counts_closed_forms():
     # 3 transcendentals per condition and sample, 11 per rule and sample
     assert bench.soft_transcendentals(b, N) == N * (3 * 3 + 11 * 2)
     assert np.isclose(bench.hard_algorithmic_ops(b, 32) / 32, 5 + 6 / 32)
+
+
+def test_skip_list_matches_whole_leg_names():
+    import bench
+    assert bench.parse_skip("paper_evolution") == {"paper_evolution"}
+    assert "evolution" not in bench.parse_skip("paper_evolution, serving")
+    assert bench.parse_skip("soft,evolution,") == {"soft", "evolution"}
+    assert bench.parse_skip("") == set()
