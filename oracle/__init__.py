@@ -164,7 +164,8 @@ def planted(plant: int):
     import types
     h = _load(build(plant=plant))
     return types.SimpleNamespace(eval_hard=functools.partial(eval_hard, _h=h),
-                                 soft=functools.partial(soft, _h=h), build=build)
+                                 soft=functools.partial(soft, _h=h),
+                                 evolve_step=functools.partial(evolve_step, _h=h), build=build)
 
 
 # ------------------------------------------------------------------------------ evolution
@@ -195,7 +196,7 @@ def philox4x64_10(ctr, key):
     return out
 
 
-def evolve_step(pop, fit, seed, gen, elite, X, K):
+def evolve_step(pop, fit, seed, gen, elite, X, K, _h=None):
     """One generation (tournament selection, crossover, mutation with randomized coefficients).
     ``pop`` is a dict of slot arrays (see POP_FIELDS; condition arrays are [P, RMAX, CMAX])."""
     cin, keep_in = _cpop(pop)
@@ -203,7 +204,7 @@ def evolve_step(pop, fit, seed, gen, elite, X, K):
     cout, keep_out = _cpop(out)
     fit = np.ascontiguousarray(fit, np.int32)
     X = np.ascontiguousarray(X, np.float32)
-    rc = lib().orc_evolve_step(ctypes.byref(cin), _ptr(fit), ctypes.byref(cout), ctypes.c_uint64(seed),
+    rc = (_h or lib()).orc_evolve_step(ctypes.byref(cin), _ptr(fit), ctypes.byref(cout), ctypes.c_uint64(seed),
                                ctypes.c_uint64(gen), ctypes.c_int32(elite), _ptr(X),
                                ctypes.c_int64(X.shape[0]), ctypes.c_int32(X.shape[1]),
                                ctypes.c_int32(K))

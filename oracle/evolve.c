@@ -27,6 +27,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* ORC_PLANT selects a deliberately wrong variant, built only by the test that checks that the
+ * pins catch it (0 = the oracle as stated). */
+#ifndef ORC_PLANT
+#define ORC_PLANT 0
+#endif
+
 typedef struct {
     int32_t P, RMAX, CMAX;
     int32_t *nrule;    /* [P] */
@@ -88,6 +94,9 @@ typedef struct {
 static float data_draw(rng_t *r, const orc_data *d, int32_t f)
 {
     int64_t n = (int64_t)(((next64(r) >> 32) * (uint64_t)d->N) >> 32);
+#if ORC_PLANT == 11
+    f = (f + 1) % d->F;                      /* planted: threshold drawn from the wrong feature */
+#endif
     return d->X[n * d->F + f];
 }
 
@@ -166,6 +175,9 @@ static void mutate(rng_t *r, indiv_t *v, const orc_data *d, int32_t RMAX, int32_
 {
     int32_t type = uniform_int(r, 8);
     int32_t j, k;
+#if ORC_PLANT == 10
+    if (type == 3) type = 4;                 /* planted: add-condition never chosen */
+#endif
     cond_t *c;
     switch (type) {
     case 0:                                  /* randomized coefficients */

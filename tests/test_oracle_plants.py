@@ -4,6 +4,7 @@ import pytest
 
 import oracle
 import test_oracle_categorical as cat
+import test_oracle_evolve as evo
 import test_oracle_pins as pins
 
 # plant id -> (description, pin calls that must not all pass)
@@ -23,6 +24,8 @@ PLANTS = {
          lambda o: cat.test_mixed_rulesets_match_isin_formulation(o, 0)]),
     9: ("category bits read in the wrong order", [lambda o: cat.test_membership_bit_order(o),
                                                    lambda o: cat.test_single_code_equals_band(o)]),
+    10: ("evolution never adds a condition", [lambda o: evo.check_operator_mix(o)]),
+    11: ("threshold drawn from the wrong feature", [lambda o: evo.check_thresholds_from_data(o)]),
 }
 
 
