@@ -211,16 +211,21 @@ rs_status rs_eval_soft_bwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, floa
  * a real-time loop that may not block in an allocator. It computes exactly what rs_eval_hard
  * computes, with the per-call scratch taken from one fixed array of RS_STATIC_SCRATCH_BYTES that
  * lives in the library's device image (every GPU that loads the library holds it until exit).
- *   batch   device arrays only (batch->mem must be RS_MEM_DEVICE); outputs are device memory
- *   limit   16*C + 20*P + 768 bytes (each part rounded up to 256 B) must fit in the array,
- *           otherwise RS_ERR_TOO_LARGE with a message; nothing is launched then
- *   set-up  the first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *           with that device current, and the first call for a dataset builds its tile
- *           descriptor; make that first call before any stream capture
+ *   batch   device arrays only (batch->mem must be RS_MEM_DEVICE)
+ *   outputs correct, per_class, preds: device memory of the context's device (or managed memory);
+ *           anything else is RS_ERR_INVALID with a message and nothing is launched
+ *   limit   16*C + 20*P + 768 bytes, plus 4*P*K when the dataset has K <= 64 classes (each part
+ *           rounded up to 256 B), must fit in the array, otherwise RS_ERR_TOO_LARGE with a
+ *           message; nothing is launched then
+ *   set-up  rs_create looks up the array's device address (cudaGetSymbolAddress, with the
+ *           context's device current) and keeps it in the context; the first call for a dataset
+ *           builds its tile descriptor on the host, so make that first call before any stream
+ *           capture
  *   sharing every call uses the same array: calls whose GPU work overlaps (different streams,
  *           host threads or contexts on one device) race on it and must be serialised by the
  *           caller. Each call clears the status word it needs; the rest is rewritten before use.
- * The dataset itself is registered beforehand with rs_dataset_create.
+ * The dataset itself is registered beforehand with rs_dataset_create. Like rs_eval_hard, the call
+ * stops a tile of one label after the set's last rule of that label (K <= 64).
  */
 #define RS_STATIC_SCRATCH_BYTES (8u << 20)
 rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,
@@ -372,8 +377,14 @@ rs_status rs_tile_config_form(int32_t id, int32_t *form);
 /* Force configuration `id` for every following hard evaluation of the context (-1 = automatic:
  * autotuned table, else heuristic). */
 rs_status rs_set_tile_config(rs_ctx *ctx, int32_t id);
+/* The configuration the next rs_eval_hard of `batch` on `ds` would use: the forced one
+ * (rs_set_tile_config), else the tuned one for the batch's shape key (feature count, class count,
+ * mean conditions per rule, log2 N, membership tests), else the built-in heuristic. */
+rs_status rs_tile_config_pick(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *id);
 /* Time every configuration on this dataset and batch (device pointers), record the fastest in the
- * context's table (and its JSON cache file) and return its id in *best. */
+ * context's table (and its JSON cache file) and return its id in *best. The cache file is read at
+ * rs_create; a file that does not parse as a whole, or that names a configuration this library
+ * does not have, is ignored (the heuristic applies until the tuner writes it again). */
 rs_status rs_autotune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, void *stream,
                       int32_t *best);
 

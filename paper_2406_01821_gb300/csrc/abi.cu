@@ -45,6 +45,8 @@ void preload_dataset_kernels();
 rs_status selftest_bounded_wait(Ctx *ctx, int64_t limit_ns, cudaStream_t stream);
 rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
                            int32_t *per_class, int32_t *preds, cudaStream_t stream);
+rs_status static_scratch_lookup(unsigned char **out);
+rs_status tile_pick(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *id);
 }  // namespace rs
 
 using namespace rs;
@@ -55,8 +57,26 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
 };
 
+// Every entry point leaves the calling thread's current device as it found it: the library makes
+// its context's device current for its own work and restores the caller's on return.
+struct CurrentDeviceRestore {
+    int prev = -1;
+    CurrentDeviceRestore()
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; }
+    }
+    ~CurrentDeviceRestore()
+    {
+        int cur = -1;
+        if (prev < 0) return;
+        if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return; }
+        if (cur != prev && cudaSetDevice(prev) != cudaSuccess) cudaGetLastError();
+    }
+};
+
 #define RS_GUARD(...)                                                    \
     try {                                                                \
+        CurrentDeviceRestore device_restore_;                            \
         NvtxRange nvtx_range_(__func__);                                 \
         __VA_ARGS__                                                      \
     } catch (const std::bad_alloc &) {                                   \
@@ -109,6 +129,12 @@ rs_status rs_create(const rs_config *cfg, rs_ctx **out)
             delete ctx;
             set_error("cannot allocate the context status word");
             return RS_ERR_OOM;
+        }
+        // device address of rs_eval_hard_static's fixed scratch array, with this device current
+        if (rs_status rc = static_scratch_lookup(&ctx->static_scratch)) {
+            cudaFree(ctx->d_sticky);
+            delete ctx;
+            return rc;
         }
         // keep freed stream-ordered scratch in the pool instead of returning it to the OS
         cudaMemPool_t pool;
@@ -342,6 +368,14 @@ rs_status rs_set_tile_config(rs_ctx *ctx, int32_t id)
     if (id < -1 || id >= tile_config_count()) { set_error("bad tile config %d", id); return RS_ERR_INVALID; }
     ctx->forced_tile = id;
     return RS_OK;
+}
+
+rs_status rs_tile_config_pick(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *id)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        return tile_pick(ctx, ds, batch, id);
+    })
 }
 
 rs_status rs_autotune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, void *stream, int32_t *best)

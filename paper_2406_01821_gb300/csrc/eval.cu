@@ -1,6 +1,7 @@
 // Orchestration of one evaluation call: argument checks, host staging, scratch, packing, tile
 // configuration choice (autotuned table or heuristic), optional CUDA-graph replay, status check.
 #include <algorithm>
+#include <cctype>
 #include <chrono>
 #include <cmath>
 #include <fstream>
@@ -137,25 +138,54 @@ static int pick_tile(Ctx *ctx, const Dataset &ds, const rs_batch *b)
     return heuristic_tile(ds);
 }
 
+// Strict reader of the cache file written by save_tune_table: {"key": id, ...} with ids of
+// compiled configurations. A file that does not parse as a whole (truncated, edited, another
+// format) or names an unknown configuration is ignored, never partly applied: the context then
+// uses the heuristic until the tuner writes the file again.
+static bool parse_tune_table(const std::string &s, std::map<std::string, int> &out)
+{
+    size_t i = 0;
+    auto ws = [&] { while (i < s.size() && std::isspace((unsigned char)s[i])) ++i; };
+    ws();
+    if (i >= s.size() || s[i++] != '{') return false;
+    ws();
+    if (i < s.size() && s[i] == '}') { ++i; ws(); return i == s.size(); }
+    while (true) {
+        ws();
+        if (i >= s.size() || s[i++] != '"') return false;
+        const size_t k0 = i;
+        while (i < s.size() && s[i] != '"' && s[i] != '\\' && (unsigned char)s[i] >= 0x20) ++i;
+        if (i >= s.size() || s[i] != '"' || i == k0) return false;
+        const std::string key = s.substr(k0, i - k0);
+        ++i;
+        ws();
+        if (i >= s.size() || s[i++] != ':') return false;
+        ws();
+        const size_t d0 = i;
+        while (i < s.size() && i - d0 < 6 && std::isdigit((unsigned char)s[i])) ++i;
+        if (i == d0 || (i < s.size() && std::isdigit((unsigned char)s[i]))) return false;
+        const int id = std::atoi(s.c_str() + d0);
+        if (id < 0 || id >= tile_config_count()) return false;
+        out[key] = id;
+        ws();
+        if (i >= s.size()) return false;
+        if (s[i] == ',') { ++i; continue; }
+        if (s[i] != '}') return false;
+        ++i;
+        ws();
+        return i == s.size();
+    }
+}
+
 void load_tune_table(Ctx *ctx)
 {
     if (ctx->autotune_path.empty()) return;
-    std::ifstream in(ctx->autotune_path);
+    std::ifstream in(ctx->autotune_path, std::ios::binary);
     if (!in) return;
-    // minimal reader for {"key": id, ...}
     std::string s((std::istreambuf_iterator<char>(in)), std::istreambuf_iterator<char>());
-    size_t i = 0;
-    while (true) {
-        size_t q0 = s.find('"', i);
-        if (q0 == std::string::npos) break;
-        size_t q1 = s.find('"', q0 + 1);
-        if (q1 == std::string::npos) break;
-        size_t colon = s.find(':', q1);
-        if (colon == std::string::npos) break;
-        int id = std::atoi(s.c_str() + colon + 1);
-        if (id >= 0 && id < tile_config_count()) ctx->tune_table[s.substr(q0 + 1, q1 - q0 - 1)] = id;
-        i = colon + 1;
-    }
+    if (s.size() > (1u << 20)) return;                 // not a file this library wrote
+    std::map<std::string, int> table;
+    if (parse_tune_table(s, table)) ctx->tune_table = std::move(table);
 }
 
 static void save_tune_table(Ctx *ctx)
@@ -626,6 +656,18 @@ rs_status autotune(Ctx *ctx, uint64_t ds_h, const rs_batch *b, cudaStream_t stre
         save_tune_table(ctx);
     }
     if (best) *best = best_id;
+    return RS_OK;
+}
+
+// The configuration the next rs_eval_hard of this batch on this dataset would use.
+rs_status tile_pick(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *id)
+{
+    rs_status rc = check_batch(b);
+    if (rc) return rc;
+    if (!id) { set_error("id is NULL"); return RS_ERR_INVALID; }
+    auto ds = find_dataset(ctx, ds_h);
+    if (!ds) { set_error("unknown dataset %llu", (unsigned long long)ds_h); return RS_ERR_NOT_FOUND; }
+    *id = pick_tile(ctx, *ds, b);
     return RS_OK;
 }
 

@@ -1,15 +1,17 @@
 // Hard evaluation for callers that cannot allocate device memory.
 //
 // rs_eval_hard_static runs the same packing and evaluator kernels as rs_eval_hard, but every
-// piece of per-call scratch (condition records, per-set table, schedule order, status word) lives
-// in one file-scope device array of fixed size instead of stream-ordered allocations. The array is
-// part of the loaded module: every GPU that loads this library holds it until the process exits.
+// piece of per-call scratch (condition records, per-set table, schedule order, status word and,
+// for datasets of at most LAST_END_MAX_K classes, the per-class last-rule ends that let a tile of
+// one label stop early) lives in one file-scope device array of fixed size instead of
+// stream-ordered allocations. The array is part of the loaded module: every GPU that loads this
+// library holds it until the process exits.
 //
 // Host code must not use the array's name as a device address (in host code it names a host-side
-// stand-in). The device address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made on that device.
-#include <mutex>
-
+// stand-in). The device address is looked up with cudaGetSymbolAddress when a context is created,
+// with the context's device current, and kept in the context: a context never outlives the
+// primary context it was created in, so the address cannot go stale (a cudaDeviceReset while an
+// rs context is alive invalidates that rs context as a whole).
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -18,41 +20,48 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[RS_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_scratch_addr[kMaxDevices] = {};
-
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
-
-rs_status static_scratch(int device, unsigned char **out)
-{
-    if (device < 0 || device >= kMaxDevices) {
-        set_error("device ordinal %d out of range for the static scratch table", device);
-        return RS_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-        g_scratch_addr[device] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_addr[device];
-    return RS_OK;
-}
 
 __global__ void k_fold_status(const uint32_t *src, uint32_t *dst)
 {
     if (*src) atomicOr(dst, *src);
 }
 
+// An output the kernels write must be device memory of the context's device (or managed memory):
+// host memory handed here by mistake is rejected instead of being written by a kernel.
+rs_status check_output(const void *p, int device, const char *name)
+{
+    if (!p) return RS_OK;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) { cudaGetLastError(); at.type = cudaMemoryTypeUnregistered; }
+    const bool ok = at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == device);
+    if (!ok) {
+        set_error("rs_eval_hard_static: %s is not device memory of device %d (use rs_eval_hard for host outputs)",
+                  name, device);
+        return RS_ERR_INVALID;
+    }
+    return RS_OK;
+}
+
 }  // namespace
 
-size_t static_scratch_need(int64_t P, int64_t C)
+// Called by rs_create with the context's device current.
+rs_status static_scratch_lookup(unsigned char **out)
 {
-    return up256(sizeof(Rec) * (size_t)std::max<int64_t>(C, 1)) +
-           up256(sizeof(SetInfo) * (size_t)std::max<int64_t>(P, 1)) +
-           up256(sizeof(int32_t) * (size_t)std::max<int64_t>(P, 1)) + 256;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    *out = static_cast<unsigned char *>(p);
+    return RS_OK;
+}
+
+size_t static_scratch_need(int64_t P, int64_t C, int64_t K)
+{
+    const int64_t P1 = std::max<int64_t>(P, 1);
+    return up256(sizeof(Rec) * (size_t)std::max<int64_t>(C, 1)) + up256(sizeof(SetInfo) * (size_t)P1) +
+           up256(sizeof(int32_t) * (size_t)P1) + 256 +
+           (K <= LAST_END_MAX_K ? up256(sizeof(int32_t) * (size_t)P1 * (size_t)std::max<int64_t>(K, 1)) : 0);
 }
 
 rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
@@ -70,19 +79,23 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
         set_error("NULL batch or output array");
         return RS_ERR_INVALID;
     }
-    const size_t need = static_scratch_need(b->P, b->C);
-    if (need > RS_STATIC_SCRATCH_BYTES) {
-        set_error("batch needs %zu bytes of scratch (P=%d, C=%d); rs_eval_hard_static holds %zu "
-                  "(16 B per condition + 20 B per set + 768 B); use rs_eval_hard",
-                  need, b->P, b->C, (size_t)RS_STATIC_SCRATCH_BYTES);
-        return RS_ERR_TOO_LARGE;
-    }
     auto ds = find_dataset(ctx, ds_h);
     if (!ds) { set_error("unknown dataset %llu", (unsigned long long)ds_h); return RS_ERR_NOT_FOUND; }
+    const size_t need = static_scratch_need(b->P, b->C, ds->K);
+    if (need > RS_STATIC_SCRATCH_BYTES) {
+        set_error("batch needs %zu bytes of scratch (P=%d, C=%d, K=%d); rs_eval_hard_static holds %zu "
+                  "(16 B per condition + 20 B per set + 4 B per set and class when K <= %d + 768 B); "
+                  "use rs_eval_hard",
+                  need, b->P, b->C, ds->K, (size_t)RS_STATIC_SCRATCH_BYTES, LAST_END_MAX_K);
+        return RS_ERR_TOO_LARGE;
+    }
     rs_status rc = device_guard(ctx);
     if (rc) return rc;
-    unsigned char *base = nullptr;
-    if ((rc = static_scratch(ctx->device, &base))) return rc;
+    if ((rc = check_output(correct, ctx->device, "correct")) || (rc = check_output(per_class, ctx->device, "per_class")) ||
+        (rc = check_output(preds, ctx->device, "preds")))
+        return rc;
+    unsigned char *base = ctx->static_scratch;
+    if (!base) { set_error("static scratch address unknown"); return RS_ERR_DEVICE; }
 
     Scratch s;
     s.recs = reinterpret_cast<Rec *>(base);
@@ -91,8 +104,10 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
                                           up256(sizeof(SetInfo) * (size_t)std::max(b->P, 1)));
     s.status = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(s.order) +
                                             up256(sizeof(int32_t) * (size_t)std::max(b->P, 1)));
+    if (ds->K <= LAST_END_MAX_K) s.last_end = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(s.status) + 256);
     // The array keeps the previous call's contents: the status word must start at zero. Records,
-    // the set table and the order are fully rewritten by the packer before they are read.
+    // the set table, the order and the per-class last-rule ends are fully rewritten by the packer
+    // before they are read.
     RS_CUDA(cudaMemsetAsync(s.status, 0, sizeof(uint32_t), stream));
 
     BatchDev bd{};

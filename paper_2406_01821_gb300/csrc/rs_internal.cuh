@@ -213,6 +213,7 @@ struct Ctx {
     std::map<std::string, int> tune_table;   // key -> tile config id
     std::map<std::string, std::shared_ptr<GraphEntry>> graphs;
     uint32_t *d_sticky = nullptr;            // async-mode sticky device status
+    unsigned char *static_scratch = nullptr; // device address of rs_eval_hard_static's fixed array
     Profiler prof;
     struct Server *server = nullptr;
 };

@@ -125,6 +125,8 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "rs_poll_soft": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
                                       ctypes.POINTER(rs_ticket_info)]),
+    "rs_tile_config_pick": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
+                                             ctypes.POINTER(ctypes.c_int32)]),
     "rs_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rs_batch),
                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "rs_selftest_threshold_rewrite": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
@@ -354,6 +356,13 @@ class Context:
     # tuning
     def set_tile_config(self, cfg_id: int):
         check(lib().rs_set_tile_config(self.h, cfg_id))
+
+    def tile_pick(self, ds: int, batch) -> int:
+        """The tile configuration the next hard evaluation of `batch` on `ds` would use."""
+        cid = ctypes.c_int32(-1)
+        cb = batch.c()
+        check(lib().rs_tile_config_pick(self.h, ds, ctypes.byref(cb), ctypes.byref(cid)))
+        return cid.value
 
     def autotune(self, ds: int, batch, stream=None) -> int:
         best = ctypes.c_int32(-1)
