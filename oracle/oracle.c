@@ -182,6 +182,26 @@ static double margin(const orc_batch *b, int64_t c, const float *xrow, double ta
 }
 
 /*
+ * log(1 - q_r) of rule r, where s = log q_r. Directly, log(-expm1(s)). When every margin of the
+ * rule is so large that s is within 1e-200 of 0 (every u_c above about 460), 1 - q_r no longer
+ * follows from s: there 1 - q_r = sum_c softplus(-u_c) = sum_c e^{-u_c} to float64 precision
+ * (the first-order term of 1 - prod_c (1 - e^{-u_c})), and its log is the log-sum-exp of the
+ * -u_c. Membership tests that hold contribute nothing; a rule of such tests only has q_r = 1.
+ */
+static double log_one_minus_q(const orc_batch *b, int32_t r, const float *xrow, double tau, double s)
+{
+    if (s == -INFINITY) return 0.0;
+#if ORC_PLANT == 12
+    return log(-expm1(s));                       /* planted: 1 - q taken from s alone */
+#endif
+    if (s < -1e-200) return log(-expm1(s));
+    double l = -INFINITY;
+    for (int32_t c = b->rule_cond_off[r]; c < b->rule_cond_off[r + 1]; ++c)
+        if (b->cond_op[c] != 2) l = log_add(l, -margin(b, c, xrow, tau));
+    return l;
+}
+
+/*
  * Soft forward (and optionally the adjoint) of every set over all samples, float64.
  *   loss[p]       = (1/N) sum_n -log p_{y_n}(n)
  *   probs[(p*N+n)*K+k] (optional) = p_k(n)
@@ -232,7 +252,7 @@ int orc_soft(const float *X, int64_t N, int32_t F, const int32_t *y, int32_t K,
                         s += (b->cond_op[c] == 2) ? (cond_true(b, c, xrow) ? 0.0 : -INFINITY)
                                                   : log_sigmoid(margin(b, c, xrow, tau));
                     lq[j] = s;
-                    l1q[j] = log(-expm1(s));
+                    l1q[j] = log_one_minus_q(b, r, xrow, tau, s);
                 }
                 for (int32_t k = 0; k < K; ++k) lp[k] = -INFINITY;
                 lu[0] = 0.0;
@@ -261,19 +281,21 @@ int orc_soft(const float *X, int64_t N, int32_t F, const int32_t *y, int32_t K,
                 for (int32_t j = R - 1; j >= 0; --j) {
                     const int32_t r = r0 + j;
                     const int same = (b->rule_class[r] == yn);
+                    /* d ell / d lq_j = sign * exp(lg); kept as its log so that the product with
+                     * sigmoid(-u_c) below is formed in the exponent (both factors may lie outside
+                     * the float64 range at large margins while the product is moderate) */
+                    const double sign = same ? -1.0 : 1.0;
 #if ORC_PLANT == 7
-                    double gq = same ? -exp(lq[j] + lu[j] + lS - lpy)     /* planted: S for 1-S */
-                                     : exp(lq[j] + lu[j] + lS - lpy);
+                    const double lg = lq[j] + lu[j] + lS - lpy;           /* planted: S for 1-S */
 #else
-                    double gq = same ? -exp(lq[j] + lu[j] + lT - lpy)
-                                     : exp(lq[j] + lu[j] + lS - lpy);
+                    const double lg = lq[j] + lu[j] + (same ? lT : lS) - lpy;
 #endif
                     lS = log_add(same ? lq[j] : -INFINITY, l1q[j] + lS);
                     lT = log_add(same ? -INFINITY : lq[j], l1q[j] + lT);
                     for (int32_t c = b->rule_cond_off[r]; c < b->rule_cond_off[r + 1]; ++c) {
                         if (b->cond_op[c] == 2) continue;           /* an indicator: no gradient */
                         const double u = margin(b, c, xrow, tau);
-                        const double du = gq * exp(log_sigmoid(-u));      /* d ell / d u */
+                        const double du = sign * exp(lg + log_sigmoid(-u));   /* d ell / d u */
                         const double s = (b->cond_op[c] == 0) ? 1.0 : -1.0;
                         const double da = du * s * (double)xrow[b->cond_f[c]] / tau;
                         grad_a[c] += scale * da;

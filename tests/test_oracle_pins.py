@@ -476,3 +476,141 @@ def test_adjoint_matches_central_differences(orc, seed):
             fd = (total(plus) - total(minus)) / step
             g = out["grad_" + name][c]
             assert abs(fd - g) <= 1e-3 * max(abs(g), 1e-3), (c, name, fd, g)
+
+
+# ----------------------------------------------------- soft path at large margins (|u| >> 1)
+#
+# Fine-tuned coefficients (Fig. 1c: a pair coefficient of 7275.88) give margins of hundreds or
+# thousands of temperatures. There q_r = 1 - e^{-u} (or e^{u}) to any float precision, and
+# 1 - q_r, products of such factors and the gradient factors sigmoid(-u) are far below the float64
+# range while the loss and the gradients stay moderate. Two references that do not share the
+# oracle's log-domain form pin it there: closed forms of a single condition, and the linear-domain
+# definition evaluated in arbitrary precision (mpmath), with 1 - q_r written as the positive sum
+# sum_c sigmoid(-u_c) prod_{c' < c} sigmoid(u_c') (no cancellation) and gradients by central
+# differences in that precision.
+
+LARGE_U = np.array([50.0, 103.0, 200.0, 1000.0, 18000.0])
+
+
+@pytest.mark.parametrize("op", [synth.GT, synth.LT])
+@pytest.mark.parametrize("pair", [False, True])
+def test_large_margin_single_condition_closed_form(orc, op, pair):
+    tau = np.float32(0.1)
+    u_target = np.concatenate([LARGE_U, -LARGE_U])
+    s = 1.0 if op == synth.GT else -1.0
+    a, bb, t = np.float32(1.5), np.float32(-2.0), np.float32(0.25)
+    x2 = np.float32(0.5)
+    rhs = np.float64(bb) * np.float64(x2) if pair else np.float64(t)
+    x0 = ((s * u_target * np.float64(tau) + rhs) / np.float64(a)).astype(np.float32)
+    X = np.zeros((2 * len(x0), 3), np.float32)
+    X[:, 0] = np.tile(x0, 2)
+    X[:, 2] = x2
+    y = np.repeat(np.array([1, 0], np.int32), len(x0))           # both labels at every margin
+    cond = (0, 2 if pair else -1, op, a, bb if pair else 0.0, 0.0 if pair else t)
+    batch = synth.from_lists([[(1, [cond])]], [0])
+    out = orc.soft(X, y, 2, batch, tau, dloss=1.0, want_mag=True)
+    u = s * (np.float64(a) * X[:, 0].astype(np.float64) - rhs) / np.float64(tau)
+    assert np.all(np.abs(np.abs(u) / np.tile(np.abs(u_target), 2) - 1) < 1e-3)
+    is1 = y == 1
+    ell = np.where(is1, np.logaddexp(0.0, -u), np.logaddexp(0.0, u))     # -log sigmoid(+-u)
+    assert np.isfinite(out["loss"][0])
+    assert np.isclose(out["loss"][0], ell.mean(), rtol=1e-13, atol=0)
+    dldu = expit(u) - is1
+    terms_a = dldu * s * X[:, 0].astype(np.float64) / np.float64(tau)
+    terms_2 = dldu * -s * (X[:, 2].astype(np.float64) if pair else 1.0) / np.float64(tau)
+    # the per-sample terms of both labels cancel in the mean: compare against their magnitude
+    for got, terms in ((out["grad_a"][0], terms_a), (out["grad_b" if pair else "grad_t"][0], terms_2)):
+        assert abs(got - terms.mean()) <= 1e-12 * np.abs(terms).mean(), (got, terms.mean())
+
+
+def mp_set_loss(X, y, b, p, tau, dps=40, param=None):
+    """Mean -log p_y of set p in the linear domain, in `dps` decimal digits; `param` =
+    (array name, condition, mpf value) replaces one parameter (for differences)."""
+    import mpmath as mp
+    with mp.workdps(dps):
+        tau_m = mp.mpf(float(tau))
+
+        def val(name, c):
+            if param is not None and param[0] == name and param[1] == c:
+                return param[2]
+            return mp.mpf(float(getattr(b, name)[c]))
+
+        def sig(u):
+            return 1 / (1 + mp.exp(-u))
+
+        total = mp.mpf(0)
+        for n in range(len(X)):
+            x = [mp.mpf(float(v)) for v in X[n]]
+            U, py = mp.mpf(1), mp.mpf(0)
+            for r in range(b.set_rule_off[p], b.set_rule_off[p + 1]):
+                pos, neg = [], []
+                for c in range(b.rule_cond_off[r], b.rule_cond_off[r + 1]):
+                    rhs = val("cond_t", c) if b.cond_g[c] < 0 else val("cond_b", c) * x[b.cond_g[c]]
+                    s = 1 if b.cond_op[c] == synth.GT else -1
+                    u = s * (val("cond_a", c) * x[b.cond_f[c]] - rhs) / tau_m
+                    pos.append(sig(u))
+                    neg.append(sig(-u))
+                q = mp.fprod(pos)
+                one_minus_q = mp.fsum(neg[c] * mp.fprod(pos[:c]) for c in range(len(pos)))
+                if b.rule_class[r] == y[n]:
+                    py += q * U
+                U *= one_minus_q
+            if b.set_default[p] == y[n]:
+                py += U
+            total += -mp.log(py)
+        return total / len(X)
+
+
+def large_margin_case(seed, N=10):
+    """Small sets with coefficients of tens to thousands (margins of ~10 to ~20,000 tau at
+    tau = 0.1), including a Fig. 1c-shaped pair condition (coefficient -7275.88), every label
+    reachable."""
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(N, 3)).astype(np.float32)
+    y = rng.integers(0, 2, N).astype(np.int32)
+    sets = []
+    for p in range(3):
+        rules = []
+        for r in range(int(rng.integers(1, 4))):
+            conds = []
+            for c in range(int(rng.integers(1, 4))):
+                f = int(rng.integers(0, 3))
+                op = int(rng.integers(0, 2))
+                a = np.float32(rng.choice([-1, 1]) * 10 ** rng.uniform(1, 3))
+                if rng.uniform() < 0.3:
+                    g = (f + 1 + int(rng.integers(0, 2))) % 3
+                    conds.append((f, g, op, a, np.float32(rng.choice([-1, 1]) * 10 ** rng.uniform(1, 3)), 0.0))
+                else:
+                    conds.append((f, -1, op, a, 0.0, np.float32(a * X[int(rng.integers(0, N)), f])))
+            rules.append((int(rng.integers(0, 2)), conds))
+        sets.append(rules)
+    sets.append([(1, [(0, -1, synth.GT, np.float32(0.06), 0.0, np.float32(0.0)),
+                      (1, 2, synth.GT, np.float32(-1.0), np.float32(-7275.88), 0.0)]),
+                 (0, [(2, -1, synth.LT, np.float32(1.0), 0.0, np.float32(0.24))])])
+    b = synth.from_lists(sets, [0, 1, 0, 0])
+    b.set_default[:] = 1 - b.rule_class[b.set_rule_off[:-1]]
+    return X, y, b
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_large_margins_match_arbitrary_precision(orc, seed):
+    import mpmath as mp
+    X, y, b = large_margin_case(seed)
+    tau = np.float32(0.1)
+    out = orc.soft(X, y, 2, b, tau, dloss=1.0, want_mag=True)
+    for p in range(b.P):
+        ref = float(mp_set_loss(X, y, b, p, tau))
+        assert np.isfinite(out["loss"][p]) and np.isclose(out["loss"][p], ref, rtol=1e-12, atol=0), \
+            (p, out["loss"][p], ref)
+        h = mp.mpf(10) ** -30
+        for c in range(b.rule_cond_off[b.set_rule_off[p]], b.rule_cond_off[b.set_rule_off[p + 1]]):
+            for name, grad in (("cond_a", "a"), ("cond_t" if b.cond_g[c] < 0 else "cond_b",
+                                                  "t" if b.cond_g[c] < 0 else "b")):
+                with mp.workdps(110):
+                    v = mp.mpf(float(getattr(b, name)[c]))
+                    fd = (mp_set_loss(X, y, b, p, tau, 110, (name, c, v + h)) -
+                          mp_set_loss(X, y, b, p, tau, 110, (name, c, v - h))) / (2 * h)
+                g, m = out["grad_" + grad][c], out["mag_" + grad][c]
+                # differences of losses below ~1e3 resolve gradients down to ~1e-77 at 110 digits
+                assert np.isfinite(g) and abs(g - float(fd)) <= 1e-10 * max(abs(float(fd)), m) + 1e-75, \
+                    (p, c, name, g, float(fd))

@@ -26,6 +26,9 @@ PLANTS = {
                                                    lambda o: cat.test_single_code_equals_band(o)]),
     10: ("evolution never adds a condition", [lambda o: evo.check_operator_mix(o)]),
     11: ("threshold drawn from the wrong feature", [lambda o: evo.check_thresholds_from_data(o)]),
+    12: ("1 - q taken from log q alone at large margins",
+         [lambda o: pins.test_large_margin_single_condition_closed_form(o, 0, False),
+          lambda o: pins.test_large_margins_match_arbitrary_precision(o, 0)]),
 }
 
 
