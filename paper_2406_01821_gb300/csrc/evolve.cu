@@ -659,7 +659,7 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
     void *soft_scratch = nullptr;
     const int64_t soft_cap_c = (int64_t)TC;
     if ((rc = B.get(&gslot, 2)) ||
-        (T > 0 && (rc = B.get(reinterpret_cast<char **>(&soft_scratch), soft_scratch_bytes(soft_cap_c, T)))))
+        (T > 0 && (rc = B.get(reinterpret_cast<char **>(&soft_scratch), soft_scratch_bytes(soft_cap_c, T, ds.N)))))
         return rc;
     RS_CUDA(cudaMemsetAsync(gslot, 0, 2 * sizeof(int64_t), s));
 
@@ -838,7 +838,7 @@ rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, fl
     if ((rc = soft_validate(ctx, sa, &maxR, &maxC, s))) return rc;
     void *scratch = nullptr;
     float *trace = nullptr;
-    if ((rc = B.get(reinterpret_cast<char **>(&scratch), soft_scratch_bytes((int64_t)C, (int)P))) ||
+    if ((rc = B.get(reinterpret_cast<char **>(&scratch), soft_scratch_bytes((int64_t)C, (int)P, ds.N))) ||
         (loss_trace && (rc = B.get(&trace, (size_t)steps * P))))
         return rc;
     SoftAdam adam;                                              // applied by the gradient reduction

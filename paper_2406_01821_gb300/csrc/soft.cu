@@ -17,7 +17,13 @@
 //                dl/du_c  = dl/dlq_r * sigmoid(-u_c);  du/da = s x_f / tau, du/dt = -s / tau,
 //                du/db = -s x_g / tau.
 // Everything is evaluated in float32 in the log domain, which keeps 1 - q_r and the products of
-// many sigmoids representable where the linear form underflows.
+// many sigmoids representable where the linear form underflows. A float32 log-probability of
+// magnitude L is only known to about L * 2^-24, and at large margins (fine-tuned coefficients)
+// L reaches thousands while the probabilities that make up the gradient are ratios of such
+// values: a 64-sample group in which some sample's log p_y exceeds SOFT_FF_LIMIT in magnitude
+// (or is not finite) is evaluated again in float-float arithmetic (about 48 significant bits),
+// with the margins formed exactly, 1 - q_r taken as a log-sum-exp of -u_c when q_r rounds to 1,
+// and each d ell / d u_c formed in the exponent (soft_group_ff). Other groups keep the float path.
 //
 // Work: one warp owns a (rule set, sample chunk) pair and walks the chunk 64 samples at a time
 // (two per lane), so each partial sum has a fixed summation order. The forward keeps lu_r per
@@ -202,6 +208,7 @@ struct SoftKArgs {
     int64_t N, n_pad;
     int32_t K;
     float inv_tau;
+    float inv_tau_lo;                // 1/tau - inv_tau (float-float path)
     int32_t nchunks, chunk;          // chunk = samples per chunk (multiple of 32)
     float *part_loss;                // [nchunks][P]
     float *part_ga, *part_gbt;       // [nchunks][C]
@@ -212,6 +219,9 @@ struct SoftKArgs {
     int64_t Ccap;                    // row stride of the gradient partials
     const uint32_t *status;          // no work if non-zero (malformed batch)
     const int32_t *order;            // sets by decreasing size (schedule only; results do not depend on it)
+    uint8_t *ffmark;                 // [nchunks][P]: the task left groups to the float-float pass
+    uint32_t *ffbits;                // [nchunks][P][ff_wpt]: bit g of a task: its group g is one of them
+    int32_t ff_wpt;                  // words per task (groups per chunk / 32, rounded up)
 };
 
 // Feature access for one group of 64 samples: the lane's first sample column either in global
@@ -328,6 +338,148 @@ __device__ __forceinline__ float2 cond_grad_cached(const SoftKArgs &a, const Sof
     return make_float2(du * xf, pair ? -du * x(rc.g, v) : -du);
 }
 
+// ------------------------------------------------------------------ float-float arithmetic
+// A value held as the unevaluated sum hi + lo of two floats (Dekker, "A floating-point technique
+// for extending the available precision", 1971; Knuth's TwoSum): about 48 significant bits. The
+// transformations below are written with explicitly rounded operations so that no contraction
+// or reassociation can change them. Non-finite values carry lo = 0 and bypass the
+// transformations (which would turn an infinity into NaN).
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ ff ff_fast_sum(float a, float b)     // |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ float ff_f(ff x) { return __fadd_rn(x.hi, x.lo); }
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    if (!isfinite(x.hi) || !isfinite(y.hi)) return {__fadd_rn(x.hi, y.hi), 0.f};
+    const ff s = ff_two_sum(x.hi, y.hi);
+    return ff_fast_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ ff ff_add_f(ff x, float y) { return ff_add(x, ff{y, 0.f}); }
+
+__device__ __forceinline__ ff ff_two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    if (!isfinite(p)) return {p, 0.f};
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    if (!isfinite(p)) return {p, 0.f};
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fadd_rn(e, __fadd_rn(__fmul_rn(x.hi, y.lo), __fmul_rn(x.lo, y.hi)));
+    return ff_fast_sum(p, e);
+}
+
+__device__ __forceinline__ bool ff_less(ff x, ff y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); }
+
+// log(e^a + e^b): the larger term plus log1p of the exponential of the (float) difference
+__device__ __forceinline__ ff ff_log_add(ff a, ff b)
+{
+    if (a.hi == -INFINITY) return b;
+    if (b.hi == -INFINITY) return a;
+    const bool ab = ff_less(b, a);
+    const ff m = ab ? a : b, o = ab ? b : a;
+    return ff_add_f(m, log1p_unit(expf(ff_f(ff_add(o, ff_neg(m))))));
+}
+
+// log y for 0 < y <= 1 in float-float: y = m 2^k with m in [sqrt(1/2), sqrt(2)), log y = k ln 2 +
+// log m; ln 2 split into a head of 15 significant bits (k * head is exact for |k| < 512) and a tail.
+__device__ __forceinline__ ff ff_log_unit(float y)
+{
+    int k;
+    float m = frexpf(y, &k);
+    if (m < 0.70710678f) { m = __fmul_rn(m, 2.f); --k; }
+    constexpr float LN2_HI = 0.693145751953125f, LN2_LO = 1.42860682030941723e-6f;
+    const ff kl = ff_fast_sum(__fmul_rn((float)k, LN2_HI), __fmul_rn((float)k, LN2_LO));
+    return ff_add_f(kl, logf(m));
+}
+
+// The signed scaled margin u = s * (a * x[f] - rhs) / tau of condition rc for the lane's sample
+// v, in float-float: the products are exact (a float times a float), 1/tau is a float-float.
+__device__ __forceinline__ ff margin_ff(const SoftKArgs &a, const SoftRec &rc, const XView &x, int v)
+{
+    const ff lhs = ff_two_prod(rc.a, x(rc.f, v));
+    const ff rhs = (rc.meta & 1u) ? ff_two_prod(rc.bt, x(rc.g, v)) : ff{rc.bt, 0.f};
+    ff u = ff_mul(ff_add(lhs, ff_neg(rhs)), ff{a.inv_tau, a.inv_tau_lo});
+    if (rc.meta & 2u) u = ff_neg(u);
+    return u;
+}
+
+// log sigmoid(u) = min(u, 0) - log1p(e^-|u|); l1pe returns log1p(e^-|u|), which log sigmoid(-u) =
+// -max(u, 0) - log1p(e^-|u|) shares.
+__device__ __forceinline__ ff log_sigmoid_ff(ff u, float &l1pe)
+{
+    l1pe = log1p_unit(expf(-fabsf(ff_f(u))));
+    return u.hi < 0.f ? ff_add_f(u, -l1pe) : ff{-l1pe, 0.f};
+}
+
+// log q of one rule for the lane's sample v in float-float (membership tests: 0 or -inf).
+template <bool CAT>
+__device__ ff rule_logq_ff(const SoftKArgs &a, int c0, int c1, const XView &x, int v)
+{
+    ff s{0.f, 0.f};
+    for (int c = c0; c < c1; ++c) {
+        const SoftRec rc = a.recs[c];
+        if (CAT && (rc.meta & 4u)) {
+            if (!category_member(x(rc.f, v), __float_as_uint(rc.a), __float_as_uint(rc.bt))) s = {-INFINITY, 0.f};
+            continue;
+        }
+        float l1pe;
+        s = ff_add(s, log_sigmoid_ff(margin_ff(a, rc, x, v), l1pe));
+    }
+    return s;
+}
+
+// log(1 - q) of one rule from its log q (float-float). Where q <= 1/2 the float value is exact to
+// its last bit's scale; below that, 1 - q = -expm1(log q) and its log is taken in float-float;
+// where log q is within 2^-24 of 0, every condition's margin exceeds ~16.6 tau and
+// 1 - q = sum_c softplus(-u_c) = sum_c e^{-u_c} to float precision, whose log is the
+// log-sum-exp of -u_c with the largest term factored out. A rule of holding membership tests
+// only has q = 1 exactly and log(1 - q) = -inf.
+template <bool CAT>
+__device__ ff rule_log1mq_ff(const SoftKArgs &a, int c0, int c1, const XView &x, int v, ff lq)
+{
+    if (lq.hi == -INFINITY) return {0.f, 0.f};
+    const float lqf = ff_f(lq);
+    if (isnan(lqf)) return {lqf, 0.f};
+    if (lqf < -0.69314718f) return {log1pf(-expf(lqf)), 0.f};
+    if (lqf < -0x1p-24f) return ff_log_unit(-expm1f(lqf));
+    ff m{INFINITY, 0.f};
+    for (int c = c0; c < c1; ++c) {
+        const SoftRec rc = a.recs[c];
+        if (CAT && (rc.meta & 4u)) continue;
+        const ff u = margin_ff(a, rc, x, v);
+        if (ff_less(u, m)) m = u;
+    }
+    if (m.hi == INFINITY) return {-INFINITY, 0.f};
+    float acc = 0.f;
+    for (int c = c0; c < c1; ++c) {
+        const SoftRec rc = a.recs[c];
+        if (CAT && (rc.meta & 4u)) continue;
+        acc += expf(ff_f(ff_add(m, ff_neg(margin_ff(a, rc, x, v)))));
+    }
+    return ff_add_f(ff_neg(m), logf(acc));
+}
+
 // The four gradient sums of conditions c and c + 1 (g0, g1: this lane's d/da, d/db-or-dt) reduced
 // over the warp in one butterfly and added to the warp's accumulators.
 __device__ __forceinline__ void reduce_pair(float2 g0, float2 g1, int ci0, bool has1, float (*acc)[4], int lane)
@@ -349,23 +501,113 @@ __device__ __forceinline__ void reduce_pair(float2 g0, float2 g1, int ci0, bool 
     }
 }
 
-// Forward (and adjoint) of set p over one group of 32 * V samples: lane l holds samples
-// n0 + l + 32 v (v < V; bit v of valid: the sample exists), whose independent chains interleave.
-// lu: the warp's per-rule log-probabilities that no earlier rule fired [rule][32 V]; lq: the
-// rules' log q, kept only when class probabilities are written (null otherwise: the adjoint
-// computes them again); acc: the per-condition gradient sums.
-// CAT: the batch may hold membership conditions.
-template <bool BWD, bool CAT, int V>
-__device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, int R, int cb, int deflt,
-                                           int64_t n0, uint32_t valid, const XView &x,
-                                           float (*lq)[32 * V], float (*lu)[32 * V], float (*acc)[4], int lane,
-                                           float &loss_s, float &loss_c)
+// Class probabilities of the sample in slot `sl` (lane + 32 v) of the group from its per-rule log q
+// and log "no earlier rule fired" (lq, lu; lu[R] for the default).
+template <int V>
+__device__ __forceinline__ void write_probs(const SoftKArgs &a, int p, int rb, int R, int deflt, int64_t n0, int sl,
+                                            float (*lq)[32 * V], float (*lu)[32 * V])
 {
-    int yn[V];
+    const int64_t orig = a.perm[n0 + sl];
+    for (int k = 0; k < a.K; ++k) {
+        float lpk = (deflt == k) ? lu[R][sl] : -INFINITY;
+        for (int j = 0; j < R; ++j)
+            if (a.rule_class[rb + j] == k) lpk = log_add(lpk, lq[j][sl] + lu[j][sl]);
+        a.probs[((int64_t)p * a.N + orig) * a.K + k] = expf(lpk);
+    }
+}
+
+constexpr float SOFT_FF_LIMIT = 32.f;    // |log p_y| beyond which a group is evaluated in float-float
+
+// soft_group in float-float arithmetic, one sample of each lane at a time (all lanes walk the same
+// rules and conditions, so the gradient butterflies stay warp-wide). Forward: log q_r and
+// log(1 - q_r) of every rule, lu and log p_y accumulated in float-float. Adjoint: lu_r recovered
+// backwards as lu_{r+1} - log(1 - q_r) (exact to float-float precision; from the saved value at
+// the first rule with q_r = 1, after which lu is -inf), the S and T recursions in float-float, and
+// d ell / d u_c = -+exp(lq_r + lu_r + lT_{r+1} or lS_{r+1} - lp_y + log sigmoid(-u_c)) formed in the
+// exponent. Per-set sums keep the float path's fixed order: the loss in the caller's Kahan sum,
+// the gradients through the same butterfly and lanes.
+template <bool BWD, bool CAT, int V>
+__device__ __forceinline__ void soft_group_ff(const SoftKArgs &a, int p, int rb, int R, int cb, int deflt, int64_t n0,
+                                           uint32_t valid, const XView &x, float (*lq)[32 * V],
+                                           float (*lu)[32 * V], float (*acc)[4], int lane, float &loss_s,
+                                           float &loss_c)
+{
+    for (int v = 0; v < V; ++v) {
+        const bool ok = (valid >> v) & 1u;
+        const int yv = ok ? a.y[n0 + lane + 32 * v] : -1;
+        const int sl = lane + 32 * v;
+        // ---------------- forward
+        ff lur{0.f, 0.f}, lpy{-INFINITY, 0.f}, lu_fin{0.f, 0.f};
+        int jinf = R;                          // first rule with q = 1 (log(1 - q) = -inf)
+        for (int j = 0; j < R; ++j) {
+            const int r = rb + j;
+            const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
+            const ff lqj = rule_logq_ff<CAT>(a, c0, c1, x, v);
+            const ff l1q = rule_log1mq_ff<CAT>(a, c0, c1, x, v, lqj);
+            if (a.rule_class[r] == yv) lpy = ff_log_add(lpy, ff_add(lqj, lur));
+            if (lq) lq[j][sl] = lqj.hi;
+            lu[j][sl] = lur.hi;
+            if (l1q.hi == -INFINITY && jinf == R) { jinf = j; lu_fin = lur; }
+            lur = ff_add(lur, l1q);
+        }
+        lu[R][sl] = lur.hi;
+        if (deflt == yv) lpy = ff_log_add(lpy, lur);
+        if (ok) kadd_loss(loss_s, loss_c, -ff_f(lpy));
+        if (a.probs && ok) write_probs<V>(a, p, rb, R, deflt, n0, sl, lq, lu);   // this lane's own slot
+        if (!BWD) continue;
+        // ---------------- adjoint
+        ff lS = deflt == yv ? ff{0.f, 0.f} : ff{-INFINITY, 0.f};
+        ff lT = deflt == yv ? ff{-INFINITY, 0.f} : ff{0.f, 0.f};
+        ff lu_next = lur;
+        for (int j = R - 1; j >= 0; --j) {
+            const int r = rb + j;
+            const int cls = a.rule_class[r];
+            const int c0 = a.rule_cond_off[r], c1 = a.rule_cond_off[r + 1];
+            const ff lqj = rule_logq_ff<CAT>(a, c0, c1, x, v);
+            const ff l1q = rule_log1mq_ff<CAT>(a, c0, c1, x, v, lqj);
+            const ff luj = j > jinf ? ff{-INFINITY, 0.f} : (j == jinf ? lu_fin : ff_add(lu_next, ff_neg(l1q)));
+            lu_next = luj;
+            const bool same = cls == yv;
+            const ff lw = same ? lT : lS;
+            const bool zero = !ok || lw.hi == -INFINITY || lqj.hi == -INFINITY || luj.hi == -INFINITY;
+            const ff G = ff_add(ff_add(ff_add(lqj, luj), lw), ff_neg(lpy));
+            const float sign = same ? -1.f : 1.f;
+            lS = ff_log_add(same ? lqj : ff{-INFINITY, 0.f}, ff_add(l1q, lS));
+            lT = ff_log_add(same ? ff{-INFINITY, 0.f} : lqj, ff_add(l1q, lT));
+            for (int c = c0; c < c1; c += 2) {
+                const bool has1 = c + 1 < c1;
+                float2 g[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    if (i == 1 && !has1) break;
+                    const SoftRec rc = a.recs[c + i];
+                    if ((CAT && (rc.meta & 4u)) || zero) continue;
+                    const ff u = margin_ff(a, rc, x, v);
+                    float l1pe;
+                    log_sigmoid_ff(u, l1pe);
+                    const ff lsn = u.hi > 0.f ? ff_add_f(ff_neg(u), -l1pe) : ff{-l1pe, 0.f};   // log sigmoid(-u)
+                    const float sg = (rc.meta & 2u) ? -1.f : 1.f;
+                    const float du = sign * expf(ff_f(ff_add(G, lsn))) * sg * a.inv_tau;
+                    g[i] = make_float2(du * x(rc.f, v), (rc.meta & 1u) ? -du * x(rc.g, v) : -du);
+                }
+                reduce_pair(g[0], g[1], c - cb, has1, acc, lane);
+            }
+        }
+    }
+}
+
+// Forward of set p over one group of 32 * V samples (lane l holds samples n0 + l + 32 v; bit v
+// of valid: the sample exists): the rules' log "no earlier rule fired" into lu (and log q into
+// lq when class probabilities are written), the labels yn and log p_y. Returns true when some
+// sample's log p_y is beyond SOFT_FF_LIMIT in magnitude or not finite (warp-uniform).
+template <bool CAT, int V>
+__device__ __forceinline__ bool soft_forward(const SoftKArgs &a, int rb, int R, int deflt, int64_t n0, uint32_t valid,
+                                             const XView &x, float (*lq)[32 * V], float (*lu)[32 * V], int lane,
+                                             int (&yn)[V], float (&lpy)[V])
+{
 #pragma unroll
     for (int v = 0; v < V; ++v) yn[v] = ((valid >> v) & 1u) ? a.y[n0 + lane + 32 * v] : -1;
-    // ---------------- forward
-    float lu_r[V], lpy[V];
+    float lu_r[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) { lu_r[v] = 0.f; lpy[v] = -INFINITY; }
     for (int j = 0; j < R; ++j) {
@@ -382,26 +624,42 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
             lu_r[v] += logf(-expm1f(s[v]));
         }
     }
+    bool big = false;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         lu[R][lane + 32 * v] = lu_r[v];
         if (deflt == yn[v]) lpy[v] = log_add(lpy[v], lu_r[v]);
-        if (((valid >> v) & 1u)) kadd_loss(loss_s, loss_c, -lpy[v]);
+        if (((valid >> v) & 1u) && !(fabsf(lpy[v]) <= SOFT_FF_LIMIT)) big = true;
     }
+    return __any_sync(FULL, big);
+}
+
+// Forward (and adjoint) of set p over one group of 32 * V samples: lane l holds samples
+// n0 + l + 32 v (v < V; bit v of valid: the sample exists), whose independent chains interleave.
+// lu: the warp's per-rule log-probabilities that no earlier rule fired [rule][32 V]; lq: the
+// rules' log q, kept only when class probabilities are written (null otherwise: the adjoint
+// computes them again); acc: the per-condition gradient sums.
+// CAT: the batch may hold membership conditions. Returns true, having added nothing, when some
+// sample's log p_y is beyond SOFT_FF_LIMIT: the task is then marked, and k_soft_ff evaluates the
+// group in float-float after this kernel.
+template <bool BWD, bool CAT, int V>
+__device__ __forceinline__ bool soft_group(const SoftKArgs &a, int p, int rb, int R, int cb, int deflt,
+                                           int64_t n0, uint32_t valid, const XView &x,
+                                           float (*lq)[32 * V], float (*lu)[32 * V], float (*acc)[4], int lane,
+                                           float &loss_s, float &loss_c)
+{
+    int yn[V];
+    float lpy[V];
+    if (soft_forward<CAT, V>(a, rb, R, deflt, n0, valid, x, lq, lu, lane, yn, lpy)) return true;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (((valid >> v) & 1u)) kadd_loss(loss_s, loss_c, -lpy[v]);
     if (a.probs) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            if (!((valid >> v) & 1u)) continue;
-            const int64_t orig = a.perm[n0 + lane + 32 * v];
-            for (int k = 0; k < a.K; ++k) {
-                float lpk = (deflt == k) ? lu_r[v] : -INFINITY;
-                for (int j = 0; j < R; ++j)
-                    if (a.rule_class[rb + j] == k) lpk = log_add(lpk, lq[j][lane + 32 * v] + lu[j][lane + 32 * v]);
-                a.probs[((int64_t)p * a.N + orig) * a.K + k] = expf(lpk);
-            }
-        }
+        for (int v = 0; v < V; ++v)
+            if ((valid >> v) & 1u) write_probs<V>(a, p, rb, R, deflt, n0, lane + 32 * v, lq, lu);
     }
-    if (!BWD) return;
+    if (!BWD) return false;
     // ---------------- adjoint
     float lS[V], lT[V];
 #pragma unroll
@@ -465,6 +723,7 @@ __device__ __forceinline__ void soft_group(const SoftKArgs &a, int p, int rb, in
             reduce_pair(g0, g1, c - cb, has1, acc, lane);
         }
     }
+    return false;
 }
 
 // Write a task's chunk partials (loss; gradient sums when BWD).
@@ -520,16 +779,26 @@ __global__ void __maxnreg__(96) k_soft(SoftKArgs a)     // launched with SOFT_W 
         float loss_s = 0.f, loss_c = 0.f;
         const int64_t s0 = (int64_t)ch * a.chunk;
         const int64_t s1 = min(s0 + a.chunk, a.N);
-        for (int64_t nb = s0; nb < s1; nb += SOFT_G) {
+        uint32_t *fbits = a.ffbits + ((int64_t)ch * a.P + p) * a.ff_wpt;
+        uint32_t fw = 0, ff = 0;
+        int gi = 0;
+        for (int64_t nb = s0; nb < s1; nb += SOFT_G, ++gi) {
             uint32_t valid = 0;
 #pragma unroll
             for (int v = 0; v < SOFT_V; ++v) valid |= (nb + lane + 32 * v < s1 ? 1u : 0u) << v;
             // the dataset is padded to a multiple of 128 samples: every read stays inside it
             const XView x{a.Xt + nb + lane, a.n_pad};
-            soft_group<BWD, CAT, SOFT_V>(a, p, rb, re - rb, cb, a.set_default[p], nb, valid, x, lq, lu, acc, lane,
-                                         loss_s, loss_c);
+            if (soft_group<BWD, CAT, SOFT_V>(a, p, rb, re - rb, cb, a.set_default[p], nb, valid, x, lq, lu, acc,
+                                             lane, loss_s, loss_c))
+                fw |= 1u << (gi & 31);
+            if ((gi & 31) == 31 || nb + SOFT_G >= s1) {
+                if (lane == 0) fbits[gi >> 5] = fw;
+                ff |= fw;
+                fw = 0;
+            }
         }
         soft_flush<BWD>(a, p, ch, cb, ce, loss_s, acc, lane);
+        if (lane == 0) a.ffmark[(int64_t)ch * a.P + p] = ff != 0;
     }
 }
 
@@ -601,9 +870,11 @@ __global__ void __maxnreg__(96) k_soft_tile(SoftKArgs a, int F)
             }
         }
         float loss_s = 0.f, loss_c = 0.f;
+        uint32_t fw = 0, ff = 0;
         const int64_t s0 = (int64_t)ch * a.chunk;
         const int64_t s1 = min(s0 + a.chunk, a.N);
         const int ngroups = (int)((s1 - s0 + SOFT_G - 1) / SOFT_G);
+        uint32_t *fbits = a.ffbits + ((int64_t)ch * a.P + p) * a.ff_wpt;
         stage_group(xbuf, a.Xt, a.n_pad, F, s0);
         for (int gi = 0; gi < ngroups; ++gi) {
             const int64_t nb = s0 + SOFT_G * (int64_t)gi;
@@ -619,12 +890,81 @@ __global__ void __maxnreg__(96) k_soft_tile(SoftKArgs a, int F)
 #pragma unroll
                 for (int v = 0; v < SOFT_V; ++v) valid |= (nb + lane + 32 * v < s1 ? 1u : 0u) << v;
                 const XView x{xbuf + (gi & 1) * F * SOFT_G + lane, SOFT_G};
-                soft_group<BWD, CAT, SOFT_V>(a, p, rb, R, cb, deflt, nb, valid, x, lq, lu, acc, lane, loss_s,
-                                             loss_c);
+                if (soft_group<BWD, CAT, SOFT_V>(a, p, rb, R, cb, deflt, nb, valid, x, lq, lu, acc, lane, loss_s,
+                                                 loss_c))
+                    fw |= 1u << (gi & 31);
+                if ((gi & 31) == 31 || gi + 1 == ngroups) {
+                    if (lane == 0) fbits[gi >> 5] = fw;
+                    ff |= fw;
+                    fw = 0;
+                }
             }
             __syncthreads();              // the buffer is restaged two groups later
         }
-        if (active) soft_flush<BWD>(a, p, ch, cb, ce, loss_s, acc, lane);
+        if (active) {
+            soft_flush<BWD>(a, p, ch, cb, ce, loss_s, acc, lane);
+            if (lane == 0) a.ffmark[(int64_t)ch * a.P + p] = ff != 0;
+        }
+    }
+}
+
+// The float-float pass: one warp per (set, chunk) task that the main kernel marked. The warp
+// evaluates, in group order, the groups whose bits the main kernel set (those it left out) in
+// float-float (soft_group_ff); their loss and gradient sums, Kahan-summed in group order, are
+// added to the task's partials. Runs after the main kernel on the same stream; features are read
+// from global memory.
+template <bool BWD, bool CAT>
+__global__ void __launch_bounds__(SOFT_W * 32) k_soft_ff(SoftKArgs a)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t task = (int64_t)blockIdx.x * SOFT_W + w;
+    if (*a.status || task >= (int64_t)a.P * a.nchunks) return;
+    const int p = (int)(task % a.P);
+    const int ch = (int)(task / a.P);
+    if (!a.ffmark[(int64_t)ch * a.P + p]) return;
+    const size_t per_warp = soft_per_warp(a.maxR, a.maxC, a.probs != nullptr);
+    float *base_w = sm + per_warp * w;
+    float(*lu)[SOFT_G] = reinterpret_cast<float(*)[SOFT_G]>(base_w);
+    float(*acc)[4] = reinterpret_cast<float(*)[4]>(base_w + (size_t)(a.maxR + 1) * SOFT_G);
+    float(*lq)[SOFT_G] = a.probs ? reinterpret_cast<float(*)[SOFT_G]>(base_w + (size_t)(a.maxR + 1) * SOFT_G +
+                                                                    (size_t)a.maxC * 4)
+                                 : nullptr;
+    const int rb = a.set_rule_off[p], re = a.set_rule_off[p + 1];
+    const int cb = a.rule_cond_off[rb], ce = a.rule_cond_off[re];
+    const int deflt = a.set_default[p];
+    if (BWD) {
+        for (int i = lane; i < (ce - cb); i += 32) {
+            acc[i][0] = 0.f; acc[i][1] = 0.f; acc[i][2] = 0.f; acc[i][3] = 0.f;
+        }
+        __syncwarp();
+    }
+    float loss_s = 0.f, loss_c = 0.f;
+    const int64_t s0 = (int64_t)ch * a.chunk;
+    const int64_t s1 = min(s0 + a.chunk, a.N);
+    const uint32_t *fbits = a.ffbits + ((int64_t)ch * a.P + p) * a.ff_wpt;
+    uint32_t fw = 0;
+    int gi = 0;
+    for (int64_t nb = s0; nb < s1; nb += SOFT_G, ++gi) {
+        if ((gi & 31) == 0) fw = fbits[gi >> 5];
+        if (!((fw >> (gi & 31)) & 1u)) continue;
+        uint32_t valid = 0;
+#pragma unroll
+        for (int v = 0; v < SOFT_V; ++v) valid |= (nb + lane + 32 * v < s1 ? 1u : 0u) << v;
+        const XView x{a.Xt + nb + lane, a.n_pad};
+        soft_group_ff<BWD, CAT, SOFT_V>(a, p, rb, re - rb, cb, deflt, nb, valid, x, lq, lu, acc, lane, loss_s,
+                                        loss_c);
+    }
+    float ls = loss_s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(FULL, ls, o);
+    if (lane == 0) a.part_loss[(int64_t)ch * a.P + p] += ls;
+    if (BWD) {
+        __syncwarp();
+        for (int i = lane; i < (ce - cb); i += 32) {
+            a.part_ga[(int64_t)ch * a.Ccap + cb + i] += acc[i][0];
+            a.part_gbt[(int64_t)ch * a.Ccap + cb + i] += acc[i][2];
+        }
     }
 }
 
@@ -704,6 +1044,8 @@ static void set_soft_attributes(Ctx *ctx)
                          (int)ctx->smem_optin - SOFT_TILE_STATIC);
     cudaFuncSetAttribute(k_soft_tile<false, CAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)ctx->smem_optin - SOFT_TILE_STATIC);
+    cudaFuncSetAttribute(k_soft_ff<true, CAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
+    cudaFuncSetAttribute(k_soft_ff<false, CAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin);
     cudaGetLastError();
 }
 
@@ -769,13 +1111,21 @@ static void launch_soft_kernel(Ctx *ctx, const SoftKArgs &k, bool tiled, bool bw
     }
 }
 
+// Words of the float-float group bits for P sets over N samples, for any chunking of at most
+// SOFT_MAX_CHUNKS chunks: chunks x ceil(groups per chunk / 32) <= N / 2048 + 2 * SOFT_MAX_CHUNKS.
+static size_t ff_words(int P, int64_t N)
+{
+    return (size_t)P * (size_t)(N / 2048 + 2 * SOFT_MAX_CHUNKS + 1);
+}
+
 // Scratch layout of one soft call: records [C], order [P], per-chunk losses [chunks][P], the work
-// counter and maxima [4], per-chunk gradient sums [chunks][C] twice (adjoint only).
+// counter and maxima [4], per-chunk gradient sums [chunks][C] twice (adjoint only), the tasks'
+// float-float marks [chunks][P] and group bits.
 struct SoftScratchLayout {
-    size_t recs, order, part_loss, next, part_ga, part_gbt, total;
+    size_t recs, order, part_loss, next, part_ga, part_gbt, ffmark, ffbits, total;
 };
 
-static SoftScratchLayout soft_layout(int64_t C, int P, int nchunks, bool bwd)
+static SoftScratchLayout soft_layout(int64_t C, int P, int nchunks, bool bwd, int64_t N)
 {
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     SoftScratchLayout L{};
@@ -786,13 +1136,15 @@ static SoftScratchLayout soft_layout(int64_t C, int P, int nchunks, bool bwd)
     L.next = o; o += 256;
     L.part_ga = o; o += bwd ? up(sizeof(float) * (size_t)nchunks * C) : 0;
     L.part_gbt = o; o += bwd ? up(sizeof(float) * (size_t)nchunks * C) : 0;
+    L.ffmark = o; o += up((size_t)nchunks * P);
+    L.ffbits = o; o += up(sizeof(uint32_t) * ff_words(P, N));
     L.total = o;
     return L;
 }
 
-size_t soft_scratch_bytes(int64_t cap_c, int cap_p)
+size_t soft_scratch_bytes(int64_t cap_c, int cap_p, int64_t N)
 {
-    return soft_layout(std::max<int64_t>(cap_c, 1), std::max(cap_p, 1), SOFT_MAX_CHUNKS, true).total;
+    return soft_layout(std::max<int64_t>(cap_c, 1), std::max(cap_p, 1), SOFT_MAX_CHUNKS, true, N).total;
 }
 
 // `repeat`: a later step on the caller's scratch over the same structure as the step before it
@@ -819,16 +1171,20 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     float *part_loss = nullptr, *part_ga = nullptr, *part_gbt = nullptr;
     int32_t *next = nullptr;   // [0] work counter, [1..2] max rules / conditions per set
     int32_t *order = nullptr;
+    uint8_t *ffmark = nullptr;
+    uint32_t *ffbits = nullptr;
     const bool bwd = s.dloss != nullptr;
     cudaError_t ae = cudaSuccess;
     if (pre) {                       // the caller's scratch, laid out for at most SOFT_MAX_CHUNKS chunks
-        const SoftScratchLayout L = soft_layout(Ccap, P, SOFT_MAX_CHUNKS, bwd);
+        const SoftScratchLayout L = soft_layout(Ccap, P, SOFT_MAX_CHUNKS, bwd, s.N);
         recs = reinterpret_cast<SoftRec *>(pre + L.recs);
         order = reinterpret_cast<int32_t *>(pre + L.order);
         part_loss = reinterpret_cast<float *>(pre + L.part_loss);
         next = reinterpret_cast<int32_t *>(pre + L.next);
         part_ga = bwd ? reinterpret_cast<float *>(pre + L.part_ga) : nullptr;
         part_gbt = bwd ? reinterpret_cast<float *>(pre + L.part_gbt) : nullptr;
+        ffmark = reinterpret_cast<uint8_t *>(pre + L.ffmark);
+        ffbits = reinterpret_cast<uint32_t *>(pre + L.ffbits);
     } else {
         ae = dev_alloc_async(&recs, sizeof(SoftRec) * Ccap, stream);
         if (ae == cudaSuccess) ae = dev_alloc_async(&order, sizeof(int32_t) * (size_t)P, stream);
@@ -836,9 +1192,12 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
         if (ae == cudaSuccess) ae = dev_alloc_async(&next, sizeof(int32_t) * 4, stream);
         if (ae == cudaSuccess && bwd) ae = dev_alloc_async(&part_ga, sizeof(float) * (size_t)nchunks * Ccap, stream);
         if (ae == cudaSuccess && bwd) ae = dev_alloc_async(&part_gbt, sizeof(float) * (size_t)nchunks * Ccap, stream);
+        if (ae == cudaSuccess) ae = dev_alloc_async(&ffmark, (size_t)nchunks * P, stream);
+        if (ae == cudaSuccess) ae = dev_alloc_async(&ffbits, sizeof(uint32_t) * ff_words(P, s.N), stream);
     }
     if (ae != cudaSuccess) {         // release what was taken before the failure
-        for (void *q : {(void *)recs, (void *)order, (void *)part_loss, (void *)next, (void *)part_ga, (void *)part_gbt})
+        for (void *q : {(void *)recs, (void *)order, (void *)part_loss, (void *)next, (void *)part_ga, (void *)part_gbt,
+                        (void *)ffmark, (void *)ffbits})
             if (q) cudaFreeAsync(q, stream);
         return cuda_fail(ae, "soft scratch");
     }
@@ -871,12 +1230,15 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     k.n_pad = s.n_pad;
     k.K = s.K;
     k.inv_tau = 1.0f / s.tau;
+    k.inv_tau_lo = (float)(1.0 / (double)s.tau - (double)k.inv_tau);
     k.nchunks = nchunks;
     k.chunk = (int32_t)chunk;
     k.part_loss = part_loss;
     k.part_ga = part_ga;
     k.part_gbt = part_gbt;
     k.order = order;
+    k.ffmark = ffmark;
+    k.ffbits = ffbits;
     k.probs = s.probs;
     k.backward = bwd;
     k.next = next;
@@ -939,10 +1301,22 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
             k.nchunks = nchunks;
             k.chunk = (int32_t)chunk;
         }
+        k.ff_wpt = (int32_t)(((k.chunk + SOFT_G - 1) / SOFT_G + 31) / 32);
         {
             TimedLaunch tl(ctx, TK_SOFT, stream);
             if (b.cond_set) launch_soft_kernel<true>(ctx, k, tiled, bwd, s.F, smem, per_warp, sh, stream);
             else launch_soft_kernel<false>(ctx, k, tiled, bwd, s.F, smem, per_warp, sh, stream);
+        }
+        {   // groups beyond float32's resolution (usually none: the kernel's warps exit at once)
+            const unsigned ffgrid = (unsigned)(((int64_t)P * k.nchunks + SOFT_W - 1) / SOFT_W);
+            if (b.cond_set) {
+                if (bwd) k_soft_ff<true, true><<<ffgrid, SOFT_W * 32, smem, stream>>>(k);
+                else k_soft_ff<false, true><<<ffgrid, SOFT_W * 32, smem, stream>>>(k);
+            } else {
+                if (bwd) k_soft_ff<true, false><<<ffgrid, SOFT_W * 32, smem, stream>>>(k);
+                else k_soft_ff<false, false><<<ffgrid, SOFT_W * 32, smem, stream>>>(k);
+            }
+            count_launch(ctx);
         }
         if (bwd)                      // the gradients and (when asked) the loss in one launch
             k_soft_reduce_grad<<<P, 128, 0, stream>>>(part_ga, part_gbt, part_loss, nchunks, b.set_rule_off,
@@ -962,6 +1336,8 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
         cudaFreeAsync(part_loss, stream);
         cudaFreeAsync(next, stream);
         if (bwd) { cudaFreeAsync(part_ga, stream); cudaFreeAsync(part_gbt, stream); }
+        cudaFreeAsync(ffmark, stream);
+        cudaFreeAsync(ffbits, stream);
     }
     return rc;
 }
@@ -1028,6 +1404,10 @@ void preload_soft_kernels()
     cudaFuncGetAttributes(&fa, k_soft_tile<true, false>);
     cudaFuncGetAttributes(&fa, k_soft_tile<false, true>);
     cudaFuncGetAttributes(&fa, k_soft_tile<true, true>);
+    cudaFuncGetAttributes(&fa, k_soft_ff<false, false>);
+    cudaFuncGetAttributes(&fa, k_soft_ff<true, false>);
+    cudaFuncGetAttributes(&fa, k_soft_ff<false, true>);
+    cudaFuncGetAttributes(&fa, k_soft_ff<true, true>);
     cudaFuncGetAttributes(&fa, k_check_sets_soft);
     cudaFuncGetAttributes(&fa, k_pack_soft);
     cudaFuncGetAttributes(&fa, k_soft_order);

@@ -14,10 +14,11 @@ struct SoftAdam {
     float lr = 0.f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
 };
 
-// Bytes of scratch for a soft step over at most `cap_p` sets and `cap_c` conditions.
-size_t soft_scratch_bytes(int64_t cap_c, int cap_p);
+// Bytes of scratch for a soft step over at most `cap_p` sets and `cap_c` conditions on a dataset
+// of N samples.
+size_t soft_scratch_bytes(int64_t cap_c, int cap_p, int64_t N);
 
-// soft_step_known on `scratch` (soft_scratch_bytes(cap_c, cap_p) bytes, 256-byte aligned);
+// soft_step_known on `scratch` (soft_scratch_bytes(cap_c, cap_p, N) bytes, 256-byte aligned);
 // a.b.P <= cap_p and the batch's condition capacity <= cap_c. `repeat`: the previous step on this
 // scratch had the same structure (sets, rules, features, classes; only a, b, t differ), so its
 // validation and set order are reused. `adam` (may be null): the update applied to the

@@ -73,11 +73,13 @@ def test_injected_allocation_failures(ctx, orc):
         check_counts(ctx, orc, X, y, K, b, ds)
         db = rs.DeviceBatch.from_host(b)
         dl = torch.ones(b.P, device="cuda")
-        for skip in range(7):          # outputs, then the soft scratch arrays one by one
+        for skip in range(9):          # outputs, then the soft scratch arrays one by one
             lib.rs_inject_alloc_failures(skip, 1)
             with pytest.raises(rs.RsError) as e:
                 ctx.soft_bwd(ds, db, 0.3, dl)
             assert e.value.code == -3
+        lib.rs_inject_alloc_failures(9, 1)    # there is no tenth allocation: the call succeeds
+        ctx.soft_bwd(ds, db, 0.3, dl)
         lib.rs_inject_alloc_failures(0, 0)
         ga, gb, gt, loss = ctx.soft_bwd(ds, db, 0.3, dl)
         torch.cuda.synchronize()

@@ -88,7 +88,7 @@ def test_soft_multiclass_probs(ctx, orc):
     got = soft_gpu(ctx, X, y, 4, b, 0.5, np.ones(b.P), probs=True)
     ref = orc.soft(X, y, 4, b, 0.5, dloss=np.ones(b.P), want_probs=True, want_mag=True)
     assert np.allclose(got["probs"].sum(axis=2), 1.0, atol=1e-5)
-    assert np.allclose(got["probs"], ref["probs"], rtol=1e-4, atol=1e-6)
+    assert np.allclose(got["probs"], ref["probs"], rtol=RTOL, atol=1e-30)
     assert np.array_equal(got["loss_fwd"], got["loss"])     # the forward and the fused pass agree
     check_against_oracle(got, ref)
 
@@ -198,3 +198,74 @@ def test_soft_full_size_sampled(ctx, orc):
     for n in ("a", "b", "t"):
         got["grad_" + n] = got_all["grad_" + n][conds]
     check_against_oracle(got, ref)
+
+
+# ------------------------------------------------- large margins (fine-tuned coefficients)
+
+def large_margin_sets(M):
+    """Sets whose samples meet rules with margins of about M tau (tau = 0.1; x0..x2 in [0.5, 1.5])
+    before the rule of their label: a single huge condition, a rule of three huge conditions (where
+    1 - q rounds to 0 in float32 and must come from the margins), two huge rules in a row, a rule
+    that is huge only on some samples, and mixed signs."""
+    A = np.float32(M / 10.0)
+    mod = (3, -1, synth.GT, np.float32(0.7), 0.0, np.float32(0.1))          # a moderate condition
+    T = lambda f, a, op=synth.GT: (f, -1, op, np.float32(a), 0.0, np.float32(0.0))
+    sets = [
+        [(0, [T(0, A)]), (1, [mod])],                                        # huge, then the label
+        [(0, [T(0, A), T(1, 1.3 * A), T(2, 0.7 * A)]), (1, [mod])],          # all three huge
+        [(0, [T(0, A)]), (0, [T(1, A)]), (1, [mod])],                        # two huge rules
+        [(1, [T(0, A), T(3, 3.0)]), (0, [T(2, -A, synth.LT)]), (1, [mod])],  # huge '<' with -a
+        [(0, [T(0, A), T(3, A)])],                                           # sign of x3 decides
+    ]
+    return synth.from_lists(sets, [1, 1, 0, 0, 1])
+
+
+def large_margin_data(N, seed):
+    rng = np.random.default_rng(seed)
+    X = np.empty((N, 4), np.float32)
+    X[:, :3] = rng.uniform(0.5, 1.5, (N, 3))
+    X[:, 3] = rng.normal(size=N)
+    y = rng.integers(0, 2, N).astype(np.int32)
+    return X, y
+
+
+@pytest.mark.parametrize("M", [50.0, 103.0, 200.0, 1000.0])
+def test_soft_large_margins_vs_oracle(ctx, orc, M):
+    """Margins of 50 to 1000 tau on every sample of some rules: loss and gradients within the
+    soft tolerance of the float64 oracle (pinned at such margins by closed forms and
+    arbitrary-precision references), class probabilities within 1e-5 relative."""
+    X, y = large_margin_data(5003, int(M))
+    b = large_margin_sets(M)
+    tau = np.float32(0.1)
+    dl = np.linspace(0.5, 1.5, b.P)
+    got = soft_gpu(ctx, X, y, 2, b, tau, dl, probs=True)
+    ref = orc.soft(X, y, 2, b, tau, dloss=dl, want_mag=True, want_probs=True)
+    assert np.isfinite(got["loss"]).all() and np.isfinite(ref["loss"]).all()
+    assert (ref["loss"] > 0.2 * M).any()              # the huge margins reach the loss
+    check_against_oracle(got, ref)
+    assert np.array_equal(got["loss_fwd"], got["loss"])
+    assert np.allclose(got["probs"], ref["probs"], rtol=RTOL, atol=1e-30)
+
+
+def test_soft_fig1c_rule_vs_oracle(ctx, orc):
+    """The fine-tuned rule set of Fig. 1c (pair coefficient -7275.88) on data of the worked
+    example's scale: margins of thousands of tau on the pair condition."""
+    rng = np.random.default_rng(11)
+    N = 4001
+    X = np.stack([rng.uniform(6, 28, N),            # mean radius
+                  rng.uniform(0.001, 0.03, N),      # fractal dimension error
+                  rng.uniform(0.03, 1.06, N),       # worst compactness
+                  rng.uniform(0.15, 0.66, N),       # worst symmetry
+                  rng.uniform(0.75, 22.0, N),       # perimeter error
+                  rng.uniform(140, 2500, N)], axis=1).astype(np.float32)
+    y = rng.integers(0, 2, N).astype(np.int32)
+    f = np.float32
+    rules = [(0, [(0, -1, synth.GT, f(1), 0.0, f(0.06)), (1, 2, synth.GT, f(-1), f(-7275.88), 0.0),
+                  (3, -1, synth.GT, f(1), 0.0, f(-3.69))]),
+             (1, [(4, -1, synth.GT, f(-1), 0.0, f(-0.98)), (5, -1, synth.GT, f(-1), 0.0, f(-0.24))])]
+    b = synth.from_lists([rules, rules[::-1]], [1, 0])
+    for tau in (0.1, 1.0):
+        got = soft_gpu(ctx, X, y, 2, b, tau, np.ones(b.P))
+        ref = orc.soft(X, y, 2, b, tau, dloss=np.ones(b.P), want_mag=True)
+        assert np.isfinite(got["loss"]).all()
+        check_against_oracle(got, ref)
