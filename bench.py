@@ -10,12 +10,14 @@ Extra legs on the same line: the soft fine-tuning pass (P=1024 x R=32 x C=4, N=2
 tau=0.1, forward + adjoint). The CPU oracle is timed on a bounded sample of the same workload.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--no-extras]
-Multi-GPU: torchrun --nproc-per-node N bench.py --gpus N  (each rank evaluates its own
-population on its own GPU: weak scaling, no collective on the data path).
+Multi-GPU: torchrun --nproc-per-node N bench.py --gpus N  (sample sharding: every rank evaluates
+the same population on its own 2^20 samples and one int32 all-reduce per step sums the counts:
+weak scaling).
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -120,6 +122,25 @@ def hard_algorithmic_ops(batch, N):
     return N * (n_thr + 3 * n_pair) + 3 * batch.R * ((N + 31) // 32)
 
 
+def executed_work(prof, batch, N):
+    """The rank-coded evaluator's own count of the work it did (one call in a work-counting
+    context, RS_CTX_COUNT_WORK): per launch, the records walked (one per condition, 128 samples each), the pair / product /
+    membership rows among them and the rule ends, as algorithmic operations counted like
+    hard_algorithmic_ops (1 per threshold sample, 3 per pair sample, 3 word operations per rule
+    end per 32 samples), and the share of the nominal records that were walked."""
+    n = max(1, prof.get("counted_launches", 0))
+    rec = prof.get("hard_records_walked", 0) / n
+    if rec <= 0:
+        return None
+    rows = prof.get("hard_rows_walked", 0) / n
+    ends = prof.get("hard_rule_ends_walked", 0) / n
+    tiles = (N + 127) // 128
+    return {"ops_per_launch": 128 * ((rec - rows) + 3 * rows) + 12 * ends,
+            "records_walked_per_launch": rec,
+            "records_walked_share": rec / (batch.C * tiles),
+            "set_tiles_per_launch": prof.get("hard_set_tiles", 0) / n}
+
+
 def source_hash():
     h = hashlib.sha256()
     for f in ("hard_eval.cu", "hard_eval4.cu", "hard_eval5.cu", "eval_rank.cuh", "eval_core.cuh", "pack.cu",
@@ -182,10 +203,16 @@ def hard_leg(args, rank, dev, ctx_mod, w):
     if args.no_autotune or args.tile is not None:
         ctx.set_tile_config(tile)
     P, K, N = w.batch.P, w.K, w.N
-    out = (torch.empty(P, dtype=torch.int32, device=dev),
-           torch.empty((P, K), dtype=torch.int32, device=dev), None)
-    for _ in range(args.warmup):
+    counts = torch.empty(P + P * K, dtype=torch.int32, device=dev)
+    out = (counts[:P], counts[P:].view(P, K), None)
+
+    def step():
         ctx.eval_hard(ds, db, K, out=out, stream=stream)
+        if ctx_mod.world > 1:          # sample sharding: the one exchange step, on the same stream
+            with torch.cuda.stream(stream):
+                ctx_mod.pg.all_reduce(counts)
+    for _ in range(args.warmup):
+        step()
     stream.synchronize()
     ctx_mod.barrier()
     ctx.profile(reset=True)
@@ -194,7 +221,7 @@ def hard_leg(args, rank, dev, ctx_mod, w):
     with ClockSampler(dev) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            ctx.eval_hard(ds, db, K, out=out, stream=stream)
+            step()
         e1.record(stream)
         e1.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
@@ -234,8 +261,20 @@ def hard_leg(args, rank, dev, ctx_mod, w):
     f1.record(stream)
     f1.synchronize()
     e2e_ms = max(f0.elapsed_time(f1), (time.perf_counter() - t0) * 1e3) / args.steps
-    e2e_ok = bool(np.array_equal(hc, correct))
+    e2e_ok = bool(np.array_equal(hc, correct)) if ctx_mod.world == 1 else None   # shard counts vs summed
     ctx2.close()
+    # one more call, untimed, in a context whose evaluator counts the work it does
+    ctx3 = rs.Context(dev, flags=rs.CTX_COUNT_WORK | rs.CTX_NO_GRAPH)
+    ds3 = ctx3.dataset(w.X, w.y, w.K)
+    ctx3.set_tile_config(tile)
+    ctx3.profile(reset=True)
+    ctx3.eval_hard(ds3, db, K, out=out, stream=stream)
+    stream.synchronize()
+    walked = ctx3.profile(reset=True)
+    ctx3.close()
+    for f in ("hard_records_walked", "hard_rows_walked", "hard_rule_ends_walked", "hard_set_tiles"):
+        prof[f] = walked[f]
+    prof["counted_launches"] = 1
     ctx.close()
     return {"ms": ms, "prof": prof, "tile": tile, "clocks": clk.summary(), "e2e_ms": e2e_ms,
             "e2e_ok": e2e_ok, "h2d": hb_nbytes(hb), "d2h": hc.nbytes + hpc.nbytes}
@@ -421,88 +460,16 @@ def evolution_leg(args, dev):
             "cpu_cores": oracle.num_threads(0)}
 
 
-def paper_evolution_leg(args, dev):
-    """The paper's experiment shape (Sec. 4): a population of 100 rule sets (R <= 8, C <= 3) evolved
-    on N=569 x F=30 two-class data for 100 generations, without and with back-propagation
-    fine-tuning of every set each generation (50 Adam steps, Baldwinian selection), on the GPU.
-    The CPU arm does the same work per generation with the oracle on the host cores (hard
-    evaluation and the evolution step; with fine-tuning, per step a float64 soft forward + adjoint
-    of all sets and an Adam update), timed over a few generations. The paper reports the CPU/GPU
-    wall-clock ratio on this shape: at least five-fold on a T4, with and without fine-tuning."""
-    import dataclasses
-    import torch
-    import oracle
-    from paper_2406_01821_gb300 import rs, synth
-    w = synth.plain_hard(seed=0)
-    X, y, K = w.X, w.y, w.K
-    P, RMAX, CMAX, G, STEPS, TAU, LR = 100, 8, 3, 100, 50, 0.1, 1e-2
-    pop = synth.initial_population(X, y, K, P, RMAX, CMAX, seed=0)
-    ctx = rs.Context(dev)
-    ds = ctx.dataset(X, y, K)
-    stream = torch.cuda.Stream(device=dev)
-    tuned = dict(tune_every=1, tune_top=P, tune_steps=STEPS, tau=TAU, lr=LR)
-    ctx.evolve(ds, pop, generations=2, elite=1, seed=1, stream=stream)                # warm-up
-    ctx.evolve(ds, pop, generations=2, elite=1, seed=1, stream=stream, **tuned)
-    t0 = time.perf_counter()
-    ctx.evolve(ds, pop, generations=G, elite=1, seed=1, stream=stream)
-    t_gpu = (time.perf_counter() - t0) / G
-    t0 = time.perf_counter()
-    _, _, best, _ = ctx.evolve(ds, pop, generations=G, elite=1, seed=1, stream=stream, **tuned)
-    t_gpu_tuned = (time.perf_counter() - t0) / G
-    # the public fine-tuning call on the whole pool (the paper's 50 epochs of gradient updates)
-    db = rs.DeviceBatch.from_host(synth.batch_from_population(pop), device=f"cuda:{dev}")
-    ctx.finetune(ds, db, TAU, LR, STEPS, stream=stream)
-    t0 = time.perf_counter()
-    ctx.finetune(ds, db, TAU, LR, STEPS, stream=stream)
-    t_finetune = time.perf_counter() - t0
-    ctx.close()
-
-    def cpu_generations(gens, finetune):
-        cur = pop
-        t0 = time.perf_counter()
-        for g in range(gens):
-            b = synth.batch_from_population(cur)
-            fit, _, _ = oracle.eval_hard(X, y, K, b, want_per_class=False)
-            if finetune:
-                theta = [b.cond_a.astype(np.float64), b.cond_b.astype(np.float64), b.cond_t.astype(np.float64)]
-                m1 = [np.zeros_like(v) for v in theta]
-                m2 = [np.zeros_like(v) for v in theta]
-                for step in range(1, STEPS + 1):
-                    bt = dataclasses.replace(b, cond_a=theta[0].astype(np.float32),
-                                             cond_b=theta[1].astype(np.float32), cond_t=theta[2].astype(np.float32))
-                    r = oracle.soft(X, y, K, bt, TAU, dloss=np.ones(P))
-                    for i, gr in enumerate((r["grad_a"], r["grad_b"], r["grad_t"])):
-                        m1[i] = 0.9 * m1[i] + 0.1 * gr
-                        m2[i] = 0.999 * m2[i] + 0.001 * gr * gr
-                        theta[i] -= LR * (m1[i] / (1 - 0.9 ** step)) / (np.sqrt(m2[i] / (1 - 0.999 ** step)) + 1e-8)
-                bt = dataclasses.replace(b, cond_a=theta[0].astype(np.float32),
-                                         cond_b=theta[1].astype(np.float32), cond_t=theta[2].astype(np.float32))
-                fit2, _, _ = oracle.eval_hard(X, y, K, bt, want_per_class=False)
-                fit = np.maximum(fit, fit2)
-            cur = oracle.evolve_step(cur, fit, 1, g, 1, X, K)
-        return (time.perf_counter() - t0) / gens
-
-    cpu_generations(2, False)                  # warm-up (the oracle's thread pool)
-    t_cpu = cpu_generations(50, False)
-    t_cpu_tuned = cpu_generations(2, True)
-    return {"workload": f"paper-shape evolution P={P} R<=8 C<=3 N={len(X)} F=30 K=2 generations={G}; "
-                        f"fine-tuned arm: all {P} sets x {STEPS} Adam steps every generation",
-            "gpu_generations_per_s": 1.0 / t_gpu, "gpu_generations_per_s_finetuned": 1.0 / t_gpu_tuned,
-            "cpu_oracle_generations_per_s": 1.0 / t_cpu, "cpu_oracle_generations_per_s_finetuned": 1.0 / t_cpu_tuned,
-            "cpu_over_gpu_time": t_cpu / t_gpu, "cpu_over_gpu_time_finetuned": t_cpu_tuned / t_gpu_tuned,
-            "best_first_last_finetuned": [int(best[0]), int(best[-1])],
-            "rs_finetune_ms": t_finetune * 1e3,
-            "cpu_cores": oracle.num_threads(0), "cpu_sample": "50 generations after 2 of warm-up (2 with fine-tuning)",
-            "paper": "CPU/GPU wall-clock ratio at least 5x on a T4 with and without fine-tuning (Sec. 4)"}
+SERVE_LOADS = (0.7, 1.0, 1.3)
 
 
 def serving_leg(args, dev):
     """Continuous batching of fitness requests from 256 concurrent evolution runs (each with its own
     resident dataset: N log-uniform [500, 500000], F ~ U{8..256}, K ~ U{2..10}); request
-    populations P log-uniform [16, 2048], R ~ U{1..64}, C ~ U{1..8}; Poisson arrivals at 0.7 of the
-    measured capacity of the plain one-request-per-launch evaluator; 40 GB budget. Latency =
-    completion - arrival, for the served path and for the plain evaluator (FIFO, one launch per
-    request) on the same GPU."""
+    populations P log-uniform [16, 2048], R ~ U{1..64}, C ~ U{1..8}; 40 GB budget. Poisson
+    arrivals at 0.7, 1.0 and 1.3 of the measured capacity of the plain one-request-per-launch
+    evaluator. Latency = completion - arrival, for the served path and for the plain evaluator
+    (FIFO, one launch per request) on the same GPU and the same arrival times."""
     import queue
     import torch
     from paper_2406_01821_gb300 import rs, synth
@@ -522,6 +489,7 @@ def serving_leg(args, dev):
         i = int(rng.integers(0, len(runs_N)))
         b = synth.random_rulesets(qtabs[i], int(runs_K[i]), int(Ps[j]), (1, 64), (1, 8), 5000 + j)
         reqs.append((i, rs.HostBatch(b), b.nominal_conditions() * int(runs_N[i])))
+    total = float(sum(r[2] for r in reqs))
     # plain capacity: mean service time of one-launch evaluation, back to back
     for j in range(8):
         i, hb, _ = reqs[j]
@@ -531,10 +499,11 @@ def serving_leg(args, dev):
         i, hb, _ = reqs[j]
         ctx.eval_hard(dss[i], hb, int(runs_K[i]))
     service = (time.perf_counter() - t0) / min(M, 64)
-    rate = 0.7 / service
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=M))
+    for j in range(8):            # warm-up of the served path: scheduler, kernel, staging pool
+        i, hb, _ = reqs[j]
+        ctx.poll(ctx.submit(dss[i], hb), hb.P, int(runs_K[i]), timeout_us=60_000_000)
 
-    def drive(submit, finish_all):
+    def drive(arrivals, submit, finish_all):
         t_start = time.perf_counter() + 0.05
         for j in range(M):
             wait = t_start + arrivals[j] - time.perf_counter()
@@ -543,55 +512,67 @@ def serving_leg(args, dev):
             submit(j, t_start + arrivals[j])
         return finish_all(), t_start
 
-    # plain: FIFO worker, one rs_eval_hard launch per request
-    q = queue.Queue()
-    lat_plain = [0.0] * M
+    def summ(lat, dur):
+        a = np.array(lat) * 1e3
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "mean_ms": float(a.mean()), "requests_per_s": M / dur, "condition_evals_per_s": total / dur}
 
-    def worker():
-        while True:
-            item = q.get()
-            if item is None:
-                return
-            j, t_arr = item
+    def at_load(load, seed):
+        arrivals = np.cumsum(np.random.default_rng(seed).exponential(service / load, size=M))
+        # plain: FIFO worker, one rs_eval_hard launch per request
+        q = queue.Queue()
+        lat_plain = [0.0] * M
+
+        def worker():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                j, t_arr = item
+                i, hb, _ = reqs[j]
+                ctx.eval_hard(dss[i], hb, int(runs_K[i]))
+                lat_plain[j] = time.perf_counter() - t_arr
+        th = threading.Thread(target=worker)
+        th.start()
+
+        def fin_plain():
+            q.put(None)
+            th.join()
+            return time.perf_counter()
+        t_end, t_start = drive(arrivals, lambda j, ta: q.put((j, ta)), fin_plain)
+        dur_plain = t_end - t_start
+        # served: rs_submit at arrival, completion times from the library's ticket info
+        tickets = [0] * M
+        t_arr_ns = [0] * M
+
+        def submit(j, ta):
             i, hb, _ = reqs[j]
-            ctx.eval_hard(dss[i], hb, int(runs_K[i]))
-            lat_plain[j] = time.perf_counter() - t_arr
-    th = threading.Thread(target=worker)
-    th.start()
+            tickets[j] = ctx.submit(dss[i], hb)
+            t_arr_ns[j] = time.monotonic_ns() - int((time.perf_counter() - ta) * 1e9)
 
-    def fin_plain():
-        q.put(None)
-        th.join()
-        return time.perf_counter()
-    t_end, t_start = drive(lambda j, ta: q.put((j, ta)), fin_plain)
-    dur_plain = t_end - t_start
-    # served: rs_submit at arrival, completion times from the library's ticket info
-    tickets = [0] * M
-    t_arr_ns = [0] * M
+        lat_srv = [0.0] * M
+        split = np.zeros((M, 3))      # arrival -> submit returned, -> admitted, -> done (seconds)
 
-    def submit(j, ta):
-        i, hb, _ = reqs[j]
-        tickets[j] = ctx.submit(dss[i], hb)
-        t_arr_ns[j] = time.monotonic_ns() - int((time.perf_counter() - ta) * 1e9)
+        def fin_served():
+            for j in range(M):
+                i, hb, _ = reqs[j]
+                out = ctx.poll(tickets[j], hb.P, int(runs_K[i]), timeout_us=120_000_000)
+                lat_srv[j] = (out[2]["done_ns"] - t_arr_ns[j]) / 1e9
+                split[j] = [(out[2]["submit_ns"] - t_arr_ns[j]) / 1e9,
+                            (out[2]["admit_ns"] - out[2]["submit_ns"]) / 1e9,
+                            (out[2]["done_ns"] - out[2]["admit_ns"]) / 1e9]
+            return time.perf_counter()
+        t_end, t_start = drive(arrivals, submit, fin_served)
+        dur_srv = t_end - t_start
+        pct = lambda c, q_: float(np.percentile(split[:, c], q_) * 1e3)
+        return {"offered_load_x_plain_capacity": load, "arrival_rate_per_s": load / service,
+                "served": summ(lat_srv, dur_srv), "plain_one_launch_per_request": summ(lat_plain, dur_plain),
+                "served_p50_split_ms": {"arrival_to_queued": pct(0, 50), "queued_to_admitted": pct(1, 50),
+                                        "admitted_to_done": pct(2, 50)},
+                "served_p99_split_ms": {"arrival_to_queued": pct(0, 99), "queued_to_admitted": pct(1, 99),
+                                        "admitted_to_done": pct(2, 99)}}
 
-    lat_srv = [0.0] * M
-    split = np.zeros((M, 3))      # arrival -> submit returned, -> admitted, -> done (seconds)
-    for j in range(8):            # warm-up, as for the plain arm: scheduler, kernel, staging pool
-        i, hb, _ = reqs[j]
-        ctx.poll(ctx.submit(dss[i], hb), hb.P, int(runs_K[i]), timeout_us=60_000_000)
-
-    def fin_served():
-        last = 0
-        for j in range(M):
-            i, hb, _ = reqs[j]
-            out = ctx.poll(tickets[j], hb.P, int(runs_K[i]), timeout_us=120_000_000)
-            lat_srv[j] = (out[2]["done_ns"] - t_arr_ns[j]) / 1e9
-            split[j] = [(out[2]["submit_ns"] - t_arr_ns[j]) / 1e9, (out[2]["admit_ns"] - out[2]["submit_ns"]) / 1e9,
-                        (out[2]["done_ns"] - out[2]["admit_ns"]) / 1e9]
-            last = max(last, out[2]["done_ns"])
-        return time.perf_counter()
-    t_end, t_start = drive(submit, fin_served)
-    dur_srv = t_end - t_start
+    sweep = [at_load(load, 7 + k) for k, load in enumerate(SERVE_LOADS)]
     # capacity: every request at once (served) / back to back (plain)
     t0 = time.perf_counter()
     ts = [ctx.submit(dss[i], hb) for (i, hb, _) in reqs]
@@ -605,22 +586,10 @@ def serving_leg(args, dev):
     burst_plain = time.perf_counter() - t0
     stats = ctx.serving_stats()
     ctx.close()
-    total = float(sum(r[2] for r in reqs))
-
-    def summ(lat, dur):
-        a = np.array(lat) * 1e3
-        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
-                "mean_ms": float(a.mean()), "requests_per_s": M / dur, "condition_evals_per_s": total / dur}
-    return {"workload": f"serving {M} requests from 256 runs, Poisson arrivals at 0.7 x plain capacity, "
-                        "40 GB budget",
-            "served": summ(lat_srv, dur_srv), "plain_one_launch_per_request": summ(lat_plain, dur_plain),
-            "served_p50_split_ms": {"arrival_to_queued": float(np.percentile(split[:, 0], 50) * 1e3),
-                                    "queued_to_admitted": float(np.percentile(split[:, 1], 50) * 1e3),
-                                    "admitted_to_done": float(np.percentile(split[:, 2], 50) * 1e3)},
-            "served_p99_split_ms": {"arrival_to_queued": float(np.percentile(split[:, 0], 99) * 1e3),
-                                    "queued_to_admitted": float(np.percentile(split[:, 1], 99) * 1e3),
-                                    "admitted_to_done": float(np.percentile(split[:, 2], 99) * 1e3)},
-            "plain_service_ms": service * 1e3, "persistent_kernel_launches": stats["kernel_launches"],
+    return {"workload": f"serving {M} requests from 256 runs, Poisson arrivals at "
+                        f"{', '.join(str(x) for x in SERVE_LOADS)} x plain capacity, 40 GB budget",
+            "plain_service_ms": service * 1e3, "sweep": sweep,
+            "persistent_kernel_launches": stats["kernel_launches"],
             "capacity_condition_evals_per_s": {"served_all_at_once": total / burst_srv,
                                                "plain_back_to_back": total / burst_plain}}
 
@@ -671,7 +640,7 @@ class Dist:
 
 def whole_job_rate(d: Dist, units: float, ms: float) -> float:
     """Units processed by all ranks per second of the slowest rank (weak scaling: every rank
-    evaluates its own population)."""
+    evaluates the population on its own samples)."""
     return d.sum(units) / (d.max(ms) / 1e3)
 
 
@@ -721,7 +690,7 @@ def main():
                          "P=256) are the cases used for ncu captures")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="force a tile configuration id")
-    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,paper_evolution,serving,categorical,plain)")
+    ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving,categorical,plain)")
     ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -743,20 +712,27 @@ def main():
         d.close()
         return
     if args.workload == "ragged-small":
-        w = synth.ragged_hard(seed=d.rank, N=1 << 19, P=512)
+        w = synth.ragged_hard(seed=0, N=1 << 19, P=512)
     else:
-        w = synth.ragged_hard(seed=d.rank)     # each rank: its own population of 4096 sets
+        w = synth.ragged_hard(seed=0)
+    if d.world > 1 and d.rank > 0:
+        # sample sharding: every rank evaluates the same population on its own samples (rank r's
+        # rows drawn from the mixture generator with seed r); the counts are summed by one
+        # all-reduce per step
+        X, y = synth.gaussian_mixture(w.N, w.F, w.K, d.rank)
+        w = dataclasses.replace(w, X=X, y=y)
     res = hard_leg(args, d.rank, dev, d, w)
     ms_max = d.max(res["ms"])
     e2e_max = d.max(res["e2e_ms"])
     nominal = w.batch.nominal_conditions() * w.N
     total_nominal = d.sum(float(nominal))
-    total_sets = d.sum(float(w.batch.P))
+    total_sets = float(w.batch.P)
     value = whole_job_rate(d, float(nominal), res["ms"])
 
     prof = res["prof"]
     kern_ms = prof["hard_ms"] / max(1, prof["hard_launches"])
     ops = hard_algorithmic_ops(w.batch, w.N)
+    executed = executed_work(prof, w.batch, w.N)
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_ops = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
@@ -768,7 +744,7 @@ def main():
     extras = {}
     if not args.no_extras and d.rank == 0:
         skip = parse_skip(args.skip)
-        for name, leg in (("soft", soft_leg), ("evolution", evolution_leg), ("paper_evolution", paper_evolution_leg),
+        for name, leg in (("soft", soft_leg), ("evolution", evolution_leg),
                           ("serving", serving_leg), ("categorical", categorical_leg), ("plain", plain_leg)):
             if name in skip:
                 continue
@@ -784,19 +760,22 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": w.name, "global_batch": int(total_sets), "samples": w.N,
+            "config": {"workload": w.name, "global_batch": int(total_sets), "samples": w.N * d.world,
                        "features": w.F, "classes": w.K,
                        "nominal_cond_evals_per_step": int(total_nominal),
                        "tile_config": rs.tile_configs()[res["tile"]],
                        "l2": "inputs larger than L2 (feature-major dataset 512 MiB per GPU)",
-                       "parallelism": f"population per GPU x{d.world}"},
-            "rule_set_samples_per_s": total_sets * w.N / (ms_max / 1e3),
+                       "parallelism": ("one GPU" if d.world == 1 else
+                                       f"samples per GPU x{d.world}, one int32 all-reduce of the counts per step")},
+            "rule_set_samples_per_s": total_sets * w.N * d.world / (ms_max / 1e3),
             "roofline": {"bound": "alu", "achieved": ops / (kern_ms / 1e3) / 1e12,
                          "peak": peak_ops / 1e12, "unit": "Tops/s",
                          "frac": (ops / (kern_ms / 1e3)) / peak_ops, "traffic": traffic,
                          "kernel": KERNEL_OF_VERSION.get(rs.tile_configs()[res["tile"]]["form"], "k_hard"),
                          "kernel_ms": kern_ms,
                          "ops_per_launch": ops, "bottleneck_pipes": pipes,
+                         "executed": None if executed is None else {
+                             **executed, "frac": executed["ops_per_launch"] / (kern_ms / 1e3) / peak_ops},
                          "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                         f"({peak_src} max clock)"},
             "cpu_baseline": cb,

@@ -64,6 +64,8 @@ typedef struct rs_ctx rs_ctx;
 #define RS_CTX_NO_AUTOTUNE  4u   /* use the built-in tile heuristic, never time candidates */
 #define RS_CTX_PROFILE      8u   /* bracket the evaluator kernels with CUDA events (read with
                                     rs_profile_read); implies RS_CTX_NO_GRAPH */
+#define RS_CTX_COUNT_WORK  16u   /* the rank-coded hard evaluator counts the work it does
+                                    (rs_profile_read: records, rows and rule ends walked) */
 
 typedef struct {
     int32_t device;              /* CUDA device ordinal */
@@ -396,6 +398,14 @@ typedef struct {
     double hard_ms;          /* their summed CUDA-event durations (RS_CTX_PROFILE contexts) */
     int64_t soft_launches;   /* soft forward/adjoint kernel launches timed */
     double soft_ms;
+    /* Work the rank-coded hard evaluator actually did (RS_CTX_COUNT_WORK contexts), summed over its
+     * walks of one rule set over one 128-sample tile: records (conditions) walked before the
+     * all-claimed exit or the class-tail stop, pair / product / membership rows among them, rule
+     * ends among them, and the number of (set, tile) walks. */
+    int64_t hard_records_walked;
+    int64_t hard_rows_walked;
+    int64_t hard_rule_ends_walked;
+    int64_t hard_set_tiles;
 } rs_profile;
 
 /* Read the counters of `ctx` (waits for the timed launches to finish); reset them if `reset`. */
@@ -410,6 +420,13 @@ rs_status rs_profile_read(rs_ctx *ctx, rs_profile *out, int32_t reset);
  */
 rs_status rs_selftest_threshold_rewrite(rs_ctx *ctx, const float *a, const float *t,
                                         const int8_t *op, int32_t n, uint64_t *mismatches);
+
+/*
+ * Self-check of the soft path's log(1 + e) for 0 <= e <= 1 (the term of every log-sigmoid and
+ * log-sum-exp of Sec. 3's sigmoid relaxation): out[i] = the kernels' log1p(e[i]) for host arrays
+ * e, out of n entries, evaluated on the context's device.
+ */
+rs_status rs_selftest_log1p_unit(rs_ctx *ctx, const float *e, int32_t n, float *out);
 
 /*
  * Fault injection on the host: of the per-call device allocations of the evaluation paths

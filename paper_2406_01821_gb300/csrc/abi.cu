@@ -47,6 +47,7 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
                            int32_t *per_class, int32_t *preds, cudaStream_t stream);
 rs_status static_scratch_lookup(unsigned char **out);
 rs_status tile_pick(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *id);
+rs_status selftest_log1p_unit(const float *e_h, int n, float *out_h, cudaStream_t stream);
 }  // namespace rs
 
 using namespace rs;
@@ -130,9 +131,18 @@ rs_status rs_create(const rs_config *cfg, rs_ctx **out)
             set_error("cannot allocate the context status word");
             return RS_ERR_OOM;
         }
+        if (cudaMalloc(&ctx->d_walked, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMemset(ctx->d_walked, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(ctx->d_sticky);
+            delete ctx;
+            set_error("cannot allocate the context's counters");
+            return RS_ERR_OOM;
+        }
         // device address of rs_eval_hard_static's fixed scratch array, with this device current
         if (rs_status rc = static_scratch_lookup(&ctx->static_scratch)) {
             cudaFree(ctx->d_sticky);
+            cudaFree(ctx->d_walked);
             delete ctx;
             return rc;
         }
@@ -172,6 +182,7 @@ rs_status rs_destroy(rs_ctx *ctx)
         for (auto id : ids) dataset_destroy(ctx, id);
         ctx->graphs.clear();
         cudaFree(ctx->d_sticky);
+        cudaFree(ctx->d_walked);
         delete ctx;
         return RS_OK;
     })
@@ -383,6 +394,16 @@ rs_status rs_autotune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, void *str
     RS_GUARD({
         if (!ctx) return RS_ERR_INVALID;
         return autotune(ctx, ds, batch, S(stream), best);
+    })
+}
+
+rs_status rs_selftest_log1p_unit(rs_ctx *ctx, const float *e, int32_t n, float *out)
+{
+    RS_GUARD({
+        if (!ctx || !e || !out || n < 1) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return selftest_log1p_unit(e, n, out, nullptr);
     })
 }
 

@@ -280,6 +280,7 @@ rs_status enqueue_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc_in, const Bat
     a.last_end = po.last_end;
     a.Xt = ds->Xt;
     a.cat = bd.cond_set != nullptr;
+    a.walked = (ctx->flags & RS_CTX_COUNT_WORK) ? ctx->d_walked : nullptr;
     return launch_hard(ctx, ds, tc, a, stream);
 }
 

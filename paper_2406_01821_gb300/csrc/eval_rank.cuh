@@ -135,12 +135,17 @@ __device__ __forceinline__ void group4(const uint32_t (&e)[4], const uint32_t *s
 // chunk's pairs that the lanes build in parallel; padding records are no-ops. The chunk is then one
 // straight run of identical steps, with the first-fire claim applied after each rule's last record
 // (a warp vote gives their positions); the all-claimed exit is tested once per chunk.
+// Work a walk did: records, pair / product / membership rows and rule ends (profiling counters).
+struct WalkCount {
+    uint32_t records = 0, rows = 0, ends = 0;
+};
+
 template <bool UNI, int VS, bool CAT>
 __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t vrow_off, int lane,
                                              const uint4 *recs, int rb, int nrec, const float *us,
                                              uint32_t rev_off, int F, int kmine, const unsigned char *rl,
                                              const unsigned char *xl, uint32_t ones_off, const int32_t *yl,
-                                             uint32_t claimed, int deflt)
+                                             uint32_t claimed, int deflt, WalkCount &wc)
 {
     static_assert(VS <= 16, "pair table and staged records share the warp's 512-byte stage");
     const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
@@ -223,7 +228,10 @@ __device__ __forceinline__ uint32_t walk_set(uint4 *st, uint32_t *vrow, uint32_t
         }
         done = __all_sync(FULL, claimed == HIGH);     // all 128 samples claimed: the set is decided
         c0 += cnt;
+        wc.rows += __popc(pm | sm);
+        wc.ends += __popc(ends);
     }
+    wc.records += c0;
     const uint32_t left = ~claimed & HIGH;
     if (UNI) hit |= (deflt == kmine) ? left : 0u;
     else hit |= left & class_bytes(yl, deflt);

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
     float *ones = reinterpret_cast<float *>(vrows + W * VS * 32);             // [T] of 1.0 (products)
     uint64_t *bar = reinterpret_cast<uint64_t *>(ones + T);
     int *next = reinterpret_cast<int *>(bar + 1);
+    uint32_t *walked = reinterpret_cast<uint32_t *>(bar + 2);        // [W][4] work counters (counting)
     const uint4 *recs = reinterpret_cast<const uint4 *>(a.recs);
 
     const int tile = blockIdx.x, group = blockIdx.y, G = gridDim.y;
@@ -40,6 +41,7 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
         *next = 0;
         fence_mbar_init();
     }
+    if (threadIdx.x < 4 * W) walked[threadIdx.x] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t ubytes = (uint32_t)F * T * 4u;
@@ -93,11 +95,19 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
 
         uint32_t *vr = vrows + warp * VS * 32;
         const uint32_t vr_off = (uint32_t)(reinterpret_cast<unsigned char *>(vr) - rs);
+        WalkCount wc;
         const uint32_t hit =
             uniform ? walk_set<true, VS, CAT>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, kmin, rl, xl,
-                                              ones_off, yl, claimed0, si.deflt)
+                                              ones_off, yl, claimed0, si.deflt, wc)
                     : walk_set<false, VS, CAT>(st, vr, vr_off, lane, recs, rb, nrec, us, rev_off, F, -2, rl, xl,
-                                               ones_off, yl, claimed0, si.deflt);
+                                               ones_off, yl, claimed0, si.deflt, wc);
+        if (a.walked && lane == 0) {           // the warp's own slots: no atomics
+            uint32_t *wk = walked + 4 * warp;
+            wk[0] += wc.records;
+            wk[1] += wc.rows;
+            wk[2] += wc.ends;
+            wk[3] += 1;
+        }
         const int hits = __reduce_add_sync(FULL, __popc(hit));
         if (lane == 0 && hits) atomicAdd(&a.correct[p], hits);
         if (a.per_class) {
@@ -111,6 +121,7 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
             }
         }
     }
+    if (a.walked && lane < 4) atomicAdd(&a.walked[lane], (unsigned long long)walked[4 * warp + lane]);
 }
 
 }  // namespace
@@ -120,7 +131,7 @@ size_t hard5_smem_bytes(int F, int W)
     const int Fb = F < 256 ? F : 256;
     const size_t Frows = (size_t)((F + Fb - 1) / Fb) * Fb;
     const size_t vs = W >= 32 ? vslots<32>() : vslots<16>();
-    return Frows * T * (4 + 2 + 4) + (size_t)W * 32 * 16 + (size_t)W * vs * 32 * 4 + T * 4 + 16;
+    return Frows * T * (4 + 2 + 4) + (size_t)W * 32 * 16 + (size_t)W * vs * 32 * 4 + T * 4 + 16 + (size_t)W * 16;
 }
 
 template <int W, bool CAT>

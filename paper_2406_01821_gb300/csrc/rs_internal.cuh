@@ -214,6 +214,7 @@ struct Ctx {
     std::map<std::string, std::shared_ptr<GraphEntry>> graphs;
     uint32_t *d_sticky = nullptr;            // async-mode sticky device status
     unsigned char *static_scratch = nullptr; // device address of rs_eval_hard_static's fixed array
+    unsigned long long *d_walked = nullptr;  // [4] walked-work counters (RS_CTX_COUNT_WORK contexts)
     Profiler prof;
     struct Server *server = nullptr;
 };
@@ -285,6 +286,8 @@ struct HardArgs {
     const int32_t *last_end; // [P*K] or null (see PackOut)
     const float *Xt;         // [F][n_pad] (read directly by the global-memory configuration)
     bool cat;                // the records may hold membership tests
+    unsigned long long *walked;  // [4] or null: records, rows, rule ends, (set, tile) walks summed
+                                 // over the rank-coded evaluator's walks (work-counting contexts)
 };
 // Zero outputs and run the evaluator with tile configuration `tc`.
 rs_status launch_hard(Ctx *ctx, Dataset *ds, const TileConfig &tc, const HardArgs &a,

@@ -182,17 +182,28 @@ rs_status profile_read(Ctx *ctx, rs_profile *out, int reset)
         ctx->prof.pool.push_back(p.e1);
     }
     ctx->prof.pending.clear();
+    unsigned long long w[4] = {0, 0, 0, 0};
+    const bool walked = ctx->d_walked && (ctx->flags & RS_CTX_COUNT_WORK);
+    if (walked) {
+        RS_CUDA(cudaDeviceSynchronize());
+        RS_CUDA(cudaMemcpy(w, ctx->d_walked, sizeof(w), cudaMemcpyDeviceToHost));
+    }
     if (out) {
         out->launches = ctx->prof.launches.load();
         out->hard_launches = ctx->prof.n[TK_HARD];
         out->hard_ms = ctx->prof.ms[TK_HARD];
         out->soft_launches = ctx->prof.n[TK_SOFT];
         out->soft_ms = ctx->prof.ms[TK_SOFT];
+        out->hard_records_walked = (int64_t)w[0];
+        out->hard_rows_walked = (int64_t)w[1];
+        out->hard_rule_ends_walked = (int64_t)w[2];
+        out->hard_set_tiles = (int64_t)w[3];
     }
     if (reset) {
         ctx->prof.launches = 0;
         ctx->prof.n[0] = ctx->prof.n[1] = 0;
         ctx->prof.ms[0] = ctx->prof.ms[1] = 0;
+        if (walked) RS_CUDA(cudaMemset(ctx->d_walked, 0, sizeof(w)));
     }
     return RS_OK;
 }

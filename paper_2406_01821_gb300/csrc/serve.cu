@@ -137,16 +137,17 @@ __device__ __forceinline__ void serve_unit_ranked(const ReqDesc &d, int tile, in
                              ? min(__ldcg(d.last_end + (int64_t)p * d.K + kmin), t.y - t.x)
                              : t.y - t.x;
         uint32_t hit;
+        rank::WalkCount wc;                 // not reported by the serving kernel
         if (d.cat)
             hit = uniform ? walk_set<true, SVS, true>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, kmin,
-                                                      rl, xl, ones_off, yl, claimed0, deflt)
+                                                      rl, xl, ones_off, yl, claimed0, deflt, wc)
                           : walk_set<false, SVS, true>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, -2,
-                                                       rl, xl, ones_off, yl, claimed0, deflt);
+                                                       rl, xl, ones_off, yl, claimed0, deflt, wc);
         else
             hit = uniform ? walk_set<true, SVS, false>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, kmin,
-                                                       rl, xl, ones_off, yl, claimed0, deflt)
+                                                       rl, xl, ones_off, yl, claimed0, deflt, wc)
                           : walk_set<false, SVS, false>(st, vr, vr_off, lane, d.recs, rb, nrec, us, rev_off, F, -2,
-                                                        rl, xl, ones_off, yl, claimed0, deflt);
+                                                        rl, xl, ones_off, yl, claimed0, deflt, wc);
         const int hits = __reduce_add_sync(FULL, __popc(hit));
         if (lane == 0 && hits) atomicAdd(&d.correct[p], hits);
         if (d.per_class) {

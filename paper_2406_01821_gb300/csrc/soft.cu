@@ -158,6 +158,11 @@ __device__ __forceinline__ float log1p_unit(float e)
     return e < 0x1p-24f ? e : fmaf(w2 * v, p, w2);       // below 2^-24, log1p(e) rounds to e
 }
 
+__global__ void k_selftest_log1p_unit(const float *e, int n, float *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = log1p_unit(e[i]);
+}
+
 __device__ __forceinline__ float log_sigmoid(float u)
 {
     // log(1/(1+e^-u)) = -(max(-u,0) + log1p(e^-|u|))
@@ -1339,6 +1344,24 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
         cudaFreeAsync(ffmark, stream);
         cudaFreeAsync(ffbits, stream);
     }
+    return rc;
+}
+
+// The soft kernels' log1p on [0, 1] evaluated on the device for host inputs (a test hook).
+rs_status selftest_log1p_unit(const float *e_h, int n, float *out_h, cudaStream_t stream)
+{
+    float *d = nullptr;
+    RS_CUDA(dev_alloc_async(&d, sizeof(float) * 2 * (size_t)n, stream));
+    rs_status rc = RS_OK;
+    cudaError_t e = cudaMemcpyAsync(d, e_h, sizeof(float) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) {
+        k_selftest_log1p_unit<<<std::min((n + 255) / 256, 4096), 256, 0, stream>>>(d, n, d + n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_h, d + n, sizeof(float) * n, cudaMemcpyDeviceToHost, stream);
+    cudaFreeAsync(d, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "log1p self-test");
     return rc;
 }
 

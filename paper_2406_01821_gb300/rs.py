@@ -19,7 +19,7 @@ ERR = {-1: "RS_ERR_INVALID", -2: "RS_ERR_TOO_LARGE", -3: "RS_ERR_OOM", -4: "RS_E
        -5: "RS_ERR_DEVICE", -6: "RS_ERR_UNSUPPORTED", -7: "RS_ERR_NOT_FOUND", -8: "RS_ERR_CANCELLED"}
 MEM_HOST, MEM_DEVICE = 0, 1
 OP_GT, OP_LT, OP_IN = 0, 1, 2          # cond_op values (OP_IN: category membership)
-CTX_ASYNC, CTX_NO_GRAPH, CTX_NO_AUTOTUNE, CTX_PROFILE = 1, 2, 4, 8
+CTX_ASYNC, CTX_NO_GRAPH, CTX_NO_AUTOTUNE, CTX_PROFILE, CTX_COUNT_WORK = 1, 2, 4, 8, 16
 
 
 class RsError(RuntimeError):
@@ -47,7 +47,9 @@ class rs_batch(ctypes.Structure):
 class rs_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("hard_launches", ctypes.c_int64),
                 ("hard_ms", ctypes.c_double), ("soft_launches", ctypes.c_int64),
-                ("soft_ms", ctypes.c_double)]
+                ("soft_ms", ctypes.c_double), ("hard_records_walked", ctypes.c_int64),
+                ("hard_rows_walked", ctypes.c_int64), ("hard_rule_ends_walked", ctypes.c_int64),
+                ("hard_set_tiles", ctypes.c_int64)]
 
 
 class rs_population(ctypes.Structure):
@@ -132,6 +134,7 @@ _SIGS = {
     "rs_selftest_threshold_rewrite": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                        ctypes.c_void_p, ctypes.c_void_p,
                                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
+    "rs_selftest_log1p_unit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "rs_inject_alloc_failures": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "rs_selftest_bounded_wait": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
 }

@@ -448,3 +448,31 @@ def test_graph_replay_reads_current_contents(ctx, orc):
             assert np.array_equal(c, want[0]) and np.array_equal(pc, want[1])
     finally:
         ctx.dataset_destroy(ds)
+
+
+def test_work_counters_of_the_rank_coded_walk(orc):
+    """A work-counting context reports what the rank-coded evaluator walked: with conditions that
+    never hold (no early exit) every record of every rule is walked on every 128-sample tile."""
+    import torch
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    X, y = synth.two_class_gaussian(1000, 6, 3)
+    big = np.float32(X.max() + 1.0)
+    never = (0, -1, synth.GT, np.float32(1.0), 0.0, big)            # x0 > max(x): never true
+    pair = (1, 2, synth.GT, np.float32(0.0), np.float32(1.0), 0.0)  # 0 * x1 > x2: a pair row
+    rules = [(0, [never, pair]), (1, [never, never]), (0, [pair, never])]
+    b = synth.from_lists([rules], [1])
+    tiles = (len(X) + 127) // 128
+    with rs.Context(0, flags=rs.CTX_COUNT_WORK | rs.CTX_NO_GRAPH) as ctx:
+        ds = ctx.dataset(X, y, 2)
+        ctx.set_tile_config(22)
+        ctx.profile(reset=True)
+        c, _, _ = ctx.eval_hard(ds, rs.DeviceBatch.from_host(b), 2)
+        torch.cuda.synchronize()
+        p = ctx.profile(reset=True)
+        ctx.dataset_destroy(ds)
+    assert c.cpu().numpy().tolist() == orc.eval_hard(X, y, 2, b)[0].tolist()
+    assert p["hard_set_tiles"] == tiles
+    assert p["hard_records_walked"] == 6 * tiles
+    assert p["hard_rule_ends_walked"] == 3 * tiles
+    assert p["hard_rows_walked"] == 2 * tiles
