@@ -366,7 +366,8 @@ struct Request {
     int32_t kind = 0;                     // RS_KIND_HARD or RS_KIND_SOFT
     float tau = 0.f;                      // soft requests: temperature
     int32_t maxR = 0, maxC = 0;           // soft requests: largest set (rules, conditions)
-    void *h_stage = nullptr;              // pinned copy of the batch arrays
+    void *h_stage = nullptr;              // pinned copy of a host batch's arrays
+    void *d_stage = nullptr;              // device copy of a device batch's arrays (same layout)
     size_t stage_bytes = 0, stage_cap = 0, result_cap = 0;   // pinned buffer capacities
     size_t off[11] = {};
     bool cat = false;                     // the batch carries category sets
@@ -426,15 +427,63 @@ struct Server {
     // can stall other CUDA calls): capacity -> buffer
     std::mutex pool_mu;
     std::multimap<size_t, void *> pinned_free;
+    cudaStream_t ustream = nullptr;            // copies of device batches at submission
+    std::mutex up_mu;
+    std::vector<cudaEvent_t> event_pool;       // completion events of finished requests, for reuse
+    char *arena = nullptr;                     // pinned staging arena (PINNED_ARENA_BYTES)
+    std::map<size_t, size_t> arena_free;       // free blocks of the arena: offset -> bytes
 };
 
 static rs_status server_start(Ctx *ctx, Server **out);
 // Pinned staging pool -------------------------------------------------------------------------
 
+// Staging comes first from one pinned arena allocated when the server starts, carved first-fit in
+// 4 KiB units with a coalescing free list, so that rs_submit does not pin memory (pinning takes
+// milliseconds and holds up other CUDA calls); a request that does not fit falls back to pinned
+// buffers of its own, pooled by size.
+constexpr size_t PINNED_ARENA_BYTES = 256ull << 20, PINNED_UNIT = 4096;
+
+static void *arena_get(Server *s, size_t bytes, size_t *cap)
+{
+    const size_t need = (bytes + PINNED_UNIT - 1) / PINNED_UNIT * PINNED_UNIT;
+    for (auto it = s->arena_free.begin(); it != s->arena_free.end(); ++it) {
+        if (it->second < need) continue;
+        const size_t off = it->first, left = it->second - need;
+        s->arena_free.erase(it);
+        if (left) s->arena_free.emplace(off + need, left);
+        *cap = need;
+        return s->arena + off;
+    }
+    return nullptr;
+}
+
+static bool arena_put(Server *s, void *p, size_t cap)
+{
+    if (!s->arena || (char *)p < s->arena || (char *)p >= s->arena + PINNED_ARENA_BYTES) return false;
+    size_t off = (size_t)((char *)p - s->arena), len = cap;
+    auto next = s->arena_free.lower_bound(off);
+    if (next != s->arena_free.end() && next->first == off + len) {     // merge with the block after
+        len += next->second;
+        next = s->arena_free.erase(next);
+    }
+    if (next != s->arena_free.begin()) {                                 // and with the one before
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            off = prev->first;
+            len += prev->second;
+            s->arena_free.erase(prev);
+        }
+    }
+    s->arena_free.emplace(off, len);
+    return true;
+}
+
 static void *pinned_get(Server *s, size_t bytes, size_t *cap)
 {
     {
         std::lock_guard<std::mutex> lk(s->pool_mu);
+        if (s->arena)
+            if (void *p = arena_get(s, bytes, cap)) return p;
         auto it = s->pinned_free.lower_bound(bytes);
         if (it != s->pinned_free.end() && it->first <= 4 * bytes + 65536) {
             void *p = it->second;
@@ -455,6 +504,7 @@ static void pinned_put(Server *s, void *p, size_t cap)
 {
     if (!p) return;
     std::lock_guard<std::mutex> lk(s->pool_mu);
+    if (arena_put(s, p, cap)) return;
     s->pinned_free.emplace(cap, p);
 }
 
@@ -496,6 +546,7 @@ static rs_status server_start(Ctx *ctx, Server **out)
     }
     if ((e = cudaMalloc(&s->d_table, sizeof(ReqDesc) * MAX_SLOTS))) return fail(e, "table");
     if ((e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking))) return fail(e, "stream");
+    if ((e = cudaStreamCreateWithFlags(&s->ustream, cudaStreamNonBlocking))) return fail(e, "stream");
     if ((e = cudaMalloc(&s->d_claims, sizeof(unsigned long long) * MAX_SLOTS))) return fail(e, "claims");
     if ((e = cudaMemset(s->d_claims, 0, sizeof(unsigned long long) * MAX_SLOTS))) return fail(e, "claims");
     if ((e = cudaMalloc(&s->d_active, sizeof(int32_t) * (MAX_SLOTS + 1)))) return fail(e, "active");
@@ -505,6 +556,13 @@ static rs_status server_start(Ctx *ctx, Server **out)
     if ((e = cudaMalloc(&s->d_done, sizeof(int32_t) * MAX_SLOTS))) return fail(e, "done");
     if ((e = cudaHostAlloc(&s->h_flag, sizeof(unsigned long long) * MAX_SLOTS, cudaHostAllocMapped))) return fail(e, "flags");
     if ((e = cudaHostAlloc(&s->h_stop, sizeof(int32_t), cudaHostAllocMapped))) return fail(e, "stop");
+    // the staging arena (without it, staging falls back to buffers of their own)
+    if (cudaHostAlloc(&s->arena, PINNED_ARENA_BYTES, cudaHostAllocDefault) == cudaSuccess)
+        s->arena_free.emplace(0, PINNED_ARENA_BYTES);
+    else {
+        cudaGetLastError();
+        s->arena = nullptr;
+    }
     memset(s->h_flag, 0, sizeof(unsigned long long) * MAX_SLOTS);
     *s->h_stop = 0;
     for (int i = MAX_SLOTS - 1; i >= 0; --i) s->free_slots.push_back(i);
@@ -537,8 +595,11 @@ void server_shutdown(Ctx *ctx)
     cudaStreamSynchronize(s->kstream);
     cudaStreamSynchronize(s->sstream);
     cudaStreamSynchronize(s->cstream);
+    cudaStreamSynchronize(s->ustream);
     for (auto &kv : s->all) {
         Request &r = *kv.second;
+        if (r.d_stage) cudaFree(r.d_stage);
+        r.d_stage = nullptr;
         if (r.h_stage) cudaFreeHost(r.h_stage);
         if (r.h_correct) cudaFreeHost(r.h_correct);
         r.h_stage = nullptr;
@@ -552,6 +613,8 @@ void server_shutdown(Ctx *ctx)
     cudaFree(s->d_rr);
     cudaFree(s->d_done);
     for (auto &kv : s->pinned_free) cudaFreeHost(kv.second);
+    for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+    if (s->arena) cudaFreeHost(s->arena);
     cudaFreeHost(s->h_flag);
     cudaFreeHost(s->h_stop);
     cudaEventDestroy(s->kevent);
@@ -559,6 +622,7 @@ void server_shutdown(Ctx *ctx)
     cudaStreamDestroy(s->sstream);
     cudaStreamDestroy(s->kstream);
     cudaStreamDestroy(s->cstream);
+    cudaStreamDestroy(s->ustream);
     delete s;
     ctx->server = nullptr;
 }
@@ -624,32 +688,50 @@ rs_status submit_impl(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, 
     size_t tot = 0;
     for (int i = 0; i < 11; ++i) { r->off[i] = tot; tot = align256(tot + sz[i]); }
     r->stage_bytes = tot;
-    r->h_stage = pinned_get(s, std::max<size_t>(tot, 256), &r->stage_cap);
-    if (!r->h_stage) { set_error("pinned host memory exhausted"); return RS_ERR_OOM; }
-    for (int i = 0; i < 11; ++i) {
-        if (!sz[i]) continue;
-        if (!src[i]) {
-            pinned_put(s, r->h_stage, r->stage_cap);
-            r->h_stage = nullptr;
-            set_error("NULL batch array");
-            return RS_ERR_INVALID;
-        }
-        if (b->mem == RS_MEM_HOST) {
-            memcpy((char *)r->h_stage + r->off[i], src[i], sz[i]);
-        } else {
-            const cudaError_t e = cudaMemcpy((char *)r->h_stage + r->off[i], src[i], sz[i], cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) {
-                pinned_put(s, r->h_stage, r->stage_cap);
-                r->h_stage = nullptr;
-                return cuda_fail(e, "rs_submit copy");
-            }
+    for (int i = 0; i < 11; ++i)
+        if (sz[i] && !src[i]) { set_error("NULL batch array"); return RS_ERR_INVALID; }
+    if (b->mem == RS_MEM_HOST) {
+        // a host batch: copied into pinned staging, uploaded at admission
+        r->h_stage = pinned_get(s, std::max<size_t>(tot, 256), &r->stage_cap);
+        if (!r->h_stage) { set_error("pinned host memory exhausted"); return RS_ERR_OOM; }
+        for (int i = 0; i < 11; ++i)
+            if (sz[i]) memcpy((char *)r->h_stage + r->off[i], src[i], sz[i]);
+    } else {
+        // a device batch: copied device to device into staging of its own (no host round trip),
+        // finished before rs_submit returns so that the caller may free its arrays
+        std::lock_guard<std::mutex> ul(s->up_mu);
+        cudaError_t e = dev_alloc_async(&r->d_stage, std::max<size_t>(tot, 256), s->ustream);
+        for (int i = 0; i < 11 && e == cudaSuccess; ++i)
+            if (sz[i]) e = cudaMemcpyAsync((char *)r->d_stage + r->off[i], src[i], sz[i], cudaMemcpyDeviceToDevice,
+                                           s->ustream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->ustream);
+        if (e != cudaSuccess) {
+            if (r->d_stage) { cudaFreeAsync(r->d_stage, s->ustream); cudaStreamSynchronize(s->ustream); }
+            r->d_stage = nullptr;
+            return cuda_fail(e, "rs_submit copy");
         }
     }
     if (kind == RS_KIND_SOFT) {
         // the largest set bounds the soft kernels' shared memory; malformed offsets are left to
         // the device checks, which see the same arrays
-        const int32_t *sro = (const int32_t *)((char *)r->h_stage + r->off[0]);
-        const int32_t *rco = (const int32_t *)((char *)r->h_stage + r->off[1]);
+        std::vector<int32_t> offs;
+        const int32_t *sro, *rco;
+        if (r->h_stage) {
+            sro = (const int32_t *)((char *)r->h_stage + r->off[0]);
+            rco = (const int32_t *)((char *)r->h_stage + r->off[1]);
+        } else {
+            offs.resize(P + 1 + R + 1);
+            const cudaError_t e1 = cudaMemcpy(offs.data(), b->set_rule_off, 4 * (P + 1), cudaMemcpyDeviceToHost);
+            const cudaError_t e2 = cudaMemcpy(offs.data() + P + 1, b->rule_cond_off, 4 * (R + 1),
+                                              cudaMemcpyDeviceToHost);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                cudaFree(r->d_stage);
+                r->d_stage = nullptr;
+                return cuda_fail(e1 != cudaSuccess ? e1 : e2, "rs_submit_soft offsets");
+            }
+            sro = offs.data();
+            rco = offs.data() + P + 1;
+        }
         int32_t mr = 1, mc = 1;
         for (size_t p = 0; p < P; ++p) {
             const int32_t rb = sro[p], re = sro[p + 1];
@@ -663,20 +745,42 @@ rs_status submit_impl(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, 
     }
     r->h_correct = (int32_t *)pinned_get(
         s, align256(4 * std::max<size_t>(P, 1)) + 4 * std::max<size_t>(P * r->K, 1) + 256, &r->result_cap);
-    if (!r->h_correct) {
+    auto release_stage = [&] {
         pinned_put(s, r->h_stage, r->stage_cap);
         r->h_stage = nullptr;
+        if (r->d_stage) cudaFree(r->d_stage);
+        r->d_stage = nullptr;
+    };
+    if (!r->h_correct) {
+        release_stage();
         set_error("pinned host memory exhausted");
         return RS_ERR_OOM;
     }
     r->h_pc = (int32_t *)((char *)r->h_correct + align256(4 * std::max<size_t>(P, 1)));
     r->h_status = (uint32_t *)((char *)r->h_pc + 4 * std::max<size_t>(P * r->K, 1));
     *r->h_status = 0;
-    RS_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+    {   // a pooled event: rs_submit makes no CUDA call for host batches once the pool is warm
+        std::lock_guard<std::mutex> lk(s->pool_mu);
+        if (!s->event_pool.empty()) {
+            r->ev = s->event_pool.back();
+            s->event_pool.pop_back();
+        }
+    }
+    if (cudaError_t e = r->ev ? cudaSuccess : cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming)) {
+        release_stage();
+        pinned_put(s, r->h_correct, r->result_cap);
+        r->h_correct = nullptr;
+        return cuda_fail(e, "cudaEventCreate");
+    }
     r->t_submit = std::chrono::steady_clock::now();
     {
         std::lock_guard<std::mutex> il(s->in_mu);
         if (s->fatal_flag.load()) {
+            release_stage();
+            pinned_put(s, r->h_correct, r->result_cap);
+            r->h_correct = nullptr;
+            cudaEventDestroy(r->ev);
+            r->ev = nullptr;
             set_error("serving stopped after a device error");
             return (rs_status)s->fatal_flag.load();
         }
@@ -701,6 +805,24 @@ static void push_active(Server *s)
                     s->sstream);
 }
 
+// The batch arrays into the request's device memory: from pinned staging (host batches, one copy
+// per array) or in one device-to-device copy from the device staging (device batches), which is
+// then released.
+static void upload_batch(Server *s, Request &r, char *base)
+{
+    if (r.d_stage) {
+        cudaMemcpyAsync(base, r.d_stage, r.stage_bytes, cudaMemcpyDeviceToDevice, s->sstream);
+        cudaFreeAsync(r.d_stage, s->sstream);
+        r.d_stage = nullptr;
+        return;
+    }
+    for (int i = 0; i < 11; ++i)
+        if ((i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) > r.off[i])
+            cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
+                            (i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
+                            s->sstream);
+}
+
 // A soft-loss request runs as its own kernels on the staging stream (next to the persistent
 // kernel): upload, the soft forward, and the copy of the per-set losses and the status word.
 static bool admit_soft(Server *s, Request &r)
@@ -714,11 +836,7 @@ static bool admit_soft(Server *s, Request &r)
     r.d_buf = base;
     s->used += r.device_bytes;
     r.t_admit = std::chrono::steady_clock::now();
-    for (int i = 0; i < 11; ++i)
-        if ((i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) > r.off[i])
-            cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
-                            (i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
-                            s->sstream);
+    upload_batch(s, r, base);
     char *p = base + r.stage_bytes;
     SoftArgs a{};
     a.b.P = r.P; a.b.R = r.R; a.b.C = r.C;
@@ -759,11 +877,7 @@ static bool try_admit(Server *s, Request &r)
     s->used += r.device_bytes;
     r.t_admit = std::chrono::steady_clock::now();
     // batch arrays
-    for (int i = 0; i < 11; ++i)
-        if ((i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) > r.off[i])
-            cudaMemcpyAsync(base + r.off[i], (char *)r.h_stage + r.off[i],
-                            (i + 1 < 11 ? r.off[i + 1] : r.stage_bytes) - r.off[i], cudaMemcpyHostToDevice,
-                            s->sstream);
+    upload_batch(s, r, base);
     char *p = base + r.stage_bytes;
     BatchDev bd{};
     bd.P = r.P; bd.R = r.R; bd.C = r.C;
@@ -961,9 +1075,16 @@ rs_status poll_impl(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t kind,
         return RS_ERR_NOT_FOUND;
     }
     // results are released at the first successful poll
+    if (r->d_stage) {                // cancelled before admission
+        cudaFree(r->d_stage);
+        r->d_stage = nullptr;
+    }
     pinned_put(s, r->h_stage, r->stage_cap);
     pinned_put(s, r->h_correct, r->result_cap);
-    if (r->ev) cudaEventDestroy(r->ev);
+    if (r->ev) {
+        std::lock_guard<std::mutex> pl(s->pool_mu);
+        s->event_pool.push_back(r->ev);
+    }
     r->h_stage = nullptr; r->h_correct = nullptr; r->ev = nullptr;
     r->state = 5;
     lk.unlock();

@@ -161,3 +161,31 @@ def test_soft_requests_in_the_mix(orc):
             ctx.submit_soft(dss[0], rs.HostBatch(jobs[0][1]), 0.0)
     finally:
         ctx.close()
+
+
+def test_device_batch_copied_at_submission(orc):
+    """A device batch is copied device to device before rs_submit returns: overwriting the
+    caller's arrays right after the call changes nothing, for hard and soft requests."""
+    import torch
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    X, y = synth.gaussian_mixture(7001, 20, 3, 41)
+    b = synth.random_rulesets(synth.quantile_table(X), 3, 120, (1, 20), (1, 6), 41)
+    want = orc.eval_hard(X, y, 3, b)
+    want_soft = orc.soft(X, y, 3, b, 0.2)["loss"]
+    with rs.Context(0) as ctx:
+        ds = ctx.dataset(X, y, 3)
+        db = rs.DeviceBatch.from_host(b)
+        th = ctx.submit(ds, db)
+        ts = ctx.submit_soft(ds, db, 0.2)
+        for t in db.t.values():                  # the caller reuses its memory at once
+            if t is not None:
+                t.zero_()
+        torch.cuda.synchronize()
+        c, pc, _ = ctx.poll(th, b.P, 3, timeout_us=30_000_000)
+        loss, _ = ctx.poll_soft(ts, b.P, timeout_us=30_000_000)
+        ctx.dataset_destroy(ds)
+    assert np.array_equal(c, want[0]) and np.array_equal(pc, want[1].reshape(b.P, 3))
+    fin = np.isfinite(want_soft)
+    assert np.allclose(loss[fin], want_soft[fin], rtol=1e-5, atol=0)
+    assert (np.isinf(loss) == ~fin).all()
