@@ -163,16 +163,24 @@ __global__ void k_selftest_log1p_unit(const float *e, int n, float *out)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = log1p_unit(e[i]);
 }
 
+// The float path's exponentials of non-positive arguments use the hardware approximation
+// (__expf: ex2.approx of x log2(e)); for the arguments that occur here (|x| up to about 100,
+// beyond which the float-float pass takes over for the terms that matter) its relative error
+// stays below a few 1e-6, within the soft tolerance. Logarithms stay accurate (the hardware lg2
+// has an absolute error near 1 that is too large relative to log1p of small arguments); the
+// float-float pass keeps expf.
+__device__ __forceinline__ float exp_np(float x) { return __expf(x); }
+
 __device__ __forceinline__ float log_sigmoid(float u)
 {
     // log(1/(1+e^-u)) = -(max(-u,0) + log1p(e^-|u|))
-    const float e = expf(-fabsf(u));
+    const float e = exp_np(-fabsf(u));
     return -(fmaxf(-u, 0.f) + log1p_unit(e));
 }
 
 __device__ __forceinline__ float sigmoid_neg(float u)     // 1/(1+e^u)
 {
-    const float e = expf(-fabsf(u));
+    const float e = exp_np(-fabsf(u));
     return __fdividef(u >= 0.f ? e : 1.f, 1.f + e);
 }
 
@@ -181,7 +189,7 @@ __device__ __forceinline__ float log_add(float a, float b)
     if (a == -INFINITY) return b;
     if (b == -INFINITY) return a;
     const float m = fmaxf(a, b);
-    return m + log1p_unit(expf(-fabsf(a - b)));
+    return m + log1p_unit(exp_np(-fabsf(a - b)));
 }
 
 // Kahan-compensated accumulation.
@@ -306,7 +314,7 @@ __device__ __forceinline__ void rule_logq_cached(const SoftKArgs &a, int c0, int
             const float rhs = (rc.meta & 1u) ? rc.bt * x(rc.g, v) : rc.bt;
             float u = (lhs - rhs) * a.inv_tau;
             if (rc.meta & 2u) u = -u;
-            const float e = expf(-fabsf(u));
+            const float e = exp_np(-fabsf(u));
             cu[k][v] = u;
             ce[k][v] = e;
             s[v] += -(fmaxf(-u, 0.f) + log1p_unit(e));
@@ -683,7 +691,7 @@ __device__ __forceinline__ bool soft_group(const SoftKArgs &a, int p, int rb, in
         for (int v = 0; v < V; ++v) {
             const float lqj = lqr[v], luj = lu[j][lane + 32 * v];
             const bool same = cls == yn[v];
-            gq[v] = same ? -expf(lqj + luj + lT[v] - lpy[v]) : expf(lqj + luj + lS[v] - lpy[v]);
+            gq[v] = same ? -exp_np(lqj + luj + lT[v] - lpy[v]) : exp_np(lqj + luj + lS[v] - lpy[v]);
             if (!((valid >> v) & 1u)) gq[v] = 0.f;
             const float l1q = logf(-expm1f(lqj));
             lS[v] = log_add(same ? lqj : -INFINITY, l1q + lS[v]);

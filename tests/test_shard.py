@@ -66,7 +66,7 @@ def _rank(rank, world, port, out):
 def test_gloo_ranks_reduce_to_whole_dataset(orc, world):
     import torch.multiprocessing as mp
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:     # no fork: the parent may hold a CUDA context
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
