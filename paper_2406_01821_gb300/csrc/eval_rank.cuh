@@ -58,15 +58,6 @@ __device__ __forceinline__ uint2 stage_cut(uint4 r, const float *us, uint32_t re
     return make_uint2((le ? rev_off : 0u) + f * T, (uint32_t)(le ? 255 - L : L + 127) * ONES);
 }
 
-// 0xFF in byte v where p[v] > q[v] (IEEE compare: false with NaN), 0 elsewhere.
-__device__ __forceinline__ uint32_t gt_bytes(const float (&p)[4], const float (&q)[4])
-{
-    uint32_t s[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(s[v]) : "f"(p[v]), "f"(q[v]));
-    return __byte_perm(__byte_perm(s[0], s[1], 0x0040), __byte_perm(s[2], s[3], 0x0040), 0x5410);
-}
-
 // Bit 7 of byte v where the lane's sample v (labels yl[0..3]) has label k. Only tiles that hold
 // more than one label need it, so the labels are read again instead of kept in registers.
 __device__ __forceinline__ uint32_t class_bytes(const int32_t *yl, int k)
@@ -78,18 +69,29 @@ __device__ __forceinline__ uint32_t class_bytes(const int32_t *yl, int k)
 
 // Pass row of a pair condition fl(a * x[f]) > fl(b * x[g]) or a product condition
 // fl(a * x[f]) > b, staged as {byte offset of row f, byte offset of row g (a row of 1.0 for a
-// product: fl(b * 1) = b), a, b}: 0xFF in byte v where the condition holds for the lane's sample v.
-// The products are separately rounded (packed two-lane multiplies).
+// product: fl(b * 1) = b), a, b}: bit 7 of byte v is set exactly where the condition holds for the
+// lane's sample v (bits 0..6 carry no meaning; the walk's constant 0xFFFFFFFF minus the word puts
+// the failure in bit 7 without a borrow). The products p, q are separately rounded (packed
+// two-lane multiplies); p > q is read as the sign of d = fl(fl(q - p) + 0): for p, q finite or
+// infinite, fl(q - p) is negative exactly when p > q (gradual underflow keeps the sign of a tiny
+// difference; equal values give +0) except q = -0, p = +0, whose -0 the added +0 turns into +0;
+// a NaN operand or inf - inf gives the canonical NaN, whose sign bit is clear (false, as the
+// IEEE compare). Used on finite datasets only (rank tables), where the products are finite or
+// +-inf.
 __device__ __forceinline__ uint32_t pass_row(uint4 q, const unsigned char *xl)
 {
     const float4 x = *reinterpret_cast<const float4 *>(xl + q.x);
     const float4 z = *reinterpret_cast<const float4 *>(xl + q.y);
     const float2 a2 = make_float2(__uint_as_float(q.z), __uint_as_float(q.z));
     const float2 b2 = make_float2(__uint_as_float(q.w), __uint_as_float(q.w));
+    const float2 m1 = make_float2(-1.f, -1.f), z2 = make_float2(0.f, 0.f);
     const float2 p01 = __fmul2_rn(make_float2(x.x, x.y), a2), p23 = __fmul2_rn(make_float2(x.z, x.w), a2);
     const float2 q01 = __fmul2_rn(make_float2(z.x, z.y), b2), q23 = __fmul2_rn(make_float2(z.z, z.w), b2);
-    const float p[4] = {p01.x, p01.y, p23.x, p23.y}, r[4] = {q01.x, q01.y, q23.x, q23.y};
-    return gt_bytes(p, r);
+    const float2 d01 = __fadd2_rn(__ffma2_rn(p01, m1, q01), z2);      // fl(q - p) + 0, exactly rounded
+    const float2 d23 = __fadd2_rn(__ffma2_rn(p23, m1, q23), z2);
+    const uint32_t s01 = __byte_perm(__float_as_uint(d01.x), __float_as_uint(d01.y), 0x0073);
+    const uint32_t s23 = __byte_perm(__float_as_uint(d23.x), __float_as_uint(d23.y), 0x0073);
+    return __byte_perm(s01, s23, 0x5410);
 }
 
 // Pass row of a membership condition, staged as {byte offset of row f, -, set bits 0..31, set
