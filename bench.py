@@ -310,13 +310,12 @@ def soft_leg(args, dev):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
     prof = ctx.profile(reset=True)
+    rates = ctx.pipe_rates()
     ctx.close()
     cs = w.batch.nominal_conditions() * w.N
     kern_ms = prof["soft_ms"] / max(1, prof["soft_launches"])
     xu = soft_transcendentals(w.batch, w.N)
-    peaks, peak_src = measured_peaks()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    xu_peak = sms * 16 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    xu_peak = rates["ex2"]
     return {"workload": w.name, "ms_per_step": ms, "condition_samples_per_s": cs / (ms / 1e3),
             "rule_set_samples_per_s": w.batch.P * w.N / (ms / 1e3),
             "kernel_ms": kern_ms, "steps": steps,
@@ -324,8 +323,7 @@ def soft_leg(args, dev):
             "roofline": {"bound": "xu", "achieved": xu / (kern_ms / 1e3) / 1e12, "peak": xu_peak / 1e12,
                          "unit": "T transcendentals/s", "frac": xu / (kern_ms / 1e3) / xu_peak,
                          "transcendentals_per_pass": xu,
-                         "peak_source": f"{sms} SMs x 16 XU lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                        f"({peak_src} max clock)"}}
+                         "peak_source": "measured: special-function unit ex2 stream (rs_measure_pipe_rates)"}}
 
 
 def categorical_leg(args, dev):
@@ -736,6 +734,8 @@ def main():
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_ops = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    with rs.Context(dev) as pctx:
+        rates = pctx.pipe_rates()
     counters = profiled_counters()
     traffic = counters.get("dram_bytes_per_launch_full") if counters else None
     pipes = ({"issue_active": counters["issue_active_pct"] / 100, "l1tex_throughput": counters["l1tex_throughput_pct"] / 100,
@@ -777,7 +777,8 @@ def main():
                          "executed": None if executed is None else {
                              **executed, "frac": executed["ops_per_launch"] / (kern_ms / 1e3) / peak_ops},
                          "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                        f"({peak_src} max clock)"},
+                                        f"({peak_src} max clock)",
+                         "measured_pipes_T_lane_ops": {k: v / 1e12 for k, v in rates.items()}},
             "cpu_baseline": cb,
             "e2e": {"value": total_nominal / (e2e_max / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"],

@@ -411,6 +411,18 @@ typedef struct {
 /* Read the counters of `ctx` (waits for the timed launches to finish); reset them if `reset`. */
 rs_status rs_profile_read(rs_ctx *ctx, rs_profile *out, int32_t reset);
 
+/*
+ * Measured issue rates of the context's GPU, in lane operations per second, for the kernels'
+ * rooflines (no paper counterpart; a measurement helper): a stream of independent FP32 fused
+ * multiply-adds, FP32 multiplies, three-input logic operations, population counts, base-2
+ * exponentials of the special-function unit, and float compares writing a register, each over
+ * 2048 threads per SM. Takes a few milliseconds; allocates and frees a small device buffer.
+ */
+typedef struct {
+    double ffma, fmul, lop3, popc, ex2, fset;
+} rs_pipe_rates;
+rs_status rs_measure_pipe_rates(rs_ctx *ctx, rs_pipe_rates *out);
+
 /* ---------------------------------------------------------------------------- test hooks */
 
 /*

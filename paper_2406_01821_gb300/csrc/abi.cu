@@ -48,6 +48,7 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
 rs_status static_scratch_lookup(unsigned char **out);
 rs_status tile_pick(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *id);
 rs_status selftest_log1p_unit(const float *e_h, int n, float *out_h, cudaStream_t stream);
+rs_status measure_pipe_rates(Ctx *ctx, rs_pipe_rates *out);
 }  // namespace rs
 
 using namespace rs;
@@ -394,6 +395,16 @@ rs_status rs_autotune(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, void *str
     RS_GUARD({
         if (!ctx) return RS_ERR_INVALID;
         return autotune(ctx, ds, batch, S(stream), best);
+    })
+}
+
+rs_status rs_measure_pipe_rates(rs_ctx *ctx, rs_pipe_rates *out)
+{
+    RS_GUARD({
+        if (!ctx || !out) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return measure_pipe_rates(ctx, out);
     })
 }
 

@@ -52,6 +52,10 @@ class rs_profile(ctypes.Structure):
                 ("hard_set_tiles", ctypes.c_int64)]
 
 
+class rs_pipe_rates(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("ffma", "fmul", "lop3", "popc", "ex2", "fset")]
+
+
 class rs_population(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("nrule", "deflt", "rcls", "ncond", "cf", "cg", "cop",
                                                "ca", "cb", "ct", "fitness")]
@@ -134,6 +138,7 @@ _SIGS = {
     "rs_selftest_threshold_rewrite": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p,
                                                        ctypes.c_void_p, ctypes.c_void_p,
                                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
+    "rs_measure_pipe_rates": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rs_pipe_rates)]),
     "rs_selftest_log1p_unit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "rs_inject_alloc_failures": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "rs_selftest_bounded_wait": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -372,6 +377,12 @@ class Context:
         cb = batch.c()
         check(lib().rs_autotune(self.h, ds, ctypes.byref(cb), _stream_ptr(stream), ctypes.byref(best)))
         return best.value
+
+    def pipe_rates(self) -> dict:
+        """Measured lane operations per second of the GPU's arithmetic pipes (rs_measure_pipe_rates)."""
+        r = rs_pipe_rates()
+        check(lib().rs_measure_pipe_rates(self.h, ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in rs_pipe_rates._fields_}
 
     def profile(self, reset=False) -> dict:
         p = rs_profile()

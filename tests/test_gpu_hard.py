@@ -476,3 +476,17 @@ def test_work_counters_of_the_rank_coded_walk(orc):
     assert p["hard_records_walked"] == 6 * tiles
     assert p["hard_rule_ends_walked"] == 3 * tiles
     assert p["hard_rows_walked"] == 2 * tiles
+
+
+def test_measured_pipe_rates():
+    """The pipe-rate measurement: every stream runs, the FP32 FMA rate is within the FP32 lanes'
+    nominal peak (128 per SM at the maximum clock) and above half of it."""
+    import torch
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    with rs.Context(0) as ctx:
+        r = ctx.pipe_rates()
+    prop = torch.cuda.get_device_properties(0)
+    nominal = prop.multi_processor_count * 128 * 2.1e9
+    assert 0.5 * nominal < r["ffma"] <= 1.05 * nominal, r
+    assert all(v > 0 for v in r.values()), r
