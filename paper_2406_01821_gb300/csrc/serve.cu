@@ -27,6 +27,7 @@
 #include "eval_core.cuh"
 #include "eval_rank.cuh"
 #include "rs_internal.cuh"
+#include "serve_sched.h"
 
 namespace rs {
 
@@ -359,8 +360,7 @@ int64_t serve_groups(const Dataset &ds, int P, bool cat)
 
 // ------------------------------------------------------------------------------ host side
 
-struct Request {
-    uint64_t ticket = 0;
+struct Request : sched::Core {
     std::shared_ptr<Dataset> ds;
     int32_t P = 0, R = 0, C = 0, K = 0;
     int32_t kind = 0;                     // RS_KIND_HARD or RS_KIND_SOFT
@@ -371,11 +371,7 @@ struct Request {
     size_t stage_bytes = 0, stage_cap = 0, result_cap = 0;   // pinned buffer capacities
     size_t off[11] = {};
     bool cat = false;                     // the batch carries category sets
-    size_t device_bytes = 0;
     void *d_buf = nullptr;
-    int slot = -1;
-    int state = 0;                        // 0 queued, 1 preparing, 2 running, 3 copying, 4 done, 5 released
-    rs_status status = RS_OK;
     cudaEvent_t ev = nullptr;
     int32_t *h_correct = nullptr, *h_pc = nullptr;   // pinned results
     int32_t *d_correct = nullptr, *d_pc = nullptr;
@@ -384,12 +380,26 @@ struct Request {
     std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
 };
 
+struct Server;
+
+// The device side of the scheduler (serve_sched.h) on CUDA.
+struct CudaBackend {
+    Server *s = nullptr;
+    bool admit(Request &r);
+    bool kernel_live();
+    void launch_kernel();
+    bool units_done(Request &r);
+    void start_copy_out(Request &r);
+    int copies_done(Request &r);
+    void release(Request &r);
+};
+
 struct Server {
     Ctx *ctx = nullptr;
     std::mutex mu;                         // scheduler state (held by the scheduler thread while it works)
     std::condition_variable cv_work, cv_done;
-    std::deque<std::shared_ptr<Request>> queued;
-    std::vector<std::shared_ptr<Request>> active;
+    sched::Scheduler<Request, CudaBackend> sch;   // queue, admission, budget, slots (under mu)
+    CudaBackend dev;
     std::thread thread;
     bool quit = false;
     // Submissions go through an inbox under their own lock, so rs_submit never waits for the
@@ -401,8 +411,6 @@ struct Server {
     uint64_t next_ticket = 1;                                       // under in_mu
     std::atomic<bool> quit_flag{false};
     std::atomic<int> fatal_flag{0};
-    size_t used = 0;
-    std::vector<int> free_slots;
     cudaStream_t sstream = nullptr, kstream = nullptr;
     // request memory: a pool of the server's own that keeps what it has mapped (up to the budget),
     // so that admissions do not wait for the CUDA driver to map memory again
@@ -422,7 +430,6 @@ struct Server {
     rs_status fatal = RS_OK;
     int grid = 0;
     size_t smem = 0;
-    int64_t launches = 0;
     // pinned host buffers of finished requests, reused by new ones (pinning memory is slow and
     // can stall other CUDA calls): capacity -> buffer
     std::mutex pool_mu;
@@ -565,7 +572,8 @@ static rs_status server_start(Ctx *ctx, Server **out)
     }
     memset(s->h_flag, 0, sizeof(unsigned long long) * MAX_SLOTS);
     *s->h_stop = 0;
-    for (int i = MAX_SLOTS - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->sch.init(ctx->budget, MAX_SLOTS);
+    s->dev.s = s;
     s->smem = SERVE_SMEM;
     if ((e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem)))
         return fail(e, "k_serve attribute");
@@ -668,6 +676,7 @@ rs_status submit_impl(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, 
     auto r = std::make_shared<Request>();
     r->ds = ds;
     r->P = b->P; r->R = b->R; r->C = b->C; r->K = ds->K; r->kind = kind; r->tau = tau; r->cat = cat;
+    r->needs_slot = kind == RS_KIND_HARD;     // soft requests run as their own kernels
     r->device_bytes = request_device_bytes(b->P, b->R, b->C, ds->K, cat);
     if (r->device_bytes > ctx->budget) {
         set_error("request needs %zu bytes of device memory; the budget is %llu", r->device_bytes,
@@ -827,14 +836,12 @@ static void upload_batch(Server *s, Request &r, char *base)
 // kernel): upload, the soft forward, and the copy of the per-set losses and the status word.
 static bool admit_soft(Server *s, Request &r)
 {
-    if (s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
     if (dev_alloc_pool_async(&base, r.device_bytes, s->pool, s->sstream) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     r.d_buf = base;
-    s->used += r.device_bytes;
     r.t_admit = std::chrono::steady_clock::now();
     upload_batch(s, r, base);
     char *p = base + r.stage_bytes;
@@ -856,25 +863,23 @@ static bool admit_soft(Server *s, Request &r)
     if (r.P > 0) cudaMemcpyAsync(r.h_correct, d_loss, 4 * (size_t)r.P, cudaMemcpyDeviceToHost, s->sstream);
     cudaMemcpyAsync(r.h_status, r.d_status, 4, cudaMemcpyDeviceToHost, s->sstream);
     cudaEventRecord(r.ev, s->sstream);
-    r.state = 3;
+    r.state = sched::COPYING;
     return true;
 }
 
-static bool try_admit(Server *s, Request &r)
+// Admission of a request the scheduler let through (budget and, for hard requests, a slot already
+// checked; r.slot set): device memory, upload, packing, descriptor and claim word.
+bool CudaBackend::admit(Request &r)
 {
     if (r.kind == RS_KIND_SOFT) return admit_soft(s, r);
     const int64_t tiles = (r.ds->N + SS - 1) / SS;
     const int64_t groups = serve_groups(*r.ds, r.P, r.cat);
-    if (s->free_slots.empty() || s->used + r.device_bytes > s->ctx->budget) return false;
     char *base = nullptr;
     if (dev_alloc_pool_async(&base, r.device_bytes, s->pool, s->sstream) != cudaSuccess) {
         cudaGetLastError();
         return false;                      // retry later, when memory is back
     }
     r.d_buf = base;
-    r.slot = s->free_slots.back();
-    s->free_slots.pop_back();
-    s->used += r.device_bytes;
     r.t_admit = std::chrono::steady_clock::now();
     // batch arrays
     upload_batch(s, r, base);
@@ -927,14 +932,67 @@ static bool try_admit(Server *s, Request &r)
         s->h_active.push_back(r.slot);
         push_active(s);
         s->published += units;
-        r.state = 2;
+        r.state = sched::RUNNING;
     } else {                   // nothing to evaluate: results are the zeros just written
         cudaMemcpyAsync(r.h_correct, r.d_correct, 4 * (size_t)r.P, cudaMemcpyDeviceToHost, s->sstream);
         cudaMemcpyAsync(r.h_status, r.d_status, 4, cudaMemcpyDeviceToHost, s->sstream);
-        r.state = 3;
+        r.state = sched::COPYING;
     }
     cudaEventRecord(r.ev, s->sstream);
     return true;
+}
+
+bool CudaBackend::kernel_live()
+{
+    if (!s->kernel_live) return false;
+    if (cudaEventQuery(s->kevent) == cudaSuccess) s->kernel_live = false;    // it left after its idle limit
+    else cudaGetLastError();
+    return s->kernel_live;
+}
+
+void CudaBackend::launch_kernel()
+{
+    // the descriptors and ring entries must be in place before the kernel starts
+    cudaStreamWaitEvent(s->kstream, s->sch.active.back()->ev, 0);
+    ServeArgs a{s->d_table, s->d_claims, s->d_active, s->d_active + MAX_SLOTS, s->d_rr, s->d_done,
+                (volatile unsigned long long *)s->h_flag, (volatile int32_t *)s->h_stop};
+    k_serve<<<s->grid, SW * 32, s->smem, s->kstream>>>(a);
+    cudaEventRecord(s->kevent, s->kstream);
+    count_launch(s->ctx);
+    s->kernel_live = true;
+}
+
+bool CudaBackend::units_done(Request &r)
+{
+    return ((volatile unsigned long long *)s->h_flag)[r.slot] == (r.ticket & 0xFFFFFFull);
+}
+
+void CudaBackend::start_copy_out(Request &r)
+{
+    cudaMemcpyAsync(r.h_correct, r.d_correct, 4 * (size_t)r.P, cudaMemcpyDeviceToHost, s->cstream);
+    cudaMemcpyAsync(r.h_pc, r.d_pc, 4 * (size_t)r.P * r.K, cudaMemcpyDeviceToHost, s->cstream);
+    cudaMemcpyAsync(r.h_status, r.d_status, 4, cudaMemcpyDeviceToHost, s->cstream);
+    cudaEventRecord(r.ev, s->cstream);
+    s->h_active.erase(std::remove(s->h_active.begin(), s->h_active.end(), r.slot), s->h_active.end());
+    push_active(s);
+}
+
+int CudaBackend::copies_done(Request &r)
+{
+    const cudaError_t q = cudaEventQuery(r.ev);
+    if (q == cudaSuccess) return 1;
+    if (q == cudaErrorNotReady) return 0;
+    s->fatal = cuda_fail(q, "serving");
+    s->fatal_flag = (int)s->fatal;
+    return (int)s->fatal;
+}
+
+void CudaBackend::release(Request &r)
+{
+    r.t_done = std::chrono::steady_clock::now();
+    r.status = *r.h_status ? RS_ERR_INVALID : RS_OK;
+    cudaFreeAsync(r.d_buf, s->sstream);   // the copies out have completed
+    r.d_buf = nullptr;
 }
 
 static void server_loop(Server *s)
@@ -944,78 +1002,14 @@ static void server_loop(Server *s)
     while (true) {
         {
             std::lock_guard<std::mutex> il(s->in_mu);
-            for (auto &r : s->inbox) s->queued.push_back(r);
+            for (auto &r : s->inbox) s->sch.queued.push_back(r);
             s->inbox.clear();
         }
-        if (s->quit && s->queued.empty() && s->active.empty()) break;
-        bool progress = false;
-        // admit in arrival order
-        while (!s->queued.empty()) {
-            auto r = s->queued.front();
-            if (r->state >= 4) { s->queued.pop_front(); continue; }   // cancelled
-            if (!try_admit(s, *r)) break;
-            s->queued.pop_front();
-            s->active.push_back(r);
-            progress = true;
-        }
-        // (re)launch the persistent kernel when units wait and it is not running
-        bool pending_units = false;
-        for (auto &r : s->active) pending_units |= r->state == 2;
-        if (pending_units && s->kernel_live) {
-            if (cudaEventQuery(s->kevent) == cudaSuccess) s->kernel_live = false;
-            else cudaGetLastError();
-        }
-        if (pending_units && !s->kernel_live) {
-            // the descriptors and ring entries must be in place before the kernel starts
-            cudaStreamWaitEvent(s->kstream, s->active.back()->ev, 0);
-            ServeArgs a{s->d_table, s->d_claims, s->d_active, s->d_active + MAX_SLOTS, s->d_rr, s->d_done,
-                        (volatile unsigned long long *)s->h_flag, (volatile int32_t *)s->h_stop};
-            k_serve<<<s->grid, SW * 32, s->smem, s->kstream>>>(a);
-            cudaEventRecord(s->kevent, s->kstream);
-            count_launch(s->ctx);
-            ++s->launches;
-            s->kernel_live = true;
-            progress = true;
-        }
-        // completions
-        for (auto &r : s->active) {
-            if (r->state == 2 &&
-                ((volatile unsigned long long *)s->h_flag)[r->slot] == (r->ticket & 0xFFFFFFull)) {
-                cudaMemcpyAsync(r->h_correct, r->d_correct, 4 * (size_t)r->P, cudaMemcpyDeviceToHost, s->cstream);
-                cudaMemcpyAsync(r->h_pc, r->d_pc, 4 * (size_t)r->P * r->K, cudaMemcpyDeviceToHost, s->cstream);
-                cudaMemcpyAsync(r->h_status, r->d_status, 4, cudaMemcpyDeviceToHost, s->cstream);
-                cudaEventRecord(r->ev, s->cstream);
-                s->h_active.erase(std::remove(s->h_active.begin(), s->h_active.end(), r->slot),
-                                  s->h_active.end());
-                push_active(s);
-                r->state = 3;
-                progress = true;
-            }
-            if (r->state == 3) {
-                cudaError_t q = cudaEventQuery(r->ev);
-                if (q == cudaSuccess) {
-                    r->t_done = std::chrono::steady_clock::now();
-                    r->status = *r->h_status ? RS_ERR_INVALID : RS_OK;
-                    cudaFreeAsync(r->d_buf, s->sstream);   // the copies out have completed
-                    r->d_buf = nullptr;
-                    s->used -= r->device_bytes;
-                    if (r->slot >= 0) s->free_slots.push_back(r->slot);
-                    r->state = 4;
-                    progress = true;
-                } else if (q != cudaErrorNotReady) {
-                    s->fatal = cuda_fail(q, "serving");
-                    s->fatal_flag = (int)s->fatal;
-                    r->status = s->fatal;
-                    r->state = 4;
-                }
-            }
-        }
-        s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
-                                       [](const std::shared_ptr<Request> &r) { return r->state == 4; }),
-                        s->active.end());
+        if (s->quit && s->sch.idle()) break;
+        const bool progress = s->sch.step(s->dev);
         if (progress) s->cv_done.notify_all();
         if (!progress) {
-            if (s->active.empty() && s->queued.empty()) {
+            if (s->sch.idle()) {
                 if (s->quit) break;
                 lk.unlock();
                 {
@@ -1050,7 +1044,7 @@ rs_status poll_impl(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t kind,
         return RS_ERR_INVALID;
     }
     std::unique_lock<std::mutex> lk(s->mu);
-    auto done = [&] { return r->state >= 4; };
+    auto done = [&] { return r->state >= sched::DONE; };
     if (!done()) {
         if (timeout_us <= 0) return RS_PENDING;
         if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done)) return RS_PENDING;
@@ -1070,7 +1064,7 @@ rs_status poll_impl(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t kind,
     } else {
         set_error("request rejected by the device checks (malformed batch)");
     }
-    if (r->state == 5) {            // another poll took the results first
+    if (r->state == sched::RELEASED) {   // another poll took the results first
         set_error("unknown ticket %llu", (unsigned long long)ticket);
         return RS_ERR_NOT_FOUND;
     }
@@ -1086,7 +1080,7 @@ rs_status poll_impl(Ctx *ctx, uint64_t ticket, int64_t timeout_us, int32_t kind,
         s->event_pool.push_back(r->ev);
     }
     r->h_stage = nullptr; r->h_correct = nullptr; r->ev = nullptr;
-    r->state = 5;
+    r->state = sched::RELEASED;
     lk.unlock();
     {
         std::lock_guard<std::mutex> il(s->in_mu);
@@ -1108,10 +1102,8 @@ rs_status cancel(Ctx *ctx, uint64_t ticket)
     }
     std::lock_guard<std::mutex> lk(s->mu);
     Request &r = *rp;
-    if (r.state != 0) { set_error("request already admitted"); return RS_ERR_INVALID; }
-    r.status = RS_ERR_CANCELLED;
+    if (!s->sch.cancel(r, RS_ERR_CANCELLED)) { set_error("request already admitted"); return RS_ERR_INVALID; }
     r.t_done = std::chrono::steady_clock::now();
-    r.state = 4;
     s->cv_done.notify_all();
     return RS_OK;
 }
@@ -1123,11 +1115,11 @@ rs_status server_stats(Ctx *ctx, rs_serving_stats *out)
     if (!s) return RS_OK;
     std::lock_guard<std::mutex> lk(s->mu);
     std::lock_guard<std::mutex> il(s->in_mu);
-    out->queued = (int64_t)(s->queued.size() + s->inbox.size());
-    out->active = (int64_t)s->active.size();
-    out->device_bytes_in_use = s->used;
+    out->queued = (int64_t)(s->sch.queued.size() + s->inbox.size());
+    out->active = (int64_t)s->sch.active.size();
+    out->device_bytes_in_use = s->sch.used;
     out->units_published = s->published;
-    out->kernel_launches = s->launches;
+    out->kernel_launches = s->sch.launches;
     return RS_OK;
 }
 
