@@ -403,11 +403,13 @@ def plain_leg(args, dev):
 
 
 def soft_transcendentals(batch, N):
-    """Algorithmic transcendentals of one forward + adjoint pass: per condition and sample an
-    exp and a log1p (log-sigmoid) and an exp (sigmoid of -u); per rule and sample an expm1 and a
-    log (log(1 - q)) forward and again in the adjoint, an exp (the gradient of lq), two
-    log-sum-exps (exp + log1p each) in the adjoint and one forward for rules of the sample's
-    class (counted for every rule: an upper bound on the forward share)."""
+    """Algorithmic transcendentals of one forward + adjoint pass, as the method states them: per
+    condition and sample an exp and a log1p (log-sigmoid) and an exp (sigmoid of -u); per rule and
+    sample an expm1 and a log (log(1 - q)) forward and again in the adjoint, an exp (the gradient
+    of lq), two log-sum-exps (exp + log1p each) in the adjoint and one forward for rules of the
+    sample's class (counted for every rule: an upper bound on the forward share). The kernels do
+    fewer per rule: the adjoint reuses the forward's log(1 - q) and runs one of its two
+    log-sum-exps (the other only adds log(1 - q))."""
     return N * (3 * batch.C + 11 * batch.R)
 
 

@@ -993,6 +993,11 @@ void CudaBackend::release(Request &r)
     r.status = *r.h_status ? RS_ERR_INVALID : RS_OK;
     cudaFreeAsync(r.d_buf, s->sstream);   // the copies out have completed
     r.d_buf = nullptr;
+    // the batch's pinned staging went to the device before the request's work ran (stream order):
+    // it returns to the pool now, not at the poll, so that requests whose results wait to be
+    // polled do not hold the staging arena
+    pinned_put(s, r.h_stage, r.stage_cap);
+    r.h_stage = nullptr;
 }
 
 static void server_loop(Server *s)

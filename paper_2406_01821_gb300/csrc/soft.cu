@@ -691,11 +691,19 @@ __device__ __forceinline__ bool soft_group(const SoftKArgs &a, int p, int rb, in
         for (int v = 0; v < V; ++v) {
             const float lqj = lqr[v], luj = lu[j][lane + 32 * v];
             const bool same = cls == yn[v];
-            gq[v] = same ? -exp_np(lqj + luj + lT[v] - lpy[v]) : exp_np(lqj + luj + lS[v] - lpy[v]);
-            if (!((valid >> v) & 1u)) gq[v] = 0.f;
-            const float l1q = logf(-expm1f(lqj));
-            lS[v] = log_add(same ? lqj : -INFINITY, l1q + lS[v]);
-            lT[v] = log_add(same ? -INFINITY : lqj, l1q + lT[v]);
+            const float g = exp_np(lqj + luj + (same ? lT[v] : lS[v]) - lpy[v]);
+            gq[v] = ((valid >> v) & 1u) ? (same ? -g : g) : 0.f;
+            // log(1 - q_j): the forward's step from lu_j to lu_{j+1}. Where lu_j is -inf (an earlier
+            // rule certainly fired) the value does not matter (every later term is multiplied by
+            // exp(lu) = 0 and lS, lT only meet it through lu): any finite value keeps them finite.
+            const float lun = lu[j + 1][lane + 32 * v];
+            const float l1q = luj == -INFINITY ? 0.f : lun - luj;
+            // one of the two recursions adds q_j (the one of the sample's label class or not), the
+            // other only carries the factor 1 - q_j
+            const float grow = log_add(lqj, l1q + (same ? lS[v] : lT[v]));
+            const float carry = l1q + (same ? lT[v] : lS[v]);
+            lS[v] = same ? grow : carry;
+            lT[v] = same ? carry : grow;
         }
         // conditions two at a time: the four sums (d/da, d/db-or-dt of both, over all 32 V samples)
         // share one butterfly; the first SOFT_CACHE conditions reuse u and e^-|u| from above
