@@ -101,6 +101,47 @@ def test_soft_ragged_and_pairs(ctx, orc):
     check_against_oracle(got, ref)
 
 
+def _as_lists(b):
+    sets = []
+    for p in range(b.P):
+        rules = []
+        for r in range(b.set_rule_off[p], b.set_rule_off[p + 1]):
+            conds = [(int(b.cond_f[c]), int(b.cond_g[c]), int(b.cond_op[c]), b.cond_a[c], b.cond_b[c], b.cond_t[c])
+                     for c in range(b.rule_cond_off[r], b.rule_cond_off[r + 1])]
+            rules.append((int(b.rule_class[r]), conds))
+        sets.append(rules)
+    return sets
+
+
+@pytest.mark.parametrize("F", [8, 160])
+def test_soft_rule_that_always_fires(ctx, orc, F):
+    """A rule without conditions (q = 1) in the middle of a set: no later rule and not the default
+    can be reached (their share and gradients are exactly 0, log of 'no earlier rule fired' is -inf
+    after it), in the staged-tile and the per-warp kernel, against the oracle."""
+    X, y = synth.two_class_gaussian(2500, F, 11)
+    b = synth.random_rulesets(synth.quantile_table(X), 2, 14, (5, 12), (1, 4), 11, pair_prob=0.3)
+    sets = _as_lists(b)
+    for p, rules in enumerate(sets):
+        rules[0] = (0, rules[0][1])
+        rules[1] = (1, rules[1][1])                     # both labels reachable before the empty rule
+        j = 2 + p % (len(rules) - 2)
+        rules[j] = (rules[j][0], [])                    # fires on every sample that reaches it
+    b = synth.from_lists(sets, [int(d) for d in b.set_default])
+    dl = np.random.default_rng(11).uniform(-1, 2, b.P)
+    got = soft_gpu(ctx, X, y, 2, b, 0.1, dl)
+    ref = orc.soft(X, y, 2, b, 0.1, dloss=dl, want_mag=True)
+    assert np.isfinite(ref["loss"]).all()
+    check_against_oracle(got, ref)
+    after = np.zeros(b.C, bool)                          # conditions of rules after the empty one
+    for p in range(b.P):
+        rs_ = range(b.set_rule_off[p], b.set_rule_off[p + 1])
+        e = next(r for r in rs_ if b.rule_cond_off[r + 1] == b.rule_cond_off[r])
+        after[b.rule_cond_off[e]:b.rule_cond_off[b.set_rule_off[p + 1]]] = True
+    assert after.any()
+    for n in ("a", "b", "t"):
+        assert (got["grad_" + n][after] == 0).all() and (ref["grad_" + n][after] == 0).all()
+
+
 @pytest.mark.parametrize("F", [8, 160])
 def test_unreachable_label_gives_infinite_loss(ctx, orc, F):
     """Sets where some sample's label has no rule and is not the default: the loss is +inf, as
