@@ -373,8 +373,9 @@ def categorical_leg(args, dev):
 
 def plain_leg(args, dev):
     """The paper's experiment shape (569 samples x 30 features, 64 sets x 8 rules x 1..3
-    conditions): launch-bound, so reported as time per call and evaluations per second, with no
-    roofline fraction."""
+    conditions), with the outputs that shape names: per-sample predictions [P][N] and per-set
+    correct counts (and, beside it, the counts alone). Launch-bound, so reported as time per call
+    and evaluations per second, with no roofline fraction."""
     import torch
     from paper_2406_01821_gb300 import rs, synth
     w = synth.plain_hard(seed=0)
@@ -383,22 +384,31 @@ def plain_leg(args, dev):
     ds = ctx.dataset(w.X, w.y, w.K)
     db = rs.DeviceBatch.from_host(w.batch, device=f"cuda:{dev}")
     P, K = w.batch.P, w.K
-    out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty((P, K), dtype=torch.int32, device=dev), None)
-    for _ in range(20):
-        ctx.eval_hard(ds, db, K, out=out, stream=stream)
-    stream.synchronize()
     reps = 200
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        ctx.eval_hard(ds, db, K, out=out, stream=stream)
-    e1.record(stream)
-    e1.synchronize()
-    us = e0.elapsed_time(e1) * 1e3 / reps
+
+    def per_call(out):
+        for _ in range(20):
+            ctx.eval_hard(ds, db, K, out=out, stream=stream)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.eval_hard(ds, db, K, out=out, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    correct = torch.empty(P, dtype=torch.int32, device=dev)
+    pc = torch.empty((P, K), dtype=torch.int32, device=dev)
+    preds = torch.empty((P, w.N), dtype=torch.int32, device=dev)
+    us = per_call((correct, pc, preds))
+    us_counts = per_call((correct, pc, None))
     ctx.close()
-    return {"workload": w.name, "us_per_call": us, "condition_evals_per_s": w.nominal_cond_evals() / (us * 1e-6),
+    return {"workload": w.name, "outputs": "predictions [P][N], correct [P], per-class counts [P][K]",
+            "us_per_call": us, "condition_evals_per_s": w.nominal_cond_evals() / (us * 1e-6),
             "rule_set_samples_per_s": P * w.N / (us * 1e-6), "calls": reps,
+            "us_per_call_counts_only": us_counts,
             "note": "launch-bound (pack + validate + evaluate: one cached graph replayed per call); no roofline fraction"}
 
 
