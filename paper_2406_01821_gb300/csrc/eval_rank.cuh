@@ -2,8 +2,10 @@
 // the serving kernel.
 //
 // A threshold condition has been rewritten exactly as x > c or x < c (pack.cu). Within one
-// 128-sample tile, let rank(x) be the number of the tile's values (same feature) strictly below
-// x. Because x is itself one of the tile's values,
+// 128-sample tile, let rank(x) be the position of x in the tile's values (same feature) in
+// ascending order, equal values in sample order: #{values below x} + #{equal values before it}.
+// Because x is itself one of the tile's values, and a group of equal values is either wholly
+// <= c or wholly > c,
 //     x >  c  <=>  rank(x) >= L,   L = #{tile values <= c}
 //     x <= c  <=>  rank(x) <  L
 // (a '<' cut x < c arrives as x <= nextdown(c)). L is counted once per tile and condition, by a
@@ -48,6 +50,22 @@ __device__ __forceinline__ int count_below(const float *row, int sw, float c)
 // pass rows per warp for pair / product conditions of one chunk
 template <int W> __host__ __device__ constexpr int vslots() { return W >= 32 ? 12 : 16; }
 constexpr uint32_t NOOP_K = 127u * ONES;     // constant - rank never has bit 7 set: never fails
+
+// The per-tile tables built in shared memory by the whole block once the tile's features xs
+// [F][T] and rank bytes rs [Frows][T] have landed: the reversed ranks (127 - rank) at rs + rev_off
+// and each feature's sorted column us[f][pos ^ (f & 31)] = x[f][n] with pos the rank of x[f][n]
+// (its position in the tile's stable ascending order: a permutation, so every slot is written).
+__device__ __forceinline__ void build_tile_tables(const float *xs, unsigned char *rs, uint32_t rev_off, float *us,
+                                                  int F, int Frows)
+{
+    const uint32_t *r32 = reinterpret_cast<const uint32_t *>(rs);
+    uint32_t *rr32 = reinterpret_cast<uint32_t *>(rs + rev_off);
+    for (int i = threadIdx.x; i < Frows * T / 4; i += blockDim.x) rr32[i] = r32[i] ^ 0x7F7F7F7Fu;
+    for (int i = threadIdx.x; i < F * T; i += blockDim.x) {
+        const int f = i / T;
+        us[f * T + (rs[i] ^ (f & 31))] = xs[i];
+    }
+}
 
 // The staged form of a cut for this tile: {rank-table byte offset of the row, per-byte constant}.
 __device__ __forceinline__ uint2 stage_cut(uint4 r, const float *us, uint32_t rev_off, int F)

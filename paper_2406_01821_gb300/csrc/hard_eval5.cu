@@ -13,8 +13,7 @@ constexpr uint64_t TMA_WAIT_LIMIT_NS = 2000000000ull;
 
 template <int W, bool CAT>
 __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUtensorMap tmx,
-                                                  const __grid_constant__ CUtensorMap tmr, HardArgs a,
-                                                  const float *__restrict__ Us)
+                                                  const __grid_constant__ CUtensorMap tmr, HardArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int F = a.F;
@@ -23,7 +22,7 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
     const int Frows = nbox * Fb;
     unsigned char *xs = smem;                                         // float [Frows][T]
     unsigned char *rs = xs + (size_t)Frows * T * 4;                   // u8 [Frows][T], then reversed
-    float *us = reinterpret_cast<float *>(rs + (size_t)Frows * T * 2);  // float [F][T] sorted
+    float *us = reinterpret_cast<float *>(rs + (size_t)Frows * T * 2);  // float [F][T] sorted (built here)
     uint4 *stage_all = reinterpret_cast<uint4 *>(us + (size_t)Frows * T);
     constexpr int VS = vslots<W>();
     uint32_t *vrows = reinterpret_cast<uint32_t *>(stage_all + W * 32);     // [W][VS][32]
@@ -44,13 +43,11 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
     if (threadIdx.x < 4 * W) walked[threadIdx.x] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t ubytes = (uint32_t)F * T * 4u;
-        mbar_arrive_expect_tx(bar, (uint32_t)Frows * T * 5u + ubytes);
+        mbar_arrive_expect_tx(bar, (uint32_t)Frows * T * 5u);
         for (int b = 0; b < nbox; ++b) {
             tma_load_2d(xs + (size_t)b * Fb * T * 4, &tmx, tile * T, b * Fb, bar);
             tma_load_2d(rs + (size_t)b * Fb * T, &tmr, tile * T, b * Fb, bar);
         }
-        bulk_load(us, Us + (size_t)tile * F * T, ubytes, bar);
     }
     const int32_t *yl = a.y + (int64_t)tile * T + lane * 4;   // n_pad is a multiple of T
     const int64_t t_last = min((int64_t)tile * T + T, a.N) - 1;
@@ -65,12 +62,8 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
         return;
     }
     const uint32_t rev_off = (uint32_t)Frows * T;
-    {
-        const uint32_t *r32 = reinterpret_cast<const uint32_t *>(rs);
-        uint32_t *rr32 = reinterpret_cast<uint32_t *>(rs + rev_off);
-        for (int i = threadIdx.x; i < Frows * T / 4; i += W * 32) rr32[i] = r32[i] ^ 0x7F7F7F7Fu;
-        if (threadIdx.x < T) ones[threadIdx.x] = 1.f;
-    }
+    build_tile_tables(reinterpret_cast<const float *>(xs), rs, rev_off, us, F, Frows);
+    if (threadIdx.x < T) ones[threadIdx.x] = 1.f;
     __syncthreads();
 
     const unsigned char *rl = rs + lane * 4;       // this lane's four rank bytes of row 0
@@ -153,7 +146,7 @@ static rs_status launch5_t(Ctx *ctx, Dataset *ds, const HardArgs &a, cudaStream_
     dim3 grid(tiles, a.groups);
     {
         TimedLaunch tl(ctx, TK_HARD, stream);
-        k_hard5<W, CAT><<<grid, W * 32, smem, stream>>>(*tmx, *tmr, a, ds->Us);
+        k_hard5<W, CAT><<<grid, W * 32, smem, stream>>>(*tmx, *tmr, a);
     }
     RS_CUDA(cudaGetLastError());
     count_launch(ctx);

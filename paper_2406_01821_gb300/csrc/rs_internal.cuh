@@ -152,11 +152,10 @@ struct Dataset {
     int32_t *inv = nullptr;       // [N] sorted position of caller index
     std::vector<int64_t> class_count;
     std::map<int, CUtensorMap> tmaps;   // keyed by samples per tile
-    // Rank tables (finite datasets with F <= RANK_MAX_F), per 128-sample tile t and feature f:
-    // Rk[f][n] = number of values of the tile's column f strictly below x[f][n] (0..127), and
-    // Us[t][f][j ^ (f & 31)] = the tile's column f in ascending order.
+    // Rank table (finite datasets with F <= RANK_MAX_F), per 128-sample tile and feature f:
+    // Rk[f][n] = the position of x[f][n] in the tile's column f in ascending order, equal values in
+    // sample order (0..127).
     uint8_t *Rk = nullptr;
-    float *Us = nullptr;
     bool ranked = false;
     bool rmap_ok = false;
     CUtensorMap rmap;

@@ -308,10 +308,11 @@ __global__ void k_nonfinite(const float *x, int64_t n, uint32_t *flag)
     if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
-// Rank tables of one 128-sample tile and feature per warp: the rank of each value (the number of
-// the tile's values strictly below it) and the tile's values in ascending order, stored at
-// position j ^ (f & 31) of the row (equal values are placed in sample order).
-__global__ void k_rank_tiles(const float *Xt, int64_t n_pad, int F, uint8_t *Rk, float *Us)
+// Rank table of one 128-sample tile and feature per warp: the position of each value in the
+// tile's ascending order, equal values in sample order (the number of the tile's values strictly
+// below it, plus the number of equal values before it). The evaluators rebuild the sorted column
+// from it in shared memory (one scatter), so it is the only table kept beside the features.
+__global__ void k_rank_tiles(const float *Xt, int64_t n_pad, int F, uint8_t *Rk)
 {
     const int lane = threadIdx.x & 31;
     const int f = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -319,24 +320,18 @@ __global__ void k_rank_tiles(const float *Xt, int64_t n_pad, int F, uint8_t *Rk,
     const int64_t t = blockIdx.x;
     const float4 x4 = *reinterpret_cast<const float4 *>(Xt + (int64_t)f * n_pad + t * RANK_TILE + 4 * lane);
     const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-    int below[4] = {0, 0, 0, 0}, tie_before[4] = {0, 0, 0, 0};
+    int pos[4] = {0, 0, 0, 0};
     for (int j = 0; j < 32; ++j) {
         const float o[4] = {__shfl_sync(0xFFFFFFFFu, x4.x, j), __shfl_sync(0xFFFFFFFFu, x4.y, j),
                             __shfl_sync(0xFFFFFFFFu, x4.z, j), __shfl_sync(0xFFFFFFFFu, x4.w, j)};
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                below[v] += o[u] < xv[v];
-                tie_before[v] += (o[u] == xv[v]) && (4 * j + u < 4 * lane + v);
-            }
+            for (int v = 0; v < 4; ++v)
+                pos[v] += (o[u] < xv[v]) || ((o[u] == xv[v]) && (4 * j + u < 4 * lane + v));
     }
-    const uint32_t w = (uint32_t)below[0] | ((uint32_t)below[1] << 8) | ((uint32_t)below[2] << 16) |
-                       ((uint32_t)below[3] << 24);
+    const uint32_t w = (uint32_t)pos[0] | ((uint32_t)pos[1] << 8) | ((uint32_t)pos[2] << 16) | ((uint32_t)pos[3] << 24);
     reinterpret_cast<uint32_t *>(Rk + (int64_t)f * n_pad + t * RANK_TILE)[lane] = w;
-    float *row = Us + ((int64_t)t * F + f) * RANK_TILE;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) row[(below[v] + tie_before[v]) ^ (f & 31)] = xv[v];
 }
 
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v)
@@ -441,7 +436,7 @@ rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, 
             rc = cuda_fail(e_, #call);                      \
             cleanup();                                      \
             cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm); cudaFree(ds->inv); \
-            cudaFree(ds->Rk); cudaFree(ds->Us);             \
+            cudaFree(ds->Rk);                               \
             return rc;                                      \
         }                                                   \
     } while (0)
@@ -497,11 +492,10 @@ rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, 
     REG_CUDA(cudaStreamSynchronize(stream));
     ds->finite = nonfinite == 0;
     if (ds->finite && F <= RANK_MAX_F) {
-        // rank tables for the rank-coded evaluator (1 + 4 bytes per value)
+        // rank table for the rank-coded evaluator (1 byte per value)
         REG_CUDA(cudaMalloc(&ds->Rk, (size_t)ds->n_pad * F));
-        REG_CUDA(cudaMalloc(&ds->Us, sizeof(float) * (size_t)ds->n_pad * F));
         dim3 rg((unsigned)(ds->n_pad / RANK_TILE), (unsigned)((F + 7) / 8));
-        k_rank_tiles<<<rg, 256, 0, stream>>>(ds->Xt, ds->n_pad, F, ds->Rk, ds->Us);
+        k_rank_tiles<<<rg, 256, 0, stream>>>(ds->Xt, ds->n_pad, F, ds->Rk);
         REG_CUDA(cudaGetLastError());
         REG_CUDA(cudaStreamSynchronize(stream));
         ds->ranked = true;
@@ -536,7 +530,6 @@ rs_status dataset_destroy(Ctx *ctx, uint64_t h)
     cudaFree(ds->perm);
     cudaFree(ds->inv);
     cudaFree(ds->Rk);
-    cudaFree(ds->Us);
     return RS_OK;
 }
 

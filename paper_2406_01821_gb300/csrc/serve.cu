@@ -66,7 +66,6 @@ struct __align__(16) ReqDesc {
     int32_t *correct, *per_class;
     uint64_t epoch;
     const uint8_t *Rk;                  // rank tables (rank-coded units), or null
-    const float *Us;
     const int32_t *last_end;            // [P*K] per-class last rule ends, or null
     int32_t ranked, gsets;              // gsets: sets per unit
     int32_t cat;                        // the records may hold membership tests
@@ -90,8 +89,8 @@ __device__ __forceinline__ uint64_t now_ns()
     return t;
 }
 
-// One unit on a dataset with rank tables: stage x, ranks, reversed ranks and the sorted columns
-// of the tile, then walk sets [set0, set1) with the rank-coded evaluator.
+// One unit on a dataset with rank tables: stage the tile's x and ranks, build its reversed ranks
+// and sorted columns, then walk sets [set0, set1) with the rank-coded evaluator.
 __device__ __forceinline__ void serve_unit_ranked(const ReqDesc &d, int tile, int set0, int set1,
                                                   unsigned char *smem, uint4 *st, uint32_t *vr, uint32_t ones_off,
                                                   int *s_next)
@@ -108,13 +107,10 @@ __device__ __forceinline__ void serve_unit_ranked(const ReqDesc &d, int tile, in
     }
     for (int i = threadIdx.x; i < F * (T / 16); i += blockDim.x) {
         const int f = i / (T / 16), c16 = i % (T / 16);
-        const uint4 w = *reinterpret_cast<const uint4 *>(d.Rk + (int64_t)f * d.n_pad + col0 + 16 * c16);
-        reinterpret_cast<uint4 *>(rs)[i] = w;
-        reinterpret_cast<uint4 *>(rs + (size_t)F * T)[i] =
-            make_uint4(w.x ^ 0x7F7F7F7Fu, w.y ^ 0x7F7F7F7Fu, w.z ^ 0x7F7F7F7Fu, w.w ^ 0x7F7F7F7Fu);
+        reinterpret_cast<uint4 *>(rs)[i] = *reinterpret_cast<const uint4 *>(d.Rk + (int64_t)f * d.n_pad + col0 + 16 * c16);
     }
-    const float4 *usrc = reinterpret_cast<const float4 *>(d.Us + (int64_t)tile * F * T);
-    for (int i = threadIdx.x; i < F * (T / 4); i += blockDim.x) reinterpret_cast<float4 *>(us)[i] = usrc[i];
+    __syncthreads();
+    build_tile_tables(reinterpret_cast<const float *>(xs), rs, (uint32_t)F * T, us, F, F);
     const int32_t *yl = d.y + col0 + lane * 4;
     const int64_t t_last = min(col0 + T, d.N) - 1;
     const int kmin = d.y[col0], kmax = d.y[t_last];
@@ -915,7 +911,6 @@ bool CudaBackend::admit(Request &r)
     d.correct = r.d_correct; d.per_class = r.d_pc;
     d.epoch = r.ticket & 0xFFFFFFull;
     d.Rk = ranked ? r.ds->Rk : nullptr;
-    d.Us = ranked ? r.ds->Us : nullptr;
     d.ranked = ranked ? 1 : 0;
     d.gsets = ranked ? GROUP_SETS_RANKED : GROUP_SETS;
     d.last_end = po.last_end;
