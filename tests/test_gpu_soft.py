@@ -313,9 +313,9 @@ def test_soft_fig1c_rule_vs_oracle(ctx, orc):
 
 
 def test_log1p_unit_against_float64(ctx):
-    """The soft kernels' log(1 + e) on [0, 1] (2 atanh(e / (2 + e)) by its series) against float64
-    log1p, on every float32 in [1, 2^-26] at a stride of 61 bit patterns plus the edges: at most
-    5 ulp of the float32 result (the documented bound)."""
+    """The soft kernels' log(1 + e) on [0, 1] (e p(e), p the degree-8 Remez fit of log1p(e) / e)
+    against float64 log1p, on every float32 in [1, 2^-26] at a stride of 61 bit patterns plus the
+    edges: at most 2.5 ulp of the float32 result (the documented bound is 2)."""
     from paper_2406_01821_gb300 import rs
     lo, hi = np.float32(2.0 ** -26).view(np.uint32), np.float32(1.0).view(np.uint32)
     bits = np.concatenate([np.arange(lo, hi + 1, 61, dtype=np.uint32),
@@ -327,5 +327,5 @@ def test_log1p_unit_against_float64(ctx):
     ref = np.log1p(e.astype(np.float64))
     ulp = np.spacing(ref.astype(np.float32)).astype(np.float64)
     err = np.abs(out.astype(np.float64) - ref) / ulp
-    assert err.max() <= 5.0, (float(err.max()), float(e[np.argmax(err)]))
+    assert err.max() <= 2.5, (float(err.max()), float(e[np.argmax(err)]))
     assert out[e == 0].tolist() == [0.0]
