@@ -99,7 +99,10 @@ rs_status rs_check(rs_ctx *ctx, void *stream);
  *   y      int32[N], labels in 0..K-1
  *   N >= 1, 1 <= F <= RS_MAX_FEATURES, 1 <= K <= RS_MAX_CLASSES
  * The library keeps its own copy (feature-major, samples grouped by label); the caller may free X
- * and y when the call returns. Errors: RS_ERR_INVALID (sizes, a label out of range), RS_ERR_OOM.
+ * and y when the call returns. Device memory held: 4 bytes per value and 12 per sample (labels,
+ * order), N rounded up to 256, plus for finite data with F <= 160 one byte per value (the rank of
+ * each value within its 128-sample tile, for the rank-coded evaluator).
+ * Errors: RS_ERR_INVALID (sizes, a label out of range), RS_ERR_OOM.
  * On success *ds_out receives a non-zero handle.
  */
 rs_status rs_dataset_create(rs_ctx *ctx, const float *X, const int32_t *y, int64_t N, int32_t F,
