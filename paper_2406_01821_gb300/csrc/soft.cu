@@ -42,7 +42,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr int SOFT_W = 4;                 // warps per CTA
 constexpr int SOFT_MAX_RULES = 64;        // rules per set held in shared memory
 constexpr int SOFT_MAX_CONDS = 512;       // conditions per set accumulated in shared memory
-constexpr int SOFT_MAX_CHUNKS = 64;
+constexpr int SOFT_MAX_CHUNKS = 128;
 constexpr int SOFT_V = 2;                 // samples per lane; a group is 32 * SOFT_V samples
 constexpr int SOFT_G = 32 * SOFT_V;
 
