@@ -189,3 +189,39 @@ def test_device_batch_copied_at_submission(orc):
     fin = np.isfinite(want_soft)
     assert np.allclose(loss[fin], want_soft[fin], rtol=1e-5, atol=0)
     assert (np.isinf(loss) == ~fin).all()
+
+
+def test_served_ranked_units_with_ties_equal_oracle(orc):
+    """Requests large enough for the serving kernel's rank-coded units (64 or more sets, F <= 128)
+    on data full of equal values (small integers, +0 and -0) with thresholds on data values and
+    one ulp either side: every count equals the oracle's."""
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    rng = np.random.default_rng(31)
+    N, F, K = 5000, 12, 3
+    X = rng.integers(-3, 4, (N, F)).astype(np.float32)
+    X[:, 1] = np.where(rng.random(N) < 0.5, np.float32(0.0), np.float32(-0.0))
+    y = rng.integers(0, K, N).astype(np.int32)
+    ctx = rs.Context(0, mem_budget_bytes=1 << 30)
+    try:
+        ds = ctx.dataset(X, y, K)
+        tickets, batches = [], []
+        for j in range(3):
+            b = synth.random_rulesets(synth.quantile_table(X), K, 96, (1, 16), (1, 5), 40 + j, pair_prob=0.25)
+            idx = np.flatnonzero(b.cond_g < 0)
+            a = rng.choice(np.array([1.0, -1.0, 0.5, -2.0], np.float32), len(idx))
+            t = (a * X[rng.integers(0, N, len(idx)), b.cond_f[idx]]).astype(np.float32)
+            shift = rng.integers(-1, 2, len(idx))
+            t = np.where(shift < 0, np.nextafter(t, np.float32(-np.inf)),
+                         np.where(shift > 0, np.nextafter(t, np.float32(np.inf)), t)).astype(np.float32)
+            b.cond_a[idx], b.cond_t[idx] = a, t
+            batches.append(b)
+            tickets.append(ctx.submit(ds, rs.HostBatch(b)))
+        for b, tk in zip(batches, tickets):
+            c, pc, _ = ctx.poll(tk, b.P, K, timeout_us=60_000_000)
+            want = orc.eval_hard(X, y, K, b)
+            assert np.array_equal(c, want[0])
+            assert np.array_equal(pc, want[1].reshape(b.P, K))
+        ctx.dataset_destroy(ds)
+    finally:
+        ctx.close()
