@@ -230,7 +230,8 @@ rs_status rs_eval_soft_bwd(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, floa
  *           host threads or contexts on one device) race on it and must be serialised by the
  *           caller. Each call clears the status word it needs; the rest is rewritten before use.
  * The dataset itself is registered beforehand with rs_dataset_create. Like rs_eval_hard, the call
- * stops a tile of one label after the set's last rule of that label (K <= 64).
+ * stops a tile of one label k where no later record can change its count (K <= 64): after the
+ * set's last rule of class k, or, when the set defaults to k, after its last rule of another class.
  */
 #define RS_STATIC_SCRATCH_BYTES (8u << 20)
 rs_status rs_eval_hard_static(rs_ctx *ctx, uint64_t ds, const rs_batch *batch, int32_t *correct,

@@ -80,9 +80,9 @@ __global__ void __launch_bounds__(W * 32, 1) k_hard5(const __grid_constant__ CUt
         const int p = a.order[group + m * G];
         const SetInfo si = a.sets[p];
         const int rb = si.rec_begin;
-        // one label in the tile and a default of another class: records after the set's last
-        // rule of that class cannot change its count
-        const int nrec = (uniform && a.last_end && si.deflt != kmin)
+        // one label k in the tile: records after the set's last rule of class k (default of another
+        // class) or of any other class (default k) cannot change its count
+        const int nrec = (uniform && a.last_end)
                              ? min(a.last_end[(int64_t)p * a.K + kmin], si.rec_end - si.rec_begin)
                              : si.rec_end - si.rec_begin;
 

@@ -207,6 +207,13 @@ __device__ int pack_one_set(const BatchDev &b, int K, int p, SetInfo *sets, int3
         c_begin = c_end = 0;
         if (last_end)
             for (int k = 0; k < K; ++k) last_end[(int64_t)p * K + k] = 0;
+    } else if (last_end) {
+        // for the default class d: the end of the last rule of any other class (after it every rule
+        // left names d, and so does the default: every sample still unclaimed counts for d)
+        int m = 0;
+        for (int k = 0; k < K; ++k)
+            if (k != si.deflt) m = max(m, last_end[(int64_t)p * K + k]);
+        last_end[(int64_t)p * K + si.deflt] = m;
     }
     si.rec_begin = c_begin;
     si.rec_end = c_end;

@@ -239,8 +239,11 @@ uint32_t *host_status_slot();
 // ------------------------------------------------------------------------------ kernels / launchers
 
 // Sets of at most LAST_END_MAX_K classes also get, per class k, the end (relative to the set's
-// first record) of the set's last rule of class k: in a tile whose samples all have label k, no
-// record after it can change the count when the default is another class.
+// first record) after which no record can change the count of a tile whose samples all have label
+// k: for a class other than the set's default, the end of its last rule of class k (later rules
+// only take samples of that tile away from a correct prediction or leave them to the default);
+// for the default class, the end of its last rule of any other class (every rule after it names
+// the default class, so every sample still unclaimed there is predicted correctly).
 constexpr int LAST_END_MAX_K = 64;
 
 struct PackOut {

@@ -128,9 +128,9 @@ __device__ __forceinline__ void serve_unit_ranked(const ReqDesc &d, int tile, in
         const int p = __ldcg(d.order + set0 + m);
         const int4 t = __ldcg(reinterpret_cast<const int4 *>(d.sets + p));
         const int rb = t.x, deflt = t.z;
-        // one label in the tile and a default of another class: records after the set's last
-        // rule of that class cannot change its count
-        const int nrec = (uniform && d.last_end && deflt != kmin)
+        // one label k in the tile: records after the set's last rule of class k (default of another
+        // class) or of any other class (default k) cannot change its count
+        const int nrec = (uniform && d.last_end)
                              ? min(__ldcg(d.last_end + (int64_t)p * d.K + kmin), t.y - t.x)
                              : t.y - t.x;
         uint32_t hit;

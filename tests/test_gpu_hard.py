@@ -360,12 +360,20 @@ def test_wide_and_nonfinite_data_fall_back_from_ranks(ctx, orc):
 @pytest.mark.parametrize("tile", RANKED)
 @pytest.mark.parametrize("K", [3, 100])
 def test_walk_stops_after_last_rule_of_tile_label(ctx, orc, tile, K):
-    """One-label tiles whose set defaults to another class stop after the set's last rule of that
-    label (K <= 64); with more classes the per-class table is not built."""
+    """One-label tiles stop where no later record can change their count (K <= 64): after the
+    set's last rule of the tile's label when the set defaults to another class, after its last
+    rule of another class when it defaults to the tile's label; with more classes the per-class
+    table is not built."""
     X, y = synth.gaussian_mixture(6000, 16, K, 3)
     b = synth.random_rulesets(synth.quantile_table(X), K, 48, (1, 40), (1, 4), 3)
     # a few sets with no rule of some classes, and sets whose only rules of a class come first
     b.rule_class[: b.set_rule_off[4]] = 0
+    # sets whose last rules name their default class (the stop after the last rule of another
+    # class), one of them made only of such rules
+    for p in range(4, 16):
+        r0, r1 = b.set_rule_off[p], b.set_rule_off[p + 1]
+        b.rule_class[max(r0, r1 - 1 - p % 4):r1] = b.set_default[p]
+    b.rule_class[b.set_rule_off[16]:b.set_rule_off[17]] = b.set_default[16]
     got = run_gpu(ctx, X, y, K, b, preds=False, tile=tile)
     want = orc.eval_hard(X, y, K, b)
     assert_same(got, want, preds=False)
@@ -476,6 +484,36 @@ def test_work_counters_of_the_rank_coded_walk(orc):
     assert p["hard_records_walked"] == 6 * tiles
     assert p["hard_rule_ends_walked"] == 3 * tiles
     assert p["hard_rows_walked"] == 2 * tiles
+
+
+def test_class_tail_stop_counts_records(orc):
+    """The class-tail stop, counted: with three labels and a set defaulting to class 2 whose rules
+    never fire, a one-label tile of label 0 walks only the first rule, label 1 the first two, and
+    label 2 also the first two (every later rule names the default's class); tiles holding
+    several labels walk everything."""
+    import torch
+    from paper_2406_01821_gb300 import build, rs
+    build.build()
+    X, y = synth.gaussian_mixture(3000, 6, 3, 8)
+    never = (0, -1, synth.GT, np.float32(1.0), 0.0, np.float32(X.max() + 1.0))
+    b = synth.from_lists([[(0, [never]), (1, [never]), (2, [never, never])]], [2])
+    ys = np.sort(y)
+    ys = np.concatenate([ys, np.full((-len(ys)) % 128, -1)])
+    want = 0
+    for t in ys.reshape(-1, 128):
+        lab = t[t >= 0]
+        want += 4 if lab.min() != lab.max() else {0: 1, 1: 2, 2: 2}[int(lab[0])]
+    with rs.Context(0, flags=rs.CTX_COUNT_WORK | rs.CTX_NO_GRAPH) as ctx:
+        ds = ctx.dataset(X, y, 3)
+        ctx.set_tile_config(22)
+        ctx.profile(reset=True)
+        c, pc, _ = ctx.eval_hard(ds, rs.DeviceBatch.from_host(b), 3)
+        torch.cuda.synchronize()
+        p = ctx.profile(reset=True)
+        ctx.dataset_destroy(ds)
+    ref = orc.eval_hard(X, y, 3, b)
+    assert c.cpu().numpy().tolist() == ref[0].tolist()
+    assert p["hard_records_walked"] == want
 
 
 def test_measured_pipe_rates():
