@@ -309,28 +309,56 @@ __global__ void k_nonfinite(const float *x, int64_t n, uint32_t *flag)
 }
 
 // Rank table of one 128-sample tile and feature per warp: the position of each value in the
-// tile's ascending order, equal values in sample order (the number of the tile's values strictly
-// below it, plus the number of equal values before it). The evaluators rebuild the sorted column
-// from it in shared memory (one scatter), so it is the only table kept beside the features.
+// tile's ascending order, equal values in sample order (-0 before +0: any order within a group of
+// equal values keeps the group contiguous, which is all the cut tests need). The evaluators
+// rebuild the sorted column from it in shared memory (one scatter), so it is the only table kept
+// beside the features. The warp sorts the keys (value order, then sample) with a bitonic network,
+// lane l holding elements 4l .. 4l+3, and scatters each element's final place back to its sample.
 __global__ void k_rank_tiles(const float *Xt, int64_t n_pad, int F, uint8_t *Rk)
 {
-    const int lane = threadIdx.x & 31;
-    const int f = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    __shared__ uint8_t pos_of[8][RANK_TILE];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int f = blockIdx.y * (blockDim.x >> 5) + wib;
     if (f >= F) return;
     const int64_t t = blockIdx.x;
     const float4 x4 = *reinterpret_cast<const float4 *>(Xt + (int64_t)f * n_pad + t * RANK_TILE + 4 * lane);
     const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-    int pos[4] = {0, 0, 0, 0};
-    for (int j = 0; j < 32; ++j) {
-        const float o[4] = {__shfl_sync(0xFFFFFFFFu, x4.x, j), __shfl_sync(0xFFFFFFFFu, x4.y, j),
-                            __shfl_sync(0xFFFFFFFFu, x4.z, j), __shfl_sync(0xFFFFFFFFu, x4.w, j)};
+    unsigned long long a[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v)
-                pos[v] += (o[u] < xv[v]) || ((o[u] == xv[v]) && (4 * j + u < 4 * lane + v));
+    for (int v = 0; v < 4; ++v) {
+        const uint32_t u = __float_as_uint(xv[v]);
+        const uint32_t key = (u & 0x80000000u) ? ~u : (u | 0x80000000u);   // float order (finite data)
+        a[v] = ((unsigned long long)key << 32) | (uint32_t)(4 * lane + v);
     }
-    const uint32_t w = (uint32_t)pos[0] | ((uint32_t)pos[1] << 8) | ((uint32_t)pos[2] << 16) | ((uint32_t)pos[3] << 24);
+#pragma unroll
+    for (int k = 2; k <= RANK_TILE; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 4) {                            // partners in lane ^ (j / 4), same slot
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int e = 4 * lane + v;
+                    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, a[v], j >> 2);
+                    const bool take_min = ((e & j) == 0) == ((e & k) == 0);
+                    a[v] = take_min ? (o < a[v] ? o : a[v]) : (o > a[v] ? o : a[v]);
+                }
+            } else {                                 // partners within the lane
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    if (v & j) continue;
+                    const int w = v | j;
+                    const bool asc = ((4 * lane + v) & k) == 0;
+                    const unsigned long long lo = a[v] < a[w] ? a[v] : a[w], hi = a[v] < a[w] ? a[w] : a[v];
+                    a[v] = asc ? lo : hi;
+                    a[w] = asc ? hi : lo;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) pos_of[wib][(uint32_t)a[v]] = (uint8_t)(4 * lane + v);
+    __syncwarp();
+    const uint32_t w = *reinterpret_cast<const uint32_t *>(&pos_of[wib][4 * lane]);
     reinterpret_cast<uint32_t *>(Rk + (int64_t)f * n_pad + t * RANK_TILE)[lane] = w;
 }
 
