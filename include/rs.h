@@ -112,6 +112,29 @@ rs_status rs_dataset_destroy(rs_ctx *ctx, uint64_t ds);
 rs_status rs_dataset_info(rs_ctx *ctx, uint64_t ds, int64_t *N, int32_t *F, int32_t *K,
                           int64_t *class_count);
 
+/*
+ * Device-memory budget of the context's registered datasets, for a server that keeps the datasets
+ * of many clients resident (no counterpart in the paper): 0 (the default) means no limit. With a
+ * budget, rs_dataset_create also keeps a host copy of X and y, and whenever registering or using a
+ * dataset would take the resident datasets beyond `bytes`, the least recently used datasets that
+ * nothing is using (no call running on them, no serving request queued or running on them, not
+ * yet polled) are evicted: their device copies are freed, and the next call that names one
+ * rebuilds it from its host copy (the registration's work again). Datasets registered before a
+ * budget was set have no host copy and stay resident. If too little can be evicted the budget is
+ * exceeded rather than a call refused. rs_eval_hard_static, which allocates nothing, returns
+ * RS_ERR_INVALID on an evicted dataset. Lowering the budget evicts at once.
+ */
+rs_status rs_set_dataset_budget(rs_ctx *ctx, uint64_t bytes);
+
+typedef struct {
+    int64_t datasets;          /* registered */
+    int64_t resident;          /* with their device copy present */
+    uint64_t resident_bytes;   /* device bytes of those */
+    int64_t evictions;         /* device copies freed under the budget so far */
+    int64_t rebuilds;          /* evicted datasets made resident again so far */
+} rs_dataset_stats;
+rs_status rs_dataset_stats_read(rs_ctx *ctx, rs_dataset_stats *out);
+
 /* --------------------------------------------------------------------------- rule sets */
 
 /*

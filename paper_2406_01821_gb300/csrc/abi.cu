@@ -210,6 +210,33 @@ rs_status rs_dataset_create(rs_ctx *ctx, const float *X, const int32_t *y, int64
     })
 }
 
+rs_status rs_set_dataset_budget(rs_ctx *ctx, uint64_t bytes)
+{
+    RS_GUARD({
+        if (!ctx) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return set_dataset_budget(ctx, bytes);
+    })
+}
+
+rs_status rs_dataset_stats_read(rs_ctx *ctx, rs_dataset_stats *out)
+{
+    RS_GUARD({
+        if (!ctx || !out) return RS_ERR_INVALID;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        *out = rs_dataset_stats{};
+        for (auto &kv : ctx->datasets) {
+            ++out->datasets;
+            if (kv.second->resident) ++out->resident;
+        }
+        out->resident_bytes = ctx->ds_resident;
+        out->evictions = ctx->ds_evictions;
+        out->rebuilds = ctx->ds_rebuilds;
+        return RS_OK;
+    })
+}
+
 rs_status rs_dataset_destroy(rs_ctx *ctx, uint64_t ds)
 {
     RS_GUARD({

@@ -553,8 +553,8 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
     rs_status rc = check_batch(b);
     if (rc) return rc;
     if (!correct && b->P > 0) { set_error("correct is NULL"); return RS_ERR_INVALID; }
-    auto ds = find_dataset(ctx, ds_h);
-    if (!ds) { set_error("unknown dataset %llu", (unsigned long long)ds_h); return RS_ERR_NOT_FOUND; }
+    std::shared_ptr<Dataset> ds;
+    if ((rc = use_dataset(ctx, ds_h, &ds))) return rc;
     if ((rc = device_guard(ctx))) return rc;
     if (b->R > 0 && ds->K > 4096) return RS_ERR_UNSUPPORTED;
 
@@ -619,8 +619,8 @@ rs_status autotune(Ctx *ctx, uint64_t ds_h, const rs_batch *b, cudaStream_t stre
     rs_status rc = check_batch(b);
     if (rc) return rc;
     if (b->mem != RS_MEM_DEVICE) { set_error("rs_autotune takes a device batch"); return RS_ERR_INVALID; }
-    auto ds = find_dataset(ctx, ds_h);
-    if (!ds) return RS_ERR_NOT_FOUND;
+    std::shared_ptr<Dataset> ds;
+    if ((rc = use_dataset(ctx, ds_h, &ds))) return rc;
     if ((rc = device_guard(ctx))) return rc;
     int32_t *correct = nullptr;
     RS_CUDA(cudaMalloc(&correct, sizeof(int32_t) * std::max(1, b->P)));
@@ -681,8 +681,8 @@ rs_status eval_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, float
     rs_status rc = check_batch(b);
     if (rc) return rc;
     if (!(tau > 0.f) || !std::isfinite(tau)) { set_error("tau must be finite and > 0"); return RS_ERR_INVALID; }
-    auto ds = find_dataset(ctx, ds_h);
-    if (!ds) { set_error("unknown dataset %llu", (unsigned long long)ds_h); return RS_ERR_NOT_FOUND; }
+    std::shared_ptr<Dataset> ds;
+    if ((rc = use_dataset(ctx, ds_h, &ds))) return rc;
     if ((rc = device_guard(ctx))) return rc;
     const bool host = b->mem == RS_MEM_HOST;
     const bool bwd = dloss != nullptr;

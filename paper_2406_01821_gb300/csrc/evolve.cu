@@ -557,8 +557,8 @@ static int build_csr(const PopDev &p, const int32_t *subset, int nsub, CsrWork &
 rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_population *hp,
                      int32_t *best_out, double *mean_out, cudaStream_t s)
 {
-    auto dsp = find_dataset(ctx, ds_h);
-    if (!dsp) { set_error("unknown dataset"); return RS_ERR_NOT_FOUND; }
+    std::shared_ptr<Dataset> dsp;
+    if (rs_status urc = use_dataset(ctx, ds_h, &dsp)) return urc;
     Dataset &ds = *dsp;
     const int P = cfg->P, RMAX = cfg->RMAX, CMAX = cfg->CMAX;
     if (P < 2 || RMAX < 1 || RMAX > 32 || CMAX < 1 || CMAX > 64 || cfg->generations < 0 ||
@@ -797,8 +797,8 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
 rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, float *pb, float *pt,
                        float tau, float lr, int steps, float *loss_trace, cudaStream_t s)
 {
-    auto dsp = find_dataset(ctx, ds_h);
-    if (!dsp) { set_error("unknown dataset"); return RS_ERR_NOT_FOUND; }
+    std::shared_ptr<Dataset> dsp;
+    if (rs_status urc = use_dataset(ctx, ds_h, &dsp)) return urc;
     if (!b || b->mem != RS_MEM_DEVICE || b->P < 0 || b->R < 0 || b->C < 0 || steps < 0 ||
         !(tau > 0.f) || (b->C > 0 && (!pa || !pb || !pt))) {
         set_error("rs_finetune: bad arguments (device batch, parameters and steps >= 0 required)");

@@ -81,6 +81,11 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
     }
     auto ds = find_dataset(ctx, ds_h);
     if (!ds) { set_error("unknown dataset %llu", (unsigned long long)ds_h); return RS_ERR_NOT_FOUND; }
+    if (!ds->resident) {   // rebuilding it would allocate: an allocating call makes it resident
+        set_error("dataset %llu was evicted under the context's dataset budget; any allocating call on it "
+                  "rebuilds it", (unsigned long long)ds_h);
+        return RS_ERR_INVALID;
+    }
     const size_t need = static_scratch_need(b->P, b->C, ds->K);
     if (need > RS_STATIC_SCRATCH_BYTES) {
         set_error("batch needs %zu bytes of scratch (P=%d, C=%d, K=%d); rs_eval_hard_static holds %zu "

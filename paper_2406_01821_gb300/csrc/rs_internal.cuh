@@ -157,6 +157,14 @@ struct Dataset {
     // sample order (0..127).
     uint8_t *Rk = nullptr;
     bool ranked = false;
+    // Contexts with a dataset budget (rs_set_dataset_budget): the caller's data kept on the host
+    // (row-major X, labels) so that the device copy can be evicted and rebuilt; whether the device
+    // copy exists, its bytes, and the registry tick of its last use.
+    std::vector<float> hX;
+    std::vector<int32_t> hy;
+    bool resident = true;
+    size_t dev_bytes = 0;
+    uint64_t last_use = 0;
     bool rmap_ok = false;
     CUtensorMap rmap;
     std::mutex mu;
@@ -208,6 +216,10 @@ struct Ctx {
     std::mutex mu;
     std::map<uint64_t, std::shared_ptr<Dataset>> datasets;
     uint64_t next_ds = 1;
+    uint64_t ds_budget = 0;                  // device bytes of resident datasets (0: no limit)
+    size_t ds_resident = 0;                  // device bytes of the resident datasets
+    uint64_t ds_tick = 0;                    // dataset use counter (least recently used order)
+    int64_t ds_evictions = 0, ds_rebuilds = 0;
     int forced_tile = -1;
     std::map<std::string, int> tune_table;   // key -> tile config id
     std::map<std::string, std::shared_ptr<GraphEntry>> graphs;
@@ -219,6 +231,11 @@ struct Ctx {
 };
 
 std::shared_ptr<Dataset> find_dataset(Ctx *ctx, uint64_t ds);
+// The dataset with its device copy present (rebuilt from the host copy if it was evicted, after
+// evicting others to make room), marked as the most recently used; errors: RS_ERR_NOT_FOUND, or
+// the rebuild's error.
+rs_status use_dataset(Ctx *ctx, uint64_t ds, std::shared_ptr<Dataset> *out);
+rs_status set_dataset_budget(Ctx *ctx, uint64_t bytes);
 
 // Count `n` kernel launches of the library.
 inline void count_launch(Ctx *ctx, int n = 1) { ctx->prof.launches += n; }

@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include "rs_internal.cuh"
+#include "dataset_lru.h"
 #include "tma.cuh"
 
 namespace rs {
@@ -431,6 +432,156 @@ const CUtensorMap *dataset_tmap(Dataset *ds, int S)
     return &res.first->second;
 }
 
+// Build the device copy of dataset d (N, F, K and n_pad set) from X and y (host or device per
+// `mem`): feature-major Xt grouped by label, labels, permutation and inverse, class counts, the
+// finite flag and, for finite data of at most RANK_MAX_F features, the rank table.
+static rs_status build_device(Dataset &d, const float *X, const int32_t *y, int32_t mem, cudaStream_t stream)
+{
+    const int64_t N = d.N;
+    const int32_t F = d.F, K = d.K;
+    const int64_t nblk = (N + REG_BLOCK - 1) / REG_BLOCK;
+
+    float *Xd = nullptr;
+    int32_t *yd = nullptr, *blk = nullptr, *rank = nullptr;
+    int64_t *ctot = nullptr, *cstart = nullptr;
+    uint32_t *st = nullptr;
+    rs_status rc = RS_OK;
+    auto cleanup = [&] {
+        if (mem == RS_MEM_HOST) { cudaFree(Xd); cudaFree(yd); }
+        cudaFree(blk); cudaFree(rank); cudaFree(ctot); cudaFree(cstart); cudaFree(st);
+    };
+    auto release = [&] {              // the dataset's own arrays, after a failure
+        cudaFree(d.Xt); cudaFree(d.y); cudaFree(d.perm); cudaFree(d.inv); cudaFree(d.Rk);
+        d.Xt = nullptr; d.y = nullptr; d.perm = nullptr; d.inv = nullptr; d.Rk = nullptr;
+    };
+#define REG_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) {                            \
+            rc = cuda_fail(e_, #call);                      \
+            cleanup();                                      \
+            release();                                      \
+            return rc;                                      \
+        }                                                   \
+    } while (0)
+
+    if (mem == RS_MEM_HOST) {
+        REG_CUDA(cudaMalloc(&Xd, sizeof(float) * N * F));
+        REG_CUDA(cudaMalloc(&yd, sizeof(int32_t) * N));
+        REG_CUDA(cudaMemcpyAsync(Xd, X, sizeof(float) * N * F, cudaMemcpyHostToDevice, stream));
+        REG_CUDA(cudaMemcpyAsync(yd, y, sizeof(int32_t) * N, cudaMemcpyHostToDevice, stream));
+    } else {
+        Xd = const_cast<float *>(X);
+        yd = const_cast<int32_t *>(y);
+    }
+    REG_CUDA(cudaMalloc(&d.Xt, sizeof(float) * d.n_pad * F));
+    REG_CUDA(cudaMalloc(&d.y, sizeof(int32_t) * d.n_pad));
+    REG_CUDA(cudaMalloc(&d.perm, sizeof(int32_t) * N));
+    REG_CUDA(cudaMalloc(&d.inv, sizeof(int32_t) * N));
+    REG_CUDA(cudaMalloc(&blk, sizeof(int32_t) * nblk * K));
+    REG_CUDA(cudaMalloc(&rank, sizeof(int32_t) * N));
+    REG_CUDA(cudaMalloc(&ctot, sizeof(int64_t) * K));
+    REG_CUDA(cudaMalloc(&cstart, sizeof(int64_t) * K));
+    REG_CUDA(cudaMalloc(&st, sizeof(uint32_t)));
+    REG_CUDA(cudaMemsetAsync(st, 0, sizeof(uint32_t), stream));
+    k_fill_i32<<<(unsigned)((d.n_pad + 255) / 256), 256, 0, stream>>>(d.y, d.n_pad, -1);
+    k_label_rank<<<(unsigned)nblk, REG_BLOCK, sizeof(int32_t) * (REG_BLOCK + K), stream>>>(
+        yd, N, K, blk, rank, st);
+    REG_CUDA(cudaGetLastError());
+    uint32_t hst = 0;
+    // labels must be valid before they are used as scatter positions
+    REG_CUDA(cudaMemcpyAsync(&hst, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    REG_CUDA(cudaStreamSynchronize(stream));
+    if (hst) {
+        cleanup();
+        set_error("dataset rejected: %s", status_text(hst).c_str());
+        release();
+        return RS_ERR_INVALID;
+    }
+    k_label_offsets<<<(K + 127) / 128, 128, 0, stream>>>(blk, nblk, K, ctot);
+    k_class_start<<<1, 32, 0, stream>>>(ctot, K, cstart);
+    k_label_scatter<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(yd, N, K, blk, cstart, rank,
+                                                                      d.perm, d.inv, d.y);
+    dim3 tg((unsigned)(d.n_pad / 32), (unsigned)((F + 31) / 32));
+    k_transpose_gather<<<tg, dim3(32, 8), 0, stream>>>(Xd, N, F, d.n_pad, d.perm, d.Xt);
+    REG_CUDA(cudaGetLastError());
+    REG_CUDA(cudaMemsetAsync(st, 0, sizeof(uint32_t), stream));
+    k_nonfinite<<<1024, 256, 0, stream>>>(d.Xt, d.n_pad * F, st);
+    REG_CUDA(cudaGetLastError());
+    uint32_t nonfinite = 0;
+    REG_CUDA(cudaMemcpyAsync(&nonfinite, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    d.class_count.resize(K);
+    REG_CUDA(cudaMemcpyAsync(d.class_count.data(), ctot, sizeof(int64_t) * K,
+                             cudaMemcpyDeviceToHost, stream));
+    REG_CUDA(cudaStreamSynchronize(stream));
+    d.finite = nonfinite == 0;
+    if (d.finite && F <= RANK_MAX_F) {
+        // rank table for the rank-coded evaluator (1 byte per value)
+        REG_CUDA(cudaMalloc(&d.Rk, (size_t)d.n_pad * F));
+        dim3 rg((unsigned)(d.n_pad / RANK_TILE), (unsigned)((F + 7) / 8));
+        k_rank_tiles<<<rg, 256, 0, stream>>>(d.Xt, d.n_pad, F, d.Rk);
+        REG_CUDA(cudaGetLastError());
+        REG_CUDA(cudaStreamSynchronize(stream));
+        d.ranked = true;
+    }
+    cleanup();
+#undef REG_CUDA
+    return RS_OK;
+}
+
+static size_t dataset_device_bytes(const Dataset &d)
+{
+    return sizeof(float) * (size_t)d.n_pad * d.F + sizeof(int32_t) * ((size_t)d.n_pad + 2 * (size_t)d.N) +
+           (d.Rk ? (size_t)d.n_pad * d.F : 0);
+}
+
+static void free_device(Dataset &d)
+{
+    cudaFree(d.Xt);
+    cudaFree(d.y);
+    cudaFree(d.perm);
+    cudaFree(d.inv);
+    cudaFree(d.Rk);
+    d.Xt = nullptr; d.y = nullptr; d.perm = nullptr; d.inv = nullptr; d.Rk = nullptr;
+    std::lock_guard<std::mutex> lk(d.mu);
+    d.tmaps.clear();                 // tensor maps hold the device addresses
+    d.rmap_ok = false;
+}
+
+// With ctx->mu held: drop the cached graphs that reference dataset h.
+static void drop_graphs(Ctx *ctx, uint64_t h)
+{
+    const std::string key = "ds" + std::to_string(h) + "|";
+    for (auto g = ctx->graphs.begin(); g != ctx->graphs.end();) {
+        if (g->first.rfind(key, 0) == 0) g = ctx->graphs.erase(g);
+        else ++g;
+    }
+}
+
+// With ctx->mu held: evict least recently used datasets so that `need` more device bytes fit the
+// budget (dataset_lru.h), `keep` excepted.
+static void make_room(Ctx *ctx, size_t need, uint64_t keep)
+{
+    if (!ctx->ds_budget) return;
+    std::vector<lru::Entry> entries;
+    for (auto &kv : ctx->datasets) {
+        const Dataset &d = *kv.second;
+        // the registry's own reference is the only one: no call or request is using the dataset
+        entries.push_back({kv.first, d.dev_bytes, d.last_use, d.resident, !d.hy.empty() && kv.second.use_count() == 1});
+    }
+    const std::vector<uint64_t> v = lru::victims(entries, ctx->ds_resident, need, ctx->ds_budget, keep);
+    if (v.empty()) return;
+    cudaDeviceSynchronize();         // work already enqueued on them (asynchronous calls) finishes first
+    for (uint64_t h : v) {
+        Dataset &d = *ctx->datasets[h];
+        drop_graphs(ctx, h);
+        free_device(d);
+        d.resident = false;
+        ctx->ds_resident -= std::min(ctx->ds_resident, d.dev_bytes);
+        ++ctx->ds_evictions;
+    }
+}
+
 rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, int32_t F,
                          int32_t K, int32_t mem, cudaStream_t stream, uint64_t *out)
 {
@@ -446,94 +597,64 @@ rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, 
     ds->F = F;
     ds->K = K;
     ds->n_pad = (N + 255) / 256 * 256;
-    const int64_t nblk = (N + REG_BLOCK - 1) / REG_BLOCK;
-
-    float *Xd = nullptr;
-    int32_t *yd = nullptr, *blk = nullptr, *rank = nullptr;
-    int64_t *ctot = nullptr, *cstart = nullptr;
-    uint32_t *st = nullptr;
-    rs_status rc = RS_OK;
-    auto cleanup = [&] {
-        if (mem == RS_MEM_HOST) { cudaFree(Xd); cudaFree(yd); }
-        cudaFree(blk); cudaFree(rank); cudaFree(ctot); cudaFree(cstart); cudaFree(st);
-    };
-#define REG_CUDA(call)                                      \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) {                            \
-            rc = cuda_fail(e_, #call);                      \
-            cleanup();                                      \
-            cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm); cudaFree(ds->inv); \
-            cudaFree(ds->Rk);                               \
-            return rc;                                      \
-        }                                                   \
-    } while (0)
-
-    if (mem == RS_MEM_HOST) {
-        REG_CUDA(cudaMalloc(&Xd, sizeof(float) * N * F));
-        REG_CUDA(cudaMalloc(&yd, sizeof(int32_t) * N));
-        REG_CUDA(cudaMemcpyAsync(Xd, X, sizeof(float) * N * F, cudaMemcpyHostToDevice, stream));
-        REG_CUDA(cudaMemcpyAsync(yd, y, sizeof(int32_t) * N, cudaMemcpyHostToDevice, stream));
-    } else {
-        Xd = const_cast<float *>(X);
-        yd = const_cast<int32_t *>(y);
+    bool budget = false;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        budget = ctx->ds_budget != 0;
+        if (budget) {                 // room for the largest form it can take (with a rank table)
+            const size_t upper = sizeof(float) * (size_t)ds->n_pad * F + sizeof(int32_t) * ((size_t)ds->n_pad + 2 * (size_t)N) +
+                                 (F <= RANK_MAX_F ? (size_t)ds->n_pad * F : 0);
+            make_room(ctx, upper, 0);
+        }
     }
-    REG_CUDA(cudaMalloc(&ds->Xt, sizeof(float) * ds->n_pad * F));
-    REG_CUDA(cudaMalloc(&ds->y, sizeof(int32_t) * ds->n_pad));
-    REG_CUDA(cudaMalloc(&ds->perm, sizeof(int32_t) * N));
-    REG_CUDA(cudaMalloc(&ds->inv, sizeof(int32_t) * N));
-    REG_CUDA(cudaMalloc(&blk, sizeof(int32_t) * nblk * K));
-    REG_CUDA(cudaMalloc(&rank, sizeof(int32_t) * N));
-    REG_CUDA(cudaMalloc(&ctot, sizeof(int64_t) * K));
-    REG_CUDA(cudaMalloc(&cstart, sizeof(int64_t) * K));
-    REG_CUDA(cudaMalloc(&st, sizeof(uint32_t)));
-    REG_CUDA(cudaMemsetAsync(st, 0, sizeof(uint32_t), stream));
-    k_fill_i32<<<(unsigned)((ds->n_pad + 255) / 256), 256, 0, stream>>>(ds->y, ds->n_pad, -1);
-    k_label_rank<<<(unsigned)nblk, REG_BLOCK, sizeof(int32_t) * (REG_BLOCK + K), stream>>>(
-        yd, N, K, blk, rank, st);
-    REG_CUDA(cudaGetLastError());
-    uint32_t hst = 0;
-    // labels must be valid before they are used as scatter positions
-    REG_CUDA(cudaMemcpyAsync(&hst, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
-    REG_CUDA(cudaStreamSynchronize(stream));
-    if (hst) {
-        cleanup();
-        set_error("dataset rejected: %s", status_text(hst).c_str());
-        cudaFree(ds->Xt); cudaFree(ds->y); cudaFree(ds->perm); cudaFree(ds->inv);
-        return RS_ERR_INVALID;
+    if (budget) {                     // the host copy an eviction rebuilds from
+        ds->hX.resize((size_t)N * F);
+        ds->hy.resize((size_t)N);
+        const cudaMemcpyKind kind = mem == RS_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+        cudaError_t e = cudaMemcpy(ds->hX.data(), X, sizeof(float) * (size_t)N * F, kind);
+        if (e == cudaSuccess) e = cudaMemcpy(ds->hy.data(), y, sizeof(int32_t) * (size_t)N, kind);
+        if (e != cudaSuccess) return cuda_fail(e, "dataset host copy");
     }
-    k_label_offsets<<<(K + 127) / 128, 128, 0, stream>>>(blk, nblk, K, ctot);
-    k_class_start<<<1, 32, 0, stream>>>(ctot, K, cstart);
-    k_label_scatter<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(yd, N, K, blk, cstart, rank,
-                                                                      ds->perm, ds->inv, ds->y);
-    dim3 tg((unsigned)(ds->n_pad / 32), (unsigned)((F + 31) / 32));
-    k_transpose_gather<<<tg, dim3(32, 8), 0, stream>>>(Xd, N, F, ds->n_pad, ds->perm, ds->Xt);
-    REG_CUDA(cudaGetLastError());
-    REG_CUDA(cudaMemsetAsync(st, 0, sizeof(uint32_t), stream));
-    k_nonfinite<<<1024, 256, 0, stream>>>(ds->Xt, ds->n_pad * F, st);
-    REG_CUDA(cudaGetLastError());
-    uint32_t nonfinite = 0;
-    REG_CUDA(cudaMemcpyAsync(&nonfinite, st, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
-    ds->class_count.resize(K);
-    REG_CUDA(cudaMemcpyAsync(ds->class_count.data(), ctot, sizeof(int64_t) * K,
-                             cudaMemcpyDeviceToHost, stream));
-    REG_CUDA(cudaStreamSynchronize(stream));
-    ds->finite = nonfinite == 0;
-    if (ds->finite && F <= RANK_MAX_F) {
-        // rank table for the rank-coded evaluator (1 byte per value)
-        REG_CUDA(cudaMalloc(&ds->Rk, (size_t)ds->n_pad * F));
-        dim3 rg((unsigned)(ds->n_pad / RANK_TILE), (unsigned)((F + 7) / 8));
-        k_rank_tiles<<<rg, 256, 0, stream>>>(ds->Xt, ds->n_pad, F, ds->Rk);
-        REG_CUDA(cudaGetLastError());
-        REG_CUDA(cudaStreamSynchronize(stream));
-        ds->ranked = true;
-    }
-    cleanup();
-#undef REG_CUDA
+    const rs_status rc = build_device(*ds, X, y, mem, stream);
+    if (rc) return rc;
+    ds->dev_bytes = dataset_device_bytes(*ds);
     std::lock_guard<std::mutex> lk(ctx->mu);
     const uint64_t h = ctx->next_ds++;
+    ds->last_use = ++ctx->ds_tick;
+    ctx->ds_resident += ds->dev_bytes;
     ctx->datasets[h] = ds;
     *out = h;
+    return RS_OK;
+}
+
+rs_status use_dataset(Ctx *ctx, uint64_t h, std::shared_ptr<Dataset> *out)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->datasets.find(h);
+    if (it == ctx->datasets.end()) {
+        set_error("unknown dataset %llu", (unsigned long long)h);
+        return RS_ERR_NOT_FOUND;
+    }
+    Dataset &d = *it->second;
+    d.last_use = ++ctx->ds_tick;
+    if (!d.resident) {                // evicted: rebuild it from the host copy
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        make_room(ctx, d.dev_bytes, h);
+        if ((rc = build_device(d, d.hX.data(), d.hy.data(), RS_MEM_HOST, nullptr))) return rc;
+        d.resident = true;
+        ctx->ds_resident += d.dev_bytes;
+        ++ctx->ds_rebuilds;
+    }
+    *out = it->second;
+    return RS_OK;
+}
+
+rs_status set_dataset_budget(Ctx *ctx, uint64_t bytes)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->ds_budget = bytes;
+    make_room(ctx, 0, 0);
     return RS_OK;
 }
 
@@ -546,18 +667,11 @@ rs_status dataset_destroy(Ctx *ctx, uint64_t h)
         if (it == ctx->datasets.end()) { set_error("unknown dataset %llu", (unsigned long long)h); return RS_ERR_NOT_FOUND; }
         ds = it->second;
         ctx->datasets.erase(it);
-        // drop cached graphs that reference this dataset
-        for (auto g = ctx->graphs.begin(); g != ctx->graphs.end();) {
-            if (g->first.rfind("ds" + std::to_string(h) + "|", 0) == 0) g = ctx->graphs.erase(g);
-            else ++g;
-        }
+        drop_graphs(ctx, h);          // cached graphs that reference this dataset
+        if (ds->resident) ctx->ds_resident -= std::min(ctx->ds_resident, ds->dev_bytes);
     }
     RS_CUDA(cudaDeviceSynchronize());
-    cudaFree(ds->Xt);
-    cudaFree(ds->y);
-    cudaFree(ds->perm);
-    cudaFree(ds->inv);
-    cudaFree(ds->Rk);
+    free_device(*ds);
     return RS_OK;
 }
 

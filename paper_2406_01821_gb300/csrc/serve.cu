@@ -653,8 +653,8 @@ rs_status submit_impl(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t kind, 
         set_error("bad batch");
         return RS_ERR_INVALID;
     }
-    auto ds = find_dataset(ctx, ds_h);
-    if (!ds) { set_error("unknown dataset"); return RS_ERR_NOT_FOUND; }
+    std::shared_ptr<Dataset> ds;
+    if (rs_status urc = use_dataset(ctx, ds_h, &ds)) return urc;
     if (kind == RS_KIND_HARD && ds->F > SERVE_MAX_F) {
         set_error("hard requests are served on datasets of at most %d features", SERVE_MAX_F);
         return RS_ERR_UNSUPPORTED;

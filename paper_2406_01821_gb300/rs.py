@@ -71,6 +71,12 @@ class rs_serving_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64)]
 
 
+class rs_dataset_stats(ctypes.Structure):
+    _fields_ = [("datasets", ctypes.c_int64), ("resident", ctypes.c_int64),
+                ("resident_bytes", ctypes.c_uint64), ("evictions", ctypes.c_int64),
+                ("rebuilds", ctypes.c_int64)]
+
+
 class rs_evolve_config(ctypes.Structure):
     _fields_ = [("P", ctypes.c_int32), ("RMAX", ctypes.c_int32), ("CMAX", ctypes.c_int32),
                 ("generations", ctypes.c_int32), ("elite", ctypes.c_int32),
@@ -93,6 +99,8 @@ _SIGS = {
                                            ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_uint64)]),
     "rs_dataset_destroy": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rs_set_dataset_budget": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rs_dataset_stats_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rs_dataset_stats)]),
     "rs_dataset_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
@@ -304,6 +312,16 @@ class Context:
 
     def dataset_destroy(self, ds: int):
         check(lib().rs_dataset_destroy(self.h, ds))
+
+    def set_dataset_budget(self, nbytes: int):
+        """Device-memory budget of this context's datasets (0: no limit); least recently used
+        datasets not in use are evicted beyond it and rebuilt when next named."""
+        check(lib().rs_set_dataset_budget(self.h, int(nbytes)))
+
+    def dataset_stats(self) -> dict:
+        st = rs_dataset_stats()
+        check(lib().rs_dataset_stats_read(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in rs_dataset_stats._fields_}
 
     def dataset_info(self, ds: int):
         N, F, K = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
