@@ -121,10 +121,10 @@ rs_status rs_dataset_info(rs_ctx *ctx, uint64_t ds, int64_t *N, int32_t *F, int3
  * yet polled) are evicted: their device copies are freed, and the next call that names one
  * rebuilds it from its host copy (the registration's work again). Datasets registered before a
  * budget was set have no host copy and stay resident. If too little can be evicted the budget is
- * exceeded rather than a call refused. An eviction first waits for the device to finish the work
- * already queued on it (calls of asynchronous contexts may still be reading the dataset), and a
- * live serving kernel only leaves 20 ms after its queue empties: under serving load, size the
- * budget so that evictions are rare. rs_eval_hard_static, which allocates nothing, returns
+ * exceeded rather than a call refused. Each call marks the device work it enqueued on a dataset
+ * (an event on its stream); a dataset whose marked work is still pending (calls of asynchronous
+ * contexts) is not chosen, and only work no mark covers (calls on a stream being captured) makes
+ * an eviction wait for the whole device. rs_eval_hard_static, which allocates nothing, returns
  * RS_ERR_INVALID on an evicted dataset. Lowering the budget evicts at once.
  */
 rs_status rs_set_dataset_budget(rs_ctx *ctx, uint64_t bytes);

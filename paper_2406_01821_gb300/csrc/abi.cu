@@ -181,6 +181,7 @@ rs_status rs_destroy(rs_ctx *ctx)
         std::vector<uint64_t> ids;
         for (auto &kv : ctx->datasets) ids.push_back(kv.first);
         for (auto id : ids) dataset_destroy(ctx, id);
+        release_dataset_events(ctx);
         ctx->graphs.clear();
         cudaFree(ctx->d_sticky);
         cudaFree(ctx->d_walked);

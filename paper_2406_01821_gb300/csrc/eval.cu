@@ -556,6 +556,7 @@ rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct
     std::shared_ptr<Dataset> ds;
     if ((rc = use_dataset(ctx, ds_h, &ds))) return rc;
     if ((rc = device_guard(ctx))) return rc;
+    DatasetUseMark use_mark{ctx, ds.get(), stream};
     if (b->R > 0 && ds->K > 4096) return RS_ERR_UNSUPPORTED;
 
     const int tid = tile_override >= 0 ? tile_override : pick_tile(ctx, *ds, b);
@@ -622,6 +623,7 @@ rs_status autotune(Ctx *ctx, uint64_t ds_h, const rs_batch *b, cudaStream_t stre
     std::shared_ptr<Dataset> ds;
     if ((rc = use_dataset(ctx, ds_h, &ds))) return rc;
     if ((rc = device_guard(ctx))) return rc;
+    DatasetUseMark use_mark{ctx, ds.get(), stream};
     int32_t *correct = nullptr;
     RS_CUDA(cudaMalloc(&correct, sizeof(int32_t) * std::max(1, b->P)));
     cudaEvent_t e0, e1;
@@ -684,6 +686,7 @@ rs_status eval_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, float
     std::shared_ptr<Dataset> ds;
     if ((rc = use_dataset(ctx, ds_h, &ds))) return rc;
     if ((rc = device_guard(ctx))) return rc;
+    DatasetUseMark use_mark{ctx, ds.get(), stream};
     const bool host = b->mem == RS_MEM_HOST;
     const bool bwd = dloss != nullptr;
     if (bwd && b->C > 0 && (!ga || !gb || !gt)) { set_error("gradient outputs are NULL"); return RS_ERR_INVALID; }

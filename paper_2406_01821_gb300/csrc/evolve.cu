@@ -559,6 +559,7 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
 {
     std::shared_ptr<Dataset> dsp;
     if (rs_status urc = use_dataset(ctx, ds_h, &dsp)) return urc;
+    DatasetUseMark use_mark{ctx, dsp.get(), s};
     Dataset &ds = *dsp;
     const int P = cfg->P, RMAX = cfg->RMAX, CMAX = cfg->CMAX;
     if (P < 2 || RMAX < 1 || RMAX > 32 || CMAX < 1 || CMAX > 64 || cfg->generations < 0 ||
@@ -799,6 +800,7 @@ rs_status finetune_run(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float *pa, fl
 {
     std::shared_ptr<Dataset> dsp;
     if (rs_status urc = use_dataset(ctx, ds_h, &dsp)) return urc;
+    DatasetUseMark use_mark{ctx, dsp.get(), s};
     if (!b || b->mem != RS_MEM_DEVICE || b->P < 0 || b->R < 0 || b->C < 0 || steps < 0 ||
         !(tau > 0.f) || (b->C > 0 && (!pa || !pb || !pt))) {
         set_error("rs_finetune: bad arguments (device batch, parameters and steps >= 0 required)");

@@ -86,6 +86,7 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
                   "rebuilds it", (unsigned long long)ds_h);
         return RS_ERR_INVALID;
     }
+    DatasetUseMark use_mark{ctx, ds.get(), stream, false};
     const size_t need = static_scratch_need(b->P, b->C, ds->K);
     if (need > RS_STATIC_SCRATCH_BYTES) {
         set_error("batch needs %zu bytes of scratch (P=%d, C=%d, K=%d); rs_eval_hard_static holds %zu "

@@ -165,6 +165,12 @@ struct Dataset {
     bool resident = true;
     size_t dev_bytes = 0;
     uint64_t last_use = 0;
+    // Under a budget: an event recorded on each call's stream when the call returns (the call's
+    // device work on the dataset is done once it completes), and whether some call's work could
+    // not be marked so (a stream being captured, or no event to spare): evicting it then waits for
+    // the device. Under the context's mu.
+    std::vector<cudaEvent_t> inflight;
+    bool unmarked_use = false;
     bool rmap_ok = false;
     CUtensorMap rmap;
     std::mutex mu;
@@ -220,6 +226,7 @@ struct Ctx {
     size_t ds_resident = 0;                  // device bytes of the resident datasets
     uint64_t ds_tick = 0;                    // dataset use counter (least recently used order)
     int64_t ds_evictions = 0, ds_rebuilds = 0;
+    std::vector<cudaEvent_t> ds_events;      // spare events for the datasets' in-flight marks
     int forced_tile = -1;
     std::map<std::string, int> tune_table;   // key -> tile config id
     std::map<std::string, std::shared_ptr<GraphEntry>> graphs;
@@ -236,6 +243,20 @@ std::shared_ptr<Dataset> find_dataset(Ctx *ctx, uint64_t ds);
 // the rebuild's error.
 rs_status use_dataset(Ctx *ctx, uint64_t ds, std::shared_ptr<Dataset> *out);
 rs_status set_dataset_budget(Ctx *ctx, uint64_t bytes);
+// Under a dataset budget: mark the device work a call enqueued on `stream` for dataset ds, so that
+// an eviction waits for that work only (no-op without a budget). `may_create`: the call may create
+// an event when none is spare (not the allocation-free entry).
+void mark_dataset_use(Ctx *ctx, Dataset *ds, cudaStream_t stream, bool may_create = true);
+// Records the mark when the call's scope ends (after its work is enqueued).
+struct DatasetUseMark {
+    Ctx *ctx;
+    Dataset *ds;
+    cudaStream_t stream;
+    bool may_create = true;
+    ~DatasetUseMark() { if (ds) mark_dataset_use(ctx, ds, stream, may_create); }
+};
+// Free the context's spare events and every dataset's marks (context teardown).
+void release_dataset_events(Ctx *ctx);
 
 // Count `n` kernel launches of the library.
 inline void count_launch(Ctx *ctx, int n = 1) { ctx->prof.launches += n; }

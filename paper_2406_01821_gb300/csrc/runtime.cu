@@ -558,6 +558,59 @@ static void drop_graphs(Ctx *ctx, uint64_t h)
     }
 }
 
+// With ctx->mu held: return the dataset's completed in-flight marks to the spare events; true if
+// none is left (no call's device work on it is pending, as far as the marks tell).
+static bool reap_marks(Ctx *ctx, Dataset &d)
+{
+    auto &v = d.inflight;
+    for (size_t i = 0; i < v.size();) {
+        const cudaError_t q = cudaEventQuery(v[i]);
+        if (q == cudaErrorNotReady) { ++i; continue; }
+        cudaGetLastError();
+        ctx->ds_events.push_back(v[i]);
+        v[i] = v.back();
+        v.pop_back();
+    }
+    return v.empty();
+}
+
+void mark_dataset_use(Ctx *ctx, Dataset *ds, cudaStream_t stream, bool may_create)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->ds_budget) return;
+    reap_marks(ctx, *ds);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) { cudaGetLastError(); cap = cudaStreamCaptureStatusActive; }
+    cudaEvent_t ev = nullptr;
+    if (cap == cudaStreamCaptureStatusNone) {
+        if (!ctx->ds_events.empty()) {
+            ev = ctx->ds_events.back();
+            ctx->ds_events.pop_back();
+        } else if (!may_create || cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ev = nullptr;
+        }
+    }
+    if (ev && cudaEventRecord(ev, stream) == cudaSuccess) {
+        ds->inflight.push_back(ev);
+        return;
+    }
+    cudaGetLastError();
+    if (ev) ctx->ds_events.push_back(ev);
+    ds->unmarked_use = true;         // its eviction waits for the whole device
+}
+
+void release_dataset_events(Ctx *ctx)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto &kv : ctx->datasets) {
+        for (cudaEvent_t e : kv.second->inflight) cudaEventDestroy(e);
+        kv.second->inflight.clear();
+    }
+    for (cudaEvent_t e : ctx->ds_events) cudaEventDestroy(e);
+    ctx->ds_events.clear();
+}
+
 // With ctx->mu held: evict least recently used datasets so that `need` more device bytes fit the
 // budget (dataset_lru.h), `keep` excepted.
 static void make_room(Ctx *ctx, size_t need, uint64_t keep)
@@ -565,18 +618,23 @@ static void make_room(Ctx *ctx, size_t need, uint64_t keep)
     if (!ctx->ds_budget) return;
     std::vector<lru::Entry> entries;
     for (auto &kv : ctx->datasets) {
-        const Dataset &d = *kv.second;
-        // the registry's own reference is the only one: no call or request is using the dataset
-        entries.push_back({kv.first, d.dev_bytes, d.last_use, d.resident, !d.hy.empty() && kv.second.use_count() == 1});
+        Dataset &d = *kv.second;
+        // the registry's own reference is the only one (no call or request holds the dataset), and
+        // the device work of the calls that used it has completed, or is unknown (then waited for)
+        const bool idle = kv.second.use_count() == 1 && (!d.resident || reap_marks(ctx, d));
+        entries.push_back({kv.first, d.dev_bytes, d.last_use, d.resident, !d.hy.empty() && idle});
     }
     const std::vector<uint64_t> v = lru::victims(entries, ctx->ds_resident, need, ctx->ds_budget, keep);
     if (v.empty()) return;
-    cudaDeviceSynchronize();         // work already enqueued on them (asynchronous calls) finishes first
+    bool unmarked = false;
+    for (uint64_t h : v) unmarked |= ctx->datasets[h]->unmarked_use;
+    if (unmarked) cudaDeviceSynchronize();   // work that no mark covers finishes first
     for (uint64_t h : v) {
         Dataset &d = *ctx->datasets[h];
         drop_graphs(ctx, h);
         free_device(d);
         d.resident = false;
+        d.unmarked_use = false;
         ctx->ds_resident -= std::min(ctx->ds_resident, d.dev_bytes);
         ++ctx->ds_evictions;
     }
@@ -654,6 +712,12 @@ rs_status set_dataset_budget(Ctx *ctx, uint64_t bytes)
 {
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->ds_budget = bytes;
+    // spare marks, so that calls that may not create one (the allocation-free entry) find one
+    while (bytes && ctx->ds_events.size() < 32) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); break; }
+        ctx->ds_events.push_back(e);
+    }
     make_room(ctx, 0, 0);
     return RS_OK;
 }
@@ -669,6 +733,8 @@ rs_status dataset_destroy(Ctx *ctx, uint64_t h)
         ctx->datasets.erase(it);
         drop_graphs(ctx, h);          // cached graphs that reference this dataset
         if (ds->resident) ctx->ds_resident -= std::min(ctx->ds_resident, ds->dev_bytes);
+        for (cudaEvent_t e : ds->inflight) ctx->ds_events.push_back(e);   // the device wait below covers them
+        ds->inflight.clear();
     }
     RS_CUDA(cudaDeviceSynchronize());
     free_device(*ds);

@@ -92,12 +92,24 @@ def test_async_calls_and_static_entry(orc):
             pc = torch.empty((dbs[i].c().P, K), dtype=torch.int32, device="cuda")
             ctx.eval_hard(dss[i], dbs[i], K, out=(c, pc, None), stream=stream)
             outs.append((c, pc))
-        dss.append(ctx.dataset(data[2][0], data[2][1], K))   # evicts the first under its queued work
+        # a dataset whose queued work has not completed is not evicted (its mark is pending);
+        # whichever is chosen, the queued results are exact
+        dss.append(ctx.dataset(data[2][0], data[2][1], K))
         rs.check(rs.lib().rs_check(ctx.h, rs._stream_ptr(stream)))
         for i in (0, 1):
             assert np.array_equal(outs[i][0].cpu().numpy(), want[i][0])
             assert np.array_equal(outs[i][1].cpu().numpy(), want[i][1].reshape(-1, K))
-        assert ctx.dataset_stats()["evictions"] == 1
+        assert ctx.dataset_stats()["evictions"] <= 1
+        if ctx.dataset_stats()["resident"] == 3:     # nothing was idle then: make room now
+            c, _, _ = ctx.eval_hard(dss[2], rs.HostBatch(data[2][2]), K)
+            ctx.set_dataset_budget(2 * one + one // 2)
+        assert ctx.dataset_stats()["resident"] == 2
+        for i in (2, 1):                           # synchronous uses: the first is left evicted
+            c = torch.empty(dbs[i].c().P, dtype=torch.int32, device="cuda")
+            ctx.eval_hard(dss[i], dbs[i], K, out=(c, None, None), stream=stream)
+            rs.check(rs.lib().rs_check(ctx.h, rs._stream_ptr(stream)))
+            assert np.array_equal(c.cpu().numpy(), want[i][0])
+        assert ctx.dataset_stats()["resident"] == 2
         # the allocation-free entry refuses an evicted dataset (rebuilding would allocate)
         cb = dbs[0].c()
         c = torch.empty(cb.P, dtype=torch.int32, device="cuda")
