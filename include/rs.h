@@ -107,6 +107,13 @@ rs_status rs_check(rs_ctx *ctx, void *stream);
  */
 rs_status rs_dataset_create(rs_ctx *ctx, const float *X, const int32_t *y, int64_t N, int32_t F,
                             int32_t K, int32_t mem, void *stream, uint64_t *ds_out);
+/*
+ * Unregister a dataset and free its device copy (and its host copy under a dataset budget). The
+ * device's queued work completes first, so no call enqueued earlier on any stream still reads it.
+ * Errors: RS_ERR_NOT_FOUND (unknown handle); RS_ERR_INVALID while the dataset is in use: a call on
+ * it is running in another thread, or a serving request on it has not been polled yet (queued,
+ * running, completed or cancelled: poll it first). The handle stays valid after an error.
+ */
 rs_status rs_dataset_destroy(rs_ctx *ctx, uint64_t ds);
 /* Shape of a dataset; class_count (host, int64[K]) may be NULL. */
 rs_status rs_dataset_info(rs_ctx *ctx, uint64_t ds, int64_t *N, int32_t *F, int32_t *K,

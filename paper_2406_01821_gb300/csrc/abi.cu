@@ -9,7 +9,7 @@ namespace rs {
 const char *last_error();
 rs_status dataset_create(Ctx *ctx, const float *X, const int32_t *y, int64_t N, int32_t F,
                          int32_t K, int32_t mem, cudaStream_t stream, uint64_t *out);
-rs_status dataset_destroy(Ctx *ctx, uint64_t h);
+rs_status dataset_destroy(Ctx *ctx, uint64_t h, bool force);
 rs_status eval_hard(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *correct,
                     int32_t *per_class, int32_t *preds, cudaStream_t stream, int tile_override);
 rs_status eval_soft(Ctx *ctx, uint64_t ds_h, const rs_batch *b, float tau, float *loss,
@@ -180,7 +180,7 @@ rs_status rs_destroy(rs_ctx *ctx)
         cudaDeviceSynchronize();
         std::vector<uint64_t> ids;
         for (auto &kv : ctx->datasets) ids.push_back(kv.first);
-        for (auto id : ids) dataset_destroy(ctx, id);
+        for (auto id : ids) dataset_destroy(ctx, id, true);   // serving is shut down: nothing reads them
         release_dataset_events(ctx);
         ctx->graphs.clear();
         cudaFree(ctx->d_sticky);
@@ -244,7 +244,7 @@ rs_status rs_dataset_destroy(rs_ctx *ctx, uint64_t ds)
         if (!ctx) return RS_ERR_INVALID;
         rs_status rc = device_guard(ctx);
         if (rc) return rc;
-        return dataset_destroy(ctx, ds);
+        return dataset_destroy(ctx, ds, false);
     })
 }
 

@@ -722,13 +722,20 @@ rs_status set_dataset_budget(Ctx *ctx, uint64_t bytes)
     return RS_OK;
 }
 
-rs_status dataset_destroy(Ctx *ctx, uint64_t h)
+rs_status dataset_destroy(Ctx *ctx, uint64_t h, bool force)
 {
     std::shared_ptr<Dataset> ds;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         auto it = ctx->datasets.find(h);
         if (it == ctx->datasets.end()) { set_error("unknown dataset %llu", (unsigned long long)h); return RS_ERR_NOT_FOUND; }
+        // another reference than the registry's: a call running on the dataset, or a serving
+        // request on it (queued, running or not yet polled) whose kernels would read the freed copy
+        if (!force && it->second.use_count() > 1) {
+            set_error("dataset %llu is in use: a call on it is running, or a serving request on it has not "
+                      "been polled", (unsigned long long)h);
+            return RS_ERR_INVALID;
+        }
         ds = it->second;
         ctx->datasets.erase(it);
         drop_graphs(ctx, h);          // cached graphs that reference this dataset

@@ -225,3 +225,40 @@ def test_served_ranked_units_with_ties_equal_oracle(orc):
         ctx.dataset_destroy(ds)
     finally:
         ctx.close()
+
+
+def test_dataset_in_use_by_a_request_is_not_destroyed(orc):
+    """A dataset that a serving request still holds (queued, running or completed but not yet
+    polled, cancelled ones included) is refused by rs_dataset_destroy, which would otherwise free
+    the device copy that the request's kernels read; once the request is polled it goes."""
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.gaussian_mixture(3000, 12, 3, 7)
+    b = synth.random_rulesets(synth.quantile_table(X), 3, 40, (1, 12), (1, 4), 7)
+    want = orc.eval_hard(X, y, 3, b)
+    ctx = rs.Context(0)
+    try:
+        ds = ctx.dataset(X, y, 3)
+        t = ctx.submit(ds, rs.HostBatch(b))
+        with pytest.raises(rs.RsError) as e:
+            ctx.dataset_destroy(ds)
+        assert e.value.code == -1 and "in use" in str(e.value)
+        c, pc, _ = ctx.poll(t, b.P, 3, timeout_us=60_000_000)
+        assert np.array_equal(c, want[0])
+        ctx.dataset_destroy(ds)
+        with pytest.raises(rs.RsError) as e:
+            ctx.dataset_destroy(ds)
+        assert e.value.code == -7                  # RS_ERR_NOT_FOUND
+        # a cancelled request holds its dataset until it is polled as well
+        ds2 = ctx.dataset(X, y, 3)
+        t2 = ctx.submit(ds2, rs.HostBatch(b))
+        if ctx.cancel(t2) == 0:
+            with pytest.raises(rs.RsError):
+                ctx.dataset_destroy(ds2)
+            with pytest.raises(rs.RsError) as e:
+                ctx.poll(t2, b.P, 3, timeout_us=60_000_000)
+            assert e.value.code == -8              # RS_ERR_CANCELLED
+        else:                                      # admitted before the cancel: poll it
+            assert ctx.poll(t2, b.P, 3, timeout_us=60_000_000) is not None
+        ctx.dataset_destroy(ds2)
+    finally:
+        ctx.close()
