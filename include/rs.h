@@ -478,6 +478,13 @@ rs_status rs_selftest_threshold_rewrite(rs_ctx *ctx, const float *a, const float
 rs_status rs_selftest_log1p_unit(rs_ctx *ctx, const float *e, int32_t n, float *out);
 
 /*
+ * Self-check of the soft forward's log(1 - q) from log q (the log-probability that a rule does not
+ * fire, Sec. 3's soft first-fire product): out[i] = the kernels' log(1 - e^s[i]) for host arrays s
+ * (s <= 0; 0 gives -inf, -inf gives 0), n entries, evaluated on the context's device.
+ */
+rs_status rs_selftest_log1m_exp(rs_ctx *ctx, const float *s, int32_t n, float *out);
+
+/*
  * Fault injection on the host: of the per-call device allocations of the evaluation paths
  * (rs_eval_hard, rs_eval_soft_fwd/bwd, serving admission), the next `skip` succeed and the `count`
  * after them fail as if the device were out of memory (process-wide; count 0 disarms). A call

@@ -47,7 +47,7 @@ rs_status eval_hard_static(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *
                            int32_t *per_class, int32_t *preds, cudaStream_t stream);
 rs_status static_scratch_lookup(unsigned char **out);
 rs_status tile_pick(Ctx *ctx, uint64_t ds_h, const rs_batch *b, int32_t *id);
-rs_status selftest_log1p_unit(const float *e_h, int n, float *out_h, cudaStream_t stream);
+rs_status selftest_soft_math(int which, const float *e_h, int n, float *out_h, cudaStream_t stream);
 rs_status measure_pipe_rates(Ctx *ctx, rs_pipe_rates *out);
 }  // namespace rs
 
@@ -442,7 +442,17 @@ rs_status rs_selftest_log1p_unit(rs_ctx *ctx, const float *e, int32_t n, float *
         if (!ctx || !e || !out || n < 1) return RS_ERR_INVALID;
         rs_status rc = device_guard(ctx);
         if (rc) return rc;
-        return selftest_log1p_unit(e, n, out, nullptr);
+        return selftest_soft_math(0, e, n, out, nullptr);
+    })
+}
+
+rs_status rs_selftest_log1m_exp(rs_ctx *ctx, const float *s, int32_t n, float *out)
+{
+    RS_GUARD({
+        if (!ctx || !s || !out || n < 1) return RS_ERR_INVALID;
+        rs_status rc = device_guard(ctx);
+        if (rc) return rc;
+        return selftest_soft_math(1, s, n, out, nullptr);
     })
 }
 

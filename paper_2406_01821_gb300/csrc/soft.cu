@@ -159,10 +159,6 @@ __device__ __forceinline__ float log1p_unit(float e)
     return e * p;
 }
 
-__global__ void k_selftest_log1p_unit(const float *e, int n, float *out)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = log1p_unit(e[i]);
-}
 
 // The float path's exponentials of non-positive arguments use the hardware approximation
 // (__expf: ex2.approx of x log2(e)); for the arguments that occur here (|x| up to about 100,
@@ -171,6 +167,56 @@ __global__ void k_selftest_log1p_unit(const float *e, int n, float *out)
 // has an absolute error near 1 that is too large relative to log1p of small arguments); the
 // float-float pass keeps expf.
 __device__ __forceinline__ float exp_np(float x) { return __expf(x); }
+
+// log(1 - e^s) for s <= 0: the log-probability that a rule whose conditions hold with
+// probability q = e^s does not fire. Both pieces are evaluated and one is selected (a warp's
+// samples fall on both sides):
+// * q <= e^(-1/2): log1p(-q) = -q a(q), a the degree-10 polynomial of least maximum relative
+//   error against -log1p(-q) / q on [0, e^(-1/2)] (Remez exchange; within 2 ulp given q). q comes
+//   from the hardware exponential, whose relative error (a few 1e-6 at most for the arguments
+//   that matter) becomes that of the result: an absolute error below 1e-7 in the log domain.
+// * t = -s < 1/2: log t + t b(t), b the degree-3 polynomial of least maximum relative error
+//   against log((1 - e^-t) / t) / t on [0, 1/2]; log t = k ln 2 + log m for t = m 2^k, 1 <= m < 2,
+//   with log m from the hardware logarithm, whose error on [1, 2] is at most 2^-21.41 absolute,
+//   whatever k: as t goes to 0 the absolute error stays at that level instead of growing with
+//   |log t| (lu, a sum of these terms, is an absolute quantity in the log domain).
+// s = 0 gives -inf (the rule fires for certain), s = -inf gives -0.
+__device__ __forceinline__ float log1m_exp(float s)
+{
+    const float t = -s;
+    const float q = exp_np(s);
+    float pa = 5.805101871e+00f;
+    pa = fmaf(pa, q, -1.336368465e+01f);
+    pa = fmaf(pa, q, 1.424522972e+01f);
+    pa = fmaf(pa, q, -8.279889107e+00f);
+    pa = fmaf(pa, q, 3.204409838e+00f);
+    pa = fmaf(pa, q, -5.293834209e-01f);
+    pa = fmaf(pa, q, 2.968223989e-01f);
+    pa = fmaf(pa, q, 2.422454804e-01f);
+    pa = fmaf(pa, q, 3.336488008e-01f);
+    pa = fmaf(pa, q, 4.999950230e-01f);
+    pa = fmaf(pa, q, 1.000000000e+00f);
+    const float ra = -q * pa;
+    float pb = -3.432709782e-04f;
+    pb = fmaf(pb, t, -1.679248726e-06f);
+    pb = fmaf(pb, t, 4.166686162e-02f);
+    pb = fmaf(pb, t, -5.000000000e-01f);
+    const bool sub = t < 0x1p-126f;                  // subnormal t: scaled by 2^24 first
+    const int it = __float_as_int(sub ? t * 0x1p24f : t);
+    const float k = (float)((it >> 23) - (sub ? 127 + 24 : 127));
+    const float m = __int_as_float((it & 0x007FFFFF) | 0x3F800000);
+    const float lt = fmaf(k, 6.931471825e-01f, fmaf(k, -1.904654212e-09f, __logf(m)));   // ln 2 as hi + lo
+    const float rb = t == 0.f ? -INFINITY : fmaf(t, pb, lt);
+    return t >= 0.5f ? ra : rb;
+}
+
+// The soft kernels' elementary functions evaluated on the device (test hooks): 0 = log1p_unit,
+// 1 = log1m_exp.
+__global__ void k_selftest_soft_math(const float *in, int n, float *out, int which)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = which == 0 ? log1p_unit(in[i]) : log1m_exp(in[i]);
+}
 
 __device__ __forceinline__ float log_sigmoid(float u)
 {
@@ -635,7 +681,7 @@ __device__ __forceinline__ bool soft_forward(const SoftKArgs &a, int rb, int R, 
             if (lq) lq[j][lane + 32 * v] = s[v];      // kept only for the class probabilities
             lu[j][lane + 32 * v] = lu_r[v];
             if (cls == yn[v]) lpy[v] = log_add(lpy[v], s[v] + lu_r[v]);
-            lu_r[v] += logf(-expm1f(s[v]));
+            lu_r[v] += log1m_exp(s[v]);
         }
     }
     bool big = false;
@@ -1364,21 +1410,22 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     return rc;
 }
 
-// The soft kernels' log1p on [0, 1] evaluated on the device for host inputs (a test hook).
-rs_status selftest_log1p_unit(const float *e_h, int n, float *out_h, cudaStream_t stream)
+// The soft kernels' log1p on [0, 1] (which = 0) or log(1 - e^s) (which = 1) evaluated on the
+// device for host inputs (a test hook).
+rs_status selftest_soft_math(int which, const float *e_h, int n, float *out_h, cudaStream_t stream)
 {
     float *d = nullptr;
     RS_CUDA(dev_alloc_async(&d, sizeof(float) * 2 * (size_t)n, stream));
     rs_status rc = RS_OK;
     cudaError_t e = cudaMemcpyAsync(d, e_h, sizeof(float) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) {
-        k_selftest_log1p_unit<<<std::min((n + 255) / 256, 4096), 256, 0, stream>>>(d, n, d + n);
+        k_selftest_soft_math<<<std::min((n + 255) / 256, 4096), 256, 0, stream>>>(d, n, d + n, which);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_h, d + n, sizeof(float) * n, cudaMemcpyDeviceToHost, stream);
     cudaFreeAsync(d, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) rc = cuda_fail(e, "log1p self-test");
+    if (e != cudaSuccess) rc = cuda_fail(e, "soft math self-test");
     return rc;
 }
 

@@ -148,6 +148,7 @@ _SIGS = {
                                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
     "rs_measure_pipe_rates": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(rs_pipe_rates)]),
     "rs_selftest_log1p_unit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "rs_selftest_log1m_exp": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "rs_inject_alloc_failures": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "rs_selftest_bounded_wait": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
 }

@@ -329,3 +329,36 @@ def test_log1p_unit_against_float64(ctx):
     err = np.abs(out.astype(np.float64) - ref) / ulp
     assert err.max() <= 2.5, (float(err.max()), float(e[np.argmax(err)]))
     assert out[e == 0].tolist() == [0.0]
+
+
+def test_log1m_exp_against_float64(ctx):
+    """The soft forward's log(1 - e^s) (a polynomial in q = e^s for q <= e^-1/2, log t + t b(t) with
+    a range-reduced hardware logarithm for t = -s < 1/2) against float64 log(-expm1(s)) for s from
+    -100 to -1e-38, both sides of the split and the special values: an absolute error of at most
+    4e-7 plus one ulp of the result (the log domain: lu sums these terms), and a relative error of
+    at most 1e-5 where e^s is a normal float (s >= -80)."""
+    from paper_2406_01821_gb300 import rs
+    rng = np.random.default_rng(3)
+    t = np.concatenate([10.0 ** rng.uniform(-38, 2, 200_000), rng.uniform(0.3, 0.7, 50_000),
+                        rng.uniform(0, 100, 50_000)]).astype(np.float32)
+    half = np.float32(0.5)
+    t = np.concatenate([t, np.float32([half, np.nextafter(half, np.float32(0)), np.nextafter(half, np.float32(1)),
+                                       1e-45, 1e-40, 2.0 ** -126, 87.0, 100.0])])
+    s = -t
+    out = np.empty_like(s)
+    rs.check(rs.lib().rs_selftest_log1m_exp(ctx.h, rs._ptr(s), len(s), rs._ptr(out)))
+    sd = s.astype(np.float64)
+    # float64 reference in the form that is accurate on each side (1 - e^s rounds to 1 for s << 0)
+    with np.errstate(divide="ignore"):
+        ref = np.where(sd < -np.log(2.0), np.log1p(-np.exp(sd)), np.log(-np.expm1(np.minimum(sd, -1e-300))))
+    got = out.astype(np.float64)
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    err = np.abs(got - ref)
+    assert (err <= 4e-7 + ulp).all(), (float((err - ulp).max()), float(s[np.argmax(err - ulp)]))
+    normal = sd >= -80.0
+    rel = err[normal] / np.abs(ref[normal])
+    assert rel.max() <= 1e-5, (float(rel.max()), float(s[normal][np.argmax(rel)]))
+    sp = np.float32([0.0, -0.0, -np.inf])
+    o = np.empty_like(sp)
+    rs.check(rs.lib().rs_selftest_log1m_exp(ctx.h, rs._ptr(sp), 3, rs._ptr(o)))
+    assert o[0] == -np.inf and o[1] == -np.inf and o[2] == 0.0
