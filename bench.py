@@ -6,8 +6,10 @@ the C ABI (rs_eval_hard) against a resident dataset. One step = one full populat
 (packing + validation + the evaluator kernel + exact counts). value = nominal condition-evals/s
 (sum over sets and rules of the rule's condition count x N, per second), summed over ranks.
 
-Extra legs on the same line: the soft fine-tuning pass (P=1024 x R=32 x C=4, N=262144, F=64,
-tau=0.1, forward + adjoint). The CPU oracle is timed on a bounded sample of the same workload.
+Extra legs on the same line (N = 1 only): the soft fine-tuning pass (P=1024 x R=32 x C=4,
+N=262144, F=64, tau=0.1, forward + adjoint), the device-resident evolution loop, serving, the
+categorical workload and the paper's plain shape. The CPU oracle is timed on a bounded sample of
+the same workload (N = 1 only; cpu_baseline is null on a multi-GPU line).
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--no-extras]
 Multi-GPU: torchrun --nproc-per-node N bench.py --gpus N  (sample sharding: every rank evaluates
@@ -754,7 +756,9 @@ def main():
               "alu_pipe": counters["alu_pipe_pct"] / 100, "source": "profiles/hard_eval_k_hard5_full.md (N=2^19)"}
              if counters and "issue_active_pct" in counters else None)
     extras = {}
-    if not args.no_extras and d.rank == 0:
+    # the extra legs and the CPU baseline run at N = 1 only (a multi-GPU launch holds every GPU
+    # while rank 0 would run them)
+    if not args.no_extras and d.world == 1:
         skip = parse_skip(args.skip)
         for name, leg in (("soft", soft_leg), ("evolution", evolution_leg),
                           ("serving", serving_leg), ("categorical", categorical_leg), ("plain", plain_leg)):
@@ -766,7 +770,7 @@ def main():
                 extras[name] = {"error": repr(e)}
 
     if d.rank == 0:
-        cb = cpu_baseline(w, args.cpu_sample, single_thread=True)
+        cb = cpu_baseline(w, args.cpu_sample, single_thread=True) if d.world == 1 else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
