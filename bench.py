@@ -226,6 +226,7 @@ def hard_leg(args, rank, dev, ctx_mod, w):
             step()
         e1.record(stream)
         e1.synchronize()
+    ctx_mod.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     prof = ctx.profile(reset=True)
     correct = out[0].cpu().numpy()
@@ -248,12 +249,24 @@ def hard_leg(args, rank, dev, ctx_mod, w):
     import ctypes
     cb = hb.c()
 
+    # several GPUs: the sharded evaluation's exchange step on the host results (up, one int32
+    # all-reduce, down), as the sample-sharded call does it
+    red = torch.empty(P + P * K, dtype=torch.int32, device=dev) if ctx_mod.world > 1 else None
+
     def e2e_call():
         check(lib().rs_eval_hard(ctx2.h, ds2, ctypes.byref(cb), _ptr(hc), _ptr(hpc), None,
                                  _stream_ptr(stream)))
+        if red is not None:
+            with torch.cuda.stream(stream):
+                red[:P].copy_(torch.from_numpy(hc))
+                red[P:].copy_(torch.from_numpy(hpc).view(-1))
+                ctx_mod.pg.all_reduce(red)
+                hc[...] = red[:P].cpu().numpy()
+                hpc[...] = red[P:].view(P, K).cpu().numpy()
     for _ in range(max(1, args.warmup)):
         e2e_call()
     stream.synchronize()
+    ctx_mod.barrier()
     t0 = time.perf_counter()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
@@ -263,7 +276,7 @@ def hard_leg(args, rank, dev, ctx_mod, w):
     f1.record(stream)
     f1.synchronize()
     e2e_ms = max(f0.elapsed_time(f1), (time.perf_counter() - t0) * 1e3) / args.steps
-    e2e_ok = bool(np.array_equal(hc, correct)) if ctx_mod.world == 1 else None   # shard counts vs summed
+    e2e_ok = bool(np.array_equal(hc, correct))       # several GPUs: both are the summed counts
     ctx2.close()
     # one more call, untimed, in a context whose evaluator counts the work it does
     ctx3 = rs.Context(dev, flags=rs.CTX_COUNT_WORK | rs.CTX_NO_GRAPH)
@@ -278,8 +291,9 @@ def hard_leg(args, rank, dev, ctx_mod, w):
         prof[f] = walked[f]
     prof["counted_launches"] = 1
     ctx.close()
+    xfer = 0 if red is None else red.numel() * 4      # the exchange's own copies
     return {"ms": ms, "prof": prof, "tile": tile, "clocks": clk.summary(), "e2e_ms": e2e_ms,
-            "e2e_ok": e2e_ok, "h2d": hb_nbytes(hb), "d2h": hc.nbytes + hpc.nbytes}
+            "e2e_ok": e2e_ok, "h2d": hb_nbytes(hb) + xfer, "d2h": hc.nbytes + hpc.nbytes + xfer}
 
 
 def hb_nbytes(hb):
