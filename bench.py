@@ -439,16 +439,17 @@ def soft_transcendentals(batch, N):
     return N * (3 * batch.C + 11 * batch.R)
 
 
-def evolution_leg(args, dev):
+def evolution_leg(args, dev, G: int = 200, arms: bool = True):
     """Device-resident evolution: population 10,000 (R <= 32, C <= 6), 200 generations on
     N=100,000 x F=32 two-class data, the best 64 fine-tuned (50 Adam steps) every 10 generations.
     Compared with two plain arms per generation: the CPU oracle (evaluation + evolution on the host
-    cores) and host-driven evolution with one GPU evaluation launch per generation."""
+    cores) and host-driven evolution with one GPU evaluation launch per generation (arms=False:
+    the device loop alone, e.g. G=10 for a launch list of one fine-tuning round)."""
     import torch
     import oracle
     from paper_2406_01821_gb300 import rs, synth
     X, y = synth.evolution_data(seed=0)
-    P, RMAX, CMAX, G = 10000, 32, 6, 200
+    P, RMAX, CMAX = 10000, 32, 6
     pop = synth.initial_population(X, y, 2, P, RMAX, CMAX, seed=0)
     ctx = rs.Context(dev)
     ds = ctx.dataset(X, y, 2)
@@ -461,6 +462,11 @@ def evolution_leg(args, dev):
     t0 = time.perf_counter()
     ctx.evolve(ds, pop, generations=G, elite=100, seed=1, stream=stream)
     t_plain_gpu = time.perf_counter() - t0
+    if not arms:
+        ctx.close()
+        return {"workload": f"evolution P={P} R<=32 C<=6 N={len(X)} F=32 K=2 generations={G} "
+                            "tune top-64 x 50 Adam steps every 10",
+                "generations_per_s": G / t_tuned, "generations_per_s_without_tuning": G / t_plain_gpu}
     # host-driven arm: one evaluation launch per generation, evolution on the host
     hb_gens = 3
     t0 = time.perf_counter()
@@ -711,9 +717,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=524288)
-    ap.add_argument("--workload", default="ragged", choices=["ragged", "ragged-small", "soft-small"],
-                    help="ragged-small (N=2^19, P=512) and soft-small (soft leg only, N=65536, "
-                         "P=256) are the cases used for ncu captures")
+    ap.add_argument("--workload", default="ragged", choices=["ragged", "ragged-small", "soft-small", "evolution-small"],
+                    help="ragged-small (N=2^19, P=512), soft-small (soft leg only, N=65536, P=256) and "
+                         "evolution-small (the evolution loop alone, 10 generations: one fine-tuning "
+                         "round) are the cases used for ncu captures")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", type=int, default=None, help="force a tile configuration id")
     ap.add_argument("--skip", default="", help="comma-separated extra legs to skip (soft,evolution,serving,categorical,plain)")
@@ -735,6 +742,10 @@ def main():
     torch.cuda.set_device(dev)
     if args.workload == "soft-small":
         print(json.dumps({"soft": soft_leg(args, dev)}), flush=True)
+        d.close()
+        return
+    if args.workload == "evolution-small":
+        print(json.dumps({"evolution": evolution_leg(args, dev, G=10, arms=False)}), flush=True)
         d.close()
         return
     if args.workload == "ragged-small":
