@@ -1225,10 +1225,10 @@ static rs_status soft_run(Ctx *ctx, const SoftArgs &s, int known_maxR, int known
     const int64_t Ccap = std::max<int64_t>(b.C, 1);     // capacity when sizes are device-side
     if (P == 0) return RS_OK;
     // Sample chunks: about 1024 samples each, and for small problems as many as it takes to give
-    // every SM some 32 (set, chunk) items, down to one 64-sample group per chunk. The chunking is
+    // every SM some 64 (set, chunk) items, down to one 64-sample group per chunk. The chunking is
     // a function of (N, P, SM count) only, so repeated calls sum in the same order.
     const int64_t groups = (s.N + SOFT_G - 1) / SOFT_G;
-    const int64_t want = std::max<int64_t>((s.N + 1023) / 1024, ((int64_t)ctx->sm_count * 32 + P - 1) / P);
+    const int64_t want = std::max<int64_t>((s.N + 1023) / 1024, ((int64_t)ctx->sm_count * 64 + P - 1) / P);
     int nchunks = (int)std::min<int64_t>(std::min<int64_t>(SOFT_MAX_CHUNKS, groups), want);
     if (nchunks < 1) nchunks = 1;
     int64_t chunk = (s.N + nchunks - 1) / nchunks;
