@@ -413,8 +413,9 @@ rs_status rs_tile_config_info(int32_t id, int32_t *samples_per_tile, int32_t *wa
  * The other configurations stage a feature tile in shared memory and need F small enough for
  * it; configuration 23 (form 1) reads the features from global memory and takes any F. */
 rs_status rs_tile_config_form(int32_t id, int32_t *form);
-/* Force configuration `id` for every following hard evaluation of the context (-1 = automatic:
- * autotuned table, else heuristic). */
+/* Force configuration `id` for every following hard evaluation of the context, those of
+ * rs_evolve included (-1 = automatic: autotuned table, else heuristic; rs_evolve then takes the
+ * heuristic). */
 rs_status rs_set_tile_config(rs_ctx *ctx, int32_t id);
 /* The configuration the next rs_eval_hard of `batch` on `ds` would use: the forced one
  * (rs_set_tile_config), else the tuned one for the batch's shape key (feature count, class count,

@@ -638,7 +638,10 @@ rs_status evolve_run(Ctx *ctx, uint64_t ds_h, const rs_evolve_config *cfg, rs_po
     RS_CUDA(cudaMemsetAsync(sc.status, 0, 4, s));
 
     DataView dv{ds.Xt, ds.inv, ds.N, ds.n_pad, ds.F, ds.K};
-    const TileConfig &tc = tile_config(heuristic_tile_for(ds));
+    // a configuration forced on the context (rs_set_tile_config) applies here too, else the heuristic
+    const TileConfig &tc = tile_config(ctx->forced_tile >= 0 && tile_config_fits(tile_config(ctx->forced_tile), ds.F)
+                                           ? ctx->forced_tile
+                                           : heuristic_tile_for(ds));
     auto evaluate = [&](int nsub, int32_t *out_fit, cudaStream_t st) -> rs_status {
         BatchDev bd{};
         bd.P = nsub;

@@ -47,6 +47,28 @@ def test_evolution_matches_oracle_bit_exact(ctx, orc, seed, K):
     assert np.allclose(mean, wmean, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("tile", [21, 18, 23])
+def test_forced_tile_configuration_gives_the_same_evolution(ctx, orc, tile):
+    """rs_set_tile_config applies to the loop's evaluations too: a forced configuration (another
+    evaluator form) gives the oracle's trajectory bit for bit, as the default one does."""
+    from paper_2406_01821_gb300 import rs
+    X, y = synth.gaussian_mixture(2501, 7, 3, 21)
+    pop = synth.initial_population(X, y, 3, 64, RMAX=6, CMAX=3, seed=21)
+    c2 = rs.Context(0)
+    ds = c2.dataset(X, y, 3)
+    try:
+        c2.set_tile_config(tile)
+        got, fit, best, mean = c2.evolve(ds, pop, generations=3, elite=2, seed=21)
+    finally:
+        c2.dataset_destroy(ds)
+        c2.close()
+    want, wfit, wbest, _ = oracle_run(orc, X, y, 3, pop, 3, 2, 21)
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+    assert np.array_equal(fit, wfit)
+    assert np.array_equal(best, wbest)
+
+
 def test_lamarckian_tuning_keeps_best_monotone(ctx, orc):
     X, y = synth.two_class_gaussian(4000, 8, 5)
     pop = synth.initial_population(X, y, 2, 64, RMAX=6, CMAX=3, seed=5)
