@@ -159,7 +159,6 @@ __device__ __forceinline__ float log1p_unit(float e)
     return e * p;
 }
 
-
 // The float path's exponentials of non-positive arguments use the hardware approximation
 // (__expf: ex2.approx of x log2(e)); for the arguments that occur here (|x| up to about 100,
 // beyond which the float-float pass takes over for the terms that matter) its relative error
