@@ -446,7 +446,6 @@ def evolution_leg(args, dev, G: int = 200, arms: bool = True):
     cores) and host-driven evolution with one GPU evaluation launch per generation (arms=False:
     the device loop alone, e.g. G=10 for a launch list of one fine-tuning round)."""
     import torch
-    import oracle
     from paper_2406_01821_gb300 import rs, synth
     X, y = synth.evolution_data(seed=0)
     P, RMAX, CMAX = 10000, 32, 6
@@ -467,6 +466,7 @@ def evolution_leg(args, dev, G: int = 200, arms: bool = True):
         return {"workload": f"evolution P={P} R<=32 C<=6 N={len(X)} F=32 K=2 generations={G} "
                             "tune top-64 x 50 Adam steps every 10",
                 "generations_per_s": G / t_tuned, "generations_per_s_without_tuning": G / t_plain_gpu}
+    import oracle                 # the plain arms: the oracle's evolution step on the host
     # host-driven arm: one evaluation launch per generation, evolution on the host
     hb_gens = 3
     t0 = time.perf_counter()
