@@ -6,9 +6,10 @@
 // the exact product is monotone and round-to-nearest is monotone, including in the subnormal
 // and overflow ranges. Hence the set {x : fl(a*x) op t} is an up-set or a down-set of the
 // ordered float32 line and equals {x > c} or {x < c} for one float32 c (NaN x is false in both
-// forms). c is found by binary search over the 2^32 ordered bit patterns, evaluating the
-// condition itself with a correctly rounded multiply, so the rewrite is exact by construction
-// (and checked exhaustively by rs_selftest_threshold_rewrite).
+// forms). c is where the condition's truth changes: looked for first within a few floats of the
+// quotient t / a, else by binary search over the 2^32 ordered bit patterns, in both cases by
+// evaluating the condition itself with a correctly rounded multiply, so the rewrite is exact by
+// construction (and checked exhaustively by rs_selftest_threshold_rewrite).
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -31,6 +32,34 @@ __device__ inline bool thr_true(float a, float x, float t, int op)
     return op == 0 ? (p > t) : (p < t);
 }
 
+// The transition of the condition's truth over the ordered float line, searched near the
+// correctly rounded quotient t / a: where products are normal numbers it lies within a float or
+// two of it. up: false below, true above (returns the last false key); else true below, false
+// above (returns the first false key). At most six steps, never past +-inf; a transition is only
+// returned once both of its sides were evaluated, and the predicate is monotone with a single
+// transition, so the result is the one the binary search finds. false: not found nearby.
+__device__ bool transition_near_quotient(float a, float t, int op, bool up, uint32_t &out)
+{
+    const float q = __fdiv_rn(t, a);
+    if (!(fabsf(q) <= 3.0e38f)) return false;
+    const uint32_t kmin = fkey(__uint_as_float(0xFF800000u)), kmax = fkey(__uint_as_float(0x7F800000u));
+    uint32_t k = fkey(q);
+    const auto on = [&](uint32_t kk) { return thr_true(a, keyf(kk), t, op); };
+    const bool here = on(k);
+    for (int i = 0; i < 6; ++i) {
+        if (up == here) {            // on the side the transition is below: step down
+            if (k <= kmin) return false;
+            if (on(k - 1) != here) { out = up ? k - 1 : k; return true; }
+            --k;
+        } else {                     // step up
+            if (k >= kmax) return false;
+            if (on(k + 1) != here) { out = up ? k : k + 1; return true; }
+            ++k;
+        }
+    }
+    return false;
+}
+
 // Rewrite  fl(a*x) op t  into (kind, v0, v1).
 __device__ void rewrite_threshold(float a, float t, int op, uint32_t &kind, float &v0, float &v1)
 {
@@ -42,6 +71,8 @@ __device__ void rewrite_threshold(float a, float t, int op, uint32_t &kind, floa
     if (up) {
         // false at -inf always; true somewhere iff true at +inf
         if (!thr_true(a, pinf, t, op)) { kind = KIND_NEVER; v0 = 0.f; v1 = 0.f; return; }
+        uint32_t k;
+        if (transition_near_quotient(a, t, op, true, k)) { kind = KIND_GT; v0 = keyf(k); v1 = 0.f; return; }
         while (hi - lo > 1u) {        // invariant: false at lo, true at hi
             uint32_t mid = lo + (hi - lo) / 2u;
             if (thr_true(a, keyf(mid), t, op)) hi = mid; else lo = mid;
@@ -50,6 +81,8 @@ __device__ void rewrite_threshold(float a, float t, int op, uint32_t &kind, floa
     } else {
         // false at +inf always; true somewhere iff true at -inf
         if (!thr_true(a, ninf, t, op)) { kind = KIND_NEVER; v0 = 0.f; v1 = 0.f; return; }
+        uint32_t k;
+        if (transition_near_quotient(a, t, op, false, k)) { kind = KIND_LT; v0 = keyf(k); v1 = 0.f; return; }
         while (hi - lo > 1u) {        // invariant: true at lo, false at hi
             uint32_t mid = lo + (hi - lo) / 2u;
             if (thr_true(a, keyf(mid), t, op)) lo = mid; else hi = mid;

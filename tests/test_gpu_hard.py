@@ -266,6 +266,19 @@ def test_threshold_rewrite_exhaustive(ctx):
     assert mm == 0
 
 
+def test_threshold_rewrite_exhaustive_random(ctx):
+    """Random coefficients and thresholds over the whole exponent range (normal products, where the
+    cut is found next to t / a, and subnormal or overflowing ones, where the binary search finds
+    it): for every float32 x, fl(a*x) op t equals the rewritten single compare."""
+    rng = np.random.default_rng(17)
+    n = 24
+    a = (rng.choice([-1.0, 1.0], n) * 10.0 ** np.concatenate([rng.uniform(-3, 3, n - 8), rng.uniform(-40, 38, 8)]))
+    t = (rng.choice([-1.0, 1.0], n) * 10.0 ** np.concatenate([rng.uniform(-3, 3, n - 8), rng.uniform(-45, 38, 8)]))
+    op = rng.integers(0, 2, n).astype(np.int8)
+    mm = ctx.selftest_threshold_rewrite(a.astype(np.float32), t.astype(np.float32), op)
+    assert mm == 0
+
+
 def test_ragged_full_size_sampled(ctx, orc):
     """The full ragged workload (P=4096, N=2^20, F=128, 10 classes) in the benchmark's launch
     configuration; sampled sets are recomputed one by one by the oracle, and every set satisfies
