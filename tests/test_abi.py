@@ -96,3 +96,14 @@ def test_device_batch_struct_follows_its_arrays():
     assert db.c().cond_set == t["cond_set"].data_ptr()
     db.P -= 1
     assert db.c().P == b.P - 1
+
+
+def test_c_consumer_compiles_and_links(lib, tmp_path):
+    """A strict C99 program that includes rs.h and calls the library through it compiles without
+    warnings and links against librs.so: the header is valid C and agrees with the exports."""
+    import c_consumer
+    try:
+        exe = c_consumer.build(str(tmp_path))
+    except FileNotFoundError:
+        pytest.skip("no C compiler")
+    assert os.path.exists(exe)
